@@ -1,0 +1,203 @@
+"""FP64 CPU oracle for the two-level granular method (arXiv 2308.01629).
+
+TEST INFRASTRUCTURE ONLY.  The tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` are the only callers.  The product library never
+imports this package and this package never imports the product; the two
+meet only through the seeded arrays of the ``scenes`` package.
+
+The arithmetic lives in ``gs_oracle.c`` (plain C, double precision, compiled
+with ``-ffp-contract=off``); this module compiles it with gcc on first use and
+marshals numpy arrays through ctypes.  Each wrapper names the passage of the
+paper the C function follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gs_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+
+SDF_STRIDE = 20
+UP_KEYS = ["r_low", "r_high", "dt", "gx", "gy", "gz", "c1", "c2", "eps_w", "eps_x"]
+PB_KEYS = ["r", "dt", "gx", "gy", "gz", "mu_s", "mu_k", "n_stab", "iters", "mass_k",
+           "ground_z", "rc", "friction_mode", "eps_x"]
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile gs_oracle.c into _build/liboracle.so (OpenMP when available)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+            "-fno-fast-math", _SRC, "-o", _LIB_PATH + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
+    return _LIB_PATH
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        L.or_set_threads.argtypes = [ctypes.c_int]
+        L.or_max_threads.restype = ctypes.c_int
+        L.or_grid.argtypes = [ctypes.c_double, P, P, P, P, P, P]
+        L.or_grid.restype = ctypes.c_int
+        L.or_cell_keys.argtypes = [P, ctypes.c_long, P, ctypes.c_float, P, ctypes.c_int, P]
+        L.or_counting_sort.argtypes = [P, ctypes.c_long, ctypes.c_long, P, P]
+        L.or_counting_sort.restype = ctypes.c_int
+        L.or_weight.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.or_weight.restype = ctypes.c_double
+        L.or_sdf_eval.argtypes = [P, P, P, P, P, ctypes.c_double]
+        L.or_sdf_eval.restype = ctypes.c_int
+        L.or_upsample.argtypes = [P, P, ctypes.c_long, P, P, ctypes.c_long, P, ctypes.c_long,
+                                  P, ctypes.c_int, P, ctypes.c_int, P, P, P, P, P, P]
+        L.or_upsample.restype = ctypes.c_int
+        L.or_pbd_step.argtypes = [P, P, P, ctypes.c_long, P, ctypes.c_int, P, ctypes.c_int, P, P]
+        L.or_pbd_step.restype = ctypes.c_int
+        L.or_pairs_within.argtypes = [P, ctypes.c_long, P, ctypes.c_long, ctypes.c_double, P, P, ctypes.c_long]
+        L.or_pairs_within.restype = ctypes.c_long
+        L.or_pairs_within_grid.argtypes = L.or_pairs_within.argtypes
+        L.or_pairs_within_grid.restype = ctypes.c_long
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a, cols=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if cols is not None:
+        a = np.ascontiguousarray(a.reshape(-1, cols))
+    return a
+
+
+def set_threads(n: int) -> None:
+    _L().or_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(_L().or_max_threads())
+
+
+# ---------------------------------------------------------------- grid ---
+def grid(r_low, box_lo, box_hi):
+    """Cell contract of the neighbour grid: (origin f32[3], h, inv_h, dims)."""
+    o = np.zeros(3, np.float32)
+    h = np.zeros(1, np.float32)
+    ih = np.zeros(1, np.float32)
+    dims = np.zeros(3, np.int32)
+    rc = _L().or_grid(float(r_low), _ptr(_f64(box_lo)), _ptr(_f64(box_hi)), _ptr(o), _ptr(h),
+                      _ptr(ih), _ptr(dims))
+    if rc != 0:
+        raise ValueError("invalid grid arguments")
+    return o, float(h[0]), np.float32(ih[0]), dims
+
+
+def cell_keys(pos4, o, inv_h, dims, fine=False):
+    """Cell id (or 8*cell + octant when fine) of each float4 position."""
+    pos4 = np.ascontiguousarray(np.asarray(pos4, dtype=np.float32).reshape(-1, 4))
+    keys = np.zeros(len(pos4), np.uint32)
+    _L().or_cell_keys(_ptr(pos4), len(pos4), _ptr(np.asarray(o, np.float32)), ctypes.c_float(inv_h),
+                      _ptr(np.asarray(dims, np.int32)), int(bool(fine)), _ptr(keys))
+    return keys
+
+
+def counting_sort(keys, nkeys):
+    """Stable counting sort: (sorted_idx, start[nkeys+1])."""
+    keys = np.ascontiguousarray(keys, dtype=np.uint32)
+    idx = np.zeros(len(keys), np.uint32)
+    start = np.zeros(int(nkeys) + 1, np.uint32)
+    rc = _L().or_counting_sort(_ptr(keys), len(keys), int(nkeys), _ptr(idx), _ptr(start))
+    if rc != 0:
+        raise ValueError("key out of range")
+    return idx, start
+
+
+# ----------------------------------------------------------- upsampling ---
+def weight(d2, r_low):
+    """Sec. 4 distance weight w = max(0, (1 - d^2 / (9 r_LR^2))^3)."""
+    return _L().or_weight(float(d2), float(r_low))
+
+
+def sdf_eval(rec, x, eps=0.0):
+    rec = _f64(rec)
+    phi = np.zeros(6)
+    n = np.zeros(18)
+    tie = np.zeros(1, np.int32)
+    nc = _L().or_sdf_eval(_ptr(rec), _ptr(_f64(x)), _ptr(phi), _ptr(n), _ptr(tie), float(eps))
+    return phi[:nc], n[:3 * nc].reshape(nc, 3), bool(tie[0])
+
+
+def _prm(d, keys):
+    return np.array([float(d[k]) for k in keys], dtype=np.float64)
+
+
+def upsample(lr_x, lr_v, hr_x, hr_v, sdf, prm, sub=None, mode=0):
+    """One HR frame of Sec. 4 for HR particles ``sub`` (all when None).
+
+    ``prm`` holds r_low, r_high, dt, gx, gy, gz, c1, c2, eps_w, eps_x.
+    Returns dict(x, v, flag, alt_x, alt_v, diag) with diag = (S, wmax, alpha, n).
+    """
+    lr_x, lr_v = _f64(lr_x, 3), _f64(lr_v, 3)
+    hr_x, hr_v = _f64(hr_x, 3), _f64(hr_v, 3)
+    sdf = _f64(sdf, SDF_STRIDE) if sdf is not None and len(sdf) else np.zeros((0, SDF_STRIDE))
+    p = _prm(prm, UP_KEYS)
+    subv = None if sub is None else np.ascontiguousarray(sub, dtype=np.int64)
+    n = len(hr_x) if subv is None else len(subv)
+    out = dict(x=np.zeros((n, 3)), v=np.zeros((n, 3)), flag=np.zeros(n, np.int32),
+               alt_x=np.zeros((n, 3)), alt_v=np.zeros((n, 3)), diag=np.zeros((n, 4)))
+    rc = _L().or_upsample(_ptr(lr_x), _ptr(lr_v), len(lr_x), _ptr(hr_x), _ptr(hr_v), len(hr_x),
+                          _ptr(subv), 0 if subv is None else len(subv), _ptr(sdf), len(sdf), _ptr(p),
+                          int(mode), _ptr(out["x"]), _ptr(out["v"]), _ptr(out["flag"]),
+                          _ptr(out["alt_x"]), _ptr(out["alt_v"]), _ptr(out["diag"]))
+    if rc != 0:
+        raise RuntimeError(f"or_upsample failed ({rc})")
+    return out
+
+
+# ------------------------------------------------------------- LR step ---
+def pbd_step(x, v, inv_m, sdf, prm, mode=0):
+    """One LR time step of Algorithm 1.  Returns (x, v, suspect, stats)."""
+    x, v = _f64(x, 3).copy(), _f64(v, 3).copy()
+    inv_m = _f64(inv_m)
+    sdf = _f64(sdf, SDF_STRIDE) if sdf is not None and len(sdf) else np.zeros((0, SDF_STRIDE))
+    p = _prm(prm, PB_KEYS)
+    sus = np.zeros(len(x), np.int32)
+    stats = np.zeros(4, np.int64)
+    rc = _L().or_pbd_step(_ptr(x), _ptr(v), _ptr(inv_m), len(x), _ptr(sdf), len(sdf), _ptr(p),
+                          int(mode), _ptr(sus), _ptr(stats))
+    if rc != 0:
+        raise RuntimeError(f"or_pbd_step failed ({rc})")
+    return x, v, sus.astype(bool), dict(pairs=int(stats[0]), ambiguous=int(stats[1]),
+                                        max_candidates=int(stats[2]), active=int(stats[3]))
+
+
+def pairs_within(a, b, R, use_grid=False):
+    """All (i, j) with |a_i - b_j| < R, sorted by (i, j)."""
+    a, b = _f64(a, 3), _f64(b, 3)
+    fn = _L().or_pairs_within_grid if use_grid else _L().or_pairs_within
+    n = fn(_ptr(a), len(a), _ptr(b), len(b), float(R), None, None, 0)
+    if n < 0:
+        raise RuntimeError("pair search failed")
+    oi = np.zeros(max(n, 1), np.int64)
+    oj = np.zeros(max(n, 1), np.int64)
+    fn(_ptr(a), len(a), _ptr(b), len(b), float(R), _ptr(oi), _ptr(oj), n)
+    return oi[:n], oj[:n]

@@ -1,0 +1,776 @@
+/*
+ * gs_oracle.c -- plain, slow FP64 CPU oracle for the two-level granular
+ * method of "Interactive High-Resolution Simulation of Granular Material"
+ * (arXiv 2308.01629): the low-resolution (LR) position-based-dynamics step of
+ * Sec. 3 / Algorithm 1 and the high-resolution (HR) upsampling of Sec. 4.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or helper with the CUDA library; both sides are written from
+ * the paper independently and meet only through seeded input arrays.
+ *
+ * Conventions (all arrays row-major, caller-owned):
+ *   positions / velocities: double[n][3]; z is up, gravity is a parameter.
+ *   SDF records: double[20] = {kind, p[12], u_b[3], mu_s, mu_k, 0, 0}
+ *     kind 1 = box interior   p = lo[3], hi[3]          (6 half-space walls)
+ *     kind 2 = cone shell     p = cx, cy, z_out, R_out, z_top, R_top, half
+ *                             thickness (a segment in (rho, z) revolved
+ *                             about the vertical axis through (cx, cy))
+ *     kind 3 = solid box      p = centre[3], half extents[3]
+ *   u_b is the velocity of the boundary (kinematic SDFs).
+ *
+ * Readings of silent or garbled passages are listed next to the code that
+ * implements them.  Every decision taken on a floating-point comparison is
+ * checked against a margin; decisions inside the margin are reported so that
+ * a lower-precision implementation can be compared against both branches.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_SDF_STRIDE 20
+#define OR_MAX_COMP 6
+
+enum { SDF_BOX_INTERIOR = 1, SDF_CONE_SHELL = 2, SDF_SOLID_BOX = 3 };
+
+/* upsampling parameters, prm[] indices */
+enum { UP_R_LOW = 0, UP_R_HIGH, UP_DT, UP_GX, UP_GY, UP_GZ, UP_C1, UP_C2,
+       UP_EPS_W, UP_EPS_X, UP_NPRM };
+/* LR step parameters, prm[] indices */
+enum { PB_R = 0, PB_DT, PB_GX, PB_GY, PB_GZ, PB_MU_S, PB_MU_K, PB_N_STAB,
+       PB_ITERS, PB_MASS_K, PB_GROUND_Z, PB_RC, PB_FRIC_MODE, PB_EPS_X,
+       PB_NPRM };
+
+static int g_threads = 1;
+
+void or_set_threads(int n) { g_threads = n > 0 ? n : 1; }
+int or_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_num_procs();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------ */
+/* small vector helpers                                                 */
+/* ------------------------------------------------------------------ */
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* ------------------------------------------------------------------ */
+/* Uniform-grid cell contract (neighbour search, Sec. 5.1 uses a        */
+/* compact-hashing grid; this library fixes a dense grid instead).      */
+/*   cell side  h = 3 r_LR (1 + 2^-10), rounded once to float           */
+/*   inv_h = float(1/h), origin o = float(box_lo), dims = ceil(L/h)     */
+/*   a = (x - o) * inv_h evaluated in float, no contraction            */
+/*   sub = clamp(floor(2a), 0, 2 dim - 1); cell = sub >> 1              */
+/*   cell id = (cz*dy + cy)*dx + cx; fine key = 8*cell + octant bits     */
+/* The factor (1 + 2^-10) keeps every pair closer than 3 r_LR within    */
+/* one cell of each other after float rounding of a.                    */
+/* ------------------------------------------------------------------ */
+int or_grid(double r_low, const double* lo, const double* hi, float* o, float* h, float* inv_h, int* dims)
+{
+    if (!(r_low > 0)) return -1;
+    double hd = 3.0 * r_low * (1.0 + 1.0 / 1024.0);
+    float hf = (float)hd;
+    *h = hf;
+    *inv_h = (float)(1.0 / (double)hf);
+    for (int k = 0; k < 3; ++k) {
+        if (!(hi[k] > lo[k])) return -1;
+        o[k] = (float)lo[k];
+        double n = ceil((hi[k] - lo[k]) / (double)hf);
+        dims[k] = n < 1 ? 1 : (int)n;
+    }
+    return 0;
+}
+
+
+void or_cell_keys(const float* pos4, long n, const float* o, float inv_h, const int* dims, int fine, uint32_t* keys)
+{
+    for (long i = 0; i < n; ++i) {
+        int s[3];
+        for (int k = 0; k < 3; ++k) {
+            float a = (pos4[4 * i + k] - o[k]) * inv_h;   /* float, no FMA (-ffp-contract=off) */
+            float f = floorf(a * 2.0f);
+            int si;
+            if (!(f >= 0.0f)) si = 0;                       /* negative (or NaN) -> 0 */
+            else if (f >= (float)(2 * dims[k] - 1)) si = 2 * dims[k] - 1;
+            else si = (int)f;
+            s[k] = si;
+        }
+        uint32_t cell = ((uint32_t)(s[2] >> 1) * (uint32_t)dims[1] + (uint32_t)(s[1] >> 1)) * (uint32_t)dims[0]
+                        + (uint32_t)(s[0] >> 1);
+        if (fine)
+            keys[i] = cell * 8u + (uint32_t)((s[2] & 1) * 4 + (s[1] & 1) * 2 + (s[0] & 1));
+        else
+            keys[i] = cell;
+    }
+}
+
+/* Stable counting sort of keys in [0, nkeys): start[c] = first slot of key c,
+ * sorted_idx lists element indices by (key, index).  Sequential scatter in
+ * index order is what makes it stable. */
+int or_counting_sort(const uint32_t* keys, long n, long nkeys, uint32_t* sorted_idx, uint32_t* start)
+{
+    uint32_t* cursor = (uint32_t*)calloc((size_t)nkeys + 1, sizeof(uint32_t));
+    if (!cursor) return -1;
+    for (long i = 0; i < n; ++i) {
+        if ((long)keys[i] >= nkeys) { free(cursor); return -2; }
+        cursor[keys[i] + 1]++;
+    }
+    for (long c = 0; c < nkeys; ++c) cursor[c + 1] += cursor[c];
+    memcpy(start, cursor, ((size_t)nkeys + 1) * sizeof(uint32_t));
+    for (long i = 0; i < n; ++i) sorted_idx[cursor[keys[i]]++] = (uint32_t)i;
+    free(cursor);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Oracle-private neighbour search: a plain grid with cell side R over  */
+/* the bounding box of the points.  It returns, for one query point,    */
+/* every point index with |x_q - x_j|^2 < R^2 in ascending order, so    */
+/* sums taken over it equal the brute-force sums bit for bit.           */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double R, lo[3];
+    long dim[3];
+    long* start;   /* ncell + 1 */
+    long* idx;     /* n */
+    const double* x;
+    long n;
+} or_grid_t;
+
+static int grid_build(or_grid_t* g, const double* x, long n, double R)
+{
+    memset(g, 0, sizeof(*g));
+    g->R = R;
+    g->x = x;
+    g->n = n;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k) { lo[k] = n ? x[k] : 0; hi[k] = lo[k]; }
+    for (long i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) {
+            if (x[3 * i + k] < lo[k]) lo[k] = x[3 * i + k];
+            if (x[3 * i + k] > hi[k]) hi[k] = x[3 * i + k];
+        }
+    long ncell = 1;
+    for (int k = 0; k < 3; ++k) {
+        g->lo[k] = lo[k];
+        long d = (long)floor((hi[k] - lo[k]) / R) + 1;
+        if (d > 1024) d = 1024;
+        g->dim[k] = d;
+        ncell *= d;
+    }
+    g->start = (long*)calloc((size_t)ncell + 1, sizeof(long));
+    g->idx = (long*)malloc((size_t)(n ? n : 1) * sizeof(long));
+    long* cell = (long*)malloc((size_t)(n ? n : 1) * sizeof(long));
+    if (!g->start || !g->idx || !cell) { free(cell); return -1; }
+    for (long i = 0; i < n; ++i) {
+        long c[3];
+        for (int k = 0; k < 3; ++k) {
+            long v = (long)floor((x[3 * i + k] - g->lo[k]) / R);
+            c[k] = v < 0 ? 0 : (v >= g->dim[k] ? g->dim[k] - 1 : v);
+        }
+        cell[i] = (c[2] * g->dim[1] + c[1]) * g->dim[0] + c[0];
+        g->start[cell[i] + 1]++;
+    }
+    for (long c = 0; c < ncell; ++c) g->start[c + 1] += g->start[c];
+    long* cur = (long*)malloc((size_t)ncell * sizeof(long));
+    if (!cur) { free(cell); return -1; }
+    memcpy(cur, g->start, (size_t)ncell * sizeof(long));
+    for (long i = 0; i < n; ++i) g->idx[cur[cell[i]]++] = i;
+    free(cur);
+    free(cell);
+    return 0;
+}
+
+static void grid_free(or_grid_t* g) { free(g->start); free(g->idx); }
+
+static int cmp_long(const void* a, const void* b)
+{
+    long x = *(const long*)a, y = *(const long*)b;
+    return (x > y) - (x < y);
+}
+
+/* Collect points within R of q (strict), ascending.  Returns the count;
+ * out must hold n entries.  Points were binned with clamped cell
+ * coordinates; clamping is monotone, so clamping the query's cell range
+ * (widened by one cell against rounding) still covers every point in
+ * reach, and each cell is visited once. */
+static long grid_query(const or_grid_t* g, const double* q, long* out)
+{
+    long c0[3], c1[3], m = 0;
+    for (int k = 0; k < 3; ++k) {
+        double a = floor((q[k] - g->R - g->lo[k]) / g->R) - 1;
+        double b = floor((q[k] + g->R - g->lo[k]) / g->R) + 1;
+        double top = (double)(g->dim[k] - 1);
+        c0[k] = (long)(a < 0 ? 0 : (a > top ? top : a));
+        c1[k] = (long)(b < 0 ? 0 : (b > top ? top : b));
+    }
+    double R2 = g->R * g->R;
+    for (long cz = c0[2]; cz <= c1[2]; ++cz)
+        for (long cy = c0[1]; cy <= c1[1]; ++cy)
+            for (long cx = c0[0]; cx <= c1[0]; ++cx) {
+                long cid = (cz * g->dim[1] + cy) * g->dim[0] + cx;
+                for (long p = g->start[cid]; p < g->start[cid + 1]; ++p) {
+                    long j = g->idx[p];
+                    double d[3] = {g->x[3 * j] - q[0], g->x[3 * j + 1] - q[1], g->x[3 * j + 2] - q[2]};
+                    if (dot3(d, d) < R2) out[m++] = j;
+                }
+            }
+    qsort(out, (size_t)m, sizeof(long), cmp_long);
+    return m;
+}
+
+/* ------------------------------------------------------------------ */
+/* Analytic SDF boundaries.  The paper samples boundaries with          */
+/* infinite-mass particles (Sec. 3, rigid bodies and domain             */
+/* boundaries); this library uses analytic signed distance functions    */
+/* instead and treats each active SDF contact as a pair whose partner   */
+/* has inverse mass 0.  Returns the number of contact components (6 for */
+/* the box interior, else 1).  phi > 0 is free space, n = grad phi.     */
+/* *tie is set when the normal is not unique within eps (solid box).    */
+/* ------------------------------------------------------------------ */
+int or_sdf_eval(const double* s, const double* x, double* phi, double* n, int* tie, double eps)
+{
+    int kind = (int)s[0];
+    const double* p = s + 1;
+    *tie = 0;
+    if (kind == SDF_BOX_INTERIOR) {
+        for (int k = 0; k < 3; ++k) {
+            phi[2 * k] = x[k] - p[k];
+            phi[2 * k + 1] = p[3 + k] - x[k];
+            for (int m = 0; m < 3; ++m) {
+                n[3 * (2 * k) + m] = (m == k) ? 1.0 : 0.0;
+                n[3 * (2 * k + 1) + m] = (m == k) ? -1.0 : 0.0;
+            }
+        }
+        return 6;
+    }
+    if (kind == SDF_CONE_SHELL) {
+        double dx = x[0] - p[0], dy = x[1] - p[1];
+        double rho = sqrt(dx * dx + dy * dy);
+        double rx = 1.0, ry = 0.0;
+        if (rho > 0) { rx = dx / rho; ry = dy / rho; }
+        double e[2] = {p[5] - p[3], p[4] - p[2]};          /* (rho, z) segment direction */
+        double q[2] = {rho - p[3], x[2] - p[2]};
+        double ee = e[0] * e[0] + e[1] * e[1];
+        double t = (q[0] * e[0] + q[1] * e[1]) / ee;
+        if (t < 0) t = 0;
+        if (t > 1) t = 1;
+        double dq[2] = {q[0] - t * e[0], q[1] - t * e[1]};
+        double dist = sqrt(dq[0] * dq[0] + dq[1] * dq[1]);
+        double n2[2];
+        if (dist > 0) { n2[0] = dq[0] / dist; n2[1] = dq[1] / dist; }
+        else { double le = sqrt(ee); n2[0] = -e[1] / le; n2[1] = e[0] / le; *tie = 1; }
+        phi[0] = dist - p[6];
+        n[0] = n2[0] * rx;
+        n[1] = n2[0] * ry;
+        n[2] = n2[1];
+        return 1;
+    }
+    if (kind == SDF_SOLID_BOX) {
+        double d[3], q[3], sg[3];
+        int outside = 0;
+        for (int k = 0; k < 3; ++k) {
+            d[k] = x[k] - p[k];
+            sg[k] = d[k] < 0 ? -1.0 : 1.0;
+            q[k] = fabs(d[k]) - p[3 + k];
+            if (q[k] > 0) outside = 1;
+        }
+        if (outside) {
+            double qp[3], l2 = 0;
+            for (int k = 0; k < 3; ++k) { qp[k] = q[k] > 0 ? q[k] : 0; l2 += qp[k] * qp[k]; }
+            double l = sqrt(l2);
+            phi[0] = l;
+            for (int k = 0; k < 3; ++k) n[k] = sg[k] * qp[k] / l;
+        } else {
+            int a = 0;
+            for (int k = 1; k < 3; ++k)
+                if (q[k] > q[a]) a = k;
+            for (int k = 0; k < 3; ++k)
+                if (k != a && q[a] - q[k] <= eps) *tie = 1;
+            phi[0] = q[a];
+            n[0] = n[1] = n[2] = 0;
+            n[a] = sg[a];
+        }
+        return 1;
+    }
+    return 0;
+}
+
+static int sdf_ncomp(const double* rec)
+{
+    int kind = (int)rec[0];
+    return kind == SDF_BOX_INTERIOR ? 6 : ((kind == SDF_CONE_SHELL || kind == SDF_SOLID_BOX) ? 1 : 0);
+}
+
+/* ------------------------------------------------------------------ */
+/* HR upsampling, Sec. 4.                                               */
+/* ------------------------------------------------------------------ */
+
+/* Distance weight between a HR and a LR particle (Sec. 4):
+ *   w = max(0, (1 - |x_ij|^2 / (9 r_LR^2))^3)                          */
+double or_weight(double d2, double r_low)
+{
+    double t = 1.0 - d2 / (9.0 * r_low * r_low);
+    double w = t * t * t;
+    return w > 0 ? w : 0.0;
+}
+
+/* Advection and boundary handling of one HR particle after the blend
+ * parameter alpha is known (Sec. 4):
+ *   v^{t+1} = (1 - alpha) vtilde + alpha (v^t + dt g),
+ *   x^{t+1} = x^t + dt v^{t+1}.
+ * The paper states only that advection was modified for the domain
+ * boundaries (Sec. 2, last paragraph) and gives no formula.  Reading used
+ * here: each SDF contact component, in list order, projects the particle to
+ * phi = r_HR along n and removes the normal velocity component that points
+ * into the boundary relative to the boundary velocity u_b; the tangential
+ * part is kept.
+ * flip_k >= 0 inverts the k-th contact decision (used for the alternative
+ * branch).  Ambiguous contact decisions are appended to amb[]. */
+static void hr_finish(const double* x0, const double* v0, const double* vt, double alpha,
+                      const double* sdf, int n_sdf, const double* prm, int flip_k,
+                      double* xo, double* vo, int* amb, int* n_amb, int* hard)
+{
+    double dt = prm[UP_DT], rh = prm[UP_R_HIGH], eps_x = prm[UP_EPS_X];
+    const double g[3] = {prm[UP_GX], prm[UP_GY], prm[UP_GZ]};
+    for (int k = 0; k < 3; ++k) {
+        vo[k] = (1.0 - alpha) * vt[k] + alpha * (v0[k] + dt * g[k]);
+        xo[k] = x0[k] + dt * vo[k];
+    }
+    int dec = 0;
+    for (int s = 0; s < n_sdf; ++s) {
+        const double* rec = sdf + OR_SDF_STRIDE * s;
+        const double* ub = rec + 13;
+        int nc = sdf_ncomp(rec);
+        for (int c = 0; c < nc; ++c, ++dec) {
+            /* re-evaluated after every applied component: sequential */
+            double phi[OR_MAX_COMP], nn[3 * OR_MAX_COMP];
+            int tie;
+            or_sdf_eval(rec, xo, phi, nn, &tie, eps_x);
+            int active = phi[c] < rh;
+            if (fabs(phi[c] - rh) <= eps_x) amb[(*n_amb)++] = dec;
+            if (dec == flip_k) active = !active;
+            if (!active) continue;
+            if (tie) *hard = 1;
+            const double* n = nn + 3 * c;
+            double push = rh - phi[c];
+            for (int k = 0; k < 3; ++k) xo[k] += push * n[k];
+            double vr[3] = {vo[0] - ub[0], vo[1] - ub[1], vo[2] - ub[2]};
+            double vn = dot3(vr, n);
+            if (vn < 0)
+                for (int k = 0; k < 3; ++k) vo[k] -= vn * n[k];
+        }
+    }
+}
+
+/* One HR frame.  lr_x, lr_v: LR state after the latest LR step (x^{t+1},
+ * v^{t+1}); hr_x, hr_v: HR state at t.  sub (optional) selects which HR
+ * particles to compute; outputs are indexed by position in sub.
+ * mode 0 sums over every LR particle (the definition); mode 1 restricts the
+ * sum to the LR particles a plain grid returns within 3 r_LR, in ascending
+ * index order, which gives the same sums bit for bit.
+ * flag: 0 = every decision clear of its margin; 1 = exactly one decision
+ * inside its margin, alt_x/alt_v hold the other branch; 2 = more than one
+ * (or a non-unique SDF normal), alt = primary.
+ * diag (optional, 4 per output): sum w, max w, alpha, #LR with w > 0. */
+int or_upsample(const double* lr_x, const double* lr_v, long N,
+                const double* hr_x, const double* hr_v, long M,
+                const long* sub, long n_sub,
+                const double* sdf, int n_sdf, const double* prm, int mode,
+                double* out_x, double* out_v, int* flag, double* alt_x, double* alt_v, double* diag)
+{
+    double r = prm[UP_R_LOW], c1 = prm[UP_C1], c2 = prm[UP_C2], eps_w = prm[UP_EPS_W];
+    double R2 = 9.0 * r * r;
+    long n_out = sub ? n_sub : M;
+    or_grid_t grid;
+    if (mode == 1 && grid_build(&grid, lr_x, N, 3.0 * r) != 0) return -1;
+    int nth = g_threads;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nth) if (nth > 1)
+    for (long k = 0; k < n_out; ++k) {
+        long i = sub ? sub[k] : k;
+        if (i < 0 || i >= M) { err = -2; continue; }
+        const double* xi = hr_x + 3 * i;
+        const double* vi = hr_v + 3 * i;
+        double S = 0, V[3] = {0, 0, 0}, wmax = 0;
+        long cnt = 0;
+        long* cand = NULL;
+        long nc = N;
+        if (mode == 1) {
+            cand = (long*)malloc((size_t)(N ? N : 1) * sizeof(long));
+            nc = grid_query(&grid, xi, cand);
+        }
+        for (long q = 0; q < nc; ++q) {
+            long j = cand ? cand[q] : q;
+            double d[3] = {xi[0] - lr_x[3 * j], xi[1] - lr_x[3 * j + 1], xi[2] - lr_x[3 * j + 2]};
+            double d2 = dot3(d, d);
+            if (!(d2 < R2)) continue;
+            double w = or_weight(d2, r);
+            S += w;
+            for (int m = 0; m < 3; ++m) V[m] += w * lr_v[3 * j + m];
+            if (w > wmax) wmax = w;
+            ++cnt;
+        }
+        free(cand);
+        /* interpolated LR velocity; with no LR particle in reach it is
+         * undefined in the paper and alpha = 1 makes it irrelevant: use 0 */
+        double vt[3] = {0, 0, 0};
+        if (S > 0)
+            for (int m = 0; m < 3; ++m) vt[m] = V[m] / S;
+        /* blend parameter (Sec. 4): alpha = 1 - max w if max w <= c1 or
+         * max w / sum w >= c2, else 0 */
+        int A = wmax <= c1;
+        int B = S > 0 && wmax >= c2 * S;
+        int Aamb = fabs(wmax - c1) <= eps_w;
+        int Bamb = S > 0 && fabs(wmax - c2 * S) <= eps_w * S;
+        int prim = A || B;
+        int alt_out = prim;
+        if (Aamb && ((!A) || B) != prim) alt_out = !prim;
+        if (Bamb && (A || (!B)) != prim) alt_out = !prim;
+        if (Aamb && Bamb && ((!A) || (!B)) != prim) alt_out = !prim;
+        double alpha = prim ? 1.0 - wmax : 0.0;
+        int amb[64], n_amb = 0, hard = 0;
+        double xo[3], vo[3];
+        hr_finish(xi, vi, vt, alpha, sdf, n_sdf, prm, -1, xo, vo, amb, &n_amb, &hard);
+        int n_total = n_amb + (alt_out != prim);
+        double ax[3] = {xo[0], xo[1], xo[2]}, av[3] = {vo[0], vo[1], vo[2]};
+        int fl = 0;
+        if (hard || n_total > 1) fl = 2;
+        else if (n_total == 1) {
+            fl = 1;
+            int tmp[64], nt = 0, h2 = 0;
+            if (alt_out != prim)
+                hr_finish(xi, vi, vt, prim ? 0.0 : 1.0 - wmax, sdf, n_sdf, prm, -1, ax, av, tmp, &nt, &h2);
+            else
+                hr_finish(xi, vi, vt, alpha, sdf, n_sdf, prm, amb[0], ax, av, tmp, &nt, &h2);
+        }
+        for (int m = 0; m < 3; ++m) {
+            out_x[3 * k + m] = xo[m];
+            out_v[3 * k + m] = vo[m];
+            if (alt_x) alt_x[3 * k + m] = ax[m];
+            if (alt_v) alt_v[3 * k + m] = av[m];
+        }
+        if (flag) flag[k] = fl;
+        if (diag) {
+            diag[4 * k] = S;
+            diag[4 * k + 1] = wmax;
+            diag[4 * k + 2] = alpha;
+            diag[4 * k + 3] = (double)cnt;
+        }
+    }
+    if (mode == 1) grid_free(&grid);
+    return err;
+}
+
+/* ------------------------------------------------------------------ */
+/* LR step, Sec. 3 and Algorithm 1.                                     */
+/* ------------------------------------------------------------------ */
+
+typedef struct { long i, j; } or_pair;
+
+/* Candidate pairs i < j with |xt_i - xt_j| < Rc, ordered by (i, j). */
+static long make_pairs(const double* xt, long N, double Rc, int mode, or_pair** out, long* n_border,
+                       unsigned char* border_mark, double eps_x)
+{
+    long cap = 1024, n = 0;
+    or_pair* P = (or_pair*)malloc((size_t)cap * sizeof(or_pair));
+    if (!P) return -1;
+    double R2 = Rc * Rc;
+    or_grid_t g;
+    long* cand = NULL;
+    if (mode == 1) {
+        if (grid_build(&g, xt, N, Rc + eps_x) != 0) { free(P); return -1; }
+        cand = (long*)malloc((size_t)(N ? N : 1) * sizeof(long));
+    }
+    *n_border = 0;
+    for (long i = 0; i < N; ++i) {
+        long nc = N, q0 = i + 1;
+        if (mode == 1) { nc = grid_query(&g, xt + 3 * i, cand); q0 = 0; }
+        for (long q = q0; q < nc; ++q) {
+            long j = cand ? cand[q] : q;
+            if (j <= i) continue;
+            double d[3] = {xt[3 * j] - xt[3 * i], xt[3 * j + 1] - xt[3 * i + 1], xt[3 * j + 2] - xt[3 * i + 2]};
+            double d2 = dot3(d, d);
+            if (fabs(sqrt(d2) - Rc) <= eps_x) { (*n_border)++; border_mark[i] = border_mark[j] = 1; }
+            if (!(d2 < R2)) continue;
+            if (n == cap) {
+                cap *= 2;
+                or_pair* Q = (or_pair*)realloc(P, (size_t)cap * sizeof(or_pair));
+                if (!Q) { free(P); free(cand); if (mode == 1) grid_free(&g); return -1; }
+                P = Q;
+            }
+            P[n].i = i;
+            P[n].j = j;
+            ++n;
+        }
+    }
+    if (mode == 1) { free(cand); grid_free(&g); }
+    *out = P;
+    return n;
+}
+
+/* Friction delta of Eqs. 3-4 for a relative tangential displacement perp
+ * (the caller multiplies by the mass ratio and the sign).  thr_s / thr_k
+ * are the static / kinetic thresholds.  *amb is set when the static test
+ * is within eps of its threshold and the two branches differ. */
+static void friction_delta(const double* perp, double thr_s, double thr_k, double eps_x, double* f, int* amb)
+{
+    double L = sqrt(dot3(perp, perp));
+    double scale;
+    if (L < thr_s) scale = 1.0;
+    else scale = (L > 0 && thr_k / L < 1.0) ? thr_k / L : 1.0;
+    if (fabs(L - thr_s) <= eps_x && thr_s != thr_k) *amb = 1;
+    for (int k = 0; k < 3; ++k) f[k] = perp[k] * scale;
+}
+
+/* One LR time step (Algorithm 1) on N particles.
+ *
+ * x, v: double[N][3], updated in place.  inv_m: inverse masses m^-1 (0 =
+ * immovable).  Readings of the passages that are silent or garbled:
+ *  - Height-scaled mass m* = m e^{-h(x)} (Sec. 3, stable piling) with
+ *    h = k (z - ground_z) in metres; k = prm[PB_MASS_K]; it is evaluated at
+ *    the positions at the start of the step.
+ *  - Stabilization (Sec. 3, Algorithm 1) repairs positions that are invalid
+ *    at the start of the step, so its contact-only constraints are
+ *    evaluated on x (as updated by earlier stabilization passes) and the
+ *    resulting delta is applied to both x and xt.  Evaluating them on xt
+ *    would cancel the gravity-induced penetration without touching the
+ *    velocity, and a resting particle would fall ever faster.
+ *  - Candidate constraints are generated once per step after the
+ *    prediction, from every pair with |xt_i - xt_j| < Rc; a candidate is an
+ *    active contact in a pass when |x_ij| < 2 r_LR (Eqs. 1-2).  A pair at
+ *    exactly zero distance has no direction and is skipped.
+ *  - Friction (Eqs. 3-4): read literally, the displacement is the contact
+ *    correction itself, which is parallel to x_ij and has no tangential
+ *    part.  Reading used: the relative displacement over the step so far,
+ *    (xt_i - x_i) - (xt_j - x_j), as in the unified-particle friction model
+ *    the paper builds on.  Static branch below 2 r_LR mu_s, kinetic branch
+ *    scaled by min(2 r_LR mu_k / |dx_perp|, 1).  friction mode 1 uses the
+ *    penetration depth (2 r_LR - |x_ij|) in place of 2 r_LR, following the
+ *    prose that follows Eqs. 3-4.
+ *  - Cross coefficients mu_ij = sqrt(mu_i mu_j) (Sec. 3) between a grain
+ *    and an SDF boundary; grains share one coefficient pair.
+ *  - A contact pair (penetration + friction) counts once towards n_i;
+ *    each active SDF contact component counts once; particles with n_i = 0
+ *    are not moved.  No over-relaxation.
+ *  - SDF contacts: a pair with an immovable partner (mass ratio 1), active
+ *    when phi(xt_i) < r_LR, penetration (r_LR - phi) along n; friction uses
+ *    the displacement relative to the boundary's displacement u_b dt.
+ * suspect (optional, N): particles whose result depends on a decision taken
+ * within eps_x of its threshold, directly or through later passes.
+ * stats (optional): [0] #candidate pairs, [1] #ambiguous decisions,
+ * [2] max candidates of one particle, [3] #active pair contacts in the last
+ * pass. */
+int or_pbd_step(double* x, double* v, const double* inv_m, long N,
+                const double* sdf, int n_sdf, const double* prm, int mode,
+                int* suspect, long* stats)
+{
+    double r = prm[PB_R], dt = prm[PB_DT];
+    const double g[3] = {prm[PB_GX], prm[PB_GY], prm[PB_GZ]};
+    double mu_s = prm[PB_MU_S], mu_k = prm[PB_MU_K];
+    int n_stab = (int)prm[PB_N_STAB], iters = (int)prm[PB_ITERS];
+    double mass_k = prm[PB_MASS_K], ground = prm[PB_GROUND_Z], Rc = prm[PB_RC];
+    int fmode = (int)prm[PB_FRIC_MODE];
+    double eps_x = prm[PB_EPS_X];
+    double d0 = 2.0 * r;
+
+    double* xt = (double*)malloc((size_t)(N ? N : 1) * 3 * sizeof(double));
+    double* ws = (double*)malloc((size_t)(N ? N : 1) * sizeof(double));
+    double* D = (double*)malloc((size_t)(N ? N : 1) * 3 * sizeof(double));
+    long* cnt = (long*)malloc((size_t)(N ? N : 1) * sizeof(long));
+    unsigned char* mark = (unsigned char*)calloc((size_t)(N ? N : 1), 1);
+    unsigned char* mark2 = (unsigned char*)calloc((size_t)(N ? N : 1), 1);
+    if (!xt || !ws || !D || !cnt || !mark || !mark2) return -1;
+
+    /* Algorithm 1, first loop: v += dt g; xt = x + dt v; m* = m e^{-h(x)}.
+     * Stored as the inverse scaled mass 1/m* = m^-1 e^{h}. */
+    for (long i = 0; i < N; ++i) {
+        for (int k = 0; k < 3; ++k) {
+            v[3 * i + k] += dt * g[k];
+            xt[3 * i + k] = x[3 * i + k] + dt * v[3 * i + k];
+        }
+        ws[i] = inv_m[i] * exp(mass_k * (x[3 * i + 2] - ground));
+    }
+
+    /* neighbour search and constraint generation */
+    or_pair* P = NULL;
+    long n_border = 0;
+    long np = make_pairs(xt, N, Rc, mode, &P, &n_border, mark, eps_x);
+    if (np < 0) return -1;
+    long n_amb = n_border;
+    long maxc = 0;
+    if (stats) {
+        long* c = (long*)calloc((size_t)(N ? N : 1), sizeof(long));
+        for (long p = 0; p < np; ++p) { c[P[p].i]++; c[P[p].j]++; }
+        for (long i = 0; i < N; ++i)
+            if (c[i] > maxc) maxc = c[i];
+        free(c);
+    }
+
+    long active_last = 0;
+    int total = n_stab + iters;
+    for (int it = 0; it < total; ++it) {
+        int stab = it < n_stab;
+        /* a particle that read a suspect neighbour in an earlier pass is
+         * itself suspect from now on */
+        if (it > 0) {
+            memcpy(mark2, mark, (size_t)N);
+            for (long p = 0; p < np; ++p) {
+                if (mark2[P[p].i]) mark[P[p].j] = 1;
+                if (mark2[P[p].j]) mark[P[p].i] = 1;
+            }
+        }
+        memset(D, 0, (size_t)N * 3 * sizeof(double));
+        memset(cnt, 0, (size_t)N * sizeof(long));
+        active_last = 0;
+        /* Stabilization repairs invalid positions at the start of the step
+         * (Sec. 3): its contacts are evaluated on x, the solver's on xt. */
+        const double* y = stab ? x : xt;
+        /* particle-particle contacts: Eqs. 1-2 (+ Eqs. 3-4 when solving) */
+        for (long p = 0; p < np; ++p) {
+            long i = P[p].i, j = P[p].j;
+            double xij[3] = {y[3 * j] - y[3 * i], y[3 * j + 1] - y[3 * i + 1], y[3 * j + 2] - y[3 * i + 2]};
+            double d2 = dot3(xij, xij);
+            double d = sqrt(d2);
+            if (fabs(d - d0) <= eps_x) { mark[i] = mark[j] = 1; ++n_amb; }
+            if (!(d < d0) || d2 == 0.0) continue;
+            double wsum = ws[i] + ws[j];
+            if (!(wsum > 0)) continue;
+            double mi = ws[i] / wsum, mj = ws[j] / wsum;
+            double pen = d0 - d;
+            double u[3] = {xij[0] / d, xij[1] / d, xij[2] / d};
+            for (int k = 0; k < 3; ++k) {
+                D[3 * i + k] -= mi * pen * u[k];
+                D[3 * j + k] += mj * pen * u[k];
+            }
+            if (!stab) {
+                double dx[3], perp[3], f[3];
+                for (int k = 0; k < 3; ++k)
+                    dx[k] = (xt[3 * i + k] - x[3 * i + k]) - (xt[3 * j + k] - x[3 * j + k]);
+                double a = dot3(dx, xij) / d2;
+                for (int k = 0; k < 3; ++k) perp[k] = dx[k] - a * xij[k];
+                double base = (fmode == 1) ? pen : d0;
+                int amb = 0;
+                friction_delta(perp, base * mu_s, base * mu_k, eps_x, f, &amb);
+                if (amb) { mark[i] = mark[j] = 1; ++n_amb; }
+                for (int k = 0; k < 3; ++k) {
+                    D[3 * i + k] -= mi * f[k];
+                    D[3 * j + k] += mj * f[k];
+                }
+            }
+            cnt[i]++;
+            cnt[j]++;
+            ++active_last;
+        }
+        /* SDF contacts */
+        for (long i = 0; i < N; ++i) {
+            if (!(ws[i] > 0)) continue;
+            for (int s = 0; s < n_sdf; ++s) {
+                const double* rec = sdf + OR_SDF_STRIDE * s;
+                double phi[OR_MAX_COMP], nn[3 * OR_MAX_COMP];
+                int tie;
+                int nc = or_sdf_eval(rec, y + 3 * i, phi, nn, &tie, eps_x);
+                const double* ub = rec + 13;
+                double bmu_s = sqrt(mu_s * rec[16]), bmu_k = sqrt(mu_k * rec[17]);
+                for (int c = 0; c < nc; ++c) {
+                    if (fabs(phi[c] - r) <= eps_x) { mark[i] = 1; ++n_amb; }
+                    if (!(phi[c] < r)) continue;
+                    if (tie) { mark[i] = 1; ++n_amb; }
+                    const double* n = nn + 3 * c;
+                    double pen = r - phi[c];
+                    for (int k = 0; k < 3; ++k) D[3 * i + k] += pen * n[k];
+                    if (!stab) {
+                        double dx[3], perp[3], f[3];
+                        for (int k = 0; k < 3; ++k) dx[k] = (xt[3 * i + k] - x[3 * i + k]) - ub[k] * dt;
+                        double a = dot3(dx, n);
+                        for (int k = 0; k < 3; ++k) perp[k] = dx[k] - a * n[k];
+                        double base = (fmode == 1) ? pen : d0;
+                        int amb = 0;
+                        friction_delta(perp, base * bmu_s, base * bmu_k, eps_x, f, &amb);
+                        if (amb) { mark[i] = 1; ++n_amb; }
+                        for (int k = 0; k < 3; ++k) D[3 * i + k] -= f[k];
+                    }
+                    cnt[i]++;
+                }
+            }
+        }
+        /* Jacobi averaging: delta_i = (1/n_i) sum_k delta_ik.  Stabilization
+         * applies it to xt and x, solver iterations to xt only. */
+        for (long i = 0; i < N; ++i) {
+            if (cnt[i] == 0) continue;
+            for (int k = 0; k < 3; ++k) {
+                double dd = D[3 * i + k] / (double)cnt[i];
+                xt[3 * i + k] += dd;
+                if (stab) x[3 * i + k] += dd;
+            }
+        }
+    }
+    /* last loop of Algorithm 1: v = (xt - x) / dt, x = xt */
+    for (long i = 0; i < N; ++i)
+        for (int k = 0; k < 3; ++k) {
+            v[3 * i + k] = (xt[3 * i + k] - x[3 * i + k]) / dt;
+            x[3 * i + k] = xt[3 * i + k];
+        }
+    if (suspect)
+        for (long i = 0; i < N; ++i) suspect[i] = mark[i];
+    if (stats) {
+        stats[0] = np;
+        stats[1] = n_amb;
+        stats[2] = maxc;
+        stats[3] = active_last;
+    }
+    free(P);
+    free(xt);
+    free(ws);
+    free(D);
+    free(cnt);
+    free(mark);
+    free(mark2);
+    return 0;
+}
+
+/* Brute-force pair listing for tests of the neighbour search: every (i, j)
+ * with |a_i - b_j|^2 < R^2, i ascending then j ascending.  Returns the
+ * number found (at most cap are written). */
+long or_pairs_within(const double* a, long na, const double* b, long nb, double R, long* out_i, long* out_j, long cap)
+{
+    long n = 0;
+    double R2 = R * R;
+    for (long i = 0; i < na; ++i)
+        for (long j = 0; j < nb; ++j) {
+            double d[3] = {a[3 * i] - b[3 * j], a[3 * i + 1] - b[3 * j + 1], a[3 * i + 2] - b[3 * j + 2]};
+            if (dot3(d, d) < R2) {
+                if (n < cap) { out_i[n] = i; out_j[n] = j; }
+                ++n;
+            }
+        }
+    return n;
+}
+
+/* Grid version of or_pairs_within (same order, same set). */
+long or_pairs_within_grid(const double* a, long na, const double* b, long nb, double R, long* out_i, long* out_j,
+                          long cap)
+{
+    or_grid_t g;
+    if (grid_build(&g, b, nb, R) != 0) return -1;
+    long* cand = (long*)malloc((size_t)(nb ? nb : 1) * sizeof(long));
+    long n = 0;
+    for (long i = 0; i < na; ++i) {
+        long nc = grid_query(&g, a + 3 * i, cand);
+        for (long q = 0; q < nc; ++q) {
+            if (n < cap) { out_i[n] = i; out_j[n] = cand[q]; }
+            ++n;
+        }
+    }
+    free(cand);
+    grid_free(&g);
+    return n;
+}

@@ -1,0 +1,300 @@
+"""Seeded synthetic scenes shaped like the paper's workloads (Sec. 5.2).
+
+This package only draws inputs: particle positions and velocities, boundary
+descriptions and per-frame boundary poses.  It holds none of the method's
+arithmetic, so both the CUDA library and the CPU oracle can be fed from it
+without sharing code.  The paper's own scenes need triangle meshes and an
+interactive excavator; these stand-ins keep their sizes, radii and shapes:
+
+* ``cube``    -- 10x10x10 jittered lattice (r_LR = 0.01 m) in a 0.5 m box,
+                 ratio 8 (a sanity scene).
+* ``funnel``  -- 20,000 LR (r_LR = 0.005 m) above an analytic cone shell
+                 with a 2 cm outlet, ratio 25 -> 500,000 HR (stands in for
+                 the hourglass scene, 10k LR / 460k HR).
+* ``digging`` -- 1 x 1 m sand bed, 0.3 m deep with seeded value-noise
+                 height, r_LR = 0.0089 m (50,527 LR), ratio 40 -> 2,021,080
+                 HR, and a kinematic box "bucket" on a piecewise-
+                 linear path (stands in for the excavator scenes).
+* ``column``  -- a falling column, 4,000 LR / 64,000 HR (differentiation).
+* ``batch``   -- many independent small scenes of uneven sizes.
+
+Arrays follow the library's layout: float32 (n, 4) with pos.w = inverse mass
+for LR and the HR particle's original index (as uint32 bits) for HR;
+vel.w = 0.  Layout of an SDF record: dict(kind, p[12], vel[3], mu_s, mu_k).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SEED_BASE = 2308016290
+SDF_BOX_INTERIOR, SDF_CONE_SHELL, SDF_SOLID_BOX = 1, 2, 3
+GRAVITY = (0.0, 0.0, -9.81)
+RHO = 1600.0                       # Sec. 5.2 granular density
+MU_S, MU_K = 0.35, 0.30            # Sec. 5.2 friction coefficients
+
+
+# ----------------------------------------------------------------- SDFs ---
+def _rec(kind, p, vel=(0.0, 0.0, 0.0), mu_s=MU_S, mu_k=MU_K):
+    pp = [0.0] * 12
+    pp[:len(p)] = [float(a) for a in p]
+    return dict(kind=int(kind), p=pp, vel=[float(a) for a in vel], mu_s=float(mu_s), mu_k=float(mu_k))
+
+
+def box_interior(lo, hi, **kw):
+    return _rec(SDF_BOX_INTERIOR, list(lo) + list(hi), **kw)
+
+
+def cone_shell(cx, cy, z_out, r_out, z_top, r_top, half_thickness, **kw):
+    return _rec(SDF_CONE_SHELL, [cx, cy, z_out, r_out, z_top, r_top, half_thickness], **kw)
+
+
+def solid_box(center, half, vel=(0.0, 0.0, 0.0), **kw):
+    return _rec(SDF_SOLID_BOX, list(center) + list(half), vel=vel, **kw)
+
+
+def sdf_table(sdfs):
+    """SDF records as the oracle's float64 (n, 20) table."""
+    t = np.zeros((len(sdfs), 20))
+    for i, s in enumerate(sdfs):
+        t[i, 0] = s["kind"]
+        t[i, 1:13] = s["p"]
+        t[i, 13:16] = s["vel"]
+        t[i, 16] = s["mu_s"]
+        t[i, 17] = s["mu_k"]
+    return t
+
+
+# ------------------------------------------------------------ sampling ---
+def _ball(rng, n):
+    """n points uniform in the unit ball (rejection sampling)."""
+    out = np.empty((0, 3))
+    while len(out) < n:
+        c = rng.uniform(-1.0, 1.0, size=(2 * (n - len(out)) + 16, 3))
+        c = c[(c * c).sum(1) <= 1.0]
+        out = np.concatenate([out, c])
+    return out[:n]
+
+
+def _hr_in_balls(rng, lr_xyz, r_low, ratio):
+    """`ratio` HR per LR particle, uniform inside that LR particle's sphere."""
+    n = len(lr_xyz)
+    off = _ball(rng, n * ratio) * r_low
+    return np.repeat(lr_xyz, ratio, axis=0) + off
+
+
+def _pack(xyz, w):
+    a = np.zeros((len(xyz), 4), np.float32)
+    a[:, :3] = xyz
+    a[:, 3] = w
+    return a
+
+
+def hr_ids(m):
+    return np.arange(m, dtype=np.uint32).view(np.float32)
+
+
+def _finish(name, seed, box_lo, box_hi, r_low, ratio, lr_xyz, rng, sdfs, dt, iters, mu_s=MU_S, mu_k=MU_K,
+            r_high=None, **extra):
+    m_lr = RHO * 4.0 / 3.0 * math.pi * r_low ** 3
+    n = len(lr_xyz)
+    lr_pos = _pack(lr_xyz, np.float32(1.0 / m_lr))
+    hr_xyz = _hr_in_balls(rng, lr_xyz, r_low, ratio)
+    hr_pos = _pack(hr_xyz, 0.0)
+    hr_pos[:, 3] = hr_ids(len(hr_xyz))
+    if r_high is None:
+        r_high = r_low * ratio ** (-1.0 / 3.0)
+    sc = dict(name=name, seed=seed, box_lo=[float(a) for a in box_lo], box_hi=[float(a) for a in box_hi],
+              r_low=float(r_low), r_high=float(r_high), ratio=int(ratio), sdfs=sdfs,
+              gravity=GRAVITY, mu_s=mu_s, mu_k=mu_k, dt=float(dt), iters=int(iters),
+              lr_pos=lr_pos, lr_vel=np.zeros((n, 4), np.float32),
+              hr_pos=hr_pos, hr_vel=np.zeros((len(hr_pos), 4), np.float32))
+    sc.update(extra)
+    return sc
+
+
+def _lattice(rng, lo, counts, spacing, jitter):
+    g = np.stack(np.meshgrid(*[np.arange(c) for c in counts], indexing="ij"), -1).reshape(-1, 3)
+    g = g[:, [0, 1, 2]].astype(np.float64)
+    xyz = np.asarray(lo, float) + g * spacing
+    return xyz + rng.uniform(-jitter, jitter, size=xyz.shape)
+
+
+# --------------------------------------------------------------- scenes ---
+def cube(seed=SEED_BASE + 0, n_side=10, r_low=0.01, ratio=8):
+    """Jittered lattice cube (spacing 2r, jitter +-0.1r) in a 0.5 m box."""
+    rng = np.random.default_rng(seed)
+    box_lo, box_hi = (0.0, 0.0, 0.0), (0.5, 0.5, 0.5)
+    sp = 2.0 * r_low
+    half = 0.5 * sp * (n_side - 1)
+    lo = (0.25 - half, 0.25 - half, 0.15 + r_low)
+    xyz = _lattice(rng, lo, (n_side,) * 3, sp, 0.1 * r_low)
+    return _finish("cube", seed, box_lo, box_hi, r_low, ratio, xyz, rng,
+                   [box_interior(box_lo, box_hi, mu_s=0.5, mu_k=0.5)], dt=1.0 / 60.0, iters=4,
+                   mu_s=0.5, mu_k=0.5)
+
+
+def funnel(seed=SEED_BASE + 1, n_low=20000, r_low=0.005, ratio=25):
+    """LR particles released above a cone shell (half-angle 35 deg, top radius
+    0.15 m, outlet diameter 0.02 m, wall thickness 2 r_LR) in a 0.4 x 0.4 x
+    0.6 m box."""
+    rng = np.random.default_rng(seed)
+    box_lo, box_hi = (0.0, 0.0, 0.0), (0.4, 0.4, 0.6)
+    cx = cy = 0.2
+    r_out, r_top = 0.01, 0.15
+    height = (r_top - r_out) / math.tan(math.radians(35.0))
+    z_out = 0.05
+    z_top = z_out + height
+    sp = 2.0 * r_low
+    rad = r_top - 2.0 * r_low
+    nxy = int(2 * rad / sp) + 1
+    layers = []
+    z = z_top + 2.0 * r_low
+    total = 0
+    while total < n_low:
+        g = np.stack(np.meshgrid(np.arange(nxy), np.arange(nxy), indexing="ij"), -1).reshape(-1, 2)
+        xy = np.array([cx - rad, cy - rad]) + g * sp
+        keep = ((xy - [cx, cy]) ** 2).sum(1) <= rad * rad
+        xy = xy[keep]
+        layers.append(np.column_stack([xy, np.full(len(xy), z)]))
+        total += len(xy)
+        z += sp
+    xyz = np.concatenate(layers)[:n_low]
+    xyz = xyz + rng.uniform(-0.1 * r_low, 0.1 * r_low, size=xyz.shape)
+    sdfs = [box_interior(box_lo, box_hi), cone_shell(cx, cy, z_out, r_out, z_top, r_top, r_low)]
+    return _finish("funnel", seed, box_lo, box_hi, r_low, ratio, xyz, rng, sdfs, dt=1.0 / 60.0, iters=6)
+
+
+def _value_noise(rng, n_ctrl, amp, u, v):
+    c = rng.uniform(-amp, amp, size=(n_ctrl, n_ctrl))
+    fu = u * (n_ctrl - 1)
+    fv = v * (n_ctrl - 1)
+    i0 = np.clip(np.floor(fu).astype(int), 0, n_ctrl - 2)
+    j0 = np.clip(np.floor(fv).astype(int), 0, n_ctrl - 2)
+    a, b = fu - i0, fv - j0
+    return ((1 - a) * (1 - b) * c[i0, j0] + a * (1 - b) * c[i0 + 1, j0]
+            + (1 - a) * b * c[i0, j0 + 1] + a * b * c[i0 + 1, j0 + 1])
+
+
+BUCKET_HALF = (0.125, 0.075, 0.075)
+BUCKET_PATH = ((0.15, 0.5, 0.42), (0.32, 0.5, 0.27), (0.68, 0.5, 0.27), (0.85, 0.5, 0.42))
+BUCKET_SPEED = 0.4
+
+
+def bucket_pose(t):
+    """Centre and velocity of the digging bucket at time t: piecewise-linear
+    ping-pong along BUCKET_PATH at BUCKET_SPEED m/s (translation only)."""
+    pts = np.asarray(BUCKET_PATH, float)
+    seg = np.linalg.norm(np.diff(pts, axis=0), axis=1)
+    total = seg.sum()
+    period = 2.0 * total / BUCKET_SPEED
+    s = (t % period) * BUCKET_SPEED
+    direction = 1.0
+    if s > total:
+        s = 2.0 * total - s
+        direction = -1.0
+    k = 0
+    while k < len(seg) - 1 and s > seg[k]:
+        s -= seg[k]
+        k += 1
+    d = (pts[k + 1] - pts[k]) / seg[k]
+    c = pts[k] + d * min(s, seg[k])
+    return c, d * BUCKET_SPEED * direction
+
+
+def bucket_sdf(t):
+    c, u = bucket_pose(t)
+    return solid_box(c, BUCKET_HALF, vel=u)
+
+
+def digging(seed=SEED_BASE + 2, r_low=0.0089, ratio=40, size=1.0, depth=0.3):
+    """Sand bed with seeded value-noise height (+-0.05 m on 8x8 control
+    points, bilinear) and a kinematic box bucket."""
+    rng = np.random.default_rng(seed)
+    box_lo, box_hi = (0.0, 0.0, 0.0), (size, size, 0.6)
+    sp = 2.0 * r_low
+    n_xy = int((size - 2 * r_low) / sp) + 1
+    g = np.arange(n_xy) * sp + r_low
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    H = depth + _value_noise(rng, 8, 0.05, X / size, Y / size)
+    cols = []
+    for k in range(int((depth + 0.05) / sp) + 2):
+        z = r_low + k * sp
+        m = z <= H - r_low
+        cols.append(np.column_stack([X[m], Y[m], np.full(m.sum(), z)]))
+    xyz = np.concatenate(cols)
+    xyz = xyz + rng.uniform(-0.1 * r_low, 0.1 * r_low, size=xyz.shape)
+    sdfs = [box_interior(box_lo, box_hi), bucket_sdf(0.0)]
+    return _finish("digging", seed, box_lo, box_hi, r_low, ratio, xyz, rng, sdfs, dt=1.0 / 60.0, iters=8,
+                   bucket_index=1)
+
+
+def column(seed=SEED_BASE + 3, n_low=4000, r_low=0.01, ratio=16):
+    """Falling column (10 x 10 footprint) in a 0.6 m box."""
+    rng = np.random.default_rng(seed)
+    box_lo, box_hi = (0.0, 0.0, 0.0), (0.6, 0.6, 1.2)
+    n_xy = 10
+    layers = -(-n_low // (n_xy * n_xy))
+    sp = 2.0 * r_low
+    lo = (0.3 - 0.5 * sp * (n_xy - 1), 0.3 - 0.5 * sp * (n_xy - 1), 0.1)
+    xyz = _lattice(rng, lo, (n_xy, n_xy, layers), sp, 0.1 * r_low)[:n_low]
+    return _finish("column", seed, box_lo, box_hi, r_low, ratio, xyz, rng,
+                   [box_interior(box_lo, box_hi)], dt=1.0 / 60.0, iters=4)
+
+
+def batch(seed=SEED_BASE + 4, n_scenes=256, lo_count=500, hi_count=8000, ratios=(8, 16, 32)):
+    """Independent small scenes with uneven particle counts, box sizes 0.2-1.0
+    m and round-robin boundary kinds (box / cone / bucket)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for s in range(n_scenes):
+        n_low = int(rng.integers(lo_count, hi_count + 1))
+        ratio = int(rng.choice(ratios))
+        L = float(rng.uniform(0.2, 1.0))
+        r_low = float(0.25 * L / max(2.0, round(n_low ** (1.0 / 3.0))))
+        r_low = min(max(r_low, 0.003), 0.02)
+        box_lo, box_hi = (0.0, 0.0, 0.0), (L, L, L)
+        sp = 2.0 * r_low
+        n_side = int(math.ceil(n_low ** (1.0 / 3.0)))
+        n_side = min(n_side, int((L - 4 * r_low) / sp))
+        layers = -(-n_low // (n_side * n_side))
+        lo = (0.5 * L - 0.5 * sp * (n_side - 1), 0.5 * L - 0.5 * sp * (n_side - 1), 2 * r_low)
+        xyz = _lattice(rng, lo, (n_side, n_side, layers), sp, 0.1 * r_low)[:n_low]
+        sdfs = [box_interior(box_lo, box_hi)]
+        kind = s % 3
+        if kind == 1:
+            sdfs.append(cone_shell(0.5 * L, 0.5 * L, 0.05 * L, 0.05 * L, 0.3 * L, 0.45 * L, r_low))
+        elif kind == 2:
+            sdfs.append(solid_box((0.5 * L, 0.5 * L, 0.8 * L), (0.1 * L, 0.1 * L, 0.05 * L),
+                                  vel=(0.0, 0.0, -0.2)))
+        out.append(_finish(f"batch{s}", seed, box_lo, box_hi, r_low, ratio, xyz, rng, sdfs,
+                           dt=1.0 / 60.0, iters=4))
+    return out
+
+
+# ------------------------------------------------------ perturbed states ---
+def stir(sc, seed, v_scale=0.5, spread=0.5, hr_v_scale=0.3):
+    """A copy of a scene with a seeded, non-uniform LR velocity field (affine
+    plus noise), random HR velocities, and a fraction of HR particles spread
+    out of the LR support so every blending case occurs."""
+    rng = np.random.default_rng(seed)
+    sc = dict(sc)
+    lr_pos = sc["lr_pos"].copy()
+    hr_pos = sc["hr_pos"].copy()
+    n, m = len(lr_pos), len(hr_pos)
+    c = lr_pos[:, :3].mean(0)
+    A = rng.normal(0, v_scale, size=(3, 3))
+    b = rng.normal(0, v_scale, size=3)
+    lr_vel = np.zeros((n, 4), np.float32)
+    lr_vel[:, :3] = b + (lr_pos[:, :3] - c) @ A.T * 5.0 + rng.normal(0, 0.1 * v_scale, size=(n, 3))
+    hr_vel = np.zeros((m, 4), np.float32)
+    hr_vel[:, :3] = rng.normal(0, hr_v_scale, size=(m, 3))
+    k = int(spread * 0.2 * m)
+    sel = rng.choice(m, size=k, replace=False)
+    hr_pos[sel, :3] += rng.normal(0, 3.0 * sc["r_low"], size=(k, 3))
+    lo = np.asarray(sc["box_lo"]) + sc["r_high"]
+    hi = np.asarray(sc["box_hi"]) - sc["r_high"]
+    hr_pos[:, :3] = np.clip(hr_pos[:, :3], lo - 2 * sc["r_high"], hi + 2 * sc["r_high"])
+    sc.update(lr_vel=lr_vel, hr_vel=hr_vel, hr_pos=hr_pos)
+    return sc

@@ -1,0 +1,366 @@
+"""Benchmark of one simulation frame of the two-level granular method.
+
+A step is one frame of the whole hot path on the digging workload (50,527 LR
+/ 2,021,080 HR particles, r_LR = 0.0089 m, ratio 40): the kinematic bucket's
+pose update, one LR step of Algorithm 1 (dt = 1/60 s, 2 stabilization + 8
+solver passes, with its binning and candidate search), and one HR
+upsampling frame of Sec. 4 (LR re-binning, the HR reorder every 8 frames,
+the fused gather / blend / advection / SDF kernel).
+
+  value  HR particles per second of whole frames, device-timed with CUDA
+         events on the library's stream, inputs resident, L2 flushed (a
+         512 MiB write) between timed steps; summed over ranks.
+  e2e    the same frames through the C ABI with the full state (LR and HR
+         position and velocity) copied from pinned host memory before and
+         the HR result copied back after every step.
+  roofline  the upsampling kernel: algorithmic bytes (64 B per HR particle
+         read + written, 32 B per LR particle, 4 B per cell start) over its
+         average CUDA-event duration, against the measured HBM copy peak.
+  cpu_baseline  the FP64 oracle on this machine's host cores on a bounded
+         sample (one full LR step + a random HR subset, scaled to the frame).
+
+--impl reference runs that oracle alone as the reference arm.
+Under torchrun every rank steps its own replica of the scene (weak scaling,
+no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenes  # noqa: E402
+
+METRIC = "high-res particles/sec (gs_upsample) and HBM GB/s vs peak at 2M; batched vs plain"
+UNIT = "HR particles/s"
+DT = 1.0 / 60.0
+FLUSH_BYTES = 512 << 20
+# DRAM bytes of one upsampling launch on this workload from an ncu capture of
+# the kernel source with this hash (profiles/); reported only while the
+# source is unchanged.
+TRAFFIC_CAPTURE = {"source_sha1": None, "bytes": None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gs", "reference"], default="gs")
+    ap.add_argument("--workload", choices=["digging", "funnel", "cube"], default="digging")
+    ap.add_argument("--bed-size", type=float, default=1.0,
+                    help="digging bed edge in metres (same particle density; 2.0 gives 4x the particles)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def make_scene(name, bed_size=1.0):
+    if name == "digging":
+        return scenes.digging(size=bed_size)
+    return {"funnel": scenes.funnel, "cube": scenes.cube}[name]()
+
+
+def workload_config(sc):
+    return {"workload": f"{sc['name']} scene, {len(sc['lr_pos'])} LR / {len(sc['hr_pos'])} HR particles, "
+                        f"r_LR {sc['r_low']} m, ratio {sc['ratio']}",
+            "n_low": len(sc["lr_pos"]), "n_high": len(sc["hr_pos"]), "r_low": sc["r_low"],
+            "ratio": sc["ratio"], "dt": DT, "lr_solver_iters": sc["iters"], "n_stab": 2,
+            "hr_reorder_every": 8, "lr_steps_per_frame": 1,
+            "l2": "flushed between timed steps (512 MiB write)"}
+
+
+def bucket_at(sc, frame):
+    if "bucket_index" not in sc:
+        return None
+    return sc["bucket_index"], scenes.bucket_sdf(frame * DT)
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------- clocks ---
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [a.strip() for a in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, val in zip(names, f[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------- CPU baseline ---
+def oracle_frame_rate(sc, budget_s, sample_hr=1_000_000):
+    """HR particles/s of the FP64 oracle on host cores: one LR step of the
+    whole LR set plus the upsampling of a random HR subset, scaled to the
+    full frame, repeated until the time budget is used."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    r = sc["r_low"]
+    g = sc["gravity"]
+    pp = dict(r=r, dt=DT, gx=g[0], gy=g[1], gz=g[2], mu_s=sc["mu_s"], mu_k=sc["mu_k"], n_stab=2,
+              iters=sc["iters"], mass_k=1.0, ground_z=sc["box_lo"][2], rc=3 * r, friction_mode=0, eps_x=1e-7,
+              eps_impact=1e-9)
+    up = dict(r_low=r, r_high=sc["r_high"], dt=DT, gx=g[0], gy=g[1], gz=g[2], c1=512 / 729, c2=0.6, eps_w=1e-4,
+              eps_x=2e-6)
+    M = len(sc["hr_pos"])
+    ns = min(sample_hr, M)
+    rng = np.random.default_rng(0)
+    sdf = scenes.sdf_table(sc["sdfs"])
+    lr_x, lr_v, im = sc["lr_pos"][:, :3], sc["lr_vel"][:, :3], sc["lr_pos"][:, 3]
+    hr_x, hr_v = sc["hr_pos"][:, :3], sc["hr_vel"][:, :3]
+    t_lr = t_up = 0.0
+    reps = 0
+    t_start = time.perf_counter()
+    while reps == 0 or time.perf_counter() - t_start < budget_s:
+        sub = np.sort(rng.choice(M, size=ns, replace=False))
+        t0 = time.perf_counter()
+        x1, v1, _, _ = oracle.pbd_step(lr_x, lr_v, im, sdf, pp, mode=1)
+        t1 = time.perf_counter()
+        oracle.upsample(x1, v1, hr_x, hr_v, sdf, up, sub=sub, mode=1)
+        t2 = time.perf_counter()
+        t_lr += t1 - t0
+        t_up += t2 - t1
+        reps += 1
+    frame_s = (t_lr + t_up * M / ns) / reps
+    return {"value": M / frame_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{reps} x (one FP64 LR step of all {len(lr_x)} LR particles on 1 thread + upsampling of "
+                      f"{ns} random HR particles on {cores} threads), scaled to the {M}-particle frame"}
+
+
+# ------------------------------------------------------------- GPU arm ---
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2308_01629_gb300 as gs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    sc = make_scene(args.workload, args.bed_size)
+    N, M = len(sc["lr_pos"]), len(sc["hr_pos"])
+    ctx = gs.Context(sc, stream=stream.cuda_stream)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    frame = [0]
+
+    def step(c):
+        b = bucket_at(sc, frame[0])
+        if b is not None:
+            c.set_sdf(*b)
+        c.step_low(DT, sc["iters"])
+        c.upsample(DT)
+        frame[0] += 1
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(ctx)
+    torch.cuda.synchronize(dev)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ctx.set_timing(True)
+    for t in range(gs.GS_TIMER_COUNT):
+        ctx.timing_read(t)
+    launches0 = ctx.launches()
+    clk = Clocks(local)
+    barrier()
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        step(ctx)
+        ends[k].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    wall = time.perf_counter() - wall0
+    clocks = clk.stop()
+    launches = ctx.launches() - launches0
+    ctx.sync()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    gather_ms, gather_n = ctx.timing_read(gs.GS_TIMER_GATHER)
+    lr_ms, lr_n = ctx.timing_read(gs.GS_TIMER_STEP_LOW)
+    bin_ms, bin_n = ctx.timing_read(gs.GS_TIMER_BIN_LOW)
+    rs_ms, rs_n = ctx.timing_read(gs.GS_TIMER_RESORT)
+    ctx.set_timing(False)
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * M * args.steps / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = {}
+        for k in ("lr_pos", "lr_vel", "hr_pos", "hr_vel"):
+            t = torch.empty(sc[k].shape, dtype=torch.float32, pin_memory=True)
+            t.numpy()[:] = sc[k]
+            pin[k] = t
+        out_x = torch.empty((M, 4), dtype=torch.float32, pin_memory=True)
+        out_v = torch.empty((M, 4), dtype=torch.float32, pin_memory=True)
+        fields = ((gs.GS_FIELD_LR_POS, "lr_pos"), (gs.GS_FIELD_LR_VEL, "lr_vel"),
+                  (gs.GS_FIELD_HR_POS, "hr_pos"), (gs.GS_FIELD_HR_VEL, "hr_vel"))
+
+        def e2e_step():
+            for f, k in fields:
+                ctx.write(f, pin[k])
+            step(ctx)
+            ctx.read(gs.GS_FIELD_HR_POS, out_x)
+            ctx.read(gs.GS_FIELD_HR_VEL, out_v)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        barrier()
+        t0 = time.perf_counter()
+        ne = max(3, args.steps // 2)
+        for _ in range(ne):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        barrier()
+        te = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([te], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * M * ne / te, "unit": UNIT, "h2d_bytes_per_step": int((2 * N + 2 * M) * 16),
+               "d2h_bytes_per_step": int(2 * M * 16), "ms_per_step": 1e3 * te / ne}
+
+    ctx.close()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return None
+
+    pk = peaks()
+    ncell = int(ctx.grid.n_cell) if hasattr(ctx, "grid") else 0
+    alg_bytes = 64 * M + 32 * N + 4 * (ncell + 1)
+    gather_avg_s = gather_ms / max(gather_n, 1) / 1e3
+    achieved = alg_bytes / gather_avg_s / 1e9
+    peak = pk["hbm_gbs"] if pk else 6800.0
+    src = open(os.path.join(ROOT, "paper_2308_01629_gb300", "csrc", "upsample.cu"), "rb").read()
+    sha = hashlib.sha1(src).hexdigest()
+    traffic = TRAFFIC_CAPTURE["bytes"] if TRAFFIC_CAPTURE["source_sha1"] == sha else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded scene generators)",
+        "config": workload_config(sc),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_upsample (fused gather + blend + advection + SDF)",
+                     "peak_source": "measured" if pk else "fallback",
+                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": gather_avg_s * 1e6},
+        "breakdown_ms_per_step": {"lr_step": lr_ms / max(lr_n, 1), "lr_binning_for_upsample": bin_ms / max(bin_n, 1),
+                                  "hr_reorder_amortized": rs_ms / args.steps,
+                                  "upsample_kernel": gather_ms / max(gather_n, 1)},
+        "upsample_kernel_hr_per_s": M / gather_avg_s,
+        "wall_s_timed_region": wall,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if not args.no_cpu:
+        line["cpu_baseline"] = oracle_frame_rate(sc, args.cpu_seconds)
+    if world > 1:
+        dist.destroy_process_group()
+    return line
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    sc = make_scene(args.workload, args.bed_size)
+    per = min(8.0, max(1.0, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_frame_rate(sc, 0.0, sample_hr=50_000)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_frame_rate(sc, per, sample_hr=200_000))
+    wall = time.perf_counter() - t0
+    v = float(np.mean([a["value"] for a in vals]))
+    M = len(sc["hr_pos"])
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * M / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded scene generators)",
+            "config": workload_config(sc), "wall_s": wall,
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    line = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * gs.h -- C ABI of the GB300 library for the two-level granular method of
+ * "Interactive High-Resolution Simulation of Granular Material" (arXiv
+ * 2308.01629): a low-resolution (LR) position-based-dynamics simulation
+ * (Sec. 3, Algorithm 1) and the per-frame upsampling of a large
+ * high-resolution (HR) particle set from it (Sec. 4).
+ *
+ * Every step runs in hand-written CUDA kernels for sm_103a on one GPU; the
+ * host side only validates arguments, owns buffers and enqueues work.
+ *
+ * Conventions
+ *   - Units are metres and seconds; z is up; gravity is a parameter.
+ *   - Particle arrays are float4 records, array-of-structures, 16-byte
+ *     aligned:  LR position (x, y, z, inverse mass), LR velocity
+ *     (vx, vy, vz, 0), HR position (x, y, z, id) where id is the particle's
+ *     original index stored as the bits of a uint32, HR velocity
+ *     (vx, vy, vz, 0).
+ *   - All buffers that hold simulation state belong to the context and live
+ *     in device memory allocated at gs_create.  Caller buffers passed to
+ *     gs_read / gs_write stay owned by the caller.
+ *   - Calls are asynchronous on the context's stream unless stated
+ *     otherwise.  gs_read into host memory, gs_sync and gs_timing_read block
+ *     until the stream is idle.
+ *   - Every call returns a gs_status.  After GS_ERR_ARG / GS_ERR_DOMAIN /
+ *     GS_ERR_CAPACITY the context stays usable; after GS_ERR_CUDA it is
+ *     poisoned and every later call returns GS_ERR_STATE.
+ *     gs_last_error gives the message of the most recent failure.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gs_ctx gs_ctx;
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_ARG = -1,       /* invalid argument (null pointer, size, range) */
+    GS_ERR_OOM = -2,       /* device or host allocation failed */
+    GS_ERR_CUDA = -3,      /* a CUDA call failed; the context is poisoned */
+    GS_ERR_DOMAIN = -4,    /* non-finite input positions or velocities */
+    GS_ERR_TIMEOUT = -5,   /* a bounded device loop reached its limit */
+    GS_ERR_STATE = -6,     /* call not valid in the context's state */
+    GS_ERR_CAPACITY = -7   /* a per-particle capacity was exceeded */
+} gs_status;
+
+/* Analytic boundaries.  The paper samples boundaries with immovable particles
+ * (Sec. 3, particle-sampled rigid bodies and domain boundaries); this library
+ * uses signed distance functions (phi > 0 in free space) instead.
+ *   GS_SDF_BOX_INTERIOR: p = lo[3], hi[3]; particles stay inside; evaluated
+ *                        as six half-space walls in the order x-lo, x-hi,
+ *                        y-lo, y-hi, z-lo, z-hi.
+ *   GS_SDF_CONE_SHELL:   p = cx, cy, z_out, R_out, z_top, R_top, half
+ *                        thickness: the segment (R_out, z_out)-(R_top, z_top)
+ *                        in the (radius, z) half-plane revolved about the
+ *                        vertical axis through (cx, cy), thickened.
+ *   GS_SDF_SOLID_BOX:    p = centre[3], half extents[3]; particles stay out.
+ * vel is the boundary's velocity (kinematic boundaries); mu_s / mu_k are its
+ * friction coefficients, combined with the grains' as sqrt(mu_i mu_b)
+ * (Sec. 3, cross friction coefficients). */
+enum { GS_SDF_BOX_INTERIOR = 1, GS_SDF_CONE_SHELL = 2, GS_SDF_SOLID_BOX = 3 };
+#define GS_MAX_SDF 16
+
+typedef struct {
+    int32_t kind;
+    float p[12];
+    float vel[3];
+    float mu_s, mu_k;
+} gs_sdf;
+
+/* Method parameters.  gs_default_params fills the paper's values. */
+typedef struct {
+    float gravity[3];        /* Algorithm 1: |g| = 9.81 m/s^2; default (0,0,-9.81) */
+    float mu_s, mu_k;        /* Sec. 3 / 5.2: grain friction, default 0.35 / 0.30 */
+    float c1, c2;            /* Sec. 4 blend constants, default 512/729 and 0.6 */
+    int32_t n_stab;          /* Algorithm 1 stabilization iterations, default 2 */
+    float mass_scale_k;      /* Sec. 3 height-scaled mass m* = m exp(-k (z - ground_z)), default 1 (1/m) */
+    float ground_z;          /* height of the ground plane for m*, default box_lo z */
+    float neighbor_radius;   /* LR candidate radius; 0 = 3 r_low */
+    int32_t friction_mode;   /* 0: thresholds 2 r mu (Eqs. 3-4); 1: penetration depth times mu */
+    int32_t resort_every;    /* reorder HR by cell every this many frames; 0 = never; default 8 */
+    int32_t max_neighbors;   /* LR candidate capacity per particle; 0 = 64 */
+} gs_params;
+
+typedef struct {
+    float box_lo[3], box_hi[3];  /* domain of the neighbour grid (metres) */
+    int32_t n_low;               /* number of LR particles */
+    int32_t n_sdf;               /* 0 .. GS_MAX_SDF */
+    const gs_sdf* sdf;           /* copied at gs_create */
+    gs_params params;
+} gs_scene;
+
+/* Readable / writable state.  HR fields are always exchanged in original-id
+ * order (index = id), whatever the internal cell order. */
+enum {
+    GS_FIELD_LR_POS = 0,         /* float4[n_low], read / write */
+    GS_FIELD_LR_VEL = 1,         /* float4[n_low], read / write */
+    GS_FIELD_HR_POS = 2,         /* float4[n_high], read / write (w is set to the id on write) */
+    GS_FIELD_HR_VEL = 3,         /* float4[n_high], read / write */
+    GS_FIELD_HR_POS_INTERNAL = 4,/* float4[n_high], read: internal (cell) order */
+    GS_FIELD_HR_VEL_INTERNAL = 5,/* float4[n_high], read: internal (cell) order */
+    GS_FIELD_LR_CELL_START = 6,  /* uint32[n_cell + 1], read: first sorted slot of each cell */
+    GS_FIELD_LR_SORTED_INDEX = 7,/* uint32[n_low], read: particle index of each sorted slot */
+    GS_FIELD_HR_SORTED_KEY = 8   /* uint32[n_high], read: fine cell key of each internal slot
+                                    after the latest reorder */
+};
+
+/* Neighbour-grid contract (Sec. 5.1 uses a compact-hashing grid; this
+ * library fixes a dense uniform grid so cell ids are reproducible):
+ *   h = float(3 r_low (1 + 2^-10)), inv_h = float(1 / h), o = box_lo,
+ *   dims[k] = ceil((box_hi[k] - box_lo[k]) / h);
+ *   a = (x - o) * inv_h in float32, round-to-nearest, no fused multiply-add;
+ *   sub = clamp(floor(2 a), 0, 2 dims - 1); cell = sub >> 1;
+ *   cell id = (cz dims[1] + cy) dims[0] + cx;
+ *   fine key (HR order) = 8 cell id + 4 (sub_z & 1) + 2 (sub_y & 1) + (sub_x & 1).
+ * Binning sorts stably by (cell id, particle index). */
+typedef struct {
+    float origin[3];
+    float h, inv_h;
+    int32_t dims[3];
+    int64_t n_cell;
+} gs_grid_info;
+
+/* Fill p with the paper's default parameters (see gs_params). */
+void gs_default_params(gs_params* p);
+
+/* Create a context: allocate LR state for scene->n_low particles and HR
+ * state for n_low * ratio particles, the neighbour grid over the scene box,
+ * and all scratch buffers.  r_low: LR radius (Sec. 3, constant for all LR
+ * particles); r_high: HR radius (<= 0 selects r_low * ratio^(-1/3)); ratio:
+ * HR per LR (>= 1).  cuda_stream: a cudaStream_t the context enqueues on, or
+ * NULL for a stream owned by the context.  The particle state starts at zero
+ * and is loaded with gs_write.  Errors: GS_ERR_ARG, GS_ERR_OOM, GS_ERR_CUDA. */
+int gs_create(const gs_scene* scene, float r_low, float r_high, int ratio, void* cuda_stream, gs_ctx** out);
+
+/* Release every buffer of the context (waits for its stream). */
+void gs_destroy(gs_ctx* ctx);
+
+/* Message of the most recent failure of this context ("" if none). */
+const char* gs_last_error(const gs_ctx* ctx);
+
+/* Counts and the grid contract of the context. */
+int gs_info(const gs_ctx* ctx, int64_t* n_low, int64_t* n_high, gs_grid_info* grid);
+
+/* Copy bytes from src (host memory when src_is_device == 0, else device
+ * memory) into a state field.  bytes must equal the field's size.  Writing
+ * GS_FIELD_HR_POS resets the internal order to the identity and sets w to
+ * each particle's index.  Non-finite x, y, z (or velocities) give
+ * GS_ERR_DOMAIN and leave the previous state in place.  Blocks when src is
+ * host memory. */
+int gs_write(gs_ctx* ctx, int field, const void* src, size_t bytes, int src_is_device);
+
+/* Copy a field into dst (host memory when dst_is_device == 0, else device
+ * memory).  bytes must equal the field's size.  HR fields come back in
+ * original-id order.  Blocks when dst is host memory; it also reports
+ * device-side errors raised since the previous check (GS_ERR_CAPACITY,
+ * GS_ERR_TIMEOUT). */
+int gs_read(gs_ctx* ctx, int field, void* dst, size_t bytes, int dst_is_device);
+
+/* Replace SDF number index (0 <= index < n_sdf) -- e.g. a kinematic bucket's
+ * pose for the next frame.  Stream-ordered. */
+int gs_set_sdf(gs_ctx* ctx, int index, const gs_sdf* sdf);
+
+/* Bin the LR particles at their current positions: stable counting sort by
+ * grid cell (fields GS_FIELD_LR_CELL_START / GS_FIELD_LR_SORTED_INDEX) and
+ * cell-ordered copies of LR position and velocity for the upsampling gather.
+ * gs_step_low and gs_upsample call this themselves. */
+int gs_bin_low(gs_ctx* ctx);
+
+/* Reorder the HR particles stably by fine cell key (grid contract above) so
+ * the upsampling gather reads them coalesced.  gs_upsample calls this every
+ * params.resort_every frames. */
+int gs_resort_high(gs_ctx* ctx);
+
+/* One LR time step of Algorithm 1 (Sec. 3): predict v += dt g, xt = x + dt v
+ * and the height-scaled inverse mass; build candidate pairs within
+ * neighbor_radius of xt; n_stab contact-only Jacobi passes (Eqs. 1-2)
+ * evaluated on x and applied to x and xt; iters contact + friction passes
+ * (Eqs. 1-4) on xt with constraint averaging; v = (xt - x)/dt, x = xt.
+ * Analytic SDF contacts act as partners of infinite mass.  dt > 0,
+ * 0 <= iters <= 1000.  Candidate overflow is reported as GS_ERR_CAPACITY by
+ * the next blocking call. */
+int gs_step_low(gs_ctx* ctx, float dt, int iters);
+
+/* One HR frame of Sec. 4 from the current LR state (x^{t+1}, v^{t+1}):
+ * (re)bin the LR particles, reorder HR when due, then for every HR particle
+ * w_ij = max(0, (1 - |x_ij|^2 / (9 r_low^2))^3) over LR within 3 r_low,
+ * vtilde = sum w v / sum w (0 when the sum is 0),
+ * alpha = 1 - max w if max w <= c1 or max w / sum w >= c2, else 0,
+ * v = (1 - alpha) vtilde + alpha (v + dt g), x = x + dt v,
+ * followed by the SDF rule: for each SDF component in order, when
+ * phi(x) < r_high the particle moves to phi = r_high along the normal and
+ * the normal velocity into the boundary (relative to the boundary velocity)
+ * is removed.  dt > 0. */
+int gs_upsample(gs_ctx* ctx, float dt);
+
+/* Block until the context's stream is idle and report device-side errors. */
+int gs_sync(gs_ctx* ctx);
+
+/* Kernel timing with CUDA events on the context's stream.  When enabled,
+ * every launch group below is bracketed by an event pair.  gs_timing_read
+ * blocks, returns the summed milliseconds and the number of launches of one
+ * group since the previous read, and resets that group. */
+enum {
+    GS_TIMER_BIN_LOW = 0,    /* LR binning (keys, sort, cell starts, copies) */
+    GS_TIMER_RESORT = 1,     /* HR reorder */
+    GS_TIMER_GATHER = 2,     /* upsampling gather + advection + SDF (one kernel) */
+    GS_TIMER_STEP_LOW = 3,   /* one whole LR step */
+    GS_TIMER_COUNT = 4
+};
+int gs_set_timing(gs_ctx* ctx, int enable);
+int gs_timing_read(gs_ctx* ctx, int timer, double* total_ms, int64_t* launches);
+
+/* Number of kernels this context has launched since creation. */
+int64_t gs_launch_count(const gs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H */

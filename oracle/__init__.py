@@ -26,7 +26,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 SDF_STRIDE = 20
 UP_KEYS = ["r_low", "r_high", "dt", "gx", "gy", "gz", "c1", "c2", "eps_w", "eps_x"]
 PB_KEYS = ["r", "dt", "gx", "gy", "gz", "mu_s", "mu_k", "n_stab", "iters", "mass_k",
-           "ground_z", "rc", "friction_mode", "eps_x"]
+           "ground_z", "rc", "friction_mode", "eps_x", "eps_impact"]
 
 _lib = None
 
@@ -154,7 +154,8 @@ def upsample(lr_x, lr_v, hr_x, hr_v, sdf, prm, sub=None, mode=0):
     """One HR frame of Sec. 4 for HR particles ``sub`` (all when None).
 
     ``prm`` holds r_low, r_high, dt, gx, gy, gz, c1, c2, eps_w, eps_x.
-    Returns dict(x, v, flag, alt_x, alt_v, diag) with diag = (S, wmax, alpha, n).
+    Returns dict(x, v, flag, alt_x, alt_v, diag) with diag = (S, wmax, alpha, n,
+    sens_x, sens_v).
     """
     lr_x, lr_v = _f64(lr_x, 3), _f64(lr_v, 3)
     hr_x, hr_v = _f64(hr_x, 3), _f64(hr_v, 3)
@@ -163,7 +164,7 @@ def upsample(lr_x, lr_v, hr_x, hr_v, sdf, prm, sub=None, mode=0):
     subv = None if sub is None else np.ascontiguousarray(sub, dtype=np.int64)
     n = len(hr_x) if subv is None else len(subv)
     out = dict(x=np.zeros((n, 3)), v=np.zeros((n, 3)), flag=np.zeros(n, np.int32),
-               alt_x=np.zeros((n, 3)), alt_v=np.zeros((n, 3)), diag=np.zeros((n, 4)))
+               alt_x=np.zeros((n, 3)), alt_v=np.zeros((n, 3)), diag=np.zeros((n, 6)))
     rc = _L().or_upsample(_ptr(lr_x), _ptr(lr_v), len(lr_x), _ptr(hr_x), _ptr(hr_v), len(hr_x),
                           _ptr(subv), 0 if subv is None else len(subv), _ptr(sdf), len(sdf), _ptr(p),
                           int(mode), _ptr(out["x"]), _ptr(out["v"]), _ptr(out["flag"]),
@@ -181,13 +182,14 @@ def pbd_step(x, v, inv_m, sdf, prm, mode=0):
     sdf = _f64(sdf, SDF_STRIDE) if sdf is not None and len(sdf) else np.zeros((0, SDF_STRIDE))
     p = _prm(prm, PB_KEYS)
     sus = np.zeros(len(x), np.int32)
-    stats = np.zeros(4, np.int64)
+    stats = np.zeros(5, np.int64)
     rc = _L().or_pbd_step(_ptr(x), _ptr(v), _ptr(inv_m), len(x), _ptr(sdf), len(sdf), _ptr(p),
                           int(mode), _ptr(sus), _ptr(stats))
     if rc != 0:
         raise RuntimeError(f"or_pbd_step failed ({rc})")
-    return x, v, sus.astype(bool), dict(pairs=int(stats[0]), ambiguous=int(stats[1]),
-                                        max_candidates=int(stats[2]), active=int(stats[3]))
+    return x, v, sus.astype(bool), dict(pairs=int(stats[0]), significant=int(stats[1]),
+                                        max_candidates=int(stats[2]), active=int(stats[3]),
+                                        ambiguous=int(stats[4]))
 
 
 def pairs_within(a, b, R, use_grid=False):

@@ -43,7 +43,7 @@ enum { UP_R_LOW = 0, UP_R_HIGH, UP_DT, UP_GX, UP_GY, UP_GZ, UP_C1, UP_C2,
 /* LR step parameters, prm[] indices */
 enum { PB_R = 0, PB_DT, PB_GX, PB_GY, PB_GZ, PB_MU_S, PB_MU_K, PB_N_STAB,
        PB_ITERS, PB_MASS_K, PB_GROUND_Z, PB_RC, PB_FRIC_MODE, PB_EPS_X,
-       PB_NPRM };
+       PB_EPS_IMPACT, PB_NPRM };
 
 static int g_threads = 1;
 
@@ -337,7 +337,7 @@ double or_weight(double d2, double r_low)
  * branch).  Ambiguous contact decisions are appended to amb[]. */
 static void hr_finish(const double* x0, const double* v0, const double* vt, double alpha,
                       const double* sdf, int n_sdf, const double* prm, int flip_k,
-                      double* xo, double* vo, int* amb, int* n_amb, int* hard)
+                      double* xo, double* vo, int* amb, int* n_amb, int* hard, int* n_act)
 {
     double dt = prm[UP_DT], rh = prm[UP_R_HIGH], eps_x = prm[UP_EPS_X];
     const double g[3] = {prm[UP_GX], prm[UP_GY], prm[UP_GZ]};
@@ -360,6 +360,7 @@ static void hr_finish(const double* x0, const double* v0, const double* vt, doub
             if (dec == flip_k) active = !active;
             if (!active) continue;
             if (tie) *hard = 1;
+            if (n_act) ++*n_act;
             const double* n = nn + 3 * c;
             double push = rh - phi[c];
             for (int k = 0; k < 3; ++k) xo[k] += push * n[k];
@@ -380,7 +381,9 @@ static void hr_finish(const double* x0, const double* v0, const double* vt, doub
  * flag: 0 = every decision clear of its margin; 1 = exactly one decision
  * inside its margin, alt_x/alt_v hold the other branch; 2 = more than one
  * (or a non-unique SDF normal), alt = primary.
- * diag (optional, 4 per output): sum w, max w, alpha, #LR with w > 0. */
+ * diag (optional, 6 per output): sum w, max w, alpha, #LR with w > 0, and
+ * the sensitivities |d x_out / d x_in| - 1 and |d v_out / d x_in| of the SDF
+ * rule (0 without an active contact). */
 int or_upsample(const double* lr_x, const double* lr_v, long N,
                 const double* hr_x, const double* hr_v, long M,
                 const long* sub, long n_sub,
@@ -394,7 +397,11 @@ int or_upsample(const double* lr_x, const double* lr_v, long N,
     if (mode == 1 && grid_build(&grid, lr_x, N, 3.0 * r) != 0) return -1;
     int nth = g_threads;
     int err = 0;
-#pragma omp parallel for schedule(dynamic, 64) num_threads(nth) if (nth > 1)
+#pragma omp parallel num_threads(nth) if (nth > 1)
+    {
+    long* cand = NULL;
+    if (mode == 1) cand = (long*)malloc((size_t)(N ? N : 1) * sizeof(long));
+#pragma omp for schedule(dynamic, 64)
     for (long k = 0; k < n_out; ++k) {
         long i = sub ? sub[k] : k;
         if (i < 0 || i >= M) { err = -2; continue; }
@@ -402,12 +409,8 @@ int or_upsample(const double* lr_x, const double* lr_v, long N,
         const double* vi = hr_v + 3 * i;
         double S = 0, V[3] = {0, 0, 0}, wmax = 0;
         long cnt = 0;
-        long* cand = NULL;
         long nc = N;
-        if (mode == 1) {
-            cand = (long*)malloc((size_t)(N ? N : 1) * sizeof(long));
-            nc = grid_query(&grid, xi, cand);
-        }
+        if (mode == 1) nc = grid_query(&grid, xi, cand);
         for (long q = 0; q < nc; ++q) {
             long j = cand ? cand[q] : q;
             double d[3] = {xi[0] - lr_x[3 * j], xi[1] - lr_x[3 * j + 1], xi[2] - lr_x[3 * j + 2]};
@@ -419,7 +422,6 @@ int or_upsample(const double* lr_x, const double* lr_v, long N,
             if (w > wmax) wmax = w;
             ++cnt;
         }
-        free(cand);
         /* interpolated LR velocity; with no LR particle in reach it is
          * undefined in the paper and alpha = 1 makes it irrelevant: use 0 */
         double vt[3] = {0, 0, 0};
@@ -437,9 +439,9 @@ int or_upsample(const double* lr_x, const double* lr_v, long N,
         if (Bamb && (A || (!B)) != prim) alt_out = !prim;
         if (Aamb && Bamb && ((!A) || (!B)) != prim) alt_out = !prim;
         double alpha = prim ? 1.0 - wmax : 0.0;
-        int amb[64], n_amb = 0, hard = 0;
+        int amb[64], n_amb = 0, hard = 0, n_act = 0;
         double xo[3], vo[3];
-        hr_finish(xi, vi, vt, alpha, sdf, n_sdf, prm, -1, xo, vo, amb, &n_amb, &hard);
+        hr_finish(xi, vi, vt, alpha, sdf, n_sdf, prm, -1, xo, vo, amb, &n_amb, &hard, &n_act);
         int n_total = n_amb + (alt_out != prim);
         double ax[3] = {xo[0], xo[1], xo[2]}, av[3] = {vo[0], vo[1], vo[2]};
         int fl = 0;
@@ -448,9 +450,32 @@ int or_upsample(const double* lr_x, const double* lr_v, long N,
             fl = 1;
             int tmp[64], nt = 0, h2 = 0;
             if (alt_out != prim)
-                hr_finish(xi, vi, vt, prim ? 0.0 : 1.0 - wmax, sdf, n_sdf, prm, -1, ax, av, tmp, &nt, &h2);
+                hr_finish(xi, vi, vt, prim ? 0.0 : 1.0 - wmax, sdf, n_sdf, prm, -1, ax, av, tmp, &nt, &h2, NULL);
             else
-                hr_finish(xi, vi, vt, alpha, sdf, n_sdf, prm, amb[0], ax, av, tmp, &nt, &h2);
+                hr_finish(xi, vi, vt, alpha, sdf, n_sdf, prm, amb[0], ax, av, tmp, &nt, &h2, NULL);
+        }
+        /* Conditioning of the SDF rule: near an edge or corner of a boundary
+         * the contact normal turns quickly with position, so a rounding of
+         * the advected position changes the result by more than the
+         * rounding itself.  Estimated by moving the particle by +-eps_x
+         * along each axis (decisions kept as they fall). */
+        double sens_x = 0.0, sens_v = 0.0;
+        if (n_act > 0 && !hard) {
+            double dlt = prm[UP_EPS_X];
+            for (int a = 0; a < 3; ++a)
+                for (int sgn = -1; sgn <= 1; sgn += 2) {
+                    double xp[3] = {xi[0], xi[1], xi[2]}, px[3], pv[3];
+                    int tmp[64], nt = 0, h2 = 0;
+                    xp[a] += sgn * dlt;
+                    hr_finish(xp, vi, vt, alpha, sdf, n_sdf, prm, -1, px, pv, tmp, &nt, &h2, NULL);
+                    if (nt != n_amb) continue;   /* a decision flipped: covered by the flags */
+                    double ex[3] = {px[0] - xo[0], px[1] - xo[1], px[2] - xo[2]};
+                    ex[a] -= sgn * dlt;
+                    double ev[3] = {pv[0] - vo[0], pv[1] - vo[1], pv[2] - vo[2]};
+                    double sx = sqrt(dot3(ex, ex)) / dlt, sv = sqrt(dot3(ev, ev)) / dlt;
+                    if (sx > sens_x) sens_x = sx;
+                    if (sv > sens_v) sens_v = sv;
+                }
         }
         for (int m = 0; m < 3; ++m) {
             out_x[3 * k + m] = xo[m];
@@ -460,11 +485,15 @@ int or_upsample(const double* lr_x, const double* lr_v, long N,
         }
         if (flag) flag[k] = fl;
         if (diag) {
-            diag[4 * k] = S;
-            diag[4 * k + 1] = wmax;
-            diag[4 * k + 2] = alpha;
-            diag[4 * k + 3] = (double)cnt;
+            diag[6 * k] = S;
+            diag[6 * k + 1] = wmax;
+            diag[6 * k + 2] = alpha;
+            diag[6 * k + 3] = (double)cnt;
+            diag[6 * k + 4] = sens_x;
+            diag[6 * k + 5] = sens_v;
         }
+    }
+    free(cand);
     }
     if (mode == 1) grid_free(&grid);
     return err;
@@ -476,21 +505,25 @@ int or_upsample(const double* lr_x, const double* lr_v, long N,
 
 typedef struct { long i, j; } or_pair;
 
-/* Candidate pairs i < j with |xt_i - xt_j| < Rc, ordered by (i, j). */
-static long make_pairs(const double* xt, long N, double Rc, int mode, or_pair** out, long* n_border,
-                       unsigned char* border_mark, double eps_x)
+/* Candidate pairs i < j with |xt_i - xt_j| < Rc, ordered by (i, j).  Pairs
+ * whose distance is within eps_x of Rc are marked in border[] (kept pairs)
+ * or listed in *out_excl (dropped pairs): a float32 implementation may
+ * decide them the other way. */
+static long make_pairs(const double* xt, long N, double Rc, int mode, or_pair** out, unsigned char** border,
+                       or_pair** out_excl, long* n_excl, double eps_x)
 {
-    long cap = 1024, n = 0;
+    long cap = 1024, n = 0, cap_e = 64, ne = 0;
     or_pair* P = (or_pair*)malloc((size_t)cap * sizeof(or_pair));
-    if (!P) return -1;
+    unsigned char* B = (unsigned char*)malloc((size_t)cap);
+    or_pair* E = (or_pair*)malloc((size_t)cap_e * sizeof(or_pair));
+    if (!P || !B || !E) return -1;
     double R2 = Rc * Rc;
     or_grid_t g;
     long* cand = NULL;
     if (mode == 1) {
-        if (grid_build(&g, xt, N, Rc + eps_x) != 0) { free(P); return -1; }
+        if (grid_build(&g, xt, N, Rc + eps_x) != 0) return -1;
         cand = (long*)malloc((size_t)(N ? N : 1) * sizeof(long));
     }
-    *n_border = 0;
     for (long i = 0; i < N; ++i) {
         long nc = N, q0 = i + 1;
         if (mode == 1) { nc = grid_query(&g, xt + 3 * i, cand); q0 = 0; }
@@ -499,36 +532,70 @@ static long make_pairs(const double* xt, long N, double Rc, int mode, or_pair** 
             if (j <= i) continue;
             double d[3] = {xt[3 * j] - xt[3 * i], xt[3 * j + 1] - xt[3 * i + 1], xt[3 * j + 2] - xt[3 * i + 2]};
             double d2 = dot3(d, d);
-            if (fabs(sqrt(d2) - Rc) <= eps_x) { (*n_border)++; border_mark[i] = border_mark[j] = 1; }
-            if (!(d2 < R2)) continue;
+            int bord = fabs(sqrt(d2) - Rc) <= eps_x;
+            if (!(d2 < R2)) {
+                if (bord) {
+                    if (ne == cap_e) { cap_e *= 2; E = (or_pair*)realloc(E, (size_t)cap_e * sizeof(or_pair)); }
+                    E[ne].i = i; E[ne].j = j; ++ne;
+                }
+                continue;
+            }
             if (n == cap) {
                 cap *= 2;
-                or_pair* Q = (or_pair*)realloc(P, (size_t)cap * sizeof(or_pair));
-                if (!Q) { free(P); free(cand); if (mode == 1) grid_free(&g); return -1; }
-                P = Q;
+                P = (or_pair*)realloc(P, (size_t)cap * sizeof(or_pair));
+                B = (unsigned char*)realloc(B, (size_t)cap);
+                if (!P || !B) return -1;
             }
             P[n].i = i;
             P[n].j = j;
+            B[n] = (unsigned char)bord;
             ++n;
         }
     }
     if (mode == 1) { free(cand); grid_free(&g); }
     *out = P;
+    *border = B;
+    *out_excl = E;
+    *n_excl = ne;
     return n;
+}
+
+/* One decision taken within its margin: had it gone the other way, the
+ * particle's summed correction would change by dD and its constraint count
+ * by dn. */
+typedef struct { long i; double dD[3]; int dn; } or_alt;
+
+typedef struct { or_alt* a; long n, cap; } or_alts;
+
+static void alt_push(or_alts* L, long i, const double* dD, int dn)
+{
+    if (L->n == L->cap) {
+        L->cap = L->cap ? 2 * L->cap : 256;
+        L->a = (or_alt*)realloc(L->a, (size_t)L->cap * sizeof(or_alt));
+    }
+    or_alt* e = &L->a[L->n++];
+    e->i = i;
+    e->dn = dn;
+    for (int k = 0; k < 3; ++k) e->dD[k] = dD[k];
 }
 
 /* Friction delta of Eqs. 3-4 for a relative tangential displacement perp
  * (the caller multiplies by the mass ratio and the sign).  thr_s / thr_k
- * are the static / kinetic thresholds.  *amb is set when the static test
- * is within eps of its threshold and the two branches differ. */
-static void friction_delta(const double* perp, double thr_s, double thr_k, double eps_x, double* f, int* amb)
+ * are the static / kinetic thresholds.  When the static test is within eps
+ * of its threshold and the branches differ, *amb is set and f_alt holds the
+ * other branch. */
+static void friction_delta(const double* perp, double thr_s, double thr_k, double eps_x, double* f, double* f_alt,
+                           int* amb)
 {
     double L = sqrt(dot3(perp, perp));
-    double scale;
-    if (L < thr_s) scale = 1.0;
-    else scale = (L > 0 && thr_k / L < 1.0) ? thr_k / L : 1.0;
-    if (fabs(L - thr_s) <= eps_x && thr_s != thr_k) *amb = 1;
-    for (int k = 0; k < 3; ++k) f[k] = perp[k] * scale;
+    double kin = (L > 0 && thr_k / L < 1.0) ? thr_k / L : 1.0;
+    double scale = L < thr_s ? 1.0 : kin;
+    double other = L < thr_s ? kin : 1.0;
+    *amb = fabs(L - thr_s) <= eps_x && scale != other;
+    for (int k = 0; k < 3; ++k) {
+        f[k] = perp[k] * scale;
+        f_alt[k] = perp[k] * other;
+    }
 }
 
 /* One LR time step (Algorithm 1) on N particles.
@@ -564,11 +631,15 @@ static void friction_delta(const double* perp, double thr_s, double thr_k, doubl
  *  - SDF contacts: a pair with an immovable partner (mass ratio 1), active
  *    when phi(xt_i) < r_LR, penetration (r_LR - phi) along n; friction uses
  *    the displacement relative to the boundary's displacement u_b dt.
- * suspect (optional, N): particles whose result depends on a decision taken
- * within eps_x of its threshold, directly or through later passes.
- * stats (optional): [0] #candidate pairs, [1] #ambiguous decisions,
- * [2] max candidates of one particle, [3] #active pair contacts in the last
- * pass. */
+ * Decisions taken within eps_x of their threshold (contact active, static or
+ * kinetic friction, SDF contact active, candidate membership) are evaluated
+ * both ways; when the other branch would move the particle's averaged
+ * correction by more than eps_impact the particle is suspect, and so is
+ * every candidate partner of a suspect in later passes.
+ * suspect (optional, N): 1 for suspect particles.
+ * stats (optional): [0] #candidate pairs, [1] #significant ambiguous
+ * decisions, [2] max candidates of one particle, [3] #active pair contacts
+ * in the last pass, [4] #ambiguous decisions (significant or not). */
 int or_pbd_step(double* x, double* v, const double* inv_m, long N,
                 const double* sdf, int n_sdf, const double* prm, int mode,
                 int* suspect, long* stats)
@@ -579,15 +650,16 @@ int or_pbd_step(double* x, double* v, const double* inv_m, long N,
     int n_stab = (int)prm[PB_N_STAB], iters = (int)prm[PB_ITERS];
     double mass_k = prm[PB_MASS_K], ground = prm[PB_GROUND_Z], Rc = prm[PB_RC];
     int fmode = (int)prm[PB_FRIC_MODE];
-    double eps_x = prm[PB_EPS_X];
+    double eps_x = prm[PB_EPS_X], eps_imp = prm[PB_EPS_IMPACT];
     double d0 = 2.0 * r;
+    size_t n1 = (size_t)(N ? N : 1);
 
-    double* xt = (double*)malloc((size_t)(N ? N : 1) * 3 * sizeof(double));
-    double* ws = (double*)malloc((size_t)(N ? N : 1) * sizeof(double));
-    double* D = (double*)malloc((size_t)(N ? N : 1) * 3 * sizeof(double));
-    long* cnt = (long*)malloc((size_t)(N ? N : 1) * sizeof(long));
-    unsigned char* mark = (unsigned char*)calloc((size_t)(N ? N : 1), 1);
-    unsigned char* mark2 = (unsigned char*)calloc((size_t)(N ? N : 1), 1);
+    double* xt = (double*)malloc(n1 * 3 * sizeof(double));
+    double* ws = (double*)malloc(n1 * sizeof(double));
+    double* D = (double*)malloc(n1 * 3 * sizeof(double));
+    long* cnt = (long*)malloc(n1 * sizeof(long));
+    unsigned char* mark = (unsigned char*)calloc(n1, 1);
+    unsigned char* mark2 = (unsigned char*)calloc(n1, 1);
     if (!xt || !ws || !D || !cnt || !mark || !mark2) return -1;
 
     /* Algorithm 1, first loop: v += dt g; xt = x + dt v; m* = m e^{-h(x)}.
@@ -601,26 +673,27 @@ int or_pbd_step(double* x, double* v, const double* inv_m, long N,
     }
 
     /* neighbour search and constraint generation */
-    or_pair* P = NULL;
-    long n_border = 0;
-    long np = make_pairs(xt, N, Rc, mode, &P, &n_border, mark, eps_x);
+    or_pair *P = NULL, *E = NULL;
+    unsigned char* border = NULL;
+    long n_excl = 0;
+    long np = make_pairs(xt, N, Rc, mode, &P, &border, &E, &n_excl, eps_x);
     if (np < 0) return -1;
-    long n_amb = n_border;
-    long maxc = 0;
+    long n_sig = 0, n_amb = 0, maxc = 0;
     if (stats) {
-        long* c = (long*)calloc((size_t)(N ? N : 1), sizeof(long));
+        long* c = (long*)calloc(n1, sizeof(long));
         for (long p = 0; p < np; ++p) { c[P[p].i]++; c[P[p].j]++; }
         for (long i = 0; i < N; ++i)
             if (c[i] > maxc) maxc = c[i];
         free(c);
     }
+    or_alts alts = {NULL, 0, 0};
 
     long active_last = 0;
     int total = n_stab + iters;
     for (int it = 0; it < total; ++it) {
         int stab = it < n_stab;
-        /* a particle that read a suspect neighbour in an earlier pass is
-         * itself suspect from now on */
+        /* a particle that read a suspect candidate partner in an earlier
+         * pass is itself suspect from now on */
         if (it > 0) {
             memcpy(mark2, mark, (size_t)N);
             for (long p = 0; p < np; ++p) {
@@ -630,45 +703,77 @@ int or_pbd_step(double* x, double* v, const double* inv_m, long N,
         }
         memset(D, 0, (size_t)N * 3 * sizeof(double));
         memset(cnt, 0, (size_t)N * sizeof(long));
+        alts.n = 0;
         active_last = 0;
         /* Stabilization repairs invalid positions at the start of the step
          * (Sec. 3): its contacts are evaluated on x, the solver's on xt. */
         const double* y = stab ? x : xt;
+        /* a candidate pair decided the other way by a float32 neighbour
+         * search matters only if it comes into contact */
+        for (long p = 0; p < n_excl; ++p) {
+            long i = E[p].i, j = E[p].j;
+            double e[3] = {y[3 * j] - y[3 * i], y[3 * j + 1] - y[3 * i + 1], y[3 * j + 2] - y[3 * i + 2]};
+            if (sqrt(dot3(e, e)) < d0 + eps_x) { mark[i] = mark[j] = 1; ++n_sig; }
+        }
         /* particle-particle contacts: Eqs. 1-2 (+ Eqs. 3-4 when solving) */
         for (long p = 0; p < np; ++p) {
             long i = P[p].i, j = P[p].j;
             double xij[3] = {y[3 * j] - y[3 * i], y[3 * j + 1] - y[3 * i + 1], y[3 * j + 2] - y[3 * i + 2]};
             double d2 = dot3(xij, xij);
             double d = sqrt(d2);
-            if (fabs(d - d0) <= eps_x) { mark[i] = mark[j] = 1; ++n_amb; }
-            if (!(d < d0) || d2 == 0.0) continue;
+            if (border[p] && d < d0 + eps_x) { mark[i] = mark[j] = 1; ++n_sig; }
+            int active = d < d0;
+            int amb_act = fabs(d - d0) <= eps_x;
+            if ((!active && !amb_act) || d2 == 0.0) continue;
             double wsum = ws[i] + ws[j];
             if (!(wsum > 0)) continue;
             double mi = ws[i] / wsum, mj = ws[j] / wsum;
             double pen = d0 - d;
             double u[3] = {xij[0] / d, xij[1] / d, xij[2] / d};
+            double ci[3], cj[3], ci_alt[3], cj_alt[3];
+            int amb_f = 0;
             for (int k = 0; k < 3; ++k) {
-                D[3 * i + k] -= mi * pen * u[k];
-                D[3 * j + k] += mj * pen * u[k];
+                ci[k] = -mi * pen * u[k];
+                cj[k] = mj * pen * u[k];
             }
+            memcpy(ci_alt, ci, sizeof ci);
+            memcpy(cj_alt, cj, sizeof cj);
             if (!stab) {
-                double dx[3], perp[3], f[3];
+                double dx[3], perp[3], f[3], fa[3];
                 for (int k = 0; k < 3; ++k)
                     dx[k] = (xt[3 * i + k] - x[3 * i + k]) - (xt[3 * j + k] - x[3 * j + k]);
                 double a = dot3(dx, xij) / d2;
                 for (int k = 0; k < 3; ++k) perp[k] = dx[k] - a * xij[k];
                 double base = (fmode == 1) ? pen : d0;
-                int amb = 0;
-                friction_delta(perp, base * mu_s, base * mu_k, eps_x, f, &amb);
-                if (amb) { mark[i] = mark[j] = 1; ++n_amb; }
+                friction_delta(perp, base * mu_s, base * mu_k, eps_x, f, fa, &amb_f);
                 for (int k = 0; k < 3; ++k) {
-                    D[3 * i + k] -= mi * f[k];
-                    D[3 * j + k] += mj * f[k];
+                    ci_alt[k] = ci[k] - mi * fa[k];
+                    cj_alt[k] = cj[k] + mj * fa[k];
+                    ci[k] -= mi * f[k];
+                    cj[k] += mj * f[k];
                 }
             }
-            cnt[i]++;
-            cnt[j]++;
-            ++active_last;
+            if (active) {
+                for (int k = 0; k < 3; ++k) {
+                    D[3 * i + k] += ci[k];
+                    D[3 * j + k] += cj[k];
+                }
+                cnt[i]++;
+                cnt[j]++;
+                ++active_last;
+            }
+            if (amb_act) {
+                double si = active ? -1.0 : 1.0;
+                double a1[3] = {si * ci[0], si * ci[1], si * ci[2]}, a2[3] = {si * cj[0], si * cj[1], si * cj[2]};
+                alt_push(&alts, i, a1, active ? -1 : 1);
+                alt_push(&alts, j, a2, active ? -1 : 1);
+            }
+            if (amb_f && active) {
+                double a1[3] = {ci_alt[0] - ci[0], ci_alt[1] - ci[1], ci_alt[2] - ci[2]};
+                double a2[3] = {cj_alt[0] - cj[0], cj_alt[1] - cj[1], cj_alt[2] - cj[2]};
+                alt_push(&alts, i, a1, 0);
+                alt_push(&alts, j, a2, 0);
+            }
         }
         /* SDF contacts */
         for (long i = 0; i < N; ++i) {
@@ -681,26 +786,58 @@ int or_pbd_step(double* x, double* v, const double* inv_m, long N,
                 const double* ub = rec + 13;
                 double bmu_s = sqrt(mu_s * rec[16]), bmu_k = sqrt(mu_k * rec[17]);
                 for (int c = 0; c < nc; ++c) {
-                    if (fabs(phi[c] - r) <= eps_x) { mark[i] = 1; ++n_amb; }
-                    if (!(phi[c] < r)) continue;
-                    if (tie) { mark[i] = 1; ++n_amb; }
+                    int active = phi[c] < r;
+                    int amb_act = fabs(phi[c] - r) <= eps_x;
+                    if (!active && !amb_act) continue;
+                    if (tie) { mark[i] = 1; ++n_sig; }
                     const double* n = nn + 3 * c;
                     double pen = r - phi[c];
-                    for (int k = 0; k < 3; ++k) D[3 * i + k] += pen * n[k];
+                    double ci[3], ci_alt[3];
+                    int amb_f = 0;
+                    for (int k = 0; k < 3; ++k) ci[k] = pen * n[k];
+                    memcpy(ci_alt, ci, sizeof ci);
                     if (!stab) {
-                        double dx[3], perp[3], f[3];
+                        double dx[3], perp[3], f[3], fa[3];
                         for (int k = 0; k < 3; ++k) dx[k] = (xt[3 * i + k] - x[3 * i + k]) - ub[k] * dt;
                         double a = dot3(dx, n);
                         for (int k = 0; k < 3; ++k) perp[k] = dx[k] - a * n[k];
                         double base = (fmode == 1) ? pen : d0;
-                        int amb = 0;
-                        friction_delta(perp, base * bmu_s, base * bmu_k, eps_x, f, &amb);
-                        if (amb) { mark[i] = 1; ++n_amb; }
-                        for (int k = 0; k < 3; ++k) D[3 * i + k] -= f[k];
+                        friction_delta(perp, base * bmu_s, base * bmu_k, eps_x, f, fa, &amb_f);
+                        for (int k = 0; k < 3; ++k) {
+                            ci_alt[k] = ci[k] - fa[k];
+                            ci[k] -= f[k];
+                        }
                     }
-                    cnt[i]++;
+                    if (active) {
+                        for (int k = 0; k < 3; ++k) D[3 * i + k] += ci[k];
+                        cnt[i]++;
+                    }
+                    if (amb_act) {
+                        double si = active ? -1.0 : 1.0;
+                        double a1[3] = {si * ci[0], si * ci[1], si * ci[2]};
+                        alt_push(&alts, i, a1, active ? -1 : 1);
+                    }
+                    if (amb_f && active) {
+                        double a1[3] = {ci_alt[0] - ci[0], ci_alt[1] - ci[1], ci_alt[2] - ci[2]};
+                        alt_push(&alts, i, a1, 0);
+                    }
                 }
             }
+        }
+        /* would the other branch of an ambiguous decision move the particle
+         * by more than eps_impact? */
+        for (long q = 0; q < alts.n; ++q) {
+            const or_alt* e = &alts.a[q];
+            long i = e->i;
+            double u0[3] = {0, 0, 0}, u1[3] = {0, 0, 0};
+            long n0 = cnt[i], n1a = cnt[i] + e->dn;
+            for (int k = 0; k < 3; ++k) {
+                if (n0 > 0) u0[k] = D[3 * i + k] / (double)n0;
+                if (n1a > 0) u1[k] = (D[3 * i + k] + e->dD[k]) / (double)n1a;
+            }
+            double dd[3] = {u1[0] - u0[0], u1[1] - u0[1], u1[2] - u0[2]};
+            ++n_amb;
+            if (sqrt(dot3(dd, dd)) > eps_imp) { mark[i] = 1; ++n_sig; }
         }
         /* Jacobi averaging: delta_i = (1/n_i) sum_k delta_ik.  Stabilization
          * applies it to xt and x, solver iterations to xt only. */
@@ -723,11 +860,15 @@ int or_pbd_step(double* x, double* v, const double* inv_m, long N,
         for (long i = 0; i < N; ++i) suspect[i] = mark[i];
     if (stats) {
         stats[0] = np;
-        stats[1] = n_amb;
+        stats[1] = n_sig;
         stats[2] = maxc;
         stats[3] = active_last;
+        stats[4] = n_amb;
     }
+    free(alts.a);
     free(P);
+    free(E);
+    free(border);
     free(xt);
     free(ws);
     free(D);

@@ -1,0 +1,309 @@
+"""Python binding of libgs (include/gs.h): argument marshalling only.
+
+Every function here has the name of the C entry point it wraps and does
+nothing but convert arguments; all of the method runs in the CUDA kernels of
+``libgs.so``.  The library must have been built (``build.build()`` or
+``__graft_entry__.build()``); if it is missing this module raises instead of
+falling back to anything else.
+
+``Context`` is a small convenience owner of one ``gs_ctx`` that builds the C
+scene structure from the dictionaries of the ``scenes`` package and moves
+numpy arrays or torch tensors through ``gs_write`` / ``gs_read``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+GS_OK, GS_ERR_ARG, GS_ERR_OOM, GS_ERR_CUDA = 0, -1, -2, -3
+GS_ERR_DOMAIN, GS_ERR_TIMEOUT, GS_ERR_STATE, GS_ERR_CAPACITY = -4, -5, -6, -7
+STATUS_NAMES = {0: "GS_OK", -1: "GS_ERR_ARG", -2: "GS_ERR_OOM", -3: "GS_ERR_CUDA", -4: "GS_ERR_DOMAIN",
+                -5: "GS_ERR_TIMEOUT", -6: "GS_ERR_STATE", -7: "GS_ERR_CAPACITY"}
+GS_SDF_BOX_INTERIOR, GS_SDF_CONE_SHELL, GS_SDF_SOLID_BOX = 1, 2, 3
+GS_MAX_SDF = 16
+(GS_FIELD_LR_POS, GS_FIELD_LR_VEL, GS_FIELD_HR_POS, GS_FIELD_HR_VEL, GS_FIELD_HR_POS_INTERNAL,
+ GS_FIELD_HR_VEL_INTERNAL, GS_FIELD_LR_CELL_START, GS_FIELD_LR_SORTED_INDEX, GS_FIELD_HR_SORTED_KEY) = range(9)
+GS_TIMER_BIN_LOW, GS_TIMER_RESORT, GS_TIMER_GATHER, GS_TIMER_STEP_LOW, GS_TIMER_COUNT = range(5)
+
+
+class gs_sdf(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("p", ctypes.c_float * 12), ("vel", ctypes.c_float * 3),
+                ("mu_s", ctypes.c_float), ("mu_k", ctypes.c_float)]
+
+
+class gs_params(ctypes.Structure):
+    _fields_ = [("gravity", ctypes.c_float * 3), ("mu_s", ctypes.c_float), ("mu_k", ctypes.c_float),
+                ("c1", ctypes.c_float), ("c2", ctypes.c_float), ("n_stab", ctypes.c_int32),
+                ("mass_scale_k", ctypes.c_float), ("ground_z", ctypes.c_float),
+                ("neighbor_radius", ctypes.c_float), ("friction_mode", ctypes.c_int32),
+                ("resort_every", ctypes.c_int32), ("max_neighbors", ctypes.c_int32)]
+
+
+class gs_scene(ctypes.Structure):
+    _fields_ = [("box_lo", ctypes.c_float * 3), ("box_hi", ctypes.c_float * 3), ("n_low", ctypes.c_int32),
+                ("n_sdf", ctypes.c_int32), ("sdf", ctypes.POINTER(gs_sdf)), ("params", gs_params)]
+
+
+class gs_grid_info(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_float * 3), ("h", ctypes.c_float), ("inv_h", ctypes.c_float),
+                ("dims", ctypes.c_int32 * 3), ("n_cell", ctypes.c_int64)]
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "gs_default_params": (None, [ctypes.POINTER(gs_params)]),
+    "gs_create": (ctypes.c_int, [ctypes.POINTER(gs_scene), ctypes.c_float, ctypes.c_float, ctypes.c_int, _P,
+                                 ctypes.POINTER(_P)]),
+    "gs_destroy": (None, [_P]),
+    "gs_last_error": (ctypes.c_char_p, [_P]),
+    "gs_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                               ctypes.POINTER(gs_grid_info)]),
+    "gs_write": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, ctypes.c_int]),
+    "gs_read": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, ctypes.c_int]),
+    "gs_set_sdf": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(gs_sdf)]),
+    "gs_bin_low": (ctypes.c_int, [_P]),
+    "gs_resort_high": (ctypes.c_int, [_P]),
+    "gs_step_low": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_int]),
+    "gs_upsample": (ctypes.c_int, [_P, ctypes.c_float]),
+    "gs_sync": (ctypes.c_int, [_P]),
+    "gs_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gs_timing_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_int64)]),
+    "gs_launch_count": (ctypes.c_int64, [_P]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libgs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgs.so is not built ({path}); run __graft_entry__.build() first")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class GsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+# --------------------------------------------------- thin C entry points ---
+def gs_default_params():
+    p = gs_params()
+    lib().gs_default_params(ctypes.byref(p))
+    return p
+
+
+def gs_create(scene, r_low, r_high, ratio, stream=None):
+    ctx = _P()
+    rc = lib().gs_create(ctypes.byref(scene), r_low, r_high, ratio, stream, ctypes.byref(ctx))
+    if rc != GS_OK:
+        raise GsError(rc, "gs_create failed")
+    return ctx
+
+
+def gs_destroy(ctx):
+    lib().gs_destroy(ctx)
+
+
+def gs_last_error(ctx):
+    return lib().gs_last_error(ctx).decode()
+
+
+def _check(ctx, rc, what):
+    if rc != GS_OK:
+        raise GsError(rc, f"{what}: {gs_last_error(ctx)}")
+    return rc
+
+
+def gs_info(ctx):
+    nl, nh, g = ctypes.c_int64(), ctypes.c_int64(), gs_grid_info()
+    _check(ctx, lib().gs_info(ctx, ctypes.byref(nl), ctypes.byref(nh), ctypes.byref(g)), "gs_info")
+    return nl.value, nh.value, g
+
+
+def gs_write(ctx, field, ptr, nbytes, src_is_device):
+    return lib().gs_write(ctx, field, ptr, nbytes, int(src_is_device))
+
+
+def gs_read(ctx, field, ptr, nbytes, dst_is_device):
+    return lib().gs_read(ctx, field, ptr, nbytes, int(dst_is_device))
+
+
+def gs_set_sdf(ctx, index, sdf):
+    return lib().gs_set_sdf(ctx, index, ctypes.byref(sdf))
+
+
+def gs_bin_low(ctx):
+    return lib().gs_bin_low(ctx)
+
+
+def gs_resort_high(ctx):
+    return lib().gs_resort_high(ctx)
+
+
+def gs_step_low(ctx, dt, iters):
+    return lib().gs_step_low(ctx, dt, iters)
+
+
+def gs_upsample(ctx, dt):
+    return lib().gs_upsample(ctx, dt)
+
+
+def gs_sync(ctx):
+    return lib().gs_sync(ctx)
+
+
+def gs_set_timing(ctx, enable):
+    return lib().gs_set_timing(ctx, int(enable))
+
+
+def gs_timing_read(ctx, timer):
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(ctx, lib().gs_timing_read(ctx, timer, ctypes.byref(ms), ctypes.byref(n)), "gs_timing_read")
+    return ms.value, n.value
+
+
+def gs_launch_count(ctx):
+    return lib().gs_launch_count(ctx)
+
+
+# ------------------------------------------------------------ marshalling ---
+def make_sdf(rec) -> gs_sdf:
+    s = gs_sdf()
+    s.kind = int(rec["kind"])
+    for k, v in enumerate(rec["p"][:12]):
+        s.p[k] = float(v)
+    for k, v in enumerate(rec["vel"][:3]):
+        s.vel[k] = float(v)
+    s.mu_s = float(rec["mu_s"])
+    s.mu_k = float(rec["mu_k"])
+    return s
+
+
+def make_scene(sc, **overrides):
+    """C scene from a ``scenes`` dictionary; keyword overrides set gs_params
+    fields (e.g. n_stab=1, resort_every=0)."""
+    prm = gs_default_params()
+    g = sc.get("gravity", (0.0, 0.0, -9.81))
+    for k in range(3):
+        prm.gravity[k] = float(g[k])
+    prm.mu_s = float(sc.get("mu_s", prm.mu_s))
+    prm.mu_k = float(sc.get("mu_k", prm.mu_k))
+    for k, v in overrides.items():
+        if k == "gravity":
+            for a in range(3):
+                prm.gravity[a] = float(v[a])
+        else:
+            setattr(prm, k, v)
+    arr = (gs_sdf * max(1, len(sc["sdfs"])))(*[make_sdf(r) for r in sc["sdfs"]])
+    scene = gs_scene()
+    for k in range(3):
+        scene.box_lo[k] = float(sc["box_lo"][k])
+        scene.box_hi[k] = float(sc["box_hi"][k])
+    scene.n_low = int(len(sc["lr_pos"]))
+    scene.n_sdf = len(sc["sdfs"])
+    scene.sdf = ctypes.cast(arr, ctypes.POINTER(gs_sdf))
+    scene.params = prm
+    scene._keep = arr
+    return scene
+
+
+def _ptr_of(a):
+    """(pointer, nbytes, is_device) of a numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return a.ctypes.data, a.nbytes, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), a.numel() * a.element_size(), int(a.is_cuda)
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+class Context:
+    """Owner of one gs_ctx built from a ``scenes`` dictionary."""
+
+    def __init__(self, sc, stream=None, load_state=True, **overrides):
+        self.scene = make_scene(sc, **overrides)
+        self.ctx = gs_create(self.scene, float(sc["r_low"]), float(sc["r_high"]), int(sc["ratio"]), stream)
+        self.n_low, self.n_high, self.grid = gs_info(self.ctx)
+        if load_state:
+            self.write(GS_FIELD_LR_POS, sc["lr_pos"])
+            self.write(GS_FIELD_LR_VEL, sc["lr_vel"])
+            self.write(GS_FIELD_HR_POS, sc["hr_pos"])
+            self.write(GS_FIELD_HR_VEL, sc["hr_vel"])
+
+    def close(self):
+        if self.ctx:
+            gs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def write(self, field, buf):
+        p, n, dev = _ptr_of(buf)
+        return _check(self.ctx, gs_write(self.ctx, field, p, n, dev), "gs_write")
+
+    def read(self, field, out=None):
+        if out is None:
+            counts = {GS_FIELD_LR_POS: (self.n_low, 4), GS_FIELD_LR_VEL: (self.n_low, 4),
+                      GS_FIELD_HR_POS: (self.n_high, 4), GS_FIELD_HR_VEL: (self.n_high, 4),
+                      GS_FIELD_HR_POS_INTERNAL: (self.n_high, 4), GS_FIELD_HR_VEL_INTERNAL: (self.n_high, 4),
+                      GS_FIELD_LR_CELL_START: (int(self.grid.n_cell) + 1,),
+                      GS_FIELD_LR_SORTED_INDEX: (self.n_low,), GS_FIELD_HR_SORTED_KEY: (self.n_high,)}
+            shape = counts[field]
+            out = np.zeros(shape, np.float32 if len(shape) == 2 else np.uint32)
+        p, n, dev = _ptr_of(out)
+        _check(self.ctx, gs_read(self.ctx, field, p, n, dev), "gs_read")
+        return out
+
+    def set_sdf(self, index, rec):
+        return _check(self.ctx, gs_set_sdf(self.ctx, index, make_sdf(rec)), "gs_set_sdf")
+
+    def bin_low(self):
+        return _check(self.ctx, gs_bin_low(self.ctx), "gs_bin_low")
+
+    def resort_high(self):
+        return _check(self.ctx, gs_resort_high(self.ctx), "gs_resort_high")
+
+    def step_low(self, dt, iters):
+        return _check(self.ctx, gs_step_low(self.ctx, float(dt), int(iters)), "gs_step_low")
+
+    def upsample(self, dt):
+        return _check(self.ctx, gs_upsample(self.ctx, float(dt)), "gs_upsample")
+
+    def sync(self):
+        return _check(self.ctx, gs_sync(self.ctx), "gs_sync")
+
+    def set_timing(self, on=True):
+        return _check(self.ctx, gs_set_timing(self.ctx, on), "gs_set_timing")
+
+    def timing_read(self, timer):
+        return gs_timing_read(self.ctx, timer)
+
+    def launches(self):
+        return gs_launch_count(self.ctx)

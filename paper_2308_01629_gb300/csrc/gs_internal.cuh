@@ -1,0 +1,165 @@
+// gs_internal.cuh -- context layout and launch helpers shared by the CUDA
+// translation units of the library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "gs.h"
+
+// Dense-grid contract (see gs.h): origin, cell side, inverse, dimensions.
+struct GridDev {
+    float ox, oy, oz;
+    float h, inv_h;
+    int dx, dy, dz;
+};
+
+// Device-side error bits, reported by the next blocking call.
+enum : int {
+    GS_DEVERR_NEIGHBOR_CAP = 1,   // an LR particle had more candidates than max_neighbors
+    GS_DEVERR_BAD_ID = 2,         // an HR id outside [0, n_high) was met while unpermuting
+};
+
+struct gs_ctx {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+
+    int64_t n_low = 0, n_high = 0;
+    float r_low = 0, r_high = 0;
+    int ratio = 1;
+    gs_params prm{};
+    int n_sdf = 0;
+    gs_sdf sdf_host[GS_MAX_SDF]{};
+    gs_sdf* d_sdf = nullptr;
+
+    GridDev grid{};
+    int64_t n_cell = 0;
+    int lr_key_bits = 0, hr_key_bits = 0;
+
+    // LR state (original order) and the binning view
+    float4* lr_pos = nullptr;
+    float4* lr_vel = nullptr;
+    uint32_t* lr_keys[2] = {nullptr, nullptr};   // radix ping-pong
+    uint32_t* lr_vals[2] = {nullptr, nullptr};
+    uint32_t* lr_sorted_keys = nullptr;           // points into lr_keys after a sort
+    uint32_t* lr_sorted_idx = nullptr;            // points into lr_vals after a sort
+    uint32_t* lr_cell_start = nullptr;            // n_cell + 1
+    float4* lr_spos = nullptr;                    // cell-ordered LR position (upsampling view)
+    float4* lr_svel = nullptr;                    // cell-ordered LR velocity
+    bool lr_binned = false;
+
+    // LR step buffers (cell order)
+    float4* s_xt[2] = {nullptr, nullptr};
+    float4* s_x[2] = {nullptr, nullptr};
+    float4* lr_xt = nullptr;                      // predicted positions, original order
+    uint32_t* nbr = nullptr;                      // [cap][n_low] candidate slots
+    uint32_t* nbr_cnt = nullptr;
+    int nbr_cap = 64;
+
+    // HR state (internal order), ping-pong
+    float4* hr_pos[2] = {nullptr, nullptr};
+    float4* hr_vel[2] = {nullptr, nullptr};
+    int hr_cur = 0;
+    bool hr_identity = true;
+    uint32_t* hr_keys[2] = {nullptr, nullptr};
+    uint32_t* hr_vals[2] = {nullptr, nullptr};
+    uint32_t* hr_sorted_keys = nullptr;
+    bool hr_keys_valid = false;
+    float4* tmp4 = nullptr;                       // n_high staging for reads / writes
+
+    // radix sort histogram scratch
+    uint32_t* sort_hist = nullptr;
+    size_t sort_hist_cap = 0;
+
+    // errors
+    int* d_err = nullptr;
+    int* h_err = nullptr;                         // pinned
+    std::string last_error;
+    bool poisoned = false;
+
+    int64_t frame = 0;
+    int64_t launches = 0;
+
+    // timing
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[GS_TIMER_COUNT];
+};
+
+// ---- launchers implemented in the .cu files --------------------------------
+// sort.cu
+size_t gs_sort_hist_words(int64_t n);
+int gs_key_bits(int64_t n_keys);
+// Stable LSD radix sort of (keys, vals) by the low key_bits bits; the result
+// lands in keys[*which] / vals[*which] (which is flipped once per pass).
+cudaError_t gs_radix_sort(cudaStream_t s, uint32_t* keys[2], uint32_t* vals[2], int* which, uint32_t* hist,
+                          int64_t n, int key_bits, int64_t* launches);
+cudaError_t gs_launch_cell_keys(cudaStream_t s, const float4* pos, int64_t n, GridDev g, int fine, uint32_t* keys,
+                                uint32_t* vals, int64_t* launches);
+cudaError_t gs_launch_cell_start(cudaStream_t s, const uint32_t* sorted_keys, int64_t n, int64_t n_cell,
+                                 uint32_t* start, int64_t* launches);
+cudaError_t gs_launch_gather2(cudaStream_t s, const uint32_t* idx, const float4* a, const float4* b, float4* a_out,
+                              float4* b_out, int64_t n, int64_t* launches);
+cudaError_t gs_launch_unpermute(cudaStream_t s, const float4* pos_internal, const float4* field_internal,
+                                float4* out, int64_t n, int* err, int64_t* launches);
+cudaError_t gs_launch_permute_in(cudaStream_t s, const float4* pos_internal, const float4* field_original,
+                                 float4* out, int64_t n, int* err, int64_t* launches);
+cudaError_t gs_launch_set_ids(cudaStream_t s, float4* pos, int64_t n, int64_t* launches);
+cudaError_t gs_launch_check_finite(cudaStream_t s, const float4* a, int64_t n, int* flag, int64_t* launches);
+
+// upsample.cu
+struct UpsampleArgs {
+    const float4* hr_pos;
+    const float4* hr_vel;
+    float4* out_pos;
+    float4* out_vel;
+    int64_t m;
+    const float4* lr_spos;
+    const float4* lr_svel;
+    const uint32_t* cell_start;
+    GridDev g;
+    float r_low, r_high, dt;
+    float gx, gy, gz;
+    float c1, c2;
+    const gs_sdf* sdf;
+    int n_sdf;
+};
+cudaError_t gs_launch_upsample(cudaStream_t s, const UpsampleArgs& a, int64_t* launches);
+
+// pbd.cu
+struct PbdArgs {
+    int64_t n;
+    float r, dt;
+    float gx, gy, gz;
+    float mu_s, mu_k;
+    float mass_k, ground_z;
+    float rc;
+    int friction_mode;
+    const gs_sdf* sdf;
+    int n_sdf;
+};
+cudaError_t gs_launch_predict(cudaStream_t s, const PbdArgs& a, const float4* pos, const float4* vel, float4* xt,
+                              int64_t* launches);
+cudaError_t gs_launch_step_gather(cudaStream_t s, int64_t n, const uint32_t* idx, const float4* xt,
+                                  const float4* pos, float4* s_xt, float4* s_x, int64_t* launches);
+cudaError_t gs_launch_neighbors(cudaStream_t s, const PbdArgs& a, const float4* s_xt, const uint32_t* skeys,
+                                const uint32_t* cell_start, GridDev g, uint32_t* nbr, uint32_t* cnt, int cap,
+                                int* err, int64_t* launches);
+cudaError_t gs_launch_pass(cudaStream_t s, const PbdArgs& a, int stab, const float4* x_in, const float4* xt_in,
+                           float4* x_out, float4* xt_out, const uint32_t* nbr, const uint32_t* cnt, int cap,
+                           int64_t* launches);
+cudaError_t gs_launch_finalize(cudaStream_t s, const PbdArgs& a, const uint32_t* idx, const float4* s_x,
+                               const float4* s_xt, float4* pos, float4* vel, int64_t* launches);
+
+// Grid-stride helper: blocks for n threads of `threads` each, capped.
+inline unsigned gs_blocks(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 2147483647LL) b = 2147483647LL;
+    return (unsigned)b;
+}

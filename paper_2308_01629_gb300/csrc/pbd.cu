@@ -1,0 +1,245 @@
+// pbd.cu -- one LR time step of Algorithm 1 (Sec. 3) on the GPU.
+//
+// The step runs in cell order: after prediction the LR set is binned on its
+// predicted positions, every particle collects its candidate partners within
+// the neighbour radius from the 27 surrounding cells once, and each Jacobi
+// pass is one launch in which a thread gathers the corrections of all its
+// active constraints (a per-particle gather instead of a scatter, so no
+// atomics and a fixed summation order):
+//   contact (Eqs. 1-2):   dx_i = -mhat_ij (2 r - |x_ij|) x_ij / |x_ij|,
+//                         mhat_ij = w_i / (w_i + w_j), w = 1 / m*
+//   friction (Eqs. 3-4):  relative displacement over the step so far
+//                         (xt_i - x_i) - (xt_j - x_j), tangential part,
+//                         static below 2 r mu_s, else scaled by
+//                         min(2 r mu_k / |dx_perp|, 1)
+//   averaging:            dx_i = (1 / n_i) sum_k dx_ik
+// SDF contacts act as partners of infinite mass (mass ratio 1).  The
+// stabilization passes evaluate their contacts on x and move x and xt; the
+// solver passes evaluate and move xt.
+#include <cuda_runtime.h>
+
+#include "gs_internal.cuh"
+#include "sdf.cuh"
+
+namespace {
+
+__global__ void k_predict(const PbdArgs a, const float4* __restrict__ pos, const float4* __restrict__ vel,
+                          float4* __restrict__ xt)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    float4 x = pos[i], v = vel[i];
+    float vx = v.x + a.dt * a.gx, vy = v.y + a.dt * a.gy, vz = v.z + a.dt * a.gz;
+    // 1/m* = (1/m) e^{h(x)}, h = k (z - ground), at the start-of-step position
+    float ws = x.w * expf(a.mass_k * (x.z - a.ground_z));
+    xt[i] = make_float4(x.x + a.dt * vx, x.y + a.dt * vy, x.z + a.dt * vz, ws);
+}
+
+__global__ void k_step_gather(int64_t n, const uint32_t* __restrict__ idx, const float4* __restrict__ xt,
+                              const float4* __restrict__ pos, float4* __restrict__ s_xt, float4* __restrict__ s_x)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    uint32_t i = idx[p];
+    s_xt[p] = xt[i];
+    s_x[p] = pos[i];   // w carries the inverse mass
+}
+
+__global__ void k_neighbors(const PbdArgs a, const float4* __restrict__ s_xt, const uint32_t* __restrict__ skeys,
+                            const uint32_t* __restrict__ cell_start, GridDev g, uint32_t* __restrict__ nbr,
+                            uint32_t* __restrict__ cnt, int cap, int* err)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.n) return;
+    const float4 xp = s_xt[p];
+    const uint32_t c = skeys[p];
+    const int cx = (int)(c % (uint32_t)g.dx);
+    const int cy = (int)((c / (uint32_t)g.dx) % (uint32_t)g.dy);
+    const int cz = (int)(c / ((uint32_t)g.dx * (uint32_t)g.dy));
+    const float rc2 = a.rc * a.rc;
+    const int x0 = cx > 0 ? cx - 1 : 0, x1 = cx + 1 < g.dx ? cx + 1 : g.dx - 1;
+    int k = 0;
+    for (int z = cz - 1; z <= cz + 1; ++z) {
+        if (z < 0 || z >= g.dz) continue;
+        for (int y = cy - 1; y <= cy + 1; ++y) {
+            if (y < 0 || y >= g.dy) continue;
+            const int64_t row = ((int64_t)z * g.dy + y) * g.dx;
+            const uint32_t b = cell_start[row + x0], e = cell_start[row + x1 + 1];
+            for (uint32_t q = b; q < e; ++q) {
+                if ((int64_t)q == p) continue;
+                float4 xq = s_xt[q];
+                float dx = xq.x - xp.x, dy = xq.y - xp.y, dz = xq.z - xp.z;
+                if (dx * dx + dy * dy + dz * dz < rc2) {
+                    if (k < cap) nbr[(int64_t)k * a.n + p] = q;
+                    ++k;
+                }
+            }
+        }
+    }
+    if (k > cap) {
+        atomicOr(err, GS_DEVERR_NEIGHBOR_CAP);
+        k = cap;
+    }
+    cnt[p] = (uint32_t)k;
+}
+
+// Eqs. 3-4 friction delta for a tangential relative displacement (px,py,pz).
+__device__ __forceinline__ float friction_scale(float L, float thr_s, float thr_k)
+{
+    if (L < thr_s) return 1.0f;
+    return (L > 0.0f && thr_k / L < 1.0f) ? thr_k / L : 1.0f;
+}
+
+__global__ void k_pass(const PbdArgs a, int stab, const float4* __restrict__ x_in, const float4* __restrict__ xt_in,
+                       float4* __restrict__ x_out, float4* __restrict__ xt_out, const uint32_t* __restrict__ nbr,
+                       const uint32_t* __restrict__ cnt)
+{
+    __shared__ gs_sdf s_sdf[GS_MAX_SDF];
+    for (int k = threadIdx.x; k < a.n_sdf; k += blockDim.x) s_sdf[k] = a.sdf[k];
+    __syncthreads();
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.n) return;
+    const float d0 = 2.0f * a.r;
+    const float4 xtp = xt_in[p];
+    const float4 xp = x_in[p];
+    const float4 yp = stab ? xp : xtp;          // positions the constraints are evaluated on
+    const float wp = xtp.w;                      // inverse height-scaled mass
+    const float dpx = xtp.x - xp.x, dpy = xtp.y - xp.y, dpz = xtp.z - xp.z;
+    float Dx = 0.f, Dy = 0.f, Dz = 0.f;
+    int n_act = 0;
+    const int nc = (int)cnt[p];
+    for (int k = 0; k < nc; ++k) {
+        const uint32_t q = nbr[(int64_t)k * a.n + p];
+        const float4 xtq = xt_in[q];
+        const float4 xq = x_in[q];
+        const float4 yq = stab ? xq : xtq;
+        const float ex = yq.x - yp.x, ey = yq.y - yp.y, ez = yq.z - yp.z;
+        const float d2 = ex * ex + ey * ey + ez * ez;
+        const float d = sqrtf(d2);
+        if (!(d < d0) || d2 == 0.0f) continue;
+        const float wsum = wp + xtq.w;
+        if (!(wsum > 0.0f)) continue;
+        const float m = wp / wsum;
+        const float pen = d0 - d;
+        const float s = m * pen / d;
+        Dx -= s * ex;
+        Dy -= s * ey;
+        Dz -= s * ez;
+        if (!stab) {
+            const float rx = dpx - (xtq.x - xq.x), ry = dpy - (xtq.y - xq.y), rz = dpz - (xtq.z - xq.z);
+            const float al = (rx * ex + ry * ey + rz * ez) / d2;
+            const float tx = rx - al * ex, ty = ry - al * ey, tz = rz - al * ez;
+            const float L = sqrtf(tx * tx + ty * ty + tz * tz);
+            const float base = a.friction_mode == 1 ? pen : d0;
+            const float f = m * friction_scale(L, base * a.mu_s, base * a.mu_k);
+            Dx -= f * tx;
+            Dy -= f * ty;
+            Dz -= f * tz;
+        }
+        ++n_act;
+    }
+    if (wp > 0.0f) {
+        for (int sI = 0; sI < a.n_sdf; ++sI) {
+            const gs_sdf& b = s_sdf[sI];
+            const int ncomp = sdf_components(b.kind);
+            const float bmu_s = sqrtf(a.mu_s * b.mu_s), bmu_k = sqrtf(a.mu_k * b.mu_k);
+            for (int c = 0; c < ncomp; ++c) {
+                const SdfHit h = sdf_eval(b, c, yp.x, yp.y, yp.z);
+                if (!(h.phi < a.r)) continue;
+                const float pen = a.r - h.phi;
+                Dx += pen * h.nx;
+                Dy += pen * h.ny;
+                Dz += pen * h.nz;
+                if (!stab) {
+                    const float rx = dpx - b.vel[0] * a.dt, ry = dpy - b.vel[1] * a.dt, rz = dpz - b.vel[2] * a.dt;
+                    const float al = rx * h.nx + ry * h.ny + rz * h.nz;
+                    const float tx = rx - al * h.nx, ty = ry - al * h.ny, tz = rz - al * h.nz;
+                    const float L = sqrtf(tx * tx + ty * ty + tz * tz);
+                    const float base = a.friction_mode == 1 ? pen : d0;
+                    const float f = friction_scale(L, base * bmu_s, base * bmu_k);
+                    Dx -= f * tx;
+                    Dy -= f * ty;
+                    Dz -= f * tz;
+                }
+                ++n_act;
+            }
+        }
+    }
+    float4 nt = xtp;
+    float4 nx = xp;
+    if (n_act > 0) {
+        const float inv = 1.0f / (float)n_act;
+        const float ux = Dx * inv, uy = Dy * inv, uz = Dz * inv;
+        nt.x += ux;
+        nt.y += uy;
+        nt.z += uz;
+        if (stab) {
+            nx.x += ux;
+            nx.y += uy;
+            nx.z += uz;
+        }
+    }
+    xt_out[p] = nt;
+    if (stab) x_out[p] = nx;
+}
+
+__global__ void k_finalize(const PbdArgs a, const uint32_t* __restrict__ idx, const float4* __restrict__ s_x,
+                           const float4* __restrict__ s_xt, float4* __restrict__ pos, float4* __restrict__ vel)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.n) return;
+    const uint32_t i = idx[p];
+    const float4 x = s_x[p], xt = s_xt[p];
+    vel[i] = make_float4((xt.x - x.x) / a.dt, (xt.y - x.y) / a.dt, (xt.z - x.z) / a.dt, 0.0f);
+    pos[i] = make_float4(xt.x, xt.y, xt.z, x.w);
+}
+
+}  // namespace
+
+cudaError_t gs_launch_predict(cudaStream_t s, const PbdArgs& a, const float4* pos, const float4* vel, float4* xt,
+                              int64_t* launches)
+{
+    if (a.n <= 0) return cudaSuccess;
+    k_predict<<<gs_blocks(a.n, 256), 256, 0, s>>>(a, pos, vel, xt);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_step_gather(cudaStream_t s, int64_t n, const uint32_t* idx, const float4* xt,
+                                  const float4* pos, float4* s_xt, float4* s_x, int64_t* launches)
+{
+    if (n <= 0) return cudaSuccess;
+    k_step_gather<<<gs_blocks(n, 256), 256, 0, s>>>(n, idx, xt, pos, s_xt, s_x);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_neighbors(cudaStream_t s, const PbdArgs& a, const float4* s_xt, const uint32_t* skeys,
+                                const uint32_t* cell_start, GridDev g, uint32_t* nbr, uint32_t* cnt, int cap,
+                                int* err, int64_t* launches)
+{
+    if (a.n <= 0) return cudaSuccess;
+    k_neighbors<<<gs_blocks(a.n, 128), 128, 0, s>>>(a, s_xt, skeys, cell_start, g, nbr, cnt, cap, err);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_pass(cudaStream_t s, const PbdArgs& a, int stab, const float4* x_in, const float4* xt_in,
+                           float4* x_out, float4* xt_out, const uint32_t* nbr, const uint32_t* cnt, int cap,
+                           int64_t* launches)
+{
+    (void)cap;
+    if (a.n <= 0) return cudaSuccess;
+    k_pass<<<gs_blocks(a.n, 128), 128, 0, s>>>(a, stab, x_in, xt_in, x_out, xt_out, nbr, cnt);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_finalize(cudaStream_t s, const PbdArgs& a, const uint32_t* idx, const float4* s_x,
+                               const float4* s_xt, float4* pos, float4* vel, int64_t* launches)
+{
+    if (a.n <= 0) return cudaSuccess;
+    k_finalize<<<gs_blocks(a.n, 256), 256, 0, s>>>(a, idx, s_x, s_xt, pos, vel);
+    *launches += 1;
+    return cudaGetLastError();
+}

@@ -1,0 +1,304 @@
+// sort.cu -- uniform-grid binning by stable LSD radix sort on cell keys.
+//
+// Neighbour search (the paper uses compact hashing, Sec. 5.1) is replaced by
+// a dense grid whose cell ids follow a fixed float32 quantization contract
+// (gs.h), so that cell ids, counts and the sorted order are bit-exact
+// reproducible.  Sorting is stable by (key, index): each 8-bit pass ranks
+// equal digits in index order within a tile (warp match + per-warp counts),
+// and tiles are laid out in order by an exclusive scan over (digit, tile).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "gs_internal.cuh"
+
+namespace {
+
+constexpr int kBins = 256;
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kScanThreads = 1024;
+constexpr int kTargetBlocks = 304;   // two blocks per SM on 152 SMs
+
+int items_for(int64_t n)
+{
+    int64_t it = (n + (int64_t)kThreads * kTargetBlocks - 1) / ((int64_t)kThreads * kTargetBlocks);
+    return (int)std::min<int64_t>(std::max<int64_t>(it, 1), 16);
+}
+
+int64_t blocks_for(int64_t n, int items) { return (n + (int64_t)kThreads * items - 1) / ((int64_t)kThreads * items); }
+
+__global__ void __launch_bounds__(kThreads) k_rs_hist(const uint32_t* __restrict__ keys, int64_t n, int shift,
+                                                      int items, uint32_t* __restrict__ hist, int64_t nblocks)
+{
+    __shared__ uint32_t h[kBins];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * items * kThreads;
+    for (int r = 0; r < items; ++r) {
+        int64_t i = base + (int64_t)r * kThreads + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & (kBins - 1)], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of total words in place, one block.
+__global__ void __launch_bounds__(kScanThreads) k_rs_scan(uint32_t* __restrict__ data, int64_t total)
+{
+    __shared__ uint32_t warp_sums[kScanThreads / 32];
+    int64_t per = (total + kScanThreads - 1) / kScanThreads;
+    int64_t start = (int64_t)threadIdx.x * per;
+    int64_t end = start + per < total ? start + per : total;
+    uint32_t s = 0;
+    for (int64_t i = start; i < end; ++i) s += data[i];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = warp_sums[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_sums[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = x - s + (warp > 0 ? warp_sums[warp - 1] : 0u);
+    for (int64_t i = start; i < end; ++i) {
+        uint32_t v = data[i];
+        data[i] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_rs_scatter(const uint32_t* __restrict__ kin,
+                                                         const uint32_t* __restrict__ vin,
+                                                         uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                         int64_t n, int shift, int items,
+                                                         const uint32_t* __restrict__ offsets, int64_t nblocks)
+{
+    __shared__ uint32_t run[kBins];
+    __shared__ uint32_t wcnt[kWarps][kBins];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    run[tid] = offsets[(int64_t)tid * nblocks + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0;
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    int64_t base = (int64_t)blockIdx.x * items * kThreads;
+    for (int r = 0; r < items; ++r) {
+        int64_t i = base + (int64_t)r * kThreads + tid;
+        bool valid = i < n;
+        uint32_t key = valid ? kin[i] : 0u;
+        uint32_t val = valid ? vin[i] : 0u;
+        uint32_t d = valid ? ((key >> shift) & (kBins - 1)) : (uint32_t)kBins;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned rank = __popc(peers & lt);
+        if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = run[d] + rank;
+            for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+        uint32_t tot = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            tot += wcnt[w][tid];
+            wcnt[w][tid] = 0;
+        }
+        run[tid] += tot;
+        __syncthreads();
+    }
+}
+
+// Grid contract quantization (gs.h): float32, round-to-nearest, no FMA.
+__device__ __forceinline__ int sub_coord(float x, float o, float inv_h, int dim)
+{
+    float a = __fmul_rn(__fsub_rn(x, o), inv_h);
+    float f = floorf(__fmul_rn(a, 2.0f));
+    if (!(f >= 0.0f)) return 0;
+    if (f >= (float)(2 * dim - 1)) return 2 * dim - 1;
+    return (int)f;
+}
+
+__global__ void k_cell_keys(const float4* __restrict__ pos, int64_t n, GridDev g, int fine,
+                            uint32_t* __restrict__ keys, uint32_t* __restrict__ vals)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 p = pos[i];
+    int sx = sub_coord(p.x, g.ox, g.inv_h, g.dx);
+    int sy = sub_coord(p.y, g.oy, g.inv_h, g.dy);
+    int sz = sub_coord(p.z, g.oz, g.inv_h, g.dz);
+    uint32_t cell = ((uint32_t)(sz >> 1) * (uint32_t)g.dy + (uint32_t)(sy >> 1)) * (uint32_t)g.dx + (uint32_t)(sx >> 1);
+    keys[i] = fine ? cell * 8u + (uint32_t)((sz & 1) * 4 + (sy & 1) * 2 + (sx & 1)) : cell;
+    vals[i] = (uint32_t)i;
+}
+
+__global__ void k_cell_start(const uint32_t* __restrict__ sk, int64_t n, int64_t n_cell, uint32_t* __restrict__ start)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > n_cell) return;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)sk[mid] < c) lo = mid + 1;
+        else hi = mid;
+    }
+    start[c] = (uint32_t)lo;
+}
+
+__global__ void k_gather2(const uint32_t* __restrict__ idx, const float4* __restrict__ a, const float4* __restrict__ b,
+                          float4* __restrict__ ao, float4* __restrict__ bo, int64_t n)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    uint32_t i = idx[p];
+    ao[p] = a[i];
+    if (b) bo[p] = b[i];
+}
+
+__global__ void k_unpermute(const float4* __restrict__ pos, const float4* __restrict__ f, float4* __restrict__ out,
+                            int64_t n, int* err)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    uint32_t id = __float_as_uint(pos[p].w);
+    if ((int64_t)id >= n) {
+        atomicOr(err, GS_DEVERR_BAD_ID);
+        return;
+    }
+    out[id] = f[p];
+}
+
+__global__ void k_permute_in(const float4* __restrict__ pos, const float4* __restrict__ f, float4* __restrict__ out,
+                             int64_t n, int* err)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    uint32_t id = __float_as_uint(pos[p].w);
+    if ((int64_t)id >= n) {
+        atomicOr(err, GS_DEVERR_BAD_ID);
+        return;
+    }
+    out[p] = f[id];
+}
+
+__global__ void k_set_ids(float4* __restrict__ pos, int64_t n)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    pos[p].w = __uint_as_float((uint32_t)p);
+}
+
+__global__ void k_check_finite(const float4* __restrict__ a, int64_t n, int* flag)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    float4 v = a[p];
+    if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) atomicOr(flag, 1);
+}
+
+}  // namespace
+
+size_t gs_sort_hist_words(int64_t n)
+{
+    int items = items_for(n);
+    int64_t nb = blocks_for(n, items);
+    return (size_t)kBins * (size_t)std::max<int64_t>(nb, 1);
+}
+
+int gs_key_bits(int64_t n_keys)
+{
+    int b = 0;
+    while (b < 32 && ((int64_t)1 << b) < n_keys) ++b;
+    return b;
+}
+
+cudaError_t gs_radix_sort(cudaStream_t s, uint32_t* keys[2], uint32_t* vals[2], int* which, uint32_t* hist,
+                          int64_t n, int key_bits, int64_t* launches)
+{
+    if (n <= 0) return cudaSuccess;
+    int items = items_for(n);
+    int64_t nb = blocks_for(n, items);
+    for (int shift = 0; shift < key_bits; shift += 8) {
+        int a = *which, b = a ^ 1;
+        k_rs_hist<<<(unsigned)nb, kThreads, 0, s>>>(keys[a], n, shift, items, hist, nb);
+        k_rs_scan<<<1, kScanThreads, 0, s>>>(hist, (int64_t)kBins * nb);
+        k_rs_scatter<<<(unsigned)nb, kThreads, 0, s>>>(keys[a], vals[a], keys[b], vals[b], n, shift, items, hist, nb);
+        *launches += 3;
+        *which = b;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_cell_keys(cudaStream_t s, const float4* pos, int64_t n, GridDev g, int fine, uint32_t* keys,
+                                uint32_t* vals, int64_t* launches)
+{
+    if (n <= 0) return cudaSuccess;
+    k_cell_keys<<<gs_blocks(n, 256), 256, 0, s>>>(pos, n, g, fine, keys, vals);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_cell_start(cudaStream_t s, const uint32_t* sorted_keys, int64_t n, int64_t n_cell,
+                                 uint32_t* start, int64_t* launches)
+{
+    k_cell_start<<<gs_blocks(n_cell + 1, 256), 256, 0, s>>>(sorted_keys, n, n_cell, start);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_gather2(cudaStream_t s, const uint32_t* idx, const float4* a, const float4* b, float4* a_out,
+                              float4* b_out, int64_t n, int64_t* launches)
+{
+    if (n <= 0) return cudaSuccess;
+    k_gather2<<<gs_blocks(n, 256), 256, 0, s>>>(idx, a, b, a_out, b_out, n);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_unpermute(cudaStream_t s, const float4* pos_internal, const float4* field_internal,
+                                float4* out, int64_t n, int* err, int64_t* launches)
+{
+    if (n <= 0) return cudaSuccess;
+    k_unpermute<<<gs_blocks(n, 256), 256, 0, s>>>(pos_internal, field_internal, out, n, err);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_permute_in(cudaStream_t s, const float4* pos_internal, const float4* field_original,
+                                 float4* out, int64_t n, int* err, int64_t* launches)
+{
+    if (n <= 0) return cudaSuccess;
+    k_permute_in<<<gs_blocks(n, 256), 256, 0, s>>>(pos_internal, field_original, out, n, err);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_set_ids(cudaStream_t s, float4* pos, int64_t n, int64_t* launches)
+{
+    if (n <= 0) return cudaSuccess;
+    k_set_ids<<<gs_blocks(n, 256), 256, 0, s>>>(pos, n);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_check_finite(cudaStream_t s, const float4* a, int64_t n, int* flag, int64_t* launches)
+{
+    if (n <= 0) return cudaSuccess;
+    k_check_finite<<<gs_blocks(n, 256), 256, 0, s>>>(a, n, flag);
+    *launches += 1;
+    return cudaGetLastError();
+}

@@ -1,0 +1,111 @@
+"""Bit-exact parity of the GPU binning (LR cell sort) and HR reordering with
+the oracle's stable counting sort on the grid contract."""
+import numpy as np
+import pytest
+
+import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _ctx(sc, **kw):
+    import paper_2308_01629_gb300 as gs
+    return gs, gs.Context(sc, **kw)
+
+
+def _oracle_grid(orc, sc):
+    # the ABI receives r_low and the box as float32
+    return orc.grid(float(np.float32(sc["r_low"])), np.float32(sc["box_lo"]).astype(float),
+                    np.float32(sc["box_hi"]).astype(float))
+
+
+@pytest.mark.parametrize("make", [scenes.cube, scenes.funnel, scenes.digging])
+def test_grid_contract_matches_oracle(orc, make):
+    sc = make()
+    gs, ctx = _ctx(sc)
+    o, h, ih, dims = _oracle_grid(orc, sc)
+    g = ctx.grid
+    assert list(g.origin) == list(o) and np.float32(g.h) == np.float32(h) and np.float32(g.inv_h) == ih
+    assert list(g.dims) == list(dims) and g.n_cell == int(np.prod(dims))
+    ctx.close()
+
+
+def _check_lr_binning(orc, sc, ctx, gs):
+    ctx.bin_low()
+    idx = ctx.read(gs.GS_FIELD_LR_SORTED_INDEX)
+    start = ctx.read(gs.GS_FIELD_LR_CELL_START)
+    o, h, ih, dims = _oracle_grid(orc, sc)
+    keys = orc.cell_keys(sc["lr_pos"], o, ih, dims)
+    ref_idx, ref_start = orc.counting_sort(keys, int(np.prod(dims)))
+    np.testing.assert_array_equal(idx, ref_idx)
+    np.testing.assert_array_equal(start, ref_start)
+
+
+@pytest.mark.parametrize("make", [scenes.cube, scenes.funnel, scenes.digging])
+def test_lr_binning_bit_exact(orc, make):
+    sc = make()
+    gs, ctx = _ctx(sc)
+    _check_lr_binning(orc, sc, ctx, gs)
+    ctx.close()
+
+
+def test_lr_binning_outside_box_and_degenerate(orc):
+    rng = np.random.default_rng(21)
+    base = scenes.cube()
+    for case in ("outside", "one_point", "single", "empty"):
+        sc = dict(base)
+        if case == "outside":
+            lr = np.zeros((3001, 4), np.float32)
+            lr[:, :3] = rng.uniform(-0.2, 0.7, size=(3001, 3))
+        elif case == "one_point":
+            lr = np.zeros((5000, 4), np.float32)
+            lr[:, :3] = 0.25
+        elif case == "single":
+            lr = np.array([[0.1, 0.2, 0.3, 1.0]], np.float32)
+        else:
+            lr = np.zeros((0, 4), np.float32)
+        sc.update(lr_pos=lr, lr_vel=np.zeros_like(lr), hr_pos=np.zeros((0, 4), np.float32),
+                  hr_vel=np.zeros((0, 4), np.float32), ratio=1)
+        sc["hr_pos"] = np.repeat(lr, 1, axis=0).copy()
+        sc["hr_vel"] = np.zeros_like(sc["hr_pos"])
+        gs, ctx = _ctx(sc)
+        _check_lr_binning(orc, sc, ctx, gs)
+        ctx.close()
+
+
+@pytest.mark.parametrize("make", [scenes.cube, scenes.funnel, scenes.digging])
+def test_hr_reorder_bit_exact_and_roundtrip(orc, make):
+    sc = make()
+    if make is scenes.cube:
+        sc = scenes.stir(sc, seed=3)
+    gs, ctx = _ctx(sc)
+    ctx.resort_high()
+    keys = ctx.read(gs.GS_FIELD_HR_SORTED_KEY)
+    internal = ctx.read(gs.GS_FIELD_HR_POS_INTERNAL)
+    o, h, ih, dims = _oracle_grid(orc, sc)
+    fk = orc.cell_keys(sc["hr_pos"], o, ih, dims, fine=True)
+    ref_idx, _ = orc.counting_sort(fk, int(np.prod(dims)) * 8)
+    np.testing.assert_array_equal(internal[:, 3].view(np.uint32), ref_idx)
+    np.testing.assert_array_equal(keys, fk[ref_idx])
+    np.testing.assert_array_equal(internal[:, :3], sc["hr_pos"][ref_idx, :3])
+    # exchanged in original-id order, untouched by the reorder
+    np.testing.assert_array_equal(ctx.read(gs.GS_FIELD_HR_POS), sc["hr_pos"])
+    np.testing.assert_array_equal(ctx.read(gs.GS_FIELD_HR_VEL), sc["hr_vel"])
+    # a second reorder of the already ordered set is the identity on its order
+    ctx.resort_high()
+    np.testing.assert_array_equal(ctx.read(gs.GS_FIELD_HR_POS_INTERNAL), internal)
+    ctx.close()
+
+
+def test_hr_velocity_write_after_reorder(orc):
+    sc = scenes.stir(scenes.cube(), seed=4)
+    gs, ctx = _ctx(sc)
+    ctx.resort_high()
+    v = np.random.default_rng(5).normal(size=sc["hr_vel"].shape).astype(np.float32)
+    v[:, 3] = 0
+    ctx.write(gs.GS_FIELD_HR_VEL, v)
+    np.testing.assert_array_equal(ctx.read(gs.GS_FIELD_HR_VEL), v)
+    np.testing.assert_array_equal(ctx.read(gs.GS_FIELD_HR_POS), sc["hr_pos"])
+    ctx.write(gs.GS_FIELD_HR_POS, sc["hr_pos"])
+    np.testing.assert_array_equal(ctx.read(gs.GS_FIELD_HR_VEL), v)
+    ctx.close()

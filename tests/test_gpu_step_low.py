@@ -1,0 +1,131 @@
+"""Parity of the GPU LR step (Algorithm 1) with the FP64 oracle.
+
+Jacobi constraint averaging divides by the number of active constraints, so
+the step is discontinuous wherever a pair sits at |x_ij| = 2 r_LR -- exactly
+where the passes themselves put resolved contacts.  Single passes from a
+generic state are therefore compared particle by particle (the oracle marks
+the rare particles whose result hangs on a decision within float32 reach of
+its threshold); whole multi-pass steps are compared particle by particle on
+the particles the oracle does not mark, and by distribution statistics on
+all of them."""
+import numpy as np
+import pytest
+
+import scenes
+from gs_testutil import ATOL_L, RTOL, box_size, f32, within
+
+pytestmark = pytest.mark.gpu
+
+
+def pb_prm(sc, dt, n_stab, iters, eps_x=1e-7, eps_impact=1e-9):
+    g = sc.get("gravity", (0.0, 0.0, -9.81))
+    r = f32(sc["r_low"])
+    return dict(r=r, dt=f32(dt), gx=f32(g[0]), gy=f32(g[1]), gz=f32(g[2]), mu_s=f32(sc["mu_s"]),
+                mu_k=f32(sc["mu_k"]), n_stab=n_stab, iters=iters, mass_k=1.0, ground_z=f32(sc["box_lo"][2]),
+                rc=f32(np.float32(3.0) * np.float32(r)), friction_mode=0, eps_x=eps_x, eps_impact=eps_impact)
+
+
+def run_both(orc, sc, dt, n_stab, iters, **kw):
+    import paper_2308_01629_gb300 as gs
+    ctx = gs.Context(sc, n_stab=n_stab)
+    ctx.step_low(dt, iters)
+    x = ctx.read(gs.GS_FIELD_LR_POS)
+    v = ctx.read(gs.GS_FIELD_LR_VEL)
+    ctx.sync()
+    ctx.close()
+    rx, rv, sus, st = orc.pbd_step(sc["lr_pos"][:, :3], sc["lr_vel"][:, :3], sc["lr_pos"][:, 3],
+                                   scenes.sdf_table(sc["sdfs"]), pb_prm(sc, dt, n_stab, iters, **kw), mode=1)
+    return x, v, rx, rv, sus, st
+
+
+def elementwise(sc, dt, x, v, rx, rv, mask):
+    L = box_size(sc)
+    okx = within(x[:, :3], rx, RTOL, ATOL_L * L)
+    okv = within(v[:, :3], rv, RTOL, ATOL_L * L / dt)
+    bad = np.nonzero(mask & ~(okx & okv))[0]
+    assert len(bad) == 0, (f"{len(bad)} of {mask.sum()} LR particles outside tolerance; first {bad[0]}: "
+                           f"gpu {x[bad[0], :3]} {v[bad[0], :3]} ref {rx[bad[0]]} {rv[bad[0]]}")
+
+
+def floor_and_bucket(sc):
+    """The digging bed with the bucket pushed into the sand."""
+    sc = dict(sc)
+    sc["sdfs"] = [sc["sdfs"][0], scenes.solid_box((0.5, 0.5, 0.28), (0.125, 0.075, 0.075), vel=(0.3, 0.0, -0.2))]
+    return sc
+
+
+CASES = {
+    "cube": lambda: scenes.cube(),
+    "cube_stir": lambda: scenes.stir(scenes.cube(), seed=31, v_scale=0.3),
+    "funnel": lambda: scenes.stir(scenes.funnel(), seed=32, v_scale=0.2),
+    "digging_bucket": lambda: floor_and_bucket(scenes.stir(scenes.digging(), seed=33, v_scale=0.1)),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("passes", [(1, 0), (0, 1), (0, 0)])
+@pytest.mark.parametrize("dt", [1.0 / 60.0, 1.0 / 240.0])
+def test_single_pass(orc, case, passes, dt):
+    sc = CASES[case]()
+    x, v, rx, rv, sus, st = run_both(orc, sc, dt, *passes)
+    assert sus.mean() < 0.01, st
+    elementwise(sc, dt, x, v, rx, rv, ~sus)
+    np.testing.assert_array_equal(x[:, 3], sc["lr_pos"][:, 3])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_full_step_small(orc, seed):
+    sc = scenes.stir(scenes.cube(seed=scenes.SEED_BASE + 200 + seed), seed=seed, v_scale=0.3)
+    dt = 1.0 / 240.0
+    x, v, rx, rv, sus, st = run_both(orc, sc, dt, 2, sc["iters"])
+    assert np.all(np.isfinite(x)) and np.all(np.isfinite(v))
+    elementwise(sc, dt, x, v, rx, rv, ~sus)
+    # all particles, including those behind a near-threshold decision
+    L = box_size(sc)
+    dx = np.linalg.norm(x[:, :3] - rx, axis=1)
+    assert np.quantile(dx, 0.99) < 0.05 * sc["r_low"] and dx.max() < sc["r_low"]
+    np.testing.assert_allclose(x[:, :3].mean(0), rx.mean(0), atol=1e-4 * sc["r_low"] + ATOL_L * L)
+
+
+@pytest.mark.parametrize("case", ["funnel", "digging_bucket"])
+def test_full_step_statistics(orc, case):
+    sc = CASES[case]()
+    dt = 1.0 / 60.0
+    x, v, rx, rv, sus, st = run_both(orc, sc, dt, 2, sc["iters"])
+    assert np.all(np.isfinite(x)) and np.all(np.isfinite(v))
+    elementwise(sc, dt, x, v, rx, rv, ~sus)
+    r = sc["r_low"]
+    dx = np.linalg.norm(x[:, :3] - rx, axis=1)
+    assert np.quantile(dx, 0.99) < 0.05 * r and dx.max() < 2 * r
+    for a, b in ((x[:, :3], rx), (v[:, :3], rv)):
+        np.testing.assert_allclose(a.mean(0), b.mean(0), rtol=1e-3, atol=1e-3 * np.abs(b).mean() + 1e-9)
+        np.testing.assert_allclose(a.std(0), b.std(0), rtol=1e-2, atol=1e-9)
+
+
+def test_candidate_capacity_overflow_is_reported():
+    import paper_2308_01629_gb300 as gs
+    sc = scenes.cube()
+    sc = dict(sc)
+    lr = sc["lr_pos"].copy()
+    lr[:200, :3] = 0.25 + np.random.default_rng(1).uniform(-0.005, 0.005, size=(200, 3))  # 200 in one spot
+    sc["lr_pos"] = lr
+    ctx = gs.Context(sc, max_neighbors=32)
+    ctx.step_low(1.0 / 240.0, 2)
+    with pytest.raises(gs.GsError) as e:
+        ctx.sync()
+    assert e.value.code == gs.GS_ERR_CAPACITY
+    ctx.sync()   # reported once, the context stays usable
+    ctx.close()
+
+
+def test_non_finite_input_rejected():
+    import paper_2308_01629_gb300 as gs
+    sc = scenes.cube()
+    ctx = gs.Context(sc)
+    bad = sc["lr_pos"].copy()
+    bad[7, 1] = np.nan
+    with pytest.raises(gs.GsError) as e:
+        ctx.write(gs.GS_FIELD_LR_POS, bad)
+    assert e.value.code == gs.GS_ERR_DOMAIN
+    np.testing.assert_array_equal(ctx.read(gs.GS_FIELD_LR_POS), sc["lr_pos"])
+    ctx.close()

@@ -25,10 +25,10 @@ def up_prm(r_low=0.01, r_high=0.004, dt=1.0 / 60.0, g=(0.0, 0.0, -9.81), c1=C1, 
 
 
 def pb_prm(r=0.0625, dt=1.0 / 16.0, g=(0.0, 0.0, -8.0), mu_s=0.35, mu_k=0.30, n_stab=2, iters=4, mass_k=0.0,
-           ground_z=0.0, rc=None, friction_mode=0, eps_x=1e-12):
+           ground_z=0.0, rc=None, friction_mode=0, eps_x=1e-12, eps_impact=1e-12):
     return dict(r=r, dt=dt, gx=g[0], gy=g[1], gz=g[2], mu_s=mu_s, mu_k=mu_k, n_stab=n_stab, iters=iters,
                 mass_k=mass_k, ground_z=ground_z, rc=3.0 * r if rc is None else rc, friction_mode=friction_mode,
-                eps_x=eps_x)
+                eps_x=eps_x, eps_impact=eps_impact)
 
 
 BIG_BOX = scenes.sdf_table([scenes.box_interior((-10.0, -10.0, 0.0), (10.0, 10.0, 10.0))])

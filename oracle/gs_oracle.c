@@ -267,7 +267,10 @@ int or_sdf_eval(const double* s, const double* x, double* phi, double* n, int* t
         double dist = sqrt(dq[0] * dq[0] + dq[1] * dq[1]);
         double n2[2];
         if (dist > 0) { n2[0] = dq[0] / dist; n2[1] = dq[1] / dist; }
-        else { double le = sqrt(ee); n2[0] = -e[1] / le; n2[1] = e[0] / le; *tie = 1; }
+        else { double le = sqrt(ee); n2[0] = -e[1] / le; n2[1] = e[0] / le; }
+        /* on the mid-surface the side the particle is pushed to is not
+         * unique */
+        if (dist <= eps) *tie = 1;
         phi[0] = dist - p[6];
         n[0] = n2[0] * rx;
         n[1] = n2[0] * ry;

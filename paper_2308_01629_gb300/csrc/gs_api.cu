@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 
 #include "gs_internal.cuh"
@@ -278,7 +279,7 @@ int gs_create(const gs_scene* scene, float r_low, float r_high, int ratio, void*
     A(dalloc(&c->nbr, (size_t)N * c->nbr_cap));
     A(dalloc(&c->nbr_cnt, N));
     A(dalloc(&c->tmp4, NM));
-    c->sort_hist_cap = gs_sort_hist_words(NM);
+    c->sort_hist_cap = std::max(gs_sort_hist_words(N), gs_sort_hist_words(M));
     A(dalloc(&c->sort_hist, c->sort_hist_cap));
     A(dalloc(&c->d_err, 1));
     if (ok) ok = cudaMallocHost((void**)&c->h_err, sizeof(int)) == cudaSuccess;

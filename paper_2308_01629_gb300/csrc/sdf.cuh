@@ -49,17 +49,30 @@ __device__ __forceinline__ SdfHit sdf_eval(const gs_sdf& s, int c, float x, floa
         float qr = rho - p[3], qz = z - p[2];
         float ee = er * er + ez * ez;
         float t = (qr * er + qz * ez) / ee;
-        t = fminf(fmaxf(t, 0.0f), 1.0f);
-        float dr = qr - t * er, dz = qz - t * ez;
-        float dist = sqrtf(dr * dr + dz * dz);
-        float n2r, n2z;
-        if (dist > 0.0f) {
-            n2r = dr / dist;
-            n2z = dz / dist;
-        } else {
+        float dist, n2r, n2z;
+        if (t > 0.0f && t < 1.0f) {
+            // closest point inside the segment: the normal is the segment's
+            // fixed perpendicular (its sign picks the side), which avoids
+            // the cancellation of q - t e close to the mid-surface
             float le = sqrtf(ee);
-            n2r = -ez / le;
-            n2z = er / le;
+            float pr = -ez / le, pz = er / le;
+            float sd = qr * pr + qz * pz;
+            dist = fabsf(sd);
+            float sg = sd < 0.0f ? -1.0f : 1.0f;
+            n2r = sg * pr;
+            n2z = sg * pz;
+        } else {
+            t = fminf(fmaxf(t, 0.0f), 1.0f);
+            float dr = qr - t * er, dz = qz - t * ez;
+            dist = sqrtf(dr * dr + dz * dz);
+            if (dist > 0.0f) {
+                n2r = dr / dist;
+                n2z = dz / dist;
+            } else {
+                float le = sqrtf(ee);
+                n2r = -ez / le;
+                n2z = er / le;
+            }
         }
         h.phi = dist - p[6];
         h.nx = n2r * rx;

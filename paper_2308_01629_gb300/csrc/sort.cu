@@ -18,12 +18,13 @@ constexpr int kBins = 256;
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kScanThreads = 1024;
-constexpr int kTargetBlocks = 304;   // two blocks per SM on 152 SMs
+constexpr int kTargetBlocks = 152;   // one tile per SM; the scan grows with the tile count
+constexpr int kMaxItems = 32;
 
 int items_for(int64_t n)
 {
     int64_t it = (n + (int64_t)kThreads * kTargetBlocks - 1) / ((int64_t)kThreads * kTargetBlocks);
-    return (int)std::min<int64_t>(std::max<int64_t>(it, 1), 16);
+    return (int)std::min<int64_t>(std::max<int64_t>(it, 1), kMaxItems);
 }
 
 int64_t blocks_for(int64_t n, int items) { return (n + (int64_t)kThreads * items - 1) / ((int64_t)kThreads * items); }
@@ -43,39 +44,69 @@ __global__ void __launch_bounds__(kThreads) k_rs_hist(const uint32_t* __restrict
     hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of total words in place, one block.
+// Exclusive scan of total words in place, one block.  The data is walked in
+// coalesced tiles of kScanThreads x 8 words (two 16-byte loads per thread),
+// each tile scanned with warp shuffles and carried into the next.  total is
+// a multiple of 256 (digits x tiles), so the vector accesses stay in bounds.
 __global__ void __launch_bounds__(kScanThreads) k_rs_scan(uint32_t* __restrict__ data, int64_t total)
 {
     __shared__ uint32_t warp_sums[kScanThreads / 32];
-    int64_t per = (total + kScanThreads - 1) / kScanThreads;
-    int64_t start = (int64_t)threadIdx.x * per;
-    int64_t end = start + per < total ? start + per : total;
-    uint32_t s = 0;
-    for (int64_t i = start; i < end; ++i) s += data[i];
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = s;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sums[warp] = x;
+    __shared__ uint32_t carry_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry_s = 0;
     __syncthreads();
-    if (warp == 0) {
-        uint32_t w = warp_sums[lane];
+    constexpr int kPer = 8;
+    for (int64_t base = 0; base < total; base += (int64_t)kScanThreads * kPer) {
+        const int64_t i0 = base + (int64_t)threadIdx.x * kPer;
+        uint32_t v[kPer];
+        if (i0 + kPer <= total) {
+            uint4 a = *reinterpret_cast<const uint4*>(data + i0);
+            uint4 b = *reinterpret_cast<const uint4*>(data + i0 + 4);
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < kPer; ++k) v[k] = i0 + k < total ? data[i0 + k] : 0u;
+        }
+        uint32_t s = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) s += v[k];
+        uint32_t x = s;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        warp_sums[lane] = w;
-    }
-    __syncthreads();
-    uint32_t run = x - s + (warp > 0 ? warp_sums[warp - 1] : 0u);
-    for (int64_t i = start; i < end; ++i) {
-        uint32_t v = data[i];
-        data[i] = run;
-        run += v;
+        if (lane == 31) warp_sums[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = warp_sums[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_sums[lane] = w;
+        }
+        __syncthreads();
+        const uint32_t carry = carry_s;
+        uint32_t run = carry + x - s + (warp > 0 ? warp_sums[warp - 1] : 0u);
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            uint32_t t = v[k];
+            v[k] = run;
+            run += t;
+        }
+        if (i0 + kPer <= total) {
+            *reinterpret_cast<uint4*>(data + i0) = make_uint4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<uint4*>(data + i0 + 4) = make_uint4(v[4], v[5], v[6], v[7]);
+        } else {
+            for (int k = 0; k < kPer; ++k)
+                if (i0 + k < total) data[i0 + k] = v[k];
+        }
+        __syncthreads();
+        if (threadIdx.x == kScanThreads - 1) carry_s = run;
+        __syncthreads();
     }
 }
 

@@ -2,10 +2,12 @@
 //
 // Each warp owns 32 consecutive HR particles of the cell-ordered HR array
 // (one float4 position + one float4 velocity each, read once, written once).
-// The warp bounds its particles with an axis-aligned box, walks the rows of
-// LR grid cells that the box widened by the 3 r_LR support touches (each row
-// of cells is one contiguous run of the cell-ordered LR array), keeps the LR
-// particles within 3 r_LR of the box, and stages them in shared memory.
+// The warp splits its lanes into spatially compact groups, bounds each group
+// with an axis-aligned box, and walks the rows of LR grid cells that the box
+// widened by the 3 r_LR support touches (each row of cells is one contiguous
+// run of the cell-ordered LR array; all rows' ranges are fetched at once and
+// the concatenated range is walked 32 candidates at a time).  LR particles
+// within 3 r_LR of the box are staged in shared memory.
 // Every lane then sums the kernel weights of Sec. 4 over the staged LR set:
 //   w = max(0, 1 - |x_ij|^2 / (9 r_LR^2))^3,  S = sum w,  V = sum w v_j,
 //   wmax = max w,  vtilde = V / S (0 when S = 0),
@@ -57,6 +59,18 @@ __device__ __forceinline__ void hr_boundary(float& x, float& y, float& z, float&
     }
 }
 
+// Lanes whose sub-cells (side h/2) are within one of the group leader's are
+// gathered together; a warp that straddles a jump in the cell order (the end
+// of a row or a slab, or particles that drifted since the last reorder)
+// splits into several compact groups instead of one box across the domain.
+__device__ __forceinline__ int sub_floor(float x, float o, float inv_h)
+{
+    float a = __fmul_rn(__fsub_rn(x, o), inv_h);
+    float f = floorf(__fmul_rn(a, 2.0f));
+    f = fminf(fmaxf(f, -1.0e6f), 1.0e6f);
+    return (int)f;
+}
+
 __global__ void __launch_bounds__(kThreads) k_upsample(const UpsampleArgs a)
 {
     __shared__ float4 s_pos[kWarps][kBuf];
@@ -77,73 +91,110 @@ __global__ void __launch_bounds__(kThreads) k_upsample(const UpsampleArgs a)
         p = __ldcs(a.hr_pos + i);
         v = __ldcs(a.hr_vel + i);
     }
-
-    // bounding box of the warp's particles
-    float lx = valid ? p.x : 3.0e38f, ly = valid ? p.y : 3.0e38f, lz = valid ? p.z : 3.0e38f;
-    float hx = valid ? p.x : -3.0e38f, hy = valid ? p.y : -3.0e38f, hz = valid ? p.z : -3.0e38f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
-        ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
-        lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
-        hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
-        hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
-        hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
-    }
+    const GridDev& g = a.g;
+    const int sx = sub_floor(p.x, g.ox, g.inv_h), sy = sub_floor(p.y, g.oy, g.inv_h), sz = sub_floor(p.z, g.oz, g.inv_h);
 
     const float R = 3.0f * a.r_low * (1.0f + 1.0e-5f);    // support, padded against rounding
     const float R2 = R * R;
     const float inv9r2 = 1.0f / (9.0f * a.r_low * a.r_low);
-    const GridDev& g = a.g;
-    const int cx0 = cell_coord(lx - R, g.ox, g.inv_h, g.dx), cx1 = cell_coord(hx + R, g.ox, g.inv_h, g.dx);
-    const int cy0 = cell_coord(ly - R, g.oy, g.inv_h, g.dy), cy1 = cell_coord(hy + R, g.oy, g.inv_h, g.dy);
-    const int cz0 = cell_coord(lz - R, g.oz, g.inv_h, g.dz), cz1 = cell_coord(hz + R, g.oz, g.inv_h, g.dz);
-
-    float S = 0.f, Vx = 0.f, Vy = 0.f, Vz = 0.f, wmax = 0.f;
-    int cnt = 0;
     const unsigned lt = (1u << lane) - 1u;
     float4* bp = s_pos[warp];
     float4* bv = s_vel[warp];
 
-    auto flush = [&](int count) {
-        __syncwarp();
-        for (int k = 0; k < count; ++k) {
-            float4 q = bp[k];
-            float4 qv = bv[k];
-            float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
-            float d2 = dx * dx + dy * dy + dz * dz;
-            float t = fmaxf(1.0f - d2 * inv9r2, 0.0f);
-            float w = t * t * t;
-            S += w;
-            Vx = fmaf(w, qv.x, Vx);
-            Vy = fmaf(w, qv.y, Vy);
-            Vz = fmaf(w, qv.z, Vz);
-            wmax = fmaxf(wmax, w);
-        }
-        __syncwarp();
-    };
+    float S = 0.f, Vx = 0.f, Vy = 0.f, Vz = 0.f, wmax = 0.f;
+    unsigned pending = __ballot_sync(0xffffffffu, valid);
+    while (pending) {
+        const int leader = __ffs(pending) - 1;
+        const int gx0 = __shfl_sync(0xffffffffu, sx, leader);
+        const int gy0 = __shfl_sync(0xffffffffu, sy, leader);
+        const int gz0 = __shfl_sync(0xffffffffu, sz, leader);
+        const bool member = ((pending >> lane) & 1u) && abs(sx - gx0) <= 1 && abs(sy - gy0) <= 1 && abs(sz - gz0) <= 1;
+        pending &= ~__ballot_sync(0xffffffffu, member);
 
-    for (int cz = cz0; cz <= cz1; ++cz) {
-        for (int cy = cy0; cy <= cy1; ++cy) {
-            const int64_t row = ((int64_t)cz * g.dy + cy) * g.dx;
-            const uint32_t b = a.cell_start[row + cx0];
-            const uint32_t e = a.cell_start[row + cx1 + 1];
-            for (uint32_t base = b; base < e; base += 32) {
-                const uint32_t j = base + lane;
+        // query point: non-members look from far away and add exact zeros
+        const float qx = member ? p.x : 1.0e30f, qy = member ? p.y : 1.0e30f, qz = member ? p.z : 1.0e30f;
+        float lx = member ? p.x : 3.0e38f, ly = member ? p.y : 3.0e38f, lz = member ? p.z : 3.0e38f;
+        float hx = member ? p.x : -3.0e38f, hy = member ? p.y : -3.0e38f, hz = member ? p.z : -3.0e38f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+            ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+            lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+            hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+            hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+            hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+        }
+        const int cx0 = cell_coord(lx - R, g.ox, g.inv_h, g.dx), cx1 = cell_coord(hx + R, g.ox, g.inv_h, g.dx);
+        const int cy0 = cell_coord(ly - R, g.oy, g.inv_h, g.dy), cy1 = cell_coord(hy + R, g.oy, g.inv_h, g.dy);
+        const int cz0 = cell_coord(lz - R, g.oz, g.inv_h, g.dz), cz1 = cell_coord(hz + R, g.oz, g.inv_h, g.dz);
+        const int ny = cy1 - cy0 + 1;
+        const int nrows = ny * (cz1 - cz0 + 1);
+
+        int cnt = 0;
+        auto flush = [&](int count) {
+            __syncwarp();
+#pragma unroll 4
+            for (int k = 0; k < count; ++k) {
+                const float4 c = bp[k];
+                const float4 cv = bv[k];
+                const float dx = c.x - qx, dy = c.y - qy, dz = c.z - qz;
+                const float d2 = dx * dx + dy * dy + dz * dz;
+                const float t = fmaxf(1.0f - d2 * inv9r2, 0.0f);
+                const float w = t * t * t;
+                S += w;
+                Vx = fmaf(w, cv.x, Vx);
+                Vy = fmaf(w, cv.y, Vy);
+                Vz = fmaf(w, cv.z, Vz);
+                wmax = fmaxf(wmax, w);
+            }
+            __syncwarp();
+        };
+
+        // rows of cells (cz, cy) in chunks of 32: lane j fetches row j's range
+        for (int r0 = 0; r0 < nrows; r0 += 32) {
+            const int j = r0 + lane;
+            uint32_t rb = 0, len = 0;
+            if (j < nrows) {
+                const int cz = cz0 + j / ny, cy = cy0 + j % ny;
+                const int64_t row = ((int64_t)cz * g.dy + cy) * g.dx;
+                rb = __ldg(a.cell_start + row + cx0);
+                len = __ldg(a.cell_start + row + cx1 + 1) - rb;
+            }
+            uint32_t incl = len;   // inclusive prefix over rows
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t excl = incl - len;
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            for (uint32_t base = 0; base < total; base += 32) {
+                const uint32_t f = base + lane;
                 bool take = false;
-                float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (j < e) {
-                    q = __ldg(a.lr_spos + j);
-                    float ex = fmaxf(fmaxf(lx - q.x, q.x - hx), 0.0f);
-                    float ey = fmaxf(fmaxf(ly - q.y, q.y - hy), 0.0f);
-                    float ez = fmaxf(fmaxf(lz - q.z, q.z - hz), 0.0f);
+                float4 c = make_float4(0.f, 0.f, 0.f, 0.f), cv = c;
+                // row of flat index f: last row whose exclusive prefix is <= f
+                int lo = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const uint32_t e = __shfl_sync(0xffffffffu, excl, lo + step);
+                    if (lo + step < 32 && e <= f) lo += step;
+                }
+                const uint32_t rbase = __shfl_sync(0xffffffffu, rb, lo);
+                const uint32_t rex = __shfl_sync(0xffffffffu, excl, lo);
+                if (f < total) {
+                    const uint32_t jj = rbase + (f - rex);
+                    c = __ldg(a.lr_spos + jj);
+                    cv = __ldg(a.lr_svel + jj);
+                    const float ex = fmaxf(fmaxf(lx - c.x, c.x - hx), 0.0f);
+                    const float ey = fmaxf(fmaxf(ly - c.y, c.y - hy), 0.0f);
+                    const float ez = fmaxf(fmaxf(lz - c.z, c.z - hz), 0.0f);
                     take = ex * ex + ey * ey + ez * ez < R2;
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, take);
                 if (take) {
-                    int slot = cnt + __popc(bal & lt);
-                    bp[slot] = q;
-                    bv[slot] = __ldg(a.lr_svel + j);
+                    const int slot = cnt + __popc(bal & lt);
+                    bp[slot] = c;
+                    bv[slot] = cv;
                 }
                 cnt += __popc(bal);
                 if (cnt >= 32) {
@@ -152,8 +203,8 @@ __global__ void __launch_bounds__(kThreads) k_upsample(const UpsampleArgs a)
                 }
             }
         }
+        if (cnt > 0) flush(cnt);
     }
-    if (cnt > 0) flush(cnt);
 
     if (!valid) return;
     float vtx = 0.f, vty = 0.f, vtz = 0.f;

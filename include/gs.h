@@ -216,6 +216,37 @@ enum {
 int gs_set_timing(gs_ctx* ctx, int enable);
 int gs_timing_read(gs_ctx* ctx, int timer, double* total_ms, int64_t* launches);
 
+/* Binning without allocation.  No counterpart in the paper: this is a service
+ * for callers that cannot call cudaMalloc -- for example code that records
+ * its work into a CUDA graph under the global capture mode (where an
+ * allocation is an error), a real-time render loop that cannot afford the
+ * implicit device synchronization cudaMalloc may cause, or a host that hands
+ * out all device memory from a pool it does not let the library touch.
+ *
+ * Bins n points exactly like gs_bin_low bins the LR set: cell ids from the
+ * grid contract above, a stable sort by (cell id, index), cell starts.
+ *   pos4          device, float4[n] (x, y, z, unused), 16-byte aligned
+ *   grid          the grid contract (e.g. from gs_info); n_cell must equal
+ *                 dims[0] dims[1] dims[2]
+ *   sorted_index  device, uint32[n]: point index of each sorted slot
+ *   cell_start    device, uint32[n_cell + 1]: first sorted slot of each cell
+ *   cuda_stream   stream to enqueue on (NULL: the legacy default stream)
+ * Inputs and outputs stay owned by the caller.  The scratch the sort needs is
+ * a fixed static array of GS_STATIC_BIN_SCRATCH_BYTES in device memory that
+ * every GPU loading this library holds until the process exits; no call
+ * allocates or frees anything.  The first call on a device looks the
+ * array's device address up (with that device current); make that first
+ * call before any stream capture.  All calls on a device share the array, so
+ * calls whose work overlaps on the GPU race: order them on one stream or
+ * synchronize between them.
+ * Returns GS_ERR_CAPACITY when n > GS_STATIC_BIN_MAX_POINTS (nothing is
+ * enqueued), GS_ERR_ARG for null or misaligned pointers or an inconsistent
+ * grid, GS_ERR_CUDA when a CUDA call fails.  Asynchronous on cuda_stream. */
+#define GS_STATIC_BIN_MAX_POINTS 262144
+#define GS_STATIC_BIN_SCRATCH_BYTES 4358144
+int gs_bin_points_static(const float* pos4, int64_t n, const gs_grid_info* grid, uint32_t* sorted_index,
+                         uint32_t* cell_start, void* cuda_stream);
+
 /* Number of kernels this context has launched since creation. */
 int64_t gs_launch_count(const gs_ctx* ctx);
 

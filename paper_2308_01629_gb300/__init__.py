@@ -74,6 +74,7 @@ _SIGS = {
     "gs_timing_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_int64)]),
     "gs_launch_count": (ctypes.c_int64, [_P]),
+    "gs_bin_points_static": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(gs_grid_info), _P, _P, _P]),
 }
 
 _lib = None
@@ -184,6 +185,14 @@ def gs_timing_read(ctx, timer):
 
 def gs_launch_count(ctx):
     return lib().gs_launch_count(ctx)
+
+
+GS_STATIC_BIN_MAX_POINTS = 262144
+
+
+def gs_bin_points_static(pos4_ptr, n, grid, sorted_index_ptr, cell_start_ptr, stream=None):
+    """Binning with the library's static scratch (no allocation); device pointers."""
+    return lib().gs_bin_points_static(pos4_ptr, n, ctypes.byref(grid), sorted_index_ptr, cell_start_ptr, stream)
 
 
 # ------------------------------------------------------------ marshalling ---

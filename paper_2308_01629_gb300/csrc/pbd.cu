@@ -90,25 +90,37 @@ __device__ __forceinline__ float friction_scale(float L, float thr_s, float thr_
     return (L > 0.0f && thr_k / L < 1.0f) ? thr_k / L : 1.0f;
 }
 
-__global__ void k_pass(const PbdArgs a, int stab, const float4* __restrict__ x_in, const float4* __restrict__ xt_in,
-                       float4* __restrict__ x_out, float4* __restrict__ xt_out, const uint32_t* __restrict__ nbr,
-                       const uint32_t* __restrict__ cnt)
+// kLanes lanes share one particle: lane `sub` takes candidates sub, sub +
+// kLanes, ...; the partial sums are added with shuffles in a fixed order, and
+// lane 0 adds the SDF contacts and writes the particle.
+constexpr int kLanes = 4;
+
+__global__ void __launch_bounds__(128) k_pass(const PbdArgs a, int stab, const float4* __restrict__ x_in,
+                                              const float4* __restrict__ xt_in, float4* __restrict__ x_out,
+                                              float4* __restrict__ xt_out, const uint32_t* __restrict__ nbr,
+                                              const uint32_t* __restrict__ cnt)
 {
     __shared__ gs_sdf s_sdf[GS_MAX_SDF];
     for (int k = threadIdx.x; k < a.n_sdf; k += blockDim.x) s_sdf[k] = a.sdf[k];
     __syncthreads();
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.n) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t p = t / kLanes;
+    const int sub = (int)(t % kLanes);
+    const bool valid = p < a.n;
     const float d0 = 2.0f * a.r;
-    const float4 xtp = xt_in[p];
-    const float4 xp = x_in[p];
+    float4 xtp = make_float4(0.f, 0.f, 0.f, 0.f), xp = xtp;
+    int nc = 0;
+    if (valid) {
+        xtp = xt_in[p];
+        xp = x_in[p];
+        nc = (int)cnt[p];
+    }
     const float4 yp = stab ? xp : xtp;          // positions the constraints are evaluated on
     const float wp = xtp.w;                      // inverse height-scaled mass
     const float dpx = xtp.x - xp.x, dpy = xtp.y - xp.y, dpz = xtp.z - xp.z;
     float Dx = 0.f, Dy = 0.f, Dz = 0.f;
     int n_act = 0;
-    const int nc = (int)cnt[p];
-    for (int k = 0; k < nc; ++k) {
+    for (int k = sub; k < nc; k += kLanes) {
         const uint32_t q = nbr[(int64_t)k * a.n + p];
         const float4 xtq = xt_in[q];
         const float4 xq = x_in[q];
@@ -138,6 +150,14 @@ __global__ void k_pass(const PbdArgs a, int stab, const float4* __restrict__ x_i
         }
         ++n_act;
     }
+#pragma unroll
+    for (int o = 1; o < kLanes; o <<= 1) {
+        Dx += __shfl_xor_sync(0xffffffffu, Dx, o);
+        Dy += __shfl_xor_sync(0xffffffffu, Dy, o);
+        Dz += __shfl_xor_sync(0xffffffffu, Dz, o);
+        n_act += __shfl_xor_sync(0xffffffffu, n_act, o);
+    }
+    if (!valid || sub != 0) return;
     if (wp > 0.0f) {
         for (int sI = 0; sI < a.n_sdf; ++sI) {
             const gs_sdf& b = s_sdf[sI];
@@ -230,7 +250,7 @@ cudaError_t gs_launch_pass(cudaStream_t s, const PbdArgs& a, int stab, const flo
 {
     (void)cap;
     if (a.n <= 0) return cudaSuccess;
-    k_pass<<<gs_blocks(a.n, 128), 128, 0, s>>>(a, stab, x_in, xt_in, x_out, xt_out, nbr, cnt);
+    k_pass<<<gs_blocks(a.n * kLanes, 128), 128, 0, s>>>(a, stab, x_in, xt_in, x_out, xt_out, nbr, cnt);
     *launches += 1;
     return cudaGetLastError();
 }

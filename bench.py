@@ -55,7 +55,7 @@ TRAFFIC_CAPTURE = {"source_sha1": None, "bytes": None}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gs", "reference"], default="gs")
     ap.add_argument("--workload", choices=["digging", "funnel", "cube"], default="digging")
@@ -105,7 +105,7 @@ class Clocks:
         self.proc = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -220,6 +220,10 @@ def run_gpu(args):
         if world > 1:
             dist.barrier()
 
+    # clocks are sampled from before the warm-up to the end of the timed
+    # steps (the timed region alone can be shorter than one sample period)
+    clk = Clocks(local)
+    time.sleep(0.3)
     for _ in range(args.warmup):
         step(ctx)
     torch.cuda.synchronize(dev)
@@ -230,7 +234,6 @@ def run_gpu(args):
     for t in range(gs.GS_TIMER_COUNT):
         ctx.timing_read(t)
     launches0 = ctx.launches()
-    clk = Clocks(local)
     barrier()
     torch.cuda.synchronize(dev)
     wall0 = time.perf_counter()
@@ -242,7 +245,10 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     barrier()
     wall = time.perf_counter() - wall0
+    time.sleep(0.15)
     clocks = clk.stop()
+    if clocks:
+        clocks["window"] = "warm-up and timed steps"
     launches = ctx.launches() - launches0
     ctx.sync()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]

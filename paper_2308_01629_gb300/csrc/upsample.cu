@@ -35,25 +35,44 @@ __device__ __forceinline__ int cell_coord(float x, float o, float inv_h, int dim
     return (int)f;
 }
 
+// One wall of a box interior along axis x_k: wall at `w`, inward normal sign
+// sg (+1 for the lower wall, -1 for the upper), boundary velocity u.
+__device__ __forceinline__ void wall_project(float& x, float& v, float w, float sg, float u, float rh)
+{
+    const float phi = sg * (x - w);
+    if (phi < rh) {
+        x += sg * (rh - phi);
+        const float vn = sg * (v - u);
+        if (vn < 0.0f) v -= sg * vn;
+    }
+}
+
 __device__ __forceinline__ void hr_boundary(float& x, float& y, float& z, float& vx, float& vy, float& vz,
                                             const gs_sdf* sdf, int n_sdf, float rh)
 {
     for (int s = 0; s < n_sdf; ++s) {
         const gs_sdf& b = sdf[s];
-        int nc = sdf_components(b.kind);
-        for (int c = 0; c < nc; ++c) {
-            SdfHit h = sdf_eval(b, c, x, y, z);
-            if (h.phi < rh) {
-                float push = rh - h.phi;
-                x += push * h.nx;
-                y += push * h.ny;
-                z += push * h.nz;
-                float vn = (vx - b.vel[0]) * h.nx + (vy - b.vel[1]) * h.ny + (vz - b.vel[2]) * h.nz;
-                if (vn < 0.0f) {
-                    vx -= vn * h.nx;
-                    vy -= vn * h.ny;
-                    vz -= vn * h.nz;
-                }
+        if (b.kind == GS_SDF_BOX_INTERIOR) {
+            // the six walls in the order x-lo, x-hi, y-lo, y-hi, z-lo, z-hi
+            wall_project(x, vx, b.p[0], 1.0f, b.vel[0], rh);
+            wall_project(x, vx, b.p[3], -1.0f, b.vel[0], rh);
+            wall_project(y, vy, b.p[1], 1.0f, b.vel[1], rh);
+            wall_project(y, vy, b.p[4], -1.0f, b.vel[1], rh);
+            wall_project(z, vz, b.p[2], 1.0f, b.vel[2], rh);
+            wall_project(z, vz, b.p[5], -1.0f, b.vel[2], rh);
+            continue;
+        }
+        SdfHit h = sdf_eval(b, 0, x, y, z);
+        if (h.phi < rh) {
+            float push = rh - h.phi;
+            x += push * h.nx;
+            y += push * h.ny;
+            z += push * h.nz;
+            float vn = (vx - b.vel[0]) * h.nx + (vy - b.vel[1]) * h.ny + (vz - b.vel[2]) * h.nz;
+            if (vn < 0.0f) {
+                vx -= vn * h.nx;
+                vy -= vn * h.ny;
+                vz -= vn * h.nz;
             }
         }
     }
@@ -71,10 +90,12 @@ __device__ __forceinline__ int sub_floor(float x, float o, float inv_h)
     return (int)f;
 }
 
-__global__ void __launch_bounds__(kThreads) k_upsample(const UpsampleArgs a)
+__global__ void __launch_bounds__(kThreads, 4) k_upsample(const UpsampleArgs a)
 {
-    __shared__ float4 s_pos[kWarps][kBuf];
-    __shared__ float4 s_vel[kWarps][kBuf];
+    // staged LR candidates of a lane group, in group-local coordinates
+    // u = (x - c0) / (3 r_LR):  A = (2 u_j, -|u_j|^2),  B = (v_j, 0)
+    __shared__ float4 s_a[kWarps][kBuf];
+    __shared__ float4 s_b[kWarps][kBuf];
     __shared__ gs_sdf s_sdf[GS_MAX_SDF];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -98,8 +119,9 @@ __global__ void __launch_bounds__(kThreads) k_upsample(const UpsampleArgs a)
     const float R2 = R * R;
     const float inv9r2 = 1.0f / (9.0f * a.r_low * a.r_low);
     const unsigned lt = (1u << lane) - 1u;
-    float4* bp = s_pos[warp];
-    float4* bv = s_vel[warp];
+    float4* ba = s_a[warp];
+    float4* bb = s_b[warp];
+    const float inv3r = 1.0f / (3.0f * a.r_low);
 
     float S = 0.f, Vx = 0.f, Vy = 0.f, Vz = 0.f, wmax = 0.f;
     unsigned pending = __ballot_sync(0xffffffffu, valid);
@@ -111,8 +133,6 @@ __global__ void __launch_bounds__(kThreads) k_upsample(const UpsampleArgs a)
         const bool member = ((pending >> lane) & 1u) && abs(sx - gx0) <= 1 && abs(sy - gy0) <= 1 && abs(sz - gz0) <= 1;
         pending &= ~__ballot_sync(0xffffffffu, member);
 
-        // query point: non-members look from far away and add exact zeros
-        const float qx = member ? p.x : 1.0e30f, qy = member ? p.y : 1.0e30f, qz = member ? p.z : 1.0e30f;
         float lx = member ? p.x : 3.0e38f, ly = member ? p.y : 3.0e38f, lz = member ? p.z : 3.0e38f;
         float hx = member ? p.x : -3.0e38f, hy = member ? p.y : -3.0e38f, hz = member ? p.z : -3.0e38f;
 #pragma unroll
@@ -129,22 +149,39 @@ __global__ void __launch_bounds__(kThreads) k_upsample(const UpsampleArgs a)
         const int cz0 = cell_coord(lz - R, g.oz, g.inv_h, g.dz), cz1 = cell_coord(hz + R, g.oz, g.inv_h, g.dz);
         const int ny = cy1 - cy0 + 1;
         const int nrows = ny * (cz1 - cz0 + 1);
+        const float inv_ny = 1.0f / (float)ny;
+
+        // Sec. 4 weight in the expanded form: with u = (x - c0) / (3 r_LR),
+        //   1 - |x_i - x_j|^2 / (9 r_LR^2) = (1 - |u_i|^2) + 2 u_i . u_j - |u_j|^2.
+        // Non-members sit far away (t hugely negative, weight exactly 0).
+        const float c0x = 0.5f * (lx + hx), c0y = 0.5f * (ly + hy), c0z = 0.5f * (lz + hz);
+        float ux = 1.0e4f, uy = 1.0e4f, uz = 1.0e4f, ci = -1.0e9f;
+        if (member) {
+            ux = (p.x - c0x) * inv3r;
+            uy = (p.y - c0y) * inv3r;
+            uz = (p.z - c0z) * inv3r;
+            ci = 1.0f - (ux * ux + uy * uy + uz * uz);
+        }
 
         int cnt = 0;
+        auto stage = [&](int slot, float4 c, float4 cv) {
+            const float wx = (c.x - c0x) * inv3r, wy = (c.y - c0y) * inv3r, wz = (c.z - c0z) * inv3r;
+            ba[slot] = make_float4(2.0f * wx, 2.0f * wy, 2.0f * wz, -(wx * wx + wy * wy + wz * wz));
+            bb[slot] = make_float4(cv.x, cv.y, cv.z, 0.0f);
+        };
         auto flush = [&](int count) {
             __syncwarp();
 #pragma unroll 4
             for (int k = 0; k < count; ++k) {
-                const float4 c = bp[k];
-                const float4 cv = bv[k];
-                const float dx = c.x - qx, dy = c.y - qy, dz = c.z - qz;
-                const float d2 = dx * dx + dy * dy + dz * dz;
-                const float t = fmaxf(1.0f - d2 * inv9r2, 0.0f);
+                const float4 ra = ba[k];
+                const float4 rb = bb[k];
+                float t = fmaf(ra.x, ux, fmaf(ra.y, uy, fmaf(ra.z, uz, ra.w + ci)));
+                t = fmaxf(t, 0.0f);
                 const float w = t * t * t;
                 S += w;
-                Vx = fmaf(w, cv.x, Vx);
-                Vy = fmaf(w, cv.y, Vy);
-                Vz = fmaf(w, cv.z, Vz);
+                Vx = fmaf(w, rb.x, Vx);
+                Vy = fmaf(w, rb.y, Vy);
+                Vz = fmaf(w, rb.z, Vz);
                 wmax = fmaxf(wmax, w);
             }
             __syncwarp();
@@ -155,7 +192,8 @@ __global__ void __launch_bounds__(kThreads) k_upsample(const UpsampleArgs a)
             const int j = r0 + lane;
             uint32_t rb = 0, len = 0;
             if (j < nrows) {
-                const int cz = cz0 + j / ny, cy = cy0 + j % ny;
+                const int jz = (int)(((float)j + 0.5f) * inv_ny);   // j / ny, exact for small j
+                const int cz = cz0 + jz, cy = cy0 + (j - jz * ny);
                 const int64_t row = ((int64_t)cz * g.dy + cy) * g.dx;
                 rb = __ldg(a.cell_start + row + cx0);
                 len = __ldg(a.cell_start + row + cx1 + 1) - rb;
@@ -191,11 +229,7 @@ __global__ void __launch_bounds__(kThreads) k_upsample(const UpsampleArgs a)
                     take = ex * ex + ey * ey + ez * ez < R2;
                 }
                 const unsigned bal = __ballot_sync(0xffffffffu, take);
-                if (take) {
-                    const int slot = cnt + __popc(bal & lt);
-                    bp[slot] = c;
-                    bv[slot] = cv;
-                }
+                if (take) stage(cnt + __popc(bal & lt), c, cv);
                 cnt += __popc(bal);
                 if (cnt >= 32) {
                     flush(cnt);
@@ -209,9 +243,10 @@ __global__ void __launch_bounds__(kThreads) k_upsample(const UpsampleArgs a)
     if (!valid) return;
     float vtx = 0.f, vty = 0.f, vtz = 0.f;
     if (S > 0.0f) {
-        vtx = Vx / S;
-        vty = Vy / S;
-        vtz = Vz / S;
+        const float inv = 1.0f / S;
+        vtx = Vx * inv;
+        vty = Vy * inv;
+        vtz = Vz * inv;
     }
     const bool A = wmax <= a.c1;
     const bool B = S > 0.0f && wmax >= a.c2 * S;

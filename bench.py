@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU baseline sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-scenes", type=int, default=256)
     return ap.parse_args()
 
 
@@ -180,6 +182,61 @@ def oracle_frame_rate(sc, budget_s, sample_hr=1_000_000):
     return {"value": M / frame_s, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{reps} x ({N_SUB} FP64 LR steps of all {len(lr_x)} LR particles on 1 thread + upsampling of "
                       f"{ns} random HR particles on {cores} threads), scaled to the {M}-particle frame"}
+
+
+# ----------------------------------------------------------- batched ---
+def run_batched(args, dev, stream, gs, torch):
+    """Many independent scenes in one context (one graph-replayed frame for
+    all of them) against the same scenes in separate contexts."""
+    sl = scenes.batch(n_scenes=args.batch_scenes)
+    iters = 8
+    M = sum(len(s["hr_pos"]) for s in sl)
+    batch = gs.Context(sl, stream=stream.cuda_stream)
+    for _ in range(2):
+        batch.frame(DT, N_SUB, iters)
+    tw, tb, tus = batch.autotune(DT, reps=3)
+    batch.set_graphs(True)
+    for _ in range(3):
+        batch.frame(DT, N_SUB, iters)
+    torch.cuda.synchronize(dev)
+    k = max(5, args.steps // 5)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    l0 = batch.launches()
+    for i in range(k):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        batch.frame(DT, N_SUB, iters)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    batch.sync()
+    nl = (batch.launches() - l0) / k
+    ms = sum(a.elapsed_time(b2) for a, b2 in ev) / k
+    batch.close()
+    # the same scenes, one context each, launched one after the other
+    ctxs = [gs.Context(s, stream=stream.cuda_stream) for s in sl]
+    for c in ctxs:
+        c.frame(DT, N_SUB, iters)
+    torch.cuda.synchronize(dev)
+    k2 = 3
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k2)]
+    for i in range(k2):
+        flush.fill_(float(i))
+        ev2[i][0].record(stream)
+        for c in ctxs:
+            c.frame(DT, N_SUB, iters)
+        ev2[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    ms2 = sum(a.elapsed_time(b2) for a, b2 in ev2) / k2
+    for c in ctxs:
+        c.sync()
+        c.close()
+    return {"scenes": len(sl), "n_low": int(sum(len(s["lr_pos"]) for s in sl)), "n_high": int(M),
+            "frame": f"{N_SUB} LR steps of {DT / N_SUB:.5f} s ({iters} solver passes) + 1 upsampling frame",
+            "batched_ms_per_frame": ms, "batched_hr_per_s": M / (ms / 1e3), "batched_kernels_per_frame": nl,
+            "separate_ms_per_frame": ms2, "separate_hr_per_s": M / (ms2 / 1e3),
+            "speedup_vs_separate": ms2 / ms, "upsample_tuning": {"warps_per_block": tw, "blocks_per_sm": tb,
+                                                                   "upsample_us": tus}}
 
 
 # ------------------------------------------------------------- GPU arm ---
@@ -304,6 +361,7 @@ def run_gpu(args):
                "d2h_bytes_per_step": int(2 * M * 16), "ms_per_step": 1e3 * te / ne}
 
     ctx.close()
+    batched = None if args.no_batched else run_batched(args, dev, stream, gs, torch)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -336,6 +394,7 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
         "e2e": e2e,
+        "batched": batched,
     }
     if not args.no_cpu:
         line["cpu_baseline"] = oracle_frame_rate(sc, args.cpu_seconds)

@@ -95,18 +95,24 @@ typedef struct {
     gs_params params;
 } gs_scene;
 
-/* Readable / writable state.  HR fields are always exchanged in original-id
- * order (index = id), whatever the internal cell order. */
+/* Readable / writable state.  LR and HR fields hold all scenes of the
+ * context back to back (scene order, see gs_scene_info).  HR fields are always
+ * exchanged in original-id order (index = id), whatever the internal cell
+ * order.  Internally every scene's HR particles occupy a range of slots that
+ * starts on a multiple of 32, followed by up to 31 padding slots (w = all
+ * ones); the *_INTERNAL fields and GS_FIELD_HR_SORTED_KEY expose those slots.
+ * Grid cells of scene s are numbered from its cell offset, and every scene
+ * owns one extra padding cell after its real cells. */
 enum {
     GS_FIELD_LR_POS = 0,         /* float4[n_low], read / write */
     GS_FIELD_LR_VEL = 1,         /* float4[n_low], read / write */
     GS_FIELD_HR_POS = 2,         /* float4[n_high], read / write (w is set to the id on write) */
     GS_FIELD_HR_VEL = 3,         /* float4[n_high], read / write */
-    GS_FIELD_HR_POS_INTERNAL = 4,/* float4[n_high], read: internal (cell) order */
-    GS_FIELD_HR_VEL_INTERNAL = 5,/* float4[n_high], read: internal (cell) order */
-    GS_FIELD_LR_CELL_START = 6,  /* uint32[n_cell + 1], read: first sorted slot of each cell */
+    GS_FIELD_HR_POS_INTERNAL = 4,/* float4[HR slots], read: internal (cell) order, see gs_scene_info */
+    GS_FIELD_HR_VEL_INTERNAL = 5,/* float4[HR slots], read: internal (cell) order */
+    GS_FIELD_LR_CELL_START = 6,  /* uint32[total cells + 1], read: first sorted slot of each cell */
     GS_FIELD_LR_SORTED_INDEX = 7,/* uint32[n_low], read: particle index of each sorted slot */
-    GS_FIELD_HR_SORTED_KEY = 8   /* uint32[n_high], read: fine cell key of each internal slot
+    GS_FIELD_HR_SORTED_KEY = 8   /* uint32[HR slots], read: fine cell key of each internal slot
                                     after the latest reorder */
 };
 
@@ -126,6 +132,16 @@ typedef struct {
     int64_t n_cell;
 } gs_grid_info;
 
+/* Layout of one scene inside a context. */
+typedef struct {
+    int64_t lr_offset, n_low;         /* LR particles [lr_offset, lr_offset + n_low) of the LR fields */
+    int64_t hr_offset, n_high;        /* HR particles (original ids) of the HR fields */
+    int64_t hr_slot_offset, hr_slot_end; /* internal HR slots of the scene, padding included */
+    int64_t cell_offset;              /* first global cell id of the scene */
+    gs_grid_info grid;                /* the scene's grid contract */
+    float r_low, r_high;
+} gs_scene_layout;
+
 /* Fill p with the paper's default parameters (see gs_params). */
 void gs_default_params(gs_params* p);
 
@@ -137,6 +153,20 @@ void gs_default_params(gs_params* p);
  * NULL for a stream owned by the context.  The particle state starts at zero
  * and is loaded with gs_write.  Errors: GS_ERR_ARG, GS_ERR_OOM, GS_ERR_CUDA. */
 int gs_create(const gs_scene* scene, float r_low, float r_high, int ratio, void* cuda_stream, gs_ctx** out);
+
+/* Create one context for n_scenes independent scenes (the batched pattern
+ * of serving many small simulations at once; not in the paper).  scenes,
+ * r_low, ratio: arrays of n_scenes entries with the meaning of gs_create's
+ * arguments; r_high may be NULL (defaults).  All scenes step together: the
+ * kernels of a frame cover every scene, the upsampling runs as one launch
+ * over all scenes' warp items, and gs_frame can replay a whole frame as one
+ * CUDA graph.  n_stab, resort_every and max_neighbors must agree across
+ * scenes.  Errors as gs_create. */
+int gs_batch_create(int n_scenes, const gs_scene* scenes, const float* r_low, const float* r_high, const int* ratio,
+                    void* cuda_stream, gs_ctx** out);
+
+/* Layout of scene number `scene` of the context. */
+int gs_scene_info(const gs_ctx* ctx, int scene, gs_scene_layout* out);
 
 /* Release every buffer of the context (waits for its stream). */
 void gs_destroy(gs_ctx* ctx);
@@ -198,6 +228,27 @@ int gs_step_low(gs_ctx* ctx, float dt, int iters);
  * the normal velocity into the boundary (relative to the boundary velocity)
  * is removed.  dt > 0. */
 int gs_upsample(gs_ctx* ctx, float dt);
+
+/* One whole frame: n_sub LR steps of dt / n_sub (Algorithm 1) followed by
+ * one HR frame of dt (gs_upsample), for every scene of the context.  With
+ * graphs enabled (gs_set_graphs) the first frame of each configuration is
+ * captured into a CUDA graph and later frames replay it (kernel timing with
+ * gs_set_timing switches the replay off).  Asynchronous. */
+int gs_frame(gs_ctx* ctx, float dt, int n_sub, int iters);
+
+/* Enable (1) or disable (0) CUDA-graph replay of gs_frame. */
+int gs_set_graphs(gs_ctx* ctx, int enable);
+
+/* Launch shape of the upsampling kernel: warps per block (4, 8 or 16) and
+ * blocks per SM of a persistent grid that pulls 32-particle work items from
+ * an atomic counter (0: one warp per item, no persistent loop). */
+int gs_set_tuning(gs_ctx* ctx, int warps_per_block, int blocks_per_sm);
+
+/* Time the upsampling kernel on the current state (written out of place,
+ * the state is not changed) for a fixed list of launch shapes, reps
+ * launches each, and keep the fastest.  Returns the shape and its time per
+ * launch in microseconds.  Blocks. */
+int gs_autotune(gs_ctx* ctx, float dt, int reps, int* warps_per_block, int* blocks_per_sm, float* best_us);
 
 /* Block until the context's stream is idle and report device-side errors. */
 int gs_sync(gs_ctx* ctx);

@@ -53,6 +53,13 @@ class gs_grid_info(ctypes.Structure):
                 ("dims", ctypes.c_int32 * 3), ("n_cell", ctypes.c_int64)]
 
 
+class gs_scene_layout(ctypes.Structure):
+    _fields_ = [("lr_offset", ctypes.c_int64), ("n_low", ctypes.c_int64), ("hr_offset", ctypes.c_int64),
+                ("n_high", ctypes.c_int64), ("hr_slot_offset", ctypes.c_int64), ("hr_slot_end", ctypes.c_int64),
+                ("cell_offset", ctypes.c_int64), ("grid", gs_grid_info), ("r_low", ctypes.c_float),
+                ("r_high", ctypes.c_float)]
+
+
 _P = ctypes.c_void_p
 _SIGS = {
     "gs_default_params": (None, [ctypes.POINTER(gs_params)]),
@@ -75,6 +82,15 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_int64)]),
     "gs_launch_count": (ctypes.c_int64, [_P]),
     "gs_bin_points_static": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(gs_grid_info), _P, _P, _P]),
+    "gs_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(gs_scene), ctypes.POINTER(ctypes.c_float),
+                                       ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int), _P,
+                                       ctypes.POINTER(_P)]),
+    "gs_scene_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(gs_scene_layout)]),
+    "gs_frame": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_int, ctypes.c_int]),
+    "gs_set_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gs_set_tuning": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    "gs_autotune": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
 }
 
 _lib = None
@@ -121,8 +137,48 @@ def gs_create(scene, r_low, r_high, ratio, stream=None):
     return ctx
 
 
+def gs_batch_create(scenes, r_low, r_high, ratio, stream=None):
+    n = len(scenes)
+    arr = (gs_scene * n)(*scenes)
+    rl = (ctypes.c_float * n)(*[float(a) for a in r_low])
+    rh = (ctypes.c_float * n)(*[float(a) for a in r_high])
+    ra = (ctypes.c_int * n)(*[int(a) for a in ratio])
+    ctx = _P()
+    rc = lib().gs_batch_create(n, arr, rl, rh, ra, stream, ctypes.byref(ctx))
+    if rc != GS_OK:
+        raise GsError(rc, "gs_batch_create failed")
+    return ctx
+
+
 def gs_destroy(ctx):
     lib().gs_destroy(ctx)
+
+
+def gs_scene_info(ctx, scene):
+    out = gs_scene_layout()
+    rc = lib().gs_scene_info(ctx, int(scene), ctypes.byref(out))
+    if rc != GS_OK:
+        raise GsError(rc, "gs_scene_info failed")
+    return out
+
+
+def gs_frame(ctx, dt, n_sub, iters):
+    return lib().gs_frame(ctx, dt, n_sub, iters)
+
+
+def gs_set_graphs(ctx, enable):
+    return lib().gs_set_graphs(ctx, int(enable))
+
+
+def gs_set_tuning(ctx, warps_per_block, blocks_per_sm):
+    return lib().gs_set_tuning(ctx, int(warps_per_block), int(blocks_per_sm))
+
+
+def gs_autotune(ctx, dt, reps=5):
+    w, b, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _check(ctx, lib().gs_autotune(ctx, dt, int(reps), ctypes.byref(w), ctypes.byref(b), ctypes.byref(us)),
+           "gs_autotune")
+    return w.value, b.value, us.value
 
 
 def gs_last_error(ctx):
@@ -250,17 +306,31 @@ def _ptr_of(a):
 
 
 class Context:
-    """Owner of one gs_ctx built from a ``scenes`` dictionary."""
+    """Owner of one gs_ctx built from a ``scenes`` dictionary, or from a list
+    of them (one batched context; arrays are concatenated in scene order)."""
 
     def __init__(self, sc, stream=None, load_state=True, **overrides):
-        self.scene = make_scene(sc, **overrides)
-        self.ctx = gs_create(self.scene, float(sc["r_low"]), float(sc["r_high"]), int(sc["ratio"]), stream)
+        batch = isinstance(sc, (list, tuple))
+        self.scene_list = list(sc) if batch else [sc]
+        self._c_scenes = [make_scene(s, **overrides) for s in self.scene_list]
+        if batch:
+            self.ctx = gs_batch_create(self._c_scenes, [s["r_low"] for s in self.scene_list],
+                                       [s["r_high"] for s in self.scene_list], [s["ratio"] for s in self.scene_list],
+                                       stream)
+        else:
+            s0 = self.scene_list[0]
+            self.ctx = gs_create(self._c_scenes[0], float(s0["r_low"]), float(s0["r_high"]), int(s0["ratio"]),
+                                 stream)
         self.n_low, self.n_high, self.grid = gs_info(self.ctx)
+        self.layouts = [gs_scene_info(self.ctx, k) for k in range(len(self.scene_list))]
+        last = self.layouts[-1]
+        self.hr_slots = int(last.hr_slot_end)
+        self.n_cell_total = int(last.cell_offset + last.grid.n_cell + 1)
+        self.sdf_offsets = np.cumsum([0] + [len(s["sdfs"]) for s in self.scene_list])
         if load_state:
-            self.write(GS_FIELD_LR_POS, sc["lr_pos"])
-            self.write(GS_FIELD_LR_VEL, sc["lr_vel"])
-            self.write(GS_FIELD_HR_POS, sc["hr_pos"])
-            self.write(GS_FIELD_HR_VEL, sc["hr_vel"])
+            for f, k in ((GS_FIELD_LR_POS, "lr_pos"), (GS_FIELD_LR_VEL, "lr_vel"), (GS_FIELD_HR_POS, "hr_pos"),
+                         (GS_FIELD_HR_VEL, "hr_vel")):
+                self.write(f, np.ascontiguousarray(np.concatenate([s[k] for s in self.scene_list])))
 
     def close(self):
         if self.ctx:
@@ -281,17 +351,25 @@ class Context:
         if out is None:
             counts = {GS_FIELD_LR_POS: (self.n_low, 4), GS_FIELD_LR_VEL: (self.n_low, 4),
                       GS_FIELD_HR_POS: (self.n_high, 4), GS_FIELD_HR_VEL: (self.n_high, 4),
-                      GS_FIELD_HR_POS_INTERNAL: (self.n_high, 4), GS_FIELD_HR_VEL_INTERNAL: (self.n_high, 4),
-                      GS_FIELD_LR_CELL_START: (int(self.grid.n_cell) + 1,),
-                      GS_FIELD_LR_SORTED_INDEX: (self.n_low,), GS_FIELD_HR_SORTED_KEY: (self.n_high,)}
+                      GS_FIELD_HR_POS_INTERNAL: (self.hr_slots, 4), GS_FIELD_HR_VEL_INTERNAL: (self.hr_slots, 4),
+                      GS_FIELD_LR_CELL_START: (self.n_cell_total + 1,),
+                      GS_FIELD_LR_SORTED_INDEX: (self.n_low,), GS_FIELD_HR_SORTED_KEY: (self.hr_slots,)}
             shape = counts[field]
             out = np.zeros(shape, np.float32 if len(shape) == 2 else np.uint32)
         p, n, dev = _ptr_of(out)
         _check(self.ctx, gs_read(self.ctx, field, p, n, dev), "gs_read")
         return out
 
-    def set_sdf(self, index, rec):
-        return _check(self.ctx, gs_set_sdf(self.ctx, index, make_sdf(rec)), "gs_set_sdf")
+    def scene_slice(self, scene, field):
+        """Index range of one scene inside a concatenated LR or HR field."""
+        L = self.layouts[scene]
+        if field in (GS_FIELD_LR_POS, GS_FIELD_LR_VEL):
+            return slice(L.lr_offset, L.lr_offset + L.n_low)
+        return slice(L.hr_offset, L.hr_offset + L.n_high)
+
+    def set_sdf(self, index, rec, scene=0):
+        k = int(self.sdf_offsets[scene]) + int(index)
+        return _check(self.ctx, gs_set_sdf(self.ctx, k, make_sdf(rec)), "gs_set_sdf")
 
     def bin_low(self):
         return _check(self.ctx, gs_bin_low(self.ctx), "gs_bin_low")
@@ -304,6 +382,18 @@ class Context:
 
     def upsample(self, dt):
         return _check(self.ctx, gs_upsample(self.ctx, float(dt)), "gs_upsample")
+
+    def frame(self, dt, n_sub, iters):
+        return _check(self.ctx, gs_frame(self.ctx, float(dt), int(n_sub), int(iters)), "gs_frame")
+
+    def set_graphs(self, on=True):
+        return _check(self.ctx, gs_set_graphs(self.ctx, on), "gs_set_graphs")
+
+    def set_tuning(self, warps_per_block, blocks_per_sm):
+        return _check(self.ctx, gs_set_tuning(self.ctx, warps_per_block, blocks_per_sm), "gs_set_tuning")
+
+    def autotune(self, dt, reps=5):
+        return gs_autotune(self.ctx, float(dt), reps)
 
     def sync(self):
         return _check(self.ctx, gs_sync(self.ctx), "gs_sync")

@@ -1,13 +1,14 @@
 // gs_api.cu -- host side of the C ABI declared in gs.h: argument checks,
-// buffer ownership, and the order in which the kernels of one LR step and
-// one HR frame are enqueued on the context's stream.
+// buffer ownership, the order in which the kernels of one LR step and one HR
+// frame are enqueued on the context's stream, CUDA graphs of whole frames,
+// and the launch-shape autotuner of the upsampling kernel.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <algorithm>
 #include <new>
 
 #include "gs_internal.cuh"
@@ -33,9 +34,9 @@ int cuda_fail(gs_ctx* c, cudaError_t e, const char* what)
     return fail(c, GS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define CK(call, what)                                  \
-    do {                                                \
-        cudaError_t e_ = (call);                        \
+#define CK(call, what)                                        \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
         if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
     } while (0)
 
@@ -98,12 +99,12 @@ size_t field_bytes(const gs_ctx* c, int field)
     case GS_FIELD_LR_POS:
     case GS_FIELD_LR_VEL: return (size_t)c->n_low * sizeof(float4);
     case GS_FIELD_HR_POS:
-    case GS_FIELD_HR_VEL:
+    case GS_FIELD_HR_VEL: return (size_t)c->n_high * sizeof(float4);
     case GS_FIELD_HR_POS_INTERNAL:
-    case GS_FIELD_HR_VEL_INTERNAL: return (size_t)c->n_high * sizeof(float4);
-    case GS_FIELD_LR_CELL_START: return (size_t)(c->n_cell + 1) * sizeof(uint32_t);
+    case GS_FIELD_HR_VEL_INTERNAL: return (size_t)c->hr_slots * sizeof(float4);
+    case GS_FIELD_LR_CELL_START: return (size_t)(c->n_cell_total + 1) * sizeof(uint32_t);
     case GS_FIELD_LR_SORTED_INDEX: return (size_t)c->n_low * sizeof(uint32_t);
-    case GS_FIELD_HR_SORTED_KEY: return (size_t)c->n_high * sizeof(uint32_t);
+    case GS_FIELD_HR_SORTED_KEY: return (size_t)c->hr_slots * sizeof(uint32_t);
     default: return (size_t)-1;
     }
 }
@@ -115,17 +116,47 @@ bool finite3_host(const float4* a, int64_t n)
     return true;
 }
 
+// ---- HR slots <-> original order (kernels local to this file) ---------------
+// Slot p of scene s that is not padding holds the particle with original id
+// hr_real_begin + (p - hr_begin) in the identity order.
+__global__ void k_hr_load(const float4* __restrict__ src, float4* __restrict__ dst, const uint32_t* __restrict__ tag,
+                          const SceneDev* __restrict__ scenes, int64_t n_slots, int set_ids)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_slots) return;
+    const uint32_t t = tag[p];
+    if (t & kPadBit) {
+        dst[p] = make_float4(0.f, 0.f, 0.f, set_ids ? __uint_as_float(0xffffffffu) : 0.f);
+        return;
+    }
+    const SceneDev& sc = scenes[t];
+    const int64_t id = sc.hr_real_begin + (p - sc.hr_begin);
+    float4 v = src[id];
+    if (set_ids) v.w = __uint_as_float((uint32_t)id);
+    dst[p] = v;
+}
+
+cudaError_t launch_hr_load(gs_ctx* c, const float4* src, float4* dst, int set_ids)
+{
+    if (c->hr_slots <= 0) return cudaSuccess;
+    k_hr_load<<<gs_blocks(c->hr_slots, 256), 256, 0, c->stream>>>(src, dst, c->hr_scene, c->d_scenes, c->hr_slots,
+                                                                   set_ids);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
 int bin_low_at(gs_ctx* c, const float4* positions)
 {
     const int64_t n = c->n_low;
-    CK(gs_launch_cell_keys(c->stream, positions, n, c->grid, 0, c->lr_keys[0], c->lr_vals[0], &c->launches),
+    CK(gs_launch_scene_keys(c->stream, positions, n, c->d_scenes, c->lr_scene, 0, c->lr_keys[0], c->lr_vals[0],
+                            &c->launches),
        "cell keys");
     int which = 0;
     CK(gs_radix_sort(c->stream, c->lr_keys, c->lr_vals, &which, c->sort_hist, n, c->lr_key_bits, &c->launches),
        "radix sort");
     c->lr_sorted_keys = c->lr_keys[which];
     c->lr_sorted_idx = c->lr_vals[which];
-    CK(gs_launch_cell_start(c->stream, c->lr_sorted_keys, n, c->n_cell, c->lr_cell_start, &c->launches),
+    CK(gs_launch_cell_start(c->stream, c->lr_sorted_keys, n, c->n_cell_total, c->lr_cell_start, &c->launches),
        "cell start");
     return GS_OK;
 }
@@ -134,20 +165,324 @@ PbdArgs pbd_args(const gs_ctx* c, float dt)
 {
     PbdArgs a;
     a.n = c->n_low;
-    a.r = c->r_low;
     a.dt = dt;
-    a.gx = c->prm.gravity[0];
-    a.gy = c->prm.gravity[1];
-    a.gz = c->prm.gravity[2];
-    a.mu_s = c->prm.mu_s;
-    a.mu_k = c->prm.mu_k;
-    a.mass_k = c->prm.mass_scale_k;
-    a.ground_z = c->prm.ground_z;
-    a.rc = c->prm.neighbor_radius;
-    a.friction_mode = c->prm.friction_mode;
+    a.scenes = c->d_scenes;
+    a.lr_scene = c->lr_scene;
     a.sdf = c->d_sdf;
-    a.n_sdf = c->n_sdf;
     return a;
+}
+
+int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* r_high, const int* ratio,
+                void* cuda_stream, gs_ctx** out)
+{
+    if (!out) return GS_ERR_ARG;
+    *out = nullptr;
+    if (S < 1 || S > 65536 || !scenes || !r_low || !ratio) return GS_ERR_ARG;
+    gs_ctx* c = new (std::nothrow) gs_ctx();
+    if (!c) return GS_ERR_OOM;
+    c->n_scenes = S;
+    c->scenes.resize(S);
+    c->prm.resize(S);
+    int64_t lr = 0, hr_real = 0, hr_slot = 0, cells = 0;
+    for (int s = 0; s < S; ++s) {
+        const gs_scene& in = scenes[s];
+        const float rl = r_low[s];
+        const float rh_in = r_high ? r_high[s] : 0.0f;
+        const int ra = ratio[s];
+        bool bad = !(rl > 0.0f) || !std::isfinite(rl) || ra < 1 || in.n_low < 0 || in.n_sdf < 0 ||
+                   in.n_sdf > GS_MAX_SDF || (in.n_sdf > 0 && !in.sdf);
+        for (int k = 0; k < 3 && !bad; ++k)
+            bad = !(in.box_hi[k] > in.box_lo[k]) || !std::isfinite(in.box_lo[k]) || !std::isfinite(in.box_hi[k]);
+        gs_params p = in.params;
+        if (std::isnan(p.ground_z)) p.ground_z = in.box_lo[2];
+        if (p.neighbor_radius <= 0.0f) p.neighbor_radius = 3.0f * rl;
+        if (p.max_neighbors <= 0) p.max_neighbors = 64;
+        bad = bad || !(p.neighbor_radius > 2.0f * rl) || p.neighbor_radius > 3.0f * rl || p.n_stab < 0 ||
+              p.n_stab > 100 || p.resort_every < 0 || p.max_neighbors > 4096 ||
+              (p.friction_mode != 0 && p.friction_mode != 1);
+        if (s > 0)   // one solver configuration per context
+            bad = bad || p.n_stab != c->prm[0].n_stab || p.resort_every != c->prm[0].resort_every ||
+                  p.max_neighbors != c->prm[0].max_neighbors;
+        if (bad) {
+            delete c;
+            return GS_ERR_ARG;
+        }
+        c->prm[s] = p;
+        SceneDev& d = c->scenes[s];
+        std::memset(&d, 0, sizeof d);
+        // grid contract
+        const double hd = 3.0 * (double)rl * (1.0 + 1.0 / 1024.0);
+        const float hf = (float)hd;
+        d.g.h = hf;
+        d.g.inv_h = (float)(1.0 / (double)hf);
+        d.g.ox = in.box_lo[0];
+        d.g.oy = in.box_lo[1];
+        d.g.oz = in.box_lo[2];
+        int dims[3];
+        for (int k = 0; k < 3; ++k) {
+            double n = std::ceil(((double)in.box_hi[k] - (double)in.box_lo[k]) / (double)hf);
+            if (n > (double)(1 << 20)) {
+                delete c;
+                return GS_ERR_ARG;
+            }
+            dims[k] = n < 1 ? 1 : (int)n;
+        }
+        d.g.dx = dims[0];
+        d.g.dy = dims[1];
+        d.g.dz = dims[2];
+        const int64_t ncell = (int64_t)dims[0] * dims[1] * dims[2];
+        d.cell_off = (uint32_t)cells;
+        d.n_cell = (uint32_t)ncell;
+        cells += ncell + 1;
+        if (cells * 8 > 0xffffffffLL) {
+            delete c;
+            return GS_ERR_ARG;
+        }
+        const int64_t m = (int64_t)in.n_low * ra;
+        d.lr_begin = lr;
+        d.lr_end = lr + in.n_low;
+        d.hr_begin = hr_slot;
+        d.hr_end = hr_slot + m;
+        d.hr_real_begin = hr_real;
+        d.warp_begin = hr_slot / 32;
+        lr += in.n_low;
+        hr_real += m;
+        hr_slot += (m + 31) / 32 * 32;
+        d.r_low = rl;
+        d.r_high = rh_in > 0.0f ? rh_in : (float)((double)rl * std::pow((double)ra, -1.0 / 3.0));
+        d.gx = p.gravity[0];
+        d.gy = p.gravity[1];
+        d.gz = p.gravity[2];
+        d.mu_s = p.mu_s;
+        d.mu_k = p.mu_k;
+        d.c1 = p.c1;
+        d.c2 = p.c2;
+        d.mass_k = p.mass_scale_k;
+        d.ground_z = p.ground_z;
+        d.rc = p.neighbor_radius;
+        d.friction_mode = p.friction_mode;
+        d.sdf_begin = (int)c->sdf_host.size();
+        d.n_sdf = in.n_sdf;
+        for (int k = 0; k < in.n_sdf; ++k) c->sdf_host.push_back(in.sdf[k]);
+    }
+    if (hr_real > 0x7fffffffLL || hr_slot > 0x7fffffffLL || lr > 0x7fffffffLL) {
+        delete c;
+        return GS_ERR_ARG;   // ids and slots are stored as uint32
+    }
+    c->n_low = lr;
+    c->n_high = hr_real;
+    c->hr_slots = hr_slot;
+    c->n_warps = hr_slot / 32;
+    c->n_cell_total = cells;
+    c->lr_key_bits = gs_key_bits(cells);
+    c->hr_key_bits = gs_key_bits(cells * 8);
+    c->resort_every = c->prm[0].resort_every;
+    c->nbr_cap = c->prm[0].max_neighbors;
+    c->n_stab = c->prm[0].n_stab;
+
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return GS_ERR_CUDA;
+    }
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return GS_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    const int64_t N = c->n_low, MS = c->hr_slots, MR = c->n_high;
+    const int64_t NM = std::max(N, MS);
+    bool ok = true;
+    auto A = [&](cudaError_t r) { ok = ok && r == cudaSuccess; };
+    A(dalloc(&c->d_scenes, (size_t)S));
+    A(dalloc(&c->d_sdf, std::max<size_t>(c->sdf_host.size(), 1)));
+    A(dalloc(&c->lr_scene, N));
+    A(dalloc(&c->hr_scene, MS));
+    A(dalloc(&c->lr_pos, N));
+    A(dalloc(&c->lr_vel, N));
+    A(dalloc(&c->lr_keys[0], N));
+    A(dalloc(&c->lr_keys[1], N));
+    A(dalloc(&c->lr_vals[0], N));
+    A(dalloc(&c->lr_vals[1], N));
+    A(dalloc(&c->lr_cell_start, cells + 1));
+    A(dalloc(&c->lr_spos, N));
+    A(dalloc(&c->lr_svel, N));
+    A(dalloc(&c->lr_xt, N));
+    for (int k = 0; k < 2; ++k) {
+        A(dalloc(&c->s_xt[k], N));
+        A(dalloc(&c->s_x[k], N));
+        A(dalloc(&c->hr_pos[k], MS));
+        A(dalloc(&c->hr_vel[k], MS));
+        A(dalloc(&c->hr_keys[k], MS));
+        A(dalloc(&c->hr_vals[k], MS));
+    }
+    A(dalloc(&c->nbr, (size_t)N * c->nbr_cap));
+    A(dalloc(&c->nbr_cnt, N));
+    A(dalloc(&c->tmp4, std::max(NM, MR)));
+    c->sort_hist_cap = std::max(gs_sort_hist_words(N), gs_sort_hist_words(MS));
+    A(dalloc(&c->sort_hist, c->sort_hist_cap));
+    A(dalloc(&c->d_work, 1));
+    A(dalloc(&c->d_err, 1));
+    if (ok) ok = cudaMallocHost((void**)&c->h_err, sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        gs_destroy(c);
+        return GS_ERR_OOM;
+    }
+    *c->h_err = 0;
+    // scene tags of every LR and HR slot
+    std::vector<uint32_t> lt((size_t)N), ht((size_t)MS);
+    for (int s = 0; s < S; ++s) {
+        const SceneDev& d = c->scenes[s];
+        for (int64_t i = d.lr_begin; i < d.lr_end; ++i) lt[(size_t)i] = (uint32_t)s;
+        const int64_t slot_end = (s + 1 < S) ? c->scenes[s + 1].hr_begin : MS;
+        for (int64_t i = d.hr_begin; i < slot_end; ++i) ht[(size_t)i] = (uint32_t)s | (i >= d.hr_end ? kPadBit : 0u);
+    }
+    bool z = true;
+    auto Z = [&](cudaError_t r) { z = z && r == cudaSuccess; };
+    Z(cudaMemcpy(c->d_scenes, c->scenes.data(), S * sizeof(SceneDev), cudaMemcpyHostToDevice));
+    if (!c->sdf_host.empty())
+        Z(cudaMemcpy(c->d_sdf, c->sdf_host.data(), c->sdf_host.size() * sizeof(gs_sdf), cudaMemcpyHostToDevice));
+    if (N) Z(cudaMemcpy(c->lr_scene, lt.data(), N * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    if (MS) Z(cudaMemcpy(c->hr_scene, ht.data(), MS * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    Z(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    Z(cudaMemsetAsync(c->lr_pos, 0, std::max<int64_t>(N, 1) * sizeof(float4), c->stream));
+    Z(cudaMemsetAsync(c->lr_vel, 0, std::max<int64_t>(N, 1) * sizeof(float4), c->stream));
+    Z(cudaMemsetAsync(c->tmp4, 0, std::max<int64_t>(std::max(NM, MR), 1) * sizeof(float4), c->stream));
+    Z(cudaMemsetAsync(c->lr_cell_start, 0, (cells + 1) * sizeof(uint32_t), c->stream));
+    if (z) Z(launch_hr_load(c, c->tmp4, c->hr_pos[0], 1));
+    if (z) Z(launch_hr_load(c, c->tmp4, c->hr_vel[0], 0));
+    if (z) Z(cudaStreamSynchronize(c->stream));
+    if (!z) {
+        gs_destroy(c);
+        return GS_ERR_CUDA;
+    }
+    *out = c;
+    return GS_OK;
+}
+
+int resort_high_impl(gs_ctx* c)
+{
+    const int64_t MS = c->hr_slots;
+    if (MS == 0) return GS_OK;
+    Timed t(c, GS_TIMER_RESORT);
+    const int cur = c->hr_cur;
+    CK(gs_launch_scene_keys(c->stream, c->hr_pos[cur], MS, c->d_scenes, c->hr_scene, 1, c->hr_keys[0],
+                            c->hr_vals[0], &c->launches),
+       "keys");
+    int which = 0;
+    CK(gs_radix_sort(c->stream, c->hr_keys, c->hr_vals, &which, c->sort_hist, MS, c->hr_key_bits, &c->launches),
+       "radix sort");
+    CK(gs_launch_gather2(c->stream, c->hr_vals[which], c->hr_pos[cur], c->hr_vel[cur], c->hr_pos[cur ^ 1],
+                         c->hr_vel[cur ^ 1], MS, &c->launches),
+       "permute");
+    c->hr_sorted_keys = c->hr_keys[which];
+    c->hr_keys_valid = true;
+    c->hr_cur = cur ^ 1;
+    c->hr_identity = false;
+    return GS_OK;
+}
+
+int bin_low_impl(gs_ctx* c)
+{
+    Timed t(c, GS_TIMER_BIN_LOW);
+    int st = bin_low_at(c, c->lr_pos);
+    if (st) return st;
+    CK(gs_launch_gather2(c->stream, c->lr_sorted_idx, c->lr_pos, c->lr_vel, c->lr_spos, c->lr_svel, c->n_low,
+                         &c->launches),
+       "gather");
+    c->lr_binned = true;
+    return GS_OK;
+}
+
+UpsampleArgs upsample_args(const gs_ctx* c, float dt, const float4* in_pos, const float4* in_vel, float4* out_pos,
+                           float4* out_vel)
+{
+    UpsampleArgs u;
+    u.hr_pos = in_pos;
+    u.hr_vel = in_vel;
+    u.out_pos = out_pos;
+    u.out_vel = out_vel;
+    u.lr_spos = c->lr_spos;
+    u.lr_svel = c->lr_svel;
+    u.cell_start = c->lr_cell_start;
+    u.scenes = c->d_scenes;
+    u.hr_tag = c->hr_scene;
+    u.sdf = c->d_sdf;
+    u.n_scenes = c->n_scenes;
+    u.n_warps = c->n_warps;
+    u.work = c->d_work;
+    u.dt = dt;
+    return u;
+}
+
+// The HR frame: reorder when due, bin LR, gather in place.
+int upsample_impl(gs_ctx* c, float dt)
+{
+    int st;
+    if (c->n_high == 0) {
+        c->frame++;
+        return GS_OK;
+    }
+    if (c->resort_every > 0 && c->frame % c->resort_every == 0) {
+        st = resort_high_impl(c);
+        if (st) return st;
+    }
+    st = bin_low_impl(c);
+    if (st) return st;
+    const int cur = c->hr_cur;
+    UpsampleArgs u = upsample_args(c, dt, c->hr_pos[cur], c->hr_vel[cur], c->hr_pos[cur], c->hr_vel[cur]);
+    {
+        Timed t(c, GS_TIMER_GATHER);
+        CK(gs_launch_upsample(c->stream, u, c->tune_warps, c->tune_blocks_per_sm, c->sm_count, &c->launches),
+           "upsample");
+    }
+    c->frame++;
+    return GS_OK;
+}
+
+int step_low_impl(gs_ctx* c, float dt, int iters)
+{
+    const int64_t N = c->n_low;
+    if (N == 0) return GS_OK;
+    Timed t(c, GS_TIMER_STEP_LOW);
+    PbdArgs a = pbd_args(c, dt);
+    CK(gs_launch_predict(c->stream, a, c->lr_pos, c->lr_vel, c->lr_xt, &c->launches), "predict");
+    int st = bin_low_at(c, c->lr_xt);
+    if (st) return st;
+    CK(gs_launch_step_gather(c->stream, N, c->lr_sorted_idx, c->lr_xt, c->lr_pos, c->s_xt[0], c->s_x[0],
+                             &c->launches),
+       "gather");
+    CK(gs_launch_neighbors(c->stream, a, c->s_xt[0], c->lr_sorted_keys, c->lr_cell_start, c->nbr, c->nbr_cnt,
+                           c->nbr_cap, c->d_err, &c->launches),
+       "neighbours");
+    int bx = 0, bt = 0;   // buffers holding the current x and xt
+    for (int it = 0; it < c->n_stab + iters; ++it) {
+        const int stab = it < c->n_stab;
+        CK(gs_launch_pass(c->stream, a, stab, c->s_x[bx], c->s_xt[bt], c->s_x[bx ^ 1], c->s_xt[bt ^ 1], c->nbr,
+                          c->nbr_cnt, &c->launches),
+           "pass");
+        bt ^= 1;
+        if (stab) bx ^= 1;
+    }
+    CK(gs_launch_finalize(c->stream, a, c->lr_sorted_idx, c->s_x[bx], c->s_xt[bt], c->lr_pos, c->lr_vel,
+                          &c->launches),
+       "finalize");
+    c->lr_binned = false;   // the binning above is of the predicted positions
+    return GS_OK;
+}
+
+void drop_graphs(gs_ctx* c)
+{
+    for (auto& g : c->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
 }
 
 }  // namespace
@@ -176,154 +511,35 @@ void gs_default_params(gs_params* p)
 
 int gs_create(const gs_scene* scene, float r_low, float r_high, int ratio, void* cuda_stream, gs_ctx** out)
 {
-    if (!out) return GS_ERR_ARG;
-    *out = nullptr;
-    if (!scene || !(r_low > 0.0f) || !std::isfinite(r_low) || ratio < 1 || scene->n_low < 0) return GS_ERR_ARG;
-    if (scene->n_sdf < 0 || scene->n_sdf > GS_MAX_SDF || (scene->n_sdf > 0 && !scene->sdf)) return GS_ERR_ARG;
-    for (int k = 0; k < 3; ++k)
-        if (!(scene->box_hi[k] > scene->box_lo[k]) || !std::isfinite(scene->box_lo[k]) ||
-            !std::isfinite(scene->box_hi[k]))
-            return GS_ERR_ARG;
-    const int64_t n_high = (int64_t)scene->n_low * ratio;
-    if (n_high > 0x7fffffffLL) return GS_ERR_ARG;   // ids are stored as uint32, indices as int32 slots
-
-    gs_ctx* c = new (std::nothrow) gs_ctx();
-    if (!c) return GS_ERR_OOM;
-    c->n_low = scene->n_low;
-    c->n_high = n_high;
-    c->ratio = ratio;
-    c->r_low = r_low;
-    c->r_high = r_high > 0.0f ? r_high : (float)((double)r_low * std::pow((double)ratio, -1.0 / 3.0));
-    c->prm = scene->params;
-    if (std::isnan(c->prm.ground_z)) c->prm.ground_z = scene->box_lo[2];
-    if (c->prm.neighbor_radius <= 0.0f) c->prm.neighbor_radius = 3.0f * r_low;
-    if (c->prm.max_neighbors <= 0) c->prm.max_neighbors = 64;
-    c->nbr_cap = c->prm.max_neighbors;
-    if (!(c->prm.neighbor_radius > 2.0f * r_low) || c->prm.neighbor_radius > 3.0f * r_low || c->prm.n_stab < 0 ||
-        c->prm.n_stab > 100 || c->prm.resort_every < 0 || c->nbr_cap > 4096 ||
-        (c->prm.friction_mode != 0 && c->prm.friction_mode != 1)) {
-        delete c;
+    if (!scene) {
+        if (out) *out = nullptr;
         return GS_ERR_ARG;
     }
-    c->n_sdf = scene->n_sdf;
-    for (int k = 0; k < c->n_sdf; ++k) c->sdf_host[k] = scene->sdf[k];
+    return create_impl(1, scene, &r_low, &r_high, &ratio, cuda_stream, out);
+}
 
-    // grid contract
-    {
-        double hd = 3.0 * (double)r_low * (1.0 + 1.0 / 1024.0);
-        float hf = (float)hd;
-        c->grid.h = hf;
-        c->grid.inv_h = (float)(1.0 / (double)hf);
-        c->grid.ox = scene->box_lo[0];
-        c->grid.oy = scene->box_lo[1];
-        c->grid.oz = scene->box_lo[2];
-        int dims[3];
-        for (int k = 0; k < 3; ++k) {
-            double n = std::ceil(((double)scene->box_hi[k] - (double)scene->box_lo[k]) / (double)hf);
-            if (n > (double)(1 << 20)) {
-                delete c;
-                return GS_ERR_ARG;
-            }
-            dims[k] = n < 1 ? 1 : (int)n;
-        }
-        c->grid.dx = dims[0];
-        c->grid.dy = dims[1];
-        c->grid.dz = dims[2];
-        c->n_cell = (int64_t)dims[0] * dims[1] * dims[2];
-        if (c->n_cell * 8 > 0xffffffffLL) {
-            delete c;
-            return GS_ERR_ARG;
-        }
-        c->lr_key_bits = gs_key_bits(c->n_cell);
-        c->hr_key_bits = gs_key_bits(c->n_cell * 8);
-    }
-
-    cudaError_t e = cudaGetDevice(&c->device);
-    if (e != cudaSuccess) {
-        delete c;
-        return GS_ERR_CUDA;
-    }
-    if (cuda_stream) {
-        c->stream = (cudaStream_t)cuda_stream;
-    } else {
-        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
-        if (e != cudaSuccess) {
-            delete c;
-            return GS_ERR_CUDA;
-        }
-        c->own_stream = true;
-    }
-    const int64_t N = c->n_low, M = c->n_high;
-    const int64_t NM = N > M ? N : M;
-    bool ok = true;
-    auto A = [&](cudaError_t r) { ok = ok && r == cudaSuccess; };
-    A(dalloc(&c->d_sdf, GS_MAX_SDF));
-    A(dalloc(&c->lr_pos, N));
-    A(dalloc(&c->lr_vel, N));
-    A(dalloc(&c->lr_keys[0], N));
-    A(dalloc(&c->lr_keys[1], N));
-    A(dalloc(&c->lr_vals[0], N));
-    A(dalloc(&c->lr_vals[1], N));
-    A(dalloc(&c->lr_cell_start, c->n_cell + 1));
-    A(dalloc(&c->lr_spos, N));
-    A(dalloc(&c->lr_svel, N));
-    A(dalloc(&c->lr_xt, N));
-    for (int k = 0; k < 2; ++k) {
-        A(dalloc(&c->s_xt[k], N));
-        A(dalloc(&c->s_x[k], N));
-        A(dalloc(&c->hr_pos[k], M));
-        A(dalloc(&c->hr_vel[k], M));
-        A(dalloc(&c->hr_keys[k], M));
-        A(dalloc(&c->hr_vals[k], M));
-    }
-    A(dalloc(&c->nbr, (size_t)N * c->nbr_cap));
-    A(dalloc(&c->nbr_cnt, N));
-    A(dalloc(&c->tmp4, NM));
-    c->sort_hist_cap = std::max(gs_sort_hist_words(N), gs_sort_hist_words(M));
-    A(dalloc(&c->sort_hist, c->sort_hist_cap));
-    A(dalloc(&c->d_err, 1));
-    if (ok) ok = cudaMallocHost((void**)&c->h_err, sizeof(int)) == cudaSuccess;
-    if (!ok) {
-        cudaGetLastError();
-        gs_destroy(c);
-        return GS_ERR_OOM;
-    }
-    *c->h_err = 0;
-    bool z = true;
-    auto Z = [&](void* p, size_t b) { z = z && cudaMemsetAsync(p, 0, b, c->stream) == cudaSuccess; };
-    Z(c->d_err, sizeof(int));
-    Z(c->lr_pos, N * sizeof(float4));
-    Z(c->lr_vel, N * sizeof(float4));
-    Z(c->hr_pos[0], M * sizeof(float4));
-    Z(c->hr_vel[0], M * sizeof(float4));
-    Z(c->lr_cell_start, (c->n_cell + 1) * sizeof(uint32_t));
-    if (c->n_sdf > 0)
-        z = z && cudaMemcpyAsync(c->d_sdf, c->sdf_host, c->n_sdf * sizeof(gs_sdf), cudaMemcpyHostToDevice,
-                                 c->stream) == cudaSuccess;
-    if (z) z = gs_launch_set_ids(c->stream, c->hr_pos[0], M, &c->launches) == cudaSuccess;
-    if (z) z = cudaStreamSynchronize(c->stream) == cudaSuccess;
-    if (!z) {
-        gs_destroy(c);
-        return GS_ERR_CUDA;
-    }
-    *out = c;
-    return GS_OK;
+int gs_batch_create(int n_scenes, const gs_scene* scenes, const float* r_low, const float* r_high, const int* ratio,
+                    void* cuda_stream, gs_ctx** out)
+{
+    return create_impl(n_scenes, scenes, r_low, r_high, ratio, cuda_stream, out);
 }
 
 void gs_destroy(gs_ctx* c)
 {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
     for (int t = 0; t < GS_TIMER_COUNT; ++t)
         for (auto& pr : c->ev[t]) {
             cudaEventDestroy(pr.first);
             cudaEventDestroy(pr.second);
         }
-    void* bufs[] = {c->d_sdf,      c->lr_pos,    c->lr_vel,     c->lr_keys[0], c->lr_keys[1], c->lr_vals[0],
-                    c->lr_vals[1], c->lr_cell_start, c->lr_spos, c->lr_svel,   c->lr_xt,      c->s_xt[0],
-                    c->s_xt[1],    c->s_x[0],    c->s_x[1],     c->hr_pos[0],  c->hr_pos[1],  c->hr_vel[0],
-                    c->hr_vel[1],  c->hr_keys[0], c->hr_keys[1], c->hr_vals[0], c->hr_vals[1], c->nbr,
-                    c->nbr_cnt,    c->tmp4,      c->sort_hist,  c->d_err};
+    void* bufs[] = {c->d_scenes,   c->d_sdf,      c->lr_scene,   c->hr_scene,   c->lr_pos,    c->lr_vel,
+                    c->lr_keys[0], c->lr_keys[1], c->lr_vals[0], c->lr_vals[1], c->lr_cell_start, c->lr_spos,
+                    c->lr_svel,    c->lr_xt,      c->s_xt[0],    c->s_xt[1],    c->s_x[0],    c->s_x[1],
+                    c->hr_pos[0],  c->hr_pos[1],  c->hr_vel[0],  c->hr_vel[1],  c->hr_keys[0], c->hr_keys[1],
+                    c->hr_vals[0], c->hr_vals[1], c->nbr,        c->nbr_cnt,    c->tmp4,      c->sort_hist,
+                    c->d_work,     c->d_err};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->h_err) cudaFreeHost(c->h_err);
@@ -339,16 +555,42 @@ int gs_info(const gs_ctx* c, int64_t* n_low, int64_t* n_high, gs_grid_info* grid
     if (n_low) *n_low = c->n_low;
     if (n_high) *n_high = c->n_high;
     if (grid) {
-        grid->origin[0] = c->grid.ox;
-        grid->origin[1] = c->grid.oy;
-        grid->origin[2] = c->grid.oz;
-        grid->h = c->grid.h;
-        grid->inv_h = c->grid.inv_h;
-        grid->dims[0] = c->grid.dx;
-        grid->dims[1] = c->grid.dy;
-        grid->dims[2] = c->grid.dz;
-        grid->n_cell = c->n_cell;
+        const SceneDev& d = c->scenes[0];
+        grid->origin[0] = d.g.ox;
+        grid->origin[1] = d.g.oy;
+        grid->origin[2] = d.g.oz;
+        grid->h = d.g.h;
+        grid->inv_h = d.g.inv_h;
+        grid->dims[0] = d.g.dx;
+        grid->dims[1] = d.g.dy;
+        grid->dims[2] = d.g.dz;
+        grid->n_cell = (int64_t)d.n_cell;
     }
+    return GS_OK;
+}
+
+int gs_scene_info(const gs_ctx* c, int scene, gs_scene_layout* out)
+{
+    if (!c || !out || scene < 0 || scene >= c->n_scenes) return GS_ERR_ARG;
+    const SceneDev& d = c->scenes[scene];
+    out->lr_offset = d.lr_begin;
+    out->n_low = d.lr_end - d.lr_begin;
+    out->hr_offset = d.hr_real_begin;
+    out->n_high = d.hr_end - d.hr_begin;
+    out->hr_slot_offset = d.hr_begin;
+    out->hr_slot_end = (scene + 1 < c->n_scenes) ? c->scenes[scene + 1].hr_begin : c->hr_slots;
+    out->cell_offset = d.cell_off;
+    out->grid.origin[0] = d.g.ox;
+    out->grid.origin[1] = d.g.oy;
+    out->grid.origin[2] = d.g.oz;
+    out->grid.h = d.g.h;
+    out->grid.inv_h = d.g.inv_h;
+    out->grid.dims[0] = d.g.dx;
+    out->grid.dims[1] = d.g.dy;
+    out->grid.dims[2] = d.g.dz;
+    out->grid.n_cell = (int64_t)d.n_cell;
+    out->r_low = d.r_low;
+    out->r_high = d.r_high;
     return GS_OK;
 }
 
@@ -376,40 +618,35 @@ int gs_write(gs_ctx* c, int field, const void* src, size_t bytes, int src_is_dev
             return fail(c, GS_ERR_DOMAIN, "non-finite value in field %d", field);
         }
     }
+    const int cur = c->hr_cur;
     switch (field) {
     case GS_FIELD_LR_POS:
         CK(cudaMemcpyAsync(c->lr_pos, src, bytes, kind, c->stream), "copy");
         c->lr_binned = false;
         break;
     case GS_FIELD_LR_VEL: CK(cudaMemcpyAsync(c->lr_vel, src, bytes, kind, c->stream), "copy"); break;
-    case GS_FIELD_HR_POS: {
-        const int cur = c->hr_cur;
+    case GS_FIELD_HR_POS:
         if (!c->hr_identity) {
-            // bring the velocities back to original-id order first
-            CK(gs_launch_unpermute(c->stream, c->hr_pos[cur], c->hr_vel[cur], c->hr_vel[cur ^ 1], c->n_high,
-                                   c->d_err, &c->launches),
+            // bring the velocities back to the identity slot order first
+            CK(gs_launch_unpermute(c->stream, c->hr_pos[cur], c->hr_vel[cur], c->hr_scene, c->tmp4, c->hr_slots,
+                                   c->n_high, c->d_err, &c->launches),
                "unpermute");
-            CK(cudaMemcpyAsync(c->hr_vel[cur], c->hr_vel[cur ^ 1], bytes, cudaMemcpyDeviceToDevice, c->stream),
-               "copy");
+            CK(launch_hr_load(c, c->tmp4, c->hr_vel[cur], 0), "load");
         }
-        CK(cudaMemcpyAsync(c->hr_pos[cur], src, bytes, kind, c->stream), "copy");
-        CK(gs_launch_set_ids(c->stream, c->hr_pos[cur], c->n_high, &c->launches), "ids");
+        CK(cudaMemcpyAsync(c->tmp4, src, bytes, kind, c->stream), "copy");
+        CK(launch_hr_load(c, c->tmp4, c->hr_pos[cur], 1), "load");
         c->hr_identity = true;
         c->hr_keys_valid = false;
         break;
-    }
-    case GS_FIELD_HR_VEL: {
-        const int cur = c->hr_cur;
-        if (c->hr_identity) {
-            CK(cudaMemcpyAsync(c->hr_vel[cur], src, bytes, kind, c->stream), "copy");
-        } else {
-            CK(cudaMemcpyAsync(c->tmp4, src, bytes, kind, c->stream), "copy");
-            CK(gs_launch_permute_in(c->stream, c->hr_pos[cur], c->tmp4, c->hr_vel[cur], c->n_high, c->d_err,
-                                    &c->launches),
+    case GS_FIELD_HR_VEL:
+        CK(cudaMemcpyAsync(c->tmp4, src, bytes, kind, c->stream), "copy");
+        if (c->hr_identity)
+            CK(launch_hr_load(c, c->tmp4, c->hr_vel[cur], 0), "load");
+        else
+            CK(gs_launch_permute_in(c->stream, c->hr_pos[cur], c->tmp4, c->hr_scene, c->hr_vel[cur], c->hr_slots,
+                                    c->n_high, c->d_err, &c->launches),
                "permute");
-        }
         break;
-    }
     }
     if (!src_is_device) CK(cudaStreamSynchronize(c->stream), "synchronize");
     return GS_OK;
@@ -446,15 +683,12 @@ int gs_read(gs_ctx* c, int field, void* dst, size_t bytes, int dst_is_device)
     case GS_FIELD_HR_POS:
     case GS_FIELD_HR_VEL: {
         const float4* f = field == GS_FIELD_HR_POS ? c->hr_pos[cur] : c->hr_vel[cur];
-        if (c->hr_identity) {
-            srcp = f;
-        } else {
-            float4* target = dst_is_device ? (float4*)dst : c->tmp4;
-            CK(gs_launch_unpermute(c->stream, c->hr_pos[cur], f, target, c->n_high, c->d_err, &c->launches),
-               "unpermute");
-            if (dst_is_device) return GS_OK;
-            srcp = c->tmp4;
-        }
+        float4* target = dst_is_device ? (float4*)dst : c->tmp4;
+        CK(gs_launch_unpermute(c->stream, c->hr_pos[cur], f, c->hr_scene, target, c->hr_slots, c->n_high, c->d_err,
+                               &c->launches),
+           "unpermute");
+        if (dst_is_device) return GS_OK;
+        srcp = c->tmp4;
         break;
     }
     }
@@ -467,7 +701,7 @@ int gs_set_sdf(gs_ctx* c, int index, const gs_sdf* sdf)
 {
     int st = check_state(c);
     if (st) return st;
-    if (!sdf || index < 0 || index >= c->n_sdf) return fail(c, GS_ERR_ARG, "bad SDF index %d", index);
+    if (!sdf || index < 0 || index >= (int)c->sdf_host.size()) return fail(c, GS_ERR_ARG, "bad SDF index %d", index);
     c->sdf_host[index] = *sdf;
     CK(cudaMemcpyAsync(c->d_sdf + index, &c->sdf_host[index], sizeof(gs_sdf), cudaMemcpyHostToDevice, c->stream),
        "copy SDF");
@@ -478,37 +712,14 @@ int gs_bin_low(gs_ctx* c)
 {
     int st = check_state(c);
     if (st) return st;
-    Timed t(c, GS_TIMER_BIN_LOW);
-    st = bin_low_at(c, c->lr_pos);
-    if (st) return st;
-    CK(gs_launch_gather2(c->stream, c->lr_sorted_idx, c->lr_pos, c->lr_vel, c->lr_spos, c->lr_svel, c->n_low,
-                         &c->launches),
-       "gather");
-    c->lr_binned = true;
-    return GS_OK;
+    return bin_low_impl(c);
 }
 
 int gs_resort_high(gs_ctx* c)
 {
     int st = check_state(c);
     if (st) return st;
-    const int64_t M = c->n_high;
-    if (M == 0) return GS_OK;
-    Timed t(c, GS_TIMER_RESORT);
-    const int cur = c->hr_cur;
-    CK(gs_launch_cell_keys(c->stream, c->hr_pos[cur], M, c->grid, 1, c->hr_keys[0], c->hr_vals[0], &c->launches),
-       "keys");
-    int which = 0;
-    CK(gs_radix_sort(c->stream, c->hr_keys, c->hr_vals, &which, c->sort_hist, M, c->hr_key_bits, &c->launches),
-       "radix sort");
-    CK(gs_launch_gather2(c->stream, c->hr_vals[which], c->hr_pos[cur], c->hr_vel[cur], c->hr_pos[cur ^ 1],
-                         c->hr_vel[cur ^ 1], M, &c->launches),
-       "permute");
-    c->hr_sorted_keys = c->hr_keys[which];
-    c->hr_keys_valid = true;
-    c->hr_cur = cur ^ 1;
-    c->hr_identity = false;
-    return GS_OK;
+    return resort_high_impl(c);
 }
 
 int gs_step_low(gs_ctx* c, float dt, int iters)
@@ -517,33 +728,7 @@ int gs_step_low(gs_ctx* c, float dt, int iters)
     if (st) return st;
     if (!(dt > 0.0f) || !std::isfinite(dt) || iters < 0 || iters > 1000)
         return fail(c, GS_ERR_ARG, "invalid dt %g or iters %d", (double)dt, iters);
-    const int64_t N = c->n_low;
-    if (N == 0) return GS_OK;
-    Timed t(c, GS_TIMER_STEP_LOW);
-    PbdArgs a = pbd_args(c, dt);
-    CK(gs_launch_predict(c->stream, a, c->lr_pos, c->lr_vel, c->lr_xt, &c->launches), "predict");
-    st = bin_low_at(c, c->lr_xt);
-    if (st) return st;
-    CK(gs_launch_step_gather(c->stream, N, c->lr_sorted_idx, c->lr_xt, c->lr_pos, c->s_xt[0], c->s_x[0],
-                             &c->launches),
-       "gather");
-    CK(gs_launch_neighbors(c->stream, a, c->s_xt[0], c->lr_sorted_keys, c->lr_cell_start, c->grid, c->nbr, c->nbr_cnt,
-                           c->nbr_cap, c->d_err, &c->launches),
-       "neighbours");
-    int bx = 0, bt = 0;   // buffers holding the current x and xt
-    for (int it = 0; it < c->prm.n_stab + iters; ++it) {
-        const int stab = it < c->prm.n_stab;
-        CK(gs_launch_pass(c->stream, a, stab, c->s_x[bx], c->s_xt[bt], c->s_x[bx ^ 1], c->s_xt[bt ^ 1], c->nbr,
-                          c->nbr_cnt, c->nbr_cap, &c->launches),
-           "pass");
-        bt ^= 1;
-        if (stab) bx ^= 1;
-    }
-    CK(gs_launch_finalize(c->stream, a, c->lr_sorted_idx, c->s_x[bx], c->s_xt[bt], c->lr_pos, c->lr_vel,
-                          &c->launches),
-       "finalize");
-    c->lr_binned = false;   // the binning above is of the predicted positions
-    return GS_OK;
+    return step_low_impl(c, dt, iters);
 }
 
 int gs_upsample(gs_ctx* c, float dt)
@@ -551,43 +736,138 @@ int gs_upsample(gs_ctx* c, float dt)
     int st = check_state(c);
     if (st) return st;
     if (!(dt > 0.0f) || !std::isfinite(dt)) return fail(c, GS_ERR_ARG, "invalid dt %g", (double)dt);
-    if (c->n_high == 0) {
-        c->frame++;
-        return GS_OK;
-    }
-    if (c->prm.resort_every > 0 && c->frame % c->prm.resort_every == 0) {
-        st = gs_resort_high(c);
-        if (st) return st;
-    }
-    st = gs_bin_low(c);
+    return upsample_impl(c, dt);
+}
+
+int gs_frame(gs_ctx* c, float dt, int n_sub, int iters)
+{
+    int st = check_state(c);
     if (st) return st;
-    UpsampleArgs u;
-    const int cur = c->hr_cur;
-    u.hr_pos = c->hr_pos[cur];
-    u.hr_vel = c->hr_vel[cur];
-    u.out_pos = c->hr_pos[cur ^ 1];
-    u.out_vel = c->hr_vel[cur ^ 1];
-    u.m = c->n_high;
-    u.lr_spos = c->lr_spos;
-    u.lr_svel = c->lr_svel;
-    u.cell_start = c->lr_cell_start;
-    u.g = c->grid;
-    u.r_low = c->r_low;
-    u.r_high = c->r_high;
-    u.dt = dt;
-    u.gx = c->prm.gravity[0];
-    u.gy = c->prm.gravity[1];
-    u.gz = c->prm.gravity[2];
-    u.c1 = c->prm.c1;
-    u.c2 = c->prm.c2;
-    u.sdf = c->d_sdf;
-    u.n_sdf = c->n_sdf;
-    {
-        Timed t(c, GS_TIMER_GATHER);
-        CK(gs_launch_upsample(c->stream, u, &c->launches), "upsample");
+    if (!(dt > 0.0f) || !std::isfinite(dt) || n_sub < 0 || n_sub > 1000 || iters < 0 || iters > 1000)
+        return fail(c, GS_ERR_ARG, "invalid frame arguments");
+    const float dts = n_sub > 0 ? dt / (float)n_sub : dt;
+    const bool resort = c->n_high > 0 && c->resort_every > 0 && c->frame % c->resort_every == 0;
+    if (!c->use_graphs || c->timing) {
+        for (int k = 0; k < n_sub; ++k) {
+            st = step_low_impl(c, dts, iters);
+            if (st) return st;
+        }
+        return upsample_impl(c, dt);
     }
-    c->hr_cur = cur ^ 1;
-    c->frame++;
+    // one graph per (time step, substeps, iterations, reorder, buffer parity)
+    uint32_t dbits;
+    std::memcpy(&dbits, &dt, 4);
+    const uint64_t key = ((uint64_t)dbits << 32) ^ ((uint64_t)(n_sub & 0x3ff) << 20) ^ ((uint64_t)(iters & 0x3ff) << 8) ^
+                         ((uint64_t)resort << 1) ^ (uint64_t)c->hr_cur ^ ((uint64_t)c->tune_warps << 2) ^
+                         ((uint64_t)c->tune_blocks_per_sm << 5);
+    GraphEntry* ge = nullptr;
+    for (auto& g : c->graphs)
+        if (g.key == key) ge = &g;
+    const int64_t frame0 = c->frame;
+    const int cur0 = c->hr_cur;
+    if (!ge) {
+        cudaGraph_t graph = nullptr;
+        const int64_t launches0 = c->launches;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        int st2 = GS_OK;
+        for (int k = 0; k < n_sub && st2 == GS_OK; ++k) st2 = step_low_impl(c, dts, iters);
+        if (st2 == GS_OK) st2 = upsample_impl(c, dt);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        if (st2 != GS_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st2;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+        GraphEntry g;
+        g.key = key;
+        g.kernels = c->launches - launches0;
+        c->launches = launches0;
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(c, e, "instantiate graph");
+        c->graphs.push_back(g);
+        ge = &c->graphs.back();
+        // the capture only recorded the frame; run it below
+        c->frame = frame0;
+        c->hr_cur = cur0;
+    }
+    CK(cudaGraphLaunch(ge->exec, c->stream), "graph launch");
+    c->launches += ge->kernels;
+    // host-side state as if the frame had been enqueued directly
+    if (resort) {
+        c->hr_cur ^= 1;
+        c->hr_identity = false;
+        c->hr_keys_valid = true;
+    }
+    c->lr_binned = c->n_high > 0;
+    c->frame = frame0 + 1;
+    return GS_OK;
+}
+
+int gs_set_graphs(gs_ctx* c, int enable)
+{
+    int st = check_state(c);
+    if (st) return st;
+    c->use_graphs = enable != 0;
+    if (!c->use_graphs) drop_graphs(c);
+    return GS_OK;
+}
+
+int gs_set_tuning(gs_ctx* c, int warps_per_block, int blocks_per_sm)
+{
+    int st = check_state(c);
+    if (st) return st;
+    if ((warps_per_block != 4 && warps_per_block != 8 && warps_per_block != 16) || blocks_per_sm < 0 ||
+        blocks_per_sm > 32)
+        return fail(c, GS_ERR_ARG, "unsupported launch shape %d x %d", warps_per_block, blocks_per_sm);
+    c->tune_warps = warps_per_block;
+    c->tune_blocks_per_sm = blocks_per_sm;
+    drop_graphs(c);
+    return GS_OK;
+}
+
+int gs_autotune(gs_ctx* c, float dt, int reps, int* warps_per_block, int* blocks_per_sm, float* best_us)
+{
+    int st = check_state(c);
+    if (st) return st;
+    if (!(dt > 0.0f) || reps < 1 || reps > 1000) return fail(c, GS_ERR_ARG, "invalid autotune arguments");
+    if (c->n_high == 0) return fail(c, GS_ERR_STATE, "no HR particles");
+    st = bin_low_impl(c);
+    if (st) return st;
+    // candidate shapes, timed on the current state written out of place
+    // (the state is left unchanged)
+    const int shapes[][2] = {{8, 0}, {4, 0}, {16, 0}, {8, 1}, {8, 2}, {8, 3}, {8, 4}, {4, 4},
+                             {4, 8}, {16, 1}, {16, 2}};
+    const int cur = c->hr_cur;
+    UpsampleArgs u = upsample_args(c, dt, c->hr_pos[cur], c->hr_vel[cur], c->hr_pos[cur ^ 1], c->hr_vel[cur ^ 1]);
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a), "event");
+    CK(cudaEventCreate(&b), "event");
+    float best = 3.0e38f;
+    int bw = c->tune_warps, bb = c->tune_blocks_per_sm;
+    for (const auto& sh : shapes) {
+        CK(gs_launch_upsample(c->stream, u, sh[0], sh[1], c->sm_count, &c->launches), "warm-up");
+        CK(cudaEventRecord(a, c->stream), "event");
+        for (int r = 0; r < reps; ++r) CK(gs_launch_upsample(c->stream, u, sh[0], sh[1], c->sm_count, &c->launches), "tune");
+        CK(cudaEventRecord(b, c->stream), "event");
+        CK(cudaEventSynchronize(b), "event");
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, a, b), "event");
+        const float us = 1000.0f * ms / (float)reps;
+        if (us < best) {
+            best = us;
+            bw = sh[0];
+            bb = sh[1];
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    c->tune_warps = bw;
+    c->tune_blocks_per_sm = bb;
+    drop_graphs(c);
+    if (warps_per_block) *warps_per_block = bw;
+    if (blocks_per_sm) *blocks_per_sm = bb;
+    if (best_us) *best_us = best;
     return GS_OK;
 }
 

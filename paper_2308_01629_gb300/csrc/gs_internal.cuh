@@ -1,5 +1,13 @@
 // gs_internal.cuh -- context layout and launch helpers shared by the CUDA
 // translation units of the library (not part of the public ABI).
+//
+// A context holds S >= 1 independent scenes.  Their particles are stored
+// back to back (LR scene-major; HR scene-major with every scene's slots
+// starting on a multiple of 32 so a warp never spans two scenes), and their
+// grids share one concatenated cell index space: scene s owns the global
+// cells [cell_off, cell_off + n_cell] where the last one is a padding cell
+// that only HR padding slots use.  Sorting by global key therefore keeps
+// every scene's particles inside its own slot range.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -18,10 +26,36 @@ struct GridDev {
     int dx, dy, dz;
 };
 
+// Per-scene descriptor, read by every kernel.
+struct SceneDev {
+    GridDev g;
+    uint32_t cell_off;       // first global cell id of the scene
+    uint32_t n_cell;         // real cells (a padding cell follows)
+    int64_t lr_begin, lr_end;
+    int64_t hr_begin, hr_end;    // real HR slots; [hr_end, next hr_begin) is padding
+    int64_t hr_real_begin;       // original id of the scene's first HR particle
+    int64_t warp_begin;          // first global warp item of the scene
+    float r_low, r_high;
+    float gx, gy, gz;
+    float mu_s, mu_k, c1, c2;
+    float mass_k, ground_z, rc;
+    int friction_mode;
+    int sdf_begin, n_sdf;        // into the context's SDF table
+};
+
 // Device-side error bits, reported by the next blocking call.
 enum : int {
     GS_DEVERR_NEIGHBOR_CAP = 1,   // an LR particle had more candidates than max_neighbors
     GS_DEVERR_BAD_ID = 2,         // an HR id outside [0, n_high) was met while unpermuting
+};
+
+// HR slot tag: scene index, with this bit set on padding slots.
+constexpr uint32_t kPadBit = 0x80000000u;
+
+struct GraphEntry {
+    uint64_t key = 0;
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;    // kernel launches the graph replays
 };
 
 struct gs_ctx {
@@ -29,17 +63,25 @@ struct gs_ctx {
     bool own_stream = false;
     int device = 0;
 
-    int64_t n_low = 0, n_high = 0;
-    float r_low = 0, r_high = 0;
-    int ratio = 1;
-    gs_params prm{};
-    int n_sdf = 0;
-    gs_sdf sdf_host[GS_MAX_SDF]{};
+    int n_scenes = 1;
+    std::vector<SceneDev> scenes;       // host copy of the descriptor table
+    std::vector<gs_params> prm;         // per scene, resolved defaults
+    std::vector<gs_sdf> sdf_host;       // all scenes' SDFs back to back
+    SceneDev* d_scenes = nullptr;
     gs_sdf* d_sdf = nullptr;
 
-    GridDev grid{};
-    int64_t n_cell = 0;
+    int64_t n_low = 0;                  // LR particles, all scenes
+    int64_t n_high = 0;                 // real HR particles, all scenes
+    int64_t hr_slots = 0;               // HR slots including padding
+    int64_t n_warps = 0;                // HR warp items (32 slots each)
+    int64_t n_cell_total = 0;           // global cells incl. one padding cell per scene
     int lr_key_bits = 0, hr_key_bits = 0;
+    int resort_every = 8;
+    int nbr_cap = 64;
+    int n_stab = 2;
+
+    uint32_t* lr_scene = nullptr;       // scene of each LR slot (same in original and cell order)
+    uint32_t* hr_scene = nullptr;       // scene of each HR slot | kPadBit on padding
 
     // LR state (original order) and the binning view
     float4* lr_pos = nullptr;
@@ -48,7 +90,7 @@ struct gs_ctx {
     uint32_t* lr_vals[2] = {nullptr, nullptr};
     uint32_t* lr_sorted_keys = nullptr;           // points into lr_keys after a sort
     uint32_t* lr_sorted_idx = nullptr;            // points into lr_vals after a sort
-    uint32_t* lr_cell_start = nullptr;            // n_cell + 1
+    uint32_t* lr_cell_start = nullptr;            // n_cell_total + 1
     float4* lr_spos = nullptr;                    // cell-ordered LR position (upsampling view)
     float4* lr_svel = nullptr;                    // cell-ordered LR velocity
     bool lr_binned = false;
@@ -59,7 +101,6 @@ struct gs_ctx {
     float4* lr_xt = nullptr;                      // predicted positions, original order
     uint32_t* nbr = nullptr;                      // [cap][n_low] candidate slots
     uint32_t* nbr_cnt = nullptr;
-    int nbr_cap = 64;
 
     // HR state (internal order), ping-pong
     float4* hr_pos[2] = {nullptr, nullptr};
@@ -70,11 +111,21 @@ struct gs_ctx {
     uint32_t* hr_vals[2] = {nullptr, nullptr};
     uint32_t* hr_sorted_keys = nullptr;
     bool hr_keys_valid = false;
-    float4* tmp4 = nullptr;                       // n_high staging for reads / writes
+    float4* tmp4 = nullptr;                       // staging for reads / writes
 
     // radix sort histogram scratch
     uint32_t* sort_hist = nullptr;
     size_t sort_hist_cap = 0;
+
+    // persistent upsampling: work counter and launch shape (autotuned)
+    unsigned* d_work = nullptr;
+    int tune_warps = 8;          // warps per block
+    int tune_blocks_per_sm = 0;  // 0: one warp item per warp (grid launch); else persistent
+    int sm_count = 152;
+
+    // CUDA graphs of whole frames
+    bool use_graphs = false;
+    std::vector<GraphEntry> graphs;
 
     // errors
     int* d_err = nullptr;
@@ -98,17 +149,23 @@ int gs_key_bits(int64_t n_keys);
 // lands in keys[*which] / vals[*which] (which is flipped once per pass).
 cudaError_t gs_radix_sort(cudaStream_t s, uint32_t* keys[2], uint32_t* vals[2], int* which, uint32_t* hist,
                           int64_t n, int key_bits, int64_t* launches);
+// Cell keys of one grid (single-grid form, used by gs_bin_points_static).
 cudaError_t gs_launch_cell_keys(cudaStream_t s, const float4* pos, int64_t n, GridDev g, int fine, uint32_t* keys,
                                 uint32_t* vals, int64_t* launches);
+// Cell keys of slots that belong to several scenes: scene of slot i is
+// tag[i] & ~kPadBit; padding slots get the scene's padding cell.
+cudaError_t gs_launch_scene_keys(cudaStream_t s, const float4* pos, int64_t n, const SceneDev* scenes,
+                                 const uint32_t* tag, int fine, uint32_t* keys, uint32_t* vals, int64_t* launches);
 cudaError_t gs_launch_cell_start(cudaStream_t s, const uint32_t* sorted_keys, int64_t n, int64_t n_cell,
                                  uint32_t* start, int64_t* launches);
 cudaError_t gs_launch_gather2(cudaStream_t s, const uint32_t* idx, const float4* a, const float4* b, float4* a_out,
                               float4* b_out, int64_t n, int64_t* launches);
 cudaError_t gs_launch_unpermute(cudaStream_t s, const float4* pos_internal, const float4* field_internal,
-                                float4* out, int64_t n, int* err, int64_t* launches);
+                                const uint32_t* hr_tag, float4* out, int64_t n_slots, int64_t n_real, int* err,
+                                int64_t* launches);
 cudaError_t gs_launch_permute_in(cudaStream_t s, const float4* pos_internal, const float4* field_original,
-                                 float4* out, int64_t n, int* err, int64_t* launches);
-cudaError_t gs_launch_set_ids(cudaStream_t s, float4* pos, int64_t n, int64_t* launches);
+                                 const uint32_t* hr_tag, float4* out, int64_t n_slots, int64_t n_real, int* err,
+                                 int64_t* launches);
 cudaError_t gs_launch_check_finite(cudaStream_t s, const float4* a, int64_t n, int* flag, int64_t* launches);
 
 // upsample.cu
@@ -117,40 +174,39 @@ struct UpsampleArgs {
     const float4* hr_vel;
     float4* out_pos;
     float4* out_vel;
-    int64_t m;
     const float4* lr_spos;
     const float4* lr_svel;
     const uint32_t* cell_start;
-    GridDev g;
-    float r_low, r_high, dt;
-    float gx, gy, gz;
-    float c1, c2;
+    const SceneDev* scenes;
+    const uint32_t* hr_tag;
     const gs_sdf* sdf;
-    int n_sdf;
+    int n_scenes;
+    int64_t n_warps;           // warp items
+    unsigned* work;            // persistent mode: next warp item (zeroed before the launch)
+    float dt;
 };
-cudaError_t gs_launch_upsample(cudaStream_t s, const UpsampleArgs& a, int64_t* launches);
+// blocks_per_sm == 0: one warp per item; else a persistent grid of
+// blocks_per_sm blocks per SM pulling items from *work (bounded loop).
+cudaError_t gs_launch_upsample(cudaStream_t s, const UpsampleArgs& a, int warps_per_block, int blocks_per_sm,
+                               int sm_count, int64_t* launches);
 
 // pbd.cu
 struct PbdArgs {
     int64_t n;
-    float r, dt;
-    float gx, gy, gz;
-    float mu_s, mu_k;
-    float mass_k, ground_z;
-    float rc;
-    int friction_mode;
+    float dt;
+    const SceneDev* scenes;
+    const uint32_t* lr_scene;
     const gs_sdf* sdf;
-    int n_sdf;
 };
 cudaError_t gs_launch_predict(cudaStream_t s, const PbdArgs& a, const float4* pos, const float4* vel, float4* xt,
                               int64_t* launches);
 cudaError_t gs_launch_step_gather(cudaStream_t s, int64_t n, const uint32_t* idx, const float4* xt,
                                   const float4* pos, float4* s_xt, float4* s_x, int64_t* launches);
 cudaError_t gs_launch_neighbors(cudaStream_t s, const PbdArgs& a, const float4* s_xt, const uint32_t* skeys,
-                                const uint32_t* cell_start, GridDev g, uint32_t* nbr, uint32_t* cnt, int cap,
-                                int* err, int64_t* launches);
+                                const uint32_t* cell_start, uint32_t* nbr, uint32_t* cnt, int cap, int* err,
+                                int64_t* launches);
 cudaError_t gs_launch_pass(cudaStream_t s, const PbdArgs& a, int stab, const float4* x_in, const float4* xt_in,
-                           float4* x_out, float4* xt_out, const uint32_t* nbr, const uint32_t* cnt, int cap,
+                           float4* x_out, float4* xt_out, const uint32_t* nbr, const uint32_t* cnt,
                            int64_t* launches);
 cudaError_t gs_launch_finalize(cudaStream_t s, const PbdArgs& a, const uint32_t* idx, const float4* s_x,
                                const float4* s_xt, float4* pos, float4* vel, int64_t* launches);

@@ -28,10 +28,11 @@ __global__ void k_predict(const PbdArgs a, const float4* __restrict__ pos, const
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
+    const SceneDev& sc = a.scenes[a.lr_scene[i]];
     float4 x = pos[i], v = vel[i];
-    float vx = v.x + a.dt * a.gx, vy = v.y + a.dt * a.gy, vz = v.z + a.dt * a.gz;
+    float vx = v.x + a.dt * sc.gx, vy = v.y + a.dt * sc.gy, vz = v.z + a.dt * sc.gz;
     // 1/m* = (1/m) e^{h(x)}, h = k (z - ground), at the start-of-step position
-    float ws = x.w * expf(a.mass_k * (x.z - a.ground_z));
+    float ws = x.w * expf(sc.mass_k * (x.z - sc.ground_z));
     xt[i] = make_float4(x.x + a.dt * vx, x.y + a.dt * vy, x.z + a.dt * vz, ws);
 }
 
@@ -46,24 +47,26 @@ __global__ void k_step_gather(int64_t n, const uint32_t* __restrict__ idx, const
 }
 
 __global__ void k_neighbors(const PbdArgs a, const float4* __restrict__ s_xt, const uint32_t* __restrict__ skeys,
-                            const uint32_t* __restrict__ cell_start, GridDev g, uint32_t* __restrict__ nbr,
+                            const uint32_t* __restrict__ cell_start, uint32_t* __restrict__ nbr,
                             uint32_t* __restrict__ cnt, int cap, int* err)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.n) return;
+    const SceneDev& sc = a.scenes[a.lr_scene[p]];
+    const GridDev& g = sc.g;
     const float4 xp = s_xt[p];
-    const uint32_t c = skeys[p];
+    const uint32_t c = skeys[p] - sc.cell_off;
     const int cx = (int)(c % (uint32_t)g.dx);
     const int cy = (int)((c / (uint32_t)g.dx) % (uint32_t)g.dy);
     const int cz = (int)(c / ((uint32_t)g.dx * (uint32_t)g.dy));
-    const float rc2 = a.rc * a.rc;
+    const float rc2 = sc.rc * sc.rc;
     const int x0 = cx > 0 ? cx - 1 : 0, x1 = cx + 1 < g.dx ? cx + 1 : g.dx - 1;
     int k = 0;
     for (int z = cz - 1; z <= cz + 1; ++z) {
         if (z < 0 || z >= g.dz) continue;
         for (int y = cy - 1; y <= cy + 1; ++y) {
             if (y < 0 || y >= g.dy) continue;
-            const int64_t row = ((int64_t)z * g.dy + y) * g.dx;
+            const int64_t row = (int64_t)sc.cell_off + ((int64_t)z * g.dy + y) * g.dx;
             const uint32_t b = cell_start[row + x0], e = cell_start[row + x1 + 1];
             for (uint32_t q = b; q < e; ++q) {
                 if ((int64_t)q == p) continue;
@@ -100,14 +103,12 @@ __global__ void __launch_bounds__(128) k_pass(const PbdArgs a, int stab, const f
                                               float4* __restrict__ xt_out, const uint32_t* __restrict__ nbr,
                                               const uint32_t* __restrict__ cnt)
 {
-    __shared__ gs_sdf s_sdf[GS_MAX_SDF];
-    for (int k = threadIdx.x; k < a.n_sdf; k += blockDim.x) s_sdf[k] = a.sdf[k];
-    __syncthreads();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t p = t / kLanes;
     const int sub = (int)(t % kLanes);
     const bool valid = p < a.n;
-    const float d0 = 2.0f * a.r;
+    const SceneDev& sc = a.scenes[valid ? a.lr_scene[p] : 0];
+    const float d0 = 2.0f * sc.r_low;
     float4 xtp = make_float4(0.f, 0.f, 0.f, 0.f), xp = xtp;
     int nc = 0;
     if (valid) {
@@ -142,8 +143,8 @@ __global__ void __launch_bounds__(128) k_pass(const PbdArgs a, int stab, const f
             const float al = (rx * ex + ry * ey + rz * ez) / d2;
             const float tx = rx - al * ex, ty = ry - al * ey, tz = rz - al * ez;
             const float L = sqrtf(tx * tx + ty * ty + tz * tz);
-            const float base = a.friction_mode == 1 ? pen : d0;
-            const float f = m * friction_scale(L, base * a.mu_s, base * a.mu_k);
+            const float base = sc.friction_mode == 1 ? pen : d0;
+            const float f = m * friction_scale(L, base * sc.mu_s, base * sc.mu_k);
             Dx -= f * tx;
             Dy -= f * ty;
             Dz -= f * tz;
@@ -159,14 +160,14 @@ __global__ void __launch_bounds__(128) k_pass(const PbdArgs a, int stab, const f
     }
     if (!valid || sub != 0) return;
     if (wp > 0.0f) {
-        for (int sI = 0; sI < a.n_sdf; ++sI) {
-            const gs_sdf& b = s_sdf[sI];
+        for (int sI = 0; sI < sc.n_sdf; ++sI) {
+            const gs_sdf& b = a.sdf[sc.sdf_begin + sI];
             const int ncomp = sdf_components(b.kind);
-            const float bmu_s = sqrtf(a.mu_s * b.mu_s), bmu_k = sqrtf(a.mu_k * b.mu_k);
+            const float bmu_s = sqrtf(sc.mu_s * b.mu_s), bmu_k = sqrtf(sc.mu_k * b.mu_k);
             for (int c = 0; c < ncomp; ++c) {
                 const SdfHit h = sdf_eval(b, c, yp.x, yp.y, yp.z);
-                if (!(h.phi < a.r)) continue;
-                const float pen = a.r - h.phi;
+                if (!(h.phi < sc.r_low)) continue;
+                const float pen = sc.r_low - h.phi;
                 Dx += pen * h.nx;
                 Dy += pen * h.ny;
                 Dz += pen * h.nz;
@@ -175,7 +176,7 @@ __global__ void __launch_bounds__(128) k_pass(const PbdArgs a, int stab, const f
                     const float al = rx * h.nx + ry * h.ny + rz * h.nz;
                     const float tx = rx - al * h.nx, ty = ry - al * h.ny, tz = rz - al * h.nz;
                     const float L = sqrtf(tx * tx + ty * ty + tz * tz);
-                    const float base = a.friction_mode == 1 ? pen : d0;
+                    const float base = sc.friction_mode == 1 ? pen : d0;
                     const float f = friction_scale(L, base * bmu_s, base * bmu_k);
                     Dx -= f * tx;
                     Dy -= f * ty;
@@ -235,20 +236,19 @@ cudaError_t gs_launch_step_gather(cudaStream_t s, int64_t n, const uint32_t* idx
 }
 
 cudaError_t gs_launch_neighbors(cudaStream_t s, const PbdArgs& a, const float4* s_xt, const uint32_t* skeys,
-                                const uint32_t* cell_start, GridDev g, uint32_t* nbr, uint32_t* cnt, int cap,
-                                int* err, int64_t* launches)
+                                const uint32_t* cell_start, uint32_t* nbr, uint32_t* cnt, int cap, int* err,
+                                int64_t* launches)
 {
     if (a.n <= 0) return cudaSuccess;
-    k_neighbors<<<gs_blocks(a.n, 128), 128, 0, s>>>(a, s_xt, skeys, cell_start, g, nbr, cnt, cap, err);
+    k_neighbors<<<gs_blocks(a.n, 128), 128, 0, s>>>(a, s_xt, skeys, cell_start, nbr, cnt, cap, err);
     *launches += 1;
     return cudaGetLastError();
 }
 
 cudaError_t gs_launch_pass(cudaStream_t s, const PbdArgs& a, int stab, const float4* x_in, const float4* xt_in,
-                           float4* x_out, float4* xt_out, const uint32_t* nbr, const uint32_t* cnt, int cap,
+                           float4* x_out, float4* xt_out, const uint32_t* nbr, const uint32_t* cnt,
                            int64_t* launches)
 {
-    (void)cap;
     if (a.n <= 0) return cudaSuccess;
     k_pass<<<gs_blocks(a.n * kLanes, 128), 128, 0, s>>>(a, stab, x_in, xt_in, x_out, xt_out, nbr, cnt);
     *launches += 1;

@@ -177,6 +177,34 @@ __global__ void k_cell_keys(const float4* __restrict__ pos, int64_t n, GridDev g
     vals[i] = (uint32_t)i;
 }
 
+// Global key of a slot that belongs to scene tag & ~kPadBit: the scene's
+// cell offset plus its cell id (times 8 plus the octant when fine); padding
+// slots take the scene's padding cell so they sort to the end of its range.
+__global__ void k_scene_keys(const float4* __restrict__ pos, int64_t n, const SceneDev* __restrict__ scenes,
+                             const uint32_t* __restrict__ tag, int fine, uint32_t* __restrict__ keys,
+                             uint32_t* __restrict__ vals)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t t = tag[i];
+    const SceneDev& sc = scenes[t & ~kPadBit];
+    uint32_t key;
+    if (t & kPadBit) {
+        key = fine ? (sc.cell_off + sc.n_cell) * 8u : sc.cell_off + sc.n_cell;
+    } else {
+        const GridDev& g = sc.g;
+        float4 p = pos[i];
+        int sx = sub_coord(p.x, g.ox, g.inv_h, g.dx);
+        int sy = sub_coord(p.y, g.oy, g.inv_h, g.dy);
+        int sz = sub_coord(p.z, g.oz, g.inv_h, g.dz);
+        uint32_t cell = sc.cell_off +
+                        ((uint32_t)(sz >> 1) * (uint32_t)g.dy + (uint32_t)(sy >> 1)) * (uint32_t)g.dx + (uint32_t)(sx >> 1);
+        key = fine ? cell * 8u + (uint32_t)((sz & 1) * 4 + (sy & 1) * 2 + (sx & 1)) : cell;
+    }
+    keys[i] = key;
+    vals[i] = (uint32_t)i;
+}
+
 __global__ void k_cell_start(const uint32_t* __restrict__ sk, int64_t n, int64_t n_cell, uint32_t* __restrict__ start)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -200,37 +228,34 @@ __global__ void k_gather2(const uint32_t* __restrict__ idx, const float4* __rest
     if (b) bo[p] = b[i];
 }
 
-__global__ void k_unpermute(const float4* __restrict__ pos, const float4* __restrict__ f, float4* __restrict__ out,
-                            int64_t n, int* err)
+// HR exchange in original-id order: slot p (a real particle, not padding)
+// holds the particle whose id is in pos.w.
+__global__ void k_unpermute(const float4* __restrict__ pos, const float4* __restrict__ f,
+                            const uint32_t* __restrict__ tag, float4* __restrict__ out, int64_t n_slots,
+                            int64_t n_real, int* err)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
+    if (p >= n_slots || (tag[p] & kPadBit)) return;
     uint32_t id = __float_as_uint(pos[p].w);
-    if ((int64_t)id >= n) {
+    if ((int64_t)id >= n_real) {
         atomicOr(err, GS_DEVERR_BAD_ID);
         return;
     }
     out[id] = f[p];
 }
 
-__global__ void k_permute_in(const float4* __restrict__ pos, const float4* __restrict__ f, float4* __restrict__ out,
-                             int64_t n, int* err)
+__global__ void k_permute_in(const float4* __restrict__ pos, const float4* __restrict__ f,
+                             const uint32_t* __restrict__ tag, float4* __restrict__ out, int64_t n_slots,
+                             int64_t n_real, int* err)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
+    if (p >= n_slots || (tag[p] & kPadBit)) return;
     uint32_t id = __float_as_uint(pos[p].w);
-    if ((int64_t)id >= n) {
+    if ((int64_t)id >= n_real) {
         atomicOr(err, GS_DEVERR_BAD_ID);
         return;
     }
     out[p] = f[id];
-}
-
-__global__ void k_set_ids(float4* __restrict__ pos, int64_t n)
-{
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    pos[p].w = __uint_as_float((uint32_t)p);
 }
 
 __global__ void k_check_finite(const float4* __restrict__ a, int64_t n, int* flag)
@@ -301,27 +326,32 @@ cudaError_t gs_launch_gather2(cudaStream_t s, const uint32_t* idx, const float4*
 }
 
 cudaError_t gs_launch_unpermute(cudaStream_t s, const float4* pos_internal, const float4* field_internal,
-                                float4* out, int64_t n, int* err, int64_t* launches)
+                                const uint32_t* hr_tag, float4* out, int64_t n_slots, int64_t n_real, int* err,
+                                int64_t* launches)
 {
-    if (n <= 0) return cudaSuccess;
-    k_unpermute<<<gs_blocks(n, 256), 256, 0, s>>>(pos_internal, field_internal, out, n, err);
+    if (n_slots <= 0) return cudaSuccess;
+    k_unpermute<<<gs_blocks(n_slots, 256), 256, 0, s>>>(pos_internal, field_internal, hr_tag, out, n_slots, n_real,
+                                                        err);
     *launches += 1;
     return cudaGetLastError();
 }
 
 cudaError_t gs_launch_permute_in(cudaStream_t s, const float4* pos_internal, const float4* field_original,
-                                 float4* out, int64_t n, int* err, int64_t* launches)
+                                 const uint32_t* hr_tag, float4* out, int64_t n_slots, int64_t n_real, int* err,
+                                 int64_t* launches)
 {
-    if (n <= 0) return cudaSuccess;
-    k_permute_in<<<gs_blocks(n, 256), 256, 0, s>>>(pos_internal, field_original, out, n, err);
+    if (n_slots <= 0) return cudaSuccess;
+    k_permute_in<<<gs_blocks(n_slots, 256), 256, 0, s>>>(pos_internal, field_original, hr_tag, out, n_slots,
+                                                         n_real, err);
     *launches += 1;
     return cudaGetLastError();
 }
 
-cudaError_t gs_launch_set_ids(cudaStream_t s, float4* pos, int64_t n, int64_t* launches)
+cudaError_t gs_launch_scene_keys(cudaStream_t s, const float4* pos, int64_t n, const SceneDev* scenes,
+                                 const uint32_t* tag, int fine, uint32_t* keys, uint32_t* vals, int64_t* launches)
 {
     if (n <= 0) return cudaSuccess;
-    k_set_ids<<<gs_blocks(n, 256), 256, 0, s>>>(pos, n);
+    k_scene_keys<<<gs_blocks(n, 256), 256, 0, s>>>(pos, n, scenes, tag, fine, keys, vals);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -22,8 +22,6 @@
 
 namespace {
 
-constexpr int kWarps = 8;
-constexpr int kThreads = kWarps * 32;
 constexpr int kBuf = 64;   // staged LR per warp; flushed at >= 32
 
 __device__ __forceinline__ int cell_coord(float x, float o, float inv_h, int dim)
@@ -90,38 +88,28 @@ __device__ __forceinline__ int sub_floor(float x, float o, float inv_h)
     return (int)f;
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_upsample(const UpsampleArgs a)
+// One warp item: the 32 HR slots [32 item, 32 item + 32) of one scene.
+__device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t item, float4* ba, float4* bb, int lane)
 {
-    // staged LR candidates of a lane group, in group-local coordinates
-    // u = (x - c0) / (3 r_LR):  A = (2 u_j, -|u_j|^2),  B = (v_j, 0)
-    __shared__ float4 s_a[kWarps][kBuf];
-    __shared__ float4 s_b[kWarps][kBuf];
-    __shared__ gs_sdf s_sdf[GS_MAX_SDF];
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = threadIdx.x; k < a.n_sdf; k += kThreads) s_sdf[k] = a.sdf[k];
-    __syncthreads();
-
-    const int64_t first = ((int64_t)blockIdx.x * kWarps + warp) * 32;
-    if (first >= a.m) return;
+    const int64_t first = item * 32;
+    const uint32_t tag = __ldg(a.hr_tag + first);          // the first slot of an item is never padding
+    const SceneDev& sc = a.scenes[tag & ~kPadBit];
     const int64_t i = first + lane;
-    const bool valid = i < a.m;
+    const bool valid = i < sc.hr_end;
 
     float4 p = make_float4(0.f, 0.f, 0.f, 0.f), v = p;
     if (valid) {
         p = __ldcs(a.hr_pos + i);
         v = __ldcs(a.hr_vel + i);
     }
-    const GridDev& g = a.g;
+    const GridDev& g = sc.g;
     const int sx = sub_floor(p.x, g.ox, g.inv_h), sy = sub_floor(p.y, g.oy, g.inv_h), sz = sub_floor(p.z, g.oz, g.inv_h);
 
-    const float R = 3.0f * a.r_low * (1.0f + 1.0e-5f);    // support, padded against rounding
+    const float R = 3.0f * sc.r_low * (1.0f + 1.0e-5f);    // support, padded against rounding
     const float R2 = R * R;
-    const float inv9r2 = 1.0f / (9.0f * a.r_low * a.r_low);
     const unsigned lt = (1u << lane) - 1u;
-    float4* ba = s_a[warp];
-    float4* bb = s_b[warp];
-    const float inv3r = 1.0f / (3.0f * a.r_low);
+    const float inv3r = 1.0f / (3.0f * sc.r_low);
+    const int64_t coff = sc.cell_off;
 
     float S = 0.f, Vx = 0.f, Vy = 0.f, Vz = 0.f, wmax = 0.f;
     unsigned pending = __ballot_sync(0xffffffffu, valid);
@@ -195,8 +183,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_upsample(const UpsampleArgs a)
                 const int jz = (int)(((float)j + 0.5f) * inv_ny);   // j / ny, exact for small j
                 const int cz = cz0 + jz, cy = cy0 + (j - jz * ny);
                 const int64_t row = ((int64_t)cz * g.dy + cy) * g.dx;
-                rb = __ldg(a.cell_start + row + cx0);
-                len = __ldg(a.cell_start + row + cx1 + 1) - rb;
+                rb = __ldg(a.cell_start + coff + row + cx0);
+                len = __ldg(a.cell_start + coff + row + cx1 + 1) - rb;
             }
             uint32_t incl = len;   // inclusive prefix over rows
 #pragma unroll
@@ -248,25 +236,71 @@ __global__ void __launch_bounds__(kThreads, 4) k_upsample(const UpsampleArgs a)
         vty = Vy * inv;
         vtz = Vz * inv;
     }
-    const bool A = wmax <= a.c1;
-    const bool B = S > 0.0f && wmax >= a.c2 * S;
+    const bool A = wmax <= sc.c1;
+    const bool B = S > 0.0f && wmax >= sc.c2 * S;
     const float alpha = (A || B) ? 1.0f - wmax : 0.0f;
-    float nvx = (1.0f - alpha) * vtx + alpha * (v.x + a.dt * a.gx);
-    float nvy = (1.0f - alpha) * vty + alpha * (v.y + a.dt * a.gy);
-    float nvz = (1.0f - alpha) * vtz + alpha * (v.z + a.dt * a.gz);
+    float nvx = (1.0f - alpha) * vtx + alpha * (v.x + a.dt * sc.gx);
+    float nvy = (1.0f - alpha) * vty + alpha * (v.y + a.dt * sc.gy);
+    float nvz = (1.0f - alpha) * vtz + alpha * (v.z + a.dt * sc.gz);
     float nx = p.x + a.dt * nvx, ny = p.y + a.dt * nvy, nz = p.z + a.dt * nvz;
-    hr_boundary(nx, ny, nz, nvx, nvy, nvz, s_sdf, a.n_sdf, a.r_high);
+    hr_boundary(nx, ny, nz, nvx, nvy, nvz, a.sdf + sc.sdf_begin, sc.n_sdf, sc.r_high);
     __stcs(a.out_pos + i, make_float4(nx, ny, nz, p.w));
     __stcs(a.out_vel + i, make_float4(nvx, nvy, nvz, 0.0f));
 }
 
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_upsample(const UpsampleArgs a, int persistent)
+{
+    __shared__ float4 s_a[WARPS][kBuf];
+    __shared__ float4 s_b[WARPS][kBuf];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // One call site for both launch modes, so both run the same code.  In
+    // the persistent mode warps pull items until the counter passes
+    // n_warps; every warp leaves after at most n_warps + 1 iterations.
+    for (int64_t guard = 0; guard <= a.n_warps; ++guard) {
+        int64_t item;
+        if (persistent) {
+            unsigned it = 0;
+            if (lane == 0) it = atomicAdd(a.work, 1u);
+            item = (int64_t)__shfl_sync(0xffffffffu, it, 0);
+        } else {
+            item = guard == 0 ? (int64_t)blockIdx.x * WARPS + warp : a.n_warps;
+        }
+        if (item >= a.n_warps) break;
+        upsample_item(a, item, s_a[warp], s_b[warp], lane);
+    }
+}
+
 }  // namespace
 
-cudaError_t gs_launch_upsample(cudaStream_t s, const UpsampleArgs& a, int64_t* launches)
+template <int WARPS>
+static cudaError_t launch_w(cudaStream_t s, const UpsampleArgs& a, int blocks_per_sm, int sm_count)
 {
-    if (a.m <= 0) return cudaSuccess;
-    int64_t warps = (a.m + 31) / 32;
-    k_upsample<<<gs_blocks(warps, kWarps), kThreads, 0, s>>>(a);
-    *launches += 1;
+    if (blocks_per_sm <= 0) {
+        k_upsample<WARPS><<<gs_blocks(a.n_warps, WARPS), WARPS * 32, 0, s>>>(a, 0);
+    } else {
+        int64_t nb = (int64_t)blocks_per_sm * sm_count;
+        const int64_t need = (a.n_warps + WARPS - 1) / WARPS;
+        if (nb > need) nb = need;
+        k_upsample<WARPS><<<(unsigned)nb, WARPS * 32, 0, s>>>(a, 1);
+    }
     return cudaGetLastError();
+}
+
+cudaError_t gs_launch_upsample(cudaStream_t s, const UpsampleArgs& a, int warps_per_block, int blocks_per_sm,
+                               int sm_count, int64_t* launches)
+{
+    if (a.n_warps <= 0) return cudaSuccess;
+    if (blocks_per_sm > 0) {
+        cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e;
+    switch (warps_per_block) {
+    case 4: e = launch_w<4>(s, a, blocks_per_sm, sm_count); break;
+    case 16: e = launch_w<16>(s, a, blocks_per_sm, sm_count); break;
+    default: e = launch_w<8>(s, a, blocks_per_sm, sm_count); break;
+    }
+    *launches += 1;
+    return e;
 }

@@ -15,8 +15,8 @@ def _reference(gs, sc):
     ctx = gs.Context(sc)
     ctx.bin_low()
     idx = ctx.read(gs.GS_FIELD_LR_SORTED_INDEX)
-    start = ctx.read(gs.GS_FIELD_LR_CELL_START)
     grid = ctx.grid
+    start = ctx.read(gs.GS_FIELD_LR_CELL_START)[:int(grid.n_cell) + 1]   # without the scene's padding cell
     ctx.close()
     return idx, start, grid
 

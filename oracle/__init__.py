@@ -72,6 +72,11 @@ def _L():
         L.or_pbd_step.restype = ctypes.c_int
         L.or_pairs_within.argtypes = [P, ctypes.c_long, P, ctypes.c_long, ctypes.c_double, P, P, ctypes.c_long]
         L.or_pairs_within.restype = ctypes.c_long
+        L.or_upsample_vjp.argtypes = [P, P, ctypes.c_long, P, P, ctypes.c_long, P, ctypes.c_int, P, P, P,
+                                      P, P, P, P]
+        L.or_upsample_vjp.restype = ctypes.c_int
+        L.or_pbd_step_vjp.argtypes = [P, P, P, ctypes.c_long, P, ctypes.c_int, P, P, P, P, P]
+        L.or_pbd_step_vjp.restype = ctypes.c_int
         L.or_pairs_within_grid.argtypes = L.or_pairs_within.argtypes
         L.or_pairs_within_grid.restype = ctypes.c_long
         _lib = L
@@ -174,6 +179,22 @@ def upsample(lr_x, lr_v, hr_x, hr_v, sdf, prm, sub=None, mode=0):
     return out
 
 
+def upsample_vjp(lr_x, lr_v, hr_x, hr_v, sdf, prm, gx, gv):
+    """Reverse mode of ``upsample``: given dL/dx^{t+1}, dL/dv^{t+1} returns
+    (dL/dX_LR, dL/dV_LR, dL/dx_HR, dL/dv_HR) for the forward branch
+    decisions (contact normals held fixed)."""
+    lr_x, lr_v = _f64(lr_x, 3), _f64(lr_v, 3)
+    hr_x, hr_v = _f64(hr_x, 3), _f64(hr_v, 3)
+    sdf = _f64(sdf, SDF_STRIDE) if sdf is not None and len(sdf) else np.zeros((0, SDF_STRIDE))
+    gx, gv = _f64(gx, 3), _f64(gv, 3)
+    out = [np.zeros_like(lr_x), np.zeros_like(lr_v), np.zeros_like(hr_x), np.zeros_like(hr_v)]
+    rc = _L().or_upsample_vjp(_ptr(lr_x), _ptr(lr_v), len(lr_x), _ptr(hr_x), _ptr(hr_v), len(hr_x), _ptr(sdf),
+                              len(sdf), _ptr(_prm(prm, UP_KEYS)), _ptr(gx), _ptr(gv), *[_ptr(o) for o in out])
+    if rc != 0:
+        raise RuntimeError("or_upsample_vjp failed")
+    return tuple(out)
+
+
 # ------------------------------------------------------------- LR step ---
 def pbd_step(x, v, inv_m, sdf, prm, mode=0):
     """One LR time step of Algorithm 1.  Returns (x, v, suspect, stats)."""
@@ -190,6 +211,22 @@ def pbd_step(x, v, inv_m, sdf, prm, mode=0):
     return x, v, sus.astype(bool), dict(pairs=int(stats[0]), significant=int(stats[1]),
                                         max_candidates=int(stats[2]), active=int(stats[3]),
                                         ambiguous=int(stats[4]))
+
+
+def pbd_step_vjp(x, v, inv_m, sdf, prm, gx, gv):
+    """Reverse mode of ``pbd_step`` (brute-force pairs): given dL/dx_out,
+    dL/dv_out returns (dL/dx, dL/dv) at the start of the step for the
+    forward pass's branch decisions."""
+    x, v = _f64(x, 3), _f64(v, 3)
+    inv_m = _f64(inv_m)
+    sdf = _f64(sdf, SDF_STRIDE) if sdf is not None and len(sdf) else np.zeros((0, SDF_STRIDE))
+    gx, gv = _f64(gx, 3), _f64(gv, 3)
+    ox, ov = np.zeros_like(x), np.zeros_like(v)
+    rc = _L().or_pbd_step_vjp(_ptr(x), _ptr(v), _ptr(inv_m), len(x), _ptr(sdf), len(sdf), _ptr(_prm(prm, PB_KEYS)),
+                              _ptr(gx), _ptr(gv), _ptr(ox), _ptr(ov))
+    if rc != 0:
+        raise RuntimeError("or_pbd_step_vjp failed")
+    return ox, ov
 
 
 def pairs_within(a, b, R, use_grid=False):

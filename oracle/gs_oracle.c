@@ -918,3 +918,463 @@ long or_pairs_within_grid(const double* a, long na, const double* b, long nb, do
     grid_free(&g);
     return n;
 }
+
+/* ------------------------------------------------------------------ */
+/* Reverse mode of the HR frame (for the differentiable pattern).       */
+/* ------------------------------------------------------------------ */
+
+/* Vector-Jacobian product of or_upsample's map
+ *   (X_j, V_j [LR], x_i, v_i [HR]) -> (x_i^{t+1}, v_i^{t+1})
+ * for the branch decisions of the forward pass (blend case, which LR
+ * particle has the largest weight, SDF contacts).  Each active SDF
+ * contact component is differentiated with its normal held fixed (exact for
+ * planar walls): the projection x + (r_HR - phi) n has Jacobian I - n n^T,
+ * and the removal of an inward normal velocity has Jacobian I - n n^T.
+ * gx, gv: dL/dx^{t+1}, dL/dv^{t+1} (HR, n x 3).  Outputs (accumulated, the
+ * caller zeroes them): gX, gV (LR, N x 3), ghx, ghv (HR, M x 3). */
+int or_upsample_vjp(const double* lr_x, const double* lr_v, long N, const double* hr_x, const double* hr_v, long M,
+                    const double* sdf, int n_sdf, const double* prm, const double* gx_out, const double* gv_out,
+                    double* gX, double* gV, double* ghx, double* ghv)
+{
+    double r = prm[UP_R_LOW], c1 = prm[UP_C1], c2 = prm[UP_C2], dt = prm[UP_DT], rh = prm[UP_R_HIGH];
+    double eps_x = prm[UP_EPS_X];
+    const double g[3] = {prm[UP_GX], prm[UP_GY], prm[UP_GZ]};
+    double R2 = 9.0 * r * r;
+    for (long i = 0; i < M; ++i) {
+        const double* xi = hr_x + 3 * i;
+        const double* vi = hr_v + 3 * i;
+        /* forward, as in or_upsample */
+        double S = 0, V[3] = {0, 0, 0}, wmax = 0;
+        long jstar = -1;
+        for (long j = 0; j < N; ++j) {
+            double d[3] = {xi[0] - lr_x[3 * j], xi[1] - lr_x[3 * j + 1], xi[2] - lr_x[3 * j + 2]};
+            double d2 = dot3(d, d);
+            if (!(d2 < R2)) continue;
+            double w = or_weight(d2, r);
+            S += w;
+            for (int m = 0; m < 3; ++m) V[m] += w * lr_v[3 * j + m];
+            if (w > wmax) { wmax = w; jstar = j; }
+        }
+        double vt[3] = {0, 0, 0};
+        if (S > 0)
+            for (int m = 0; m < 3; ++m) vt[m] = V[m] / S;
+        int branch = (wmax <= c1) || (S > 0 && wmax >= c2 * S);
+        double alpha = branch ? 1.0 - wmax : 0.0;
+        double vp[3], xp[3];
+        for (int m = 0; m < 3; ++m) {
+            vp[m] = (1.0 - alpha) * vt[m] + alpha * (vi[m] + dt * g[m]);
+            xp[m] = xi[m] + dt * vp[m];
+        }
+        /* SDF rule forward, recording the normals of the active steps */
+        double nrm[64][3];
+        int kind_v[64], n_steps = 0;
+        for (int s = 0; s < n_sdf; ++s) {
+            const double* rec = sdf + OR_SDF_STRIDE * s;
+            const double* ub = rec + 13;
+            int nc = sdf_ncomp(rec);
+            for (int c = 0; c < nc; ++c) {
+                double phi[OR_MAX_COMP], nn[3 * OR_MAX_COMP];
+                int tie;
+                or_sdf_eval(rec, xp, phi, nn, &tie, eps_x);
+                if (!(phi[c] < rh)) continue;
+                const double* n = nn + 3 * c;
+                double push = rh - phi[c];
+                for (int m = 0; m < 3; ++m) xp[m] += push * n[m];
+                double vr[3] = {vp[0] - ub[0], vp[1] - ub[1], vp[2] - ub[2]};
+                double vn = dot3(vr, n);
+                if (vn < 0)
+                    for (int m = 0; m < 3; ++m) vp[m] -= vn * n[m];
+                if (n_steps < 64) {
+                    for (int m = 0; m < 3; ++m) nrm[n_steps][m] = n[m];
+                    kind_v[n_steps] = vn < 0;
+                    ++n_steps;
+                }
+            }
+        }
+        /* reverse: SDF steps, last first */
+        double ax[3], av[3];
+        for (int m = 0; m < 3; ++m) { ax[m] = gx_out[3 * i + m]; av[m] = gv_out[3 * i + m]; }
+        for (int k = n_steps - 1; k >= 0; --k) {
+            const double* n = nrm[k];
+            if (kind_v[k]) {
+                double a = dot3(av, n);
+                for (int m = 0; m < 3; ++m) av[m] -= a * n[m];
+            }
+            double a = dot3(ax, n);
+            for (int m = 0; m < 3; ++m) ax[m] -= a * n[m];
+        }
+        /* x' = x + dt v' */
+        double gvp[3], gvt[3], galpha = 0;
+        for (int m = 0; m < 3; ++m) {
+            ghx[3 * i + m] += ax[m];
+            gvp[m] = av[m] + dt * ax[m];
+        }
+        /* v' = (1 - alpha) vtilde + alpha (v + dt g) */
+        for (int m = 0; m < 3; ++m) {
+            gvt[m] = (1.0 - alpha) * gvp[m];
+            ghv[3 * i + m] += alpha * gvp[m];
+            galpha += gvp[m] * (vi[m] + dt * g[m] - vt[m]);
+        }
+        double gwmax = branch ? -galpha : 0.0;
+        if (!(S > 0)) continue;           /* no LR particle in reach: nothing else depends on LR */
+        /* vtilde = V / S */
+        double gV_[3] = {gvt[0] / S, gvt[1] / S, gvt[2] / S};
+        double gS = -dot3(gvt, vt) / S;
+        for (long j = 0; j < N; ++j) {
+            double d[3] = {xi[0] - lr_x[3 * j], xi[1] - lr_x[3 * j + 1], xi[2] - lr_x[3 * j + 2]};
+            double d2 = dot3(d, d);
+            if (!(d2 < R2)) continue;
+            double t = 1.0 - d2 / R2;
+            double w = t * t * t;
+            double gw = gS + dot3(gV_, lr_v + 3 * j) + (j == jstar ? gwmax : 0.0);
+            /* dw/dx_i = -6 t^2 d / (9 r^2) = -dw/dX_j */
+            double k6 = 6.0 * t * t / R2;
+            for (int m = 0; m < 3; ++m) {
+                gX[3 * j + m] += gw * k6 * d[m];
+                ghx[3 * i + m] -= gw * k6 * d[m];
+                gV[3 * j + m] += w * gV_[m];
+            }
+        }
+    }
+    return 0;
+}
+
+/* Reverse mode of one LR step (Algorithm 1) for the branch decisions of the
+ * forward pass: which candidate pairs and SDF components are in contact in
+ * each pass, static or kinetic friction, and whether the kinetic scale is
+ * clipped.  SDF normals are held fixed (exact for planar walls).
+ *
+ * Pair (i, j) evaluated on positions y (x in stabilization, xt in the solver),
+ * e = y_j - y_i, L = |e|, u = e / L, pen = 2r - L, W = w_i + w_j (inverse
+ * scaled masses), m_i = w_i / W, m_j = w_j / W:
+ *   contact     c_i = -m_i pen u,  c_j = +m_j pen u,
+ *               d(pen u)/de = (2r/L - 1) I - (2r/L) u u^T =: K
+ *   friction    rel = (xt_i - x_i) - (xt_j - x_j),  perp = P rel,
+ *               P = I - e e^T / (e.e),  F = s perp  (s = 1, or
+ *               thr_k / |perp| when clipped),  c_i -= m_i F,  c_j += m_j F
+ *               dF/d rel = Q P,  dF/de = Q dperp/de,  Q = I or
+ *               (thr_k / |perp|)(I - p p^T) (+ threshold terms in mode 1)
+ *   SDF         c = (r - phi) n - F(d),  d = (xt - x) - u_b dt
+ * A pass moves particle i by (sum_k c_ik) / n_i; the adjoint pushes
+ * h_i = g_i / n_i back through every contribution. */
+
+typedef struct { double v[9]; } m33;
+
+static void m33_outer_add(m33* A, double s, const double* a, const double* b)
+{
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) A->v[3 * r + c] += s * a[r] * b[c];
+}
+
+static void m33_eye(m33* A, double s)
+{
+    memset(A, 0, sizeof *A);
+    A->v[0] = A->v[4] = A->v[8] = s;
+}
+
+/* out += s * A^T h */
+static void m33_tmul_add(double* out, double s, const m33* A, const double* h)
+{
+    for (int c = 0; c < 3; ++c)
+        out[c] += s * (A->v[c] * h[0] + A->v[3 + c] * h[1] + A->v[6 + c] * h[2]);
+}
+
+static void m33_mul(m33* C, const m33* A, const m33* B)
+{
+    m33 R;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            R.v[3 * r + c] = A->v[3 * r] * B->v[c] + A->v[3 * r + 1] * B->v[3 + c] + A->v[3 * r + 2] * B->v[6 + c];
+    *C = R;
+}
+
+/* Friction F(rel) with tangent plane normal to e (pair) or n (SDF): value
+ * and Jacobians dF/drel and dF/de (zero for SDF, where e_is_normal). */
+static void friction_jac(const double* rel, const double* e, int e_is_normal, double thr_s, double thr_k,
+                         int mode1, double mu_k, const double* u_for_thr, double* F, m33* Frel, m33* Fe)
+{
+    double ee = dot3(e, e);
+    double a = dot3(rel, e) / ee;
+    double perp[3] = {rel[0] - a * e[0], rel[1] - a * e[1], rel[2] - a * e[2]};
+    m33 P, G;
+    m33_eye(&P, 1.0);
+    m33_outer_add(&P, -1.0 / ee, e, e);
+    memset(&G, 0, sizeof G);
+    if (!e_is_normal) {
+        /* dperp_a/de_b = -(e_a rel_b + (rel.e) delta_ab)/(e.e) + 2 (rel.e) e_a e_b/(e.e)^2 */
+        double re = dot3(rel, e);
+        m33_outer_add(&G, -1.0 / ee, e, rel);
+        for (int k = 0; k < 3; ++k) G.v[4 * k] -= re / ee;
+        m33_outer_add(&G, 2.0 * re / (ee * ee), e, e);
+    }
+    double Lp = sqrt(dot3(perp, perp));
+    int clipped = !(Lp < thr_s) && Lp > 0 && thr_k / Lp < 1.0;
+    m33 Q;
+    if (clipped) {
+        double p[3] = {perp[0] / Lp, perp[1] / Lp, perp[2] / Lp};
+        m33_eye(&Q, thr_k / Lp);
+        m33_outer_add(&Q, -thr_k / Lp, p, p);
+        for (int k = 0; k < 3; ++k) F[k] = thr_k * p[k];
+        m33_mul(Frel, &Q, &P);
+        m33_mul(Fe, &Q, &G);
+        if (mode1) {   /* thr_k = pen mu_k, dpen/de = -u^T */
+            m33_outer_add(Fe, -mu_k, p, u_for_thr);
+        }
+    } else {
+        for (int k = 0; k < 3; ++k) F[k] = perp[k];
+        *Frel = P;
+        *Fe = G;
+    }
+}
+
+int or_pbd_step_vjp(const double* x0, const double* v0, const double* inv_m, long N, const double* sdf, int n_sdf,
+                    const double* prm, const double* gx_out, const double* gv_out, double* gx0, double* gv0)
+{
+    double r = prm[PB_R], dt = prm[PB_DT];
+    const double g[3] = {prm[PB_GX], prm[PB_GY], prm[PB_GZ]};
+    double mu_s = prm[PB_MU_S], mu_k = prm[PB_MU_K];
+    int n_stab = (int)prm[PB_N_STAB], iters = (int)prm[PB_ITERS];
+    double mass_k = prm[PB_MASS_K], ground = prm[PB_GROUND_Z], Rc = prm[PB_RC];
+    int fmode = (int)prm[PB_FRIC_MODE];
+    double d0 = 2.0 * r;
+    int total = n_stab + iters;
+    size_t n1 = (size_t)(N ? N : 1);
+    /* forward with snapshots: Y[p] = positions the pass p evaluates on */
+    double* x = (double*)malloc(n1 * 3 * sizeof(double));
+    double* xt = (double*)malloc(n1 * 3 * sizeof(double));
+    double* ws = (double*)malloc(n1 * sizeof(double));
+    double* Y = (double*)malloc((size_t)(total + 1) * n1 * 3 * sizeof(double));
+    double* XT = (double*)malloc((size_t)(total + 1) * n1 * 3 * sizeof(double));
+    double* D = (double*)malloc(n1 * 3 * sizeof(double));
+    long* cnt = (long*)malloc(n1 * sizeof(long));
+    long* CNT = (long*)malloc((size_t)(total + 1) * n1 * sizeof(long));
+    if (!x || !xt || !ws || !Y || !XT || !D || !cnt || !CNT) return -1;
+    for (long i = 0; i < N; ++i) {
+        for (int k = 0; k < 3; ++k) {
+            x[3 * i + k] = x0[3 * i + k];
+            xt[3 * i + k] = x0[3 * i + k] + dt * (v0[3 * i + k] + dt * g[k]);
+        }
+        ws[i] = inv_m[i] * exp(mass_k * (x0[3 * i + 2] - ground));
+    }
+    or_pair *Pp = NULL, *E = NULL;
+    unsigned char* border = NULL;
+    long n_excl = 0;
+    long np = make_pairs(xt, N, Rc, 0, &Pp, &border, &E, &n_excl, 0.0);
+    if (np < 0) return -1;
+    double* Xfix = NULL;
+    for (int it = 0; it < total; ++it) {
+        int stab = it < n_stab;
+        const double* y = stab ? x : xt;
+        memcpy(Y + (size_t)it * n1 * 3, y, (size_t)N * 3 * sizeof(double));
+        memcpy(XT + (size_t)it * n1 * 3, xt, (size_t)N * 3 * sizeof(double));
+        memset(D, 0, (size_t)N * 3 * sizeof(double));
+        memset(cnt, 0, (size_t)N * sizeof(long));
+        for (long p = 0; p < np; ++p) {
+            long i = Pp[p].i, j = Pp[p].j;
+            double e[3] = {y[3 * j] - y[3 * i], y[3 * j + 1] - y[3 * i + 1], y[3 * j + 2] - y[3 * i + 2]};
+            double L = sqrt(dot3(e, e));
+            if (!(L < d0) || L == 0.0 || !(ws[i] + ws[j] > 0)) continue;
+            double W = ws[i] + ws[j], mi = ws[i] / W, mj = ws[j] / W, pen = d0 - L;
+            double u[3] = {e[0] / L, e[1] / L, e[2] / L};
+            for (int k = 0; k < 3; ++k) {
+                D[3 * i + k] -= mi * pen * u[k];
+                D[3 * j + k] += mj * pen * u[k];
+            }
+            if (!stab) {
+                double rel[3], F[3];
+                m33 Fr, Fe;
+                for (int k = 0; k < 3; ++k) rel[k] = (xt[3 * i + k] - x[3 * i + k]) - (xt[3 * j + k] - x[3 * j + k]);
+                double base = fmode == 1 ? pen : d0;
+                friction_jac(rel, e, 0, base * mu_s, base * mu_k, fmode == 1, mu_k, u, F, &Fr, &Fe);
+                for (int k = 0; k < 3; ++k) {
+                    D[3 * i + k] -= mi * F[k];
+                    D[3 * j + k] += mj * F[k];
+                }
+            }
+            cnt[i]++;
+            cnt[j]++;
+        }
+        for (long i = 0; i < N; ++i) {
+            if (!(ws[i] > 0)) continue;
+            for (int s = 0; s < n_sdf; ++s) {
+                const double* rec = sdf + OR_SDF_STRIDE * s;
+                double phi[OR_MAX_COMP], nn[3 * OR_MAX_COMP];
+                int tie;
+                int nc = or_sdf_eval(rec, y + 3 * i, phi, nn, &tie, 0.0);
+                double bmu_s = sqrt(mu_s * rec[16]), bmu_k = sqrt(mu_k * rec[17]);
+                for (int c = 0; c < nc; ++c) {
+                    if (!(phi[c] < r)) continue;
+                    const double* n = nn + 3 * c;
+                    double pen = r - phi[c];
+                    for (int k = 0; k < 3; ++k) D[3 * i + k] += pen * n[k];
+                    if (!stab) {
+                        double d[3], F[3];
+                        m33 Fr, Fe;
+                        for (int k = 0; k < 3; ++k) d[k] = (xt[3 * i + k] - x[3 * i + k]) - rec[13 + k] * dt;
+                        double base = fmode == 1 ? pen : d0;
+                        friction_jac(d, n, 1, base * bmu_s, base * bmu_k, fmode == 1, bmu_k, n, F, &Fr, &Fe);
+                        for (int k = 0; k < 3; ++k) D[3 * i + k] -= F[k];
+                    }
+                    cnt[i]++;
+                }
+            }
+        }
+        memcpy(CNT + (size_t)it * n1, cnt, (size_t)N * sizeof(long));
+        for (long i = 0; i < N; ++i) {
+            if (cnt[i] == 0) continue;
+            for (int k = 0; k < 3; ++k) {
+                double dd = D[3 * i + k] / (double)cnt[i];
+                xt[3 * i + k] += dd;
+                if (stab) x[3 * i + k] += dd;
+            }
+        }
+        if (it == n_stab - 1 || (n_stab == 0 && it == 0)) {
+            if (!Xfix) Xfix = (double*)malloc(n1 * 3 * sizeof(double));
+        }
+    }
+    if (!Xfix) Xfix = (double*)malloc(n1 * 3 * sizeof(double));
+    memcpy(Xfix, x, (size_t)N * 3 * sizeof(double));   /* x after stabilization (fixed in the solver) */
+
+    /* reverse: outputs x_out = xt, v_out = (xt - x) / dt */
+    double* gxt = (double*)calloc(n1 * 3, sizeof(double));
+    double* gx = (double*)calloc(n1 * 3, sizeof(double));
+    double* gws = (double*)calloc(n1, sizeof(double));
+    double* H = (double*)malloc(n1 * 3 * sizeof(double));
+    double* acc = (double*)malloc(n1 * 3 * sizeof(double));
+    for (long i = 0; i < N; ++i)
+        for (int k = 0; k < 3; ++k) {
+            gxt[3 * i + k] = gx_out[3 * i + k] + gv_out[3 * i + k] / dt;
+            gx[3 * i + k] = -gv_out[3 * i + k] / dt;
+        }
+    for (int it = total - 1; it >= 0; --it) {
+        int stab = it < n_stab;
+        const double* y = Y + (size_t)it * n1 * 3;
+        const double* xtp = XT + (size_t)it * n1 * 3;
+        const long* cn = CNT + (size_t)it * n1;
+        /* upstream of the averaged delta */
+        for (long i = 0; i < N; ++i)
+            for (int k = 0; k < 3; ++k) {
+                double up = stab ? gx[3 * i + k] + gxt[3 * i + k] : gxt[3 * i + k];
+                H[3 * i + k] = cn[i] > 0 ? up / (double)cn[i] : 0.0;
+            }
+        /* gradient w.r.t. the positions the pass evaluates on (y) and, in
+         * the solver, w.r.t. x through the friction */
+        memset(acc, 0, (size_t)N * 3 * sizeof(double));
+        double* accx = stab ? NULL : (double*)calloc(n1 * 3, sizeof(double));
+        for (long p = 0; p < np; ++p) {
+            long i = Pp[p].i, j = Pp[p].j;
+            double e[3] = {y[3 * j] - y[3 * i], y[3 * j + 1] - y[3 * i + 1], y[3 * j + 2] - y[3 * i + 2]};
+            double L = sqrt(dot3(e, e));
+            if (!(L < d0) || L == 0.0 || !(ws[i] + ws[j] > 0)) continue;
+            double W = ws[i] + ws[j], mi = ws[i] / W, mj = ws[j] / W, pen = d0 - L;
+            double u[3] = {e[0] / L, e[1] / L, e[2] / L};
+            const double* hi = H + 3 * i;
+            const double* hj = H + 3 * j;
+            m33 K;
+            m33_eye(&K, d0 / L - 1.0);
+            m33_outer_add(&K, -d0 / L, u, u);
+            /* c_i = -m_i pen u(e), c_j = m_j pen u(e), e = y_j - y_i */
+            double tvec[3] = {0, 0, 0};
+            m33_tmul_add(tvec, -mi, &K, hi);   /* (dc_i/de)^T h_i */
+            m33_tmul_add(tvec, mj, &K, hj);    /* (dc_j/de)^T h_j */
+            for (int k = 0; k < 3; ++k) {
+                acc[3 * j + k] += tvec[k];
+                acc[3 * i + k] -= tvec[k];
+            }
+            /* mass ratios: dc_i/dm_i = -pen u, dc_j/dm_j = pen u */
+            double pu_hi = pen * dot3(u, hi), pu_hj = pen * dot3(u, hj);
+            double dmi_dwi = ws[j] / (W * W), dmi_dwj = -ws[i] / (W * W);
+            gws[i] += -pu_hi * dmi_dwi + pu_hj * (-dmi_dwi);
+            gws[j] += -pu_hi * dmi_dwj + pu_hj * (-dmi_dwj);
+            if (!stab) {
+                double rel[3], F[3];
+                m33 Fr, Fe;
+                for (int k = 0; k < 3; ++k)
+                    rel[k] = (xtp[3 * i + k] - Xfix[3 * i + k]) - (xtp[3 * j + k] - Xfix[3 * j + k]);
+                double base = fmode == 1 ? pen : d0;
+                friction_jac(rel, e, 0, base * mu_s, base * mu_k, fmode == 1, mu_k, u, F, &Fr, &Fe);
+                /* c_i -= m_i F, c_j += m_j F; rel = (xt_i - x_i) - (xt_j - x_j) */
+                double hF[3] = {-mi * hi[0] + mj * hj[0], -mi * hi[1] + mj * hj[1], -mi * hi[2] + mj * hj[2]};
+                double grel[3] = {0, 0, 0}, ge[3] = {0, 0, 0};
+                m33_tmul_add(grel, 1.0, &Fr, hF);
+                m33_tmul_add(ge, 1.0, &Fe, hF);
+                for (int k = 0; k < 3; ++k) {
+                    acc[3 * i + k] += grel[k] - ge[k];
+                    acc[3 * j + k] += -grel[k] + ge[k];
+                    accx[3 * i + k] -= grel[k];
+                    accx[3 * j + k] += grel[k];
+                }
+                double Fh_i = dot3(F, hi), Fh_j = dot3(F, hj);
+                gws[i] += -Fh_i * dmi_dwi + Fh_j * (-dmi_dwi);
+                gws[j] += -Fh_i * dmi_dwj + Fh_j * (-dmi_dwj);
+            }
+        }
+        for (long i = 0; i < N; ++i) {
+            if (!(ws[i] > 0)) continue;
+            const double* hi = H + 3 * i;
+            for (int s = 0; s < n_sdf; ++s) {
+                const double* rec = sdf + OR_SDF_STRIDE * s;
+                double phi[OR_MAX_COMP], nn[3 * OR_MAX_COMP];
+                int tie;
+                int nc = or_sdf_eval(rec, y + 3 * i, phi, nn, &tie, 0.0);
+                double bmu_s = sqrt(mu_s * rec[16]), bmu_k = sqrt(mu_k * rec[17]);
+                for (int c = 0; c < nc; ++c) {
+                    if (!(phi[c] < r)) continue;
+                    const double* n = nn + 3 * c;
+                    double a = dot3(n, hi);       /* d((r - phi) n)/dy = -n n^T */
+                    for (int k = 0; k < 3; ++k) acc[3 * i + k] -= a * n[k];
+                    if (!stab) {
+                        double d[3], F[3];
+                        m33 Fr, Fe;
+                        double pen = r - phi[c];
+                        for (int k = 0; k < 3; ++k) d[k] = (xtp[3 * i + k] - Xfix[3 * i + k]) - rec[13 + k] * dt;
+                        double base = fmode == 1 ? pen : d0;
+                        friction_jac(d, n, 1, base * bmu_s, base * bmu_k, fmode == 1, bmu_k, n, F, &Fr, &Fe);
+                        double gd[3] = {0, 0, 0};
+                        m33_tmul_add(gd, -1.0, &Fr, hi);   /* c -= F(d) */
+                        for (int k = 0; k < 3; ++k) {
+                            acc[3 * i + k] += gd[k];
+                            accx[3 * i + k] -= gd[k];
+                        }
+                        if (fmode == 1) {          /* clipped F depends on y through pen */
+                            double Lp = sqrt(dot3(F, F));
+                            (void)Lp;
+                            m33 Fy;
+                            memset(&Fy, 0, sizeof Fy);
+                            double dd[3], perp[3];
+                            for (int k = 0; k < 3; ++k) dd[k] = d[k];
+                            double an = dot3(dd, n);
+                            for (int k = 0; k < 3; ++k) perp[k] = dd[k] - an * n[k];
+                            double Lq = sqrt(dot3(perp, perp));
+                            if (!(Lq < base * bmu_s) && Lq > 0 && base * bmu_k / Lq < 1.0) {
+                                /* F = pen mu_k perp/|perp|, dpen/dy = -n^T */
+                                double q = dot3(perp, hi) / Lq;
+                                for (int k = 0; k < 3; ++k) acc[3 * i + k] += q * bmu_k * n[k];
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (stab) {
+            for (long i = 0; i < N * 3; ++i) gx[i] += acc[i];
+        } else {
+            for (long i = 0; i < N * 3; ++i) {
+                gxt[i] += acc[i];
+                gx[i] += accx[i];
+            }
+            free(accx);
+        }
+    }
+    /* predict: xt = x + dt (v + dt g), w_i = inv_m e^{k (z - ground)} */
+    for (long i = 0; i < N; ++i) {
+        for (int k = 0; k < 3; ++k) {
+            gx0[3 * i + k] += gx[3 * i + k] + gxt[3 * i + k];
+            gv0[3 * i + k] += dt * gxt[3 * i + k];
+        }
+        gx0[3 * i + 2] += gws[i] * ws[i] * mass_k;
+    }
+    free(x); free(xt); free(ws); free(Y); free(XT); free(D); free(cnt); free(CNT); free(Pp); free(E); free(border);
+    free(Xfix); free(gxt); free(gx); free(gws); free(H); free(acc);
+    return 0;
+}

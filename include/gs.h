@@ -250,6 +250,43 @@ int gs_set_tuning(gs_ctx* ctx, int warps_per_block, int blocks_per_sm);
  * launch in microseconds.  Blocks. */
 int gs_autotune(gs_ctx* ctx, float dt, int reps, int* warps_per_block, int* blocks_per_sm, float* best_us);
 
+/* Differentiable pattern (not in the paper): one HR frame as a function of
+ * caller-owned device buffers, and its reverse mode.  Single-scene contexts
+ * only; the context is used as workspace and its LR and HR state are
+ * overwritten.  All arrays are float4 records in original order (w of
+ * positions is ignored on input, gradients have w = 0):
+ *   gs_upsample_forward:  (lr_pos, lr_vel [n_low], hr_pos_in, hr_vel_in
+ *                          [n_high]) -> hr_pos_out, hr_vel_out [n_high],
+ *                          the same map as gs_upsample (Sec. 4).
+ *   gs_upsample_backward: given dL/d hr_pos_out and dL/d hr_vel_out, writes
+ *                          dL/d lr_pos, dL/d lr_vel, dL/d hr_pos_in and
+ *                          dL/d hr_vel_in for the forward pass's branch
+ *                          decisions (blend case, LR particle of largest
+ *                          weight, SDF contacts); each SDF contact is
+ *                          differentiated with its normal held fixed, which
+ *                          is exact for planar walls.
+ * Outputs are overwritten, not accumulated.  Asynchronous. */
+int gs_upsample_forward(gs_ctx* ctx, const float* lr_pos, const float* lr_vel, const float* hr_pos_in,
+                        const float* hr_vel_in, float* hr_pos_out, float* hr_vel_out, float dt);
+int gs_upsample_backward(gs_ctx* ctx, const float* lr_pos, const float* lr_vel, const float* hr_pos_in,
+                         const float* hr_vel_in, const float* g_hr_pos_out, const float* g_hr_vel_out, float* g_lr_pos,
+                         float* g_lr_vel, float* g_hr_pos_in, float* g_hr_vel_in, float dt);
+
+/* One LR step (Algorithm 1, as gs_step_low) as a function of caller-owned
+ * device buffers, and its reverse mode (differentiable pattern; not in the
+ * paper).  x, v: float4[n_low] in original order (w of x is the inverse
+ * mass).  The context is used as workspace; its LR state is overwritten.
+ * gs_step_low_backward recomputes the step from (x_in, v_in) and, given
+ * dL/dx_out and dL/dv_out, writes dL/dx_in and dL/dv_in for the forward
+ * pass's branch decisions (contact sets, static / kinetic / clipped
+ * friction, SDF contacts with fixed normals), including the dependence of the
+ * height-scaled mass ratios on the start-of-step heights.  Outputs are
+ * overwritten.  Asynchronous. */
+int gs_step_low_forward(gs_ctx* ctx, const float* x_in, const float* v_in, float* x_out, float* v_out, float dt,
+                        int iters);
+int gs_step_low_backward(gs_ctx* ctx, const float* x_in, const float* v_in, const float* g_x_out, const float* g_v_out,
+                         float* g_x_in, float* g_v_in, float dt, int iters);
+
 /* Block until the context's stream is idle and report device-side errors. */
 int gs_sync(gs_ctx* ctx);
 

@@ -91,6 +91,10 @@ _SIGS = {
     "gs_set_tuning": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "gs_autotune": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
+    "gs_upsample_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_float]),
+    "gs_upsample_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_float]),
+    "gs_step_low_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int]),
+    "gs_step_low_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int]),
 }
 
 _lib = None
@@ -251,6 +255,24 @@ def gs_bin_points_static(pos4_ptr, n, grid, sorted_index_ptr, cell_start_ptr, st
     return lib().gs_bin_points_static(pos4_ptr, n, ctypes.byref(grid), sorted_index_ptr, cell_start_ptr, stream)
 
 
+def gs_upsample_forward(ctx, lr_pos, lr_vel, hr_pos_in, hr_vel_in, hr_pos_out, hr_vel_out, dt):
+    return lib().gs_upsample_forward(ctx, lr_pos, lr_vel, hr_pos_in, hr_vel_in, hr_pos_out, hr_vel_out, dt)
+
+
+def gs_upsample_backward(ctx, lr_pos, lr_vel, hr_pos_in, hr_vel_in, g_hr_pos_out, g_hr_vel_out, g_lr_pos, g_lr_vel,
+                         g_hr_pos_in, g_hr_vel_in, dt):
+    return lib().gs_upsample_backward(ctx, lr_pos, lr_vel, hr_pos_in, hr_vel_in, g_hr_pos_out, g_hr_vel_out,
+                                      g_lr_pos, g_lr_vel, g_hr_pos_in, g_hr_vel_in, dt)
+
+
+def gs_step_low_forward(ctx, x_in, v_in, x_out, v_out, dt, iters):
+    return lib().gs_step_low_forward(ctx, x_in, v_in, x_out, v_out, dt, iters)
+
+
+def gs_step_low_backward(ctx, x_in, v_in, g_x_out, g_v_out, g_x_in, g_v_in, dt, iters):
+    return lib().gs_step_low_backward(ctx, x_in, v_in, g_x_out, g_v_out, g_x_in, g_v_in, dt, iters)
+
+
 # ------------------------------------------------------------ marshalling ---
 def make_sdf(rec) -> gs_sdf:
     s = gs_sdf()
@@ -310,6 +332,13 @@ class Context:
     of them (one batched context; arrays are concatenated in scene order)."""
 
     def __init__(self, sc, stream=None, load_state=True, **overrides):
+        if isinstance(stream, str) and stream == "torch":
+            # torch's current stream; its legacy default stream has handle 0,
+            # which the C side would take as "create a stream", so pass the
+            # legacy-stream handle (1) instead
+            import torch
+            h = torch.cuda.current_stream().cuda_stream
+            stream = h if h else 1
         batch = isinstance(sc, (list, tuple))
         self.scene_list = list(sc) if batch else [sc]
         self._c_scenes = [make_scene(s, **overrides) for s in self.scene_list]

@@ -1,0 +1,510 @@
+// adjoint.cu -- reverse mode of the HR frame (Sec. 4) for the
+// differentiable pattern: gradients of a loss on the HR particles after one
+// frame with respect to the LR positions and velocities and the HR state
+// before the frame.
+//
+// One thread per HR particle recomputes the forward pass of its particle
+// (weights, blend case, the LR particle of largest weight, SDF contacts) and
+// then applies the chain rule backwards for those branch decisions:
+//   SDF steps (last first), normal held fixed:  g <- g - n (n . g)
+//   x' = x + dt v'        :  g_v' = g_v'' + dt g_x'',  g_x += g_x''
+//   v' = (1-a) vt + a (v + dt g):  g_vt = (1-a) g_v',  g_v = a g_v',
+//                                  g_a = g_v' . (v + dt g - vt)
+//   a = 1 - wmax (blend case)   :  g_wmax = -g_a
+//   vt = V / S                  :  g_V = g_vt / S,  g_S = -(g_vt . vt) / S
+//   w_j = (1 - |x - X_j|^2 / 9r^2)^3:
+//        g_w_j = g_S + g_V . V_j + [j = argmax] g_wmax
+//        g_X_j += g_w_j 6 t^2 (x - X_j) / 9r^2,  g_x -= the same,
+//        g_V_j += w_j g_V
+// LR gradients are summed in cell order with atomics and then scattered back
+// to the original LR order.
+#include <cuda_runtime.h>
+
+#include "gs_internal.cuh"
+#include "pbd_common.cuh"
+#include "sdf.cuh"
+
+namespace {
+
+__device__ __forceinline__ int cell_of(float x, float o, float inv_h, int dim)
+{
+    float a = __fmul_rn(__fsub_rn(x, o), inv_h);
+    float f = floorf(a);
+    if (!(f >= 0.0f)) return 0;
+    if (f >= (float)(dim - 1)) return dim - 1;
+    return (int)f;
+}
+
+constexpr int kMaxSteps = 32;
+
+__global__ void k_upsample_bwd(const SceneDev* __restrict__ scenes, const gs_sdf* __restrict__ sdf,
+                               const float4* __restrict__ lr_spos, const float4* __restrict__ lr_svel,
+                               const uint32_t* __restrict__ cell_start, const float4* __restrict__ hx,
+                               const float4* __restrict__ hv, const float4* __restrict__ gxo,
+                               const float4* __restrict__ gvo, float4* __restrict__ ghx, float4* __restrict__ ghv,
+                               float* __restrict__ gXs, float* __restrict__ gVs, int64_t m, float dt)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const SceneDev& sc = scenes[0];
+    const GridDev& g = sc.g;
+    const float4 p = hx[i], v = hv[i];
+    const float R = 3.0f * sc.r_low;
+    const float R2 = R * R;
+    const float inv9r2 = 1.0f / R2;
+    const int cx0 = cell_of(p.x - R, g.ox, g.inv_h, g.dx), cx1 = cell_of(p.x + R, g.ox, g.inv_h, g.dx);
+    const int cy0 = cell_of(p.y - R, g.oy, g.inv_h, g.dy), cy1 = cell_of(p.y + R, g.oy, g.inv_h, g.dy);
+    const int cz0 = cell_of(p.z - R, g.oz, g.inv_h, g.dz), cz1 = cell_of(p.z + R, g.oz, g.inv_h, g.dz);
+    // forward
+    float S = 0.f, Vx = 0.f, Vy = 0.f, Vz = 0.f, wmax = 0.f;
+    uint32_t jstar = 0xffffffffu;
+    for (int cz = cz0; cz <= cz1; ++cz)
+        for (int cy = cy0; cy <= cy1; ++cy) {
+            const int64_t row = (int64_t)sc.cell_off + ((int64_t)cz * g.dy + cy) * g.dx;
+            const uint32_t b = cell_start[row + cx0], e = cell_start[row + cx1 + 1];
+            for (uint32_t j = b; j < e; ++j) {
+                const float4 q = lr_spos[j];
+                const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+                const float d2 = dx * dx + dy * dy + dz * dz;
+                if (!(d2 < R2)) continue;
+                const float t = 1.0f - d2 * inv9r2;
+                const float w = t * t * t;
+                const float4 qv = lr_svel[j];
+                S += w;
+                Vx += w * qv.x;
+                Vy += w * qv.y;
+                Vz += w * qv.z;
+                if (w > wmax) {
+                    wmax = w;
+                    jstar = j;
+                }
+            }
+        }
+    float vtx = 0.f, vty = 0.f, vtz = 0.f;
+    if (S > 0.0f) {
+        vtx = Vx / S;
+        vty = Vy / S;
+        vtz = Vz / S;
+    }
+    const bool branch = (wmax <= sc.c1) || (S > 0.0f && wmax >= sc.c2 * S);
+    const float alpha = branch ? 1.0f - wmax : 0.0f;
+    const float bx = v.x + dt * sc.gx, by = v.y + dt * sc.gy, bz = v.z + dt * sc.gz;
+    float vpx = (1.0f - alpha) * vtx + alpha * bx, vpy = (1.0f - alpha) * vty + alpha * by,
+          vpz = (1.0f - alpha) * vtz + alpha * bz;
+    float xpx = p.x + dt * vpx, xpy = p.y + dt * vpy, xpz = p.z + dt * vpz;
+    float nx_[kMaxSteps], ny_[kMaxSteps], nz_[kMaxSteps];
+    bool vrem[kMaxSteps];
+    int n_steps = 0;
+    for (int s = 0; s < sc.n_sdf; ++s) {
+        const gs_sdf& bsdf = sdf[sc.sdf_begin + s];
+        const int nc = sdf_components(bsdf.kind);
+        for (int c = 0; c < nc; ++c) {
+            const SdfHit h = sdf_eval(bsdf, c, xpx, xpy, xpz);
+            if (!(h.phi < sc.r_high)) continue;
+            const float push = sc.r_high - h.phi;
+            xpx += push * h.nx;
+            xpy += push * h.ny;
+            xpz += push * h.nz;
+            const float vn = (vpx - bsdf.vel[0]) * h.nx + (vpy - bsdf.vel[1]) * h.ny + (vpz - bsdf.vel[2]) * h.nz;
+            if (vn < 0.0f) {
+                vpx -= vn * h.nx;
+                vpy -= vn * h.ny;
+                vpz -= vn * h.nz;
+            }
+            if (n_steps < kMaxSteps) {
+                nx_[n_steps] = h.nx;
+                ny_[n_steps] = h.ny;
+                nz_[n_steps] = h.nz;
+                vrem[n_steps] = vn < 0.0f;
+                ++n_steps;
+            }
+        }
+    }
+    // reverse
+    float4 go = gxo[i], gw = gvo[i];
+    float ax = go.x, ay = go.y, az = go.z, avx = gw.x, avy = gw.y, avz = gw.z;
+    for (int k = n_steps - 1; k >= 0; --k) {
+        if (vrem[k]) {
+            const float d = avx * nx_[k] + avy * ny_[k] + avz * nz_[k];
+            avx -= d * nx_[k];
+            avy -= d * ny_[k];
+            avz -= d * nz_[k];
+        }
+        const float d = ax * nx_[k] + ay * ny_[k] + az * nz_[k];
+        ax -= d * nx_[k];
+        ay -= d * ny_[k];
+        az -= d * nz_[k];
+    }
+    float gpx = ax, gpy = ay, gpz = az;   // dL/dx (HR input)
+    const float gvpx = avx + dt * ax, gvpy = avy + dt * ay, gvpz = avz + dt * az;
+    const float gvtx = (1.0f - alpha) * gvpx, gvty = (1.0f - alpha) * gvpy, gvtz = (1.0f - alpha) * gvpz;
+    const float galpha = gvpx * (bx - vtx) + gvpy * (by - vty) + gvpz * (bz - vtz);
+    const float gwmax = branch ? -galpha : 0.0f;
+    ghv[i] = make_float4(alpha * gvpx, alpha * gvpy, alpha * gvpz, 0.0f);
+    if (S > 0.0f) {
+        const float gVx = gvtx / S, gVy = gvty / S, gVz = gvtz / S;
+        const float gS = -(gvtx * vtx + gvty * vty + gvtz * vtz) / S;
+        for (int cz = cz0; cz <= cz1; ++cz)
+            for (int cy = cy0; cy <= cy1; ++cy) {
+                const int64_t row = (int64_t)sc.cell_off + ((int64_t)cz * g.dy + cy) * g.dx;
+                const uint32_t b = cell_start[row + cx0], e = cell_start[row + cx1 + 1];
+                for (uint32_t j = b; j < e; ++j) {
+                    const float4 q = lr_spos[j];
+                    const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+                    const float d2 = dx * dx + dy * dy + dz * dz;
+                    if (!(d2 < R2)) continue;
+                    const float t = 1.0f - d2 * inv9r2;
+                    const float w = t * t * t;
+                    const float4 qv = lr_svel[j];
+                    const float gwj = gS + gVx * qv.x + gVy * qv.y + gVz * qv.z + (j == jstar ? gwmax : 0.0f);
+                    const float k6 = gwj * 6.0f * t * t * inv9r2;
+                    atomicAdd(gXs + 4 * (int64_t)j + 0, k6 * dx);
+                    atomicAdd(gXs + 4 * (int64_t)j + 1, k6 * dy);
+                    atomicAdd(gXs + 4 * (int64_t)j + 2, k6 * dz);
+                    atomicAdd(gVs + 4 * (int64_t)j + 0, w * gVx);
+                    atomicAdd(gVs + 4 * (int64_t)j + 1, w * gVy);
+                    atomicAdd(gVs + 4 * (int64_t)j + 2, w * gVz);
+                    gpx -= k6 * dx;
+                    gpy -= k6 * dy;
+                    gpz -= k6 * dz;
+                }
+            }
+    }
+    ghx[i] = make_float4(gpx, gpy, gpz, 0.0f);
+}
+
+// out[idx[p]] = in[p] for both arrays
+__global__ void k_scatter2(const uint32_t* __restrict__ idx, const float4* __restrict__ a, const float4* __restrict__ b,
+                           float4* __restrict__ ao, float4* __restrict__ bo, int64_t n)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const uint32_t i = idx[p];
+    ao[i] = a[p];
+    bo[i] = b[p];
+}
+
+
+// ---------------------------------------------------------------------------
+// Reverse mode of one LR step (Algorithm 1) for the forward pass's branch
+// decisions.  Pair (p, q) evaluated on y (x in stabilization, xt in the
+// solver), e = y_q - y_p, L = |e|, u = e / L, pen = 2r - L, W = w_p + w_q:
+//   contact   c_p = -m_p pen u,  c_q = +m_q pen u,
+//             d(pen u)/de = (2r/L - 1) I - (2r/L) u u^T =: K
+//   friction  rel = (xt_p - x_p) - (xt_q - x_q),  c_p -= m_p F,  c_q += m_q F,
+//             F = s P rel (P = I - e e^T / e.e; s = 1 or thr_k / |P rel|)
+// A pass moves p by (sum c)/n_p; the reverse pass pushes h = g / n back
+// through every contribution that involves p (its own and its partners').
+struct M3 {
+    float a[9];
+};
+
+__device__ __forceinline__ void m3_eye(M3& A, float s)
+{
+#pragma unroll
+    for (int k = 0; k < 9; ++k) A.a[k] = 0.0f;
+    A.a[0] = A.a[4] = A.a[8] = s;
+}
+
+__device__ __forceinline__ void m3_outer_add(M3& A, float s, const float* u, const float* v)
+{
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) A.a[3 * r + c] += s * u[r] * v[c];
+}
+
+// out += s A^T h
+__device__ __forceinline__ void m3_tmul_add(float* out, float s, const M3& A, const float* h)
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[c] += s * (A.a[c] * h[0] + A.a[3 + c] * h[1] + A.a[6 + c] * h[2]);
+}
+
+__device__ __forceinline__ M3 m3_mul(const M3& A, const M3& B)
+{
+    M3 R;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            R.a[3 * r + c] = A.a[3 * r] * B.a[c] + A.a[3 * r + 1] * B.a[3 + c] + A.a[3 * r + 2] * B.a[6 + c];
+    return R;
+}
+
+// F and its Jacobians with respect to rel and e (e_is_normal: SDF, e = n).
+__device__ void fric_jac(const float* rel, const float* e, float ee, bool e_is_normal, float thr_s, float thr_k,
+                         bool mode1, float mu_k, const float* u, float* F, M3& Fr, M3& Fe)
+{
+    const Tangent tg = tangent_part(rel[0], rel[1], rel[2], e[0], e[1], e[2], ee);
+    const float perp[3] = {tg.tx, tg.ty, tg.tz};
+    M3 P, G;
+    m3_eye(P, 1.0f);
+    m3_outer_add(P, -1.0f / ee, e, e);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) G.a[k] = 0.0f;
+    if (!e_is_normal) {
+        const float re = rel[0] * e[0] + rel[1] * e[1] + rel[2] * e[2];
+        m3_outer_add(G, -1.0f / ee, e, rel);
+        G.a[0] -= re / ee;
+        G.a[4] -= re / ee;
+        G.a[8] -= re / ee;
+        m3_outer_add(G, 2.0f * re / (ee * ee), e, e);
+    }
+    const float Lp = tg.L;
+    const bool clipped = !(Lp < thr_s) && Lp > 0.0f && thr_k / Lp < 1.0f;
+    if (clipped) {
+        const float pu[3] = {perp[0] / Lp, perp[1] / Lp, perp[2] / Lp};
+        M3 Q;
+        m3_eye(Q, thr_k / Lp);
+        m3_outer_add(Q, -thr_k / Lp, pu, pu);
+        F[0] = thr_k * pu[0];
+        F[1] = thr_k * pu[1];
+        F[2] = thr_k * pu[2];
+        Fr = m3_mul(Q, P);
+        Fe = m3_mul(Q, G);
+        if (mode1) m3_outer_add(Fe, -mu_k, pu, u);
+    } else {
+        F[0] = perp[0];
+        F[1] = perp[1];
+        F[2] = perp[2];
+        Fr = P;
+        Fe = G;
+    }
+}
+
+__global__ void k_adj_init(int64_t n, const uint32_t* __restrict__ idx, const float4* __restrict__ gxo,
+                           const float4* __restrict__ gvo, float dt, float4* __restrict__ gx, float4* __restrict__ gxt,
+                           float* __restrict__ gws)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const uint32_t i = idx[p];
+    const float4 a = gxo[i], b = gvo[i];
+    gxt[p] = make_float4(a.x + b.x / dt, a.y + b.y / dt, a.z + b.z / dt, 0.0f);
+    gx[p] = make_float4(-b.x / dt, -b.y / dt, -b.z / dt, 0.0f);
+    gws[p] = 0.0f;
+}
+
+// h_p = upstream_p / n_p for one pass (n_p = active pair and SDF contacts)
+__global__ void k_adj_h(const PbdArgs a, int stab, const float4* __restrict__ Y, const float4* __restrict__ WS,
+                        const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ cnt,
+                        const float4* __restrict__ gx, const float4* __restrict__ gxt, float4* __restrict__ H)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.n) return;
+    const SceneDev& sc = a.scenes[a.lr_scene[p]];
+    const float d0 = 2.0f * sc.r_low;
+    const float4 yp = Y[p];
+    const float wp = WS[p].w;
+    int n_act = 0;
+    const int nc = (int)cnt[p];
+    for (int k = 0; k < nc; ++k) {
+        const uint32_t q = nbr[(int64_t)k * a.n + p];
+        const PairGeo g = pair_geo(yp, Y[q]);
+        if (!(g.d < d0) || g.d2 == 0.0f) continue;
+        if (!(wp + WS[q].w > 0.0f)) continue;
+        ++n_act;
+    }
+    if (wp > 0.0f)
+        for (int s = 0; s < sc.n_sdf; ++s) {
+            const gs_sdf& b = a.sdf[sc.sdf_begin + s];
+            const int ncomp = sdf_components(b.kind);
+            for (int c = 0; c < ncomp; ++c)
+                if (sdf_eval(b, c, yp.x, yp.y, yp.z).phi < sc.r_low) ++n_act;
+        }
+    float4 up = gxt[p];
+    if (stab) {
+        const float4 u2 = gx[p];
+        up.x += u2.x;
+        up.y += u2.y;
+        up.z += u2.z;
+    }
+    const float inv = n_act > 0 ? 1.0f / (float)n_act : 0.0f;
+    H[p] = make_float4(up.x * inv, up.y * inv, up.z * inv, 0.0f);
+}
+
+__global__ void k_adj_pass(const PbdArgs a, int stab, const float4* __restrict__ Y, const float4* __restrict__ XT,
+                           const float4* __restrict__ XF, const float4* __restrict__ WS,
+                           const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ cnt,
+                           const float4* __restrict__ H, float4* __restrict__ gx, float4* __restrict__ gxt,
+                           float* __restrict__ gws)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.n) return;
+    const SceneDev& sc = a.scenes[a.lr_scene[p]];
+    const float d0 = 2.0f * sc.r_low;
+    const float4 yp = Y[p];
+    const float wp = WS[p].w;
+    const float4 hp4 = H[p];
+    const float hp[3] = {hp4.x, hp4.y, hp4.z};
+    float acc[3] = {0.f, 0.f, 0.f}, accx[3] = {0.f, 0.f, 0.f}, gw = 0.0f;
+    const float4 xtp = XT[p], xfp = XF[p];
+    const int nc = (int)cnt[p];
+    for (int k = 0; k < nc; ++k) {
+        const uint32_t q = nbr[(int64_t)k * a.n + p];
+        const float4 yq = Y[q];
+        const PairGeo g = pair_geo(yp, yq);
+        if (!(g.d < d0) || g.d2 == 0.0f) continue;
+        const float wq = WS[q].w;
+        const float W = wp + wq;
+        if (!(W > 0.0f)) continue;
+        const float mp = wp / W, mq = wq / W, pen = d0 - g.d;
+        const float e[3] = {g.ex, g.ey, g.ez};
+        const float u[3] = {g.ex / g.d, g.ey / g.d, g.ez / g.d};
+        const float4 hq4 = H[q];
+        const float hq[3] = {hq4.x, hq4.y, hq4.z};
+        M3 K;
+        m3_eye(K, d0 / g.d - 1.0f);
+        m3_outer_add(K, -d0 / g.d, u, u);
+        float tv[3] = {0.f, 0.f, 0.f};
+        m3_tmul_add(tv, -mp, K, hp);
+        m3_tmul_add(tv, mq, K, hq);
+        acc[0] -= tv[0];
+        acc[1] -= tv[1];
+        acc[2] -= tv[2];
+        const float uh = u[0] * (hp[0] + hq[0]) + u[1] * (hp[1] + hq[1]) + u[2] * (hp[2] + hq[2]);
+        gw += -pen * (wq / (W * W)) * uh;
+        if (!stab) {
+            const float4 xtq = XT[q], xfq = XF[q];
+            const float rel[3] = {(xtp.x - xfp.x) - (xtq.x - xfq.x), (xtp.y - xfp.y) - (xtq.y - xfq.y),
+                                  (xtp.z - xfp.z) - (xtq.z - xfq.z)};
+            const float base = sc.friction_mode == 1 ? pen : d0;
+            float F[3];
+            M3 Fr, Fe;
+            fric_jac(rel, e, g.d2, false, base * sc.mu_s, base * sc.mu_k, sc.friction_mode == 1, sc.mu_k, u, F, Fr,
+                     Fe);
+            const float hF[3] = {-mp * hp[0] + mq * hq[0], -mp * hp[1] + mq * hq[1], -mp * hp[2] + mq * hq[2]};
+            float grel[3] = {0.f, 0.f, 0.f}, ge[3] = {0.f, 0.f, 0.f};
+            m3_tmul_add(grel, 1.0f, Fr, hF);
+            m3_tmul_add(ge, 1.0f, Fe, hF);
+#pragma unroll
+            for (int k2 = 0; k2 < 3; ++k2) {
+                acc[k2] += grel[k2] - ge[k2];
+                accx[k2] -= grel[k2];
+            }
+            const float Fh = F[0] * (hp[0] + hq[0]) + F[1] * (hp[1] + hq[1]) + F[2] * (hp[2] + hq[2]);
+            gw += -(wq / (W * W)) * Fh;
+        }
+    }
+    if (wp > 0.0f) {
+        for (int s = 0; s < sc.n_sdf; ++s) {
+            const gs_sdf& b = a.sdf[sc.sdf_begin + s];
+            const int ncomp = sdf_components(b.kind);
+            const float bmu_s = sqrtf(sc.mu_s * b.mu_s), bmu_k = sqrtf(sc.mu_k * b.mu_k);
+            for (int c = 0; c < ncomp; ++c) {
+                const SdfHit h = sdf_eval(b, c, yp.x, yp.y, yp.z);
+                if (!(h.phi < sc.r_low)) continue;
+                const float n[3] = {h.nx, h.ny, h.nz};
+                const float an = n[0] * hp[0] + n[1] * hp[1] + n[2] * hp[2];
+                acc[0] -= an * n[0];
+                acc[1] -= an * n[1];
+                acc[2] -= an * n[2];
+                if (!stab) {
+                    const float pen = sc.r_low - h.phi;
+                    const float dv[3] = {(xtp.x - xfp.x) - b.vel[0] * a.dt, (xtp.y - xfp.y) - b.vel[1] * a.dt,
+                                         (xtp.z - xfp.z) - b.vel[2] * a.dt};
+                    const float base = sc.friction_mode == 1 ? pen : d0;
+                    float F[3];
+                    M3 Fr, Fe;
+                    fric_jac(dv, n, 1.0f, true, base * bmu_s, base * bmu_k, false, bmu_k, n, F, Fr, Fe);
+                    float gd[3] = {0.f, 0.f, 0.f};
+                    m3_tmul_add(gd, -1.0f, Fr, hp);
+#pragma unroll
+                    for (int k2 = 0; k2 < 3; ++k2) {
+                        acc[k2] += gd[k2];
+                        accx[k2] -= gd[k2];
+                    }
+                    if (sc.friction_mode == 1) {
+                        const Tangent tg = tangent_part(dv[0], dv[1], dv[2], n[0], n[1], n[2], 1.0f);
+                        const float thr_s = base * bmu_s, thr_k = base * bmu_k;
+                        if (!(tg.L < thr_s) && tg.L > 0.0f && thr_k / tg.L < 1.0f) {
+                            const float q = (tg.tx * hp[0] + tg.ty * hp[1] + tg.tz * hp[2]) / tg.L;
+                            acc[0] += q * bmu_k * n[0];
+                            acc[1] += q * bmu_k * n[1];
+                            acc[2] += q * bmu_k * n[2];
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (stab) {
+        float4 v = gx[p];
+        gx[p] = make_float4(v.x + acc[0], v.y + acc[1], v.z + acc[2], 0.0f);
+    } else {
+        float4 v = gxt[p];
+        gxt[p] = make_float4(v.x + acc[0], v.y + acc[1], v.z + acc[2], 0.0f);
+        float4 w = gx[p];
+        gx[p] = make_float4(w.x + accx[0], w.y + accx[1], w.z + accx[2], 0.0f);
+    }
+    gws[p] += gw;
+}
+
+// predict: xt = x + dt (v + dt g), w = (1/m) e^{k (z - ground)}
+__global__ void k_adj_final(const PbdArgs a, const uint32_t* __restrict__ idx, const float4* __restrict__ WS,
+                            const float4* __restrict__ gx, const float4* __restrict__ gxt,
+                            const float* __restrict__ gws, float4* __restrict__ gx0, float4* __restrict__ gv0)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= a.n) return;
+    const SceneDev& sc = a.scenes[a.lr_scene[p]];
+    const uint32_t i = idx[p];
+    const float4 u = gx[p], t = gxt[p];
+    gx0[i] = make_float4(u.x + t.x, u.y + t.y, u.z + t.z + gws[p] * WS[p].w * sc.mass_k, 0.0f);
+    gv0[i] = make_float4(a.dt * t.x, a.dt * t.y, a.dt * t.z, 0.0f);
+}
+
+}  // namespace
+
+cudaError_t gs_launch_upsample_bwd(cudaStream_t s, const SceneDev* scenes, const gs_sdf* sdf, const float4* lr_spos,
+                                   const float4* lr_svel, const uint32_t* cell_start, const float4* hx,
+                                   const float4* hv, const float4* gxo, const float4* gvo, float4* ghx, float4* ghv,
+                                   float4* gXs, float4* gVs, int64_t m, float dt, int64_t* launches)
+{
+    if (m <= 0) return cudaSuccess;
+    k_upsample_bwd<<<gs_blocks(m, 128), 128, 0, s>>>(scenes, sdf, lr_spos, lr_svel, cell_start, hx, hv, gxo, gvo, ghx,
+                                                      ghv, reinterpret_cast<float*>(gXs),
+                                                      reinterpret_cast<float*>(gVs), m, dt);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_scatter2(cudaStream_t s, const uint32_t* idx, const float4* a, const float4* b, float4* ao,
+                               float4* bo, int64_t n, int64_t* launches)
+{
+    if (n <= 0) return cudaSuccess;
+    k_scatter2<<<gs_blocks(n, 256), 256, 0, s>>>(idx, a, b, ao, bo, n);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_adj_init(cudaStream_t s, int64_t n, const uint32_t* idx, const float4* gxo, const float4* gvo,
+                               float dt, float4* gx, float4* gxt, float* gws, int64_t* launches)
+{
+    if (n <= 0) return cudaSuccess;
+    k_adj_init<<<gs_blocks(n, 256), 256, 0, s>>>(n, idx, gxo, gvo, dt, gx, gxt, gws);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_adj_pass(cudaStream_t s, const PbdArgs& a, int stab, const float4* Y, const float4* XT,
+                               const float4* XF, const float4* WS, const uint32_t* nbr, const uint32_t* cnt, float4* H,
+                               float4* gx, float4* gxt, float* gws, int64_t* launches)
+{
+    if (a.n <= 0) return cudaSuccess;
+    k_adj_h<<<gs_blocks(a.n, 128), 128, 0, s>>>(a, stab, Y, WS, nbr, cnt, gx, gxt, H);
+    k_adj_pass<<<gs_blocks(a.n, 128), 128, 0, s>>>(a, stab, Y, XT, XF, WS, nbr, cnt, H, gx, gxt, gws);
+    *launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_adj_final(cudaStream_t s, const PbdArgs& a, const uint32_t* idx, const float4* WS,
+                                const float4* gx, const float4* gxt, const float* gws, float4* gx0, float4* gv0,
+                                int64_t* launches)
+{
+    if (a.n <= 0) return cudaSuccess;
+    k_adj_final<<<gs_blocks(a.n, 256), 256, 0, s>>>(a, idx, WS, gx, gxt, gws, gx0, gv0);
+    *launches += 1;
+    return cudaGetLastError();
+}

@@ -323,6 +323,8 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
         A(dalloc(&c->hr_vals[k], MS));
     }
     A(dalloc(&c->nbr, (size_t)N * c->nbr_cap));
+    A(dalloc(&c->gXs, N));
+    A(dalloc(&c->gVs, N));
     A(dalloc(&c->nbr_cnt, N));
     A(dalloc(&c->tmp4, std::max(NM, MR)));
     c->sort_hist_cap = std::max(gs_sort_hist_words(N), gs_sort_hist_words(MS));
@@ -539,7 +541,8 @@ void gs_destroy(gs_ctx* c)
                     c->lr_svel,    c->lr_xt,      c->s_xt[0],    c->s_xt[1],    c->s_x[0],    c->s_x[1],
                     c->hr_pos[0],  c->hr_pos[1],  c->hr_vel[0],  c->hr_vel[1],  c->hr_keys[0], c->hr_keys[1],
                     c->hr_vals[0], c->hr_vals[1], c->nbr,        c->nbr_cnt,    c->tmp4,      c->sort_hist,
-                    c->d_work,     c->d_err};
+                    c->d_work,     c->d_err,      c->gXs,        c->gVs,       c->snap,      c->snap_xt,
+                    c->adj_gx,     c->adj_gxt,    c->adj_h,      c->adj_gws};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->h_err) cudaFreeHost(c->h_err);
@@ -868,6 +871,171 @@ int gs_autotune(gs_ctx* c, float dt, int reps, int* warps_per_block, int* blocks
     if (warps_per_block) *warps_per_block = bw;
     if (blocks_per_sm) *blocks_per_sm = bb;
     if (best_us) *best_us = best;
+    return GS_OK;
+}
+
+int gs_upsample_forward(gs_ctx* c, const float* lr_pos, const float* lr_vel, const float* hr_pos_in,
+                        const float* hr_vel_in, float* hr_pos_out, float* hr_vel_out, float dt)
+{
+    int st = check_state(c);
+    if (st) return st;
+    if (c->n_scenes != 1) return fail(c, GS_ERR_STATE, "the functional frame needs a single-scene context");
+    if (!(dt > 0.0f) || !std::isfinite(dt)) return fail(c, GS_ERR_ARG, "invalid dt %g", (double)dt);
+    const int64_t N = c->n_low, M = c->n_high;
+    if ((N > 0 && (!lr_pos || !lr_vel)) || (M > 0 && (!hr_pos_in || !hr_vel_in || !hr_pos_out || !hr_vel_out)))
+        return fail(c, GS_ERR_ARG, "null buffer");
+    if (N) {
+        CK(cudaMemcpyAsync(c->lr_pos, lr_pos, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+        CK(cudaMemcpyAsync(c->lr_vel, lr_vel, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    }
+    c->lr_binned = false;
+    if (M == 0) return GS_OK;
+    int cur = c->hr_cur;
+    CK(cudaMemcpyAsync(c->tmp4, hr_pos_in, M * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    CK(launch_hr_load(c, c->tmp4, c->hr_pos[cur], 1), "load");
+    CK(cudaMemcpyAsync(c->tmp4, hr_vel_in, M * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    CK(launch_hr_load(c, c->tmp4, c->hr_vel[cur], 0), "load");
+    c->hr_identity = true;
+    st = resort_high_impl(c);
+    if (st) return st;
+    st = bin_low_impl(c);
+    if (st) return st;
+    cur = c->hr_cur;
+    UpsampleArgs u = upsample_args(c, dt, c->hr_pos[cur], c->hr_vel[cur], c->hr_pos[cur], c->hr_vel[cur]);
+    CK(gs_launch_upsample(c->stream, u, c->tune_warps, c->tune_blocks_per_sm, c->sm_count, &c->launches), "upsample");
+    CK(gs_launch_unpermute(c->stream, c->hr_pos[cur], c->hr_pos[cur], c->hr_scene, (float4*)hr_pos_out, c->hr_slots,
+                           M, c->d_err, &c->launches),
+       "unpermute");
+    CK(gs_launch_unpermute(c->stream, c->hr_pos[cur], c->hr_vel[cur], c->hr_scene, (float4*)hr_vel_out, c->hr_slots,
+                           M, c->d_err, &c->launches),
+       "unpermute");
+    return GS_OK;
+}
+
+int gs_upsample_backward(gs_ctx* c, const float* lr_pos, const float* lr_vel, const float* hr_pos_in,
+                         const float* hr_vel_in, const float* g_hr_pos_out, const float* g_hr_vel_out, float* g_lr_pos,
+                         float* g_lr_vel, float* g_hr_pos_in, float* g_hr_vel_in, float dt)
+{
+    int st = check_state(c);
+    if (st) return st;
+    if (c->n_scenes != 1) return fail(c, GS_ERR_STATE, "the functional frame needs a single-scene context");
+    if (!(dt > 0.0f) || !std::isfinite(dt)) return fail(c, GS_ERR_ARG, "invalid dt %g", (double)dt);
+    const int64_t N = c->n_low, M = c->n_high;
+    if ((N > 0 && (!lr_pos || !lr_vel || !g_lr_pos || !g_lr_vel)) ||
+        (M > 0 && (!hr_pos_in || !hr_vel_in || !g_hr_pos_out || !g_hr_vel_out || !g_hr_pos_in || !g_hr_vel_in)))
+        return fail(c, GS_ERR_ARG, "null buffer");
+    if (N) {
+        CK(cudaMemcpyAsync(c->lr_pos, lr_pos, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+        CK(cudaMemcpyAsync(c->lr_vel, lr_vel, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+        CK(cudaMemsetAsync(c->gXs, 0, N * sizeof(float4), c->stream), "clear");
+        CK(cudaMemsetAsync(c->gVs, 0, N * sizeof(float4), c->stream), "clear");
+    }
+    st = bin_low_impl(c);
+    if (st) return st;
+    CK(gs_launch_upsample_bwd(c->stream, c->d_scenes, c->d_sdf, c->lr_spos, c->lr_svel, c->lr_cell_start,
+                              (const float4*)hr_pos_in, (const float4*)hr_vel_in, (const float4*)g_hr_pos_out,
+                              (const float4*)g_hr_vel_out, (float4*)g_hr_pos_in, (float4*)g_hr_vel_in, c->gXs, c->gVs,
+                              M, dt, &c->launches),
+       "upsample backward");
+    CK(gs_launch_scatter2(c->stream, c->lr_sorted_idx, c->gXs, c->gVs, (float4*)g_lr_pos, (float4*)g_lr_vel, N,
+                          &c->launches),
+       "scatter");
+    return GS_OK;
+}
+
+int gs_step_low_forward(gs_ctx* c, const float* x_in, const float* v_in, float* x_out, float* v_out, float dt,
+                        int iters)
+{
+    int st = check_state(c);
+    if (st) return st;
+    if (!(dt > 0.0f) || !std::isfinite(dt) || iters < 0 || iters > 1000)
+        return fail(c, GS_ERR_ARG, "invalid dt %g or iters %d", (double)dt, iters);
+    const int64_t N = c->n_low;
+    if (N == 0) return GS_OK;
+    if (!x_in || !v_in || !x_out || !v_out) return fail(c, GS_ERR_ARG, "null buffer");
+    CK(cudaMemcpyAsync(c->lr_pos, x_in, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    CK(cudaMemcpyAsync(c->lr_vel, v_in, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    st = step_low_impl(c, dt, iters);
+    if (st) return st;
+    CK(cudaMemcpyAsync(x_out, c->lr_pos, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    CK(cudaMemcpyAsync(v_out, c->lr_vel, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    return GS_OK;
+}
+
+int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const float* g_x_out, const float* g_v_out,
+                         float* g_x_in, float* g_v_in, float dt, int iters)
+{
+    int st = check_state(c);
+    if (st) return st;
+    if (!(dt > 0.0f) || !std::isfinite(dt) || iters < 0 || iters > 1000)
+        return fail(c, GS_ERR_ARG, "invalid dt %g or iters %d", (double)dt, iters);
+    const int64_t N = c->n_low;
+    if (N == 0) return GS_OK;
+    if (!x_in || !v_in || !g_x_out || !g_v_out || !g_x_in || !g_v_in) return fail(c, GS_ERR_ARG, "null buffer");
+    const int total = c->n_stab + iters;
+    if (total > c->snap_cap) {
+        if (c->snap) cudaFree(c->snap);
+        if (c->snap_xt) cudaFree(c->snap_xt);
+        c->snap = c->snap_xt = nullptr;
+        c->snap_cap = 0;
+        if (dalloc(&c->snap, (size_t)(total + 1) * N) != cudaSuccess ||
+            dalloc(&c->snap_xt, (size_t)(total + 1) * N) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, GS_ERR_OOM, "no memory for the reverse-mode snapshots");
+        }
+        c->snap_cap = total;
+    }
+    if (!c->adj_gx) {
+        bool ok = dalloc(&c->adj_gx, N) == cudaSuccess && dalloc(&c->adj_gxt, N) == cudaSuccess &&
+                  dalloc(&c->adj_h, N) == cudaSuccess && dalloc(&c->adj_gws, N) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return fail(c, GS_ERR_OOM, "no memory for the reverse-mode buffers");
+        }
+    }
+    // forward again, keeping what every pass evaluates on
+    CK(cudaMemcpyAsync(c->lr_pos, x_in, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    CK(cudaMemcpyAsync(c->lr_vel, v_in, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    PbdArgs a = pbd_args(c, dt);
+    CK(gs_launch_predict(c->stream, a, c->lr_pos, c->lr_vel, c->lr_xt, &c->launches), "predict");
+    st = bin_low_at(c, c->lr_xt);
+    if (st) return st;
+    CK(gs_launch_step_gather(c->stream, N, c->lr_sorted_idx, c->lr_xt, c->lr_pos, c->s_xt[0], c->s_x[0],
+                             &c->launches),
+       "gather");
+    CK(gs_launch_neighbors(c->stream, a, c->s_xt[0], c->lr_sorted_keys, c->lr_cell_start, c->nbr, c->nbr_cnt,
+                           c->nbr_cap, c->d_err, &c->launches),
+       "neighbours");
+    int bx = 0, bt = 0;
+    for (int it = 0; it < total; ++it) {
+        const int stab = it < c->n_stab;
+        CK(cudaMemcpyAsync(c->snap + (size_t)it * N, stab ? c->s_x[bx] : c->s_xt[bt], N * sizeof(float4),
+                           cudaMemcpyDeviceToDevice, c->stream),
+           "snapshot");
+        CK(cudaMemcpyAsync(c->snap_xt + (size_t)it * N, c->s_xt[bt], N * sizeof(float4), cudaMemcpyDeviceToDevice,
+                           c->stream),
+           "snapshot");
+        CK(gs_launch_pass(c->stream, a, stab, c->s_x[bx], c->s_xt[bt], c->s_x[bx ^ 1], c->s_xt[bt ^ 1], c->nbr,
+                          c->nbr_cnt, &c->launches),
+           "pass");
+        bt ^= 1;
+        if (stab) bx ^= 1;
+    }
+    const float4* xfix = c->s_x[bx];          // x after stabilization
+    const float4* ws = c->s_xt[0];            // w of xt carries the inverse scaled mass
+    CK(gs_launch_adj_init(c->stream, N, c->lr_sorted_idx, (const float4*)g_x_out, (const float4*)g_v_out, dt,
+                          c->adj_gx, c->adj_gxt, c->adj_gws, &c->launches),
+       "reverse init");
+    for (int it = total - 1; it >= 0; --it) {
+        const int stab = it < c->n_stab;
+        CK(gs_launch_adj_pass(c->stream, a, stab, c->snap + (size_t)it * N, c->snap_xt + (size_t)it * N, xfix, ws,
+                              c->nbr, c->nbr_cnt, c->adj_h, c->adj_gx, c->adj_gxt, c->adj_gws, &c->launches),
+           "reverse pass");
+    }
+    CK(gs_launch_adj_final(c->stream, a, c->lr_sorted_idx, ws, c->adj_gx, c->adj_gxt, c->adj_gws, (float4*)g_x_in,
+                           (float4*)g_v_in, &c->launches),
+       "reverse predict");
+    c->lr_binned = false;
     return GS_OK;
 }
 

@@ -113,6 +113,18 @@ struct gs_ctx {
     bool hr_keys_valid = false;
     float4* tmp4 = nullptr;                       // staging for reads / writes
 
+    // reverse-mode scratch: LR gradients in cell order
+    float4* gXs = nullptr;
+    float4* gVs = nullptr;
+    // LR-step reverse mode: per-pass snapshots (allocated on first use)
+    float4* snap = nullptr;        // [n_pass_cap][n_low] positions each pass evaluates on
+    float4* snap_xt = nullptr;     // [n_pass_cap][n_low] xt at each pass input
+    int snap_cap = 0;
+    float4* adj_gx = nullptr;
+    float4* adj_gxt = nullptr;
+    float4* adj_h = nullptr;
+    float* adj_gws = nullptr;
+
     // radix sort histogram scratch
     uint32_t* sort_hist = nullptr;
     size_t sort_hist_cap = 0;
@@ -210,6 +222,22 @@ cudaError_t gs_launch_pass(cudaStream_t s, const PbdArgs& a, int stab, const flo
                            int64_t* launches);
 cudaError_t gs_launch_finalize(cudaStream_t s, const PbdArgs& a, const uint32_t* idx, const float4* s_x,
                                const float4* s_xt, float4* pos, float4* vel, int64_t* launches);
+
+// adjoint.cu
+cudaError_t gs_launch_upsample_bwd(cudaStream_t s, const SceneDev* scenes, const gs_sdf* sdf, const float4* lr_spos,
+                                   const float4* lr_svel, const uint32_t* cell_start, const float4* hx,
+                                   const float4* hv, const float4* gxo, const float4* gvo, float4* ghx, float4* ghv,
+                                   float4* gXs, float4* gVs, int64_t m, float dt, int64_t* launches);
+cudaError_t gs_launch_scatter2(cudaStream_t s, const uint32_t* idx, const float4* a, const float4* b, float4* ao,
+                               float4* bo, int64_t n, int64_t* launches);
+cudaError_t gs_launch_adj_init(cudaStream_t s, int64_t n, const uint32_t* idx, const float4* gxo, const float4* gvo,
+                               float dt, float4* gx, float4* gxt, float* gws, int64_t* launches);
+cudaError_t gs_launch_adj_pass(cudaStream_t s, const PbdArgs& a, int stab, const float4* Y, const float4* XT,
+                               const float4* XF, const float4* WS, const uint32_t* nbr, const uint32_t* cnt, float4* H,
+                               float4* gx, float4* gxt, float* gws, int64_t* launches);
+cudaError_t gs_launch_adj_final(cudaStream_t s, const PbdArgs& a, const uint32_t* idx, const float4* WS,
+                                const float4* gx, const float4* gxt, const float* gws, float4* gx0, float4* gv0,
+                                int64_t* launches);
 
 // Grid-stride helper: blocks for n threads of `threads` each, capped.
 inline unsigned gs_blocks(int64_t n, int threads)

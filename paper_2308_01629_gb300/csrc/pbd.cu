@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include "gs_internal.cuh"
+#include "pbd_common.cuh"
 #include "sdf.cuh"
 
 namespace {
@@ -86,13 +87,6 @@ __global__ void k_neighbors(const PbdArgs a, const float4* __restrict__ s_xt, co
     cnt[p] = (uint32_t)k;
 }
 
-// Eqs. 3-4 friction delta for a tangential relative displacement (px,py,pz).
-__device__ __forceinline__ float friction_scale(float L, float thr_s, float thr_k)
-{
-    if (L < thr_s) return 1.0f;
-    return (L > 0.0f && thr_k / L < 1.0f) ? thr_k / L : 1.0f;
-}
-
 // kLanes lanes share one particle: lane `sub` takes candidates sub, sub +
 // kLanes, ...; the partial sums are added with shuffles in a fixed order, and
 // lane 0 adds the SDF contacts and writes the particle.
@@ -126,9 +120,8 @@ __global__ void __launch_bounds__(128) k_pass(const PbdArgs a, int stab, const f
         const float4 xtq = xt_in[q];
         const float4 xq = x_in[q];
         const float4 yq = stab ? xq : xtq;
-        const float ex = yq.x - yp.x, ey = yq.y - yp.y, ez = yq.z - yp.z;
-        const float d2 = ex * ex + ey * ey + ez * ez;
-        const float d = sqrtf(d2);
+        const PairGeo pg = pair_geo(yp, yq);
+        const float ex = pg.ex, ey = pg.ey, ez = pg.ez, d2 = pg.d2, d = pg.d;
         if (!(d < d0) || d2 == 0.0f) continue;
         const float wsum = wp + xtq.w;
         if (!(wsum > 0.0f)) continue;
@@ -140,14 +133,12 @@ __global__ void __launch_bounds__(128) k_pass(const PbdArgs a, int stab, const f
         Dz -= s * ez;
         if (!stab) {
             const float rx = dpx - (xtq.x - xq.x), ry = dpy - (xtq.y - xq.y), rz = dpz - (xtq.z - xq.z);
-            const float al = (rx * ex + ry * ey + rz * ez) / d2;
-            const float tx = rx - al * ex, ty = ry - al * ey, tz = rz - al * ez;
-            const float L = sqrtf(tx * tx + ty * ty + tz * tz);
+            const Tangent tg = tangent_part(rx, ry, rz, ex, ey, ez, d2);
             const float base = sc.friction_mode == 1 ? pen : d0;
-            const float f = m * friction_scale(L, base * sc.mu_s, base * sc.mu_k);
-            Dx -= f * tx;
-            Dy -= f * ty;
-            Dz -= f * tz;
+            const float f = m * friction_scale(tg.L, base * sc.mu_s, base * sc.mu_k);
+            Dx -= f * tg.tx;
+            Dy -= f * tg.ty;
+            Dz -= f * tg.tz;
         }
         ++n_act;
     }
@@ -173,14 +164,12 @@ __global__ void __launch_bounds__(128) k_pass(const PbdArgs a, int stab, const f
                 Dz += pen * h.nz;
                 if (!stab) {
                     const float rx = dpx - b.vel[0] * a.dt, ry = dpy - b.vel[1] * a.dt, rz = dpz - b.vel[2] * a.dt;
-                    const float al = rx * h.nx + ry * h.ny + rz * h.nz;
-                    const float tx = rx - al * h.nx, ty = ry - al * h.ny, tz = rz - al * h.nz;
-                    const float L = sqrtf(tx * tx + ty * ty + tz * tz);
+                    const Tangent tg = tangent_part(rx, ry, rz, h.nx, h.ny, h.nz, 1.0f);
                     const float base = sc.friction_mode == 1 ? pen : d0;
-                    const float f = friction_scale(L, base * bmu_s, base * bmu_k);
-                    Dx -= f * tx;
-                    Dy -= f * ty;
-                    Dz -= f * tz;
+                    const float f = friction_scale(tg.L, base * bmu_s, base * bmu_k);
+                    Dx -= f * tg.tx;
+                    Dy -= f * tg.ty;
+                    Dz -= f * tg.tz;
                 }
                 ++n_act;
             }

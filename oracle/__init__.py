@@ -77,6 +77,12 @@ def _L():
         L.or_upsample_vjp.restype = ctypes.c_int
         L.or_pbd_step_vjp.argtypes = [P, P, P, ctypes.c_long, P, ctypes.c_int, P, P, P, P, P]
         L.or_pbd_step_vjp.restype = ctypes.c_int
+        L.or_upsample_tape.argtypes = [P, P, ctypes.c_long, P, P, ctypes.c_long, P, ctypes.c_int, P, ctypes.c_int,
+                                       P, P, P]
+        L.or_upsample_tape.restype = ctypes.c_int
+        L.or_pbd_step_tape.argtypes = [P, P, P, ctypes.c_long, P, ctypes.c_int, P, ctypes.c_int, P, ctypes.c_long,
+                                       P]
+        L.or_pbd_step_tape.restype = ctypes.c_int
         L.or_pairs_within_grid.argtypes = L.or_pairs_within.argtypes
         L.or_pairs_within_grid.restype = ctypes.c_long
         _lib = L
@@ -227,6 +233,99 @@ def pbd_step_vjp(x, v, inv_m, sdf, prm, gx, gv):
     if rc != 0:
         raise RuntimeError("or_pbd_step_vjp failed")
     return ox, ov
+
+
+# ------------------------------------------------------- decision tapes ---
+# The method is piecewise smooth (blend branch, largest weight, contact
+# activation, static/kinetic friction, SDF active set).  A tape records the
+# decisions of one evaluation; replaying it evaluates the recorded branch of
+# every decision, i.e. the smooth piece that contains the recording point,
+# whose derivative the reverse modes compute.
+TAPE_RECORD, TAPE_REPLAY = 1, 2
+
+
+def upsample_tape(lr_x, lr_v, hr_x, hr_v, sdf, prm, tape=None):
+    """One HR frame (Sec. 4) recording its decisions (tape None) or replaying
+    them.  Returns (x, v, tape)."""
+    lr_x, lr_v = _f64(lr_x, 3), _f64(lr_v, 3)
+    hr_x, hr_v = _f64(hr_x, 3), _f64(hr_v, 3)
+    sdf = _f64(sdf, SDF_STRIDE) if sdf is not None and len(sdf) else np.zeros((0, SDF_STRIDE))
+    mode = TAPE_REPLAY if tape is not None else TAPE_RECORD
+    if tape is None:
+        tape = np.zeros((len(hr_x), 4), np.uint32)
+    elif tape.shape != (len(hr_x), 4):
+        raise ValueError("tape does not match the HR count")
+    ox, ov = np.zeros_like(hr_x), np.zeros_like(hr_v)
+    rc = _L().or_upsample_tape(_ptr(lr_x), _ptr(lr_v), len(lr_x), _ptr(hr_x), _ptr(hr_v), len(hr_x), _ptr(sdf),
+                               len(sdf), _ptr(_prm(prm, UP_KEYS)), mode, _ptr(tape), _ptr(ox), _ptr(ov))
+    if rc != 0:
+        raise RuntimeError(f"or_upsample_tape failed ({rc})")
+    return ox, ov, tape
+
+
+def pbd_step_tape(x, v, inv_m, sdf, prm, tape=None):
+    """One LR step (Algorithm 1) recording its decisions (tape None) or
+    replaying them.  Returns (x, v, tape)."""
+    x0, v0 = _f64(x, 3), _f64(v, 3)
+    inv_m = _f64(inv_m)
+    sdf = _f64(sdf, SDF_STRIDE) if sdf is not None and len(sdf) else np.zeros((0, SDF_STRIDE))
+    p = _prm(prm, PB_KEYS)
+    mode = TAPE_REPLAY if tape is not None else TAPE_RECORD
+    buf = tape if tape is not None else np.zeros(32 + 64 * len(x0) * 8, np.uint8)
+    need = ctypes.c_long(0)
+    while True:
+        xo, vo = x0.copy(), v0.copy()
+        rc = _L().or_pbd_step_tape(_ptr(xo), _ptr(vo), _ptr(inv_m), len(xo), _ptr(sdf), len(sdf), _ptr(p), mode,
+                                   _ptr(buf), buf.size, ctypes.byref(need))
+        if rc == -3 and mode == TAPE_RECORD and need.value > buf.size:
+            buf = np.zeros(need.value, np.uint8)
+            continue
+        if rc != 0:
+            raise RuntimeError(f"or_pbd_step_tape failed ({rc})")
+        break
+    return xo, vo, (buf[:need.value].copy() if mode == TAPE_RECORD else buf)
+
+
+def rollout(lr_x, lr_v, inv_m, hr_x, hr_v, sdf, pb, up, frames, n_sub=1, tapes=None):
+    """`frames` frames of the two-level method: per frame n_sub LR steps of
+    Algorithm 1 (parameters pb, pb["dt"] each), then one HR frame of Sec. 4
+    (parameters up) driven by the new LR state.  Decisions are recorded
+    (tapes None) or replayed from the tapes of an earlier call.  Returns a
+    dict with the final state, the per-operation inputs (for rollout_vjp)
+    and the tapes."""
+    X, V, x, v = _f64(lr_x, 3), _f64(lr_v, 3), _f64(hr_x, 3), _f64(hr_v, 3)
+    ops, out_tapes = [], []
+    k = 0
+    for _ in range(frames):
+        for _ in range(n_sub):
+            ops.append(("lr", X, V))
+            X, V, t = pbd_step_tape(X, V, inv_m, sdf, pb, None if tapes is None else tapes[k])
+            out_tapes.append(t)
+            k += 1
+        ops.append(("hr", X, V, x, v))
+        x, v, t = upsample_tape(X, V, x, v, sdf, up, None if tapes is None else tapes[k])
+        out_tapes.append(t)
+        k += 1
+    return dict(lr_x=X, lr_v=V, hr_x=x, hr_v=v, ops=ops, tapes=out_tapes)
+
+
+def rollout_vjp(ro, inv_m, sdf, pb, up, g_hr_x, g_hr_v, g_lr_x=None, g_lr_v=None):
+    """Reverse mode of ``rollout`` by the chain rule over its operations, last
+    first (``pbd_step_vjp`` and ``upsample_vjp`` at the recorded inputs).
+    Returns (dL/dlr_x, dL/dlr_v, dL/dhr_x, dL/dhr_v) at the initial state."""
+    a, b = _f64(g_hr_x, 3).copy(), _f64(g_hr_v, 3).copy()
+    GX = np.zeros_like(ro["lr_x"]) if g_lr_x is None else _f64(g_lr_x, 3).copy()
+    GV = np.zeros_like(ro["lr_v"]) if g_lr_v is None else _f64(g_lr_v, 3).copy()
+    for op in reversed(ro["ops"]):
+        if op[0] == "hr":
+            _, X, V, x, v = op
+            gX, gV, a, b = upsample_vjp(X, V, x, v, sdf, up, a, b)
+            GX += gX
+            GV += gV
+        else:
+            _, X, V = op
+            GX, GV = pbd_step_vjp(X, V, inv_m, sdf, pb, GX, GV)
+    return GX, GV, a, b
 
 
 def pairs_within(a, b, R, use_grid=False):

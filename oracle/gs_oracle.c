@@ -326,6 +326,16 @@ double or_weight(double d2, double r_low)
     return w > 0 ? w : 0.0;
 }
 
+/* Decision tapes.  The method is piecewise smooth: the blend branch, the
+ * largest weight, contact activation, static or kinetic friction and the
+ * SDF active set switch discontinuously.  A tape records these decisions in
+ * one evaluation (tape mode 1) and imposes them in another (mode 2), which
+ * then evaluates the formula of each recorded branch even where the
+ * comparison would now go the other way.  The replayed map is the smooth
+ * piece that contains the recording point; its derivative is the one the
+ * reverse modes compute, so finite differences of replays check them. */
+enum { TAPE_OFF = 0, TAPE_RECORD = 1, TAPE_REPLAY = 2 };
+
 /* Advection and boundary handling of one HR particle after the blend
  * parameter alpha is known (Sec. 4):
  *   v^{t+1} = (1 - alpha) vtilde + alpha (v^t + dt g),
@@ -340,7 +350,8 @@ double or_weight(double d2, double r_low)
  * branch).  Ambiguous contact decisions are appended to amb[]. */
 static void hr_finish(const double* x0, const double* v0, const double* vt, double alpha,
                       const double* sdf, int n_sdf, const double* prm, int flip_k,
-                      double* xo, double* vo, int* amb, int* n_amb, int* hard, int* n_act)
+                      double* xo, double* vo, int* amb, int* n_amb, int* hard, int* n_act,
+                      int tmode, uint32_t* tp)
 {
     double dt = prm[UP_DT], rh = prm[UP_R_HIGH], eps_x = prm[UP_EPS_X];
     const double g[3] = {prm[UP_GX], prm[UP_GY], prm[UP_GZ]};
@@ -361,6 +372,10 @@ static void hr_finish(const double* x0, const double* v0, const double* vt, doub
             int active = phi[c] < rh;
             if (fabs(phi[c] - rh) <= eps_x) amb[(*n_amb)++] = dec;
             if (dec == flip_k) active = !active;
+            /* tape words: tp[0] bit dec = component active, tp[1] bit dec =
+             * normal velocity removed */
+            if (tmode == TAPE_REPLAY) active = (tp[0] >> dec) & 1u;
+            else if (tmode == TAPE_RECORD && active) tp[0] |= 1u << dec;
             if (!active) continue;
             if (tie) *hard = 1;
             if (n_act) ++*n_act;
@@ -369,7 +384,10 @@ static void hr_finish(const double* x0, const double* v0, const double* vt, doub
             for (int k = 0; k < 3; ++k) xo[k] += push * n[k];
             double vr[3] = {vo[0] - ub[0], vo[1] - ub[1], vo[2] - ub[2]};
             double vn = dot3(vr, n);
-            if (vn < 0)
+            int rem = vn < 0;
+            if (tmode == TAPE_REPLAY) rem = (tp[1] >> dec) & 1u;
+            else if (tmode == TAPE_RECORD && rem) tp[1] |= 1u << dec;
+            if (rem)
                 for (int k = 0; k < 3; ++k) vo[k] -= vn * n[k];
         }
     }
@@ -387,11 +405,12 @@ static void hr_finish(const double* x0, const double* v0, const double* vt, doub
  * diag (optional, 6 per output): sum w, max w, alpha, #LR with w > 0, and
  * the sensitivities |d x_out / d x_in| - 1 and |d v_out / d x_in| of the SDF
  * rule (0 without an active contact). */
-int or_upsample(const double* lr_x, const double* lr_v, long N,
-                const double* hr_x, const double* hr_v, long M,
-                const long* sub, long n_sub,
-                const double* sdf, int n_sdf, const double* prm, int mode,
-                double* out_x, double* out_v, int* flag, double* alt_x, double* alt_v, double* diag)
+static int upsample_impl(const double* lr_x, const double* lr_v, long N,
+                         const double* hr_x, const double* hr_v, long M,
+                         const long* sub, long n_sub,
+                         const double* sdf, int n_sdf, const double* prm, int mode,
+                         double* out_x, double* out_v, int* flag, double* alt_x, double* alt_v, double* diag,
+                         int tmode, uint32_t* tape)
 {
     double r = prm[UP_R_LOW], c1 = prm[UP_C1], c2 = prm[UP_C2], eps_w = prm[UP_EPS_W];
     double R2 = 9.0 * r * r;
@@ -411,7 +430,7 @@ int or_upsample(const double* lr_x, const double* lr_v, long N,
         const double* xi = hr_x + 3 * i;
         const double* vi = hr_v + 3 * i;
         double S = 0, V[3] = {0, 0, 0}, wmax = 0;
-        long cnt = 0;
+        long cnt = 0, jstar = -1;
         long nc = N;
         if (mode == 1) nc = grid_query(&grid, xi, cand);
         for (long q = 0; q < nc; ++q) {
@@ -422,8 +441,19 @@ int or_upsample(const double* lr_x, const double* lr_v, long N,
             double w = or_weight(d2, r);
             S += w;
             for (int m = 0; m < 3; ++m) V[m] += w * lr_v[3 * j + m];
-            if (w > wmax) wmax = w;
+            if (w > wmax) { wmax = w; jstar = j; }
             ++cnt;
+        }
+        /* tape record of one HR particle: {argmax LR index, blend branch,
+         * SDF active bits, velocity removal bits} */
+        uint32_t* tp = tape ? tape + 4 * k : NULL;
+        if (tmode == TAPE_REPLAY) {
+            jstar = (long)(int32_t)tp[0];
+            wmax = 0.0;
+            if (jstar >= 0 && jstar < N) {
+                double d[3] = {xi[0] - lr_x[3 * jstar], xi[1] - lr_x[3 * jstar + 1], xi[2] - lr_x[3 * jstar + 2]};
+                wmax = or_weight(dot3(d, d), r);
+            }
         }
         /* interpolated LR velocity; with no LR particle in reach it is
          * undefined in the paper and alpha = 1 makes it irrelevant: use 0 */
@@ -437,6 +467,12 @@ int or_upsample(const double* lr_x, const double* lr_v, long N,
         int Aamb = fabs(wmax - c1) <= eps_w;
         int Bamb = S > 0 && fabs(wmax - c2 * S) <= eps_w * S;
         int prim = A || B;
+        if (tmode == TAPE_REPLAY) prim = (int)tp[1];
+        else if (tmode == TAPE_RECORD) {
+            tp[0] = (uint32_t)(int32_t)jstar;
+            tp[1] = (uint32_t)prim;
+            tp[2] = tp[3] = 0;
+        }
         int alt_out = prim;
         if (Aamb && ((!A) || B) != prim) alt_out = !prim;
         if (Bamb && (A || (!B)) != prim) alt_out = !prim;
@@ -444,7 +480,13 @@ int or_upsample(const double* lr_x, const double* lr_v, long N,
         double alpha = prim ? 1.0 - wmax : 0.0;
         int amb[64], n_amb = 0, hard = 0, n_act = 0;
         double xo[3], vo[3];
-        hr_finish(xi, vi, vt, alpha, sdf, n_sdf, prm, -1, xo, vo, amb, &n_amb, &hard, &n_act);
+        hr_finish(xi, vi, vt, alpha, sdf, n_sdf, prm, -1, xo, vo, amb, &n_amb, &hard, &n_act, tmode,
+                  tp ? tp + 2 : NULL);
+        if (tmode != TAPE_OFF) {
+            /* taped evaluation: no branch diagnostics */
+            for (int m = 0; m < 3; ++m) { out_x[3 * k + m] = xo[m]; out_v[3 * k + m] = vo[m]; }
+            continue;
+        }
         int n_total = n_amb + (alt_out != prim);
         double ax[3] = {xo[0], xo[1], xo[2]}, av[3] = {vo[0], vo[1], vo[2]};
         int fl = 0;
@@ -453,9 +495,11 @@ int or_upsample(const double* lr_x, const double* lr_v, long N,
             fl = 1;
             int tmp[64], nt = 0, h2 = 0;
             if (alt_out != prim)
-                hr_finish(xi, vi, vt, prim ? 0.0 : 1.0 - wmax, sdf, n_sdf, prm, -1, ax, av, tmp, &nt, &h2, NULL);
+                hr_finish(xi, vi, vt, prim ? 0.0 : 1.0 - wmax, sdf, n_sdf, prm, -1, ax, av, tmp, &nt, &h2, NULL,
+                          TAPE_OFF, NULL);
             else
-                hr_finish(xi, vi, vt, alpha, sdf, n_sdf, prm, amb[0], ax, av, tmp, &nt, &h2, NULL);
+                hr_finish(xi, vi, vt, alpha, sdf, n_sdf, prm, amb[0], ax, av, tmp, &nt, &h2, NULL, TAPE_OFF,
+                          NULL);
         }
         /* Conditioning of the SDF rule: near an edge or corner of a boundary
          * the contact normal turns quickly with position, so a rounding of
@@ -470,7 +514,8 @@ int or_upsample(const double* lr_x, const double* lr_v, long N,
                     double xp[3] = {xi[0], xi[1], xi[2]}, px[3], pv[3];
                     int tmp[64], nt = 0, h2 = 0;
                     xp[a] += sgn * dlt;
-                    hr_finish(xp, vi, vt, alpha, sdf, n_sdf, prm, -1, px, pv, tmp, &nt, &h2, NULL);
+                    hr_finish(xp, vi, vt, alpha, sdf, n_sdf, prm, -1, px, pv, tmp, &nt, &h2, NULL, TAPE_OFF,
+                              NULL);
                     if (nt != n_amb) continue;   /* a decision flipped: covered by the flags */
                     double ex[3] = {px[0] - xo[0], px[1] - xo[1], px[2] - xo[2]};
                     ex[a] -= sgn * dlt;
@@ -500,6 +545,34 @@ int or_upsample(const double* lr_x, const double* lr_v, long N,
     }
     if (mode == 1) grid_free(&grid);
     return err;
+}
+
+int or_upsample(const double* lr_x, const double* lr_v, long N,
+                const double* hr_x, const double* hr_v, long M,
+                const long* sub, long n_sub,
+                const double* sdf, int n_sdf, const double* prm, int mode,
+                double* out_x, double* out_v, int* flag, double* alt_x, double* alt_v, double* diag)
+{
+    return upsample_impl(lr_x, lr_v, N, hr_x, hr_v, M, sub, n_sub, sdf, n_sdf, prm, mode, out_x, out_v, flag,
+                         alt_x, alt_v, diag, TAPE_OFF, NULL);
+}
+
+static int total_components(const double* sdf, int n_sdf)
+{
+    int t = 0;
+    for (int s = 0; s < n_sdf; ++s) t += sdf_ncomp(sdf + OR_SDF_STRIDE * s);
+    return t;
+}
+
+/* One HR frame (grid neighbour search) that records its decisions into, or
+ * replays them from, tape = uint32[M][4].  At most 32 SDF components. */
+int or_upsample_tape(const double* lr_x, const double* lr_v, long N, const double* hr_x, const double* hr_v, long M,
+                     const double* sdf, int n_sdf, const double* prm, int tmode, uint32_t* tape,
+                     double* out_x, double* out_v)
+{
+    if ((tmode != TAPE_RECORD && tmode != TAPE_REPLAY) || !tape || total_components(sdf, n_sdf) > 32) return -1;
+    return upsample_impl(lr_x, lr_v, N, hr_x, hr_v, M, NULL, 0, sdf, n_sdf, prm, 1, out_x, out_v, NULL, NULL, NULL,
+                         NULL, tmode, tape);
 }
 
 /* ------------------------------------------------------------------ */
@@ -588,13 +661,21 @@ static void alt_push(or_alts* L, long i, const double* dD, int dn)
  * of its threshold and the branches differ, *amb is set and f_alt holds the
  * other branch. */
 static void friction_delta(const double* perp, double thr_s, double thr_k, double eps_x, double* f, double* f_alt,
-                           int* amb)
+                           int* amb, int tmode, unsigned char* bits)
 {
     double L = sqrt(dot3(perp, perp));
     double kin = (L > 0 && thr_k / L < 1.0) ? thr_k / L : 1.0;
     double scale = L < thr_s ? 1.0 : kin;
     double other = L < thr_s ? kin : 1.0;
     *amb = fabs(L - thr_s) <= eps_x && scale != other;
+    /* tape bit 1: the kinetic scale thr_k / |perp| applies (otherwise the
+     * whole tangential displacement is removed) */
+    if (tmode == TAPE_RECORD && !(L < thr_s) && L > 0 && thr_k / L < 1.0) *bits |= 2;
+    if (tmode == TAPE_REPLAY) {
+        scale = ((*bits & 2) && L > 0) ? thr_k / L : 1.0;
+        other = scale;
+        *amb = 0;
+    }
     for (int k = 0; k < 3; ++k) {
         f[k] = perp[k] * scale;
         f_alt[k] = perp[k] * other;
@@ -643,9 +724,18 @@ static void friction_delta(const double* perp, double thr_s, double thr_k, doubl
  * stats (optional): [0] #candidate pairs, [1] #significant ambiguous
  * decisions, [2] max candidates of one particle, [3] #active pair contacts
  * in the last pass, [4] #ambiguous decisions (significant or not). */
-int or_pbd_step(double* x, double* v, const double* inv_m, long N,
-                const double* sdf, int n_sdf, const double* prm, int mode,
-                int* suspect, long* stats)
+/* Tape of one LR step (bytes): int64 header {#pairs, N, #SDF components,
+ * #passes}, the candidate pairs as int64 (i, j), then per pass one byte per
+ * pair and one per (particle, SDF component): bit 0 = contact active,
+ * bit 1 = kinetic friction scale applies. */
+static long pbd_tape_bytes(long np, long N, int nct, int passes)
+{
+    return 32 + 16 * np + (long)passes * (np + N * (long)nct);
+}
+
+static int pbd_impl(double* x, double* v, const double* inv_m, long N,
+                    const double* sdf, int n_sdf, const double* prm, int mode,
+                    int* suspect, long* stats, int tmode, unsigned char* tape, long tape_cap, long* tape_len)
 {
     double r = prm[PB_R], dt = prm[PB_DT];
     const double g[3] = {prm[PB_GX], prm[PB_GY], prm[PB_GZ]};
@@ -679,8 +769,36 @@ int or_pbd_step(double* x, double* v, const double* inv_m, long N,
     or_pair *P = NULL, *E = NULL;
     unsigned char* border = NULL;
     long n_excl = 0;
-    long np = make_pairs(xt, N, Rc, mode, &P, &border, &E, &n_excl, eps_x);
-    if (np < 0) return -1;
+    long np;
+    int nct = total_components(sdf, n_sdf);
+    int total = n_stab + iters;
+    int64_t* th = (int64_t*)tape;
+    if (tmode == TAPE_REPLAY) {
+        /* the candidate pairs are part of the recorded decisions */
+        if (tape_cap < 32 || th[1] != N || th[2] != nct || th[3] != total) return -3;
+        np = (long)th[0];
+        if (tape_cap < pbd_tape_bytes(np, N, nct, total)) return -3;
+        P = (or_pair*)malloc((size_t)(np ? np : 1) * sizeof(or_pair));
+        border = (unsigned char*)calloc((size_t)(np ? np : 1), 1);
+        E = (or_pair*)malloc(sizeof(or_pair));
+        if (!P || !border || !E) return -1;
+        for (long q = 0; q < np; ++q) { P[q].i = (long)th[4 + 2 * q]; P[q].j = (long)th[5 + 2 * q]; }
+    } else {
+        np = make_pairs(xt, N, Rc, mode, &P, &border, &E, &n_excl, eps_x);
+        if (np < 0) return -1;
+    }
+    unsigned char* tpass = NULL;
+    if (tmode != TAPE_OFF) {
+        long need = pbd_tape_bytes(np, N, nct, total);
+        if (tape_len) *tape_len = need;
+        if (tape_cap < need) { free(P); free(E); free(border); return -3; }
+        if (tmode == TAPE_RECORD) {
+            th[0] = np; th[1] = N; th[2] = nct; th[3] = total;
+            for (long q = 0; q < np; ++q) { th[4 + 2 * q] = P[q].i; th[5 + 2 * q] = P[q].j; }
+            memset(tape + 32 + 16 * np, 0, (size_t)(need - 32 - 16 * np));
+        }
+        tpass = tape + 32 + 16 * np;
+    }
     long n_sig = 0, n_amb = 0, maxc = 0;
     if (stats) {
         long* c = (long*)calloc(n1, sizeof(long));
@@ -692,9 +810,10 @@ int or_pbd_step(double* x, double* v, const double* inv_m, long N,
     or_alts alts = {NULL, 0, 0};
 
     long active_last = 0;
-    int total = n_stab + iters;
     for (int it = 0; it < total; ++it) {
         int stab = it < n_stab;
+        unsigned char* tpair = tpass ? tpass + (long)it * (np + N * (long)nct) : NULL;
+        unsigned char* tsdf = tpair ? tpair + np : NULL;
         /* a particle that read a suspect candidate partner in an earlier
          * pass is itself suspect from now on */
         if (it > 0) {
@@ -727,6 +846,8 @@ int or_pbd_step(double* x, double* v, const double* inv_m, long N,
             if (border[p] && d < d0 + eps_x) { mark[i] = mark[j] = 1; ++n_sig; }
             int active = d < d0;
             int amb_act = fabs(d - d0) <= eps_x;
+            if (tmode == TAPE_REPLAY) { active = tpair[p] & 1; amb_act = 0; }
+            else if (tmode == TAPE_RECORD && active) tpair[p] |= 1;
             if ((!active && !amb_act) || d2 == 0.0) continue;
             double wsum = ws[i] + ws[j];
             if (!(wsum > 0)) continue;
@@ -748,7 +869,8 @@ int or_pbd_step(double* x, double* v, const double* inv_m, long N,
                 double a = dot3(dx, xij) / d2;
                 for (int k = 0; k < 3; ++k) perp[k] = dx[k] - a * xij[k];
                 double base = (fmode == 1) ? pen : d0;
-                friction_delta(perp, base * mu_s, base * mu_k, eps_x, f, fa, &amb_f);
+                friction_delta(perp, base * mu_s, base * mu_k, eps_x, f, fa, &amb_f, tmode,
+                               tpair ? tpair + p : NULL);
                 for (int k = 0; k < 3; ++k) {
                     ci_alt[k] = ci[k] - mi * fa[k];
                     cj_alt[k] = cj[k] + mj * fa[k];
@@ -781,7 +903,8 @@ int or_pbd_step(double* x, double* v, const double* inv_m, long N,
         /* SDF contacts */
         for (long i = 0; i < N; ++i) {
             if (!(ws[i] > 0)) continue;
-            for (int s = 0; s < n_sdf; ++s) {
+            int comp0 = 0;
+            for (int s = 0; s < n_sdf; comp0 += sdf_ncomp(sdf + OR_SDF_STRIDE * s), ++s) {
                 const double* rec = sdf + OR_SDF_STRIDE * s;
                 double phi[OR_MAX_COMP], nn[3 * OR_MAX_COMP];
                 int tie;
@@ -791,6 +914,9 @@ int or_pbd_step(double* x, double* v, const double* inv_m, long N,
                 for (int c = 0; c < nc; ++c) {
                     int active = phi[c] < r;
                     int amb_act = fabs(phi[c] - r) <= eps_x;
+                    unsigned char* tb = tsdf ? tsdf + i * (long)nct + comp0 + c : NULL;
+                    if (tmode == TAPE_REPLAY) { active = *tb & 1; amb_act = 0; }
+                    else if (tmode == TAPE_RECORD && active) *tb |= 1;
                     if (!active && !amb_act) continue;
                     if (tie) { mark[i] = 1; ++n_sig; }
                     const double* n = nn + 3 * c;
@@ -805,7 +931,7 @@ int or_pbd_step(double* x, double* v, const double* inv_m, long N,
                         double a = dot3(dx, n);
                         for (int k = 0; k < 3; ++k) perp[k] = dx[k] - a * n[k];
                         double base = (fmode == 1) ? pen : d0;
-                        friction_delta(perp, base * bmu_s, base * bmu_k, eps_x, f, fa, &amb_f);
+                        friction_delta(perp, base * bmu_s, base * bmu_k, eps_x, f, fa, &amb_f, tmode, tb);
                         for (int k = 0; k < 3; ++k) {
                             ci_alt[k] = ci[k] - fa[k];
                             ci[k] -= f[k];
@@ -879,6 +1005,25 @@ int or_pbd_step(double* x, double* v, const double* inv_m, long N,
     free(mark);
     free(mark2);
     return 0;
+}
+
+int or_pbd_step(double* x, double* v, const double* inv_m, long N,
+                const double* sdf, int n_sdf, const double* prm, int mode,
+                int* suspect, long* stats)
+{
+    return pbd_impl(x, v, inv_m, N, sdf, n_sdf, prm, mode, suspect, stats, TAPE_OFF, NULL, 0, NULL);
+}
+
+/* One LR step (grid neighbour search) that records its decisions into, or
+ * replays them from, a byte tape of tape_cap bytes.  *tape_len receives the
+ * size the tape needs; -3 when tape_cap is too small (x and v are then
+ * partly updated and must be restored by the caller) or a replayed tape does
+ * not match N, the SDF list or the pass count. */
+int or_pbd_step_tape(double* x, double* v, const double* inv_m, long N, const double* sdf, int n_sdf,
+                     const double* prm, int tmode, unsigned char* tape, long tape_cap, long* tape_len)
+{
+    if ((tmode != TAPE_RECORD && tmode != TAPE_REPLAY) || !tape) return -1;
+    return pbd_impl(x, v, inv_m, N, sdf, n_sdf, prm, 1, NULL, NULL, tmode, tape, tape_cap, tape_len);
 }
 
 /* Brute-force pair listing for tests of the neighbour search: every (i, j)

@@ -230,17 +230,35 @@ def digging(seed=SEED_BASE + 2, r_low=0.0089, ratio=40, size=1.0, depth=0.3):
                    bucket_index=1)
 
 
-def column(seed=SEED_BASE + 3, n_low=4000, r_low=0.01, ratio=16):
-    """Falling column (10 x 10 footprint) in a 0.6 m box."""
+def column(seed=SEED_BASE + 3, n_low=4000, r_low=0.01, ratio=16, z0=0.1):
+    """Falling column (10 x 10 footprint) in a 0.6 m box, lowest layer
+    centred z0 above the floor."""
     rng = np.random.default_rng(seed)
     box_lo, box_hi = (0.0, 0.0, 0.0), (0.6, 0.6, 1.2)
     n_xy = 10
     layers = -(-n_low // (n_xy * n_xy))
     sp = 2.0 * r_low
-    lo = (0.3 - 0.5 * sp * (n_xy - 1), 0.3 - 0.5 * sp * (n_xy - 1), 0.1)
+    lo = (0.3 - 0.5 * sp * (n_xy - 1), 0.3 - 0.5 * sp * (n_xy - 1), z0)
     xyz = _lattice(rng, lo, (n_xy, n_xy, layers), sp, 0.1 * r_low)[:n_low]
     return _finish("column", seed, box_lo, box_hi, r_low, ratio, xyz, rng,
                    [box_interior(box_lo, box_hi)], dt=1.0 / 60.0, iters=4)
+
+
+def diff_column(seed=SEED_BASE + 5, n_low=4000, ratio=16):
+    """Workload of the differentiable pattern: the falling column released
+    with its lowest layer 1 cm above resting contact, so it lands within the
+    rollout; 30 steps of 1/240 s, each one LR step (2 stabilization + 4
+    solver passes) and one HR frame; recomputation checkpoints every 5 steps.
+    The loss is sum_i |x_i - t_i|^2 over the HR particles after the rollout,
+    with targets t = initial HR positions moved by (5, 0, -2) cm plus seeded
+    N(0, 1 cm) noise (float32, shared by both sides)."""
+    sc = column(n_low=n_low, ratio=ratio, z0=0.02)
+    rng = np.random.default_rng(seed)
+    m = len(sc["hr_pos"])
+    t = sc["hr_pos"][:, :3].astype(np.float64) + np.array([0.05, 0.0, -0.02]) + rng.normal(0.0, 0.01, (m, 3))
+    sc.update(name="diff_column", target=t.astype(np.float32), dt=1.0 / 240.0, steps=30, checkpoint_every=5,
+              n_stab=2, iters=4)
+    return sc
 
 
 def batch(seed=SEED_BASE + 4, n_scenes=256, lo_count=500, hi_count=8000, ratios=(8, 16, 32)):

@@ -61,3 +61,22 @@ def check_hr(sc, dt, gx, gv, ref, max_multi_frac=1e-3):
     return dict(n=len(ok), flag1=int((fl == 1).sum()), flag2=int((fl == 2).sum()),
                 max_dx=float(np.linalg.norm(gx - ref["x"], axis=1)[fl == 0].max(initial=0.0)),
                 max_dv=float(np.linalg.norm(gv - ref["v"], axis=1)[fl == 0].max(initial=0.0)))
+
+
+def pb_prm(sc, dt, n_stab, iters, eps_x=1e-7, eps_impact=1e-9, mass_k=1.0, friction_mode=0):
+    """Oracle LR-step parameters matching a context built from the scene with
+    default gs_params (height-scaled mass k = 1/m, ground at the box floor,
+    neighbour radius 3 r_LR)."""
+    g = sc.get("gravity", (0.0, 0.0, -9.81))
+    r = f32(sc["r_low"])
+    return dict(r=r, dt=f32(dt), gx=f32(g[0]), gy=f32(g[1]), gz=f32(g[2]), mu_s=f32(sc["mu_s"]),
+                mu_k=f32(sc["mu_k"]), n_stab=n_stab, iters=iters, mass_k=mass_k, ground_z=f32(sc["box_lo"][2]),
+                rc=f32(np.float32(3.0) * np.float32(r)), friction_mode=friction_mode, eps_x=eps_x,
+                eps_impact=eps_impact)
+
+
+def diff_prms(sc):
+    """(LR-step, HR-frame) oracle parameters of a differentiable-rollout
+    scene: one LR step and one HR frame of the same dt per step."""
+    return (pb_prm(sc, sc["dt"], sc["n_stab"], sc["iters"], eps_impact=0.0),
+            up_prm(sc, sc["dt"], eps_x=1e-6))

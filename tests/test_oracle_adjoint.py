@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import scenes
+from gs_testutil import diff_prms
 
 EPS = 1e-7
 
@@ -118,3 +119,54 @@ def test_pbd_step_vjp_matches_central_differences(orc, case):
         scale = np.abs(fd).max()
         assert scale > 0
         np.testing.assert_allclose(grad.ravel(), fd, rtol=0, atol=2e-5 * scale, err_msg=f"{name} arg {which}")
+
+
+def _rollout_inputs(sc):
+    return (sc["lr_pos"][:, :3], sc["lr_vel"][:, :3], sc["lr_pos"][:, 3].astype(float), sc["hr_pos"][:, :3],
+            sc["hr_vel"][:, :3], scenes.sdf_table(sc["sdfs"]))
+
+
+def test_rollout_replay_reproduces_recording(orc):
+    sc = scenes.diff_column(n_low=300, ratio=8)
+    pb, up = diff_prms(sc)
+    X, V, im, x, v, sdf = _rollout_inputs(sc)
+    ro = orc.rollout(X, V, im, x, v, sdf, pb, up, 12)
+    rr = orc.rollout(X, V, im, x, v, sdf, pb, up, 12, tapes=ro["tapes"])
+    for k in ("lr_x", "lr_v", "hr_x", "hr_v"):
+        np.testing.assert_array_equal(rr[k], ro[k])
+    # the plain (untaped) step is the same function
+    x1, v1, _, _ = orc.pbd_step(X, V, im, sdf, pb)
+    np.testing.assert_array_equal(x1, ro["ops"][1][1])
+
+
+def test_rollout_vjp_matches_frozen_central_differences(orc):
+    """Gradient of a 30-step rollout loss w.r.t. every initial quantity
+    against central differences (eps 1e-4) of the rollout with its decisions
+    replayed from the unperturbed run."""
+    sc = scenes.diff_column(n_low=400, ratio=8)
+    pb, up = diff_prms(sc)
+    X, V, im, x, v, sdf = _rollout_inputs(sc)
+    T = sc["target"].astype(float)
+    F = sc["steps"]
+    ro = orc.rollout(X, V, im, x, v, sdf, pb, up, F)
+    # the column lands: floor contacts are active in the last LR steps
+    assert ro["lr_x"][:, 2].min() < pb["r"]
+    gX, gV, gx, gv = orc.rollout_vjp(ro, im, sdf, pb, up, 2.0 * (ro["hr_x"] - T), np.zeros_like(T))
+    rng = np.random.default_rng(17)
+    base = [np.asarray(a, float) for a in (X, V, x, v)]
+    for which, grad in enumerate((gX, gV, gx, gv)):
+        d = rng.normal(size=base[which].shape)
+        # velocities: the step of the differentiation workload (1e-4 m/s,
+        # about 1e-5 m of displacement over the rollout); positions: a step
+        # on the same displacement scale
+        eps = 1e-4 if which in (1, 3) else 1e-6
+
+        def loss(s):
+            args = [a.copy() for a in base]
+            args[which] = args[which] + s * d
+            out = orc.rollout(args[0], args[1], im, args[2], args[3], sdf, pb, up, F, tapes=ro["tapes"])
+            return float(((out["hr_x"] - T) ** 2).sum())
+
+        fd = (loss(eps) - loss(-eps)) / (2 * eps)
+        an = float((grad * d).sum())
+        assert abs(an - fd) <= 1e-3 * abs(fd), (which, an, fd)

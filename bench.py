@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--batch-scenes", type=int, default=256)
     return ap.parse_args()
 
@@ -239,6 +240,60 @@ def run_batched(args, dev, stream, gs, torch):
                                                                    "upsample_us": tus}}
 
 
+def run_diff(args, dev, stream, gs, torch):
+    """The differentiable form on the falling-column workload (4k LR / 64k
+    HR, 30 steps of one LR step and one HR frame, recomputation checkpoints
+    every 5 steps): forward + loss + backward to the initial LR velocities,
+    against the plain in-place forward of the same rollout."""
+    from paper_2308_01629_gb300.diff import rollout
+    sc = scenes.diff_column()
+    dt, F, iters, every = sc["dt"], sc["steps"], sc["iters"], sc["checkpoint_every"]
+    M = len(sc["hr_pos"])
+    k = max(3, args.steps // 10)
+    with torch.cuda.stream(stream):
+        plain = gs.Context(sc, stream=stream.cuda_stream)
+        ctx = gs.Context(sc, stream=stream.cuda_stream)
+        state = [torch.from_numpy(np.ascontiguousarray(sc[n])).to(dev) for n in ("lr_pos", "lr_vel", "hr_pos",
+                                                                                  "hr_vel")]
+        target = torch.from_numpy(sc["target"]).to(dev)
+
+        def plain_rollout():
+            for _ in range(F):
+                plain.frame(dt, 1, iters)
+
+        def diff_rollout():
+            X, V, x, v = state
+            V = V.clone().requires_grad_(True)
+            out = rollout(ctx, X, V, x, v, dt, frames=F, n_sub=1, iters=iters, checkpoint_every=every)
+            loss = ((out[2][:, :3] - target) ** 2).sum()
+            loss.backward()
+            return V.grad
+
+        def timed(fn):
+            for _ in range(2):
+                fn()
+            torch.cuda.synchronize(dev)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+            for a, b in ev:
+                a.record(stream)
+                fn()
+                b.record(stream)
+            torch.cuda.synchronize(dev)
+            return sum(a.elapsed_time(b) for a, b in ev) / k
+
+        ms_plain = timed(plain_rollout)
+        l0 = ctx.launches()
+        ms_diff = timed(diff_rollout)
+        nl = (ctx.launches() - l0) / (k + 2)
+        plain.close()
+        ctx.close()
+    return {"workload": f"falling column {len(sc['lr_pos'])} LR / {M} HR, {F} steps of {dt:.6f} s, "
+                        f"checkpoint every {every}", "loss": "sum |x_HR - target|^2 after the rollout",
+            "plain_forward_ms_per_rollout": ms_plain, "forward_backward_ms_per_rollout": ms_diff,
+            "forward_backward_hr_steps_per_s": M * F / (ms_diff / 1e3),
+            "backward_overhead_vs_plain_forward": ms_diff / ms_plain, "library_kernels_per_rollout": nl}
+
+
 # ------------------------------------------------------------- GPU arm ---
 def run_gpu(args):
     import torch
@@ -265,12 +320,12 @@ def run_gpu(args):
     frame = [0]
 
     def step(c):
+        # one frame: the bucket pose, N_SUB LR steps and the HR frame; with
+        # graphs on and timers off it is one graph launch
         b = bucket_at(sc, frame[0])
         if b is not None:
             c.set_sdf(*b)
-        for _ in range(N_SUB):
-            c.step_low(DT / N_SUB, sc["iters"])
-        c.upsample(DT)
+        c.frame(DT, N_SUB, sc["iters"])
         frame[0] += 1
 
     def barrier():
@@ -281,15 +336,13 @@ def run_gpu(args):
     # steps (the timed region alone can be shorter than one sample period)
     clk = Clocks(local)
     time.sleep(0.3)
+    ctx.set_graphs(True)
     for _ in range(args.warmup):
         step(ctx)
     torch.cuda.synchronize(dev)
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ctx.set_timing(True)
-    for t in range(gs.GS_TIMER_COUNT):
-        ctx.timing_read(t)
     launches0 = ctx.launches()
     barrier()
     torch.cuda.synchronize(dev)
@@ -309,12 +362,25 @@ def run_gpu(args):
     launches = ctx.launches() - launches0
     ctx.sync()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+
+    # The same frames with the library's event timers around each phase
+    # (timers bypass the graphs): the breakdown and the gather kernel's
+    # launch duration for the roofline.
+    ctx.set_timing(True)
+    for t in range(gs.GS_TIMER_COUNT):
+        ctx.timing_read(t)
+    n_brk = max(4, args.steps // 2)
+    for k in range(n_brk):
+        flush.fill_(float(k))
+        step(ctx)
+    torch.cuda.synchronize(dev)
+    ctx.sync()
     gather_ms, gather_n = ctx.timing_read(gs.GS_TIMER_GATHER)
     lr_ms, lr_n = ctx.timing_read(gs.GS_TIMER_STEP_LOW)
     bin_ms, bin_n = ctx.timing_read(gs.GS_TIMER_BIN_LOW)
     rs_ms, rs_n = ctx.timing_read(gs.GS_TIMER_RESORT)
     ctx.set_timing(False)
-    total_ms = float(sum(step_ms))
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -362,6 +428,7 @@ def run_gpu(args):
 
     ctx.close()
     batched = None if args.no_batched else run_batched(args, dev, stream, gs, torch)
+    differentiable = None if args.no_diff else run_diff(args, dev, stream, gs, torch)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -386,15 +453,19 @@ def run_gpu(args):
                      "kernel": "k_upsample (fused gather + blend + advection + SDF)",
                      "peak_source": "measured" if pk else "fallback",
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": gather_avg_s * 1e6},
-        "breakdown_ms_per_step": {"lr_steps": lr_ms / args.steps, "lr_binning_for_upsample": bin_ms / max(bin_n, 1),
-                                  "hr_reorder_amortized": rs_ms / args.steps,
-                                  "upsample_kernel": gather_ms / max(gather_n, 1)},
+        "breakdown_ms_per_step": {"lr_steps": lr_ms / n_brk, "lr_binning_for_upsample": bin_ms / max(bin_n, 1),
+                                  "hr_reorder_amortized": rs_ms / n_brk,
+                                  "upsample_kernel": gather_ms / max(gather_n, 1),
+                                  "source": f"{n_brk} frames after the timed region, library event timers "
+                                            "around each phase (no graphs)"},
+        "timed_region": "one CUDA-graph launch per frame (bucket pose copied before it)",
         "upsample_kernel_hr_per_s": M / gather_avg_s,
         "wall_s_timed_region": wall,
         "gpu_launches": int(launches),
         "clocks": clocks,
         "e2e": e2e,
         "batched": batched,
+        "differentiable": differentiable,
     }
     if not args.no_cpu:
         line["cpu_baseline"] = oracle_frame_rate(sc, args.cpu_seconds)

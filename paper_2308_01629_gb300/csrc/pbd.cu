@@ -47,12 +47,23 @@ __global__ void k_step_gather(int64_t n, const uint32_t* __restrict__ idx, const
     s_x[p] = pos[i];   // w carries the inverse mass
 }
 
-__global__ void k_neighbors(const PbdArgs a, const float4* __restrict__ s_xt, const uint32_t* __restrict__ skeys,
-                            const uint32_t* __restrict__ cell_start, uint32_t* __restrict__ nbr,
-                            uint32_t* __restrict__ cnt, int cap, int* err)
+// Candidate partners of every particle within the neighbour radius, in
+// ascending sorted index row by row of the 27 surrounding cells.  Four lanes
+// share one particle and take every fourth candidate of a row; a ballot over
+// the four keeps the list in ascending order.
+constexpr int kNbrLanes = 4;
+
+__global__ void __launch_bounds__(128) k_neighbors(const PbdArgs a, const float4* __restrict__ s_xt,
+                                                   const uint32_t* __restrict__ skeys,
+                                                   const uint32_t* __restrict__ cell_start, uint32_t* __restrict__ nbr,
+                                                   uint32_t* __restrict__ cnt, int cap, int* err)
 {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.n) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t p = t / kNbrLanes;
+    const int sub = (int)(t % kNbrLanes);
+    const int gbase = (int)(threadIdx.x & 31u) & ~(kNbrLanes - 1);
+    const unsigned gmask = ((1u << kNbrLanes) - 1u) << gbase;
+    if (p >= a.n) return;   // the four lanes of a particle leave together
     const SceneDev& sc = a.scenes[a.lr_scene[p]];
     const GridDev& g = sc.g;
     const float4 xp = s_xt[p];
@@ -62,6 +73,7 @@ __global__ void k_neighbors(const PbdArgs a, const float4* __restrict__ s_xt, co
     const int cz = (int)(c / ((uint32_t)g.dx * (uint32_t)g.dy));
     const float rc2 = sc.rc * sc.rc;
     const int x0 = cx > 0 ? cx - 1 : 0, x1 = cx + 1 < g.dx ? cx + 1 : g.dx - 1;
+    const unsigned below = (1u << sub) - 1u;
     int k = 0;
     for (int z = cz - 1; z <= cz + 1; ++z) {
         if (z < 0 || z >= g.dz) continue;
@@ -69,17 +81,24 @@ __global__ void k_neighbors(const PbdArgs a, const float4* __restrict__ s_xt, co
             if (y < 0 || y >= g.dy) continue;
             const int64_t row = (int64_t)sc.cell_off + ((int64_t)z * g.dy + y) * g.dx;
             const uint32_t b = cell_start[row + x0], e = cell_start[row + x1 + 1];
-            for (uint32_t q = b; q < e; ++q) {
-                if ((int64_t)q == p) continue;
-                float4 xq = s_xt[q];
-                float dx = xq.x - xp.x, dy = xq.y - xp.y, dz = xq.z - xp.z;
-                if (dx * dx + dy * dy + dz * dz < rc2) {
-                    if (k < cap) nbr[(int64_t)k * a.n + p] = q;
-                    ++k;
+            for (uint32_t q0 = b; q0 < e; q0 += kNbrLanes) {
+                const uint32_t q = q0 + (uint32_t)sub;
+                bool take = false;
+                if (q < e && (int64_t)q != p) {
+                    const float4 xq = s_xt[q];
+                    const float dx = xq.x - xp.x, dy = xq.y - xp.y, dz = xq.z - xp.z;
+                    take = dx * dx + dy * dy + dz * dz < rc2;
                 }
+                const unsigned bal = __ballot_sync(gmask, take) >> gbase;
+                if (take) {
+                    const int pos = k + __popc(bal & below);
+                    if (pos < cap) nbr[(int64_t)pos * a.n + p] = q;
+                }
+                k += __popc(bal);
             }
         }
     }
+    if (sub != 0) return;
     if (k > cap) {
         atomicOr(err, GS_DEVERR_NEIGHBOR_CAP);
         k = cap;
@@ -88,9 +107,42 @@ __global__ void k_neighbors(const PbdArgs a, const float4* __restrict__ s_xt, co
 }
 
 // kLanes lanes share one particle: lane `sub` takes candidates sub, sub +
-// kLanes, ...; the partial sums are added with shuffles in a fixed order, and
-// lane 0 adds the SDF contacts and writes the particle.
+// kLanes, ... two at a time (so the loads of both are in flight together)
+// and the SDF components whose running index is sub modulo kLanes; the
+// partial sums are added with shuffles in a fixed order and lane 0 writes
+// the particle.
 constexpr int kLanes = 4;
+
+struct PassAcc {
+    float Dx, Dy, Dz;
+    int n;
+};
+
+__device__ __forceinline__ void pair_term(PassAcc& acc, const SceneDev& sc, int stab, float4 yp, float wp, float dpx,
+                                          float dpy, float dpz, float4 xtq, float4 xq, float d0)
+{
+    const float4 yq = stab ? xq : xtq;
+    const PairGeo pg = pair_geo(yp, yq);
+    if (!(pg.d < d0) || pg.d2 == 0.0f) return;
+    const float wsum = wp + xtq.w;
+    if (!(wsum > 0.0f)) return;
+    const float m = wp / wsum;
+    const float pen = d0 - pg.d;
+    const float s = m * pen / pg.d;
+    acc.Dx -= s * pg.ex;
+    acc.Dy -= s * pg.ey;
+    acc.Dz -= s * pg.ez;
+    if (!stab) {
+        const float rx = dpx - (xtq.x - xq.x), ry = dpy - (xtq.y - xq.y), rz = dpz - (xtq.z - xq.z);
+        const Tangent tg = tangent_part(rx, ry, rz, pg.ex, pg.ey, pg.ez, pg.d2);
+        const float base = sc.friction_mode == 1 ? pen : d0;
+        const float f = m * friction_scale(tg.L, base * sc.mu_s, base * sc.mu_k);
+        acc.Dx -= f * tg.tx;
+        acc.Dy -= f * tg.ty;
+        acc.Dz -= f * tg.tz;
+    }
+    ++acc.n;
+}
 
 __global__ void __launch_bounds__(128) k_pass(const PbdArgs a, int stab, const float4* __restrict__ x_in,
                                               const float4* __restrict__ xt_in, float4* __restrict__ x_out,
@@ -113,73 +165,57 @@ __global__ void __launch_bounds__(128) k_pass(const PbdArgs a, int stab, const f
     const float4 yp = stab ? xp : xtp;          // positions the constraints are evaluated on
     const float wp = xtp.w;                      // inverse height-scaled mass
     const float dpx = xtp.x - xp.x, dpy = xtp.y - xp.y, dpz = xtp.z - xp.z;
-    float Dx = 0.f, Dy = 0.f, Dz = 0.f;
-    int n_act = 0;
-    for (int k = sub; k < nc; k += kLanes) {
-        const uint32_t q = nbr[(int64_t)k * a.n + p];
-        const float4 xtq = xt_in[q];
-        const float4 xq = x_in[q];
-        const float4 yq = stab ? xq : xtq;
-        const PairGeo pg = pair_geo(yp, yq);
-        const float ex = pg.ex, ey = pg.ey, ez = pg.ez, d2 = pg.d2, d = pg.d;
-        if (!(d < d0) || d2 == 0.0f) continue;
-        const float wsum = wp + xtq.w;
-        if (!(wsum > 0.0f)) continue;
-        const float m = wp / wsum;
-        const float pen = d0 - d;
-        const float s = m * pen / d;
-        Dx -= s * ex;
-        Dy -= s * ey;
-        Dz -= s * ez;
-        if (!stab) {
-            const float rx = dpx - (xtq.x - xq.x), ry = dpy - (xtq.y - xq.y), rz = dpz - (xtq.z - xq.z);
-            const Tangent tg = tangent_part(rx, ry, rz, ex, ey, ez, d2);
-            const float base = sc.friction_mode == 1 ? pen : d0;
-            const float f = m * friction_scale(tg.L, base * sc.mu_s, base * sc.mu_k);
-            Dx -= f * tg.tx;
-            Dy -= f * tg.ty;
-            Dz -= f * tg.tz;
-        }
-        ++n_act;
+    PassAcc acc = {0.f, 0.f, 0.f, 0};
+    for (int k = sub; k < nc; k += 2 * kLanes) {
+        const int k2 = k + kLanes;
+        const bool two = k2 < nc;
+        const uint32_t q1 = nbr[(int64_t)k * a.n + p];
+        const uint32_t q2 = two ? nbr[(int64_t)k2 * a.n + p] : q1;
+        const float4 xtq1 = xt_in[q1], xq1 = x_in[q1];
+        const float4 xtq2 = xt_in[q2], xq2 = x_in[q2];
+        pair_term(acc, sc, stab, yp, wp, dpx, dpy, dpz, xtq1, xq1, d0);
+        if (two) pair_term(acc, sc, stab, yp, wp, dpx, dpy, dpz, xtq2, xq2, d0);
     }
-#pragma unroll
-    for (int o = 1; o < kLanes; o <<= 1) {
-        Dx += __shfl_xor_sync(0xffffffffu, Dx, o);
-        Dy += __shfl_xor_sync(0xffffffffu, Dy, o);
-        Dz += __shfl_xor_sync(0xffffffffu, Dz, o);
-        n_act += __shfl_xor_sync(0xffffffffu, n_act, o);
-    }
-    if (!valid || sub != 0) return;
-    if (wp > 0.0f) {
+    if (valid && wp > 0.0f) {
+        int gc = 0;
         for (int sI = 0; sI < sc.n_sdf; ++sI) {
             const gs_sdf& b = a.sdf[sc.sdf_begin + sI];
             const int ncomp = sdf_components(b.kind);
-            const float bmu_s = sqrtf(sc.mu_s * b.mu_s), bmu_k = sqrtf(sc.mu_k * b.mu_k);
-            for (int c = 0; c < ncomp; ++c) {
+            for (int c = 0; c < ncomp; ++c, ++gc) {
+                if ((gc & (kLanes - 1)) != sub) continue;
                 const SdfHit h = sdf_eval(b, c, yp.x, yp.y, yp.z);
                 if (!(h.phi < sc.r_low)) continue;
                 const float pen = sc.r_low - h.phi;
-                Dx += pen * h.nx;
-                Dy += pen * h.ny;
-                Dz += pen * h.nz;
+                acc.Dx += pen * h.nx;
+                acc.Dy += pen * h.ny;
+                acc.Dz += pen * h.nz;
                 if (!stab) {
+                    const float bmu_s = sqrtf(sc.mu_s * b.mu_s), bmu_k = sqrtf(sc.mu_k * b.mu_k);
                     const float rx = dpx - b.vel[0] * a.dt, ry = dpy - b.vel[1] * a.dt, rz = dpz - b.vel[2] * a.dt;
                     const Tangent tg = tangent_part(rx, ry, rz, h.nx, h.ny, h.nz, 1.0f);
                     const float base = sc.friction_mode == 1 ? pen : d0;
                     const float f = friction_scale(tg.L, base * bmu_s, base * bmu_k);
-                    Dx -= f * tg.tx;
-                    Dy -= f * tg.ty;
-                    Dz -= f * tg.tz;
+                    acc.Dx -= f * tg.tx;
+                    acc.Dy -= f * tg.ty;
+                    acc.Dz -= f * tg.tz;
                 }
-                ++n_act;
+                ++acc.n;
             }
         }
     }
+#pragma unroll
+    for (int o = 1; o < kLanes; o <<= 1) {
+        acc.Dx += __shfl_xor_sync(0xffffffffu, acc.Dx, o);
+        acc.Dy += __shfl_xor_sync(0xffffffffu, acc.Dy, o);
+        acc.Dz += __shfl_xor_sync(0xffffffffu, acc.Dz, o);
+        acc.n += __shfl_xor_sync(0xffffffffu, acc.n, o);
+    }
+    if (!valid || sub != 0) return;
     float4 nt = xtp;
     float4 nx = xp;
-    if (n_act > 0) {
-        const float inv = 1.0f / (float)n_act;
-        const float ux = Dx * inv, uy = Dy * inv, uz = Dz * inv;
+    if (acc.n > 0) {
+        const float inv = 1.0f / (float)acc.n;
+        const float ux = acc.Dx * inv, uy = acc.Dy * inv, uz = acc.Dz * inv;
         nt.x += ux;
         nt.y += uy;
         nt.z += uz;
@@ -229,7 +265,7 @@ cudaError_t gs_launch_neighbors(cudaStream_t s, const PbdArgs& a, const float4* 
                                 int64_t* launches)
 {
     if (a.n <= 0) return cudaSuccess;
-    k_neighbors<<<gs_blocks(a.n, 128), 128, 0, s>>>(a, s_xt, skeys, cell_start, nbr, cnt, cap, err);
+    k_neighbors<<<gs_blocks(a.n * kNbrLanes, 128), 128, 0, s>>>(a, s_xt, skeys, cell_start, nbr, cnt, cap, err);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -148,16 +148,11 @@ cudaError_t launch_hr_load(gs_ctx* c, const float4* src, float4* dst, int set_id
 int bin_low_at(gs_ctx* c, const float4* positions)
 {
     const int64_t n = c->n_low;
-    CK(gs_launch_scene_keys(c->stream, positions, n, c->d_scenes, c->lr_scene, 0, c->lr_keys[0], c->lr_vals[0],
-                            &c->launches),
-       "cell keys");
-    int which = 0;
-    CK(gs_radix_sort(c->stream, c->lr_keys, c->lr_vals, &which, c->sort_hist, n, c->lr_key_bits, &c->launches),
-       "radix sort");
-    c->lr_sorted_keys = c->lr_keys[which];
-    c->lr_sorted_idx = c->lr_vals[which];
-    CK(gs_launch_cell_start(c->stream, c->lr_sorted_keys, n, c->n_cell_total, c->lr_cell_start, &c->launches),
-       "cell start");
+    CK(gs_count_sort_cells(c->stream, positions, n, c->d_scenes, c->lr_scene, c->n_cell_total, c->lr_keys[0],
+                           c->lr_vals[0], c->lr_keys[1], c->lr_vals[1], c->lr_cell_start, c->scan_aux, &c->launches),
+       "bin by cell");
+    c->lr_sorted_keys = c->lr_keys[1];
+    c->lr_sorted_idx = c->lr_vals[1];
     return GS_OK;
 }
 
@@ -311,6 +306,7 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
     A(dalloc(&c->lr_vals[0], N));
     A(dalloc(&c->lr_vals[1], N));
     A(dalloc(&c->lr_cell_start, cells + 1));
+    A(dalloc(&c->scan_aux, gs_scan_aux_words(cells + 1)));
     A(dalloc(&c->lr_spos, N));
     A(dalloc(&c->lr_svel, N));
     A(dalloc(&c->lr_xt, N));
@@ -542,7 +538,7 @@ void gs_destroy(gs_ctx* c)
                     c->hr_pos[0],  c->hr_pos[1],  c->hr_vel[0],  c->hr_vel[1],  c->hr_keys[0], c->hr_keys[1],
                     c->hr_vals[0], c->hr_vals[1], c->nbr,        c->nbr_cnt,    c->tmp4,      c->sort_hist,
                     c->d_work,     c->d_err,      c->gXs,        c->gVs,       c->snap,      c->snap_xt,
-                    c->adj_gx,     c->adj_gxt,    c->adj_h,      c->adj_gws};
+                    c->adj_gx,     c->adj_gxt,    c->adj_h,      c->adj_gws,   c->scan_aux};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->h_err) cudaFreeHost(c->h_err);

@@ -91,6 +91,7 @@ struct gs_ctx {
     uint32_t* lr_sorted_keys = nullptr;           // points into lr_keys after a sort
     uint32_t* lr_sorted_idx = nullptr;            // points into lr_vals after a sort
     uint32_t* lr_cell_start = nullptr;            // n_cell_total + 1
+    uint32_t* scan_aux = nullptr;                 // tile sums of the cell-start scan
     float4* lr_spos = nullptr;                    // cell-ordered LR position (upsampling view)
     float4* lr_svel = nullptr;                    // cell-ordered LR velocity
     bool lr_binned = false;
@@ -166,6 +167,15 @@ cudaError_t gs_launch_cell_keys(cudaStream_t s, const float4* pos, int64_t n, Gr
                                 uint32_t* vals, int64_t* launches);
 // Cell keys of slots that belong to several scenes: scene of slot i is
 // tag[i] & ~kPadBit; padding slots get the scene's padding cell.
+// Stable counting sort of n items by the cell of their position (coarse
+// keys): out_keys / out_idx in ascending (cell, item) order and cell_start
+// (n_cell + 1 entries) the start of every cell.  aux holds
+// gs_scan_aux_words(n_cell + 1) words.
+size_t gs_scan_aux_words(int64_t total);
+cudaError_t gs_count_sort_cells(cudaStream_t s, const float4* pos, int64_t n, const SceneDev* scenes,
+                                const uint32_t* tag, int64_t n_cell, uint32_t* keys, uint32_t* rank,
+                                uint32_t* out_keys, uint32_t* out_idx, uint32_t* cell_start, uint32_t* aux,
+                                int64_t* launches);
 cudaError_t gs_launch_scene_keys(cudaStream_t s, const float4* pos, int64_t n, const SceneDev* scenes,
                                  const uint32_t* tag, int fine, uint32_t* keys, uint32_t* vals, int64_t* launches);
 cudaError_t gs_launch_cell_start(cudaStream_t s, const uint32_t* sorted_keys, int64_t n, int64_t n_cell,

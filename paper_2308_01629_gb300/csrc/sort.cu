@@ -205,6 +205,152 @@ __global__ void k_scene_keys(const float4* __restrict__ pos, int64_t n, const Sc
     vals[i] = (uint32_t)i;
 }
 
+// ---- stable counting sort by cell (the LR set) ------------------------
+// Items are counted per cell with atomics, each keeping its arrival rank
+// within its cell; the exclusive scan of the counts is the cell start table;
+// items go to start + rank; finally every cell's entries are put in
+// ascending item order, which makes the result that of a stable sort.
+
+__global__ void k_cs_keys(const float4* __restrict__ pos, int64_t n, const SceneDev* __restrict__ scenes,
+                          const uint32_t* __restrict__ tag, uint32_t* __restrict__ keys, uint32_t* __restrict__ rank,
+                          uint32_t* __restrict__ cnt)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const SceneDev& sc = scenes[tag[i] & ~kPadBit];
+    const GridDev& g = sc.g;
+    const float4 p = pos[i];
+    const int sx = sub_coord(p.x, g.ox, g.inv_h, g.dx);
+    const int sy = sub_coord(p.y, g.oy, g.inv_h, g.dy);
+    const int sz = sub_coord(p.z, g.oz, g.inv_h, g.dz);
+    const uint32_t cell = sc.cell_off +
+                          ((uint32_t)(sz >> 1) * (uint32_t)g.dy + (uint32_t)(sy >> 1)) * (uint32_t)g.dx +
+                          (uint32_t)(sx >> 1);
+    keys[i] = cell;
+    rank[i] = atomicAdd(cnt + cell, 1u);
+}
+
+constexpr int kScanBlock = 1024;
+constexpr int kScanPer = 4;
+constexpr int kScanTile = kScanBlock * kScanPer;
+
+// Block-wide inclusive scan of one value per thread; returns the inclusive
+// sum, *total receives the block total.
+__device__ __forceinline__ uint32_t block_scan(uint32_t x, uint32_t* warp_sums, uint32_t* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_sums[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t r = x + (warp > 0 ? warp_sums[warp - 1] : 0u);
+    *total = warp_sums[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ void load_tile(const uint32_t* data, int64_t total, int64_t i0, uint32_t v[kScanPer])
+{
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) v[k] = i0 + k < total ? data[i0 + k] : 0u;
+}
+
+// tile_sums[b] = sum of tile b
+__global__ void __launch_bounds__(kScanBlock) k_scan_tiles(const uint32_t* __restrict__ data, int64_t total,
+                                                           uint32_t* __restrict__ tile_sums)
+{
+    __shared__ uint32_t ws[32];
+    const int64_t i0 = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    uint32_t v[kScanPer];
+    load_tile(data, total, i0, v);
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) s += v[k];
+    uint32_t tot;
+    block_scan(s, ws, &tot);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+// exclusive scan of the nt tile sums in place (one block, chunks with carry)
+__global__ void __launch_bounds__(kScanBlock) k_scan_sums(uint32_t* __restrict__ sums, int64_t nt)
+{
+    __shared__ uint32_t ws[32];
+    uint32_t carry = 0;
+    for (int64_t b = 0; b < nt; b += kScanBlock) {
+        const int64_t i = b + threadIdx.x;
+        const uint32_t x = i < nt ? sums[i] : 0u;
+        uint32_t tot;
+        const uint32_t inc = block_scan(x, ws, &tot);
+        if (i < nt) sums[i] = carry + inc - x;
+        carry += tot;
+    }
+}
+
+// exclusive scan of every tile plus its tile offset, in place
+__global__ void __launch_bounds__(kScanBlock) k_scan_apply(uint32_t* __restrict__ data, int64_t total,
+                                                           const uint32_t* __restrict__ tile_sums)
+{
+    __shared__ uint32_t ws[32];
+    const int64_t i0 = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    uint32_t v[kScanPer];
+    load_tile(data, total, i0, v);
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) s += v[k];
+    uint32_t tot;
+    const uint32_t inc = block_scan(s, ws, &tot);
+    uint32_t run = tile_sums[blockIdx.x] + inc - s;
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k) {
+        const uint32_t t = v[k];
+        if (i0 + k < total) data[i0 + k] = run;
+        run += t;
+    }
+}
+
+__global__ void k_cs_scatter(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ rank, int64_t n,
+                             const uint32_t* __restrict__ start, uint32_t* __restrict__ out_keys,
+                             uint32_t* __restrict__ out_idx)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t k = keys[i];
+    const uint32_t pos = start[k] + rank[i];
+    out_keys[pos] = k;
+    out_idx[pos] = (uint32_t)i;
+}
+
+// every cell's entries in ascending item order (insertion sort; a cell holds
+// a handful of LR particles)
+__global__ void k_cs_order(const uint32_t* __restrict__ start, int64_t n_cell, uint32_t* __restrict__ idx)
+{
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n_cell) return;
+    const uint32_t b = start[c], e = start[c + 1];
+    for (uint32_t j = b + 1; j < e; ++j) {
+        const uint32_t v = idx[j];
+        uint32_t k = j;
+        while (k > b && idx[k - 1] > v) {
+            idx[k] = idx[k - 1];
+            --k;
+        }
+        idx[k] = v;
+    }
+}
+
 __global__ void k_cell_start(const uint32_t* __restrict__ sk, int64_t n, int64_t n_cell, uint32_t* __restrict__ start)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -295,6 +441,33 @@ cudaError_t gs_radix_sort(cudaStream_t s, uint32_t* keys[2], uint32_t* vals[2], 
         k_rs_scatter<<<(unsigned)nb, kThreads, 0, s>>>(keys[a], vals[a], keys[b], vals[b], n, shift, items, hist, nb);
         *launches += 3;
         *which = b;
+    }
+    return cudaGetLastError();
+}
+
+size_t gs_scan_aux_words(int64_t total) { return (size_t)std::max<int64_t>(1, (total + kScanTile - 1) / kScanTile); }
+
+cudaError_t gs_count_sort_cells(cudaStream_t s, const float4* pos, int64_t n, const SceneDev* scenes,
+                                const uint32_t* tag, int64_t n_cell, uint32_t* keys, uint32_t* rank,
+                                uint32_t* out_keys, uint32_t* out_idx, uint32_t* cell_start, uint32_t* aux,
+                                int64_t* launches)
+{
+    cudaError_t e = cudaMemsetAsync(cell_start, 0, (size_t)(n_cell + 1) * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+        k_cs_keys<<<gs_blocks(n, 256), 256, 0, s>>>(pos, n, scenes, tag, keys, rank, cell_start);
+        *launches += 1;
+    }
+    const int64_t total = n_cell + 1;
+    const int64_t nt = (total + kScanTile - 1) / kScanTile;
+    k_scan_tiles<<<(unsigned)nt, kScanBlock, 0, s>>>(cell_start, total, aux);
+    k_scan_sums<<<1, kScanBlock, 0, s>>>(aux, nt);
+    k_scan_apply<<<(unsigned)nt, kScanBlock, 0, s>>>(cell_start, total, aux);
+    *launches += 3;
+    if (n > 0) {
+        k_cs_scatter<<<gs_blocks(n, 256), 256, 0, s>>>(keys, rank, n, cell_start, out_keys, out_idx);
+        k_cs_order<<<gs_blocks(n_cell, 256), 256, 0, s>>>(cell_start, n_cell, out_idx);
+        *launches += 2;
     }
     return cudaGetLastError();
 }

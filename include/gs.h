@@ -239,6 +239,16 @@ int gs_frame(gs_ctx* ctx, float dt, int n_sub, int iters);
 /* Enable (1) or disable (0) CUDA-graph replay of gs_frame. */
 int gs_set_graphs(gs_ctx* ctx, int enable);
 
+/* How gs_step_low runs the n_stab + iters Jacobi passes of a step: 1 = one
+ * persistent cooperative launch whose blocks are all resident and meet at a
+ * grid barrier between passes (where the device supports cooperative
+ * launches); 0 (the default) = one launch per pass, which measured faster
+ * when frames are replayed as CUDA graphs.  Both give the same bits.  A barrier
+ * that waits longer than about a second gives up and the next gs_sync or
+ * gs_read returns GS_ERR_TIMEOUT.  Does not apply to the functional forms
+ * (gs_step_low_forward / _backward), which keep every pass's input. */
+int gs_set_lr_solver(gs_ctx* ctx, int persistent);
+
 /* Launch shape of the upsampling kernel: warps per block (4, 8 or 16) and
  * blocks per SM of a persistent grid that pulls 32-particle work items from
  * an atomic counter (0: one warp per item, no persistent loop). */

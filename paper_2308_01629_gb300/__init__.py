@@ -88,6 +88,7 @@ _SIGS = {
     "gs_scene_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(gs_scene_layout)]),
     "gs_frame": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_int, ctypes.c_int]),
     "gs_set_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gs_set_lr_solver": (ctypes.c_int, [_P, ctypes.c_int]),
     "gs_set_tuning": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "gs_autotune": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
@@ -172,6 +173,10 @@ def gs_frame(ctx, dt, n_sub, iters):
 
 def gs_set_graphs(ctx, enable):
     return lib().gs_set_graphs(ctx, int(enable))
+
+
+def gs_set_lr_solver(ctx, persistent):
+    return lib().gs_set_lr_solver(ctx, int(persistent))
 
 
 def gs_set_tuning(ctx, warps_per_block, blocks_per_sm):
@@ -417,6 +422,9 @@ class Context:
 
     def set_graphs(self, on=True):
         return _check(self.ctx, gs_set_graphs(self.ctx, on), "gs_set_graphs")
+
+    def set_lr_solver(self, persistent=True):
+        return _check(self.ctx, gs_set_lr_solver(self.ctx, persistent), "gs_set_lr_solver")
 
     def set_tuning(self, warps_per_block, blocks_per_sm):
         return _check(self.ctx, gs_set_tuning(self.ctx, warps_per_block, blocks_per_sm), "gs_set_tuning")

@@ -89,6 +89,8 @@ int report_device_errors(gs_ctx* c)
             return fail(c, GS_ERR_CAPACITY, "an LR particle had more than %d candidate partners (max_neighbors)",
                         c->nbr_cap);
         if (e & GS_DEVERR_BAD_ID) return fail(c, GS_ERR_STATE, "HR id outside [0, n_high) met while unpermuting");
+        if (e & GS_DEVERR_BARRIER_TIMEOUT)
+            return fail(c, GS_ERR_TIMEOUT, "a grid barrier of the persistent LR solver timed out; results are invalid");
     }
     return GS_OK;
 }
@@ -277,6 +279,9 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
 
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+    int coop = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
+    if (e == cudaSuccess && coop) c->solve_blocks = gs_solve_blocks(c->sm_count);
     if (e != cudaSuccess) {
         delete c;
         return GS_ERR_CUDA;
@@ -327,6 +332,7 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
     A(dalloc(&c->sort_hist, c->sort_hist_cap));
     A(dalloc(&c->d_work, 1));
     A(dalloc(&c->d_err, 1));
+    A(dalloc(&c->d_bar, 2));
     if (ok) ok = cudaMallocHost((void**)&c->h_err, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -457,17 +463,27 @@ int step_low_impl(gs_ctx* c, float dt, int iters)
     CK(gs_launch_step_gather(c->stream, N, c->lr_sorted_idx, c->lr_xt, c->lr_pos, c->s_xt[0], c->s_x[0],
                              &c->launches),
        "gather");
-    CK(gs_launch_neighbors(c->stream, a, c->s_xt[0], c->lr_sorted_keys, c->lr_cell_start, c->nbr, c->nbr_cnt,
+    CK(gs_launch_neighbors(c->stream, a, c->s_xt[0], c->lr_sorted_keys, c->lr_cell_start, c->n_cell_total, c->nbr, c->nbr_cnt,
                            c->nbr_cap, c->d_err, &c->launches),
        "neighbours");
     int bx = 0, bt = 0;   // buffers holding the current x and xt
-    for (int it = 0; it < c->n_stab + iters; ++it) {
-        const int stab = it < c->n_stab;
-        CK(gs_launch_pass(c->stream, a, stab, c->s_x[bx], c->s_xt[bt], c->s_x[bx ^ 1], c->s_xt[bt ^ 1], c->nbr,
-                          c->nbr_cnt, &c->launches),
-           "pass");
-        bt ^= 1;
-        if (stab) bx ^= 1;
+    if (c->use_solver && c->solve_blocks > 0) {
+        // all passes in one cooperative launch; the buffers alternate as in
+        // the loop below
+        CK(gs_launch_solve(c->stream, a, c->n_stab, iters, c->s_x, c->s_xt, c->nbr, c->nbr_cnt, c->d_bar, c->d_err,
+                           c->solve_blocks, &c->launches),
+           "solver");
+        bt = (c->n_stab + iters) & 1;
+        bx = c->n_stab & 1;
+    } else {
+        for (int it = 0; it < c->n_stab + iters; ++it) {
+            const int stab = it < c->n_stab;
+            CK(gs_launch_pass(c->stream, a, stab, c->s_x[bx], c->s_xt[bt], c->s_x[bx ^ 1], c->s_xt[bt ^ 1], c->nbr,
+                              c->nbr_cnt, &c->launches),
+               "pass");
+            bt ^= 1;
+            if (stab) bx ^= 1;
+        }
     }
     CK(gs_launch_finalize(c->stream, a, c->lr_sorted_idx, c->s_x[bx], c->s_xt[bt], c->lr_pos, c->lr_vel,
                           &c->launches),
@@ -538,7 +554,7 @@ void gs_destroy(gs_ctx* c)
                     c->hr_pos[0],  c->hr_pos[1],  c->hr_vel[0],  c->hr_vel[1],  c->hr_keys[0], c->hr_keys[1],
                     c->hr_vals[0], c->hr_vals[1], c->nbr,        c->nbr_cnt,    c->tmp4,      c->sort_hist,
                     c->d_work,     c->d_err,      c->gXs,        c->gVs,       c->snap,      c->snap_xt,
-                    c->adj_gx,     c->adj_gxt,    c->adj_h,      c->adj_gws,   c->scan_aux};
+                    c->adj_gx,     c->adj_gxt,    c->adj_h,      c->adj_gws,   c->scan_aux,   c->d_bar};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->h_err) cudaFreeHost(c->h_err);
@@ -812,6 +828,15 @@ int gs_set_graphs(gs_ctx* c, int enable)
     return GS_OK;
 }
 
+int gs_set_lr_solver(gs_ctx* c, int persistent)
+{
+    int st = check_state(c);
+    if (st) return st;
+    c->use_solver = persistent != 0;
+    drop_graphs(c);
+    return GS_OK;
+}
+
 int gs_set_tuning(gs_ctx* c, int warps_per_block, int blocks_per_sm)
 {
     int st = check_state(c);
@@ -999,7 +1024,7 @@ int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const 
     CK(gs_launch_step_gather(c->stream, N, c->lr_sorted_idx, c->lr_xt, c->lr_pos, c->s_xt[0], c->s_x[0],
                              &c->launches),
        "gather");
-    CK(gs_launch_neighbors(c->stream, a, c->s_xt[0], c->lr_sorted_keys, c->lr_cell_start, c->nbr, c->nbr_cnt,
+    CK(gs_launch_neighbors(c->stream, a, c->s_xt[0], c->lr_sorted_keys, c->lr_cell_start, c->n_cell_total, c->nbr, c->nbr_cnt,
                            c->nbr_cap, c->d_err, &c->launches),
        "neighbours");
     int bx = 0, bt = 0;

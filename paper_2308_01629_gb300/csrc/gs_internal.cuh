@@ -47,6 +47,7 @@ struct SceneDev {
 enum : int {
     GS_DEVERR_NEIGHBOR_CAP = 1,   // an LR particle had more candidates than max_neighbors
     GS_DEVERR_BAD_ID = 2,         // an HR id outside [0, n_high) was met while unpermuting
+    GS_DEVERR_BARRIER_TIMEOUT = 4,   // a grid barrier of the persistent LR solver gave up waiting
 };
 
 // HR slot tag: scene index, with this bit set on padding slots.
@@ -142,6 +143,9 @@ struct gs_ctx {
 
     // errors
     int* d_err = nullptr;
+    unsigned* d_bar = nullptr;   // grid-barrier words of the persistent LR solver
+    int solve_blocks = 0;        // resident blocks of the solver; 0 = per-pass launches
+    bool use_solver = false;    // per-pass launches by default: faster under graph replay
     int* h_err = nullptr;                         // pinned
     std::string last_error;
     bool poisoned = false;
@@ -225,11 +229,19 @@ cudaError_t gs_launch_predict(cudaStream_t s, const PbdArgs& a, const float4* po
 cudaError_t gs_launch_step_gather(cudaStream_t s, int64_t n, const uint32_t* idx, const float4* xt,
                                   const float4* pos, float4* s_xt, float4* s_x, int64_t* launches);
 cudaError_t gs_launch_neighbors(cudaStream_t s, const PbdArgs& a, const float4* s_xt, const uint32_t* skeys,
-                                const uint32_t* cell_start, uint32_t* nbr, uint32_t* cnt, int cap, int* err,
-                                int64_t* launches);
+                                const uint32_t* cell_start, int64_t n_cell, uint32_t* nbr, uint32_t* cnt, int cap,
+                                int* err, int64_t* launches);
 cudaError_t gs_launch_pass(cudaStream_t s, const PbdArgs& a, int stab, const float4* x_in, const float4* xt_in,
                            float4* x_out, float4* xt_out, const uint32_t* nbr, const uint32_t* cnt,
                            int64_t* launches);
+// All n_stab + iters passes of one step in one cooperative launch of at most
+// max_blocks blocks (gs_solve_blocks: the blocks that fit on the GPU at
+// once), with grid barriers between passes.  bar: two words of scratch.
+// The result lands where the per-pass loop would leave it.
+int gs_solve_blocks(int sm_count);
+cudaError_t gs_launch_solve(cudaStream_t s, const PbdArgs& a, int n_stab, int iters, float4* x[2], float4* xt[2],
+                            const uint32_t* nbr, const uint32_t* cnt, unsigned* bar, int* err, int max_blocks,
+                            int64_t* launches);
 cudaError_t gs_launch_finalize(cudaStream_t s, const PbdArgs& a, const uint32_t* idx, const float4* s_x,
                                const float4* s_xt, float4* pos, float4* vel, int64_t* launches);
 

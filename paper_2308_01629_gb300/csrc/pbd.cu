@@ -18,6 +18,8 @@
 // solver passes evaluate and move xt.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "gs_internal.cuh"
 #include "pbd_common.cuh"
 #include "sdf.cuh"
@@ -48,62 +50,89 @@ __global__ void k_step_gather(int64_t n, const uint32_t* __restrict__ idx, const
 }
 
 // Candidate partners of every particle within the neighbour radius, in
-// ascending sorted index row by row of the 27 surrounding cells.  Four lanes
-// share one particle and take every fourth candidate of a row; a ballot over
-// the four keeps the list in ascending order.
-constexpr int kNbrLanes = 4;
-
+// ascending sorted index row by row of the 27 surrounding cells.  One warp
+// per cell: the particles of a cell share their 27-cell candidate set, so
+// the warp walks it once, 32 candidates at a time (lane j takes flat
+// candidate j of the concatenated row ranges), and for each particle of the
+// cell a ballot keeps its accepted candidates in ascending order.
 __global__ void __launch_bounds__(128) k_neighbors(const PbdArgs a, const float4* __restrict__ s_xt,
-                                                   const uint32_t* __restrict__ skeys,
-                                                   const uint32_t* __restrict__ cell_start, uint32_t* __restrict__ nbr,
-                                                   uint32_t* __restrict__ cnt, int cap, int* err)
+                                                   const uint32_t* __restrict__ cell_start, int64_t n_cell,
+                                                   uint32_t* __restrict__ nbr, uint32_t* __restrict__ cnt, int cap,
+                                                   int* err)
 {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t p = t / kNbrLanes;
-    const int sub = (int)(t % kNbrLanes);
-    const int gbase = (int)(threadIdx.x & 31u) & ~(kNbrLanes - 1);
-    const unsigned gmask = ((1u << kNbrLanes) - 1u) << gbase;
-    if (p >= a.n) return;   // the four lanes of a particle leave together
-    const SceneDev& sc = a.scenes[a.lr_scene[p]];
+    const int lane = (int)(threadIdx.x & 31u);
+    const int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (cell >= n_cell) return;                       // whole warps leave together
+    const uint32_t pb = __ldg(cell_start + cell), pe = __ldg(cell_start + cell + 1);
+    if (pb == pe) return;
+    const SceneDev& sc = a.scenes[a.lr_scene[pb]];
     const GridDev& g = sc.g;
-    const float4 xp = s_xt[p];
-    const uint32_t c = skeys[p] - sc.cell_off;
+    const uint32_t c = (uint32_t)(cell - sc.cell_off);
     const int cx = (int)(c % (uint32_t)g.dx);
     const int cy = (int)((c / (uint32_t)g.dx) % (uint32_t)g.dy);
     const int cz = (int)(c / ((uint32_t)g.dx * (uint32_t)g.dy));
     const float rc2 = sc.rc * sc.rc;
     const int x0 = cx > 0 ? cx - 1 : 0, x1 = cx + 1 < g.dx ? cx + 1 : g.dx - 1;
-    const unsigned below = (1u << sub) - 1u;
-    int k = 0;
-    for (int z = cz - 1; z <= cz + 1; ++z) {
-        if (z < 0 || z >= g.dz) continue;
-        for (int y = cy - 1; y <= cy + 1; ++y) {
-            if (y < 0 || y >= g.dy) continue;
+    // lane r < 9 fetches row r = (z, y) of the 3 x 3 rows around the cell
+    uint32_t rb = 0, len = 0;
+    if (lane < 9) {
+        const int z = cz - 1 + lane / 3, y = cy - 1 + lane % 3;
+        if (z >= 0 && z < g.dz && y >= 0 && y < g.dy) {
             const int64_t row = (int64_t)sc.cell_off + ((int64_t)z * g.dy + y) * g.dx;
-            const uint32_t b = cell_start[row + x0], e = cell_start[row + x1 + 1];
-            for (uint32_t q0 = b; q0 < e; q0 += kNbrLanes) {
-                const uint32_t q = q0 + (uint32_t)sub;
-                bool take = false;
-                if (q < e && (int64_t)q != p) {
-                    const float4 xq = s_xt[q];
-                    const float dx = xq.x - xp.x, dy = xq.y - xp.y, dz = xq.z - xp.z;
-                    take = dx * dx + dy * dy + dz * dz < rc2;
-                }
-                const unsigned bal = __ballot_sync(gmask, take) >> gbase;
-                if (take) {
-                    const int pos = k + __popc(bal & below);
-                    if (pos < cap) nbr[(int64_t)pos * a.n + p] = q;
-                }
-                k += __popc(bal);
-            }
+            rb = __ldg(cell_start + row + x0);
+            len = __ldg(cell_start + row + x1 + 1) - rb;
         }
     }
-    if (sub != 0) return;
-    if (k > cap) {
-        atomicOr(err, GS_DEVERR_NEIGHBOR_CAP);
-        k = cap;
+    uint32_t incl = len;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
     }
-    cnt[p] = (uint32_t)k;
+    const uint32_t excl = incl - len;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 8);
+    const unsigned lt = (1u << lane) - 1u;
+    for (uint32_t i0 = pb; i0 < pe; i0 += 32) {       // the cell's particles, 32 at a time
+        const uint32_t mine = i0 + (uint32_t)lane;
+        const bool own = mine < pe;
+        const float4 xo = own ? s_xt[mine] : make_float4(0.f, 0.f, 0.f, 0.f);
+        int k = 0;                                      // lane j: count of particle i0 + j
+        const int np = (int)min(pe - i0, 32u);
+        for (uint32_t base = 0; base < total; base += 32) {
+            const uint32_t f = base + (uint32_t)lane;
+            // row of flat index f: last row whose exclusive prefix is <= f
+            int r = 0;
+#pragma unroll
+            for (int step = 8; step > 0; step >>= 1) {
+                const uint32_t e = __shfl_sync(0xffffffffu, excl, (r + step) & 31);
+                if (r + step < 9 && e <= f) r += step;
+            }
+            const uint32_t q = __shfl_sync(0xffffffffu, rb, r) + (f - __shfl_sync(0xffffffffu, excl, r));
+            const bool in = f < total;
+            const float4 xq = in ? s_xt[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int j = 0; j < np; ++j) {
+                const float px = __shfl_sync(0xffffffffu, xo.x, j);
+                const float py = __shfl_sync(0xffffffffu, xo.y, j);
+                const float pz = __shfl_sync(0xffffffffu, xo.z, j);
+                const float dx = xq.x - px, dy = xq.y - py, dz = xq.z - pz;
+                const bool take = in && q != i0 + (uint32_t)j && dx * dx + dy * dy + dz * dz < rc2;
+                const unsigned bal = __ballot_sync(0xffffffffu, take);
+                const int kj = __shfl_sync(0xffffffffu, k, j);
+                if (take) {
+                    const int pos = kj + __popc(bal & lt);
+                    if (pos < cap) nbr[(int64_t)pos * a.n + i0 + j] = q;
+                }
+                if (lane == j) k += __popc(bal);
+            }
+        }
+        if (own) {
+            if (k > cap) {
+                atomicOr(err, GS_DEVERR_NEIGHBOR_CAP);
+                k = cap;
+            }
+            cnt[mine] = (uint32_t)k;
+        }
+    }
 }
 
 // kLanes lanes share one particle: lane `sub` takes candidates sub, sub +
@@ -111,7 +140,7 @@ __global__ void __launch_bounds__(128) k_neighbors(const PbdArgs a, const float4
 // and the SDF components whose running index is sub modulo kLanes; the
 // partial sums are added with shuffles in a fixed order and lane 0 writes
 // the particle.
-constexpr int kLanes = 4;
+constexpr int kLanes = 2;
 
 struct PassAcc {
     float Dx, Dy, Dz;
@@ -144,23 +173,48 @@ __device__ __forceinline__ void pair_term(PassAcc& acc, const SceneDev& sc, int 
     ++acc.n;
 }
 
-__global__ void __launch_bounds__(128) k_pass(const PbdArgs a, int stab, const float4* __restrict__ x_in,
-                                              const float4* __restrict__ xt_in, float4* __restrict__ x_out,
-                                              float4* __restrict__ xt_out, const uint32_t* __restrict__ nbr,
-                                              const uint32_t* __restrict__ cnt)
+// Loads and stores of the position buffers.  The per-pass kernel reads
+// buffers that no thread of the launch writes.  The persistent solver reads
+// buffers other blocks wrote before the last grid barrier: plain (weak,
+// L1-cacheable) loads, which the barrier's fences order after those writes,
+// but never the non-coherent read-only path a const __restrict__ pointer
+// may select, hence the explicit instruction.
+template <bool kL2>
+__device__ __forceinline__ float4 ld_pos(const float4* p)
 {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t p = t / kLanes;
-    const int sub = (int)(t % kLanes);
-    const bool valid = p < a.n;
+    if constexpr (kL2) {
+        float4 v;
+        asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                     : "l"(p));
+        return v;
+    } else {
+        return *p;
+    }
+}
+template <bool kL2>
+__device__ __forceinline__ void st_pos(float4* p, float4 v)
+{
+    if constexpr (kL2) __stcg(p, v);
+    else *p = v;
+}
+
+// One Jacobi pass of particle p (valid == p < n) by its kLanes lanes; every
+// lane of the warp takes part (the partial sums meet in full-warp shuffles).
+template <bool kL2>
+__device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_t p, bool valid, int sub,
+                                              const float4* __restrict__ x_in, const float4* __restrict__ xt_in,
+                                              float4* __restrict__ x_out, float4* __restrict__ xt_out,
+                                              const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ cnt)
+{
     const SceneDev& sc = a.scenes[valid ? a.lr_scene[p] : 0];
     const float d0 = 2.0f * sc.r_low;
     float4 xtp = make_float4(0.f, 0.f, 0.f, 0.f), xp = xtp;
     int nc = 0;
     if (valid) {
-        xtp = xt_in[p];
-        xp = x_in[p];
-        nc = (int)cnt[p];
+        xtp = ld_pos<kL2>(xt_in + p);
+        xp = ld_pos<kL2>(x_in + p);
+        nc = (int)__ldg(cnt + p);
     }
     const float4 yp = stab ? xp : xtp;          // positions the constraints are evaluated on
     const float wp = xtp.w;                      // inverse height-scaled mass
@@ -169,10 +223,10 @@ __global__ void __launch_bounds__(128) k_pass(const PbdArgs a, int stab, const f
     for (int k = sub; k < nc; k += 2 * kLanes) {
         const int k2 = k + kLanes;
         const bool two = k2 < nc;
-        const uint32_t q1 = nbr[(int64_t)k * a.n + p];
-        const uint32_t q2 = two ? nbr[(int64_t)k2 * a.n + p] : q1;
-        const float4 xtq1 = xt_in[q1], xq1 = x_in[q1];
-        const float4 xtq2 = xt_in[q2], xq2 = x_in[q2];
+        const uint32_t q1 = __ldg(nbr + (int64_t)k * a.n + p);
+        const uint32_t q2 = two ? __ldg(nbr + (int64_t)k2 * a.n + p) : q1;
+        const float4 xtq1 = ld_pos<kL2>(xt_in + q1), xq1 = ld_pos<kL2>(x_in + q1);
+        const float4 xtq2 = ld_pos<kL2>(xt_in + q2), xq2 = ld_pos<kL2>(x_in + q2);
         pair_term(acc, sc, stab, yp, wp, dpx, dpy, dpz, xtq1, xq1, d0);
         if (two) pair_term(acc, sc, stab, yp, wp, dpx, dpy, dpz, xtq2, xq2, d0);
     }
@@ -225,8 +279,91 @@ __global__ void __launch_bounds__(128) k_pass(const PbdArgs a, int stab, const f
             nx.z += uz;
         }
     }
-    xt_out[p] = nt;
-    if (stab) x_out[p] = nx;
+    st_pos<kL2>(xt_out + p, nt);
+    if (stab) st_pos<kL2>(x_out + p, nx);
+}
+
+__global__ void __launch_bounds__(128, 7) k_pass(const PbdArgs a, int stab, const float4* __restrict__ x_in,
+                                              const float4* __restrict__ xt_in, float4* __restrict__ x_out,
+                                              float4* __restrict__ xt_out, const uint32_t* __restrict__ nbr,
+                                              const uint32_t* __restrict__ cnt)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t p = t / kLanes;
+    pass_particle<false>(a, stab, p, p < a.n, (int)(t % kLanes), x_in, xt_in, x_out, xt_out, nbr, cnt);
+}
+
+// ---- all passes of one step in one launch --------------------------------
+// Every block is resident at once (cooperative launch); the passes are
+// separated by a grid barrier.  Its wait is bounded: a block that waits
+// longer than kBarrierSpins polls sets GS_DEVERR_BARRIER_TIMEOUT and leaves,
+// and every other block then times out at the same barrier, so the launch
+// always ends.  The passes, lanes and summation order are those of k_pass,
+// so the two paths give the same bits.
+constexpr unsigned kBarrierSpins = 1u << 24;   // with 32 ns naps and the polls: about one second
+
+struct SolveArgs {
+    PbdArgs a;
+    int n_stab, iters;
+    float4 *x0, *x1, *xt0, *xt1;   // separate fields: an indexed parameter array would go to local memory
+    const uint32_t* nbr;
+    const uint32_t* cnt;
+    unsigned* bar;   // {arrived, generation}, zero at launch
+    int* err;
+};
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned gen, int* err)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicExch(bar + 1, gen);
+        } else {
+            unsigned spins = 0;
+            while (atomicAdd(bar + 1, 0u) != gen) {
+                if (++spins > kBarrierSpins || atomicAdd(err, 0) & GS_DEVERR_BARRIER_TIMEOUT) {
+                    atomicOr(err, GS_DEVERR_BARRIER_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(128, 6) k_solve(const SolveArgs s)
+{
+    const int sub = (int)(threadIdx.x % kLanes);
+    const int64_t groups = (int64_t)gridDim.x * (blockDim.x / kLanes);
+    const int64_t group = (int64_t)blockIdx.x * (blockDim.x / kLanes) + threadIdx.x / kLanes;
+    // the warp's first group decides the trip count, so whole warps iterate
+    const int64_t warp_first = group & ~(int64_t)(32 / kLanes - 1);
+    int bx = 0, bt = 0;
+    const int total = s.n_stab + s.iters;
+    for (int it = 0; it < total; ++it) {
+        const int stab = it < s.n_stab;
+        for (int64_t base = warp_first; base < s.a.n; base += groups) {
+            const int64_t p = base + (group - warp_first);
+            float4* xi = bx ? s.x1 : s.x0;
+            float4* xo = bx ? s.x0 : s.x1;
+            float4* ti = bt ? s.xt1 : s.xt0;
+            float4* to = bt ? s.xt0 : s.xt1;
+            pass_particle<true>(s.a, stab, p, p < s.a.n, sub, xi, ti, xo, to, s.nbr, s.cnt);
+        }
+        bt ^= 1;
+        if (stab) bx ^= 1;
+        if (it + 1 < total && !grid_barrier(s.bar, gridDim.x, (unsigned)it + 1u, s.err)) return;
+    }
 }
 
 __global__ void k_finalize(const PbdArgs a, const uint32_t* __restrict__ idx, const float4* __restrict__ s_x,
@@ -261,11 +398,12 @@ cudaError_t gs_launch_step_gather(cudaStream_t s, int64_t n, const uint32_t* idx
 }
 
 cudaError_t gs_launch_neighbors(cudaStream_t s, const PbdArgs& a, const float4* s_xt, const uint32_t* skeys,
-                                const uint32_t* cell_start, uint32_t* nbr, uint32_t* cnt, int cap, int* err,
-                                int64_t* launches)
+                                const uint32_t* cell_start, int64_t n_cell, uint32_t* nbr, uint32_t* cnt, int cap,
+                                int* err, int64_t* launches)
 {
+    (void)skeys;
     if (a.n <= 0) return cudaSuccess;
-    k_neighbors<<<gs_blocks(a.n * kNbrLanes, 128), 128, 0, s>>>(a, s_xt, skeys, cell_start, nbr, cnt, cap, err);
+    k_neighbors<<<gs_blocks(n_cell * 32, 128), 128, 0, s>>>(a, s_xt, cell_start, n_cell, nbr, cnt, cap, err);
     *launches += 1;
     return cudaGetLastError();
 }
@@ -278,6 +416,40 @@ cudaError_t gs_launch_pass(cudaStream_t s, const PbdArgs& a, int stab, const flo
     k_pass<<<gs_blocks(a.n * kLanes, 128), 128, 0, s>>>(a, stab, x_in, xt_in, x_out, xt_out, nbr, cnt);
     *launches += 1;
     return cudaGetLastError();
+}
+
+int gs_solve_blocks(int sm_count)
+{
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve, 128, 0) != cudaSuccess || per_sm <= 0) return 0;
+    return per_sm * sm_count;
+}
+
+cudaError_t gs_launch_solve(cudaStream_t s, const PbdArgs& a, int n_stab, int iters, float4* x[2], float4* xt[2],
+                            const uint32_t* nbr, const uint32_t* cnt, unsigned* bar, int* err, int max_blocks,
+                            int64_t* launches)
+{
+    if (a.n <= 0 || n_stab + iters <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    SolveArgs sa;
+    sa.a = a;
+    sa.n_stab = n_stab;
+    sa.iters = iters;
+    sa.x0 = x[0];
+    sa.x1 = x[1];
+    sa.xt0 = xt[0];
+    sa.xt1 = xt[1];
+    sa.nbr = nbr;
+    sa.cnt = cnt;
+    sa.bar = bar;
+    sa.err = err;
+    int64_t need = (a.n * kLanes + 127) / 128;
+    const int grid = (int)std::min<int64_t>(need, max_blocks);
+    void* args[] = {&sa};
+    e = cudaLaunchCooperativeKernel((const void*)k_solve, dim3((unsigned)grid), dim3(128), args, 0, s);
+    *launches += 1;
+    return e;
 }
 
 cudaError_t gs_launch_finalize(cudaStream_t s, const PbdArgs& a, const uint32_t* idx, const float4* s_x,

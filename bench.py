@@ -52,7 +52,7 @@ FLUSH_BYTES = 512 << 20
 TRAFFIC_CAPTURE = {"source_sha1": None, "bytes": None}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--batch-scenes", type=int, default=256)
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def make_scene(name, bed_size=1.0):
@@ -294,6 +294,24 @@ def run_diff(args, dev, stream, gs, torch):
             "backward_overhead_vs_plain_forward": ms_diff / ms_plain, "library_kernels_per_rollout": nl}
 
 
+def max_over_ranks(x, world, dev):
+    """The largest value of x over all ranks (one all_reduce, outside the
+    timed work); x itself on a single rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units processed by all ranks per second of the slowest rank (weak
+    scaling: every rank processes the same number of units)."""
+    return world * units_per_rank / seconds
+
+
 # ------------------------------------------------------------- GPU arm ---
 def run_gpu(args):
     import torch
@@ -381,12 +399,9 @@ def run_gpu(args):
     bin_ms, bin_n = ctx.timing_read(gs.GS_TIMER_BIN_LOW)
     rs_ms, rs_n = ctx.timing_read(gs.GS_TIMER_RESORT)
     ctx.set_timing(False)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * M * args.steps / (total_ms / 1e3)
+    value = whole_job_rate(M * args.steps, world, total_ms / 1e3)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -419,11 +434,8 @@ def run_gpu(args):
         torch.cuda.synchronize(dev)
         barrier()
         te = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([te], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": world * M * ne / te, "unit": UNIT, "h2d_bytes_per_step": int((2 * N + 2 * M) * 16),
+        te = max_over_ranks(te, world, dev)
+        e2e = {"value": whole_job_rate(M * ne, world, te), "unit": UNIT, "h2d_bytes_per_step": int((2 * N + 2 * M) * 16),
                "d2h_bytes_per_step": int(2 * M * 16), "ms_per_step": 1e3 * te / ne}
 
     ctx.close()

@@ -249,7 +249,7 @@ __device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t ite
 }
 
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 32 / WARPS) k_upsample(const UpsampleArgs a, int persistent)
+__global__ void __launch_bounds__(WARPS * 32, 24 / WARPS) k_upsample(const UpsampleArgs a, int persistent)
 {
     __shared__ float4 s_a[WARPS][kBuf];
     __shared__ float4 s_b[WARPS][kBuf];

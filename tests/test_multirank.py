@@ -1,0 +1,59 @@
+"""Host logic of the multi-rank benchmark on CPU: two gloo ranks, each with
+its own scene replica (weak scaling, no collective on the data path).  The
+timing reduction takes the slowest rank and the whole-job rate counts the
+units of all ranks; the reference arm runs on rank 0 only."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        local_ms = 10.0 + 5.0 * rank                  # rank 1 is the slow one
+        total_ms = bench.max_over_ranks(local_ms, world, torch.device("cpu"))
+        rate = bench.whole_job_rate(1000 * 4, world, total_ms / 1e3)
+        ref = bench.run_reference(bench.parse(["--impl", "reference", "--steps", "1", "--warmup", "0"])) \
+            if rank == 1 else "rank0-skipped"
+        out.put((rank, total_ms, rate, ref))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_reduce_to_the_slowest_and_count_all_units():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, total_ms, rate, ref in res:
+        assert total_ms == 15.0                       # the maximum over both ranks
+        assert rate == pytest.approx(2 * 4000 / 0.015)  # both ranks' units over the slowest time
+    assert res[1][3] is None                          # the reference arm does no work off rank 0
+
+
+def test_single_rank_needs_no_process_group():
+    import bench
+    assert bench.max_over_ranks(3.5, 1, None) == 3.5
+    assert bench.whole_job_rate(100, 1, 0.5) == 200

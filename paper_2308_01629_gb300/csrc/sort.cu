@@ -333,21 +333,53 @@ __global__ void k_cs_scatter(const uint32_t* __restrict__ keys, const uint32_t* 
     out_idx[pos] = (uint32_t)i;
 }
 
-// every cell's entries in ascending item order (insertion sort; a cell holds
-// a handful of LR particles)
+// every cell's entries in ascending item order.  A cell holds a handful of
+// LR particles: its entries are loaded at once into registers (padded with
+// the largest key) and ordered by a fixed compare-exchange network; larger
+// cells fall back to an insertion sort in place.
+template <int K>
+__device__ __forceinline__ void order_small(uint32_t* __restrict__ idx, uint32_t b, uint32_t n)
+{
+    uint32_t v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = (uint32_t)k < n ? idx[b + k] : 0xffffffffu;
+#pragma unroll
+    for (int i = 0; i < K - 1; ++i) {
+#pragma unroll
+        for (int j = 0; j < K - 1 - i; ++j) {
+            const uint32_t lo = min(v[j], v[j + 1]), hi = max(v[j], v[j + 1]);
+            v[j] = lo;
+            v[j + 1] = hi;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        if ((uint32_t)k < n) idx[b + k] = v[k];
+}
+
 __global__ void k_cs_order(const uint32_t* __restrict__ start, int64_t n_cell, uint32_t* __restrict__ idx)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_cell) return;
     const uint32_t b = start[c], e = start[c + 1];
-    for (uint32_t j = b + 1; j < e; ++j) {
-        const uint32_t v = idx[j];
-        uint32_t k = j;
-        while (k > b && idx[k - 1] > v) {
-            idx[k] = idx[k - 1];
-            --k;
+    const uint32_t n = e - b;
+    if (n <= 1) return;
+    if (n <= 4) {
+        order_small<4>(idx, b, n);
+    } else if (n <= 8) {
+        order_small<8>(idx, b, n);
+    } else if (n <= 16) {
+        order_small<16>(idx, b, n);
+    } else {
+        for (uint32_t j = b + 1; j < e; ++j) {
+            const uint32_t v = idx[j];
+            uint32_t k = j;
+            while (k > b && idx[k - 1] > v) {
+                idx[k] = idx[k - 1];
+                --k;
+            }
+            idx[k] = v;
         }
-        idx[k] = v;
     }
 }
 

@@ -396,11 +396,16 @@ int resort_high_impl(gs_ctx* c)
 int bin_low_impl(gs_ctx* c)
 {
     Timed t(c, GS_TIMER_BIN_LOW);
-    int st = bin_low_at(c, c->lr_pos);
-    if (st) return st;
-    CK(gs_launch_gather2(c->stream, c->lr_sorted_idx, c->lr_pos, c->lr_vel, c->lr_spos, c->lr_svel, c->n_low,
-                         &c->launches),
-       "gather");
+    // counting sort by cell; its last stage copies pos and vel into cell order
+    CK(gs_cs_clear(c->stream, c->lr_cell_start, c->n_cell_total), "clear counts");
+    CK(gs_cs_keys(c->stream, c->lr_pos, c->n_low, c->d_scenes, c->lr_scene, c->lr_keys[0], c->lr_vals[0],
+                  c->lr_cell_start, &c->launches),
+       "cell keys");
+    CK(gs_cs_finish(c->stream, c->n_low, c->n_cell_total, c->lr_keys[0], c->lr_vals[0], c->lr_keys[1], c->lr_vals[1],
+                    c->lr_cell_start, c->scan_aux, c->lr_pos, c->lr_vel, c->lr_spos, c->lr_svel, &c->launches),
+       "bin by cell");
+    c->lr_sorted_keys = c->lr_keys[1];
+    c->lr_sorted_idx = c->lr_vals[1];
     c->lr_binned = true;
     return GS_OK;
 }
@@ -457,12 +462,17 @@ int step_low_impl(gs_ctx* c, float dt, int iters)
     if (N == 0) return GS_OK;
     Timed t(c, GS_TIMER_STEP_LOW);
     PbdArgs a = pbd_args(c, dt);
-    CK(gs_launch_predict(c->stream, a, c->lr_pos, c->lr_vel, c->lr_xt, &c->launches), "predict");
-    int st = bin_low_at(c, c->lr_xt);
-    if (st) return st;
-    CK(gs_launch_step_gather(c->stream, N, c->lr_sorted_idx, c->lr_xt, c->lr_pos, c->s_xt[0], c->s_x[0],
-                             &c->launches),
-       "gather");
+    // prediction fused with the counting stage of the binning of x~; the
+    // binning's last stage copies x~ and x into cell order
+    CK(gs_cs_clear(c->stream, c->lr_cell_start, c->n_cell_total), "clear counts");
+    CK(gs_launch_predict_keys(c->stream, a, c->lr_pos, c->lr_vel, c->lr_xt, c->lr_keys[0], c->lr_vals[0],
+                              c->lr_cell_start, &c->launches),
+       "predict");
+    CK(gs_cs_finish(c->stream, N, c->n_cell_total, c->lr_keys[0], c->lr_vals[0], c->lr_keys[1], c->lr_vals[1],
+                    c->lr_cell_start, c->scan_aux, c->lr_xt, c->lr_pos, c->s_xt[0], c->s_x[0], &c->launches),
+       "bin by cell");
+    c->lr_sorted_keys = c->lr_keys[1];
+    c->lr_sorted_idx = c->lr_vals[1];
     CK(gs_launch_neighbors(c->stream, a, c->s_xt[0], c->lr_sorted_keys, c->lr_cell_start, c->n_cell_total, c->nbr, c->nbr_cnt,
                            c->nbr_cap, c->d_err, &c->launches),
        "neighbours");
@@ -476,13 +486,21 @@ int step_low_impl(gs_ctx* c, float dt, int iters)
         bt = (c->n_stab + iters) & 1;
         bx = c->n_stab & 1;
     } else {
-        for (int it = 0; it < c->n_stab + iters; ++it) {
+        // the last pass also finalizes (v = (x~ - x) / dt, x = x~, original order)
+        const int total = c->n_stab + iters;
+        for (int it = 0; it < total; ++it) {
             const int stab = it < c->n_stab;
+            const bool last = it + 1 == total;
             CK(gs_launch_pass(c->stream, a, stab, c->s_x[bx], c->s_xt[bt], c->s_x[bx ^ 1], c->s_xt[bt ^ 1], c->nbr,
-                              c->nbr_cnt, &c->launches),
+                              c->nbr_cnt, &c->launches, last ? c->lr_sorted_idx : nullptr,
+                              last ? c->lr_pos : nullptr, last ? c->lr_vel : nullptr),
                "pass");
             bt ^= 1;
             if (stab) bx ^= 1;
+        }
+        if (total > 0) {
+            c->lr_binned = false;   // the binning above is of the predicted positions
+            return GS_OK;
         }
     }
     CK(gs_launch_finalize(c->stream, a, c->lr_sorted_idx, c->s_x[bx], c->s_xt[bt], c->lr_pos, c->lr_vel,

@@ -176,6 +176,16 @@ cudaError_t gs_launch_cell_keys(cudaStream_t s, const float4* pos, int64_t n, Gr
 // (n_cell + 1 entries) the start of every cell.  aux holds
 // gs_scan_aux_words(n_cell + 1) words.
 size_t gs_scan_aux_words(int64_t total);
+// The same sort in stages, so that the keys can come from a fused kernel:
+// clear the counts, count (keys + arrival ranks; gs_cs_keys or a kernel
+// that does the same with grid_cell_of), then scan + scatter + per-cell
+// order; finish also copies ga / gb (when not null) into cell order.
+cudaError_t gs_cs_clear(cudaStream_t s, uint32_t* cell_start, int64_t n_cell);
+cudaError_t gs_cs_keys(cudaStream_t s, const float4* pos, int64_t n, const SceneDev* scenes, const uint32_t* tag,
+                       uint32_t* keys, uint32_t* rank, uint32_t* cell_start, int64_t* launches);
+cudaError_t gs_cs_finish(cudaStream_t s, int64_t n, int64_t n_cell, const uint32_t* keys, const uint32_t* rank,
+                         uint32_t* out_keys, uint32_t* out_idx, uint32_t* cell_start, uint32_t* aux, const float4* ga,
+                         const float4* gb, float4* ga_out, float4* gb_out, int64_t* launches);
 cudaError_t gs_count_sort_cells(cudaStream_t s, const float4* pos, int64_t n, const SceneDev* scenes,
                                 const uint32_t* tag, int64_t n_cell, uint32_t* keys, uint32_t* rank,
                                 uint32_t* out_keys, uint32_t* out_idx, uint32_t* cell_start, uint32_t* aux,
@@ -231,9 +241,16 @@ cudaError_t gs_launch_step_gather(cudaStream_t s, int64_t n, const uint32_t* idx
 cudaError_t gs_launch_neighbors(cudaStream_t s, const PbdArgs& a, const float4* s_xt, const uint32_t* skeys,
                                 const uint32_t* cell_start, int64_t n_cell, uint32_t* nbr, uint32_t* cnt, int cap,
                                 int* err, int64_t* launches);
+// One Jacobi pass.  With fin_idx not null the pass is the step's last: it
+// writes the finalized position and velocity to original order (fin_pos,
+// fin_vel through fin_idx) instead of x_out / xt_out.
 cudaError_t gs_launch_pass(cudaStream_t s, const PbdArgs& a, int stab, const float4* x_in, const float4* xt_in,
                            float4* x_out, float4* xt_out, const uint32_t* nbr, const uint32_t* cnt,
-                           int64_t* launches);
+                           int64_t* launches, const uint32_t* fin_idx = nullptr, float4* fin_pos = nullptr,
+                           float4* fin_vel = nullptr);
+// Prediction + cell keys + arrival ranks (the counting stage of the binning).
+cudaError_t gs_launch_predict_keys(cudaStream_t s, const PbdArgs& a, const float4* pos, const float4* vel,
+                                   float4* xt, uint32_t* keys, uint32_t* rank, uint32_t* cnt, int64_t* launches);
 // All n_stab + iters passes of one step in one cooperative launch of at most
 // max_blocks blocks (gs_solve_blocks: the blocks that fit on the GPU at
 // once), with grid barriers between passes.  bar: two words of scratch.

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 
+#include "grid.cuh"
 #include "gs_internal.cuh"
 #include "pbd_common.cuh"
 #include "sdf.cuh"
@@ -37,6 +38,25 @@ __global__ void k_predict(const PbdArgs a, const float4* __restrict__ pos, const
     // 1/m* = (1/m) e^{h(x)}, h = k (z - ground), at the start-of-step position
     float ws = x.w * expf(sc.mass_k * (x.z - sc.ground_z));
     xt[i] = make_float4(x.x + a.dt * vx, x.y + a.dt * vy, x.z + a.dt * vz, ws);
+}
+
+// Prediction fused with the first stage of the binning: x~ as above, then
+// the cell of x~ under the grid contract and its arrival rank in the cell.
+__global__ void k_predict_keys(const PbdArgs a, const float4* __restrict__ pos, const float4* __restrict__ vel,
+                               float4* __restrict__ xt, uint32_t* __restrict__ keys, uint32_t* __restrict__ rank,
+                               uint32_t* __restrict__ cnt)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const SceneDev& sc = a.scenes[a.lr_scene[i]];
+    float4 x = pos[i], v = vel[i];
+    float vx = v.x + a.dt * sc.gx, vy = v.y + a.dt * sc.gy, vz = v.z + a.dt * sc.gz;
+    float ws = x.w * expf(sc.mass_k * (x.z - sc.ground_z));
+    const float4 p = make_float4(x.x + a.dt * vx, x.y + a.dt * vy, x.z + a.dt * vz, ws);
+    xt[i] = p;
+    const uint32_t cell = grid_cell_of(sc, p.x, p.y, p.z);
+    keys[i] = cell;
+    rank[i] = atomicAdd(cnt + cell, 1u);
 }
 
 __global__ void k_step_gather(int64_t n, const uint32_t* __restrict__ idx, const float4* __restrict__ xt,
@@ -201,11 +221,20 @@ __device__ __forceinline__ void st_pos(float4* p, float4 v)
 
 // One Jacobi pass of particle p (valid == p < n) by its kLanes lanes; every
 // lane of the warp takes part (the partial sums meet in full-warp shuffles).
+// Finalize of the step (last loop of Algorithm 1) folded into its last pass:
+// v = (x~ - x) / dt and x = x~, written to original order through idx.
+struct FinalOut {
+    const uint32_t* idx;   // null: write the pass's outputs instead
+    float4* pos;
+    float4* vel;
+};
+
 template <bool kL2>
 __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_t p, bool valid, int sub,
                                               const float4* __restrict__ x_in, const float4* __restrict__ xt_in,
                                               float4* __restrict__ x_out, float4* __restrict__ xt_out,
-                                              const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ cnt)
+                                              const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ cnt,
+                                              const FinalOut fin = FinalOut{nullptr, nullptr, nullptr})
 {
     const SceneDev& sc = a.scenes[valid ? a.lr_scene[p] : 0];
     const float d0 = 2.0f * sc.r_low;
@@ -279,6 +308,12 @@ __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_
             nx.z += uz;
         }
     }
+    if (fin.idx) {
+        const uint32_t i = fin.idx[p];
+        fin.vel[i] = make_float4((nt.x - nx.x) / a.dt, (nt.y - nx.y) / a.dt, (nt.z - nx.z) / a.dt, 0.0f);
+        fin.pos[i] = make_float4(nt.x, nt.y, nt.z, nx.w);
+        return;
+    }
     st_pos<kL2>(xt_out + p, nt);
     if (stab) st_pos<kL2>(x_out + p, nx);
 }
@@ -286,11 +321,11 @@ __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_
 __global__ void __launch_bounds__(128, 7) k_pass(const PbdArgs a, int stab, const float4* __restrict__ x_in,
                                               const float4* __restrict__ xt_in, float4* __restrict__ x_out,
                                               float4* __restrict__ xt_out, const uint32_t* __restrict__ nbr,
-                                              const uint32_t* __restrict__ cnt)
+                                              const uint32_t* __restrict__ cnt, const FinalOut fin)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t p = t / kLanes;
-    pass_particle<false>(a, stab, p, p < a.n, (int)(t % kLanes), x_in, xt_in, x_out, xt_out, nbr, cnt);
+    pass_particle<false>(a, stab, p, p < a.n, (int)(t % kLanes), x_in, xt_in, x_out, xt_out, nbr, cnt, fin);
 }
 
 // ---- all passes of one step in one launch --------------------------------
@@ -388,6 +423,15 @@ cudaError_t gs_launch_predict(cudaStream_t s, const PbdArgs& a, const float4* po
     return cudaGetLastError();
 }
 
+cudaError_t gs_launch_predict_keys(cudaStream_t s, const PbdArgs& a, const float4* pos, const float4* vel,
+                                   float4* xt, uint32_t* keys, uint32_t* rank, uint32_t* cnt, int64_t* launches)
+{
+    if (a.n <= 0) return cudaSuccess;
+    k_predict_keys<<<gs_blocks(a.n, 256), 256, 0, s>>>(a, pos, vel, xt, keys, rank, cnt);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
 cudaError_t gs_launch_step_gather(cudaStream_t s, int64_t n, const uint32_t* idx, const float4* xt,
                                   const float4* pos, float4* s_xt, float4* s_x, int64_t* launches)
 {
@@ -410,10 +454,11 @@ cudaError_t gs_launch_neighbors(cudaStream_t s, const PbdArgs& a, const float4* 
 
 cudaError_t gs_launch_pass(cudaStream_t s, const PbdArgs& a, int stab, const float4* x_in, const float4* xt_in,
                            float4* x_out, float4* xt_out, const uint32_t* nbr, const uint32_t* cnt,
-                           int64_t* launches)
+                           int64_t* launches, const uint32_t* fin_idx, float4* fin_pos, float4* fin_vel)
 {
     if (a.n <= 0) return cudaSuccess;
-    k_pass<<<gs_blocks(a.n * kLanes, 128), 128, 0, s>>>(a, stab, x_in, xt_in, x_out, xt_out, nbr, cnt);
+    k_pass<<<gs_blocks(a.n * kLanes, 128), 128, 0, s>>>(a, stab, x_in, xt_in, x_out, xt_out, nbr, cnt,
+                                                        FinalOut{fin_idx, fin_pos, fin_vel});
     *launches += 1;
     return cudaGetLastError();
 }

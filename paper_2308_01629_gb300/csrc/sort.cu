@@ -10,6 +10,7 @@
 
 #include <algorithm>
 
+#include "grid.cuh"
 #include "gs_internal.cuh"
 
 namespace {
@@ -153,15 +154,6 @@ __global__ void __launch_bounds__(kThreads) k_rs_scatter(const uint32_t* __restr
     }
 }
 
-// Grid contract quantization (gs.h): float32, round-to-nearest, no FMA.
-__device__ __forceinline__ int sub_coord(float x, float o, float inv_h, int dim)
-{
-    float a = __fmul_rn(__fsub_rn(x, o), inv_h);
-    float f = floorf(__fmul_rn(a, 2.0f));
-    if (!(f >= 0.0f)) return 0;
-    if (f >= (float)(2 * dim - 1)) return 2 * dim - 1;
-    return (int)f;
-}
 
 __global__ void k_cell_keys(const float4* __restrict__ pos, int64_t n, GridDev g, int fine,
                             uint32_t* __restrict__ keys, uint32_t* __restrict__ vals)
@@ -169,9 +161,9 @@ __global__ void k_cell_keys(const float4* __restrict__ pos, int64_t n, GridDev g
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float4 p = pos[i];
-    int sx = sub_coord(p.x, g.ox, g.inv_h, g.dx);
-    int sy = sub_coord(p.y, g.oy, g.inv_h, g.dy);
-    int sz = sub_coord(p.z, g.oz, g.inv_h, g.dz);
+    int sx = grid_sub_coord(p.x, g.ox, g.inv_h, g.dx);
+    int sy = grid_sub_coord(p.y, g.oy, g.inv_h, g.dy);
+    int sz = grid_sub_coord(p.z, g.oz, g.inv_h, g.dz);
     uint32_t cell = ((uint32_t)(sz >> 1) * (uint32_t)g.dy + (uint32_t)(sy >> 1)) * (uint32_t)g.dx + (uint32_t)(sx >> 1);
     keys[i] = fine ? cell * 8u + (uint32_t)((sz & 1) * 4 + (sy & 1) * 2 + (sx & 1)) : cell;
     vals[i] = (uint32_t)i;
@@ -194,9 +186,9 @@ __global__ void k_scene_keys(const float4* __restrict__ pos, int64_t n, const Sc
     } else {
         const GridDev& g = sc.g;
         float4 p = pos[i];
-        int sx = sub_coord(p.x, g.ox, g.inv_h, g.dx);
-        int sy = sub_coord(p.y, g.oy, g.inv_h, g.dy);
-        int sz = sub_coord(p.z, g.oz, g.inv_h, g.dz);
+        int sx = grid_sub_coord(p.x, g.ox, g.inv_h, g.dx);
+        int sy = grid_sub_coord(p.y, g.oy, g.inv_h, g.dy);
+        int sz = grid_sub_coord(p.z, g.oz, g.inv_h, g.dz);
         uint32_t cell = sc.cell_off +
                         ((uint32_t)(sz >> 1) * (uint32_t)g.dy + (uint32_t)(sy >> 1)) * (uint32_t)g.dx + (uint32_t)(sx >> 1);
         key = fine ? cell * 8u + (uint32_t)((sz & 1) * 4 + (sy & 1) * 2 + (sx & 1)) : cell;
@@ -218,14 +210,8 @@ __global__ void k_cs_keys(const float4* __restrict__ pos, int64_t n, const Scene
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const SceneDev& sc = scenes[tag[i] & ~kPadBit];
-    const GridDev& g = sc.g;
     const float4 p = pos[i];
-    const int sx = sub_coord(p.x, g.ox, g.inv_h, g.dx);
-    const int sy = sub_coord(p.y, g.oy, g.inv_h, g.dy);
-    const int sz = sub_coord(p.z, g.oz, g.inv_h, g.dz);
-    const uint32_t cell = sc.cell_off +
-                          ((uint32_t)(sz >> 1) * (uint32_t)g.dy + (uint32_t)(sy >> 1)) * (uint32_t)g.dx +
-                          (uint32_t)(sx >> 1);
+    const uint32_t cell = grid_cell_of(sc, p.x, p.y, p.z);
     keys[i] = cell;
     rank[i] = atomicAdd(cnt + cell, 1u);
 }
@@ -357,14 +343,17 @@ __device__ __forceinline__ void order_small(uint32_t* __restrict__ idx, uint32_t
         if ((uint32_t)k < n) idx[b + k] = v[k];
 }
 
-__global__ void k_cs_order(const uint32_t* __restrict__ start, int64_t n_cell, uint32_t* __restrict__ idx)
+__global__ void k_cs_order(const uint32_t* __restrict__ start, int64_t n_cell, uint32_t* __restrict__ idx,
+                           const float4* __restrict__ ga, const float4* __restrict__ gb, float4* __restrict__ ga_out,
+                           float4* __restrict__ gb_out)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_cell) return;
     const uint32_t b = start[c], e = start[c + 1];
     const uint32_t n = e - b;
-    if (n <= 1) return;
-    if (n <= 4) {
+    if (n == 0) return;
+    if (n == 1) {
+    } else if (n <= 4) {
         order_small<4>(idx, b, n);
     } else if (n <= 8) {
         order_small<8>(idx, b, n);
@@ -379,6 +368,14 @@ __global__ void k_cs_order(const uint32_t* __restrict__ start, int64_t n_cell, u
                 --k;
             }
             idx[k] = v;
+        }
+    }
+    // the cell's entries of two arrays, copied into cell order
+    if (ga) {
+        for (uint32_t j = b; j < e; ++j) {
+            const uint32_t i = idx[j];
+            ga_out[j] = ga[i];
+            if (gb) gb_out[j] = gb[i];
         }
     }
 }
@@ -479,17 +476,24 @@ cudaError_t gs_radix_sort(cudaStream_t s, uint32_t* keys[2], uint32_t* vals[2], 
 
 size_t gs_scan_aux_words(int64_t total) { return (size_t)std::max<int64_t>(1, (total + kScanTile - 1) / kScanTile); }
 
-cudaError_t gs_count_sort_cells(cudaStream_t s, const float4* pos, int64_t n, const SceneDev* scenes,
-                                const uint32_t* tag, int64_t n_cell, uint32_t* keys, uint32_t* rank,
-                                uint32_t* out_keys, uint32_t* out_idx, uint32_t* cell_start, uint32_t* aux,
-                                int64_t* launches)
+cudaError_t gs_cs_clear(cudaStream_t s, uint32_t* cell_start, int64_t n_cell)
 {
-    cudaError_t e = cudaMemsetAsync(cell_start, 0, (size_t)(n_cell + 1) * sizeof(uint32_t), s);
-    if (e != cudaSuccess) return e;
-    if (n > 0) {
-        k_cs_keys<<<gs_blocks(n, 256), 256, 0, s>>>(pos, n, scenes, tag, keys, rank, cell_start);
-        *launches += 1;
-    }
+    return cudaMemsetAsync(cell_start, 0, (size_t)(n_cell + 1) * sizeof(uint32_t), s);
+}
+
+cudaError_t gs_cs_keys(cudaStream_t s, const float4* pos, int64_t n, const SceneDev* scenes, const uint32_t* tag,
+                       uint32_t* keys, uint32_t* rank, uint32_t* cell_start, int64_t* launches)
+{
+    if (n <= 0) return cudaSuccess;
+    k_cs_keys<<<gs_blocks(n, 256), 256, 0, s>>>(pos, n, scenes, tag, keys, rank, cell_start);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_cs_finish(cudaStream_t s, int64_t n, int64_t n_cell, const uint32_t* keys, const uint32_t* rank,
+                         uint32_t* out_keys, uint32_t* out_idx, uint32_t* cell_start, uint32_t* aux, const float4* ga,
+                         const float4* gb, float4* ga_out, float4* gb_out, int64_t* launches)
+{
     const int64_t total = n_cell + 1;
     const int64_t nt = (total + kScanTile - 1) / kScanTile;
     k_scan_tiles<<<(unsigned)nt, kScanBlock, 0, s>>>(cell_start, total, aux);
@@ -498,10 +502,23 @@ cudaError_t gs_count_sort_cells(cudaStream_t s, const float4* pos, int64_t n, co
     *launches += 3;
     if (n > 0) {
         k_cs_scatter<<<gs_blocks(n, 256), 256, 0, s>>>(keys, rank, n, cell_start, out_keys, out_idx);
-        k_cs_order<<<gs_blocks(n_cell, 256), 256, 0, s>>>(cell_start, n_cell, out_idx);
+        k_cs_order<<<gs_blocks(n_cell, 256), 256, 0, s>>>(cell_start, n_cell, out_idx, ga, gb, ga_out, gb_out);
         *launches += 2;
     }
     return cudaGetLastError();
+}
+
+cudaError_t gs_count_sort_cells(cudaStream_t s, const float4* pos, int64_t n, const SceneDev* scenes,
+                                const uint32_t* tag, int64_t n_cell, uint32_t* keys, uint32_t* rank,
+                                uint32_t* out_keys, uint32_t* out_idx, uint32_t* cell_start, uint32_t* aux,
+                                int64_t* launches)
+{
+    cudaError_t e = gs_cs_clear(s, cell_start, n_cell);
+    if (e == cudaSuccess) e = gs_cs_keys(s, pos, n, scenes, tag, keys, rank, cell_start, launches);
+    if (e == cudaSuccess)
+        e = gs_cs_finish(s, n, n_cell, keys, rank, out_keys, out_idx, cell_start, aux, nullptr, nullptr, nullptr,
+                         nullptr, launches);
+    return e;
 }
 
 cudaError_t gs_launch_cell_keys(cudaStream_t s, const float4* pos, int64_t n, GridDev g, int fine, uint32_t* keys,

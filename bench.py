@@ -66,6 +66,8 @@ def parse(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
+    ap.add_argument("--no-pipeline", action="store_true",
+                    help="do not try pipelined frames (HR frame overlapping the next frame's LR steps)")
     ap.add_argument("--batch-scenes", type=int, default=256)
     return ap.parse_args(argv)
 
@@ -197,6 +199,20 @@ def run_batched(args, dev, stream, gs, torch):
         batch.frame(DT, N_SUB, iters)
     tw, tb, tus = batch.autotune(DT, reps=3)
     batch.set_graphs(True)
+    tried = {}
+    for shape in (None, (8, 2), (16, 2), (8, 4)):
+        if shape is None:
+            batch.set_pipeline(False, 8, 1)
+        else:
+            batch.set_pipeline(True, *shape)
+        tried["sequential" if shape is None else f"pipelined {shape[0]}x{shape[1]}"] = \
+            frame_ms(lambda: batch.frame(DT, N_SUB, iters), stream, dev, torch)
+    pick = min(tried, key=tried.get)
+    if pick == "sequential":
+        batch.set_pipeline(False, 8, 1)
+    else:
+        w, b = (int(t) for t in pick.split()[1].split("x"))
+        batch.set_pipeline(True, w, b)
     for _ in range(3):
         batch.frame(DT, N_SUB, iters)
     torch.cuda.synchronize(dev)
@@ -236,7 +252,8 @@ def run_batched(args, dev, stream, gs, torch):
             "frame": f"{N_SUB} LR steps of {DT / N_SUB:.5f} s ({iters} solver passes) + 1 upsampling frame",
             "batched_ms_per_frame": ms, "batched_hr_per_s": M / (ms / 1e3), "batched_kernels_per_frame": nl,
             "separate_ms_per_frame": ms2, "separate_hr_per_s": M / (ms2 / 1e3),
-            "speedup_vs_separate": ms2 / ms, "upsample_tuning": {"warps_per_block": tw, "blocks_per_sm": tb,
+            "speedup_vs_separate": ms2 / ms, "frame_ms_tried": tried, "frame_mode": pick,
+            "upsample_tuning": {"warps_per_block": tw, "blocks_per_sm": tb,
                                                                    "upsample_us": tus}}
 
 
@@ -292,6 +309,20 @@ def run_diff(args, dev, stream, gs, torch):
             "plain_forward_ms_per_rollout": ms_plain, "forward_backward_ms_per_rollout": ms_diff,
             "forward_backward_hr_steps_per_s": M * F / (ms_diff / 1e3),
             "backward_overhead_vs_plain_forward": ms_diff / ms_plain, "library_kernels_per_rollout": nl}
+
+
+def frame_ms(fn, stream, dev, torch, warm=2, reps=3):
+    """Mean time of fn() on the stream over reps calls after warm calls."""
+    for _ in range(warm):
+        fn()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    return a.elapsed_time(b) / reps
 
 
 def max_over_ranks(x, world, dev):
@@ -355,9 +386,32 @@ def run_gpu(args):
     # the library's launch-shape autotuner on the first frames' state
     step(ctx)
     tune_w, tune_b, tune_us = ctx.autotune(DT, reps=3)
+    ctx.set_graphs(True)
+    pipe = {"enabled": False}
+    if not args.no_pipeline:
+        # sequential frames against pipelined ones (the HR frame of frame f
+        # overlapping the LR steps of frame f + 1, for a few gather shapes):
+        # whichever whole frame is faster is timed below
+        tried = {}
+        for shape in (None, (8, 1), (4, 2), (4, 0)):
+            if shape is None:
+                ctx.set_pipeline(False, 8, 1)
+            else:
+                ctx.set_pipeline(True, *shape)
+            tried["sequential" if shape is None else f"pipelined {shape[0]}x{shape[1]}"] = \
+                frame_ms(lambda: step(ctx), stream, dev, torch)
+        name = min(tried, key=tried.get)
+        if name == "sequential":
+            ctx.set_pipeline(False, 8, 1)
+        else:
+            w, b = (int(t) for t in name.split()[1].split("x"))
+            ctx.set_pipeline(True, w, b)
+            pipe = {"enabled": True, "gather_warps_per_block": w, "gather_blocks_per_sm": b,
+                    "note": "each timed frame runs its LR steps on the main stream while the HR frame of the "
+                            "previous frame runs on a second stream; K timed frames hold K frames of each"}
+        pipe["frame_ms_tried"] = tried
     clk = Clocks(local)
     time.sleep(0.3)
-    ctx.set_graphs(True)
     for _ in range(args.warmup):
         step(ctx)
     torch.cuda.synchronize(dev)
@@ -475,6 +529,7 @@ def run_gpu(args):
                                             "around each phase (no graphs)"},
         "timed_region": "one CUDA-graph launch per frame (bucket pose copied before it)",
         "upsample_tuning": {"warps_per_block": tune_w, "blocks_per_sm": tune_b, "autotune_us": tune_us},
+        "pipeline": pipe,
         "upsample_kernel_hr_per_s": M / gather_avg_s,
         "wall_s_timed_region": wall,
         "gpu_launches": int(launches),

@@ -239,6 +239,21 @@ int gs_frame(gs_ctx* ctx, float dt, int n_sub, int iters);
 /* Enable (1) or disable (0) CUDA-graph replay of gs_frame. */
 int gs_set_graphs(gs_ctx* ctx, int enable);
 
+/* Pipelined frames (enable = 1): the HR frame of frame f is deferred and
+ * runs, on a second stream of the context, while gs_frame of frame f + 1
+ * runs its LR steps (Sec. 4's HR frame reads only the LR state at the end
+ * of frame f, which the LR steps of frame f + 1 start from; the deferred
+ * frame keeps a copy of the SDF table as of frame f).  warps_per_block /
+ * blocks_per_sm: the upsampling launch shape while it overlaps the LR steps
+ * (blocks_per_sm 0 = one warp item per warp).  Every other call that reads
+ * or changes the HR state or the binned LR view (gs_read, gs_write, gs_sync,
+ * gs_upsample, gs_step_low, gs_bin_low, gs_resort_high, gs_autotune, the
+ * functional forms) first completes the deferred frame in stream order, so
+ * results equal those of sequential frames bit for bit; gs_frame with
+ * timing enabled runs sequentially.  Disabling completes a deferred frame.
+ * Returns GS_ERR_ARG for an unsupported launch shape. */
+int gs_set_pipeline(gs_ctx* ctx, int enable, int warps_per_block, int blocks_per_sm);
+
 /* How gs_step_low runs the n_stab + iters Jacobi passes of a step: 1 = one
  * persistent cooperative launch whose blocks are all resident and meet at a
  * grid barrier between passes (where the device supports cooperative

@@ -89,6 +89,7 @@ _SIGS = {
     "gs_frame": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_int, ctypes.c_int]),
     "gs_set_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
     "gs_set_lr_solver": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gs_set_pipeline": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "gs_set_tuning": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "gs_autotune": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                    ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]),
@@ -177,6 +178,10 @@ def gs_set_graphs(ctx, enable):
 
 def gs_set_lr_solver(ctx, persistent):
     return lib().gs_set_lr_solver(ctx, int(persistent))
+
+
+def gs_set_pipeline(ctx, enable, warps_per_block=8, blocks_per_sm=1):
+    return lib().gs_set_pipeline(ctx, int(enable), int(warps_per_block), int(blocks_per_sm))
 
 
 def gs_set_tuning(ctx, warps_per_block, blocks_per_sm):
@@ -425,6 +430,9 @@ class Context:
 
     def set_lr_solver(self, persistent=True):
         return _check(self.ctx, gs_set_lr_solver(self.ctx, persistent), "gs_set_lr_solver")
+
+    def set_pipeline(self, enable=True, warps_per_block=8, blocks_per_sm=1):
+        return _check(self.ctx, gs_set_pipeline(self.ctx, enable, warps_per_block, blocks_per_sm), "gs_set_pipeline")
 
     def set_tuning(self, warps_per_block, blocks_per_sm):
         return _check(self.ctx, gs_set_tuning(self.ctx, warps_per_block, blocks_per_sm), "gs_set_tuning")

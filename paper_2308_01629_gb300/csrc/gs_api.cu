@@ -296,6 +296,13 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
         }
         c->own_stream = true;
     }
+    e = cudaStreamCreateWithFlags(&c->stream_hr, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        gs_destroy(c);
+        return GS_ERR_CUDA;
+    }
     const int64_t N = c->n_low, MS = c->hr_slots, MR = c->n_high;
     const int64_t NM = std::max(N, MS);
     bool ok = true;
@@ -311,6 +318,8 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
     A(dalloc(&c->lr_vals[0], N));
     A(dalloc(&c->lr_vals[1], N));
     A(dalloc(&c->lr_cell_start, cells + 1));
+    A(dalloc(&c->step_cell_start, cells + 1));
+    A(dalloc(&c->d_sdf_pend, std::max<size_t>(c->sdf_host.size(), 1)));
     A(dalloc(&c->scan_aux, gs_scan_aux_words(cells + 1)));
     A(dalloc(&c->lr_spos, N));
     A(dalloc(&c->lr_svel, N));
@@ -464,16 +473,16 @@ int step_low_impl(gs_ctx* c, float dt, int iters)
     PbdArgs a = pbd_args(c, dt);
     // prediction fused with the counting stage of the binning of x~; the
     // binning's last stage copies x~ and x into cell order
-    CK(gs_cs_clear(c->stream, c->lr_cell_start, c->n_cell_total), "clear counts");
+    CK(gs_cs_clear(c->stream, c->step_cell_start, c->n_cell_total), "clear counts");
     CK(gs_launch_predict_keys(c->stream, a, c->lr_pos, c->lr_vel, c->lr_xt, c->lr_keys[0], c->lr_vals[0],
-                              c->lr_cell_start, &c->launches),
+                              c->step_cell_start, &c->launches),
        "predict");
     CK(gs_cs_finish(c->stream, N, c->n_cell_total, c->lr_keys[0], c->lr_vals[0], c->lr_keys[1], c->lr_vals[1],
-                    c->lr_cell_start, c->scan_aux, c->lr_xt, c->lr_pos, c->s_xt[0], c->s_x[0], &c->launches),
+                    c->step_cell_start, c->scan_aux, c->lr_xt, c->lr_pos, c->s_xt[0], c->s_x[0], &c->launches),
        "bin by cell");
     c->lr_sorted_keys = c->lr_keys[1];
     c->lr_sorted_idx = c->lr_vals[1];
-    CK(gs_launch_neighbors(c->stream, a, c->s_xt[0], c->lr_sorted_keys, c->lr_cell_start, c->n_cell_total, c->nbr, c->nbr_cnt,
+    CK(gs_launch_neighbors(c->stream, a, c->s_xt[0], c->lr_sorted_keys, c->step_cell_start, c->n_cell_total, c->nbr, c->nbr_cnt,
                            c->nbr_cap, c->d_err, &c->launches),
        "neighbours");
     int bx = 0, bt = 0;   // buffers holding the current x and xt
@@ -515,6 +524,151 @@ void drop_graphs(gs_ctx* c)
     for (auto& g : c->graphs)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     c->graphs.clear();
+}
+
+// ---- pipelined frames ------------------------------------------------------
+// The HR frame of frame f depends only on the LR state at the end of frame f,
+// and the LR steps of frame f + 1 only on that state too, so the HR frame is
+// deferred: the next gs_frame runs it on stream_hr while its own LR steps run
+// on the main stream (their binning uses step_cell_start, the gather reads
+// the binned view lr_spos / lr_svel / lr_cell_start and the SDF table as of
+// frame f).  Every call that reads or changes the HR state or the binned
+// view completes a deferred frame first, in stream order, so results equal
+// those of sequential frames bit for bit.
+
+// Enqueues the deferred HR frame on stream s.
+int run_pending_on(gs_ctx* c, cudaStream_t s, int warps, int blocks)
+{
+    cudaStream_t main_stream = c->stream;
+    c->stream = s;
+    c->pending = false;
+    int st = GS_OK;
+    if (c->pend_resort) st = resort_high_impl(c);
+    if (st == GS_OK) {
+        const int cur = c->hr_cur;
+        UpsampleArgs u = upsample_args(c, c->pend_dt, c->hr_pos[cur], c->hr_vel[cur], c->hr_pos[cur], c->hr_vel[cur]);
+        u.sdf = c->d_sdf_pend;
+        cudaError_t e = gs_launch_upsample(c->stream, u, warps, blocks, c->sm_count, &c->launches);
+        if (e != cudaSuccess) st = cuda_fail(c, e, "upsample (deferred frame)");
+    }
+    c->stream = main_stream;
+    return st;
+}
+
+int flush_pending(gs_ctx* c)
+{
+    if (!c->pending) return GS_OK;
+    return run_pending_on(c, c->stream, c->tune_warps, c->tune_blocks_per_sm);
+}
+
+// One pipelined frame: [deferred HR frame on stream_hr] || [n_sub LR steps],
+// join, then bin the new LR state and defer this frame's HR part.
+int frame_pipelined(gs_ctx* c, float dt, int n_sub, int iters)
+{
+    const float dts = n_sub > 0 ? dt / (float)n_sub : dt;
+    const bool had = c->pending;
+    int st;
+    if (had) {
+        CK(cudaEventRecord(c->ev_fork, c->stream), "fork");
+        CK(cudaStreamWaitEvent(c->stream_hr, c->ev_fork, 0), "fork");
+        st = run_pending_on(c, c->stream_hr, c->pipe_warps, c->pipe_blocks_per_sm);
+        if (st) return st;
+    }
+    for (int k = 0; k < n_sub; ++k) {
+        st = step_low_impl(c, dts, iters);
+        if (st) return st;
+    }
+    if (had) {
+        CK(cudaEventRecord(c->ev_join, c->stream_hr), "join");
+        CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0), "join");
+    }
+    if (c->n_high > 0) {
+        st = bin_low_impl(c);
+        if (st) return st;
+        if (!c->sdf_host.empty())
+            CK(cudaMemcpyAsync(c->d_sdf_pend, c->d_sdf, c->sdf_host.size() * sizeof(gs_sdf), cudaMemcpyDeviceToDevice,
+                               c->stream),
+               "SDF snapshot");
+        c->pending = true;
+        c->pend_dt = dt;
+        c->pend_resort = c->resort_every > 0 && c->frame % c->resort_every == 0;
+    }
+    c->frame++;
+    return GS_OK;
+}
+
+int frame_pipelined_graph(gs_ctx* c, float dt, int n_sub, int iters)
+{
+    // what the captured work depends on
+    uint32_t dbits, pbits;
+    std::memcpy(&dbits, &dt, 4);
+    std::memcpy(&pbits, &c->pend_dt, 4);
+    const bool had = c->pending;
+    uint64_t key = 0x9e3779b97f4a7c15ull;
+    auto mix = [&](uint64_t v) { key = (key ^ v) * 0x100000001b3ull; };
+    mix(1);   // pipelined
+    mix(dbits);
+    mix((uint64_t)(n_sub & 0x3ff) | ((uint64_t)(iters & 0x3ff) << 10));
+    mix((uint64_t)had | ((uint64_t)(had && c->pend_resort) << 1) | ((uint64_t)c->hr_cur << 2));
+    mix(had ? pbits : 0u);
+    mix((uint64_t)c->pipe_warps | ((uint64_t)c->pipe_blocks_per_sm << 8) | ((uint64_t)c->n_stab << 16));
+    GraphEntry* ge = nullptr;
+    for (auto& g : c->graphs)
+        if (g.key == key) ge = &g;
+    const int64_t frame0 = c->frame;
+    const int cur0 = c->hr_cur;
+    const bool ident0 = c->hr_identity, keys0 = c->hr_keys_valid, binned0 = c->lr_binned;
+    const bool pend0 = c->pending, pres0 = c->pend_resort;
+    const float pdt0 = c->pend_dt;
+    uint32_t* skeys0 = c->hr_sorted_keys;
+    if (!ge) {
+        cudaGraph_t graph = nullptr;
+        const int64_t launches0 = c->launches;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        int st2 = frame_pipelined(c, dt, n_sub, iters);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        if (st2 != GS_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st2;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+        GraphEntry g;
+        g.key = key;
+        g.kernels = c->launches - launches0;
+        c->launches = launches0;
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(c, e, "instantiate graph");
+        c->graphs.push_back(g);
+        ge = &c->graphs.back();
+        // the capture only recorded the frame: restore the host state, run it below
+        c->frame = frame0;
+        c->hr_cur = cur0;
+        c->hr_identity = ident0;
+        c->hr_keys_valid = keys0;
+        c->lr_binned = binned0;
+        c->pending = pend0;
+        c->pend_resort = pres0;
+        c->pend_dt = pdt0;
+        c->hr_sorted_keys = skeys0;
+    }
+    CK(cudaGraphLaunch(ge->exec, c->stream), "graph launch");
+    c->launches += ge->kernels;
+    // host-side state as if the frame had been enqueued directly
+    if (had && c->pend_resort) {
+        c->hr_sorted_keys = c->hr_keys[((c->hr_key_bits + 7) / 8) & 1];   // where the radix passes end
+        c->hr_cur ^= 1;
+        c->hr_identity = false;
+        c->hr_keys_valid = true;
+    }
+    if (c->n_high > 0) {
+        c->lr_binned = true;
+        c->pending = true;
+        c->pend_dt = dt;
+        c->pend_resort = c->resort_every > 0 && c->frame % c->resort_every == 0;
+    }
+    c->frame = frame0 + 1;
+    return GS_OK;
 }
 
 }  // namespace
@@ -560,6 +714,7 @@ void gs_destroy(gs_ctx* c)
 {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->stream_hr) cudaStreamSynchronize(c->stream_hr);
     drop_graphs(c);
     for (int t = 0; t < GS_TIMER_COUNT; ++t)
         for (auto& pr : c->ev[t]) {
@@ -572,11 +727,15 @@ void gs_destroy(gs_ctx* c)
                     c->hr_pos[0],  c->hr_pos[1],  c->hr_vel[0],  c->hr_vel[1],  c->hr_keys[0], c->hr_keys[1],
                     c->hr_vals[0], c->hr_vals[1], c->nbr,        c->nbr_cnt,    c->tmp4,      c->sort_hist,
                     c->d_work,     c->d_err,      c->gXs,        c->gVs,       c->snap,      c->snap_xt,
-                    c->adj_gx,     c->adj_gxt,    c->adj_h,      c->adj_gws,   c->scan_aux,   c->d_bar};
+                    c->adj_gx,     c->adj_gxt,    c->adj_h,      c->adj_gws,   c->scan_aux,   c->d_bar,
+                    c->step_cell_start, c->d_sdf_pend};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    if (c->stream_hr) cudaStreamDestroy(c->stream_hr);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 
@@ -630,6 +789,8 @@ int gs_scene_info(const gs_ctx* c, int scene, gs_scene_layout* out)
 int gs_write(gs_ctx* c, int field, const void* src, size_t bytes, int src_is_device)
 {
     int st = check_state(c);
+    if (st) return st;
+    st = flush_pending(c);
     if (st) return st;
     if (field != GS_FIELD_LR_POS && field != GS_FIELD_LR_VEL && field != GS_FIELD_HR_POS && field != GS_FIELD_HR_VEL)
         return fail(c, GS_ERR_ARG, "field %d is not writable", field);
@@ -689,6 +850,8 @@ int gs_read(gs_ctx* c, int field, void* dst, size_t bytes, int dst_is_device)
 {
     int st = check_state(c);
     if (st) return st;
+    st = flush_pending(c);
+    if (st) return st;
     size_t fb = field_bytes(c, field);
     if (fb == (size_t)-1) return fail(c, GS_ERR_ARG, "unknown field %d", field);
     if (bytes != fb) return fail(c, GS_ERR_ARG, "size %zu does not match field %d", bytes, field);
@@ -745,6 +908,8 @@ int gs_bin_low(gs_ctx* c)
 {
     int st = check_state(c);
     if (st) return st;
+    st = flush_pending(c);
+    if (st) return st;
     return bin_low_impl(c);
 }
 
@@ -752,12 +917,16 @@ int gs_resort_high(gs_ctx* c)
 {
     int st = check_state(c);
     if (st) return st;
+    st = flush_pending(c);
+    if (st) return st;
     return resort_high_impl(c);
 }
 
 int gs_step_low(gs_ctx* c, float dt, int iters)
 {
     int st = check_state(c);
+    if (st) return st;
+    st = flush_pending(c);
     if (st) return st;
     if (!(dt > 0.0f) || !std::isfinite(dt) || iters < 0 || iters > 1000)
         return fail(c, GS_ERR_ARG, "invalid dt %g or iters %d", (double)dt, iters);
@@ -768,8 +937,26 @@ int gs_upsample(gs_ctx* c, float dt)
 {
     int st = check_state(c);
     if (st) return st;
+    st = flush_pending(c);
+    if (st) return st;
     if (!(dt > 0.0f) || !std::isfinite(dt)) return fail(c, GS_ERR_ARG, "invalid dt %g", (double)dt);
     return upsample_impl(c, dt);
+}
+
+int gs_set_pipeline(gs_ctx* c, int enable, int warps_per_block, int blocks_per_sm)
+{
+    int st = check_state(c);
+    if (st) return st;
+    if ((warps_per_block != 4 && warps_per_block != 8 && warps_per_block != 16) || blocks_per_sm < 0 ||
+        blocks_per_sm > 32)
+        return fail(c, GS_ERR_ARG, "unsupported launch shape %d x %d", warps_per_block, blocks_per_sm);
+    st = flush_pending(c);
+    if (st) return st;
+    c->pipeline = enable != 0;
+    c->pipe_warps = warps_per_block;
+    c->pipe_blocks_per_sm = blocks_per_sm;
+    drop_graphs(c);
+    return GS_OK;
 }
 
 int gs_frame(gs_ctx* c, float dt, int n_sub, int iters)
@@ -778,6 +965,12 @@ int gs_frame(gs_ctx* c, float dt, int n_sub, int iters)
     if (st) return st;
     if (!(dt > 0.0f) || !std::isfinite(dt) || n_sub < 0 || n_sub > 1000 || iters < 0 || iters > 1000)
         return fail(c, GS_ERR_ARG, "invalid frame arguments");
+    if (c->pipeline && !c->timing) {
+        if (c->use_graphs) return frame_pipelined_graph(c, dt, n_sub, iters);
+        return frame_pipelined(c, dt, n_sub, iters);
+    }
+    st = flush_pending(c);
+    if (st) return st;
     const float dts = n_sub > 0 ? dt / (float)n_sub : dt;
     const bool resort = c->n_high > 0 && c->resort_every > 0 && c->frame % c->resort_every == 0;
     if (!c->use_graphs || c->timing) {
@@ -872,6 +1065,8 @@ int gs_autotune(gs_ctx* c, float dt, int reps, int* warps_per_block, int* blocks
 {
     int st = check_state(c);
     if (st) return st;
+    st = flush_pending(c);
+    if (st) return st;
     if (!(dt > 0.0f) || reps < 1 || reps > 1000) return fail(c, GS_ERR_ARG, "invalid autotune arguments");
     if (c->n_high == 0) return fail(c, GS_ERR_STATE, "no HR particles");
     st = bin_low_impl(c);
@@ -918,6 +1113,8 @@ int gs_upsample_forward(gs_ctx* c, const float* lr_pos, const float* lr_vel, con
 {
     int st = check_state(c);
     if (st) return st;
+    st = flush_pending(c);
+    if (st) return st;
     if (c->n_scenes != 1) return fail(c, GS_ERR_STATE, "the functional frame needs a single-scene context");
     if (!(dt > 0.0f) || !std::isfinite(dt)) return fail(c, GS_ERR_ARG, "invalid dt %g", (double)dt);
     const int64_t N = c->n_low, M = c->n_high;
@@ -957,6 +1154,8 @@ int gs_upsample_backward(gs_ctx* c, const float* lr_pos, const float* lr_vel, co
 {
     int st = check_state(c);
     if (st) return st;
+    st = flush_pending(c);
+    if (st) return st;
     if (c->n_scenes != 1) return fail(c, GS_ERR_STATE, "the functional frame needs a single-scene context");
     if (!(dt > 0.0f) || !std::isfinite(dt)) return fail(c, GS_ERR_ARG, "invalid dt %g", (double)dt);
     const int64_t N = c->n_low, M = c->n_high;
@@ -987,6 +1186,8 @@ int gs_step_low_forward(gs_ctx* c, const float* x_in, const float* v_in, float* 
 {
     int st = check_state(c);
     if (st) return st;
+    st = flush_pending(c);
+    if (st) return st;
     if (!(dt > 0.0f) || !std::isfinite(dt) || iters < 0 || iters > 1000)
         return fail(c, GS_ERR_ARG, "invalid dt %g or iters %d", (double)dt, iters);
     const int64_t N = c->n_low;
@@ -1005,6 +1206,8 @@ int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const 
                          float* g_x_in, float* g_v_in, float dt, int iters)
 {
     int st = check_state(c);
+    if (st) return st;
+    st = flush_pending(c);
     if (st) return st;
     if (!(dt > 0.0f) || !std::isfinite(dt) || iters < 0 || iters > 1000)
         return fail(c, GS_ERR_ARG, "invalid dt %g or iters %d", (double)dt, iters);
@@ -1081,6 +1284,8 @@ int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const 
 int gs_sync(gs_ctx* c)
 {
     int st = check_state(c);
+    if (st) return st;
+    st = flush_pending(c);
     if (st) return st;
     return report_device_errors(c);
 }

@@ -62,6 +62,16 @@ struct GraphEntry {
 struct gs_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // pipelined frames: the HR frame of frame f runs on stream_hr while the
+    // LR steps of frame f + 1 run on stream (fork / join by events)
+    cudaStream_t stream_hr = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool pipeline = false;
+    int pipe_warps = 8, pipe_blocks_per_sm = 1;   // gather launch shape while it overlaps the LR steps
+    bool pending = false;        // an HR frame is deferred
+    float pend_dt = 0.0f;
+    bool pend_resort = false;
+    gs_sdf* d_sdf_pend = nullptr;   // the SDF table as of the deferred frame
     int device = 0;
 
     int n_scenes = 1;
@@ -91,7 +101,8 @@ struct gs_ctx {
     uint32_t* lr_vals[2] = {nullptr, nullptr};
     uint32_t* lr_sorted_keys = nullptr;           // points into lr_keys after a sort
     uint32_t* lr_sorted_idx = nullptr;            // points into lr_vals after a sort
-    uint32_t* lr_cell_start = nullptr;            // n_cell_total + 1
+    uint32_t* lr_cell_start = nullptr;            // n_cell_total + 1 (upsampling view)
+    uint32_t* step_cell_start = nullptr;          // n_cell_total + 1 (binning of x~ in the LR step)
     uint32_t* scan_aux = nullptr;                 // tile sums of the cell-start scan
     float4* lr_spos = nullptr;                    // cell-ordered LR position (upsampling view)
     float4* lr_svel = nullptr;                    // cell-ordered LR velocity

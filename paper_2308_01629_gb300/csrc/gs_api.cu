@@ -111,13 +111,6 @@ size_t field_bytes(const gs_ctx* c, int field)
     }
 }
 
-bool finite3_host(const float4* a, int64_t n)
-{
-    for (int64_t i = 0; i < n; ++i)
-        if (!(std::isfinite(a[i].x) && std::isfinite(a[i].y) && std::isfinite(a[i].z))) return false;
-    return true;
-}
-
 // ---- HR slots <-> original order (kernels local to this file) ---------------
 // Slot p of scene s that is not padding holds the particle with original id
 // hr_real_begin + (p - hr_begin) in the identity order.
@@ -337,6 +330,7 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
     A(dalloc(&c->gVs, N));
     A(dalloc(&c->nbr_cnt, N));
     A(dalloc(&c->tmp4, std::max(NM, MR)));
+    A(dalloc(&c->stage_in, std::max(N, MR)));
     c->sort_hist_cap = std::max(gs_sort_hist_words(N), gs_sort_hist_words(MS));
     A(dalloc(&c->sort_hist, c->sort_hist_cap));
     A(dalloc(&c->d_work, 1));
@@ -728,7 +722,7 @@ void gs_destroy(gs_ctx* c)
                     c->hr_vals[0], c->hr_vals[1], c->nbr,        c->nbr_cnt,    c->tmp4,      c->sort_hist,
                     c->d_work,     c->d_err,      c->gXs,        c->gVs,       c->snap,      c->snap_xt,
                     c->adj_gx,     c->adj_gxt,    c->adj_h,      c->adj_gws,   c->scan_aux,   c->d_bar,
-                    c->step_cell_start, c->d_sdf_pend};
+                    c->step_cell_start, c->d_sdf_pend, c->stage_in};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->h_err) cudaFreeHost(c->h_err);
@@ -797,28 +791,30 @@ int gs_write(gs_ctx* c, int field, const void* src, size_t bytes, int src_is_dev
     if (bytes != field_bytes(c, field)) return fail(c, GS_ERR_ARG, "size %zu does not match field %d", bytes, field);
     if (bytes == 0) return GS_OK;
     if (!src) return fail(c, GS_ERR_ARG, "null source");
-    const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const int64_t n = (field == GS_FIELD_LR_POS || field == GS_FIELD_LR_VEL) ? c->n_low : c->n_high;
+    // host data is staged on the device first; the finiteness check runs
+    // there, before anything of the context's state changes
+    const float4* dsrc = (const float4*)src;
     if (!src_is_device) {
-        if (!finite3_host((const float4*)src, n))
-            return fail(c, GS_ERR_DOMAIN, "non-finite value in field %d", field);
-    } else {
-        CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream), "clear flag");
-        CK(gs_launch_check_finite(c->stream, (const float4*)src, n, c->d_err, &c->launches), "finite check");
-        CK(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read flag");
-        CK(cudaStreamSynchronize(c->stream), "synchronize");
-        if (*c->h_err) {
-            CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream), "clear flag");
-            return fail(c, GS_ERR_DOMAIN, "non-finite value in field %d", field);
-        }
+        CK(cudaMemcpyAsync(c->stage_in, src, bytes, cudaMemcpyHostToDevice, c->stream), "copy in");
+        dsrc = c->stage_in;
     }
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream), "clear flag");
+    CK(gs_launch_check_finite(c->stream, dsrc, n, c->d_err, &c->launches), "finite check");
+    CK(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read flag");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");   // the host source is consumed from here on
+    if (*c->h_err) {
+        CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream), "clear flag");
+        return fail(c, GS_ERR_DOMAIN, "non-finite value in field %d", field);
+    }
+    const cudaMemcpyKind kind = cudaMemcpyDeviceToDevice;
     const int cur = c->hr_cur;
     switch (field) {
     case GS_FIELD_LR_POS:
-        CK(cudaMemcpyAsync(c->lr_pos, src, bytes, kind, c->stream), "copy");
+        CK(cudaMemcpyAsync(c->lr_pos, dsrc, bytes, kind, c->stream), "copy");
         c->lr_binned = false;
         break;
-    case GS_FIELD_LR_VEL: CK(cudaMemcpyAsync(c->lr_vel, src, bytes, kind, c->stream), "copy"); break;
+    case GS_FIELD_LR_VEL: CK(cudaMemcpyAsync(c->lr_vel, dsrc, bytes, kind, c->stream), "copy"); break;
     case GS_FIELD_HR_POS:
         if (!c->hr_identity) {
             // bring the velocities back to the identity slot order first
@@ -827,22 +823,19 @@ int gs_write(gs_ctx* c, int field, const void* src, size_t bytes, int src_is_dev
                "unpermute");
             CK(launch_hr_load(c, c->tmp4, c->hr_vel[cur], 0), "load");
         }
-        CK(cudaMemcpyAsync(c->tmp4, src, bytes, kind, c->stream), "copy");
-        CK(launch_hr_load(c, c->tmp4, c->hr_pos[cur], 1), "load");
+        CK(launch_hr_load(c, dsrc, c->hr_pos[cur], 1), "load");
         c->hr_identity = true;
         c->hr_keys_valid = false;
         break;
     case GS_FIELD_HR_VEL:
-        CK(cudaMemcpyAsync(c->tmp4, src, bytes, kind, c->stream), "copy");
         if (c->hr_identity)
-            CK(launch_hr_load(c, c->tmp4, c->hr_vel[cur], 0), "load");
+            CK(launch_hr_load(c, dsrc, c->hr_vel[cur], 0), "load");
         else
-            CK(gs_launch_permute_in(c->stream, c->hr_pos[cur], c->tmp4, c->hr_scene, c->hr_vel[cur], c->hr_slots,
+            CK(gs_launch_permute_in(c->stream, c->hr_pos[cur], dsrc, c->hr_scene, c->hr_vel[cur], c->hr_slots,
                                     c->n_high, c->d_err, &c->launches),
                "permute");
         break;
     }
-    if (!src_is_device) CK(cudaStreamSynchronize(c->stream), "synchronize");
     return GS_OK;
 }
 

@@ -125,6 +125,7 @@ struct gs_ctx {
     uint32_t* hr_sorted_keys = nullptr;
     bool hr_keys_valid = false;
     float4* tmp4 = nullptr;                       // staging for reads / writes
+    float4* stage_in = nullptr;                   // host data written in, checked on the device
 
     // reverse-mode scratch: LR gradients in cell order
     float4* gXs = nullptr;

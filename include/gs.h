@@ -256,11 +256,15 @@ int gs_set_pipeline(gs_ctx* ctx, int enable, int warps_per_block, int blocks_per
 
 /* How gs_step_low runs the n_stab + iters Jacobi passes of a step: 1 = one
  * persistent cooperative launch whose blocks are all resident and meet at a
- * grid barrier between passes (where the device supports cooperative
- * launches); 0 (the default) = one launch per pass, which measured faster
- * when frames are replayed as CUDA graphs.  Both give the same bits.  A barrier
- * that waits longer than about a second gives up and the next gs_sync or
- * gs_read returns GS_ERR_TIMEOUT.  Does not apply to the functional forms
+ * grid barrier between passes; 0 (the default) = one launch per pass, which
+ * measured faster when frames are replayed as CUDA graphs.  Both give the
+ * same bits.  A barrier that waits longer than one second (GPU global timer)
+ * gives up, every block leaves, and the next gs_sync or gs_read returns
+ * GS_ERR_TIMEOUT; the context stays usable but the LR state of that step is
+ * invalid.  2 = self-test of that path: the barrier waits for one block more
+ * than the launch has, so every step times out after about a second.
+ * GS_ERR_ARG for another mode, GS_ERR_STATE where the device has no
+ * cooperative launches.  Does not apply to the functional forms
  * (gs_step_low_forward / _backward), which keep every pass's input. */
 int gs_set_lr_solver(gs_ctx* ctx, int persistent);
 

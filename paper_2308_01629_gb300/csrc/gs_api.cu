@@ -484,7 +484,7 @@ int step_low_impl(gs_ctx* c, float dt, int iters)
         // all passes in one cooperative launch; the buffers alternate as in
         // the loop below
         CK(gs_launch_solve(c->stream, a, c->n_stab, iters, c->s_x, c->s_xt, c->nbr, c->nbr_cnt, c->d_bar, c->d_err,
-                           c->solve_blocks, &c->launches),
+                           c->solve_blocks, &c->launches, c->solver_selftest ? 1u : 0u),
            "solver");
         bt = (c->n_stab + iters) & 1;
         bx = c->n_stab & 1;
@@ -1036,7 +1036,11 @@ int gs_set_lr_solver(gs_ctx* c, int persistent)
 {
     int st = check_state(c);
     if (st) return st;
+    if (persistent < 0 || persistent > 2) return fail(c, GS_ERR_ARG, "unknown solver mode %d", persistent);
+    if (persistent && c->solve_blocks <= 0)
+        return fail(c, GS_ERR_STATE, "the device does not support cooperative launches");
     c->use_solver = persistent != 0;
+    c->solver_selftest = persistent == 2;
     drop_graphs(c);
     return GS_OK;
 }

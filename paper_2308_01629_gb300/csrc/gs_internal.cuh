@@ -158,6 +158,7 @@ struct gs_ctx {
     unsigned* d_bar = nullptr;   // grid-barrier words of the persistent LR solver
     int solve_blocks = 0;        // resident blocks of the solver; 0 = per-pass launches
     bool use_solver = false;    // per-pass launches by default: faster under graph replay
+    bool solver_selftest = false;   // the barrier waits for one block that does not exist
     int* h_err = nullptr;                         // pinned
     std::string last_error;
     bool poisoned = false;
@@ -270,7 +271,7 @@ cudaError_t gs_launch_predict_keys(cudaStream_t s, const PbdArgs& a, const float
 int gs_solve_blocks(int sm_count);
 cudaError_t gs_launch_solve(cudaStream_t s, const PbdArgs& a, int n_stab, int iters, float4* x[2], float4* xt[2],
                             const uint32_t* nbr, const uint32_t* cnt, unsigned* bar, int* err, int max_blocks,
-                            int64_t* launches);
+                            int64_t* launches, unsigned extra_arrivals = 0);
 cudaError_t gs_launch_finalize(cudaStream_t s, const PbdArgs& a, const uint32_t* idx, const float4* s_x,
                                const float4* s_xt, float4* pos, float4* vel, int64_t* launches);
 

@@ -331,11 +331,21 @@ __global__ void __launch_bounds__(128, 7) k_pass(const PbdArgs a, int stab, cons
 // ---- all passes of one step in one launch --------------------------------
 // Every block is resident at once (cooperative launch); the passes are
 // separated by a grid barrier.  Its wait is bounded: a block that waits
-// longer than kBarrierSpins polls sets GS_DEVERR_BARRIER_TIMEOUT and leaves,
-// and every other block then times out at the same barrier, so the launch
+// longer than kBarrierTimeoutNs (GPU global timer) or kBarrierSpins polls
+// sets GS_DEVERR_BARRIER_TIMEOUT and leaves, and every other block then
+// gives up at the same barrier as soon as it sees the flag, so the launch
 // always ends.  The passes, lanes and summation order are those of k_pass,
-// so the two paths give the same bits.
-constexpr unsigned kBarrierSpins = 1u << 24;   // with 32 ns naps and the polls: about one second
+// so the two paths give the same bits.  extra_arrivals > 0 is a self-test:
+// the barrier then waits for blocks that do not exist and must time out.
+constexpr unsigned long long kBarrierTimeoutNs = 1000000000ull;   // one second
+constexpr unsigned kBarrierSpins = 1u << 26;                       // backstop to the timer
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 struct SolveArgs {
     PbdArgs a;
@@ -345,6 +355,7 @@ struct SolveArgs {
     const uint32_t* cnt;
     unsigned* bar;   // {arrived, generation}, zero at launch
     int* err;
+    unsigned extra_arrivals;   // 0; > 0 only in the timeout self-test
 };
 
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned gen, int* err)
@@ -360,13 +371,15 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, un
             atomicExch(bar + 1, gen);
         } else {
             unsigned spins = 0;
+            const unsigned long long t0 = global_ns();
             while (atomicAdd(bar + 1, 0u) != gen) {
-                if (++spins > kBarrierSpins || atomicAdd(err, 0) & GS_DEVERR_BARRIER_TIMEOUT) {
+                if (++spins > kBarrierSpins || global_ns() - t0 > kBarrierTimeoutNs ||
+                    (atomicAdd(err, 0) & GS_DEVERR_BARRIER_TIMEOUT)) {
                     atomicOr(err, GS_DEVERR_BARRIER_TIMEOUT);
                     ok = 0;
                     break;
                 }
-                __nanosleep(32);
+                __nanosleep(64);
             }
         }
         __threadfence();
@@ -397,7 +410,7 @@ __global__ void __launch_bounds__(128, 6) k_solve(const SolveArgs s)
         }
         bt ^= 1;
         if (stab) bx ^= 1;
-        if (it + 1 < total && !grid_barrier(s.bar, gridDim.x, (unsigned)it + 1u, s.err)) return;
+        if (it + 1 < total && !grid_barrier(s.bar, gridDim.x + s.extra_arrivals, (unsigned)it + 1u, s.err)) return;
     }
 }
 
@@ -472,7 +485,7 @@ int gs_solve_blocks(int sm_count)
 
 cudaError_t gs_launch_solve(cudaStream_t s, const PbdArgs& a, int n_stab, int iters, float4* x[2], float4* xt[2],
                             const uint32_t* nbr, const uint32_t* cnt, unsigned* bar, int* err, int max_blocks,
-                            int64_t* launches)
+                            int64_t* launches, unsigned extra_arrivals)
 {
     if (a.n <= 0 || n_stab + iters <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
@@ -489,6 +502,7 @@ cudaError_t gs_launch_solve(cudaStream_t s, const PbdArgs& a, int n_stab, int it
     sa.cnt = cnt;
     sa.bar = bar;
     sa.err = err;
+    sa.extra_arrivals = extra_arrivals;
     int64_t need = (a.n * kLanes + 127) / 128;
     const int grid = (int)std::min<int64_t>(need, max_blocks);
     void* args[] = {&sa};

@@ -151,3 +151,30 @@ def test_persistent_solver_matches_per_pass_launches(case):
         out.append((x, v))
     np.testing.assert_array_equal(out[0][0], out[1][0])
     np.testing.assert_array_equal(out[0][1], out[1][1])
+
+
+def test_solver_barrier_timeout_is_reported_and_context_survives():
+    """Failure detection without a GPU fault: in its self-test mode the
+    persistent solver's grid barrier waits for a block that does not exist;
+    its bounded wait must give up (about a second), the error must reach the
+    host as GS_ERR_TIMEOUT, and the context must step normally afterwards."""
+    import time
+
+    import paper_2308_01629_gb300 as gs
+    sc = CASES["cube_stir"]()
+    ctx = gs.Context(sc)
+    ctx.set_lr_solver(2)
+    t0 = time.time()
+    ctx.step_low(1.0 / 240.0, sc["iters"])
+    with pytest.raises(gs.GsError) as e:
+        ctx.sync()
+    assert e.value.code == gs.GS_ERR_TIMEOUT
+    assert time.time() - t0 < 30.0
+    ctx.set_lr_solver(0)
+    ctx.write(gs.GS_FIELD_LR_POS, np.ascontiguousarray(sc["lr_pos"]))
+    ctx.write(gs.GS_FIELD_LR_VEL, np.ascontiguousarray(sc["lr_vel"]))
+    ctx.step_low(1.0 / 240.0, sc["iters"])
+    x = ctx.read(gs.GS_FIELD_LR_POS)
+    ctx.sync()
+    assert np.all(np.isfinite(x))
+    ctx.close()

@@ -110,3 +110,54 @@ def test_batch_upsample_matches_oracle(orc):
                            scenes.sdf_table(sc["sdfs"]), up_prm(sc, DT), sub=sub, mode=1)
         check_hr(sc, DT, hx[sl_k][sub], hv[sl_k][sub], ref)
     ctx.close()
+
+
+def _empty_like(sc):
+    """The same scene with no particles at all (no LR, hence no HR)."""
+    e = dict(sc)
+    for k in ("lr_pos", "lr_vel", "hr_pos", "hr_vel"):
+        e[k] = np.zeros((0, 4), np.float32)
+    return e
+
+
+def test_context_without_particles():
+    import paper_2308_01629_gb300 as gs
+    ctx = gs.Context(_empty_like(scenes.cube(n_side=4)))
+    ctx.set_graphs(True)
+    for _ in range(3):
+        ctx.frame(DT, 4, 8)
+    ctx.step_low(DT, 8)
+    ctx.upsample(DT)
+    assert ctx.read(gs.GS_FIELD_LR_POS).shape == (0, 4)
+    assert ctx.read(gs.GS_FIELD_HR_VEL).shape == (0, 4)
+    ctx.sync()
+    ctx.close()
+
+
+@pytest.mark.parametrize("pipelined", [False, True])
+def test_batch_with_an_empty_scene_equals_separate_contexts(pipelined):
+    """A scene without particles between two others changes nothing for them
+    (slot and cell layouts, graph replay, pipelined frames)."""
+    import paper_2308_01629_gb300 as gs
+    a, b = _scenes(2, seed=scenes.SEED_BASE + 60)
+    sl = [a, _empty_like(scenes.cube(n_side=3)), b]
+    batch = gs.Context(sl)
+    batch.set_graphs(True)
+    if pipelined:
+        batch.set_pipeline(True, 8, 2)
+    _frames(batch, 9, use_frame=True)
+    got = _state(gs, batch)
+    assert batch.layouts[1].n_low == 0 and batch.layouts[1].n_high == 0
+    for k, sc in ((0, a), (2, b)):
+        one = gs.Context(sc)
+        _frames(one, 9, use_frame=True)
+        ref = _state(gs, one)
+        one.close()
+        for name in ("lr_x", "lr_v"):
+            np.testing.assert_array_equal(got[name][batch.scene_slice(k, gs.GS_FIELD_LR_POS)], ref[name])
+        for name in ("hr_x", "hr_v"):
+            part = got[name][batch.scene_slice(k, gs.GS_FIELD_HR_POS)].copy()
+            if name == "hr_x":
+                part[:, 3] = ref[name][:, 3]
+            np.testing.assert_array_equal(part, ref[name])
+    batch.close()

@@ -236,6 +236,25 @@ int gs_upsample(gs_ctx* ctx, float dt);
  * gs_set_timing switches the replay off).  Asynchronous. */
 int gs_frame(gs_ctx* ctx, float dt, int n_sub, int iters);
 
+/* Asynchronous forms of gs_write / gs_read for the four state fields
+ * (GS_FIELD_LR_POS, _LR_VEL, _HR_POS, _HR_VEL; same layouts and sizes), so
+ * that a caller can overlap host <-> device traffic with the simulation.
+ * gs_write_async copies src into a device staging buffer on a copy stream of
+ * the context and returns at once; the field is checked for finite values on
+ * the device and applied, in order, before the next call that reads or
+ * changes the state (gs_frame, gs_step_low, gs_upsample, gs_read, ...).  src
+ * must stay valid and unchanged until the next gs_sync.  A non-finite value
+ * cannot be refused synchronously: the field is applied and the next gs_sync
+ * or gs_read returns GS_ERR_DOMAIN (the state is then invalid).
+ * gs_read_async takes the field's value as of this point in the context's
+ * work (everything enqueued before it) into a device snapshot and copies it
+ * to dst on a second copy stream; dst holds it after the next gs_sync.  A
+ * device dst is written as by gs_read.  GS_ERR_ARG for another field or a
+ * size mismatch, GS_ERR_OOM if a transfer buffer cannot be allocated (on
+ * first use of a field). */
+int gs_write_async(gs_ctx* ctx, int field, const void* src, size_t bytes, int src_is_device);
+int gs_read_async(gs_ctx* ctx, int field, void* dst, size_t bytes, int dst_is_device);
+
 /* Enable (1) or disable (0) CUDA-graph replay of gs_frame. */
 int gs_set_graphs(gs_ctx* ctx, int enable);
 

@@ -89,6 +89,8 @@ _SIGS = {
     "gs_frame": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_int, ctypes.c_int]),
     "gs_set_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
     "gs_set_lr_solver": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gs_write_async": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, ctypes.c_int]),
+    "gs_read_async": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, ctypes.c_int]),
     "gs_set_pipeline": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "gs_set_tuning": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "gs_autotune": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -213,6 +215,14 @@ def gs_info(ctx):
 
 def gs_write(ctx, field, ptr, nbytes, src_is_device):
     return lib().gs_write(ctx, field, ptr, nbytes, int(src_is_device))
+
+
+def gs_write_async(ctx, field, ptr, nbytes, src_is_device):
+    return lib().gs_write_async(ctx, field, ptr, nbytes, int(src_is_device))
+
+
+def gs_read_async(ctx, field, ptr, nbytes, dst_is_device):
+    return lib().gs_read_async(ctx, field, ptr, nbytes, int(dst_is_device))
 
 
 def gs_read(ctx, field, ptr, nbytes, dst_is_device):
@@ -397,6 +407,18 @@ class Context:
             out = np.zeros(shape, np.float32 if len(shape) == 2 else np.uint32)
         p, n, dev = _ptr_of(out)
         _check(self.ctx, gs_read(self.ctx, field, p, n, dev), "gs_read")
+        return out
+
+    def write_async(self, field, buf):
+        """Stage a field for the next state-reading call; buf must stay valid
+        and unchanged until sync()."""
+        p, n, dev = _ptr_of(buf)
+        return _check(self.ctx, gs_write_async(self.ctx, field, p, n, dev), "gs_write_async")
+
+    def read_async(self, field, out):
+        """Copy the field's current value into out (filled after sync())."""
+        p, n, dev = _ptr_of(out)
+        _check(self.ctx, gs_read_async(self.ctx, field, p, n, dev), "gs_read_async")
         return out
 
     def scene_slice(self, scene, field):

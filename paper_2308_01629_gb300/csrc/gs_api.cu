@@ -89,6 +89,8 @@ int report_device_errors(gs_ctx* c)
             return fail(c, GS_ERR_CAPACITY, "an LR particle had more than %d candidate partners (max_neighbors)",
                         c->nbr_cap);
         if (e & GS_DEVERR_BAD_ID) return fail(c, GS_ERR_STATE, "HR id outside [0, n_high) met while unpermuting");
+        if (e & GS_DEVERR_NONFINITE_ASYNC)
+            return fail(c, GS_ERR_DOMAIN, "an asynchronously written field held a non-finite value; the state is invalid");
         if (e & GS_DEVERR_BARRIER_TIMEOUT)
             return fail(c, GS_ERR_TIMEOUT, "a grid barrier of the persistent LR solver timed out; results are invalid");
     }
@@ -292,6 +294,14 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
     e = cudaStreamCreateWithFlags(&c->stream_hr, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream_h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream_d2h, cudaStreamNonBlocking);
+    for (int f = 0; f < 4 && e == cudaSuccess; ++f) {
+        e = cudaEventCreateWithFlags(&c->ev_in_ready[f], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in_free[f], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out_ready[f], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_out_free[f], cudaEventDisableTiming);
+    }
     if (e != cudaSuccess) {
         gs_destroy(c);
         return GS_ERR_CUDA;
@@ -667,6 +677,83 @@ int frame_pipelined_graph(gs_ctx* c, float dt, int n_sub, int iters)
 
 }  // namespace
 
+// Writes a checked device copy of a state field (original order) into the
+// context's state, on the main stream.
+int apply_field(gs_ctx* c, int field, const float4* dsrc, size_t bytes)
+{
+    const cudaMemcpyKind kind = cudaMemcpyDeviceToDevice;
+    const int cur = c->hr_cur;
+    switch (field) {
+    case GS_FIELD_LR_POS:
+        CK(cudaMemcpyAsync(c->lr_pos, dsrc, bytes, kind, c->stream), "copy");
+        c->lr_binned = false;
+        break;
+    case GS_FIELD_LR_VEL: CK(cudaMemcpyAsync(c->lr_vel, dsrc, bytes, kind, c->stream), "copy"); break;
+    case GS_FIELD_HR_POS:
+        if (!c->hr_identity) {
+            // bring the velocities back to the identity slot order first
+            CK(gs_launch_unpermute(c->stream, c->hr_pos[cur], c->hr_vel[cur], c->hr_scene, c->tmp4, c->hr_slots,
+                                   c->n_high, c->d_err, &c->launches),
+               "unpermute");
+            CK(launch_hr_load(c, c->tmp4, c->hr_vel[cur], 0), "load");
+        }
+        CK(launch_hr_load(c, dsrc, c->hr_pos[cur], 1), "load");
+        c->hr_identity = true;
+        c->hr_keys_valid = false;
+        break;
+    case GS_FIELD_HR_VEL:
+        if (c->hr_identity)
+            CK(launch_hr_load(c, dsrc, c->hr_vel[cur], 0), "load");
+        else
+            CK(gs_launch_permute_in(c->stream, c->hr_pos[cur], dsrc, c->hr_scene, c->hr_vel[cur], c->hr_slots,
+                                    c->n_high, c->d_err, &c->launches),
+               "permute");
+        break;
+    }
+    return GS_OK;
+}
+
+// Commits asynchronously written fields, in field order, on the main stream
+// once their host -> device copies are done.  Each is checked for finite
+// values on the device (an offending field sets GS_DEVERR_NONFINITE_ASYNC,
+// reported by the next gs_sync or gs_read) and then applied.
+int commit_async_writes(gs_ctx* c)
+{
+    for (int f = 0; f < 4; ++f) {
+        if (!c->in_pending[f]) continue;
+        c->in_pending[f] = false;
+        CK(cudaStreamWaitEvent(c->stream, c->ev_in_ready[f], 0), "wait for a staged field");
+        const int64_t n = f < 2 ? c->n_low : c->n_high;
+        CK(gs_launch_check_finite(c->stream, c->async_in[f], n, c->d_err, &c->launches, GS_DEVERR_NONFINITE_ASYNC),
+           "finite check");
+        int st = apply_field(c, f, c->async_in[f], field_bytes(c, f));
+        if (st) return st;
+        CK(cudaEventRecord(c->ev_in_free[f], c->stream), "record");
+    }
+    return GS_OK;
+}
+
+// Everything a call that reads or changes the state must see first: the
+// deferred HR frame of a pipelined frame (it reads the state as of its
+// frame), then the asynchronously written fields.
+int settle(gs_ctx* c)
+{
+    int st = flush_pending(c);
+    if (st) return st;
+    return commit_async_writes(c);
+}
+
+int async_buffer(gs_ctx* c, float4** buf, int field)
+{
+    if (*buf) return GS_OK;
+    const int64_t n = field < 2 ? c->n_low : c->n_high;
+    if (dalloc(buf, (size_t)std::max<int64_t>(n, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, GS_ERR_OOM, "no memory for an asynchronous transfer buffer");
+    }
+    return GS_OK;
+}
+
 extern "C" {
 
 void gs_default_params(gs_params* p)
@@ -709,6 +796,8 @@ void gs_destroy(gs_ctx* c)
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->stream_hr) cudaStreamSynchronize(c->stream_hr);
+    if (c->stream_h2d) cudaStreamSynchronize(c->stream_h2d);
+    if (c->stream_d2h) cudaStreamSynchronize(c->stream_d2h);
     drop_graphs(c);
     for (int t = 0; t < GS_TIMER_COUNT; ++t)
         for (auto& pr : c->ev[t]) {
@@ -722,7 +811,9 @@ void gs_destroy(gs_ctx* c)
                     c->hr_vals[0], c->hr_vals[1], c->nbr,        c->nbr_cnt,    c->tmp4,      c->sort_hist,
                     c->d_work,     c->d_err,      c->gXs,        c->gVs,       c->snap,      c->snap_xt,
                     c->adj_gx,     c->adj_gxt,    c->adj_h,      c->adj_gws,   c->scan_aux,   c->d_bar,
-                    c->step_cell_start, c->d_sdf_pend, c->stage_in};
+                    c->step_cell_start, c->d_sdf_pend, c->stage_in,
+                    c->async_in[0], c->async_in[1], c->async_in[2], c->async_in[3],
+                    c->async_out[0], c->async_out[1], c->async_out[2], c->async_out[3]};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->h_err) cudaFreeHost(c->h_err);
@@ -730,6 +821,11 @@ void gs_destroy(gs_ctx* c)
     if (c->stream_hr) cudaStreamDestroy(c->stream_hr);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->stream_h2d) cudaStreamDestroy(c->stream_h2d);
+    if (c->stream_d2h) cudaStreamDestroy(c->stream_d2h);
+    for (int f = 0; f < 4; ++f)
+        for (cudaEvent_t ev : {c->ev_in_ready[f], c->ev_in_free[f], c->ev_out_ready[f], c->ev_out_free[f]})
+            if (ev) cudaEventDestroy(ev);
     delete c;
 }
 
@@ -784,7 +880,7 @@ int gs_write(gs_ctx* c, int field, const void* src, size_t bytes, int src_is_dev
 {
     int st = check_state(c);
     if (st) return st;
-    st = flush_pending(c);
+    st = settle(c);
     if (st) return st;
     if (field != GS_FIELD_LR_POS && field != GS_FIELD_LR_VEL && field != GS_FIELD_HR_POS && field != GS_FIELD_HR_VEL)
         return fail(c, GS_ERR_ARG, "field %d is not writable", field);
@@ -807,43 +903,15 @@ int gs_write(gs_ctx* c, int field, const void* src, size_t bytes, int src_is_dev
         CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream), "clear flag");
         return fail(c, GS_ERR_DOMAIN, "non-finite value in field %d", field);
     }
-    const cudaMemcpyKind kind = cudaMemcpyDeviceToDevice;
-    const int cur = c->hr_cur;
-    switch (field) {
-    case GS_FIELD_LR_POS:
-        CK(cudaMemcpyAsync(c->lr_pos, dsrc, bytes, kind, c->stream), "copy");
-        c->lr_binned = false;
-        break;
-    case GS_FIELD_LR_VEL: CK(cudaMemcpyAsync(c->lr_vel, dsrc, bytes, kind, c->stream), "copy"); break;
-    case GS_FIELD_HR_POS:
-        if (!c->hr_identity) {
-            // bring the velocities back to the identity slot order first
-            CK(gs_launch_unpermute(c->stream, c->hr_pos[cur], c->hr_vel[cur], c->hr_scene, c->tmp4, c->hr_slots,
-                                   c->n_high, c->d_err, &c->launches),
-               "unpermute");
-            CK(launch_hr_load(c, c->tmp4, c->hr_vel[cur], 0), "load");
-        }
-        CK(launch_hr_load(c, dsrc, c->hr_pos[cur], 1), "load");
-        c->hr_identity = true;
-        c->hr_keys_valid = false;
-        break;
-    case GS_FIELD_HR_VEL:
-        if (c->hr_identity)
-            CK(launch_hr_load(c, dsrc, c->hr_vel[cur], 0), "load");
-        else
-            CK(gs_launch_permute_in(c->stream, c->hr_pos[cur], dsrc, c->hr_scene, c->hr_vel[cur], c->hr_slots,
-                                    c->n_high, c->d_err, &c->launches),
-               "permute");
-        break;
-    }
-    return GS_OK;
+    return apply_field(c, field, dsrc, bytes);
 }
+
 
 int gs_read(gs_ctx* c, int field, void* dst, size_t bytes, int dst_is_device)
 {
     int st = check_state(c);
     if (st) return st;
-    st = flush_pending(c);
+    st = settle(c);
     if (st) return st;
     size_t fb = field_bytes(c, field);
     if (fb == (size_t)-1) return fail(c, GS_ERR_ARG, "unknown field %d", field);
@@ -901,7 +969,7 @@ int gs_bin_low(gs_ctx* c)
 {
     int st = check_state(c);
     if (st) return st;
-    st = flush_pending(c);
+    st = settle(c);
     if (st) return st;
     return bin_low_impl(c);
 }
@@ -910,7 +978,7 @@ int gs_resort_high(gs_ctx* c)
 {
     int st = check_state(c);
     if (st) return st;
-    st = flush_pending(c);
+    st = settle(c);
     if (st) return st;
     return resort_high_impl(c);
 }
@@ -919,7 +987,7 @@ int gs_step_low(gs_ctx* c, float dt, int iters)
 {
     int st = check_state(c);
     if (st) return st;
-    st = flush_pending(c);
+    st = settle(c);
     if (st) return st;
     if (!(dt > 0.0f) || !std::isfinite(dt) || iters < 0 || iters > 1000)
         return fail(c, GS_ERR_ARG, "invalid dt %g or iters %d", (double)dt, iters);
@@ -930,7 +998,7 @@ int gs_upsample(gs_ctx* c, float dt)
 {
     int st = check_state(c);
     if (st) return st;
-    st = flush_pending(c);
+    st = settle(c);
     if (st) return st;
     if (!(dt > 0.0f) || !std::isfinite(dt)) return fail(c, GS_ERR_ARG, "invalid dt %g", (double)dt);
     return upsample_impl(c, dt);
@@ -943,7 +1011,7 @@ int gs_set_pipeline(gs_ctx* c, int enable, int warps_per_block, int blocks_per_s
     if ((warps_per_block != 4 && warps_per_block != 8 && warps_per_block != 16) || blocks_per_sm < 0 ||
         blocks_per_sm > 32)
         return fail(c, GS_ERR_ARG, "unsupported launch shape %d x %d", warps_per_block, blocks_per_sm);
-    st = flush_pending(c);
+    st = settle(c);
     if (st) return st;
     c->pipeline = enable != 0;
     c->pipe_warps = warps_per_block;
@@ -959,10 +1027,14 @@ int gs_frame(gs_ctx* c, float dt, int n_sub, int iters)
     if (!(dt > 0.0f) || !std::isfinite(dt) || n_sub < 0 || n_sub > 1000 || iters < 0 || iters > 1000)
         return fail(c, GS_ERR_ARG, "invalid frame arguments");
     if (c->pipeline && !c->timing) {
+        if (c->in_pending[0] || c->in_pending[1] || c->in_pending[2] || c->in_pending[3]) {
+            st = settle(c);   // staged fields must see the deferred frame first
+            if (st) return st;
+        }
         if (c->use_graphs) return frame_pipelined_graph(c, dt, n_sub, iters);
         return frame_pipelined(c, dt, n_sub, iters);
     }
-    st = flush_pending(c);
+    st = settle(c);
     if (st) return st;
     const float dts = n_sub > 0 ? dt / (float)n_sub : dt;
     const bool resort = c->n_high > 0 && c->resort_every > 0 && c->frame % c->resort_every == 0;
@@ -1062,7 +1134,7 @@ int gs_autotune(gs_ctx* c, float dt, int reps, int* warps_per_block, int* blocks
 {
     int st = check_state(c);
     if (st) return st;
-    st = flush_pending(c);
+    st = settle(c);
     if (st) return st;
     if (!(dt > 0.0f) || reps < 1 || reps > 1000) return fail(c, GS_ERR_ARG, "invalid autotune arguments");
     if (c->n_high == 0) return fail(c, GS_ERR_STATE, "no HR particles");
@@ -1110,7 +1182,7 @@ int gs_upsample_forward(gs_ctx* c, const float* lr_pos, const float* lr_vel, con
 {
     int st = check_state(c);
     if (st) return st;
-    st = flush_pending(c);
+    st = settle(c);
     if (st) return st;
     if (c->n_scenes != 1) return fail(c, GS_ERR_STATE, "the functional frame needs a single-scene context");
     if (!(dt > 0.0f) || !std::isfinite(dt)) return fail(c, GS_ERR_ARG, "invalid dt %g", (double)dt);
@@ -1151,7 +1223,7 @@ int gs_upsample_backward(gs_ctx* c, const float* lr_pos, const float* lr_vel, co
 {
     int st = check_state(c);
     if (st) return st;
-    st = flush_pending(c);
+    st = settle(c);
     if (st) return st;
     if (c->n_scenes != 1) return fail(c, GS_ERR_STATE, "the functional frame needs a single-scene context");
     if (!(dt > 0.0f) || !std::isfinite(dt)) return fail(c, GS_ERR_ARG, "invalid dt %g", (double)dt);
@@ -1183,7 +1255,7 @@ int gs_step_low_forward(gs_ctx* c, const float* x_in, const float* v_in, float* 
 {
     int st = check_state(c);
     if (st) return st;
-    st = flush_pending(c);
+    st = settle(c);
     if (st) return st;
     if (!(dt > 0.0f) || !std::isfinite(dt) || iters < 0 || iters > 1000)
         return fail(c, GS_ERR_ARG, "invalid dt %g or iters %d", (double)dt, iters);
@@ -1204,7 +1276,7 @@ int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const 
 {
     int st = check_state(c);
     if (st) return st;
-    st = flush_pending(c);
+    st = settle(c);
     if (st) return st;
     if (!(dt > 0.0f) || !std::isfinite(dt) || iters < 0 || iters > 1000)
         return fail(c, GS_ERR_ARG, "invalid dt %g or iters %d", (double)dt, iters);
@@ -1282,9 +1354,67 @@ int gs_sync(gs_ctx* c)
 {
     int st = check_state(c);
     if (st) return st;
-    st = flush_pending(c);
+    st = settle(c);
     if (st) return st;
+    CK(cudaStreamSynchronize(c->stream_h2d), "synchronize host-to-device copies");
+    CK(cudaStreamSynchronize(c->stream_d2h), "synchronize device-to-host copies");
     return report_device_errors(c);
+}
+
+int gs_write_async(gs_ctx* c, int field, const void* src, size_t bytes, int src_is_device)
+{
+    int st = check_state(c);
+    if (st) return st;
+    if (field < GS_FIELD_LR_POS || field > GS_FIELD_HR_VEL)
+        return fail(c, GS_ERR_ARG, "field %d is not writable", field);
+    if (bytes != field_bytes(c, field)) return fail(c, GS_ERR_ARG, "size %zu does not match field %d", bytes, field);
+    if (bytes == 0) return GS_OK;
+    if (!src) return fail(c, GS_ERR_ARG, "null source");
+    st = async_buffer(c, &c->async_in[field], field);
+    if (st) return st;
+    // the staging buffer is reused once the previous commit has read it
+    CK(cudaStreamWaitEvent(c->stream_h2d, c->ev_in_free[field], 0), "wait for the staging buffer");
+    CK(cudaMemcpyAsync(c->async_in[field], src, bytes, src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       c->stream_h2d),
+       "copy in");
+    CK(cudaEventRecord(c->ev_in_ready[field], c->stream_h2d), "record");
+    c->in_pending[field] = true;
+    return GS_OK;
+}
+
+int gs_read_async(gs_ctx* c, int field, void* dst, size_t bytes, int dst_is_device)
+{
+    int st = check_state(c);
+    if (st) return st;
+    if (field < GS_FIELD_LR_POS || field > GS_FIELD_HR_VEL)
+        return fail(c, GS_ERR_ARG, "field %d has no asynchronous read", field);
+    if (bytes != field_bytes(c, field)) return fail(c, GS_ERR_ARG, "size %zu does not match field %d", bytes, field);
+    if (bytes > 0 && !dst) return fail(c, GS_ERR_ARG, "null destination");
+    if (dst_is_device) return gs_read(c, field, dst, bytes, 1);   // already asynchronous
+    st = settle(c);
+    if (st) return st;
+    if (bytes == 0) return GS_OK;
+    st = async_buffer(c, &c->async_out[field], field);
+    if (st) return st;
+    // snapshot in stream order, then copy it out on its own stream
+    CK(cudaStreamWaitEvent(c->stream, c->ev_out_free[field], 0), "wait for the snapshot buffer");
+    const int cur = c->hr_cur;
+    float4* out = c->async_out[field];
+    switch (field) {
+    case GS_FIELD_LR_POS: CK(cudaMemcpyAsync(out, c->lr_pos, bytes, cudaMemcpyDeviceToDevice, c->stream), "snapshot"); break;
+    case GS_FIELD_LR_VEL: CK(cudaMemcpyAsync(out, c->lr_vel, bytes, cudaMemcpyDeviceToDevice, c->stream), "snapshot"); break;
+    default: {
+        const float4* f = field == GS_FIELD_HR_POS ? c->hr_pos[cur] : c->hr_vel[cur];
+        CK(gs_launch_unpermute(c->stream, c->hr_pos[cur], f, c->hr_scene, out, c->hr_slots, c->n_high, c->d_err,
+                               &c->launches),
+           "unpermute");
+    }
+    }
+    CK(cudaEventRecord(c->ev_out_ready[field], c->stream), "record");
+    CK(cudaStreamWaitEvent(c->stream_d2h, c->ev_out_ready[field], 0), "wait for the snapshot");
+    CK(cudaMemcpyAsync(dst, out, bytes, cudaMemcpyDeviceToHost, c->stream_d2h), "copy out");
+    CK(cudaEventRecord(c->ev_out_free[field], c->stream_d2h), "record");
+    return GS_OK;
 }
 
 int gs_set_timing(gs_ctx* c, int enable)

@@ -48,6 +48,7 @@ enum : int {
     GS_DEVERR_NEIGHBOR_CAP = 1,   // an LR particle had more candidates than max_neighbors
     GS_DEVERR_BAD_ID = 2,         // an HR id outside [0, n_high) was met while unpermuting
     GS_DEVERR_BARRIER_TIMEOUT = 4,   // a grid barrier of the persistent LR solver gave up waiting
+    GS_DEVERR_NONFINITE_ASYNC = 8,   // an asynchronously written field held a non-finite value
 };
 
 // HR slot tag: scene index, with this bit set on padding slots.
@@ -126,6 +127,16 @@ struct gs_ctx {
     bool hr_keys_valid = false;
     float4* tmp4 = nullptr;                       // staging for reads / writes
     float4* stage_in = nullptr;                   // host data written in, checked on the device
+    // asynchronous field I/O (LR_POS, LR_VEL, HR_POS, HR_VEL): host -> device
+    // copies on stream_h2d into async_in, committed in stream order before
+    // the next call that reads the state; device -> host copies of a
+    // snapshot (async_out) on stream_d2h
+    cudaStream_t stream_h2d = nullptr, stream_d2h = nullptr;
+    float4* async_in[4] = {nullptr, nullptr, nullptr, nullptr};
+    float4* async_out[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_in_ready[4] = {}, ev_in_free[4] = {}, ev_out_ready[4] = {}, ev_out_free[4] = {};
+    bool in_pending[4] = {false, false, false, false};
+    bool in_used[4] = {false, false, false, false}, out_used[4] = {false, false, false, false};
 
     // reverse-mode scratch: LR gradients in cell order
     float4* gXs = nullptr;
@@ -215,7 +226,8 @@ cudaError_t gs_launch_unpermute(cudaStream_t s, const float4* pos_internal, cons
 cudaError_t gs_launch_permute_in(cudaStream_t s, const float4* pos_internal, const float4* field_original,
                                  const uint32_t* hr_tag, float4* out, int64_t n_slots, int64_t n_real, int* err,
                                  int64_t* launches);
-cudaError_t gs_launch_check_finite(cudaStream_t s, const float4* a, int64_t n, int* flag, int64_t* launches);
+cudaError_t gs_launch_check_finite(cudaStream_t s, const float4* a, int64_t n, int* flag, int64_t* launches,
+                                   int bit = 1);
 
 // upsample.cu
 struct UpsampleArgs {

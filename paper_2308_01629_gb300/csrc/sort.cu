@@ -433,12 +433,12 @@ __global__ void k_permute_in(const float4* __restrict__ pos, const float4* __res
     out[p] = f[id];
 }
 
-__global__ void k_check_finite(const float4* __restrict__ a, int64_t n, int* flag)
+__global__ void k_check_finite(const float4* __restrict__ a, int64_t n, int* flag, int bit)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     float4 v = a[p];
-    if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) atomicOr(flag, 1);
+    if (!(isfinite(v.x) && isfinite(v.y) && isfinite(v.z))) atomicOr(flag, bit);
 }
 
 }  // namespace
@@ -578,10 +578,10 @@ cudaError_t gs_launch_scene_keys(cudaStream_t s, const float4* pos, int64_t n, c
     return cudaGetLastError();
 }
 
-cudaError_t gs_launch_check_finite(cudaStream_t s, const float4* a, int64_t n, int* flag, int64_t* launches)
+cudaError_t gs_launch_check_finite(cudaStream_t s, const float4* a, int64_t n, int* flag, int64_t* launches, int bit)
 {
     if (n <= 0) return cudaSuccess;
-    k_check_finite<<<gs_blocks(n, 256), 256, 0, s>>>(a, n, flag);
+    k_check_finite<<<gs_blocks(n, 256), 256, 0, s>>>(a, n, flag, bit);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -70,21 +70,21 @@ __global__ void k_step_gather(int64_t n, const uint32_t* __restrict__ idx, const
 }
 
 // Candidate partners of every particle within the neighbour radius, in
-// ascending sorted index row by row of the 27 surrounding cells.  One warp
-// per cell: the particles of a cell share their 27-cell candidate set, so
-// the warp walks it once, 32 candidates at a time (lane j takes flat
-// candidate j of the concatenated row ranges), and for each particle of the
-// cell a ballot keeps its accepted candidates in ascending order.
-__global__ void __launch_bounds__(128) k_neighbors(const PbdArgs a, const float4* __restrict__ s_xt,
-                                                   const uint32_t* __restrict__ cell_start, int64_t n_cell,
-                                                   uint32_t* __restrict__ nbr, uint32_t* __restrict__ cnt, int cap,
-                                                   int* err)
+// ascending sorted index row by row of the 27 surrounding cells.  The
+// particles of a cell share their 27-cell candidate set, so one warp walks
+// it once, 32 candidates at a time (lane j takes flat candidate j of the
+// concatenated row ranges), and for each particle of the cell a ballot keeps
+// its accepted candidates in ascending order.  Warp w owns the cells whose
+// first (sorted) particle lies in [kNbrGroup w, kNbrGroup (w + 1)): empty
+// cells cost nothing, which matters for sparse grids (many small scenes).
+constexpr int kNbrGroup = 8;
+
+__device__ __forceinline__ void neighbors_of_cell(const PbdArgs& a, const float4* __restrict__ s_xt,
+                                                  const uint32_t* __restrict__ cell_start, int64_t cell,
+                                                  uint32_t* __restrict__ nbr, uint32_t* __restrict__ cnt, int cap,
+                                                  int* err, int lane)
 {
-    const int lane = (int)(threadIdx.x & 31u);
-    const int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (cell >= n_cell) return;                       // whole warps leave together
     const uint32_t pb = __ldg(cell_start + cell), pe = __ldg(cell_start + cell + 1);
-    if (pb == pe) return;
     const SceneDev& sc = a.scenes[a.lr_scene[pb]];
     const GridDev& g = sc.g;
     const uint32_t c = (uint32_t)(cell - sc.cell_off);
@@ -152,6 +152,30 @@ __global__ void __launch_bounds__(128) k_neighbors(const PbdArgs a, const float4
             }
             cnt[mine] = (uint32_t)k;
         }
+    }
+}
+
+__global__ void __launch_bounds__(128) k_neighbors(const PbdArgs a, const float4* __restrict__ s_xt,
+                                                   const uint32_t* __restrict__ skeys,
+                                                   const uint32_t* __restrict__ cell_start,
+                                                   uint32_t* __restrict__ nbr, uint32_t* __restrict__ cnt, int cap,
+                                                   int* err)
+{
+    const int lane = (int)(threadIdx.x & 31u);
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t p = w * kNbrGroup + lane;
+    bool head = false;
+    uint32_t key = 0;
+    if (lane < kNbrGroup && p < a.n) {
+        key = __ldg(skeys + p);
+        head = p == 0 || __ldg(skeys + p - 1) != key;   // the first particle of its cell
+    }
+    unsigned heads = __ballot_sync(0xffffffffu, head);
+    while (heads) {                                    // warp-uniform
+        const int j = __ffs(heads) - 1;
+        heads &= heads - 1u;
+        const int64_t cell = (int64_t)__shfl_sync(0xffffffffu, key, j);
+        neighbors_of_cell(a, s_xt, cell_start, cell, nbr, cnt, cap, err, lane);
     }
 }
 
@@ -458,9 +482,10 @@ cudaError_t gs_launch_neighbors(cudaStream_t s, const PbdArgs& a, const float4* 
                                 const uint32_t* cell_start, int64_t n_cell, uint32_t* nbr, uint32_t* cnt, int cap,
                                 int* err, int64_t* launches)
 {
-    (void)skeys;
+    (void)n_cell;
     if (a.n <= 0) return cudaSuccess;
-    k_neighbors<<<gs_blocks(n_cell * 32, 128), 128, 0, s>>>(a, s_xt, cell_start, n_cell, nbr, cnt, cap, err);
+    const int64_t warps = (a.n + kNbrGroup - 1) / kNbrGroup;
+    k_neighbors<<<gs_blocks(warps * 32, 128), 128, 0, s>>>(a, s_xt, skeys, cell_start, nbr, cnt, cap, err);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -74,9 +74,11 @@ __global__ void k_step_gather(int64_t n, const uint32_t* __restrict__ idx, const
 // particles of a cell share their 27-cell candidate set, so one warp walks
 // it once, 32 candidates at a time (lane j takes flat candidate j of the
 // concatenated row ranges), and for each particle of the cell a ballot keeps
-// its accepted candidates in ascending order.  Warp w owns the cells whose
-// first (sorted) particle lies in [kNbrGroup w, kNbrGroup (w + 1)): empty
-// cells cost nothing, which matters for sparse grids (many small scenes).
+// its accepted candidates in ascending order.  Two ways to hand out cells,
+// with the same lists: on a dense grid one warp per cell (empty cells leave
+// at once); on a sparse grid (many small scenes) warp w takes the cells whose
+// first sorted particle lies in [kNbrGroup w, kNbrGroup (w + 1)), so empty
+// cells cost nothing.
 constexpr int kNbrGroup = 8;
 
 __device__ __forceinline__ void neighbors_of_cell(const PbdArgs& a, const float4* __restrict__ s_xt,
@@ -153,6 +155,18 @@ __device__ __forceinline__ void neighbors_of_cell(const PbdArgs& a, const float4
             cnt[mine] = (uint32_t)k;
         }
     }
+}
+
+__global__ void __launch_bounds__(128) k_neighbors_cells(const PbdArgs a, const float4* __restrict__ s_xt,
+                                                         const uint32_t* __restrict__ cell_start, int64_t n_cell,
+                                                         uint32_t* __restrict__ nbr, uint32_t* __restrict__ cnt,
+                                                         int cap, int* err)
+{
+    const int lane = (int)(threadIdx.x & 31u);
+    const int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (cell >= n_cell) return;   // whole warps leave together
+    if (__ldg(cell_start + cell) == __ldg(cell_start + cell + 1)) return;
+    neighbors_of_cell(a, s_xt, cell_start, cell, nbr, cnt, cap, err, lane);
 }
 
 __global__ void __launch_bounds__(128) k_neighbors(const PbdArgs a, const float4* __restrict__ s_xt,
@@ -482,10 +496,14 @@ cudaError_t gs_launch_neighbors(cudaStream_t s, const PbdArgs& a, const float4* 
                                 const uint32_t* cell_start, int64_t n_cell, uint32_t* nbr, uint32_t* cnt, int cap,
                                 int* err, int64_t* launches)
 {
-    (void)n_cell;
     if (a.n <= 0) return cudaSuccess;
-    const int64_t warps = (a.n + kNbrGroup - 1) / kNbrGroup;
-    k_neighbors<<<gs_blocks(warps * 32, 128), 128, 0, s>>>(a, s_xt, skeys, cell_start, nbr, cnt, cap, err);
+    if (n_cell <= 2 * a.n) {
+        k_neighbors_cells<<<gs_blocks(n_cell * 32, 128), 128, 0, s>>>(a, s_xt, cell_start, n_cell, nbr, cnt, cap,
+                                                                      err);
+    } else {
+        const int64_t warps = (a.n + kNbrGroup - 1) / kNbrGroup;
+        k_neighbors<<<gs_blocks(warps * 32, 128), 128, 0, s>>>(a, s_xt, skeys, cell_start, nbr, cnt, cap, err);
+    }
     *launches += 1;
     return cudaGetLastError();
 }

@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(128) k_neighbors(const PbdArgs a, const float4
 }
 
 // kLanes lanes share one particle: lane `sub` takes candidates sub, sub +
-// kLanes, ... two at a time (so the loads of both are in flight together)
+// kLanes, ... four at a time (so their loads are in flight together)
 // and the SDF components whose running index is sub modulo kLanes; the
 // partial sums are added with shuffles in a fixed order and lane 0 writes
 // the particle.
@@ -287,15 +287,25 @@ __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_
     const float wp = xtp.w;                      // inverse height-scaled mass
     const float dpx = xtp.x - xp.x, dpy = xtp.y - xp.y, dpz = xtp.z - xp.z;
     PassAcc acc = {0.f, 0.f, 0.f, 0};
-    for (int k = sub; k < nc; k += 2 * kLanes) {
-        const int k2 = k + kLanes;
-        const bool two = k2 < nc;
-        const uint32_t q1 = __ldg(nbr + (int64_t)k * a.n + p);
-        const uint32_t q2 = two ? __ldg(nbr + (int64_t)k2 * a.n + p) : q1;
-        const float4 xtq1 = ld_pos<kL2>(xt_in + q1), xq1 = ld_pos<kL2>(x_in + q1);
-        const float4 xtq2 = ld_pos<kL2>(xt_in + q2), xq2 = ld_pos<kL2>(x_in + q2);
-        pair_term(acc, sc, stab, yp, wp, dpx, dpy, dpz, xtq1, xq1, d0);
-        if (two) pair_term(acc, sc, stab, yp, wp, dpx, dpy, dpz, xtq2, xq2, d0);
+    // four candidates at a time (k, k + kLanes, ...), their loads in flight
+    // together; the summation order is the candidate order of the lane
+    for (int k = sub; k < nc; k += 4 * kLanes) {
+        uint32_t q[4];
+        bool in[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            in[j] = k + j * kLanes < nc;
+            q[j] = in[j] ? __ldg(nbr + (int64_t)(k + j * kLanes) * a.n + p) : (uint32_t)p;
+        }
+        float4 xtq[4], xq[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            xtq[j] = ld_pos<kL2>(xt_in + q[j]);
+            xq[j] = ld_pos<kL2>(x_in + q[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (in[j]) pair_term(acc, sc, stab, yp, wp, dpx, dpy, dpz, xtq[j], xq[j], d0);
     }
     if (valid && wp > 0.0f) {
         int gc = 0;
@@ -356,7 +366,7 @@ __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_
     if (stab) st_pos<kL2>(x_out + p, nx);
 }
 
-__global__ void __launch_bounds__(128, 7) k_pass(const PbdArgs a, int stab, const float4* __restrict__ x_in,
+__global__ void __launch_bounds__(128, 6) k_pass(const PbdArgs a, int stab, const float4* __restrict__ x_in,
                                               const float4* __restrict__ xt_in, float4* __restrict__ x_out,
                                               float4* __restrict__ xt_out, const uint32_t* __restrict__ nbr,
                                               const uint32_t* __restrict__ cnt, const FinalOut fin)

@@ -98,10 +98,10 @@ struct gs_ctx {
     // LR state (original order) and the binning view
     float4* lr_pos = nullptr;
     float4* lr_vel = nullptr;
-    uint32_t* lr_keys[2] = {nullptr, nullptr};   // radix ping-pong
-    uint32_t* lr_vals[2] = {nullptr, nullptr};
-    uint32_t* lr_sorted_keys = nullptr;           // points into lr_keys after a sort
-    uint32_t* lr_sorted_idx = nullptr;            // points into lr_vals after a sort
+    uint32_t* lr_keys[2] = {nullptr, nullptr};   // counting sort: [0] cell keys, [1] keys in cell order
+    uint32_t* lr_vals[2] = {nullptr, nullptr};   // [0] arrival ranks, [1] particle indices in cell order
+    uint32_t* lr_sorted_keys = nullptr;           // lr_keys[1] after a binning
+    uint32_t* lr_sorted_idx = nullptr;            // lr_vals[1] after a binning
     uint32_t* lr_cell_start = nullptr;            // n_cell_total + 1 (upsampling view)
     uint32_t* step_cell_start = nullptr;          // n_cell_total + 1 (binning of x~ in the LR step)
     uint32_t* scan_aux = nullptr;                 // tile sums of the cell-start scan
@@ -150,7 +150,7 @@ struct gs_ctx {
     float4* adj_h = nullptr;
     float* adj_gws = nullptr;
 
-    // radix sort histogram scratch
+    // radix sort histogram scratch (HR reorder, static-scratch binning)
     uint32_t* sort_hist = nullptr;
     size_t sort_hist_cap = 0;
 

@@ -267,6 +267,17 @@ __global__ void __launch_bounds__(WARPS * 32, 24 / WARPS) k_upsample(const Upsam
             item = guard == 0 ? (int64_t)blockIdx.x * WARPS + warp : a.n_warps;
         }
         if (item >= a.n_warps) break;
+        if (persistent) {
+            // Pull the HR lines of the item one wave ahead into L2 (one lane
+            // per 128-byte line); whichever warp takes that item then finds
+            // its first loads there.  ahead < n_warps keeps the address
+            // inside the n_warps * 32 slot arrays.
+            const int64_t ahead = item + (int64_t)gridDim.x * WARPS;
+            if (ahead < a.n_warps && (lane & 7) == 0) {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(a.hr_pos + ahead * 32 + lane));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(a.hr_vel + ahead * 32 + lane));
+            }
+        }
         upsample_item(a, item, s_a[warp], s_b[warp], lane);
     }
 }

@@ -70,6 +70,8 @@ def _L():
         L.or_upsample.restype = ctypes.c_int
         L.or_pbd_step.argtypes = [P, P, P, ctypes.c_long, P, ctypes.c_int, P, ctypes.c_int, P, P]
         L.or_pbd_step.restype = ctypes.c_int
+        L.or_pbd_step_mu.argtypes = [P, P, P, ctypes.c_long, P, ctypes.c_int, P, ctypes.c_int, P, P, P]
+        L.or_pbd_step_mu.restype = ctypes.c_int
         L.or_pairs_within.argtypes = [P, ctypes.c_long, P, ctypes.c_long, ctypes.c_double, P, P, ctypes.c_long]
         L.or_pairs_within.restype = ctypes.c_long
         L.or_upsample_vjp.argtypes = [P, P, ctypes.c_long, P, P, ctypes.c_long, P, ctypes.c_int, P, P, P,
@@ -202,16 +204,25 @@ def upsample_vjp(lr_x, lr_v, hr_x, hr_v, sdf, prm, gx, gv):
 
 
 # ------------------------------------------------------------- LR step ---
-def pbd_step(x, v, inv_m, sdf, prm, mode=0):
-    """One LR time step of Algorithm 1.  Returns (x, v, suspect, stats)."""
+def pbd_step(x, v, inv_m, sdf, prm, mode=0, mu=None):
+    """One LR time step of Algorithm 1.  Returns (x, v, suspect, stats).
+    mu (N x 2: mu_s, mu_k per particle), when given, replaces the step's
+    friction coefficients; pairs use the cross coefficients of Sec. 3."""
     x, v = _f64(x, 3).copy(), _f64(v, 3).copy()
     inv_m = _f64(inv_m)
     sdf = _f64(sdf, SDF_STRIDE) if sdf is not None and len(sdf) else np.zeros((0, SDF_STRIDE))
     p = _prm(prm, PB_KEYS)
     sus = np.zeros(len(x), np.int32)
     stats = np.zeros(5, np.int64)
-    rc = _L().or_pbd_step(_ptr(x), _ptr(v), _ptr(inv_m), len(x), _ptr(sdf), len(sdf), _ptr(p),
-                          int(mode), _ptr(sus), _ptr(stats))
+    if mu is None:
+        rc = _L().or_pbd_step(_ptr(x), _ptr(v), _ptr(inv_m), len(x), _ptr(sdf), len(sdf), _ptr(p),
+                              int(mode), _ptr(sus), _ptr(stats))
+    else:
+        mu = _f64(mu, 2)
+        if len(mu) != len(x):
+            raise ValueError("mu must hold one (mu_s, mu_k) pair per particle")
+        rc = _L().or_pbd_step_mu(_ptr(x), _ptr(v), _ptr(inv_m), len(x), _ptr(sdf), len(sdf), _ptr(p),
+                                 int(mode), _ptr(mu), _ptr(sus), _ptr(stats))
     if rc != 0:
         raise RuntimeError(f"or_pbd_step failed ({rc})")
     return x, v, sus.astype(bool), dict(pairs=int(stats[0]), significant=int(stats[1]),

@@ -707,8 +707,11 @@ static void friction_delta(const double* perp, double thr_s, double thr_k, doubl
  *    scaled by min(2 r_LR mu_k / |dx_perp|, 1).  friction mode 1 uses the
  *    penetration depth (2 r_LR - |x_ij|) in place of 2 r_LR, following the
  *    prose that follows Eqs. 3-4.
- *  - Cross coefficients mu_ij = sqrt(mu_i mu_j) (Sec. 3) between a grain
- *    and an SDF boundary; grains share one coefficient pair.
+ *  - Cross coefficients mu_ij = sqrt(mu_i mu_j) (Sec. 3), the static and
+ *    the kinetic one each from the two partners' own: between two grains
+ *    when per-particle coefficients mu (N x 2: mu_s, mu_k) are given, and
+ *    between a grain and an SDF boundary.  Without mu every grain has the
+ *    step's mu_s, mu_k.
  *  - A contact pair (penetration + friction) counts once towards n_i;
  *    each active SDF contact component counts once; particles with n_i = 0
  *    are not moved.  No over-relaxation.
@@ -734,7 +737,7 @@ static long pbd_tape_bytes(long np, long N, int nct, int passes)
 }
 
 static int pbd_impl(double* x, double* v, const double* inv_m, long N,
-                    const double* sdf, int n_sdf, const double* prm, int mode,
+                    const double* sdf, int n_sdf, const double* prm, const double* mu, int mode,
                     int* suspect, long* stats, int tmode, unsigned char* tape, long tape_cap, long* tape_len)
 {
     double r = prm[PB_R], dt = prm[PB_DT];
@@ -869,7 +872,12 @@ static int pbd_impl(double* x, double* v, const double* inv_m, long N,
                 double a = dot3(dx, xij) / d2;
                 for (int k = 0; k < 3; ++k) perp[k] = dx[k] - a * xij[k];
                 double base = (fmode == 1) ? pen : d0;
-                friction_delta(perp, base * mu_s, base * mu_k, eps_x, f, fa, &amb_f, tmode,
+                double pmu_s = mu_s, pmu_k = mu_k;
+                if (mu) {   /* cross coefficients of the pair (Sec. 3) */
+                    pmu_s = sqrt(mu[2 * i] * mu[2 * j]);
+                    pmu_k = sqrt(mu[2 * i + 1] * mu[2 * j + 1]);
+                }
+                friction_delta(perp, base * pmu_s, base * pmu_k, eps_x, f, fa, &amb_f, tmode,
                                tpair ? tpair + p : NULL);
                 for (int k = 0; k < 3; ++k) {
                     ci_alt[k] = ci[k] - mi * fa[k];
@@ -910,7 +918,8 @@ static int pbd_impl(double* x, double* v, const double* inv_m, long N,
                 int tie;
                 int nc = or_sdf_eval(rec, y + 3 * i, phi, nn, &tie, eps_x);
                 const double* ub = rec + 13;
-                double bmu_s = sqrt(mu_s * rec[16]), bmu_k = sqrt(mu_k * rec[17]);
+                double gmu_s = mu ? mu[2 * i] : mu_s, gmu_k = mu ? mu[2 * i + 1] : mu_k;
+                double bmu_s = sqrt(gmu_s * rec[16]), bmu_k = sqrt(gmu_k * rec[17]);
                 for (int c = 0; c < nc; ++c) {
                     int active = phi[c] < r;
                     int amb_act = fabs(phi[c] - r) <= eps_x;
@@ -1011,7 +1020,17 @@ int or_pbd_step(double* x, double* v, const double* inv_m, long N,
                 const double* sdf, int n_sdf, const double* prm, int mode,
                 int* suspect, long* stats)
 {
-    return pbd_impl(x, v, inv_m, N, sdf, n_sdf, prm, mode, suspect, stats, TAPE_OFF, NULL, 0, NULL);
+    return pbd_impl(x, v, inv_m, N, sdf, n_sdf, prm, NULL, mode, suspect, stats, TAPE_OFF, NULL, 0, NULL);
+}
+
+/* or_pbd_step with per-particle friction coefficients mu (N x 2: mu_s,
+ * mu_k); pairs and boundary contacts use the cross coefficients of Sec. 3. */
+int or_pbd_step_mu(double* x, double* v, const double* inv_m, long N,
+                   const double* sdf, int n_sdf, const double* prm, int mode, const double* mu,
+                   int* suspect, long* stats)
+{
+    if (!mu && N > 0) return -1;
+    return pbd_impl(x, v, inv_m, N, sdf, n_sdf, prm, mu, mode, suspect, stats, TAPE_OFF, NULL, 0, NULL);
 }
 
 /* One LR step (grid neighbour search) that records its decisions into, or
@@ -1023,7 +1042,7 @@ int or_pbd_step_tape(double* x, double* v, const double* inv_m, long N, const do
                      const double* prm, int tmode, unsigned char* tape, long tape_cap, long* tape_len)
 {
     if ((tmode != TAPE_RECORD && tmode != TAPE_REPLAY) || !tape) return -1;
-    return pbd_impl(x, v, inv_m, N, sdf, n_sdf, prm, 1, NULL, NULL, tmode, tape, tape_cap, tape_len);
+    return pbd_impl(x, v, inv_m, N, sdf, n_sdf, prm, NULL, 1, NULL, NULL, tmode, tape, tape_cap, tape_len);
 }
 
 /* Brute-force pair listing for tests of the neighbour search: every (i, j)

@@ -402,6 +402,68 @@ def test_friction_mode_uses_penetration_depth(orc):
     assert v1[0, 0] == pytest.approx(0.25 - (1.0 / 32.0) * 0.30 * 16.0, abs=1e-12)
 
 
+ROUGH_FLOOR = scenes.sdf_table([scenes.box_interior((-10.0, -10.0, 0.0), (10.0, 10.0, 10.0), mu_s=1.0, mu_k=1.0)])
+
+
+@pytest.mark.parametrize("u,expect", [(0.75, 0.0), (1.5, 1.5 - 2 * 0.0625 * 0.4 * 16.0)])
+def test_boundary_friction_uses_cross_coefficients(orc, u, expect):
+    # Sec. 3: mu_ib = sqrt(mu_i mu_b).  Grain (0.25, 0.16) on a floor (1, 1):
+    # thresholds 2 r (0.5, 0.4) = (0.0625, 0.05).  The slide u dt is
+    #   0.046875 (u = 0.75): static; with the grain's own mu_s it would be
+    #   kinetic (0.046875 >= 2 r 0.25 = 0.03125)
+    #   0.09375 (u = 1.5): kinetic, reduced by 2 r 0.4 (mean 0.58 or the
+    #   floor's own 1.0 would cancel the slide; the grain's 0.16 would leave
+    #   1.5 - 0.32)
+    r, dt = 0.0625, 1.0 / 16.0
+    x = np.array([[0.5, 0.5, r]])
+    v = np.array([[u, 0.0, 0.0]])
+    x1, v1, _, _ = orc.pbd_step(x, v, [1.0], ROUGH_FLOOR, pb_prm(r=r, dt=dt, g=(0, 0, -8.0)), mu=[[0.25, 0.16]])
+    assert v1[0, 0] == pytest.approx(expect, abs=1e-12)
+    assert v1[0, 1] == 0.0 and x1[0, 2] == r
+
+
+@pytest.mark.parametrize("u,expect", [(0.25, 0.0), (0.5, 0.5 - 0.0625 * 0.2 * 16.0)])
+def test_pair_friction_uses_cross_coefficients(orc, u, expect):
+    # Sec. 3: a pair of grains with coefficients (0.09, 0.04) and (1, 1)
+    # uses mu_ij = (sqrt(0.09), sqrt(0.04)) = (0.3, 0.2).  The grains start
+    # offset in y and slide past each other at -/+u so that after the
+    # prediction they sit side by side along x, overlapping by delta: the
+    # contact normal is x and the relative displacement 2 u dt is
+    # tangential.  The first solver pass (no stabilization, no gravity):
+    #   static (2 u dt = 0.03125 < 2 r 0.3): the slide is cancelled, v_y = 0
+    #   kinetic (2 u dt = 0.0625 >= 0.0375): each grain gives back r mu_k,
+    #   v_y = +/-(u - r 0.2 / dt) = +/-0.3 (the arithmetic mean or the
+    #   maximum would be static, v_y = 0; the minimum 0.46; either grain's
+    #   own coefficient, 0.46 or static)
+    # and both grains leave contact (|x_ij| > 2 r), so later passes add
+    # nothing; the overlap delta is split, v_x = -/+ delta / (2 dt).
+    r, dt, delta = 0.0625, 1.0 / 16.0, 1.0 / 64.0
+    x = np.array([[1.0, 1.0 - u * dt, 1.0], [1.0 + 2 * r - delta, 1.0 + u * dt, 1.0]])
+    v = np.array([[0.0, u, 0.0], [0.0, -u, 0.0]])
+    mu = [[0.09, 0.04], [1.0, 1.0]]
+    for m in (mu, mu[::-1]):   # the cross coefficient is symmetric
+        _, v1, _, _ = orc.pbd_step(x, v, [1.0, 1.0], BIG_BOX, pb_prm(r=r, dt=dt, g=(0, 0, 0), n_stab=0, iters=3),
+                                   mu=m)
+        np.testing.assert_allclose(v1[:, 1], [expect, -expect], atol=1e-12)
+        np.testing.assert_allclose(v1[:, 0], [-delta / (2 * dt), delta / (2 * dt)], atol=1e-12)
+
+
+def test_uniform_per_particle_friction_equals_the_step_coefficients(orc):
+    # sqrt(mu mu) = mu exactly in binary floating point, so per-particle
+    # coefficients that all equal the step's give the step bit for bit
+    rng = np.random.default_rng(7)
+    r = 0.0625
+    x = np.array([[0.5 + 0.11 * (k % 4), 0.5 + 0.11 * (k // 4 % 4), r + 0.11 * (k // 16)] for k in range(40)])
+    x += rng.uniform(-0.01, 0.01, x.shape)
+    v = rng.uniform(-1.0, 1.0, x.shape)
+    prm = pb_prm(r=r)
+    a = orc.pbd_step(x, v, [1.0] * len(x), BIG_BOX, prm)
+    b = orc.pbd_step(x, v, [1.0] * len(x), BIG_BOX, prm, mu=[[prm["mu_s"], prm["mu_k"]]] * len(x))
+    assert a[3]["active"] > 0
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+
+
 def test_jacobi_averaging_three_in_a_row(orc):
     r, d1, d2 = 0.0625, 0.015625, 0.0078125
     x = np.array([[1.0, 1, 1], [1.0 + 2 * r - d1, 1, 1], [1.0 + 4 * r - d1 - d2, 1, 1]])

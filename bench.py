@@ -66,6 +66,7 @@ def parse(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
+    ap.add_argument("--no-materials", action="store_true", help="skip the grain-material frame timing")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="do not try pipelined frames (HR frame overlapping the next frame's LR steps)")
     ap.add_argument("--batch-scenes", type=int, default=256)
@@ -468,6 +469,26 @@ def run_gpu(args):
     ms_per_step = total_ms / args.steps
     value = whole_job_rate(M * args.steps, world, total_ms / 1e3)
 
+    # grain materials (per-particle friction, Sec. 3 cross coefficients):
+    # the same frames with the bed above its median height a second
+    # material, against frames without a table, timed alike (graph replay,
+    # no L2 flush, alternating so both see the same stretch of the run)
+    materials = None
+    if not args.no_materials:
+        table, ids = scenes.materials(sc, seed=0, layout="layers")
+        tried = {"scene_coefficients": [], "two_materials": []}
+        for _ in range(3):
+            ctx.set_materials([])
+            tried["scene_coefficients"].append(frame_ms(lambda: step(ctx), stream, dev, torch, warm=3, reps=8))
+            ctx.set_materials(table, ids)
+            tried["two_materials"].append(frame_ms(lambda: step(ctx), stream, dev, torch, warm=3, reps=8))
+        ctx.set_materials([])
+        base_ms, mat_ms = (float(np.median(tried[k])) for k in ("scene_coefficients", "two_materials"))
+        materials = {"layout": "LR above the median height: material 1, below: material 0",
+                     "table_mu_s_mu_k": table[:2].tolist(), "frame_ms_scene_coefficients": base_ms,
+                     "frame_ms_two_materials": mat_ms, "overhead": mat_ms / base_ms - 1.0,
+                     "timing": "median of 3 alternating runs of 8 graph-replayed frames, L2 not flushed"}
+
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -564,6 +585,7 @@ def run_gpu(args):
         "e2e": e2e,
         "batched": batched,
         "differentiable": differentiable,
+        "materials": materials,
     }
     if not args.no_cpu:
         line["cpu_baseline"] = oracle_frame_rate(sc, args.cpu_seconds)

@@ -112,8 +112,10 @@ enum {
     GS_FIELD_HR_VEL_INTERNAL = 5,/* float4[HR slots], read: internal (cell) order */
     GS_FIELD_LR_CELL_START = 6,  /* uint32[total cells + 1], read: first sorted slot of each cell */
     GS_FIELD_LR_SORTED_INDEX = 7,/* uint32[n_low], read: particle index of each sorted slot */
-    GS_FIELD_HR_SORTED_KEY = 8   /* uint32[HR slots], read: fine cell key of each internal slot
+    GS_FIELD_HR_SORTED_KEY = 8,  /* uint32[HR slots], read: fine cell key of each internal slot
                                     after the latest reorder */
+    GS_FIELD_LR_MATERIAL = 9     /* uint32[n_low], read / write: material of each LR particle
+                                    (gs_set_materials); all 0 at gs_create */
 };
 
 /* Neighbour-grid contract (Sec. 5.1 uses a compact-hashing grid; this
@@ -254,6 +256,25 @@ int gs_frame(gs_ctx* ctx, float dt, int n_sub, int iters);
  * first use of a field). */
 int gs_write_async(gs_ctx* ctx, int field, const void* src, size_t bytes, int src_is_device);
 int gs_read_async(gs_ctx* ctx, int field, void* dst, size_t bytes, int dst_is_device);
+
+/* Grain materials: per-particle friction coefficients (Sec. 3).  mu holds
+ * n_materials pairs (mu_s, mu_k) in host memory, each finite and >= 0;
+ * 1 <= n_materials <= GS_MAX_MATERIALS.  From the next LR step on, LR
+ * particle i has the coefficients of its material m_i (field
+ * GS_FIELD_LR_MATERIAL, 0 unless written) instead of its scene's
+ * params.mu_s / mu_k, and a contact uses the cross coefficients of the two
+ * partners, static and kinetic alike: mu_ij = sqrt(mu_i mu_j) between
+ * grains, sqrt(mu_i mu_b) with an SDF boundary.  One table serves all scenes
+ * of a context.  n_materials = 0 returns to the scenes' coefficients and
+ * resets every particle's material to 0.  Errors: GS_ERR_ARG for an invalid
+ * count or coefficient, or when a particle's material id is >= n_materials
+ * (the table is then unchanged).  gs_step_low_backward refuses to run
+ * (GS_ERR_STATE) while a material table is set: the LR step's reverse mode
+ * knows the scenes' coefficients only.  Writing
+ * GS_FIELD_LR_MATERIAL needs a table; ids >= n_materials give GS_ERR_ARG
+ * and leave the field unchanged. */
+#define GS_MAX_MATERIALS 16
+int gs_set_materials(gs_ctx* ctx, int n_materials, const float* mu);
 
 /* Enable (1) or disable (0) CUDA-graph replay of gs_frame. */
 int gs_set_graphs(gs_ctx* ctx, int enable);

@@ -26,7 +26,9 @@ STATUS_NAMES = {0: "GS_OK", -1: "GS_ERR_ARG", -2: "GS_ERR_OOM", -3: "GS_ERR_CUDA
 GS_SDF_BOX_INTERIOR, GS_SDF_CONE_SHELL, GS_SDF_SOLID_BOX = 1, 2, 3
 GS_MAX_SDF = 16
 (GS_FIELD_LR_POS, GS_FIELD_LR_VEL, GS_FIELD_HR_POS, GS_FIELD_HR_VEL, GS_FIELD_HR_POS_INTERNAL,
- GS_FIELD_HR_VEL_INTERNAL, GS_FIELD_LR_CELL_START, GS_FIELD_LR_SORTED_INDEX, GS_FIELD_HR_SORTED_KEY) = range(9)
+ GS_FIELD_HR_VEL_INTERNAL, GS_FIELD_LR_CELL_START, GS_FIELD_LR_SORTED_INDEX, GS_FIELD_HR_SORTED_KEY,
+ GS_FIELD_LR_MATERIAL) = range(10)
+GS_MAX_MATERIALS = 16
 GS_TIMER_BIN_LOW, GS_TIMER_RESORT, GS_TIMER_GATHER, GS_TIMER_STEP_LOW, GS_TIMER_COUNT = range(5)
 
 
@@ -88,6 +90,7 @@ _SIGS = {
     "gs_scene_info": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(gs_scene_layout)]),
     "gs_frame": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_int, ctypes.c_int]),
     "gs_set_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gs_set_materials": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
     "gs_set_lr_solver": (ctypes.c_int, [_P, ctypes.c_int]),
     "gs_write_async": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, ctypes.c_int]),
     "gs_read_async": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, ctypes.c_int]),
@@ -184,6 +187,12 @@ def gs_set_lr_solver(ctx, persistent):
 
 def gs_set_pipeline(ctx, enable, warps_per_block=8, blocks_per_sm=1):
     return lib().gs_set_pipeline(ctx, int(enable), int(warps_per_block), int(blocks_per_sm))
+
+
+def gs_set_materials(ctx, mu):
+    """mu: (n, 2) array of (mu_s, mu_k) per material; empty turns materials off."""
+    mu = np.ascontiguousarray(np.asarray(mu, np.float32).reshape(-1, 2))
+    return lib().gs_set_materials(ctx, len(mu), mu.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
 
 
 def gs_set_tuning(ctx, warps_per_block, blocks_per_sm):
@@ -402,7 +411,8 @@ class Context:
                       GS_FIELD_HR_POS: (self.n_high, 4), GS_FIELD_HR_VEL: (self.n_high, 4),
                       GS_FIELD_HR_POS_INTERNAL: (self.hr_slots, 4), GS_FIELD_HR_VEL_INTERNAL: (self.hr_slots, 4),
                       GS_FIELD_LR_CELL_START: (self.n_cell_total + 1,),
-                      GS_FIELD_LR_SORTED_INDEX: (self.n_low,), GS_FIELD_HR_SORTED_KEY: (self.hr_slots,)}
+                      GS_FIELD_LR_SORTED_INDEX: (self.n_low,), GS_FIELD_HR_SORTED_KEY: (self.hr_slots,),
+                      GS_FIELD_LR_MATERIAL: (self.n_low,)}
             shape = counts[field]
             out = np.zeros(shape, np.float32 if len(shape) == 2 else np.uint32)
         p, n, dev = _ptr_of(out)
@@ -449,6 +459,14 @@ class Context:
 
     def set_graphs(self, on=True):
         return _check(self.ctx, gs_set_graphs(self.ctx, on), "gs_set_graphs")
+
+    def set_materials(self, mu, ids=None):
+        """Grain materials (Sec. 3): mu is an (n, 2) table of (mu_s, mu_k);
+        ids (uint32 per LR particle, optional) assigns them.  An empty table
+        returns to the scenes' coefficients."""
+        _check(self.ctx, gs_set_materials(self.ctx, mu), "gs_set_materials")
+        if ids is not None:
+            self.write(GS_FIELD_LR_MATERIAL, np.ascontiguousarray(np.asarray(ids, np.uint32)))
 
     def set_lr_solver(self, persistent=True):
         return _check(self.ctx, gs_set_lr_solver(self.ctx, persistent), "gs_set_lr_solver")

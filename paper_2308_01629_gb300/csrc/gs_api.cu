@@ -109,6 +109,7 @@ size_t field_bytes(const gs_ctx* c, int field)
     case GS_FIELD_LR_CELL_START: return (size_t)(c->n_cell_total + 1) * sizeof(uint32_t);
     case GS_FIELD_LR_SORTED_INDEX: return (size_t)c->n_low * sizeof(uint32_t);
     case GS_FIELD_HR_SORTED_KEY: return (size_t)c->hr_slots * sizeof(uint32_t);
+    case GS_FIELD_LR_MATERIAL: return (size_t)c->n_low * sizeof(uint32_t);
     default: return (size_t)-1;
     }
 }
@@ -131,6 +132,16 @@ __global__ void k_hr_load(const float4* __restrict__ src, float4* __restrict__ d
     float4 v = src[id];
     if (set_ids) v.w = __uint_as_float((uint32_t)id);
     dst[p] = v;
+}
+
+// Largest of n material ids (into *out, zero beforehand).
+__global__ void k_max_id(const uint32_t* __restrict__ ids, int64_t n, unsigned* out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned m = i < n ? ids[i] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
 }
 
 cudaError_t launch_hr_load(gs_ctx* c, const float4* src, float4* dst, int set_ids)
@@ -161,6 +172,9 @@ PbdArgs pbd_args(const gs_ctx* c, float dt)
     a.scenes = c->d_scenes;
     a.lr_scene = c->lr_scene;
     a.sdf = c->d_sdf;
+    const bool mat = c->n_materials > 0;
+    a.mu_mat = mat ? c->d_mu : nullptr;
+    a.mu_cross = mat ? c->d_mu + GS_MAX_MATERIALS : nullptr;
     return a;
 }
 
@@ -327,6 +341,8 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
     A(dalloc(&c->lr_spos, N));
     A(dalloc(&c->lr_svel, N));
     A(dalloc(&c->lr_xt, N));
+    A(dalloc(&c->lr_mat, N));
+    A(dalloc(&c->d_mu, (size_t)GS_MAX_MATERIALS * (GS_MAX_MATERIALS + 1)));
     for (int k = 0; k < 2; ++k) {
         A(dalloc(&c->s_xt[k], N));
         A(dalloc(&c->s_x[k], N));
@@ -344,7 +360,7 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
     c->sort_hist_cap = std::max(gs_sort_hist_words(N), gs_sort_hist_words(MS));
     A(dalloc(&c->sort_hist, c->sort_hist_cap));
     A(dalloc(&c->d_work, 1));
-    A(dalloc(&c->d_err, 1));
+    A(dalloc(&c->d_err, 2));   // [0] device error bits, [1] scratch word of the host checks
     A(dalloc(&c->d_bar, 2));
     if (ok) ok = cudaMallocHost((void**)&c->h_err, sizeof(int)) == cudaSuccess;
     if (!ok) {
@@ -371,6 +387,7 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
     Z(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     Z(cudaMemsetAsync(c->lr_pos, 0, std::max<int64_t>(N, 1) * sizeof(float4), c->stream));
     Z(cudaMemsetAsync(c->lr_vel, 0, std::max<int64_t>(N, 1) * sizeof(float4), c->stream));
+    Z(cudaMemsetAsync(c->lr_mat, 0, std::max<int64_t>(N, 1) * sizeof(uint32_t), c->stream));
     Z(cudaMemsetAsync(c->tmp4, 0, std::max<int64_t>(std::max(NM, MR), 1) * sizeof(float4), c->stream));
     Z(cudaMemsetAsync(c->lr_cell_start, 0, (cells + 1) * sizeof(uint32_t), c->stream));
     if (z) Z(launch_hr_load(c, c->tmp4, c->hr_pos[0], 1));
@@ -482,7 +499,8 @@ int step_low_impl(gs_ctx* c, float dt, int iters)
                               c->step_cell_start, &c->launches),
        "predict");
     CK(gs_cs_finish(c->stream, N, c->n_cell_total, c->lr_keys[0], c->lr_vals[0], c->lr_keys[1], c->lr_vals[1],
-                    c->step_cell_start, c->scan_aux, c->lr_xt, c->lr_pos, c->s_xt[0], c->s_x[0], &c->launches),
+                    c->step_cell_start, c->scan_aux, c->lr_xt, c->lr_pos, c->s_xt[0], c->s_x[0], &c->launches,
+                    a.mu_cross ? c->lr_mat : nullptr),
        "bin by cell");
     c->lr_sorted_keys = c->lr_keys[1];
     c->lr_sorted_idx = c->lr_vals[1];
@@ -811,7 +829,7 @@ void gs_destroy(gs_ctx* c)
                     c->hr_vals[0], c->hr_vals[1], c->nbr,        c->nbr_cnt,    c->tmp4,      c->sort_hist,
                     c->d_work,     c->d_err,      c->gXs,        c->gVs,       c->snap,      c->snap_xt,
                     c->adj_gx,     c->adj_gxt,    c->adj_h,      c->adj_gws,   c->scan_aux,   c->d_bar,
-                    c->step_cell_start, c->d_sdf_pend, c->stage_in,
+                    c->step_cell_start, c->d_sdf_pend, c->stage_in, c->lr_mat, c->d_mu,
                     c->async_in[0], c->async_in[1], c->async_in[2], c->async_in[3],
                     c->async_out[0], c->async_out[1], c->async_out[2], c->async_out[3]};
     for (void* b : bufs)
@@ -876,12 +894,81 @@ int gs_scene_info(const gs_ctx* c, int scene, gs_scene_layout* out)
     return GS_OK;
 }
 
+// The material field: ids checked against the table before anything of the
+// state changes.
+static int write_materials(gs_ctx* c, const void* src, size_t bytes, int src_is_device)
+{
+    if (bytes != field_bytes(c, GS_FIELD_LR_MATERIAL))
+        return fail(c, GS_ERR_ARG, "size %zu does not match the material field", bytes);
+    if (c->n_materials == 0) return fail(c, GS_ERR_STATE, "no material table (gs_set_materials)");
+    const int64_t n = c->n_low;
+    if (n == 0) return GS_OK;
+    if (!src) return fail(c, GS_ERR_ARG, "null source");
+    const uint32_t* dsrc = (const uint32_t*)src;
+    if (!src_is_device) {
+        CK(cudaMemcpyAsync(c->stage_in, src, bytes, cudaMemcpyHostToDevice, c->stream), "copy in");
+        dsrc = (const uint32_t*)c->stage_in;
+    }
+    unsigned* word = (unsigned*)(c->d_err + 1);
+    CK(cudaMemsetAsync(word, 0, sizeof(unsigned), c->stream), "clear word");
+    k_max_id<<<gs_blocks(n, 256), 256, 0, c->stream>>>(dsrc, n, word);
+    c->launches += 1;
+    CK(cudaGetLastError(), "max id");
+    CK(cudaMemcpyAsync(c->h_err, word, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream), "read word");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    const uint32_t max_id = (uint32_t)*c->h_err;
+    if (max_id >= (uint32_t)c->n_materials)
+        return fail(c, GS_ERR_ARG, "material id %u >= %d materials", max_id, c->n_materials);
+    CK(cudaMemcpyAsync(c->lr_mat, dsrc, bytes, cudaMemcpyDeviceToDevice, c->stream), "copy");
+    c->mat_max_id = max_id;
+    return GS_OK;
+}
+
+int gs_set_materials(gs_ctx* c, int n_materials, const float* mu)
+{
+    int st = check_state(c);
+    if (st) return st;
+    st = settle(c);
+    if (st) return st;
+    if (n_materials < 0 || n_materials > GS_MAX_MATERIALS)
+        return fail(c, GS_ERR_ARG, "material count %d outside 0..%d", n_materials, GS_MAX_MATERIALS);
+    if (n_materials == 0) {
+        if (c->n_low > 0) CK(cudaMemsetAsync(c->lr_mat, 0, c->n_low * sizeof(uint32_t), c->stream), "reset ids");
+        c->mat_max_id = 0;
+        if (c->n_materials != 0) drop_graphs(c);
+        c->n_materials = 0;
+        return GS_OK;
+    }
+    if (!mu) return fail(c, GS_ERR_ARG, "null coefficient table");
+    for (int m = 0; m < 2 * n_materials; ++m)
+        if (!(std::isfinite(mu[m]) && mu[m] >= 0.0f)) return fail(c, GS_ERR_ARG, "invalid coefficient %g", (double)mu[m]);
+    if (c->mat_max_id >= (uint32_t)n_materials)
+        return fail(c, GS_ERR_ARG, "material id %u in use, table of %d", c->mat_max_id, n_materials);
+    // Sec. 3 cross coefficients mu_ij = sqrt(mu_i mu_j), static and kinetic,
+    // rounded once from double; unused entries stay zero
+    float2* h = c->h_mu;
+    for (int k = 0; k < GS_MAX_MATERIALS * (GS_MAX_MATERIALS + 1); ++k) h[k] = make_float2(0.0f, 0.0f);
+    for (int i = 0; i < n_materials; ++i) {
+        h[i] = make_float2(mu[2 * i], mu[2 * i + 1]);
+        for (int j = 0; j < n_materials; ++j)
+            h[GS_MAX_MATERIALS + i * GS_MAX_MATERIALS + j] =
+                make_float2((float)std::sqrt((double)mu[2 * i] * (double)mu[2 * j]),
+                            (float)std::sqrt((double)mu[2 * i + 1] * (double)mu[2 * j + 1]));
+    }
+    CK(cudaMemcpyAsync(c->d_mu, h, sizeof(c->h_mu), cudaMemcpyHostToDevice, c->stream), "copy table");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");   // the host table is reused by the next call
+    if (c->n_materials == 0) drop_graphs(c);   // the captured steps gather no materials
+    c->n_materials = n_materials;
+    return GS_OK;
+}
+
 int gs_write(gs_ctx* c, int field, const void* src, size_t bytes, int src_is_device)
 {
     int st = check_state(c);
     if (st) return st;
     st = settle(c);
     if (st) return st;
+    if (field == GS_FIELD_LR_MATERIAL) return write_materials(c, src, bytes, src_is_device);
     if (field != GS_FIELD_LR_POS && field != GS_FIELD_LR_VEL && field != GS_FIELD_HR_POS && field != GS_FIELD_HR_VEL)
         return fail(c, GS_ERR_ARG, "field %d is not writable", field);
     if (bytes != field_bytes(c, field)) return fail(c, GS_ERR_ARG, "size %zu does not match field %d", bytes, field);
@@ -923,6 +1010,7 @@ int gs_read(gs_ctx* c, int field, void* dst, size_t bytes, int dst_is_device)
     switch (field) {
     case GS_FIELD_LR_POS: srcp = c->lr_pos; break;
     case GS_FIELD_LR_VEL: srcp = c->lr_vel; break;
+    case GS_FIELD_LR_MATERIAL: srcp = c->lr_mat; break;
     case GS_FIELD_HR_POS_INTERNAL: srcp = c->hr_pos[cur]; break;
     case GS_FIELD_HR_VEL_INTERNAL: srcp = c->hr_vel[cur]; break;
     case GS_FIELD_LR_CELL_START:
@@ -1280,6 +1368,8 @@ int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const 
     if (st) return st;
     if (!(dt > 0.0f) || !std::isfinite(dt) || iters < 0 || iters > 1000)
         return fail(c, GS_ERR_ARG, "invalid dt %g or iters %d", (double)dt, iters);
+    if (c->n_materials > 0)
+        return fail(c, GS_ERR_STATE, "the reverse mode of the LR step does not support grain materials");
     const int64_t N = c->n_low;
     if (N == 0) return GS_OK;
     if (!x_in || !v_in || !g_x_out || !g_v_out || !g_x_in || !g_v_in) return fail(c, GS_ERR_ARG, "null buffer");

@@ -114,6 +114,15 @@ struct gs_ctx {
     float4* s_x[2] = {nullptr, nullptr};
     float4* lr_xt = nullptr;                      // predicted positions, original order
     uint32_t* nbr = nullptr;                      // [cap][n_low] candidate slots
+
+    // grain materials (per-particle friction); off while n_materials == 0
+    int n_materials = 0;
+    uint32_t mat_max_id = 0;                      // largest material id stored in lr_mat
+    uint32_t* lr_mat = nullptr;                   // n_low material ids, original order (in the LR
+                                                  // step they ride in the w of the cell-ordered x)
+    float2* d_mu = nullptr;                       // [GS_MAX_MATERIALS] (mu_s, mu_k), then the
+                                                  // [GS_MAX_MATERIALS^2] cross coefficients
+    float2 h_mu[GS_MAX_MATERIALS * (GS_MAX_MATERIALS + 1)];   // host copy of d_mu
     uint32_t* nbr_cnt = nullptr;
 
     // HR state (internal order), ping-pong
@@ -207,9 +216,12 @@ size_t gs_scan_aux_words(int64_t total);
 cudaError_t gs_cs_clear(cudaStream_t s, uint32_t* cell_start, int64_t n_cell);
 cudaError_t gs_cs_keys(cudaStream_t s, const float4* pos, int64_t n, const SceneDev* scenes, const uint32_t* tag,
                        uint32_t* keys, uint32_t* rank, uint32_t* cell_start, int64_t* launches);
+// ga and gb are copied into cell order: x_out[slot] = x[particle of the
+// slot]; with gb_w not null the w of gb's copies is gb_w[particle] (as bits).
 cudaError_t gs_cs_finish(cudaStream_t s, int64_t n, int64_t n_cell, const uint32_t* keys, const uint32_t* rank,
                          uint32_t* out_keys, uint32_t* out_idx, uint32_t* cell_start, uint32_t* aux, const float4* ga,
-                         const float4* gb, float4* ga_out, float4* gb_out, int64_t* launches);
+                         const float4* gb, float4* ga_out, float4* gb_out, int64_t* launches,
+                         const uint32_t* gb_w = nullptr);
 cudaError_t gs_count_sort_cells(cudaStream_t s, const float4* pos, int64_t n, const SceneDev* scenes,
                                 const uint32_t* tag, int64_t n_cell, uint32_t* keys, uint32_t* rank,
                                 uint32_t* out_keys, uint32_t* out_idx, uint32_t* cell_start, uint32_t* aux,
@@ -258,6 +270,14 @@ struct PbdArgs {
     const SceneDev* scenes;
     const uint32_t* lr_scene;
     const gs_sdf* sdf;
+    // grain materials: null for the scenes' coefficients; else the table
+    // (mu_s, mu_k) per material and the cross coefficients
+    // [m_i * GS_MAX_MATERIALS + m_j].  With materials the w of the
+    // cell-ordered x holds the particle's material id (as bits) instead of
+    // its inverse mass, which the step's finalize reads from the
+    // original-order positions.
+    const float2* mu_mat;
+    const float2* mu_cross;
 };
 cudaError_t gs_launch_predict(cudaStream_t s, const PbdArgs& a, const float4* pos, const float4* vel, float4* xt,
                               int64_t* launches);

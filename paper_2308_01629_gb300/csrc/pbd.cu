@@ -11,7 +11,8 @@
 //   friction (Eqs. 3-4):  relative displacement over the step so far
 //                         (xt_i - x_i) - (xt_j - x_j), tangential part,
 //                         static below 2 r mu_s, else scaled by
-//                         min(2 r mu_k / |dx_perp|, 1)
+//                         min(2 r mu_k / |dx_perp|, 1); with grain
+//                         materials mu = sqrt(mu_i mu_j) per pair (Sec. 3)
 //   averaging:            dx_i = (1 / n_i) sum_k dx_ik
 // SDF contacts act as partners of infinite mass (mass ratio 1).  The
 // stabilization passes evaluate their contacts on x and move x and xt; the
@@ -205,8 +206,11 @@ struct PassAcc {
     int n;
 };
 
+// mu_s, mu_k: the pair's friction coefficients (the scene's, or the cross
+// coefficients of the two grains' materials)
 __device__ __forceinline__ void pair_term(PassAcc& acc, const SceneDev& sc, int stab, float4 yp, float wp, float dpx,
-                                          float dpy, float dpz, float4 xtq, float4 xq, float d0)
+                                          float dpy, float dpz, float4 xtq, float4 xq, float d0, float mu_s,
+                                          float mu_k)
 {
     const float4 yq = stab ? xq : xtq;
     const PairGeo pg = pair_geo(yp, yq);
@@ -223,7 +227,7 @@ __device__ __forceinline__ void pair_term(PassAcc& acc, const SceneDev& sc, int 
         const float rx = dpx - (xtq.x - xq.x), ry = dpy - (xtq.y - xq.y), rz = dpz - (xtq.z - xq.z);
         const Tangent tg = tangent_part(rx, ry, rz, pg.ex, pg.ey, pg.ez, pg.d2);
         const float base = sc.friction_mode == 1 ? pen : d0;
-        const float f = m * friction_scale(tg.L, base * sc.mu_s, base * sc.mu_k);
+        const float f = m * friction_scale(tg.L, base * mu_s, base * mu_k);
         acc.Dx -= f * tg.tx;
         acc.Dy -= f * tg.ty;
         acc.Dz -= f * tg.tz;
@@ -267,7 +271,10 @@ struct FinalOut {
     float4* vel;
 };
 
-template <bool kL2>
+// kMat: grains carry materials (their ids in the w of x); a pair's
+// coefficients are the cross coefficients of the two materials, an SDF
+// contact's sqrt(mu_i mu_b).
+template <bool kL2, bool kMat>
 __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_t p, bool valid, int sub,
                                               const float4* __restrict__ x_in, const float4* __restrict__ xt_in,
                                               float4* __restrict__ x_out, float4* __restrict__ xt_out,
@@ -283,6 +290,8 @@ __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_
         xp = ld_pos<kL2>(x_in + p);
         nc = (int)__ldg(cnt + p);
     }
+    const uint32_t matp = kMat ? __float_as_uint(xp.w) : 0u;
+    const float2* cross_p = kMat ? a.mu_cross + matp * GS_MAX_MATERIALS : nullptr;
     const float4 yp = stab ? xp : xtp;          // positions the constraints are evaluated on
     const float wp = xtp.w;                      // inverse height-scaled mass
     const float dpx = xtp.x - xp.x, dpy = xtp.y - xp.y, dpz = xtp.z - xp.z;
@@ -304,10 +313,23 @@ __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_
             xq[j] = ld_pos<kL2>(x_in + q[j]);
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (in[j]) pair_term(acc, sc, stab, yp, wp, dpx, dpy, dpz, xtq[j], xq[j], d0);
+        for (int j = 0; j < 4; ++j) {
+            if (!in[j]) continue;
+            if constexpr (kMat) {
+                const float2 mu = __ldg(cross_p + __float_as_uint(xq[j].w));
+                pair_term(acc, sc, stab, yp, wp, dpx, dpy, dpz, xtq[j], xq[j], d0, mu.x, mu.y);
+            } else {
+                pair_term(acc, sc, stab, yp, wp, dpx, dpy, dpz, xtq[j], xq[j], d0, sc.mu_s, sc.mu_k);
+            }
+        }
     }
     if (valid && wp > 0.0f) {
+        float gmu_s = sc.mu_s, gmu_k = sc.mu_k;   // the grain's own coefficients
+        if constexpr (kMat) {
+            const float2 mu = __ldg(a.mu_mat + matp);
+            gmu_s = mu.x;
+            gmu_k = mu.y;
+        }
         int gc = 0;
         for (int sI = 0; sI < sc.n_sdf; ++sI) {
             const gs_sdf& b = a.sdf[sc.sdf_begin + sI];
@@ -321,7 +343,7 @@ __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_
                 acc.Dy += pen * h.ny;
                 acc.Dz += pen * h.nz;
                 if (!stab) {
-                    const float bmu_s = sqrtf(sc.mu_s * b.mu_s), bmu_k = sqrtf(sc.mu_k * b.mu_k);
+                    const float bmu_s = sqrtf(gmu_s * b.mu_s), bmu_k = sqrtf(gmu_k * b.mu_k);
                     const float rx = dpx - b.vel[0] * a.dt, ry = dpy - b.vel[1] * a.dt, rz = dpz - b.vel[2] * a.dt;
                     const Tangent tg = tangent_part(rx, ry, rz, h.nx, h.ny, h.nz, 1.0f);
                     const float base = sc.friction_mode == 1 ? pen : d0;
@@ -359,13 +381,17 @@ __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_
     if (fin.idx) {
         const uint32_t i = fin.idx[p];
         fin.vel[i] = make_float4((nt.x - nx.x) / a.dt, (nt.y - nx.y) / a.dt, (nt.z - nx.z) / a.dt, 0.0f);
-        fin.pos[i] = make_float4(nt.x, nt.y, nt.z, nx.w);
+        // with materials x.w holds the material id: the inverse mass comes
+        // from the step-start position, which only this thread touches
+        const float w = kMat ? fin.pos[i].w : nx.w;
+        fin.pos[i] = make_float4(nt.x, nt.y, nt.z, w);
         return;
     }
     st_pos<kL2>(xt_out + p, nt);
     if (stab) st_pos<kL2>(x_out + p, nx);
 }
 
+template <bool kMat>
 __global__ void __launch_bounds__(128, 6) k_pass(const PbdArgs a, int stab, const float4* __restrict__ x_in,
                                               const float4* __restrict__ xt_in, float4* __restrict__ x_out,
                                               float4* __restrict__ xt_out, const uint32_t* __restrict__ nbr,
@@ -373,7 +399,7 @@ __global__ void __launch_bounds__(128, 6) k_pass(const PbdArgs a, int stab, cons
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t p = t / kLanes;
-    pass_particle<false>(a, stab, p, p < a.n, (int)(t % kLanes), x_in, xt_in, x_out, xt_out, nbr, cnt, fin);
+    pass_particle<false, kMat>(a, stab, p, p < a.n, (int)(t % kLanes), x_in, xt_in, x_out, xt_out, nbr, cnt, fin);
 }
 
 // ---- all passes of one step in one launch --------------------------------
@@ -437,6 +463,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, un
     return s_ok != 0;
 }
 
+template <bool kMat>
 __global__ void __launch_bounds__(128, 6) k_solve(const SolveArgs s)
 {
     const int sub = (int)(threadIdx.x % kLanes);
@@ -454,7 +481,7 @@ __global__ void __launch_bounds__(128, 6) k_solve(const SolveArgs s)
             float4* xo = bx ? s.x0 : s.x1;
             float4* ti = bt ? s.xt1 : s.xt0;
             float4* to = bt ? s.xt0 : s.xt1;
-            pass_particle<true>(s.a, stab, p, p < s.a.n, sub, xi, ti, xo, to, s.nbr, s.cnt);
+            pass_particle<true, kMat>(s.a, stab, p, p < s.a.n, sub, xi, ti, xo, to, s.nbr, s.cnt);
         }
         bt ^= 1;
         if (stab) bx ^= 1;
@@ -470,7 +497,8 @@ __global__ void k_finalize(const PbdArgs a, const uint32_t* __restrict__ idx, co
     const uint32_t i = idx[p];
     const float4 x = s_x[p], xt = s_xt[p];
     vel[i] = make_float4((xt.x - x.x) / a.dt, (xt.y - x.y) / a.dt, (xt.z - x.z) / a.dt, 0.0f);
-    pos[i] = make_float4(xt.x, xt.y, xt.z, x.w);
+    const float w = a.mu_cross ? pos[i].w : x.w;   // x.w is the material id with materials
+    pos[i] = make_float4(xt.x, xt.y, xt.z, w);
 }
 
 }  // namespace
@@ -523,16 +551,24 @@ cudaError_t gs_launch_pass(cudaStream_t s, const PbdArgs& a, int stab, const flo
                            int64_t* launches, const uint32_t* fin_idx, float4* fin_pos, float4* fin_vel)
 {
     if (a.n <= 0) return cudaSuccess;
-    k_pass<<<gs_blocks(a.n * kLanes, 128), 128, 0, s>>>(a, stab, x_in, xt_in, x_out, xt_out, nbr, cnt,
-                                                        FinalOut{fin_idx, fin_pos, fin_vel});
+    const FinalOut fin{fin_idx, fin_pos, fin_vel};
+    if (a.mu_cross)
+        k_pass<true><<<gs_blocks(a.n * kLanes, 128), 128, 0, s>>>(a, stab, x_in, xt_in, x_out, xt_out, nbr, cnt, fin);
+    else
+        k_pass<false><<<gs_blocks(a.n * kLanes, 128), 128, 0, s>>>(a, stab, x_in, xt_in, x_out, xt_out, nbr, cnt, fin);
     *launches += 1;
     return cudaGetLastError();
 }
 
 int gs_solve_blocks(int sm_count)
 {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve, 128, 0) != cudaSuccess || per_sm <= 0) return 0;
+    // both variants must fit: the grid is sized once per context
+    int per_sm = 0, per_sm_mat = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<false>, 128, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_mat, k_solve<true>, 128, 0) != cudaSuccess)
+        return 0;
+    per_sm = std::min(per_sm, per_sm_mat);
+    if (per_sm <= 0) return 0;
     return per_sm * sm_count;
 }
 
@@ -559,7 +595,8 @@ cudaError_t gs_launch_solve(cudaStream_t s, const PbdArgs& a, int n_stab, int it
     int64_t need = (a.n * kLanes + 127) / 128;
     const int grid = (int)std::min<int64_t>(need, max_blocks);
     void* args[] = {&sa};
-    e = cudaLaunchCooperativeKernel((const void*)k_solve, dim3((unsigned)grid), dim3(128), args, 0, s);
+    const void* fn = a.mu_cross ? (const void*)k_solve<true> : (const void*)k_solve<false>;
+    e = cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(128), args, 0, s);
     *launches += 1;
     return e;
 }

@@ -345,7 +345,7 @@ __device__ __forceinline__ void order_small(uint32_t* __restrict__ idx, uint32_t
 
 __global__ void k_cs_order(const uint32_t* __restrict__ start, int64_t n_cell, uint32_t* __restrict__ idx,
                            const float4* __restrict__ ga, const float4* __restrict__ gb, float4* __restrict__ ga_out,
-                           float4* __restrict__ gb_out)
+                           float4* __restrict__ gb_out, const uint32_t* __restrict__ gb_w)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_cell) return;
@@ -375,7 +375,11 @@ __global__ void k_cs_order(const uint32_t* __restrict__ start, int64_t n_cell, u
         for (uint32_t j = b; j < e; ++j) {
             const uint32_t i = idx[j];
             ga_out[j] = ga[i];
-            if (gb) gb_out[j] = gb[i];
+            if (gb) {
+                float4 v = gb[i];
+                if (gb_w) v.w = __uint_as_float(gb_w[i]);
+                gb_out[j] = v;
+            }
         }
     }
 }
@@ -492,7 +496,7 @@ cudaError_t gs_cs_keys(cudaStream_t s, const float4* pos, int64_t n, const Scene
 
 cudaError_t gs_cs_finish(cudaStream_t s, int64_t n, int64_t n_cell, const uint32_t* keys, const uint32_t* rank,
                          uint32_t* out_keys, uint32_t* out_idx, uint32_t* cell_start, uint32_t* aux, const float4* ga,
-                         const float4* gb, float4* ga_out, float4* gb_out, int64_t* launches)
+                         const float4* gb, float4* ga_out, float4* gb_out, int64_t* launches, const uint32_t* gb_w)
 {
     const int64_t total = n_cell + 1;
     const int64_t nt = (total + kScanTile - 1) / kScanTile;
@@ -502,7 +506,7 @@ cudaError_t gs_cs_finish(cudaStream_t s, int64_t n, int64_t n_cell, const uint32
     *launches += 3;
     if (n > 0) {
         k_cs_scatter<<<gs_blocks(n, 256), 256, 0, s>>>(keys, rank, n, cell_start, out_keys, out_idx);
-        k_cs_order<<<gs_blocks(n_cell, 256), 256, 0, s>>>(cell_start, n_cell, out_idx, ga, gb, ga_out, gb_out);
+        k_cs_order<<<gs_blocks(n_cell, 256), 256, 0, s>>>(cell_start, n_cell, out_idx, ga, gb, ga_out, gb_out, gb_w);
         *launches += 2;
     }
     return cudaGetLastError();

@@ -316,3 +316,25 @@ def stir(sc, seed, v_scale=0.5, spread=0.5, hr_v_scale=0.3):
     hr_pos[:, :3] = np.clip(hr_pos[:, :3], lo - 2 * sc["r_high"], hi + 2 * sc["r_high"])
     sc.update(lr_vel=lr_vel, hr_vel=hr_vel, hr_pos=hr_pos)
     return sc
+
+
+# ------------------------------------------------------- grain materials ---
+# Friction coefficient pairs (mu_s, mu_k) of three grain materials, from
+# smooth to rough around the paper's default pair (Sec. 5.2).
+MATERIALS = np.array([[MU_S, MU_K], [0.8, 0.6], [0.1, 0.05]], np.float32)
+
+
+def materials(sc, seed, layout="random", table=MATERIALS):
+    """(table, ids): a material per LR particle.  "random" draws each
+    particle's material independently (every pairing of materials occurs);
+    "layers" gives the particles above the median height the second
+    material and the rest the first (a bed covered by another grain)."""
+    n = len(sc["lr_pos"])
+    if layout == "random":
+        ids = np.random.default_rng(seed).integers(0, len(table), size=n)
+    elif layout == "layers":
+        z = sc["lr_pos"][:, 2]
+        ids = (z > np.median(z)).astype(np.int64) if n else np.zeros(0, np.int64)
+    else:
+        raise ValueError(layout)
+    return np.asarray(table, np.float32), ids.astype(np.uint32)

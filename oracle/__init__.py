@@ -297,6 +297,63 @@ def pbd_step_tape(x, v, inv_m, sdf, prm, tape=None):
     return xo, vo, (buf[:need.value].copy() if mode == TAPE_RECORD else buf)
 
 
+# ------------------------------------------- CFL-limited LR substeps ---
+# Sec. 5.2: the LR simulation runs with a default time step that the CFL
+# condition shortens when the grains move fast, and one HR frame covers many
+# LR steps.  Reading used (the paper gives no formula): a step may move no
+# grain by more than cfl times its diameter, dt <= cfl 2 r_LR / max |v|, and
+# never exceeds the default dt_max; the frame time left is split into the
+# fewest equal steps within that limit, decided again after every step from
+# the new velocities; at most max_sub steps per frame (the last one takes
+# what is left).  The decisions fix an integer (the step count), so they are
+# taken in float32 with correctly rounded operations, as the library does.
+def cfl_rate(v, r_low):
+    """max over particles of |v| / (2 r_LR) in float32 (0 for no particles);
+    r_low may be one value or one per particle."""
+    v = np.asarray(v, np.float32)
+    if len(v) == 0:
+        return np.float32(0.0)
+    v = v.reshape(len(v), -1)[:, :3]
+    s = (v[:, 0] * v[:, 0] + v[:, 1] * v[:, 1]) + v[:, 2] * v[:, 2]
+    d = np.float32(2.0) * np.asarray(r_low, np.float32)
+    q = np.sqrt(s) / d
+    return np.float32(q.max())
+
+
+def cfl_substep(t_rem, rate, dt_max, cfl, left):
+    """(dt, more): the next substep for t_rem seconds of frame left, the
+    current rate max |v| / (2 r_LR) and `left` >= 1 steps allowed; more is
+    False for the frame's last step."""
+    f = np.float32
+    t_rem, rate, dt_max, cfl = f(t_rem), f(rate), f(dt_max), f(cfl)
+    if not np.isfinite(rate):
+        lim = f(0.0)
+    elif rate > 0:
+        lim = min(dt_max, f(cfl / rate))
+    else:
+        lim = dt_max
+    with np.errstate(divide="ignore"):
+        q = f(t_rem / lim) if lim > 0 else f(np.inf)
+    n = left if (left <= 1 or not q < f(left)) else max(1, int(np.ceil(q)))
+    return f(t_rem / f(n)), n > 1
+
+
+def frame_adaptive(x, v, inv_m, sdf, prm, dt_frame, dt_max, cfl, max_sub, mode=1):
+    """LR steps of Algorithm 1 covering one frame of dt_frame with the CFL
+    limit above.  Returns (x, v, dts) with dts the float32 substeps."""
+    x, v = _f64(x, 3), _f64(v, 3)
+    t_rem = np.float32(dt_frame)
+    dts = []
+    while True:
+        dt, more = cfl_substep(t_rem, cfl_rate(v, prm["r"]), dt_max, cfl, max_sub - len(dts))
+        step = dict(prm, dt=float(dt))
+        x, v, _, _ = pbd_step(x, v, inv_m, sdf, step, mode=mode)
+        dts.append(dt)
+        if not more:
+            return x, v, np.array(dts, np.float32)
+        t_rem = np.float32(t_rem - dt)
+
+
 def rollout(lr_x, lr_v, inv_m, hr_x, hr_v, sdf, pb, up, frames, n_sub=1, tapes=None):
     """`frames` frames of the two-level method: per frame n_sub LR steps of
     Algorithm 1 (parameters pb, pb["dt"] each), then one HR frame of Sec. 4

@@ -45,6 +45,7 @@ METRIC = "high-res particles/sec (gs_upsample) and HBM GB/s vs peak at 2M; batch
 UNIT = "HR particles/s"
 DT = 1.0 / 60.0
 N_SUB = 4            # LR substeps per frame: dt_LR = 1/240 s, about the paper's 0.005 s
+DT_LR_MAX, CFL = 0.005, 0.4   # adaptive frames: the paper's default LR step and the CFL number
 FLUSH_BYTES = 512 << 20
 # DRAM bytes of one upsampling launch on this workload from an ncu capture of
 # the kernel source with this hash (profiles/); reported only while the
@@ -67,6 +68,7 @@ def parse(argv=None):
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--no-materials", action="store_true", help="skip the grain-material frame timing")
+    ap.add_argument("--no-adaptive", action="store_true", help="skip the CFL-limited substep frame timing")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="do not try pipelined frames (HR frame overlapping the next frame's LR steps)")
     ap.add_argument("--batch-scenes", type=int, default=256)
@@ -372,13 +374,17 @@ def run_gpu(args):
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     frame = [0]
 
-    def step(c):
-        # one frame: the bucket pose, N_SUB LR steps and the HR frame; with
-        # graphs on and timers off it is one graph launch
+    def step(c, adaptive=False):
+        # one frame: the bucket pose, N_SUB LR steps (or CFL-limited steps of
+        # at most DT_LR_MAX) and the HR frame; with graphs on and timers off
+        # it is one graph launch
         b = bucket_at(sc, frame[0])
         if b is not None:
             c.set_sdf(*b)
-        c.frame(DT, N_SUB, sc["iters"])
+        if adaptive:
+            c.frame_adaptive(DT, sc["iters"], dt_max=DT_LR_MAX, cfl=CFL)
+        else:
+            c.frame(DT, N_SUB, sc["iters"])
         frame[0] += 1
 
     def barrier():
@@ -489,6 +495,24 @@ def run_gpu(args):
                      "frame_ms_two_materials": mat_ms, "overhead": mat_ms / base_ms - 1.0,
                      "timing": "median of 3 alternating runs of 8 graph-replayed frames, L2 not flushed"}
 
+    # CFL-limited substeps (Sec. 5.2): the same frames with the LR steps
+    # decided on the device each frame (default 0.005 s, shortened by the
+    # CFL condition), against the fixed four steps, timed alike
+    adaptive = None
+    if not args.no_adaptive:
+        tried = {"fixed_4_steps": [], "adaptive": []}
+        steps = []
+        for _ in range(3):
+            tried["fixed_4_steps"].append(frame_ms(lambda: step(ctx), stream, dev, torch, warm=3, reps=8))
+            tried["adaptive"].append(frame_ms(lambda: step(ctx, adaptive=True), stream, dev, torch, warm=3,
+                                              reps=8))
+            steps.append(len(ctx.substeps()))
+        fixed_ms, adapt_ms = (float(np.median(tried[k])) for k in ("fixed_4_steps", "adaptive"))
+        adaptive = {"dt_lr_max": DT_LR_MAX, "cfl": CFL, "frame_ms_fixed_4_steps": fixed_ms,
+                    "frame_ms_adaptive": adapt_ms, "lr_steps_per_frame": steps,
+                    "timing": "median of 3 alternating runs of 8 graph-replayed frames, L2 not flushed; the "
+                              "adaptive frame's LR steps run in a device-side loop (conditional graph node)"}
+
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -586,6 +610,7 @@ def run_gpu(args):
         "batched": batched,
         "differentiable": differentiable,
         "materials": materials,
+        "adaptive_substeps": adaptive,
     }
     if not args.no_cpu:
         line["cpu_baseline"] = oracle_frame_rate(sc, args.cpu_seconds)

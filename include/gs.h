@@ -238,6 +238,31 @@ int gs_upsample(gs_ctx* ctx, float dt);
  * gs_set_timing switches the replay off).  Asynchronous. */
 int gs_frame(gs_ctx* ctx, float dt, int n_sub, int iters);
 
+/* One frame with CFL-limited LR substeps (Sec. 5.2: a default LR time step
+ * dt_max, shortened by the CFL condition when grains move fast; one HR frame
+ * of dt).  Before every LR step the library takes
+ *   rate = max over LR particles of |v| / (2 r_LR)   (float32),
+ *   limit = min(dt_max, cfl / rate)   (dt_max when rate = 0; 0 when rate is
+ *           not finite),
+ * and splits the frame time left into the fewest equal steps no longer than
+ * limit: n = ceil(t_left / limit), capped by the steps still allowed
+ * (max_sub per frame), step = t_left / n.  The last step of the frame is
+ * the one with n = 1, so the steps add up to dt.  All in float32, correctly
+ * rounded.  Then one HR frame of dt (gs_upsample).  With graphs enabled the
+ * frame is one CUDA graph whose LR steps run in a device-side loop (a
+ * conditional while node), so the host neither waits nor learns the step
+ * count; otherwise (graphs off, or kernel timing on) the host waits after
+ * every step.  Adaptive frames are not pipelined (gs_set_pipeline).  dt,
+ * dt_max, cfl > 0 and finite, 1 <= max_sub <= GS_MAX_SUBSTEPS, 0 <= iters
+ * <= 1000.  The LR steps of adaptive frames enter gs_launch_count at the
+ * next gs_sync or gs_substeps. */
+#define GS_MAX_SUBSTEPS 256
+int gs_frame_adaptive(gs_ctx* ctx, float dt, float dt_max, float cfl, int max_sub, int iters);
+
+/* The LR steps of the latest adaptive frame: *n_out receives their number
+ * and dts[0 .. min(n, cap)) their lengths.  Blocks. */
+int gs_substeps(gs_ctx* ctx, float* dts, int cap, int* n_out);
+
 /* Asynchronous forms of gs_write / gs_read for the four state fields
  * (GS_FIELD_LR_POS, _LR_VEL, _HR_POS, _HR_VEL; same layouts and sizes), so
  * that a caller can overlap host <-> device traffic with the simulation.

@@ -29,6 +29,7 @@ GS_MAX_SDF = 16
  GS_FIELD_HR_VEL_INTERNAL, GS_FIELD_LR_CELL_START, GS_FIELD_LR_SORTED_INDEX, GS_FIELD_HR_SORTED_KEY,
  GS_FIELD_LR_MATERIAL) = range(10)
 GS_MAX_MATERIALS = 16
+GS_MAX_SUBSTEPS = 256
 GS_TIMER_BIN_LOW, GS_TIMER_RESORT, GS_TIMER_GATHER, GS_TIMER_STEP_LOW, GS_TIMER_COUNT = range(5)
 
 
@@ -91,6 +92,9 @@ _SIGS = {
     "gs_frame": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_int, ctypes.c_int]),
     "gs_set_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
     "gs_set_materials": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]),
+    "gs_frame_adaptive": (ctypes.c_int, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_int,
+                                         ctypes.c_int]),
+    "gs_substeps": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "gs_set_lr_solver": (ctypes.c_int, [_P, ctypes.c_int]),
     "gs_write_async": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, ctypes.c_int]),
     "gs_read_async": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_size_t, ctypes.c_int]),
@@ -187,6 +191,18 @@ def gs_set_lr_solver(ctx, persistent):
 
 def gs_set_pipeline(ctx, enable, warps_per_block=8, blocks_per_sm=1):
     return lib().gs_set_pipeline(ctx, int(enable), int(warps_per_block), int(blocks_per_sm))
+
+
+def gs_frame_adaptive(ctx, dt, dt_max, cfl, max_sub, iters):
+    return lib().gs_frame_adaptive(ctx, float(dt), float(dt_max), float(cfl), int(max_sub), int(iters))
+
+
+def gs_substeps(ctx):
+    """(status, dts): the LR step lengths of the latest adaptive frame."""
+    out = np.zeros(GS_MAX_SUBSTEPS, np.float32)
+    n = ctypes.c_int()
+    rc = lib().gs_substeps(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), len(out), ctypes.byref(n))
+    return rc, out[:max(n.value, 0)].copy()
 
 
 def gs_set_materials(ctx, mu):
@@ -459,6 +475,17 @@ class Context:
 
     def set_graphs(self, on=True):
         return _check(self.ctx, gs_set_graphs(self.ctx, on), "gs_set_graphs")
+
+    def frame_adaptive(self, dt, iters, dt_max=0.005, cfl=0.4, max_sub=64):
+        """One frame of dt with CFL-limited LR substeps (at most dt_max each,
+        a grain moves at most cfl diameters per step) and one HR frame."""
+        return _check(self.ctx, gs_frame_adaptive(self.ctx, dt, dt_max, cfl, max_sub, iters), "gs_frame_adaptive")
+
+    def substeps(self):
+        """The LR step lengths of the latest adaptive frame (float32 array)."""
+        rc, dts = gs_substeps(self.ctx)
+        _check(self.ctx, rc, "gs_substeps")
+        return dts
 
     def set_materials(self, mu, ids=None):
         """Grain materials (Sec. 3): mu is an (n, 2) table of (mu_s, mu_k);

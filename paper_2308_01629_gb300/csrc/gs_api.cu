@@ -169,6 +169,7 @@ PbdArgs pbd_args(const gs_ctx* c, float dt)
     PbdArgs a;
     a.n = c->n_low;
     a.dt = dt;
+    a.dt_dev = nullptr;
     a.scenes = c->d_scenes;
     a.lr_scene = c->lr_scene;
     a.sdf = c->d_sdf;
@@ -362,6 +363,7 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
     A(dalloc(&c->d_work, 1));
     A(dalloc(&c->d_err, 2));   // [0] device error bits, [1] scratch word of the host checks
     A(dalloc(&c->d_bar, 2));
+    A(dalloc(&c->d_cfl, 1));
     if (ok) ok = cudaMallocHost((void**)&c->h_err, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -388,6 +390,7 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
     Z(cudaMemsetAsync(c->lr_pos, 0, std::max<int64_t>(N, 1) * sizeof(float4), c->stream));
     Z(cudaMemsetAsync(c->lr_vel, 0, std::max<int64_t>(N, 1) * sizeof(float4), c->stream));
     Z(cudaMemsetAsync(c->lr_mat, 0, std::max<int64_t>(N, 1) * sizeof(uint32_t), c->stream));
+    Z(cudaMemsetAsync(c->d_cfl, 0, sizeof(CflState), c->stream));
     Z(cudaMemsetAsync(c->tmp4, 0, std::max<int64_t>(std::max(NM, MR), 1) * sizeof(float4), c->stream));
     Z(cudaMemsetAsync(c->lr_cell_start, 0, (cells + 1) * sizeof(uint32_t), c->stream));
     if (z) Z(launch_hr_load(c, c->tmp4, c->hr_pos[0], 1));
@@ -486,12 +489,15 @@ int upsample_impl(gs_ctx* c, float dt)
     return GS_OK;
 }
 
-int step_low_impl(gs_ctx* c, float dt, int iters)
+// dt_dev (adaptive frames): the step length is read from device memory
+// instead of dt; rate: the finalize's atomic max of |v| / (2 r_LR).
+int step_low_impl(gs_ctx* c, float dt, int iters, const float* dt_dev = nullptr, unsigned* rate = nullptr)
 {
     const int64_t N = c->n_low;
     if (N == 0) return GS_OK;
     Timed t(c, GS_TIMER_STEP_LOW);
     PbdArgs a = pbd_args(c, dt);
+    a.dt_dev = dt_dev;
     // prediction fused with the counting stage of the binning of x~; the
     // binning's last stage copies x~ and x into cell order
     CK(gs_cs_clear(c->stream, c->step_cell_start, c->n_cell_total), "clear counts");
@@ -524,7 +530,7 @@ int step_low_impl(gs_ctx* c, float dt, int iters)
             const bool last = it + 1 == total;
             CK(gs_launch_pass(c->stream, a, stab, c->s_x[bx], c->s_xt[bt], c->s_x[bx ^ 1], c->s_xt[bt ^ 1], c->nbr,
                               c->nbr_cnt, &c->launches, last ? c->lr_sorted_idx : nullptr,
-                              last ? c->lr_pos : nullptr, last ? c->lr_vel : nullptr),
+                              last ? c->lr_pos : nullptr, last ? c->lr_vel : nullptr, last ? rate : nullptr),
                "pass");
             bt ^= 1;
             if (stab) bx ^= 1;
@@ -535,7 +541,7 @@ int step_low_impl(gs_ctx* c, float dt, int iters)
         }
     }
     CK(gs_launch_finalize(c->stream, a, c->lr_sorted_idx, c->s_x[bx], c->s_xt[bt], c->lr_pos, c->lr_vel,
-                          &c->launches),
+                          &c->launches, rate),
        "finalize");
     c->lr_binned = false;   // the binning above is of the predicted positions
     return GS_OK;
@@ -543,8 +549,10 @@ int step_low_impl(gs_ctx* c, float dt, int iters)
 
 void drop_graphs(gs_ctx* c)
 {
-    for (auto& g : c->graphs)
+    for (auto& g : c->graphs) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+    }
     c->graphs.clear();
 }
 
@@ -636,7 +644,7 @@ int frame_pipelined_graph(gs_ctx* c, float dt, int n_sub, int iters)
     mix((uint64_t)c->pipe_warps | ((uint64_t)c->pipe_blocks_per_sm << 8) | ((uint64_t)c->n_stab << 16));
     GraphEntry* ge = nullptr;
     for (auto& g : c->graphs)
-        if (g.key == key) ge = &g;
+        if (g.key == key && !g.graph) ge = &g;
     const int64_t frame0 = c->frame;
     const int cur0 = c->hr_cur;
     const bool ident0 = c->hr_identity, keys0 = c->hr_keys_valid, binned0 = c->lr_binned;
@@ -829,7 +837,7 @@ void gs_destroy(gs_ctx* c)
                     c->hr_vals[0], c->hr_vals[1], c->nbr,        c->nbr_cnt,    c->tmp4,      c->sort_hist,
                     c->d_work,     c->d_err,      c->gXs,        c->gVs,       c->snap,      c->snap_xt,
                     c->adj_gx,     c->adj_gxt,    c->adj_h,      c->adj_gws,   c->scan_aux,   c->d_bar,
-                    c->step_cell_start, c->d_sdf_pend, c->stage_in, c->lr_mat, c->d_mu,
+                    c->step_cell_start, c->d_sdf_pend, c->stage_in, c->lr_mat, c->d_mu, c->d_cfl,
                     c->async_in[0], c->async_in[1], c->async_in[2], c->async_in[3],
                     c->async_out[0], c->async_out[1], c->async_out[2], c->async_out[3]};
     for (void* b : bufs)
@@ -1108,6 +1116,127 @@ int gs_set_pipeline(gs_ctx* c, int enable, int warps_per_block, int blocks_per_s
     return GS_OK;
 }
 
+// ---- CFL-limited LR substeps (gs_frame_adaptive) -------------------------
+namespace {
+
+// Frame prologue: reset the control block, then the rate of the current
+// velocities.
+int adaptive_begin(gs_ctx* c, float dt)
+{
+    CK(gs_launch_cfl_begin(c->stream, c->d_cfl, dt, &c->launches), "begin frame");
+    const PbdArgs a = pbd_args(c, dt);
+    CK(gs_launch_cfl_rate(c->stream, a, c->lr_vel, &c->d_cfl->rate, &c->launches), "rate");
+    return GS_OK;
+}
+
+// One LR step: pick its length, then the step reading it, whose finalize
+// accumulates the rate for the next pick.
+int adaptive_step(gs_ctx* c, float dt_max, float cfl, int max_sub, int iters, cudaGraphConditionalHandle h,
+                  int in_graph, unsigned body_kernels)
+{
+    CK(gs_launch_cfl_pick(c->stream, c->d_cfl, dt_max, cfl, max_sub, h, in_graph, body_kernels, &c->launches),
+       "pick step");
+    return step_low_impl(c, dt_max, iters, &c->d_cfl->dt, &c->d_cfl->rate);
+}
+
+// Captures one loop body into `body` (or, with body null, into a throwaway
+// graph to count its launches); *kernels receives the count.
+int capture_body(gs_ctx* c, cudaGraph_t body, float dt_max, float cfl, int max_sub, int iters,
+                 cudaGraphConditionalHandle h, unsigned body_kernels, int64_t* kernels)
+{
+    const int64_t l0 = c->launches;
+    cudaError_t e = body ? cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0,
+                                                         cudaStreamCaptureModeThreadLocal)
+                         : cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
+    int st = adaptive_step(c, dt_max, cfl, max_sub, iters, h, 1, body_kernels);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(c->stream, &g);
+    if (!body && g) cudaGraphDestroy(g);
+    *kernels = c->launches - l0;
+    c->launches = l0;
+    if (st) return st;
+    if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+    return GS_OK;
+}
+
+// The frame as one graph: prologue -> while (more) { pick; LR step } -> HR
+// frame.  The while node's condition starts at 1 on every launch.
+int build_adaptive_graph(gs_ctx* c, float dt, float dt_max, float cfl, int max_sub, int iters, GraphEntry* out)
+{
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0), "create graph");
+    const int64_t l0 = c->launches;
+    int st = GS_OK;
+    cudaError_t e = cudaSuccess;
+    std::vector<cudaGraphNode_t> deps;
+    cudaGraphNode_t wnode = nullptr;
+    do {
+        // 1. prologue, and the nodes the loop depends on
+        e = cudaStreamBeginCaptureToGraph(c->stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        st = adaptive_begin(c, dt);
+        if (st == GS_OK) {
+            cudaStreamCaptureStatus cs;
+            const cudaGraphNode_t* d = nullptr;
+            size_t nd = 0;
+            e = cudaStreamGetCaptureInfo(c->stream, &cs, nullptr, nullptr, &d, nullptr, &nd);
+            if (e == cudaSuccess) deps.assign(d, d + nd);
+        }
+        cudaGraph_t gg = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(c->stream, &gg);
+        if (st != GS_OK || e != cudaSuccess) break;
+        if ((e = e2) != cudaSuccess) break;
+        // 2. the loop
+        cudaGraphConditionalHandle h;
+        e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+        if (e != cudaSuccess) break;
+        cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};   // the rest zero
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(&wnode, g, deps.data(), nullptr, deps.size(), &np);
+        if (e != cudaSuccess) break;
+        int64_t body_kernels = 0;
+        st = capture_body(c, nullptr, dt_max, cfl, max_sub, iters, h, 0u, &body_kernels);
+        if (st) break;
+        st = capture_body(c, np.conditional.phGraph_out[0], dt_max, cfl, max_sub, iters, h, (unsigned)body_kernels,
+                          &body_kernels);
+        if (st) break;
+        // 3. the HR frame after the loop
+        e = cudaStreamBeginCaptureToGraph(c->stream, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        st = upsample_impl(c, dt);
+        e = cudaStreamEndCapture(c->stream, &gg);
+        if (st != GS_OK || e != cudaSuccess) break;
+        e = cudaGraphInstantiate(&out->exec, g, 0);
+    } while (false);
+    out->kernels = c->launches - l0;   // prologue and HR frame; the loop's steps are credited on the device
+    c->launches = l0;
+    if (st != GS_OK || e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        out->exec = nullptr;
+        return st != GS_OK ? st : cuda_fail(c, e, "adaptive frame graph");
+    }
+    out->graph = g;   // a graph with a conditional node stays with its single instantiation
+    return GS_OK;
+}
+
+}  // namespace
+
+// Adds the kernel launches of device-looped LR steps (counted by the step
+// picker) to the context's launch count.  Blocks.
+static int fold_cfl_launches(gs_ctx* c)
+{
+    if (!c->cfl_used) return GS_OK;
+    unsigned long long k = 0;
+    CK(cudaMemcpyAsync(&k, &c->d_cfl->kernels, sizeof(k), cudaMemcpyDeviceToHost, c->stream), "read count");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    c->launches += (int64_t)(k - c->cfl_kernels_seen);
+    c->cfl_kernels_seen = k;
+    return GS_OK;
+}
+
 int gs_frame(gs_ctx* c, float dt, int n_sub, int iters)
 {
     int st = check_state(c);
@@ -1141,7 +1270,7 @@ int gs_frame(gs_ctx* c, float dt, int n_sub, int iters)
                          ((uint64_t)c->tune_blocks_per_sm << 5);
     GraphEntry* ge = nullptr;
     for (auto& g : c->graphs)
-        if (g.key == key) ge = &g;
+        if (g.key == key && !g.graph) ge = &g;
     const int64_t frame0 = c->frame;
     const int cur0 = c->hr_cur;
     if (!ge) {
@@ -1180,6 +1309,85 @@ int gs_frame(gs_ctx* c, float dt, int n_sub, int iters)
     }
     c->lr_binned = c->n_high > 0;
     c->frame = frame0 + 1;
+    return GS_OK;
+}
+
+int gs_frame_adaptive(gs_ctx* c, float dt, float dt_max, float cfl, int max_sub, int iters)
+{
+    int st = check_state(c);
+    if (st) return st;
+    if (!(dt > 0.0f) || !std::isfinite(dt) || !(dt_max > 0.0f) || !std::isfinite(dt_max) || !(cfl > 0.0f) ||
+        !std::isfinite(cfl) || max_sub < 1 || max_sub > GS_MAX_SUBSTEPS || iters < 0 || iters > 1000)
+        return fail(c, GS_ERR_ARG, "invalid adaptive frame arguments");
+    st = settle(c);   // a deferred pipelined HR frame and staged writes come first
+    if (st) return st;
+    c->cfl_used = true;
+    if (!c->use_graphs || c->timing) {
+        // host-driven: the same kernels, the host reads after every step
+        // whether another follows
+        st = adaptive_begin(c, dt);
+        if (st) return st;
+        for (int k = 0; k < max_sub; ++k) {
+            st = adaptive_step(c, dt_max, cfl, max_sub, iters, cudaGraphConditionalHandle{}, 0, 0u);
+            if (st) return st;
+            CK(cudaMemcpyAsync(c->h_err, &c->d_cfl->more, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read");
+            CK(cudaStreamSynchronize(c->stream), "synchronize");
+            if (!*c->h_err) break;
+        }
+        return upsample_impl(c, dt);
+    }
+    const bool resort = c->n_high > 0 && c->resort_every > 0 && c->frame % c->resort_every == 0;
+    uint32_t b[3];
+    std::memcpy(&b[0], &dt, 4);
+    std::memcpy(&b[1], &dt_max, 4);
+    std::memcpy(&b[2], &cfl, 4);
+    uint64_t key = 0xadadadad00000000ull;
+    for (uint64_t v : {(uint64_t)b[0], (uint64_t)b[1], (uint64_t)b[2], (uint64_t)max_sub, (uint64_t)iters,
+                       (uint64_t)resort, (uint64_t)c->hr_cur, (uint64_t)c->tune_warps,
+                       (uint64_t)c->tune_blocks_per_sm})
+        key = (key ^ v) * 0x100000001b3ull;
+    GraphEntry* ge = nullptr;
+    for (auto& g : c->graphs)
+        if (g.key == key && g.graph) ge = &g;
+    const int64_t frame0 = c->frame;
+    const int cur0 = c->hr_cur;
+    if (!ge) {
+        GraphEntry g;
+        g.key = key;
+        st = build_adaptive_graph(c, dt, dt_max, cfl, max_sub, iters, &g);
+        c->frame = frame0;   // the capture only recorded the frame
+        c->hr_cur = cur0;
+        if (st) return st;
+        c->graphs.push_back(g);
+        ge = &c->graphs.back();
+    }
+    CK(cudaGraphLaunch(ge->exec, c->stream), "graph launch");
+    c->launches += ge->kernels;
+    if (resort) {
+        c->hr_cur ^= 1;
+        c->hr_identity = false;
+        c->hr_keys_valid = true;
+    }
+    c->lr_binned = c->n_high > 0;
+    c->frame = frame0 + 1;
+    return GS_OK;
+}
+
+int gs_substeps(gs_ctx* c, float* dts, int cap, int* n_out)
+{
+    int st = check_state(c);
+    if (st) return st;
+    if (!n_out || cap < 0 || (cap > 0 && !dts)) return fail(c, GS_ERR_ARG, "invalid substep buffer");
+    st = settle(c);
+    if (st) return st;
+    CflState h;
+    CK(cudaMemcpyAsync(&h, c->d_cfl, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "read substeps");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    st = fold_cfl_launches(c);
+    if (st) return st;
+    const int n = std::min(std::max(h.taken, 0), GS_MAX_SUBSTEPS);
+    *n_out = n;
+    for (int k = 0; k < std::min(n, cap); ++k) dts[k] = h.log[k];
     return GS_OK;
 }
 
@@ -1448,6 +1656,8 @@ int gs_sync(gs_ctx* c)
     if (st) return st;
     CK(cudaStreamSynchronize(c->stream_h2d), "synchronize host-to-device copies");
     CK(cudaStreamSynchronize(c->stream_d2h), "synchronize device-to-host copies");
+    st = fold_cfl_launches(c);
+    if (st) return st;
     return report_device_errors(c);
 }
 

@@ -58,6 +58,19 @@ struct GraphEntry {
     uint64_t key = 0;
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;    // kernel launches the graph replays
+    cudaGraph_t graph = nullptr;   // kept with the exec when it holds a conditional node
+};
+
+// Device state of an adaptive frame's LR substeps (gs_frame_adaptive).
+struct CflState {
+    float t_rem;                     // frame time left
+    float dt;                        // the current LR step, read by the step's kernels
+    unsigned rate;                   // max |v| / (2 r_LR) as float bits, accumulated by the step's finalize
+    int taken;                       // LR steps taken in this frame
+    int more;                        // 1 while another step follows (read by the host-driven loop)
+    int pad;
+    unsigned long long kernels;      // kernel launches of device-looped steps, for the launch count
+    float log[GS_MAX_SUBSTEPS];      // the frame's step lengths
 };
 
 struct gs_ctx {
@@ -172,6 +185,10 @@ struct gs_ctx {
     // CUDA graphs of whole frames
     bool use_graphs = false;
     std::vector<GraphEntry> graphs;
+    // adaptive frames: device control block, kernel credit folded so far
+    CflState* d_cfl = nullptr;
+    unsigned long long cfl_kernels_seen = 0;
+    bool cfl_used = false;
 
     // errors
     int* d_err = nullptr;
@@ -267,6 +284,7 @@ cudaError_t gs_launch_upsample(cudaStream_t s, const UpsampleArgs& a, int warps_
 struct PbdArgs {
     int64_t n;
     float dt;
+    const float* dt_dev;   // not null: the step length is *dt_dev (adaptive frames), not dt
     const SceneDev* scenes;
     const uint32_t* lr_scene;
     const gs_sdf* sdf;
@@ -289,10 +307,12 @@ cudaError_t gs_launch_neighbors(cudaStream_t s, const PbdArgs& a, const float4* 
 // One Jacobi pass.  With fin_idx not null the pass is the step's last: it
 // writes the finalized position and velocity to original order (fin_pos,
 // fin_vel through fin_idx) instead of x_out / xt_out.
+// fin_rate (not null, last pass only): atomic max of |v| / (2 r_LR) of the
+// finalized velocities, as float bits.
 cudaError_t gs_launch_pass(cudaStream_t s, const PbdArgs& a, int stab, const float4* x_in, const float4* xt_in,
                            float4* x_out, float4* xt_out, const uint32_t* nbr, const uint32_t* cnt,
                            int64_t* launches, const uint32_t* fin_idx = nullptr, float4* fin_pos = nullptr,
-                           float4* fin_vel = nullptr);
+                           float4* fin_vel = nullptr, unsigned* fin_rate = nullptr);
 // Prediction + cell keys + arrival ranks (the counting stage of the binning).
 cudaError_t gs_launch_predict_keys(cudaStream_t s, const PbdArgs& a, const float4* pos, const float4* vel,
                                    float4* xt, uint32_t* keys, uint32_t* rank, uint32_t* cnt, int64_t* launches);
@@ -305,7 +325,16 @@ cudaError_t gs_launch_solve(cudaStream_t s, const PbdArgs& a, int n_stab, int it
                             const uint32_t* nbr, const uint32_t* cnt, unsigned* bar, int* err, int max_blocks,
                             int64_t* launches, unsigned extra_arrivals = 0);
 cudaError_t gs_launch_finalize(cudaStream_t s, const PbdArgs& a, const uint32_t* idx, const float4* s_x,
-                               const float4* s_xt, float4* pos, float4* vel, int64_t* launches);
+                               const float4* s_xt, float4* pos, float4* vel, int64_t* launches,
+                               unsigned* rate = nullptr);
+// CFL-limited substeps (gs_frame_adaptive): reset the control block for a
+// frame of t seconds; the largest |v| / (2 r_LR) of vel into st->rate; pick
+// the next step (and, in a graph, set the while node's condition).
+cudaError_t gs_launch_cfl_begin(cudaStream_t s, CflState* st, float t, int64_t* launches);
+cudaError_t gs_launch_cfl_rate(cudaStream_t s, const PbdArgs& a, const float4* vel, unsigned* rate,
+                               int64_t* launches);
+cudaError_t gs_launch_cfl_pick(cudaStream_t s, CflState* st, float dt_max, float cfl, int max_sub,
+                               cudaGraphConditionalHandle h, int in_graph, unsigned body_kernels, int64_t* launches);
 
 // adjoint.cu
 cudaError_t gs_launch_upsample_bwd(cudaStream_t s, const SceneDev* scenes, const gs_sdf* sdf, const float4* lr_spos,

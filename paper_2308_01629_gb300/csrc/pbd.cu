@@ -28,17 +28,31 @@
 
 namespace {
 
+// The step length: a kernel parameter, or (adaptive frames) the value the
+// substep picker left in device memory.
+__device__ __forceinline__ float step_dt(const PbdArgs& a) { return a.dt_dev ? *a.dt_dev : a.dt; }
+
+// |v| / (2 r_LR) in float32 with correctly rounded operations and no fused
+// multiply-add (the CFL rate of gs_frame_adaptive), as float bits: the
+// value is >= 0, so the bits order like the values.
+__device__ __forceinline__ unsigned cfl_rate_bits(float vx, float vy, float vz, float r_low)
+{
+    const float s = __fadd_rn(__fadd_rn(__fmul_rn(vx, vx), __fmul_rn(vy, vy)), __fmul_rn(vz, vz));
+    return __float_as_uint(__fdiv_rn(__fsqrt_rn(s), __fmul_rn(2.0f, r_low)));
+}
+
 __global__ void k_predict(const PbdArgs a, const float4* __restrict__ pos, const float4* __restrict__ vel,
                           float4* __restrict__ xt)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const SceneDev& sc = a.scenes[a.lr_scene[i]];
+    const float dt = step_dt(a);
     float4 x = pos[i], v = vel[i];
-    float vx = v.x + a.dt * sc.gx, vy = v.y + a.dt * sc.gy, vz = v.z + a.dt * sc.gz;
+    float vx = v.x + dt * sc.gx, vy = v.y + dt * sc.gy, vz = v.z + dt * sc.gz;
     // 1/m* = (1/m) e^{h(x)}, h = k (z - ground), at the start-of-step position
     float ws = x.w * expf(sc.mass_k * (x.z - sc.ground_z));
-    xt[i] = make_float4(x.x + a.dt * vx, x.y + a.dt * vy, x.z + a.dt * vz, ws);
+    xt[i] = make_float4(x.x + dt * vx, x.y + dt * vy, x.z + dt * vz, ws);
 }
 
 // Prediction fused with the first stage of the binning: x~ as above, then
@@ -50,10 +64,11 @@ __global__ void k_predict_keys(const PbdArgs a, const float4* __restrict__ pos, 
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const SceneDev& sc = a.scenes[a.lr_scene[i]];
+    const float dt = step_dt(a);
     float4 x = pos[i], v = vel[i];
-    float vx = v.x + a.dt * sc.gx, vy = v.y + a.dt * sc.gy, vz = v.z + a.dt * sc.gz;
+    float vx = v.x + dt * sc.gx, vy = v.y + dt * sc.gy, vz = v.z + dt * sc.gz;
     float ws = x.w * expf(sc.mass_k * (x.z - sc.ground_z));
-    const float4 p = make_float4(x.x + a.dt * vx, x.y + a.dt * vy, x.z + a.dt * vz, ws);
+    const float4 p = make_float4(x.x + dt * vx, x.y + dt * vy, x.z + dt * vz, ws);
     xt[i] = p;
     const uint32_t cell = grid_cell_of(sc, p.x, p.y, p.z);
     keys[i] = cell;
@@ -269,6 +284,7 @@ struct FinalOut {
     const uint32_t* idx;   // null: write the pass's outputs instead
     float4* pos;
     float4* vel;
+    unsigned* rate;        // not null: atomic max of the CFL rate of the new velocities
 };
 
 // kMat: grains carry materials (their ids in the w of x); a pair's
@@ -279,7 +295,7 @@ __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_
                                               const float4* __restrict__ x_in, const float4* __restrict__ xt_in,
                                               float4* __restrict__ x_out, float4* __restrict__ xt_out,
                                               const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ cnt,
-                                              const FinalOut fin = FinalOut{nullptr, nullptr, nullptr})
+                                              const FinalOut fin = FinalOut{nullptr, nullptr, nullptr, nullptr})
 {
     const SceneDev& sc = a.scenes[valid ? a.lr_scene[p] : 0];
     const float d0 = 2.0f * sc.r_low;
@@ -330,6 +346,7 @@ __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_
             gmu_s = mu.x;
             gmu_k = mu.y;
         }
+        const float sdt = step_dt(a);
         int gc = 0;
         for (int sI = 0; sI < sc.n_sdf; ++sI) {
             const gs_sdf& b = a.sdf[sc.sdf_begin + sI];
@@ -344,7 +361,7 @@ __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_
                 acc.Dz += pen * h.nz;
                 if (!stab) {
                     const float bmu_s = sqrtf(gmu_s * b.mu_s), bmu_k = sqrtf(gmu_k * b.mu_k);
-                    const float rx = dpx - b.vel[0] * a.dt, ry = dpy - b.vel[1] * a.dt, rz = dpz - b.vel[2] * a.dt;
+                    const float rx = dpx - b.vel[0] * sdt, ry = dpy - b.vel[1] * sdt, rz = dpz - b.vel[2] * sdt;
                     const Tangent tg = tangent_part(rx, ry, rz, h.nx, h.ny, h.nz, 1.0f);
                     const float base = sc.friction_mode == 1 ? pen : d0;
                     const float f = friction_scale(tg.L, base * bmu_s, base * bmu_k);
@@ -363,10 +380,12 @@ __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_
         acc.Dz += __shfl_xor_sync(0xffffffffu, acc.Dz, o);
         acc.n += __shfl_xor_sync(0xffffffffu, acc.n, o);
     }
-    if (!valid || sub != 0) return;
+    const bool writer = valid && sub == 0;
+    const bool reduce = fin.idx && fin.rate;   // the whole warp meets in the rate reduction below
+    if (!writer && !reduce) return;
     float4 nt = xtp;
     float4 nx = xp;
-    if (acc.n > 0) {
+    if (writer && acc.n > 0) {
         const float inv = 1.0f / (float)acc.n;
         const float ux = acc.Dx * inv, uy = acc.Dy * inv, uz = acc.Dz * inv;
         nt.x += ux;
@@ -379,12 +398,22 @@ __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_
         }
     }
     if (fin.idx) {
-        const uint32_t i = fin.idx[p];
-        fin.vel[i] = make_float4((nt.x - nx.x) / a.dt, (nt.y - nx.y) / a.dt, (nt.z - nx.z) / a.dt, 0.0f);
-        // with materials x.w holds the material id: the inverse mass comes
-        // from the step-start position, which only this thread touches
-        const float w = kMat ? fin.pos[i].w : nx.w;
-        fin.pos[i] = make_float4(nt.x, nt.y, nt.z, w);
+        unsigned q = 0u;
+        if (writer) {
+            const float dt = step_dt(a);
+            const uint32_t i = fin.idx[p];
+            const float4 nv = make_float4((nt.x - nx.x) / dt, (nt.y - nx.y) / dt, (nt.z - nx.z) / dt, 0.0f);
+            fin.vel[i] = nv;
+            // with materials x.w holds the material id: the inverse mass comes
+            // from the step-start position, which only this thread touches
+            const float w = kMat ? fin.pos[i].w : nx.w;
+            fin.pos[i] = make_float4(nt.x, nt.y, nt.z, w);
+            if (reduce) q = cfl_rate_bits(nv.x, nv.y, nv.z, sc.r_low);
+        }
+        if (reduce) {
+            q = __reduce_max_sync(0xffffffffu, q);
+            if ((threadIdx.x & 31) == 0 && q != 0u) atomicMax(fin.rate, q);
+        }
         return;
     }
     st_pos<kL2>(xt_out + p, nt);
@@ -490,15 +519,80 @@ __global__ void __launch_bounds__(128, 6) k_solve(const SolveArgs s)
 }
 
 __global__ void k_finalize(const PbdArgs a, const uint32_t* __restrict__ idx, const float4* __restrict__ s_x,
-                           const float4* __restrict__ s_xt, float4* __restrict__ pos, float4* __restrict__ vel)
+                           const float4* __restrict__ s_xt, float4* __restrict__ pos, float4* __restrict__ vel,
+                           unsigned* rate)
 {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.n) return;
-    const uint32_t i = idx[p];
-    const float4 x = s_x[p], xt = s_xt[p];
-    vel[i] = make_float4((xt.x - x.x) / a.dt, (xt.y - x.y) / a.dt, (xt.z - x.z) / a.dt, 0.0f);
-    const float w = a.mu_cross ? pos[i].w : x.w;   // x.w is the material id with materials
-    pos[i] = make_float4(xt.x, xt.y, xt.z, w);
+    unsigned q = 0u;
+    if (p < a.n) {
+        const float dt = step_dt(a);
+        const uint32_t i = idx[p];
+        const float4 x = s_x[p], xt = s_xt[p];
+        const float4 nv = make_float4((xt.x - x.x) / dt, (xt.y - x.y) / dt, (xt.z - x.z) / dt, 0.0f);
+        vel[i] = nv;
+        const float w = a.mu_cross ? pos[i].w : x.w;   // x.w is the material id with materials
+        pos[i] = make_float4(xt.x, xt.y, xt.z, w);
+        if (rate) q = cfl_rate_bits(nv.x, nv.y, nv.z, a.scenes[a.lr_scene[i]].r_low);
+    }
+    if (rate) {   // whole warps: the launch covers multiples of 32 threads
+        q = __reduce_max_sync(0xffffffffu, q);
+        if ((threadIdx.x & 31) == 0 && q != 0u) atomicMax(rate, q);
+    }
+}
+
+// ---- CFL-limited LR substeps of a frame (gs_frame_adaptive) ----------------
+__global__ void k_cfl_begin(CflState* st, float t)
+{
+    st->t_rem = t;
+    st->dt = 0.0f;
+    st->rate = 0u;
+    st->taken = 0;
+    st->more = 1;
+}
+
+__global__ void k_cfl_rate(const PbdArgs a, const float4* __restrict__ vel, unsigned* rate)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned q = 0u;
+    if (i < a.n) {
+        const float4 v = vel[i];
+        q = cfl_rate_bits(v.x, v.y, v.z, a.scenes[a.lr_scene[i]].r_low);
+    }
+    q = __reduce_max_sync(0xffffffffu, q);
+    if ((threadIdx.x & 31) == 0 && q != 0u) atomicMax(rate, q);
+}
+
+// One thread.  limit = min(dt_max, cfl / rate) (dt_max for rate 0, 0 for a
+// rate that is not finite); n = ceil(t_rem / limit) within the steps still
+// allowed; this step = t_rem / n; the frame ends with the step of n = 1.
+// n <= max_sub - taken, and taken grows by one per call, so a frame takes
+// at most max_sub steps whatever the velocities.
+__global__ void k_cfl_pick(CflState* st, float dt_max, float cfl, int max_sub, cudaGraphConditionalHandle h,
+                           int in_graph, unsigned body_kernels)
+{
+    const float rate = __uint_as_float(st->rate);
+    st->rate = 0u;   // the step's finalize accumulates the next rate
+    float lim = dt_max;
+    if (!(rate <= 3.40282347e38f)) lim = 0.0f;
+    else if (rate > 0.0f) lim = fminf(dt_max, __fdiv_rn(cfl, rate));
+    const int left = max_sub - st->taken;
+    int n = left;
+    if (left > 1) {
+        const float q = lim > 0.0f ? __fdiv_rn(st->t_rem, lim) : __int_as_float(0x7f800000);
+        if (q < (float)left) n = max(1, (int)ceilf(q));
+    } else {
+        n = 1;
+    }
+    const float dt = __fdiv_rn(st->t_rem, (float)n);
+    st->dt = dt;
+    if (st->taken >= 0 && st->taken < GS_MAX_SUBSTEPS) st->log[st->taken] = dt;
+    st->taken += 1;
+    st->t_rem = n > 1 ? __fsub_rn(st->t_rem, dt) : 0.0f;
+    st->more = n > 1 ? 1 : 0;
+    if (in_graph) {
+        st->kernels += body_kernels;
+        cudaGraphSetConditional(h, n > 1 ? 1u : 0u);
+    }
 }
 
 }  // namespace
@@ -548,10 +642,11 @@ cudaError_t gs_launch_neighbors(cudaStream_t s, const PbdArgs& a, const float4* 
 
 cudaError_t gs_launch_pass(cudaStream_t s, const PbdArgs& a, int stab, const float4* x_in, const float4* xt_in,
                            float4* x_out, float4* xt_out, const uint32_t* nbr, const uint32_t* cnt,
-                           int64_t* launches, const uint32_t* fin_idx, float4* fin_pos, float4* fin_vel)
+                           int64_t* launches, const uint32_t* fin_idx, float4* fin_pos, float4* fin_vel,
+                           unsigned* fin_rate)
 {
     if (a.n <= 0) return cudaSuccess;
-    const FinalOut fin{fin_idx, fin_pos, fin_vel};
+    const FinalOut fin{fin_idx, fin_pos, fin_vel, fin_idx ? fin_rate : nullptr};
     if (a.mu_cross)
         k_pass<true><<<gs_blocks(a.n * kLanes, 128), 128, 0, s>>>(a, stab, x_in, xt_in, x_out, xt_out, nbr, cnt, fin);
     else
@@ -602,10 +697,33 @@ cudaError_t gs_launch_solve(cudaStream_t s, const PbdArgs& a, int n_stab, int it
 }
 
 cudaError_t gs_launch_finalize(cudaStream_t s, const PbdArgs& a, const uint32_t* idx, const float4* s_x,
-                               const float4* s_xt, float4* pos, float4* vel, int64_t* launches)
+                               const float4* s_xt, float4* pos, float4* vel, int64_t* launches, unsigned* rate)
 {
     if (a.n <= 0) return cudaSuccess;
-    k_finalize<<<gs_blocks(a.n, 256), 256, 0, s>>>(a, idx, s_x, s_xt, pos, vel);
+    k_finalize<<<gs_blocks(a.n, 256), 256, 0, s>>>(a, idx, s_x, s_xt, pos, vel, rate);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_cfl_begin(cudaStream_t s, CflState* st, float t, int64_t* launches)
+{
+    k_cfl_begin<<<1, 1, 0, s>>>(st, t);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_cfl_rate(cudaStream_t s, const PbdArgs& a, const float4* vel, unsigned* rate, int64_t* launches)
+{
+    if (a.n <= 0) return cudaSuccess;
+    k_cfl_rate<<<gs_blocks(a.n, 256), 256, 0, s>>>(a, vel, rate);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_cfl_pick(cudaStream_t s, CflState* st, float dt_max, float cfl, int max_sub,
+                               cudaGraphConditionalHandle h, int in_graph, unsigned body_kernels, int64_t* launches)
+{
+    k_cfl_pick<<<1, 1, 0, s>>>(st, dt_max, cfl, max_sub, h, in_graph, body_kernels);
     *launches += 1;
     return cudaGetLastError();
 }

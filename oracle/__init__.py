@@ -68,6 +68,9 @@ def _L():
         L.or_upsample.argtypes = [P, P, ctypes.c_long, P, P, ctypes.c_long, P, ctypes.c_long,
                                   P, ctypes.c_int, P, ctypes.c_int, P, P, P, P, P, P]
         L.or_upsample.restype = ctypes.c_int
+        L.or_upsample_solid.argtypes = [P, P, P, ctypes.c_long, P, P, ctypes.c_long, P, ctypes.c_long,
+                                        P, ctypes.c_int, P, ctypes.c_int, P, P, P, P, P, P]
+        L.or_upsample_solid.restype = ctypes.c_int
         L.or_pbd_step.argtypes = [P, P, P, ctypes.c_long, P, ctypes.c_int, P, ctypes.c_int, P, P]
         L.or_pbd_step.restype = ctypes.c_int
         L.or_pbd_step_mu.argtypes = [P, P, P, ctypes.c_long, P, ctypes.c_int, P, ctypes.c_int, P, P, P]
@@ -163,10 +166,13 @@ def _prm(d, keys):
     return np.array([float(d[k]) for k in keys], dtype=np.float64)
 
 
-def upsample(lr_x, lr_v, hr_x, hr_v, sdf, prm, sub=None, mode=0):
+def upsample(lr_x, lr_v, hr_x, hr_v, sdf, prm, sub=None, mode=0, solid=None):
     """One HR frame of Sec. 4 for HR particles ``sub`` (all when None).
 
     ``prm`` holds r_low, r_high, dt, gx, gy, gz, c1, c2, eps_w, eps_x.
+    ``solid`` (optional, one flag per LR particle) marks LR particles of
+    infinite mass (sampled boundaries, rigid bodies): they count in the
+    weights unless no grain reaches the HR particle.
     Returns dict(x, v, flag, alt_x, alt_v, diag) with diag = (S, wmax, alpha, n,
     sens_x, sens_v).
     """
@@ -178,10 +184,16 @@ def upsample(lr_x, lr_v, hr_x, hr_v, sdf, prm, sub=None, mode=0):
     n = len(hr_x) if subv is None else len(subv)
     out = dict(x=np.zeros((n, 3)), v=np.zeros((n, 3)), flag=np.zeros(n, np.int32),
                alt_x=np.zeros((n, 3)), alt_v=np.zeros((n, 3)), diag=np.zeros((n, 6)))
-    rc = _L().or_upsample(_ptr(lr_x), _ptr(lr_v), len(lr_x), _ptr(hr_x), _ptr(hr_v), len(hr_x),
-                          _ptr(subv), 0 if subv is None else len(subv), _ptr(sdf), len(sdf), _ptr(p),
-                          int(mode), _ptr(out["x"]), _ptr(out["v"]), _ptr(out["flag"]),
-                          _ptr(out["alt_x"]), _ptr(out["alt_v"]), _ptr(out["diag"]))
+    args = (_ptr(hr_x), _ptr(hr_v), len(hr_x), _ptr(subv), 0 if subv is None else len(subv), _ptr(sdf), len(sdf),
+            _ptr(p), int(mode), _ptr(out["x"]), _ptr(out["v"]), _ptr(out["flag"]), _ptr(out["alt_x"]),
+            _ptr(out["alt_v"]), _ptr(out["diag"]))
+    if solid is None:
+        rc = _L().or_upsample(_ptr(lr_x), _ptr(lr_v), len(lr_x), *args)
+    else:
+        solid = np.ascontiguousarray(np.asarray(solid).astype(np.uint8))
+        if len(solid) != len(lr_x):
+            raise ValueError("solid needs one flag per LR particle")
+        rc = _L().or_upsample_solid(_ptr(lr_x), _ptr(lr_v), _ptr(solid), len(lr_x), *args)
     if rc != 0:
         raise RuntimeError(f"or_upsample failed ({rc})")
     return out

@@ -405,12 +405,20 @@ static void hr_finish(const double* x0, const double* v0, const double* vt, doub
  * diag (optional, 6 per output): sum w, max w, alpha, #LR with w > 0, and
  * the sensitivities |d x_out / d x_in| - 1 and |d v_out / d x_in| of the SDF
  * rule (0 without an active contact). */
+/* solid (optional, N): 1 for LR particles of infinite mass (particle-sampled
+ * boundaries and rigid bodies, Sec. 3), 0 for grains.  Sec. 4 counts both
+ * in the weights, except that an HR particle with no grain of positive
+ * weight in its support ignores the solid ones (the paper's rule against HR
+ * particles sticking to rigid bodies moved externally): sum w = 0, alpha =
+ * 1, ballistic motion.  A grain whose t = 1 - |x_ij|^2 / (9 r_LR^2) lies
+ * within kRuleEps of 0 makes that decision ambiguous (flag 2). */
+#define kRuleEps 4e-6
 static int upsample_impl(const double* lr_x, const double* lr_v, long N,
                          const double* hr_x, const double* hr_v, long M,
                          const long* sub, long n_sub,
                          const double* sdf, int n_sdf, const double* prm, int mode,
                          double* out_x, double* out_v, int* flag, double* alt_x, double* alt_v, double* diag,
-                         int tmode, uint32_t* tape)
+                         int tmode, uint32_t* tape, const unsigned char* solid)
 {
     double r = prm[UP_R_LOW], c1 = prm[UP_C1], c2 = prm[UP_C2], eps_w = prm[UP_EPS_W];
     double R2 = 9.0 * r * r;
@@ -432,17 +440,40 @@ static int upsample_impl(const double* lr_x, const double* lr_v, long N,
         double S = 0, V[3] = {0, 0, 0}, wmax = 0;
         long cnt = 0, jstar = -1;
         long nc = N;
+        int grain_hit = 0, grain_edge = 0;
         if (mode == 1) nc = grid_query(&grid, xi, cand);
         for (long q = 0; q < nc; ++q) {
             long j = cand ? cand[q] : q;
             double d[3] = {xi[0] - lr_x[3 * j], xi[1] - lr_x[3 * j + 1], xi[2] - lr_x[3 * j + 2]};
             double d2 = dot3(d, d);
+            if (solid && !solid[j] && fabs(1.0 - d2 / R2) <= kRuleEps) grain_edge = 1;
             if (!(d2 < R2)) continue;
             double w = or_weight(d2, r);
+            if (solid && !solid[j] && w > 0 && 1.0 - d2 / R2 > kRuleEps) grain_hit = 1;
             S += w;
             for (int m = 0; m < 3; ++m) V[m] += w * lr_v[3 * j + m];
             if (w > wmax) { wmax = w; jstar = j; }
             ++cnt;
+        }
+        int rule_amb = 0;
+        if (solid && !grain_hit) {
+            /* no grain in reach (or only at the edge of the support): the
+             * solid particles are ignored */
+            rule_amb = grain_edge && S > 0;
+            int any_grain = 0;
+            for (long q = 0; q < nc && !any_grain; ++q) {
+                long j = cand ? cand[q] : q;
+                if (solid[j]) continue;
+                double d[3] = {xi[0] - lr_x[3 * j], xi[1] - lr_x[3 * j + 1], xi[2] - lr_x[3 * j + 2]};
+                if (dot3(d, d) < R2 && or_weight(dot3(d, d), r) > 0) any_grain = 1;
+            }
+            if (!any_grain) {
+                S = 0;
+                V[0] = V[1] = V[2] = 0;
+                wmax = 0;
+                jstar = -1;
+                cnt = 0;
+            }
         }
         /* tape record of one HR particle: {argmax LR index, blend branch,
          * SDF active bits, velocity removal bits} */
@@ -478,7 +509,7 @@ static int upsample_impl(const double* lr_x, const double* lr_v, long N,
         if (Bamb && (A || (!B)) != prim) alt_out = !prim;
         if (Aamb && Bamb && ((!A) || (!B)) != prim) alt_out = !prim;
         double alpha = prim ? 1.0 - wmax : 0.0;
-        int amb[64], n_amb = 0, hard = 0, n_act = 0;
+        int amb[64], n_amb = 0, hard = rule_amb, n_act = 0;
         double xo[3], vo[3];
         hr_finish(xi, vi, vt, alpha, sdf, n_sdf, prm, -1, xo, vo, amb, &n_amb, &hard, &n_act, tmode,
                   tp ? tp + 2 : NULL);
@@ -554,7 +585,20 @@ int or_upsample(const double* lr_x, const double* lr_v, long N,
                 double* out_x, double* out_v, int* flag, double* alt_x, double* alt_v, double* diag)
 {
     return upsample_impl(lr_x, lr_v, N, hr_x, hr_v, M, sub, n_sub, sdf, n_sdf, prm, mode, out_x, out_v, flag,
-                         alt_x, alt_v, diag, TAPE_OFF, NULL);
+                         alt_x, alt_v, diag, TAPE_OFF, NULL, NULL);
+}
+
+/* or_upsample with particle-sampled boundaries and rigid bodies: solid[j]
+ * = 1 marks LR particle j as one of infinite mass (see upsample_impl). */
+int or_upsample_solid(const double* lr_x, const double* lr_v, const unsigned char* solid, long N,
+                      const double* hr_x, const double* hr_v, long M,
+                      const long* sub, long n_sub,
+                      const double* sdf, int n_sdf, const double* prm, int mode,
+                      double* out_x, double* out_v, int* flag, double* alt_x, double* alt_v, double* diag)
+{
+    if (!solid && N > 0) return -1;
+    return upsample_impl(lr_x, lr_v, N, hr_x, hr_v, M, sub, n_sub, sdf, n_sdf, prm, mode, out_x, out_v, flag,
+                         alt_x, alt_v, diag, TAPE_OFF, NULL, solid);
 }
 
 static int total_components(const double* sdf, int n_sdf)
@@ -572,7 +616,7 @@ int or_upsample_tape(const double* lr_x, const double* lr_v, long N, const doubl
 {
     if ((tmode != TAPE_RECORD && tmode != TAPE_REPLAY) || !tape || total_components(sdf, n_sdf) > 32) return -1;
     return upsample_impl(lr_x, lr_v, N, hr_x, hr_v, M, NULL, 0, sdf, n_sdf, prm, 1, out_x, out_v, NULL, NULL, NULL,
-                         NULL, tmode, tape);
+                         NULL, tmode, tape, NULL);
 }
 
 /* ------------------------------------------------------------------ */
@@ -759,10 +803,12 @@ static int pbd_impl(double* x, double* v, const double* inv_m, long N,
     if (!xt || !ws || !D || !cnt || !mark || !mark2) return -1;
 
     /* Algorithm 1, first loop: v += dt g; xt = x + dt v; m* = m e^{-h(x)}.
-     * Stored as the inverse scaled mass 1/m* = m^-1 e^{h}. */
+     * Stored as the inverse scaled mass 1/m* = m^-1 e^{h}.  Particles of
+     * infinite mass (m^-1 = 0: sampled boundaries and rigid bodies, Sec. 3)
+     * keep their prescribed velocity: no gravity. */
     for (long i = 0; i < N; ++i) {
         for (int k = 0; k < 3; ++k) {
-            v[3 * i + k] += dt * g[k];
+            if (inv_m[i] > 0) v[3 * i + k] += dt * g[k];
             xt[3 * i + k] = x[3 * i + k] + dt * v[3 * i + k];
         }
         ws[i] = inv_m[i] * exp(mass_k * (x[3 * i + 2] - ground));

@@ -69,6 +69,7 @@ def parse(argv=None):
     ap.add_argument("--no-diff", action="store_true")
     ap.add_argument("--no-materials", action="store_true", help="skip the grain-material frame timing")
     ap.add_argument("--no-adaptive", action="store_true", help="skip the CFL-limited substep frame timing")
+    ap.add_argument("--no-solid", action="store_true", help="skip the particle-sampled bucket frame timing")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="do not try pipelined frames (HR frame overlapping the next frame's LR steps)")
     ap.add_argument("--batch-scenes", type=int, default=256)
@@ -513,6 +514,28 @@ def run_gpu(args):
                     "timing": "median of 3 alternating runs of 8 graph-replayed frames, L2 not flushed; the "
                               "adaptive frame's LR steps run in a device-side loop (conditional graph node)"}
 
+    # particle-sampled rigid body (Sec. 3 / Sec. 4): the same bed with the
+    # bucket sampled as LR particles of inverse mass 0 (moving with the
+    # bucket's velocity) instead of the bucket SDF, in a second context,
+    # timed alike against the SDF bucket's frames
+    solid = None
+    if not args.no_solid and args.workload == "digging":
+        ps = scenes.digging_particle_bucket(size=args.bed_size)
+        pctx = gs.Context(ps, stream=stream.cuda_stream)
+        pctx.set_tuning(tune_w, tune_b)
+        pctx.set_graphs(True)
+        tried = {"sdf_bucket": [], "particle_bucket": []}
+        for _ in range(3):
+            tried["sdf_bucket"].append(frame_ms(lambda: step(ctx), stream, dev, torch, warm=3, reps=8))
+            tried["particle_bucket"].append(frame_ms(lambda: pctx.frame(DT, N_SUB, ps["iters"]), stream, dev,
+                                                     torch, warm=3, reps=8))
+        pctx.sync()
+        pctx.close()
+        solid = {"bucket_particles": int(ps["n_solid"]), "n_low": len(ps["lr_pos"]),
+                 "frame_ms_sdf_bucket": float(np.median(tried["sdf_bucket"])),
+                 "frame_ms_particle_bucket": float(np.median(tried["particle_bucket"])),
+                 "timing": "median of 3 alternating runs of 8 graph-replayed frames, L2 not flushed"}
+
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -611,6 +634,7 @@ def run_gpu(args):
         "differentiable": differentiable,
         "materials": materials,
         "adaptive_substeps": adaptive,
+        "solid_particles": solid,
     }
     if not args.no_cpu:
         line["cpu_baseline"] = oracle_frame_rate(sc, args.cpu_seconds)

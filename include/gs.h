@@ -104,7 +104,11 @@ typedef struct {
  * Grid cells of scene s are numbered from its cell offset, and every scene
  * owns one extra padding cell after its real cells. */
 enum {
-    GS_FIELD_LR_POS = 0,         /* float4[n_low], read / write */
+    GS_FIELD_LR_POS = 0,         /* float4[n_low], read / write; w = inverse mass 1/m.  w = 0 marks a
+                                    particle of a sampled boundary or rigid body (Sec. 3): it feels no
+                                    gravity, moves with its velocity (GS_FIELD_LR_VEL, set by the
+                                    caller), is an infinite mass in contacts, and counts in the
+                                    upsampling weights only where a grain reaches the HR particle */
     GS_FIELD_LR_VEL = 1,         /* float4[n_low], read / write */
     GS_FIELD_HR_POS = 2,         /* float4[n_high], read / write (w is set to the id on write) */
     GS_FIELD_HR_VEL = 3,         /* float4[n_high], read / write */
@@ -219,7 +223,11 @@ int gs_resort_high(gs_ctx* ctx);
  * the next blocking call. */
 int gs_step_low(gs_ctx* ctx, float dt, int iters);
 
-/* One HR frame of Sec. 4 from the current LR state (x^{t+1}, v^{t+1}):
+/* One HR frame of Sec. 4 from the current LR state (x^{t+1}, v^{t+1}).
+ * LR particles of infinite mass (w = 0) count in the sums below, except for
+ * an HR particle that no grain reaches with a positive weight: there they
+ * are ignored (sum w = 0, so alpha = 1), the paper's rule against HR
+ * particles sticking to rigid bodies that are moved externally.  In order:
  * (re)bin the LR particles, reorder HR when due, then for every HR particle
  * w_ij = max(0, (1 - |x_ij|^2 / (9 r_low^2))^3) over LR within 3 r_low,
  * vtilde = sum w v / sum w (0 when the sum is 0),
@@ -375,7 +383,9 @@ int gs_upsample_backward(gs_ctx* ctx, const float* lr_pos, const float* lr_vel, 
  * pass's branch decisions (contact sets, static / kinetic / clipped
  * friction, SDF contacts with fixed normals), including the dependence of the
  * height-scaled mass ratios on the start-of-step heights.  Outputs are
- * overwritten.  Asynchronous. */
+ * overwritten.  Asynchronous.  Both backward entry points differentiate
+ * grains only: they return GS_ERR_STATE (and wait for the stream) when the
+ * LR positions hold particles of inverse mass 0. */
 int gs_step_low_forward(gs_ctx* ctx, const float* x_in, const float* v_in, float* x_out, float* v_out, float dt,
                         int iters);
 int gs_step_low_backward(gs_ctx* ctx, const float* x_in, const float* v_in, const float* g_x_out, const float* g_v_out,

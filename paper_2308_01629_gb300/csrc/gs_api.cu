@@ -144,6 +144,14 @@ __global__ void k_max_id(const uint32_t* __restrict__ ids, int64_t n, unsigned* 
     if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
 }
 
+// Number of positions with w = 0 (LR particles of infinite mass) into *out.
+__global__ void k_count_solid(const float4* __restrict__ pos, int64_t n, unsigned* out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned b = __ballot_sync(0xffffffffu, i < n && pos[i].w == 0.0f);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(out, (unsigned)__popc(b));
+}
+
 cudaError_t launch_hr_load(gs_ctx* c, const float4* src, float4* dst, int set_ids)
 {
     if (c->hr_slots <= 0) return cudaSuccess;
@@ -1513,6 +1521,23 @@ int gs_upsample_forward(gs_ctx* c, const float* lr_pos, const float* lr_vel, con
     return GS_OK;
 }
 
+// The reverse modes differentiate grains only: GS_ERR_STATE when the LR
+// positions (device memory, n of them) hold particles of infinite mass.
+static int refuse_solid(gs_ctx* c, const float* pos, int64_t n)
+{
+    if (n <= 0) return GS_OK;
+    unsigned* word = (unsigned*)(c->d_err + 1);
+    CK(cudaMemsetAsync(word, 0, sizeof(unsigned), c->stream), "clear word");
+    k_count_solid<<<gs_blocks(n, 256), 256, 0, c->stream>>>((const float4*)pos, n, word);
+    c->launches += 1;
+    CK(cudaGetLastError(), "count");
+    CK(cudaMemcpyAsync(c->h_err, word, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream), "read word");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    if (*c->h_err != 0)
+        return fail(c, GS_ERR_STATE, "reverse mode with %u LR particles of infinite mass", (unsigned)*c->h_err);
+    return GS_OK;
+}
+
 int gs_upsample_backward(gs_ctx* c, const float* lr_pos, const float* lr_vel, const float* hr_pos_in,
                          const float* hr_vel_in, const float* g_hr_pos_out, const float* g_hr_vel_out, float* g_lr_pos,
                          float* g_lr_vel, float* g_hr_pos_in, float* g_hr_vel_in, float dt)
@@ -1527,6 +1552,8 @@ int gs_upsample_backward(gs_ctx* c, const float* lr_pos, const float* lr_vel, co
     if ((N > 0 && (!lr_pos || !lr_vel || !g_lr_pos || !g_lr_vel)) ||
         (M > 0 && (!hr_pos_in || !hr_vel_in || !g_hr_pos_out || !g_hr_vel_out || !g_hr_pos_in || !g_hr_vel_in)))
         return fail(c, GS_ERR_ARG, "null buffer");
+    st = refuse_solid(c, lr_pos, N);
+    if (st) return st;
     if (N) {
         CK(cudaMemcpyAsync(c->lr_pos, lr_pos, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
         CK(cudaMemcpyAsync(c->lr_vel, lr_vel, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
@@ -1581,6 +1608,8 @@ int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const 
     const int64_t N = c->n_low;
     if (N == 0) return GS_OK;
     if (!x_in || !v_in || !g_x_out || !g_v_out || !g_x_in || !g_v_in) return fail(c, GS_ERR_ARG, "null buffer");
+    st = refuse_solid(c, x_in, N);
+    if (st) return st;
     const int total = c->n_stab + iters;
     if (total > c->snap_cap) {
         if (c->snap) cudaFree(c->snap);

@@ -14,7 +14,9 @@
 //                         min(2 r mu_k / |dx_perp|, 1); with grain
 //                         materials mu = sqrt(mu_i mu_j) per pair (Sec. 3)
 //   averaging:            dx_i = (1 / n_i) sum_k dx_ik
-// SDF contacts act as partners of infinite mass (mass ratio 1).  The
+// SDF contacts act as partners of infinite mass (mass ratio 1), as do LR
+// particles of inverse mass 0 (sampled boundaries and rigid bodies, which
+// move with their prescribed velocity and feel no gravity).  The
 // stabilization passes evaluate their contacts on x and move x and xt; the
 // solver passes evaluate and move xt.
 #include <cuda_runtime.h>
@@ -49,7 +51,10 @@ __global__ void k_predict(const PbdArgs a, const float4* __restrict__ pos, const
     const SceneDev& sc = a.scenes[a.lr_scene[i]];
     const float dt = step_dt(a);
     float4 x = pos[i], v = vel[i];
-    float vx = v.x + dt * sc.gx, vy = v.y + dt * sc.gy, vz = v.z + dt * sc.gz;
+    // particles of infinite mass (1/m = 0: sampled boundaries, rigid bodies)
+    // keep their prescribed velocity
+    const float gdt = x.w > 0.0f ? dt : 0.0f;
+    float vx = v.x + gdt * sc.gx, vy = v.y + gdt * sc.gy, vz = v.z + gdt * sc.gz;
     // 1/m* = (1/m) e^{h(x)}, h = k (z - ground), at the start-of-step position
     float ws = x.w * expf(sc.mass_k * (x.z - sc.ground_z));
     xt[i] = make_float4(x.x + dt * vx, x.y + dt * vy, x.z + dt * vz, ws);
@@ -66,7 +71,8 @@ __global__ void k_predict_keys(const PbdArgs a, const float4* __restrict__ pos, 
     const SceneDev& sc = a.scenes[a.lr_scene[i]];
     const float dt = step_dt(a);
     float4 x = pos[i], v = vel[i];
-    float vx = v.x + dt * sc.gx, vy = v.y + dt * sc.gy, vz = v.z + dt * sc.gz;
+    const float gdt = x.w > 0.0f ? dt : 0.0f;   // no gravity for 1/m = 0
+    float vx = v.x + gdt * sc.gx, vy = v.y + gdt * sc.gy, vz = v.z + gdt * sc.gz;
     float ws = x.w * expf(sc.mass_k * (x.z - sc.ground_z));
     const float4 p = make_float4(x.x + dt * vx, x.y + dt * vy, x.z + dt * vz, ws);
     xt[i] = p;

@@ -15,6 +15,11 @@
 //   v = (1 - alpha) vtilde + alpha (v + dt g),  x = x + dt v,
 // and applies the SDF rule (project to phi = r_HR, drop the inward normal
 // velocity relative to the boundary), then writes the particle back.
+// LR particles of infinite mass (w of the position 0: sampled boundaries and
+// rigid bodies) are staged from the far end of the buffer and summed apart
+// (per lane, in shared memory); they join the sums only where some grain
+// has a positive weight, so an HR particle with no grain in reach moves
+// ballistically instead of sticking to them (Sec. 4).
 #include <cuda_runtime.h>
 
 #include "gs_internal.cuh"
@@ -22,7 +27,7 @@
 
 namespace {
 
-constexpr int kBuf = 64;   // staged LR per warp; flushed at >= 32
+constexpr int kBuf = 64;   // staged LR per warp (grains from the front, solids from the back); flushed at >= 32
 
 __device__ __forceinline__ int cell_coord(float x, float o, float inv_h, int dim)
 {
@@ -89,7 +94,10 @@ __device__ __forceinline__ int sub_floor(float x, float o, float inv_h)
 }
 
 // One warp item: the 32 HR slots [32 item, 32 item + 32) of one scene.
-__device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t item, float4* ba, float4* bb, int lane)
+// sol: this warp's 5 x 32 sums of solid particles (S, V, max w per lane),
+// zero on entry and on return.
+__device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t item, float4* ba, float4* bb,
+                                              float* sol, int lane)
 {
     const int64_t first = item * 32;
     const uint32_t tag = __ldg(a.hr_tag + first);          // the first slot of an item is never padding
@@ -111,7 +119,8 @@ __device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t ite
     const float inv3r = 1.0f / (3.0f * sc.r_low);
     const int64_t coff = sc.cell_off;
 
-    float S = 0.f, Vx = 0.f, Vy = 0.f, Vz = 0.f, wmax = 0.f;
+    float S = 0.f, Vx = 0.f, Vy = 0.f, Vz = 0.f, wmax = 0.f;   // grains
+    bool any_solid = false;                                    // warp-uniform
     unsigned pending = __ballot_sync(0xffffffffu, valid);
     while (pending) {
         const int leader = __ffs(pending) - 1;
@@ -151,14 +160,36 @@ __device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t ite
             ci = 1.0f - (ux * ux + uy * uy + uz * uz);
         }
 
-        int cnt = 0;
+        int cnt = 0, nsol = 0;
         auto stage = [&](int slot, float4 c, float4 cv) {
             const float wx = (c.x - c0x) * inv3r, wy = (c.y - c0y) * inv3r, wz = (c.z - c0z) * inv3r;
             ba[slot] = make_float4(2.0f * wx, 2.0f * wy, 2.0f * wz, -(wx * wx + wy * wy + wz * wz));
             bb[slot] = make_float4(cv.x, cv.y, cv.z, 0.0f);
         };
-        auto flush = [&](int count) {
+        auto flush = [&](int count, int count_sol) {
             __syncwarp();
+            if (count_sol > 0) {
+                float s = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, sm = 0.f;
+#pragma unroll 1
+                for (int k = kBuf - count_sol; k < kBuf; ++k) {
+                    const float4 ra = ba[k];
+                    const float4 rb = bb[k];
+                    float t = fmaf(ra.x, ux, fmaf(ra.y, uy, fmaf(ra.z, uz, ra.w + ci)));
+                    t = fmaxf(t, 0.0f);
+                    const float w = t * t * t;
+                    s += w;
+                    sx = fmaf(w, rb.x, sx);
+                    sy = fmaf(w, rb.y, sy);
+                    sz = fmaf(w, rb.z, sz);
+                    sm = fmaxf(sm, w);
+                }
+                sol[lane] += s;
+                sol[32 + lane] += sx;
+                sol[64 + lane] += sy;
+                sol[96 + lane] += sz;
+                sol[128 + lane] = fmaxf(sol[128 + lane], sm);
+                any_solid = true;
+            }
 #pragma unroll 4
             for (int k = 0; k < count; ++k) {
                 const float4 ra = ba[k];
@@ -216,16 +247,31 @@ __device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t ite
                     const float ez = fmaxf(fmaxf(lz - c.z, c.z - hz), 0.0f);
                     take = ex * ex + ey * ey + ez * ez < R2;
                 }
-                const unsigned bal = __ballot_sync(0xffffffffu, take);
-                if (take) stage(cnt + __popc(bal & lt), c, cv);
+                const bool solid = take && c.w == 0.0f;
+                const unsigned bal = __ballot_sync(0xffffffffu, take && !solid);
+                const unsigned bsol = __ballot_sync(0xffffffffu, solid);
+                if (take) stage(solid ? kBuf - 1 - (nsol + __popc(bsol & lt)) : cnt + __popc(bal & lt), c, cv);
                 cnt += __popc(bal);
-                if (cnt >= 32) {
-                    flush(cnt);
-                    cnt = 0;
+                nsol += __popc(bsol);
+                if (cnt + nsol >= 32) {   // below 32 before a round of at most 32: the two ends never meet
+                    flush(cnt, nsol);
+                    cnt = nsol = 0;
                 }
             }
         }
-        if (cnt > 0) flush(cnt);
+        if (cnt + nsol > 0) flush(cnt, nsol);
+    }
+    if (any_solid) {
+        // the solid particles count only where a grain has a positive weight
+        if (S > 0.0f) {
+            S += sol[lane];
+            Vx += sol[32 + lane];
+            Vy += sol[64 + lane];
+            Vz += sol[96 + lane];
+            wmax = fmaxf(wmax, sol[128 + lane]);
+        }
+        for (int m = 0; m < 5; ++m) sol[32 * m + lane] = 0.0f;
+        __syncwarp();
     }
 
     if (!valid) return;
@@ -253,7 +299,10 @@ __global__ void __launch_bounds__(WARPS * 32, 24 / WARPS) k_upsample(const Upsam
 {
     __shared__ float4 s_a[WARPS][kBuf];
     __shared__ float4 s_b[WARPS][kBuf];
+    __shared__ float s_sol[WARPS][5 * 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int m = 0; m < 5; ++m) s_sol[warp][32 * m + lane] = 0.0f;
+    __syncwarp();
     // One call site for both launch modes, so both run the same code.  In
     // the persistent mode warps pull items until the counter passes
     // n_warps; every warp leaves after at most n_warps + 1 iterations.
@@ -278,7 +327,7 @@ __global__ void __launch_bounds__(WARPS * 32, 24 / WARPS) k_upsample(const Upsam
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(a.hr_vel + ahead * 32 + lane));
             }
         }
-        upsample_item(a, item, s_a[warp], s_b[warp], lane);
+        upsample_item(a, item, s_a[warp], s_b[warp], s_sol[warp], lane);
     }
 }
 

@@ -338,3 +338,86 @@ def materials(sc, seed, layout="random", table=MATERIALS):
     else:
         raise ValueError(layout)
     return np.asarray(table, np.float32), ids.astype(np.uint32)
+
+
+# ------------------------------------------ particle-sampled solid bodies ---
+# Sec. 3: boundaries and rigid bodies sampled with LR particles of inverse
+# mass 0.  Their HR share is drawn around the grains, so a context of
+# n_low = grains + solids particles and ratio HR per LR holds only granular
+# HR particles.
+def _face_lattice(lo, hi, spacing, axes):
+    """Points on the face of a box where the coordinates `axes` vary (a
+    lattice of the given spacing, centred on the face)."""
+    out = []
+    for a in axes:
+        n = max(int(round((hi[a] - lo[a]) / spacing)) + 1, 1)
+        out.append(np.linspace(lo[a], hi[a], n))
+    g = np.stack(np.meshgrid(*out, indexing="ij"), -1).reshape(-1, len(axes))
+    return g
+
+
+def box_surface(center, half, spacing):
+    """Particles on the surface of an axis-aligned box (each face a lattice,
+    shared edges once)."""
+    c, h = np.asarray(center, float), np.asarray(half, float)
+    lo, hi = c - h, c + h
+    pts = []
+    for a in range(3):
+        b, e = [k for k in range(3) if k != a]
+        face = _face_lattice(lo, hi, spacing, (b, e))
+        for s in (lo[a], hi[a]):
+            p = np.zeros((len(face), 3))
+            p[:, a] = s
+            p[:, b], p[:, e] = face[:, 0], face[:, 1]
+            pts.append(p)
+    p = np.unique(np.round(np.concatenate(pts), 12), axis=0)
+    return p
+
+
+def with_solids(sc, solid_xyz, solid_vel, seed):
+    """A copy of a scene with LR particles of inverse mass 0 appended at
+    solid_xyz (velocities solid_vel) and the HR set redrawn around the
+    grains (ratio x all LR particles, each grain's share in turn)."""
+    rng = np.random.default_rng(seed)
+    sc = dict(sc)
+    n_g = len(sc["lr_pos"])
+    solid_xyz = np.asarray(solid_xyz, float).reshape(-1, 3)
+    lr_pos = np.concatenate([sc["lr_pos"], _pack(solid_xyz, 0.0)])
+    lr_vel = np.concatenate([sc["lr_vel"], np.zeros((len(solid_xyz), 4), np.float32)])
+    lr_vel[n_g:, :3] = np.broadcast_to(np.asarray(solid_vel, np.float32), (len(solid_xyz), 3))
+    m = sc["ratio"] * len(lr_pos)
+    owner = np.arange(m) % max(n_g, 1)
+    hr_xyz = sc["lr_pos"][owner, :3].astype(np.float64) + _ball(rng, m) * sc["r_low"]
+    hr_pos = _pack(hr_xyz, 0.0)
+    hr_pos[:, 3] = hr_ids(m)
+    hr_vel = np.zeros((m, 4), np.float32)
+    hr_vel[:, :3] = sc["hr_vel"][owner % len(sc["hr_vel"]), :3] if len(sc["hr_vel"]) else 0.0
+    sc.update(lr_pos=lr_pos, lr_vel=lr_vel, hr_pos=hr_pos, hr_vel=hr_vel, n_solid=len(solid_xyz))
+    return sc
+
+
+def cube_on_particle_floor(seed=SEED_BASE + 6, v_scale=0.3):
+    """The cube (stirred) standing on a particle-sampled floor instead of the
+    box's floor: a 2 r_LR lattice one radius below the lowest layer, wider
+    than the cube by three particles on each side."""
+    sc = stir(cube(), seed=seed, v_scale=v_scale)
+    r = sc["r_low"]
+    lo = sc["lr_pos"][:, :3].min(0) - 3 * 2 * r
+    hi = sc["lr_pos"][:, :3].max(0) + 3 * 2 * r
+    z = sc["lr_pos"][:, 2].min() - 2 * r
+    face = _face_lattice(lo, hi, 2 * r, (0, 1))
+    floor = np.column_stack([face, np.full(len(face), z)])
+    return with_solids(sc, floor, (0.0, 0.0, 0.0), seed)
+
+
+def digging_particle_bucket(seed=SEED_BASE + 7, t=0.0, **kw):
+    """The digging bed with the bucket sampled as particles (a 2 r_LR lattice
+    on the box surface) moving with the bucket's velocity at time t, in place
+    of the bucket SDF."""
+    sc = digging(**kw)
+    c, u = bucket_pose(t)
+    pts = box_surface(c, BUCKET_HALF, 2 * sc["r_low"])
+    sc = with_solids(sc, pts, u, seed)
+    sc["sdfs"] = [sc["sdfs"][0]]
+    sc.pop("bucket_index", None)
+    return sc

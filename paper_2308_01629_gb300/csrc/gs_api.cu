@@ -343,7 +343,7 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
     A(dalloc(&c->lr_keys[1], N));
     A(dalloc(&c->lr_vals[0], N));
     A(dalloc(&c->lr_vals[1], N));
-    A(dalloc(&c->lr_cell_start, cells + 1));
+    A(dalloc(&c->lr_cell_start, cells + 2));   // + the flag of particles of infinite mass
     A(dalloc(&c->step_cell_start, cells + 1));
     A(dalloc(&c->d_sdf_pend, std::max<size_t>(c->sdf_host.size(), 1)));
     A(dalloc(&c->scan_aux, gs_scan_aux_words(cells + 1)));
@@ -400,7 +400,7 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
     Z(cudaMemsetAsync(c->lr_mat, 0, std::max<int64_t>(N, 1) * sizeof(uint32_t), c->stream));
     Z(cudaMemsetAsync(c->d_cfl, 0, sizeof(CflState), c->stream));
     Z(cudaMemsetAsync(c->tmp4, 0, std::max<int64_t>(std::max(NM, MR), 1) * sizeof(float4), c->stream));
-    Z(cudaMemsetAsync(c->lr_cell_start, 0, (cells + 1) * sizeof(uint32_t), c->stream));
+    Z(cudaMemsetAsync(c->lr_cell_start, 0, (cells + 2) * sizeof(uint32_t), c->stream));
     if (z) Z(launch_hr_load(c, c->tmp4, c->hr_pos[0], 1));
     if (z) Z(launch_hr_load(c, c->tmp4, c->hr_vel[0], 0));
     if (z) Z(cudaStreamSynchronize(c->stream));
@@ -438,9 +438,11 @@ int bin_low_impl(gs_ctx* c)
 {
     Timed t(c, GS_TIMER_BIN_LOW);
     // counting sort by cell; its last stage copies pos and vel into cell order
-    CK(gs_cs_clear(c->stream, c->lr_cell_start, c->n_cell_total), "clear counts");
+    // the word after the cell starts flags LR particles of infinite mass
+    // for the gather (the binning reads every position anyway)
+    CK(gs_cs_clear(c->stream, c->lr_cell_start, c->n_cell_total, 1), "clear counts");
     CK(gs_cs_keys(c->stream, c->lr_pos, c->n_low, c->d_scenes, c->lr_scene, c->lr_keys[0], c->lr_vals[0],
-                  c->lr_cell_start, &c->launches),
+                  c->lr_cell_start, &c->launches, c->lr_cell_start + c->n_cell_total + 1),
        "cell keys");
     CK(gs_cs_finish(c->stream, c->n_low, c->n_cell_total, c->lr_keys[0], c->lr_vals[0], c->lr_keys[1], c->lr_vals[1],
                     c->lr_cell_start, c->scan_aux, c->lr_pos, c->lr_vel, c->lr_spos, c->lr_svel, &c->launches),
@@ -468,6 +470,7 @@ UpsampleArgs upsample_args(const gs_ctx* c, float dt, const float4* in_pos, cons
     u.n_scenes = c->n_scenes;
     u.n_warps = c->n_warps;
     u.work = c->d_work;
+    u.solid_flag = c->lr_cell_start + c->n_cell_total + 1;
     u.dt = dt;
     return u;
 }

@@ -230,9 +230,12 @@ size_t gs_scan_aux_words(int64_t total);
 // clear the counts, count (keys + arrival ranks; gs_cs_keys or a kernel
 // that does the same with grid_cell_of), then scan + scatter + per-cell
 // order; finish also copies ga / gb (when not null) into cell order.
-cudaError_t gs_cs_clear(cudaStream_t s, uint32_t* cell_start, int64_t n_cell);
+// Zeroes the n_cell + 1 cell starts and `extra` words after them.
+cudaError_t gs_cs_clear(cudaStream_t s, uint32_t* cell_start, int64_t n_cell, int extra = 0);
+// solid_flag (optional): set to 1 when some position has w = 0.
 cudaError_t gs_cs_keys(cudaStream_t s, const float4* pos, int64_t n, const SceneDev* scenes, const uint32_t* tag,
-                       uint32_t* keys, uint32_t* rank, uint32_t* cell_start, int64_t* launches);
+                       uint32_t* keys, uint32_t* rank, uint32_t* cell_start, int64_t* launches,
+                       unsigned* solid_flag = nullptr);
 // ga and gb are copied into cell order: x_out[slot] = x[particle of the
 // slot]; with gb_w not null the w of gb's copies is gb_w[particle] (as bits).
 cudaError_t gs_cs_finish(cudaStream_t s, int64_t n, int64_t n_cell, const uint32_t* keys, const uint32_t* rank,
@@ -273,6 +276,7 @@ struct UpsampleArgs {
     int n_scenes;
     int64_t n_warps;           // warp items
     unsigned* work;            // persistent mode: next warp item (zeroed before the launch)
+    const unsigned* solid_flag;   // nonzero: some LR particle has w = 0 (set by the LR binning)
     float dt;
 };
 // blocks_per_sm == 0: one warp per item; else a persistent grid of

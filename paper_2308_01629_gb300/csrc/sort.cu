@@ -205,12 +205,13 @@ __global__ void k_scene_keys(const float4* __restrict__ pos, int64_t n, const Sc
 
 __global__ void k_cs_keys(const float4* __restrict__ pos, int64_t n, const SceneDev* __restrict__ scenes,
                           const uint32_t* __restrict__ tag, uint32_t* __restrict__ keys, uint32_t* __restrict__ rank,
-                          uint32_t* __restrict__ cnt)
+                          uint32_t* __restrict__ cnt, unsigned* solid_flag)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const SceneDev& sc = scenes[tag[i] & ~kPadBit];
     const float4 p = pos[i];
+    if (solid_flag && p.w == 0.0f) atomicOr(solid_flag, 1u);   // a particle of infinite mass
     const uint32_t cell = grid_cell_of(sc, p.x, p.y, p.z);
     keys[i] = cell;
     rank[i] = atomicAdd(cnt + cell, 1u);
@@ -480,16 +481,17 @@ cudaError_t gs_radix_sort(cudaStream_t s, uint32_t* keys[2], uint32_t* vals[2], 
 
 size_t gs_scan_aux_words(int64_t total) { return (size_t)std::max<int64_t>(1, (total + kScanTile - 1) / kScanTile); }
 
-cudaError_t gs_cs_clear(cudaStream_t s, uint32_t* cell_start, int64_t n_cell)
+cudaError_t gs_cs_clear(cudaStream_t s, uint32_t* cell_start, int64_t n_cell, int extra)
 {
-    return cudaMemsetAsync(cell_start, 0, (size_t)(n_cell + 1) * sizeof(uint32_t), s);
+    return cudaMemsetAsync(cell_start, 0, (size_t)(n_cell + 1 + extra) * sizeof(uint32_t), s);
 }
 
 cudaError_t gs_cs_keys(cudaStream_t s, const float4* pos, int64_t n, const SceneDev* scenes, const uint32_t* tag,
-                       uint32_t* keys, uint32_t* rank, uint32_t* cell_start, int64_t* launches)
+                       uint32_t* keys, uint32_t* rank, uint32_t* cell_start, int64_t* launches,
+                       unsigned* solid_flag)
 {
     if (n <= 0) return cudaSuccess;
-    k_cs_keys<<<gs_blocks(n, 256), 256, 0, s>>>(pos, n, scenes, tag, keys, rank, cell_start);
+    k_cs_keys<<<gs_blocks(n, 256), 256, 0, s>>>(pos, n, scenes, tag, keys, rank, cell_start, solid_flag);
     *launches += 1;
     return cudaGetLastError();
 }

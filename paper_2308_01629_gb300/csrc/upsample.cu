@@ -16,10 +16,13 @@
 // and applies the SDF rule (project to phi = r_HR, drop the inward normal
 // velocity relative to the boundary), then writes the particle back.
 // LR particles of infinite mass (w of the position 0: sampled boundaries and
-// rigid bodies) are staged from the far end of the buffer and summed apart
-// (per lane, in shared memory); they join the sums only where some grain
-// has a positive weight, so an HR particle with no grain in reach moves
-// ballistically instead of sticking to them (Sec. 4).
+// rigid bodies) are summed apart (per lane, in shared memory) and join the
+// sums only where some grain has a positive weight, so an HR particle with
+// no grain in reach moves ballistically instead of sticking to them
+// (Sec. 4).  That handling lives in a second instantiation of the kernel;
+// the LR binning before the gather raises a device flag when any LR particle
+// has w = 0, and each instantiation returns at once unless the flag selects
+// it, so scenes without such particles run the plain gather.
 #include <cuda_runtime.h>
 
 #include "gs_internal.cuh"
@@ -27,7 +30,7 @@
 
 namespace {
 
-constexpr int kBuf = 64;   // staged LR per warp (grains from the front, solids from the back); flushed at >= 32
+constexpr int kBuf = 64;   // staged LR per warp; flushed at >= 32
 
 __device__ __forceinline__ int cell_coord(float x, float o, float inv_h, int dim)
 {
@@ -94,8 +97,9 @@ __device__ __forceinline__ int sub_floor(float x, float o, float inv_h)
 }
 
 // One warp item: the 32 HR slots [32 item, 32 item + 32) of one scene.
-// sol: this warp's 5 x 32 sums of solid particles (S, V, max w per lane),
-// zero on entry and on return.
+// sol (kSolid): this warp's 5 x 32 sums of solid particles (S, V, max w per
+// lane), zero on entry and on return.
+template <bool kSolid>
 __device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t item, float4* ba, float4* bb,
                                               float* sol, int lane)
 {
@@ -160,28 +164,38 @@ __device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t ite
             ci = 1.0f - (ux * ux + uy * uy + uz * uz);
         }
 
-        int cnt = 0, nsol = 0;
+        int cnt = 0;
+        bool batch_solid = false;
         auto stage = [&](int slot, float4 c, float4 cv) {
             const float wx = (c.x - c0x) * inv3r, wy = (c.y - c0y) * inv3r, wz = (c.z - c0z) * inv3r;
             ba[slot] = make_float4(2.0f * wx, 2.0f * wy, 2.0f * wz, -(wx * wx + wy * wy + wz * wz));
-            bb[slot] = make_float4(cv.x, cv.y, cv.z, 0.0f);
+            bb[slot] = make_float4(cv.x, cv.y, cv.z, kSolid && c.w == 0.0f ? 1.0f : 0.0f);
         };
-        auto flush = [&](int count, int count_sol) {
+        auto flush = [&](int count, bool with_solid) {
             __syncwarp();
-            if (count_sol > 0) {
+            if (kSolid && with_solid) {
+                // the batch holds solid particles (rb.w = 1): their sums apart
                 float s = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, sm = 0.f;
 #pragma unroll 1
-                for (int k = kBuf - count_sol; k < kBuf; ++k) {
+                for (int k = 0; k < count; ++k) {
                     const float4 ra = ba[k];
                     const float4 rb = bb[k];
                     float t = fmaf(ra.x, ux, fmaf(ra.y, uy, fmaf(ra.z, uz, ra.w + ci)));
                     t = fmaxf(t, 0.0f);
                     const float w = t * t * t;
-                    s += w;
-                    sx = fmaf(w, rb.x, sx);
-                    sy = fmaf(w, rb.y, sy);
-                    sz = fmaf(w, rb.z, sz);
-                    sm = fmaxf(sm, w);
+                    if (rb.w != 0.0f) {   // the same k on every lane: uniform
+                        s += w;
+                        sx = fmaf(w, rb.x, sx);
+                        sy = fmaf(w, rb.y, sy);
+                        sz = fmaf(w, rb.z, sz);
+                        sm = fmaxf(sm, w);
+                    } else {
+                        S += w;
+                        Vx = fmaf(w, rb.x, Vx);
+                        Vy = fmaf(w, rb.y, Vy);
+                        Vz = fmaf(w, rb.z, Vz);
+                        wmax = fmaxf(wmax, w);
+                    }
                 }
                 sol[lane] += s;
                 sol[32 + lane] += sx;
@@ -189,6 +203,8 @@ __device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t ite
                 sol[96 + lane] += sz;
                 sol[128 + lane] = fmaxf(sol[128 + lane], sm);
                 any_solid = true;
+                __syncwarp();
+                return;
             }
 #pragma unroll 4
             for (int k = 0; k < count; ++k) {
@@ -247,21 +263,20 @@ __device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t ite
                     const float ez = fmaxf(fmaxf(lz - c.z, c.z - hz), 0.0f);
                     take = ex * ex + ey * ey + ez * ez < R2;
                 }
-                const bool solid = take && c.w == 0.0f;
-                const unsigned bal = __ballot_sync(0xffffffffu, take && !solid);
-                const unsigned bsol = __ballot_sync(0xffffffffu, solid);
-                if (take) stage(solid ? kBuf - 1 - (nsol + __popc(bsol & lt)) : cnt + __popc(bal & lt), c, cv);
+                const unsigned bal = __ballot_sync(0xffffffffu, take);
+                if (take) stage(cnt + __popc(bal & lt), c, cv);
                 cnt += __popc(bal);
-                nsol += __popc(bsol);
-                if (cnt + nsol >= 32) {   // below 32 before a round of at most 32: the two ends never meet
-                    flush(cnt, nsol);
-                    cnt = nsol = 0;
+                if constexpr (kSolid) batch_solid |= __any_sync(0xffffffffu, take && c.w == 0.0f);
+                if (cnt >= 32) {
+                    flush(cnt, batch_solid);
+                    cnt = 0;
+                    batch_solid = false;
                 }
             }
         }
-        if (cnt + nsol > 0) flush(cnt, nsol);
+        if (cnt > 0) flush(cnt, batch_solid);
     }
-    if (any_solid) {
+    if (kSolid && any_solid) {
         // the solid particles count only where a grain has a positive weight
         if (S > 0.0f) {
             S += sol[lane];
@@ -294,15 +309,18 @@ __device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t ite
     __stcs(a.out_vel + i, make_float4(nvx, nvy, nvz, 0.0f));
 }
 
-template <int WARPS>
+template <int WARPS, bool kSolid>
 __global__ void __launch_bounds__(WARPS * 32, 24 / WARPS) k_upsample(const UpsampleArgs a, int persistent)
 {
+    if ((*a.solid_flag != 0u) != kSolid) return;   // the other instantiation does the frame
     __shared__ float4 s_a[WARPS][kBuf];
     __shared__ float4 s_b[WARPS][kBuf];
-    __shared__ float s_sol[WARPS][5 * 32];
+    __shared__ float s_sol[kSolid ? WARPS : 1][5 * 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int m = 0; m < 5; ++m) s_sol[warp][32 * m + lane] = 0.0f;
-    __syncwarp();
+    if constexpr (kSolid) {
+        for (int m = 0; m < 5; ++m) s_sol[warp][32 * m + lane] = 0.0f;
+        __syncwarp();
+    }
     // One call site for both launch modes, so both run the same code.  In
     // the persistent mode warps pull items until the counter passes
     // n_warps; every warp leaves after at most n_warps + 1 iterations.
@@ -327,7 +345,7 @@ __global__ void __launch_bounds__(WARPS * 32, 24 / WARPS) k_upsample(const Upsam
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(a.hr_vel + ahead * 32 + lane));
             }
         }
-        upsample_item(a, item, s_a[warp], s_b[warp], s_sol[warp], lane);
+        upsample_item<kSolid>(a, item, s_a[warp], s_b[warp], s_sol[kSolid ? warp : 0], lane);
     }
 }
 
@@ -336,13 +354,16 @@ __global__ void __launch_bounds__(WARPS * 32, 24 / WARPS) k_upsample(const Upsam
 template <int WARPS>
 static cudaError_t launch_w(cudaStream_t s, const UpsampleArgs& a, int blocks_per_sm, int sm_count)
 {
+    // both instantiations; the one the device flag does not select returns
     if (blocks_per_sm <= 0) {
-        k_upsample<WARPS><<<gs_blocks(a.n_warps, WARPS), WARPS * 32, 0, s>>>(a, 0);
+        k_upsample<WARPS, false><<<gs_blocks(a.n_warps, WARPS), WARPS * 32, 0, s>>>(a, 0);
+        k_upsample<WARPS, true><<<gs_blocks(a.n_warps, WARPS), WARPS * 32, 0, s>>>(a, 0);
     } else {
         int64_t nb = (int64_t)blocks_per_sm * sm_count;
         const int64_t need = (a.n_warps + WARPS - 1) / WARPS;
         if (nb > need) nb = need;
-        k_upsample<WARPS><<<(unsigned)nb, WARPS * 32, 0, s>>>(a, 1);
+        k_upsample<WARPS, false><<<(unsigned)nb, WARPS * 32, 0, s>>>(a, 1);
+        k_upsample<WARPS, true><<<(unsigned)nb, WARPS * 32, 0, s>>>(a, 1);
     }
     return cudaGetLastError();
 }
@@ -361,6 +382,6 @@ cudaError_t gs_launch_upsample(cudaStream_t s, const UpsampleArgs& a, int warps_
     case 16: e = launch_w<16>(s, a, blocks_per_sm, sm_count); break;
     default: e = launch_w<8>(s, a, blocks_per_sm, sm_count); break;
     }
-    *launches += 1;
+    *launches += 2;   // the two instantiations
     return e;
 }

@@ -75,6 +75,11 @@ def _L():
         L.or_pbd_step.restype = ctypes.c_int
         L.or_pbd_step_mu.argtypes = [P, P, P, ctypes.c_long, P, ctypes.c_int, P, ctypes.c_int, P, P, P]
         L.or_pbd_step_mu.restype = ctypes.c_int
+        L.or_pbd_step_bodies.argtypes = [P, P, P, ctypes.c_long, P, ctypes.c_int, P, ctypes.c_int, P, P, P,
+                                         ctypes.c_int, P, P]
+        L.or_pbd_step_bodies.restype = ctypes.c_int
+        L.or_polar_rotation.argtypes = [P, P]
+        L.or_polar_rotation.restype = ctypes.c_int
         L.or_pairs_within.argtypes = [P, ctypes.c_long, P, ctypes.c_long, ctypes.c_double, P, P, ctypes.c_long]
         L.or_pairs_within.restype = ctypes.c_long
         L.or_upsample_vjp.argtypes = [P, P, ctypes.c_long, P, P, ctypes.c_long, P, ctypes.c_int, P, P, P,
@@ -216,17 +221,48 @@ def upsample_vjp(lr_x, lr_v, hr_x, hr_v, sdf, prm, gx, gv):
 
 
 # ------------------------------------------------------------- LR step ---
-def pbd_step(x, v, inv_m, sdf, prm, mode=0, mu=None):
+def polar_rotation(C):
+    """Rotation of the polar decomposition of the 3 x 3 matrix C."""
+    C = _f64(C).reshape(3, 3).copy()
+    R = np.zeros((3, 3))
+    if _L().or_polar_rotation(_ptr(C), _ptr(R)) != 0:
+        raise ValueError("degenerate matrix")
+    return R
+
+
+def body_rest_offsets(x, inv_m, body):
+    """Offsets of every body particle from its body's centre of mass (masses
+    1 / inv_m) in the configuration x; 0 for grains (body 0)."""
+    x, inv_m, body = _f64(x, 3), _f64(inv_m), np.asarray(body, np.int64)
+    xo = np.zeros_like(x)
+    for b in np.unique(body[body > 0]):
+        sel = body == b
+        m = 1.0 / inv_m[sel]
+        xo[sel] = x[sel] - (m[:, None] * x[sel]).sum(0) / m.sum()
+    return xo
+
+
+def pbd_step(x, v, inv_m, sdf, prm, mode=0, mu=None, bodies=None):
     """One LR time step of Algorithm 1.  Returns (x, v, suspect, stats).
     mu (N x 2: mu_s, mu_k per particle), when given, replaces the step's
-    friction coefficients; pairs use the cross coefficients of Sec. 3."""
+    friction coefficients; pairs use the cross coefficients of Sec. 3.
+    bodies = (body, xo): body id per particle (0: grain, 1..B: rigid body)
+    and rest offsets (body_rest_offsets); each body is shape-matched in the
+    solver passes (Sec. 3)."""
     x, v = _f64(x, 3).copy(), _f64(v, 3).copy()
     inv_m = _f64(inv_m)
     sdf = _f64(sdf, SDF_STRIDE) if sdf is not None and len(sdf) else np.zeros((0, SDF_STRIDE))
     p = _prm(prm, PB_KEYS)
     sus = np.zeros(len(x), np.int32)
     stats = np.zeros(5, np.int64)
-    if mu is None:
+    if bodies is not None:
+        body = np.ascontiguousarray(np.asarray(bodies[0], np.int32))
+        xo = _f64(bodies[1], 3)
+        muv = None if mu is None else _f64(mu, 2)
+        rc = _L().or_pbd_step_bodies(_ptr(x), _ptr(v), _ptr(inv_m), len(x), _ptr(sdf), len(sdf), _ptr(p),
+                                     int(mode), _ptr(muv), _ptr(body), _ptr(xo), int(body.max(initial=0)),
+                                     _ptr(sus), _ptr(stats))
+    elif mu is None:
         rc = _L().or_pbd_step(_ptr(x), _ptr(v), _ptr(inv_m), len(x), _ptr(sdf), len(sdf), _ptr(p),
                               int(mode), _ptr(sus), _ptr(stats))
     else:

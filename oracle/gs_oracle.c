@@ -780,9 +780,100 @@ static long pbd_tape_bytes(long np, long N, int nct, int passes)
     return 32 + 16 * np + (long)passes * (np + N * (long)nct);
 }
 
+/* Rotation of the polar decomposition C = R S (S symmetric positive
+ * definite): R = C (C^T C)^(-1/2), with (C^T C)^(-1/2) from the eigen-
+ * decomposition of C^T C by cyclic Jacobi rotations (the textbook method).
+ * When det C < 0 the closest rotation flips the direction of the smallest
+ * singular value: R = C S^-1 - 2 u3 v3^T with v3 its eigenvector and u3 =
+ * C v3 / sigma3.  Returns -1 for a degenerate C (smallest eigenvalue below
+ * 1e-24 of the largest: a body whose rest shape is flat or a line). */
+static int polar_rotation(const double C[9], double R[9])
+{
+    double S[9], V[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k) s += C[3 * k + a] * C[3 * k + b];
+            S[3 * a + b] = s;
+        }
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = fabs(S[1]) + fabs(S[2]) + fabs(S[5]);
+        double norm = fabs(S[0]) + fabs(S[4]) + fabs(S[8]);
+        if (off <= 1e-18 * norm) break;
+        for (int pp = 0; pp < 2; ++pp)
+            for (int q = pp + 1; q < 3; ++q) {
+                double apq = S[3 * pp + q];
+                if (apq == 0.0) continue;
+                double theta = (S[3 * q + q] - S[3 * pp + pp]) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < 3; ++k) {   /* S <- J^T S J, columns then rows */
+                    double skp = S[3 * k + pp], skq = S[3 * k + q];
+                    S[3 * k + pp] = c * skp - s * skq;
+                    S[3 * k + q] = s * skp + c * skq;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    double spk = S[3 * pp + k], sqk = S[3 * q + k];
+                    S[3 * pp + k] = c * spk - s * sqk;
+                    S[3 * q + k] = s * spk + c * sqk;
+                }
+                for (int k = 0; k < 3; ++k) {   /* V <- V J */
+                    double vkp = V[3 * k + pp], vkq = V[3 * k + q];
+                    V[3 * k + pp] = c * vkp - s * vkq;
+                    V[3 * k + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    double lam[3] = {S[0], S[4], S[8]};
+    double lmax = fmax(lam[0], fmax(lam[1], lam[2]));
+    int kmin = 0;
+    for (int k = 1; k < 3; ++k)
+        if (lam[k] < lam[kmin]) kmin = k;
+    if (!(lmax > 0) || !(lam[kmin] > 1e-24 * lmax)) return -1;
+    double Sinv[9];   /* V diag(lam^-1/2) V^T */
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k) s += V[3 * a + k] * V[3 * b + k] / sqrt(lam[k]);
+            Sinv[3 * a + b] = s;
+        }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double s = 0;
+            for (int k = 0; k < 3; ++k) s += C[3 * a + k] * Sinv[3 * k + b];
+            R[3 * a + b] = s;
+        }
+    double det = R[0] * (R[4] * R[8] - R[5] * R[7]) - R[1] * (R[3] * R[8] - R[5] * R[6]) +
+                 R[2] * (R[3] * R[7] - R[4] * R[6]);
+    if (det < 0) {
+        double v3[3] = {V[kmin], V[3 + kmin], V[6 + kmin]}, u3[3];
+        double sig = sqrt(lam[kmin]);
+        for (int a = 0; a < 3; ++a) u3[a] = (C[3 * a] * v3[0] + C[3 * a + 1] * v3[1] + C[3 * a + 2] * v3[2]) / sig;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) R[3 * a + b] -= 2.0 * u3[a] * v3[b];
+    }
+    return 0;
+}
+
+int or_polar_rotation(const double* C, double* R) { return polar_rotation(C, R); }
+
+/* Shape matching of rigid bodies (Sec. 3): body[i] = b >= 1 puts particle i
+ * in body b (0: a grain); xo[i] is its offset from the body's centre of mass
+ * at rest.  In every solver pass each body, from the pass's positions xt:
+ *   c = sum m xt / sum m (m = 1 / inv_m, the unscaled masses),
+ *   C = sum m (xt - c) xo^T,  R = rotation of the polar decomposition of C,
+ * and each of its particles receives the constraint delta (R xo + c) - xt,
+ * counted once in n_i. */
+typedef struct {
+    const int* body;
+    const double* xo;
+    int n_bodies;
+} or_bodies;
+
 static int pbd_impl(double* x, double* v, const double* inv_m, long N,
                     const double* sdf, int n_sdf, const double* prm, const double* mu, int mode,
-                    int* suspect, long* stats, int tmode, unsigned char* tape, long tape_cap, long* tape_len)
+                    int* suspect, long* stats, int tmode, unsigned char* tape, long tape_cap, long* tape_len,
+                    const or_bodies* bodies)
 {
     double r = prm[PB_R], dt = prm[PB_DT];
     const double g[3] = {prm[PB_GX], prm[PB_GY], prm[PB_GZ]};
@@ -1008,6 +1099,40 @@ static int pbd_impl(double* x, double* v, const double* inv_m, long N,
                 }
             }
         }
+        /* shape matching of the rigid bodies (solver passes) */
+        if (!stab && bodies && bodies->n_bodies > 0) {
+            int nb = bodies->n_bodies;
+            double* acc = (double*)calloc((size_t)nb * 13, sizeof(double));   /* M, sum m xt, sum m xt xo^T */
+            double* tf = (double*)malloc((size_t)nb * 12 * sizeof(double));   /* R, c */
+            if (!acc || !tf) return -1;
+            for (long i = 0; i < N; ++i) {
+                int b = bodies->body[i];
+                if (b < 1 || b > nb) continue;
+                double m = 1.0 / inv_m[i], *a = acc + 13 * (b - 1);
+                a[0] += m;
+                for (int k = 0; k < 3; ++k) a[1 + k] += m * xt[3 * i + k];
+                for (int r = 0; r < 3; ++r)
+                    for (int s = 0; s < 3; ++s) a[4 + 3 * r + s] += m * xt[3 * i + r] * bodies->xo[3 * i + s];
+            }
+            for (int b = 0; b < nb; ++b) {
+                double *a = acc + 13 * b, *t = tf + 12 * b, C[9];
+                if (!(a[0] > 0)) continue;
+                for (int k = 0; k < 3; ++k) t[9 + k] = a[1 + k] / a[0];
+                /* C = sum m xt xo^T - c sum m xo^T, and sum m xo = 0 at rest */
+                for (int k = 0; k < 9; ++k) C[k] = a[4 + k];
+                if (polar_rotation(C, t) != 0) { free(acc); free(tf); return -4; }
+            }
+            for (long i = 0; i < N; ++i) {
+                int b = bodies->body[i];
+                if (b < 1 || b > nb) continue;
+                const double *t = tf + 12 * (b - 1), *o = bodies->xo + 3 * i;
+                for (int r = 0; r < 3; ++r)
+                    D[3 * i + r] += t[3 * r] * o[0] + t[3 * r + 1] * o[1] + t[3 * r + 2] * o[2] + t[9 + r] - xt[3 * i + r];
+                cnt[i]++;
+            }
+            free(acc);
+            free(tf);
+        }
         /* would the other branch of an ambiguous decision move the particle
          * by more than eps_impact? */
         for (long q = 0; q < alts.n; ++q) {
@@ -1066,7 +1191,7 @@ int or_pbd_step(double* x, double* v, const double* inv_m, long N,
                 const double* sdf, int n_sdf, const double* prm, int mode,
                 int* suspect, long* stats)
 {
-    return pbd_impl(x, v, inv_m, N, sdf, n_sdf, prm, NULL, mode, suspect, stats, TAPE_OFF, NULL, 0, NULL);
+    return pbd_impl(x, v, inv_m, N, sdf, n_sdf, prm, NULL, mode, suspect, stats, TAPE_OFF, NULL, 0, NULL, NULL);
 }
 
 /* or_pbd_step with per-particle friction coefficients mu (N x 2: mu_s,
@@ -1076,7 +1201,22 @@ int or_pbd_step_mu(double* x, double* v, const double* inv_m, long N,
                    int* suspect, long* stats)
 {
     if (!mu && N > 0) return -1;
-    return pbd_impl(x, v, inv_m, N, sdf, n_sdf, prm, mu, mode, suspect, stats, TAPE_OFF, NULL, 0, NULL);
+    return pbd_impl(x, v, inv_m, N, sdf, n_sdf, prm, mu, mode, suspect, stats, TAPE_OFF, NULL, 0, NULL, NULL);
+}
+
+/* or_pbd_step with optional per-particle friction coefficients (mu, may be
+ * NULL) and rigid bodies matched to their rest shapes (body, xo; n_bodies
+ * bodies numbered from 1; see pbd_impl).  -4 for a body whose shape is
+ * degenerate. */
+int or_pbd_step_bodies(double* x, double* v, const double* inv_m, long N,
+                       const double* sdf, int n_sdf, const double* prm, int mode, const double* mu,
+                       const int* body, const double* xo, int n_bodies, int* suspect, long* stats)
+{
+    if (n_bodies > 0 && (!body || !xo)) return -1;
+    for (long i = 0; i < N && n_bodies > 0; ++i)
+        if (body[i] > 0 && !(inv_m[i] > 0)) return -1;   /* body particles have finite mass */
+    or_bodies bd = {body, xo, n_bodies};
+    return pbd_impl(x, v, inv_m, N, sdf, n_sdf, prm, mu, mode, suspect, stats, TAPE_OFF, NULL, 0, NULL, &bd);
 }
 
 /* One LR step (grid neighbour search) that records its decisions into, or
@@ -1088,7 +1228,7 @@ int or_pbd_step_tape(double* x, double* v, const double* inv_m, long N, const do
                      const double* prm, int tmode, unsigned char* tape, long tape_cap, long* tape_len)
 {
     if ((tmode != TAPE_RECORD && tmode != TAPE_REPLAY) || !tape) return -1;
-    return pbd_impl(x, v, inv_m, N, sdf, n_sdf, prm, NULL, 1, NULL, NULL, tmode, tape, tape_cap, tape_len);
+    return pbd_impl(x, v, inv_m, N, sdf, n_sdf, prm, NULL, 1, NULL, NULL, tmode, tape, tape_cap, tape_len, NULL);
 }
 
 /* Brute-force pair listing for tests of the neighbour search: every (i, j)

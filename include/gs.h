@@ -118,9 +118,28 @@ enum {
     GS_FIELD_LR_SORTED_INDEX = 7,/* uint32[n_low], read: particle index of each sorted slot */
     GS_FIELD_HR_SORTED_KEY = 8,  /* uint32[HR slots], read: fine cell key of each internal slot
                                     after the latest reorder */
-    GS_FIELD_LR_MATERIAL = 9     /* uint32[n_low], read / write: material of each LR particle
+    GS_FIELD_LR_MATERIAL = 9,    /* uint32[n_low], read / write: material of each LR particle
                                     (gs_set_materials); all 0 at gs_create */
+    GS_FIELD_LR_BODY = 10        /* uint32[n_low], read / write: rigid body of each LR particle
+                                    (0: a grain; 1 .. GS_MAX_BODIES); writing it takes every body's
+                                    rest shape from the current LR positions (see below) */
 };
+
+/* Rigid bodies (Sec. 3, shape matching): the particles of a movable rigid
+ * body are LR particles of finite mass that collide like grains; in every
+ * solver pass each body b is matched to its rest shape:
+ *   c = sum m x~ / sum m over the body (m = 1 / w, unscaled masses),
+ *   C = sum m (x~ - c) xo^T,  R = the rotation of the polar decomposition
+ *   of C,  and each body particle receives the constraint
+ *   delta = (R xo + c) - x~, counted once in the Jacobi average;
+ * xo are the particles' offsets from the body's centre of mass when
+ * GS_FIELD_LR_BODY was written.  The paper's rule against HR particles
+ * sticking to rigid bodies covers body particles too (see gs_upsample).
+ * Writing the field synchronizes; GS_ERR_ARG for an id above
+ * GS_MAX_BODIES or a body particle with w = 0.  With bodies the LR step
+ * runs one launch per pass (not the persistent solver), and the reverse
+ * modes refuse to run (GS_ERR_STATE). */
+#define GS_MAX_BODIES 256
 
 /* Neighbour-grid contract (Sec. 5.1 uses a compact-hashing grid; this
  * library fixes a dense uniform grid so cell ids are reproducible):

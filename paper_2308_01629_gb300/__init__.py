@@ -29,6 +29,8 @@ GS_MAX_SDF = 16
  GS_FIELD_HR_VEL_INTERNAL, GS_FIELD_LR_CELL_START, GS_FIELD_LR_SORTED_INDEX, GS_FIELD_HR_SORTED_KEY,
  GS_FIELD_LR_MATERIAL) = range(10)
 GS_MAX_MATERIALS = 16
+GS_FIELD_LR_BODY = 10
+GS_MAX_BODIES = 256
 GS_MAX_SUBSTEPS = 256
 GS_TIMER_BIN_LOW, GS_TIMER_RESORT, GS_TIMER_GATHER, GS_TIMER_STEP_LOW, GS_TIMER_COUNT = range(5)
 
@@ -405,6 +407,15 @@ class Context:
             for f, k in ((GS_FIELD_LR_POS, "lr_pos"), (GS_FIELD_LR_VEL, "lr_vel"), (GS_FIELD_HR_POS, "hr_pos"),
                          (GS_FIELD_HR_VEL, "hr_vel")):
                 self.write(f, np.ascontiguousarray(np.concatenate([s[k] for s in self.scene_list])))
+            if any("lr_body" in s for s in self.scene_list):
+                # rigid bodies (after the positions: the rest shapes come from
+                # them); every scene's ids follow the previous scenes'
+                ids, base = [], 0
+                for s in self.scene_list:
+                    b = np.asarray(s.get("lr_body", np.zeros(len(s["lr_pos"]))), np.uint32)
+                    ids.append(np.where(b > 0, b + base, 0).astype(np.uint32))
+                    base += int(b.max(initial=0))
+                self.write(GS_FIELD_LR_BODY, np.ascontiguousarray(np.concatenate(ids)))
 
     def close(self):
         if self.ctx:
@@ -428,7 +439,7 @@ class Context:
                       GS_FIELD_HR_POS_INTERNAL: (self.hr_slots, 4), GS_FIELD_HR_VEL_INTERNAL: (self.hr_slots, 4),
                       GS_FIELD_LR_CELL_START: (self.n_cell_total + 1,),
                       GS_FIELD_LR_SORTED_INDEX: (self.n_low,), GS_FIELD_HR_SORTED_KEY: (self.hr_slots,),
-                      GS_FIELD_LR_MATERIAL: (self.n_low,)}
+                      GS_FIELD_LR_MATERIAL: (self.n_low,), GS_FIELD_LR_BODY: (self.n_low,)}
             shape = counts[field]
             out = np.zeros(shape, np.float32 if len(shape) == 2 else np.uint32)
         p, n, dev = _ptr_of(out)

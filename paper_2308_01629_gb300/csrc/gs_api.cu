@@ -109,7 +109,8 @@ size_t field_bytes(const gs_ctx* c, int field)
     case GS_FIELD_LR_CELL_START: return (size_t)(c->n_cell_total + 1) * sizeof(uint32_t);
     case GS_FIELD_LR_SORTED_INDEX: return (size_t)c->n_low * sizeof(uint32_t);
     case GS_FIELD_HR_SORTED_KEY: return (size_t)c->hr_slots * sizeof(uint32_t);
-    case GS_FIELD_LR_MATERIAL: return (size_t)c->n_low * sizeof(uint32_t);
+    case GS_FIELD_LR_MATERIAL:
+    case GS_FIELD_LR_BODY: return (size_t)c->n_low * sizeof(uint32_t);
     default: return (size_t)-1;
     }
 }
@@ -184,7 +185,22 @@ PbdArgs pbd_args(const gs_ctx* c, float dt)
     const bool mat = c->n_materials > 0;
     a.mu_mat = mat ? c->d_mu : nullptr;
     a.mu_cross = mat ? c->d_mu + GS_MAX_MATERIALS : nullptr;
+    const bool bodies = c->n_bodies > 0;
+    a.body = bodies ? c->lr_body : nullptr;
+    a.xo = bodies ? c->lr_xo : nullptr;
+    a.body_xf = bodies ? c->body_xf : nullptr;
+    a.sorted_idx = c->lr_vals[1];   // the step's binning leaves the particle of each slot here
     return a;
+}
+
+// The LR step's cell-order copy: material ids ride in the w of x; with rigid
+// bodies the slot of every particle is recorded for the body reductions.
+CsExtras step_extras(const gs_ctx* c, const PbdArgs& a)
+{
+    CsExtras ex;
+    ex.gb_w = a.mu_cross ? c->lr_mat : nullptr;
+    ex.slot_of = c->n_bodies > 0 ? c->lr_slot : nullptr;
+    return ex;
 }
 
 int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* r_high, const int* ratio,
@@ -351,6 +367,12 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
     A(dalloc(&c->lr_svel, N));
     A(dalloc(&c->lr_xt, N));
     A(dalloc(&c->lr_mat, N));
+    A(dalloc(&c->lr_body, N));
+    A(dalloc(&c->lr_xo, N));
+    A(dalloc(&c->body_members, N));
+    A(dalloc(&c->body_start, GS_MAX_BODIES + 1));
+    A(dalloc(&c->body_xf, 4 * GS_MAX_BODIES));
+    A(dalloc(&c->lr_slot, N));
     A(dalloc(&c->d_mu, (size_t)GS_MAX_MATERIALS * (GS_MAX_MATERIALS + 1)));
     for (int k = 0; k < 2; ++k) {
         A(dalloc(&c->s_xt[k], N));
@@ -398,6 +420,7 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
     Z(cudaMemsetAsync(c->lr_pos, 0, std::max<int64_t>(N, 1) * sizeof(float4), c->stream));
     Z(cudaMemsetAsync(c->lr_vel, 0, std::max<int64_t>(N, 1) * sizeof(float4), c->stream));
     Z(cudaMemsetAsync(c->lr_mat, 0, std::max<int64_t>(N, 1) * sizeof(uint32_t), c->stream));
+    Z(cudaMemsetAsync(c->lr_body, 0, std::max<int64_t>(N, 1) * sizeof(uint32_t), c->stream));
     Z(cudaMemsetAsync(c->d_cfl, 0, sizeof(CflState), c->stream));
     Z(cudaMemsetAsync(c->tmp4, 0, std::max<int64_t>(std::max(NM, MR), 1) * sizeof(float4), c->stream));
     Z(cudaMemsetAsync(c->lr_cell_start, 0, (cells + 2) * sizeof(uint32_t), c->stream));
@@ -438,14 +461,18 @@ int bin_low_impl(gs_ctx* c)
 {
     Timed t(c, GS_TIMER_BIN_LOW);
     // counting sort by cell; its last stage copies pos and vel into cell order
-    // the word after the cell starts flags LR particles of infinite mass
-    // for the gather (the binning reads every position anyway)
+    // the word after the cell starts flags LR particles of infinite mass or
+    // of rigid bodies for the gather (the binning reads every position
+    // anyway); body particles enter the gather's view with w = 0
+    const uint32_t* body = c->n_bodies > 0 ? c->lr_body : nullptr;
     CK(gs_cs_clear(c->stream, c->lr_cell_start, c->n_cell_total, 1), "clear counts");
     CK(gs_cs_keys(c->stream, c->lr_pos, c->n_low, c->d_scenes, c->lr_scene, c->lr_keys[0], c->lr_vals[0],
-                  c->lr_cell_start, &c->launches, c->lr_cell_start + c->n_cell_total + 1),
+                  c->lr_cell_start, &c->launches, c->lr_cell_start + c->n_cell_total + 1, body),
        "cell keys");
+    CsExtras ex;
+    ex.ga_solid = body;
     CK(gs_cs_finish(c->stream, c->n_low, c->n_cell_total, c->lr_keys[0], c->lr_vals[0], c->lr_keys[1], c->lr_vals[1],
-                    c->lr_cell_start, c->scan_aux, c->lr_pos, c->lr_vel, c->lr_spos, c->lr_svel, &c->launches),
+                    c->lr_cell_start, c->scan_aux, c->lr_pos, c->lr_vel, c->lr_spos, c->lr_svel, &c->launches, ex),
        "bin by cell");
     c->lr_sorted_keys = c->lr_keys[1];
     c->lr_sorted_idx = c->lr_vals[1];
@@ -517,7 +544,7 @@ int step_low_impl(gs_ctx* c, float dt, int iters, const float* dt_dev = nullptr,
        "predict");
     CK(gs_cs_finish(c->stream, N, c->n_cell_total, c->lr_keys[0], c->lr_vals[0], c->lr_keys[1], c->lr_vals[1],
                     c->step_cell_start, c->scan_aux, c->lr_xt, c->lr_pos, c->s_xt[0], c->s_x[0], &c->launches,
-                    a.mu_cross ? c->lr_mat : nullptr),
+                    step_extras(c, a)),
        "bin by cell");
     c->lr_sorted_keys = c->lr_keys[1];
     c->lr_sorted_idx = c->lr_vals[1];
@@ -525,7 +552,7 @@ int step_low_impl(gs_ctx* c, float dt, int iters, const float* dt_dev = nullptr,
                            c->nbr_cap, c->d_err, &c->launches),
        "neighbours");
     int bx = 0, bt = 0;   // buffers holding the current x and xt
-    if (c->use_solver && c->solve_blocks > 0) {
+    if (c->use_solver && c->solve_blocks > 0 && c->n_bodies == 0) {
         // all passes in one cooperative launch; the buffers alternate as in
         // the loop below
         CK(gs_launch_solve(c->stream, a, c->n_stab, iters, c->s_x, c->s_xt, c->nbr, c->nbr_cnt, c->d_bar, c->d_err,
@@ -539,6 +566,10 @@ int step_low_impl(gs_ctx* c, float dt, int iters, const float* dt_dev = nullptr,
         for (int it = 0; it < total; ++it) {
             const int stab = it < c->n_stab;
             const bool last = it + 1 == total;
+            if (c->n_bodies > 0 && !stab)   // the bodies' transforms from this pass's x~
+                CK(gs_launch_body_xform(c->stream, c->n_bodies, c->body_start, c->body_members, c->lr_slot,
+                                        c->s_xt[bt], c->lr_xo, c->body_xf, &c->launches),
+                   "body transforms");
             CK(gs_launch_pass(c->stream, a, stab, c->s_x[bx], c->s_xt[bt], c->s_x[bx ^ 1], c->s_xt[bt ^ 1], c->nbr,
                               c->nbr_cnt, &c->launches, last ? c->lr_sorted_idx : nullptr,
                               last ? c->lr_pos : nullptr, last ? c->lr_vel : nullptr, last ? rate : nullptr),
@@ -848,7 +879,8 @@ void gs_destroy(gs_ctx* c)
                     c->hr_vals[0], c->hr_vals[1], c->nbr,        c->nbr_cnt,    c->tmp4,      c->sort_hist,
                     c->d_work,     c->d_err,      c->gXs,        c->gVs,       c->snap,      c->snap_xt,
                     c->adj_gx,     c->adj_gxt,    c->adj_h,      c->adj_gws,   c->scan_aux,   c->d_bar,
-                    c->step_cell_start, c->d_sdf_pend, c->stage_in, c->lr_mat, c->d_mu, c->d_cfl,
+                    c->step_cell_start, c->d_sdf_pend, c->stage_in, c->lr_mat, c->d_mu, c->d_cfl, c->lr_body, c->lr_xo, c->body_members,
+                    c->body_start, c->body_xf, c->lr_slot,
                     c->async_in[0], c->async_in[1], c->async_in[2], c->async_in[3],
                     c->async_out[0], c->async_out[1], c->async_out[2], c->async_out[3]};
     for (void* b : bufs)
@@ -943,6 +975,81 @@ static int write_materials(gs_ctx* c, const void* src, size_t bytes, int src_is_
     return GS_OK;
 }
 
+// The body field: ids, then every body's rest shape from the current LR
+// positions (offsets from its centre of mass, masses 1 / w), in double on
+// the host; the transforms start at R = I, c = the centre of mass.
+static int write_bodies(gs_ctx* c, const void* src, size_t bytes, int src_is_device)
+{
+    if (bytes != field_bytes(c, GS_FIELD_LR_BODY))
+        return fail(c, GS_ERR_ARG, "size %zu does not match the body field", bytes);
+    const int64_t n = c->n_low;
+    if (n == 0) return GS_OK;
+    if (!src) return fail(c, GS_ERR_ARG, "null source");
+    std::vector<uint32_t> ids((size_t)n);
+    std::vector<float4> pos((size_t)n);
+    CK(cudaMemcpyAsync(ids.data(), src, bytes, src_is_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost,
+                       c->stream),
+       "copy ids");
+    CK(cudaMemcpyAsync(pos.data(), c->lr_pos, n * sizeof(float4), cudaMemcpyDeviceToHost, c->stream), "copy pos");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    int nb = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (ids[(size_t)i] > (uint32_t)GS_MAX_BODIES)
+            return fail(c, GS_ERR_ARG, "body id %u above %d", ids[(size_t)i], GS_MAX_BODIES);
+        if (ids[(size_t)i] != 0u && !(pos[(size_t)i].w > 0.0f))
+            return fail(c, GS_ERR_ARG, "particle %lld of body %u has no finite mass", (long long)i, ids[(size_t)i]);
+        nb = std::max(nb, (int)ids[(size_t)i]);
+    }
+    std::vector<double> M((size_t)nb + 1, 0.0), cx((size_t)nb + 1, 0.0), cy(cx), cz(cx);
+    std::vector<uint32_t> count((size_t)nb + 1, 0u);
+    for (int64_t i = 0; i < n; ++i) {
+        const uint32_t b = ids[(size_t)i];
+        if (!b) continue;
+        const double m = 1.0 / (double)pos[(size_t)i].w;
+        M[b] += m;
+        cx[b] += m * pos[(size_t)i].x;
+        cy[b] += m * pos[(size_t)i].y;
+        cz[b] += m * pos[(size_t)i].z;
+        count[b] += 1u;
+    }
+    // start[b - 1] = first member of body b, start[b] one past its last
+    std::vector<uint32_t> start((size_t)GS_MAX_BODIES + 1, 0u);
+    for (int b = 1; b <= GS_MAX_BODIES; ++b) start[(size_t)b] = start[(size_t)b - 1] + (b <= nb ? count[(size_t)b] : 0u);
+    const uint32_t run = start[(size_t)nb];
+    std::vector<uint32_t> members(std::max<size_t>(run, 1)), fill(start.begin(), start.end());
+    std::vector<float4> xo((size_t)n, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int64_t i = 0; i < n; ++i) {
+        const uint32_t b = ids[(size_t)i];
+        if (!b) continue;
+        members[fill[b - 1]++] = (uint32_t)i;
+        const double m = 1.0 / (double)pos[(size_t)i].w;
+        xo[(size_t)i] = make_float4((float)(pos[(size_t)i].x - cx[b] / M[b]), (float)(pos[(size_t)i].y - cy[b] / M[b]),
+                                    (float)(pos[(size_t)i].z - cz[b] / M[b]), (float)m);
+    }
+    std::vector<float4> xf((size_t)4 * GS_MAX_BODIES, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int b = 1; b <= nb; ++b) {
+        const double cc[3] = {M[b] > 0 ? cx[b] / M[b] : 0.0, M[b] > 0 ? cy[b] / M[b] : 0.0, M[b] > 0 ? cz[b] / M[b] : 0.0};
+        for (int r = 0; r < 3; ++r)
+            xf[(size_t)4 * (b - 1) + r] = make_float4(r == 0 ? 1.f : 0.f, r == 1 ? 1.f : 0.f, r == 2 ? 1.f : 0.f,
+                                                      (float)cc[r]);
+        xf[(size_t)4 * (b - 1) + 3] = make_float4(0.f, 0.f, 0.f, 1.f);
+    }
+    CK(cudaMemcpyAsync(c->lr_body, ids.data(), bytes, cudaMemcpyHostToDevice, c->stream), "copy");
+    CK(cudaMemcpyAsync(c->lr_xo, xo.data(), n * sizeof(float4), cudaMemcpyHostToDevice, c->stream), "copy");
+    if (run) CK(cudaMemcpyAsync(c->body_members, members.data(), run * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                c->stream),
+                "copy");
+    CK(cudaMemcpyAsync(c->body_start, start.data(), start.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                       c->stream),
+       "copy");
+    CK(cudaMemcpyAsync(c->body_xf, xf.data(), xf.size() * sizeof(float4), cudaMemcpyHostToDevice, c->stream),
+       "copy");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");   // the host vectors go out of scope
+    if ((nb > 0) != (c->n_bodies > 0)) drop_graphs(c);
+    c->n_bodies = nb;
+    return GS_OK;
+}
+
 int gs_set_materials(gs_ctx* c, int n_materials, const float* mu)
 {
     int st = check_state(c);
@@ -988,6 +1095,7 @@ int gs_write(gs_ctx* c, int field, const void* src, size_t bytes, int src_is_dev
     st = settle(c);
     if (st) return st;
     if (field == GS_FIELD_LR_MATERIAL) return write_materials(c, src, bytes, src_is_device);
+    if (field == GS_FIELD_LR_BODY) return write_bodies(c, src, bytes, src_is_device);
     if (field != GS_FIELD_LR_POS && field != GS_FIELD_LR_VEL && field != GS_FIELD_HR_POS && field != GS_FIELD_HR_VEL)
         return fail(c, GS_ERR_ARG, "field %d is not writable", field);
     if (bytes != field_bytes(c, field)) return fail(c, GS_ERR_ARG, "size %zu does not match field %d", bytes, field);
@@ -1030,6 +1138,7 @@ int gs_read(gs_ctx* c, int field, void* dst, size_t bytes, int dst_is_device)
     case GS_FIELD_LR_POS: srcp = c->lr_pos; break;
     case GS_FIELD_LR_VEL: srcp = c->lr_vel; break;
     case GS_FIELD_LR_MATERIAL: srcp = c->lr_mat; break;
+    case GS_FIELD_LR_BODY: srcp = c->lr_body; break;
     case GS_FIELD_HR_POS_INTERNAL: srcp = c->hr_pos[cur]; break;
     case GS_FIELD_HR_VEL_INTERNAL: srcp = c->hr_vel[cur]; break;
     case GS_FIELD_LR_CELL_START:
@@ -1555,6 +1664,7 @@ int gs_upsample_backward(gs_ctx* c, const float* lr_pos, const float* lr_vel, co
     if ((N > 0 && (!lr_pos || !lr_vel || !g_lr_pos || !g_lr_vel)) ||
         (M > 0 && (!hr_pos_in || !hr_vel_in || !g_hr_pos_out || !g_hr_vel_out || !g_hr_pos_in || !g_hr_vel_in)))
         return fail(c, GS_ERR_ARG, "null buffer");
+    if (c->n_bodies > 0) return fail(c, GS_ERR_STATE, "the reverse modes do not support rigid bodies");
     st = refuse_solid(c, lr_pos, N);
     if (st) return st;
     if (N) {
@@ -1608,6 +1718,7 @@ int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const 
         return fail(c, GS_ERR_ARG, "invalid dt %g or iters %d", (double)dt, iters);
     if (c->n_materials > 0)
         return fail(c, GS_ERR_STATE, "the reverse mode of the LR step does not support grain materials");
+    if (c->n_bodies > 0) return fail(c, GS_ERR_STATE, "the reverse modes do not support rigid bodies");
     const int64_t N = c->n_low;
     if (N == 0) return GS_OK;
     if (!x_in || !v_in || !g_x_out || !g_v_out || !g_x_in || !g_v_in) return fail(c, GS_ERR_ARG, "null buffer");

@@ -136,6 +136,15 @@ struct gs_ctx {
     float2* d_mu = nullptr;                       // [GS_MAX_MATERIALS] (mu_s, mu_k), then the
                                                   // [GS_MAX_MATERIALS^2] cross coefficients
     float2 h_mu[GS_MAX_MATERIALS * (GS_MAX_MATERIALS + 1)];   // host copy of d_mu
+
+    // rigid bodies (shape matching); off while n_bodies == 0
+    int n_bodies = 0;
+    uint32_t* lr_body = nullptr;        // n_low body ids (0: a grain), original order
+    float4* lr_xo = nullptr;            // n_low rest offsets from the body's centre of mass, w = mass
+    uint32_t* body_members = nullptr;   // the particles of body 1, body 2, ... (original indices)
+    uint32_t* body_start = nullptr;     // GS_MAX_BODIES + 1 offsets into body_members
+    float4* body_xf = nullptr;          // 4 per body: (R_r0, R_r1, R_r2, c_r) for r = 0..2, quaternion
+    uint32_t* lr_slot = nullptr;        // n_low: slot of each particle in the LR step's cell order
     uint32_t* nbr_cnt = nullptr;
 
     // HR state (internal order), ping-pong
@@ -232,16 +241,23 @@ size_t gs_scan_aux_words(int64_t total);
 // order; finish also copies ga / gb (when not null) into cell order.
 // Zeroes the n_cell + 1 cell starts and `extra` words after them.
 cudaError_t gs_cs_clear(cudaStream_t s, uint32_t* cell_start, int64_t n_cell, int extra = 0);
-// solid_flag (optional): set to 1 when some position has w = 0.
+// solid_flag (optional): set to 1 when some position has w = 0 or, with
+// body not null, some particle belongs to a rigid body.
 cudaError_t gs_cs_keys(cudaStream_t s, const float4* pos, int64_t n, const SceneDev* scenes, const uint32_t* tag,
                        uint32_t* keys, uint32_t* rank, uint32_t* cell_start, int64_t* launches,
-                       unsigned* solid_flag = nullptr);
+                       unsigned* solid_flag = nullptr, const uint32_t* body = nullptr);
+// Optional work of the cell-order copy (all null: none).
+struct CsExtras {
+    const uint32_t* gb_w = nullptr;       // the w of gb's copies is gb_w[particle] (as bits)
+    const uint32_t* ga_solid = nullptr;   // nonzero: the w of ga's copy is 0
+    uint32_t* slot_of = nullptr;          // slot_of[particle] = its slot
+};
 // ga and gb are copied into cell order: x_out[slot] = x[particle of the
-// slot]; with gb_w not null the w of gb's copies is gb_w[particle] (as bits).
+// slot], with the extras above.
 cudaError_t gs_cs_finish(cudaStream_t s, int64_t n, int64_t n_cell, const uint32_t* keys, const uint32_t* rank,
                          uint32_t* out_keys, uint32_t* out_idx, uint32_t* cell_start, uint32_t* aux, const float4* ga,
                          const float4* gb, float4* ga_out, float4* gb_out, int64_t* launches,
-                         const uint32_t* gb_w = nullptr);
+                         const CsExtras& ex = CsExtras{});
 cudaError_t gs_count_sort_cells(cudaStream_t s, const float4* pos, int64_t n, const SceneDev* scenes,
                                 const uint32_t* tag, int64_t n_cell, uint32_t* keys, uint32_t* rank,
                                 uint32_t* out_keys, uint32_t* out_idx, uint32_t* cell_start, uint32_t* aux,
@@ -300,6 +316,13 @@ struct PbdArgs {
     // original-order positions.
     const float2* mu_mat;
     const float2* mu_cross;
+    // rigid bodies: null without; else the body of each particle (original
+    // order), rest offsets (w = mass), per-body transforms of the current
+    // pass (k_body_xform) and the particle of each slot of the step's order
+    const uint32_t* body;
+    const float4* xo;
+    const float4* body_xf;
+    const uint32_t* sorted_idx;
 };
 cudaError_t gs_launch_predict(cudaStream_t s, const PbdArgs& a, const float4* pos, const float4* vel, float4* xt,
                               int64_t* launches);
@@ -335,6 +358,13 @@ cudaError_t gs_launch_finalize(cudaStream_t s, const PbdArgs& a, const uint32_t*
 // frame of t seconds; the largest |v| / (2 r_LR) of vel into st->rate; pick
 // the next step (and, in a graph, set the while node's condition).
 cudaError_t gs_launch_cfl_begin(cudaStream_t s, CflState* st, float t, int64_t* launches);
+// Shape matching (Sec. 3): for each of n_bodies bodies, c and the rotation
+// R of C = sum m (x~ - c) xo^T from the pass's cell-ordered positions xt
+// (slot_of maps particles to slots), into xf (4 float4 per body; the
+// quaternion entry is also the start of the next extraction).
+cudaError_t gs_launch_body_xform(cudaStream_t s, int n_bodies, const uint32_t* start, const uint32_t* members,
+                                 const uint32_t* slot_of, const float4* xt, const float4* xo, float4* xf,
+                                 int64_t* launches);
 cudaError_t gs_launch_cfl_rate(cudaStream_t s, const PbdArgs& a, const float4* vel, unsigned* rate,
                                int64_t* launches);
 cudaError_t gs_launch_cfl_pick(cudaStream_t s, CflState* st, float dt_max, float cfl, int max_sub,

@@ -296,7 +296,9 @@ struct FinalOut {
 // kMat: grains carry materials (their ids in the w of x); a pair's
 // coefficients are the cross coefficients of the two materials, an SDF
 // contact's sqrt(mu_i mu_b).
-template <bool kL2, bool kMat>
+// kBody: rigid bodies; in solver passes a body particle also receives its
+// shape-matching delta (R xo + c) - x~ (Sec. 3), counted once in n_i.
+template <bool kL2, bool kMat, bool kBody = false>
 __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_t p, bool valid, int sub,
                                               const float4* __restrict__ x_in, const float4* __restrict__ xt_in,
                                               float4* __restrict__ x_out, float4* __restrict__ xt_out,
@@ -379,6 +381,20 @@ __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_
             }
         }
     }
+    if constexpr (kBody) {
+        if (!stab && valid && sub == 0) {
+            const uint32_t i = __ldg(a.sorted_idx + p);
+            const uint32_t bid = __ldg(a.body + i);
+            if (bid != 0u) {
+                const float4* T = a.body_xf + 4 * (bid - 1);
+                const float4 r0 = T[0], r1 = T[1], r2 = T[2], o = __ldg(a.xo + i);
+                acc.Dx += fmaf(r0.x, o.x, fmaf(r0.y, o.y, fmaf(r0.z, o.z, r0.w))) - xtp.x;
+                acc.Dy += fmaf(r1.x, o.x, fmaf(r1.y, o.y, fmaf(r1.z, o.z, r1.w))) - xtp.y;
+                acc.Dz += fmaf(r2.x, o.x, fmaf(r2.y, o.y, fmaf(r2.z, o.z, r2.w))) - xtp.z;
+                ++acc.n;
+            }
+        }
+    }
 #pragma unroll
     for (int o = 1; o < kLanes; o <<= 1) {
         acc.Dx += __shfl_xor_sync(0xffffffffu, acc.Dx, o);
@@ -426,7 +442,7 @@ __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_
     if (stab) st_pos<kL2>(x_out + p, nx);
 }
 
-template <bool kMat>
+template <bool kMat, bool kBody>
 __global__ void __launch_bounds__(128, 6) k_pass(const PbdArgs a, int stab, const float4* __restrict__ x_in,
                                               const float4* __restrict__ xt_in, float4* __restrict__ x_out,
                                               float4* __restrict__ xt_out, const uint32_t* __restrict__ nbr,
@@ -434,7 +450,8 @@ __global__ void __launch_bounds__(128, 6) k_pass(const PbdArgs a, int stab, cons
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t p = t / kLanes;
-    pass_particle<false, kMat>(a, stab, p, p < a.n, (int)(t % kLanes), x_in, xt_in, x_out, xt_out, nbr, cnt, fin);
+    pass_particle<false, kMat, kBody>(a, stab, p, p < a.n, (int)(t % kLanes), x_in, xt_in, x_out, xt_out, nbr, cnt,
+                                      fin);
 }
 
 // ---- all passes of one step in one launch --------------------------------
@@ -546,6 +563,124 @@ __global__ void k_finalize(const PbdArgs a, const uint32_t* __restrict__ idx, co
     }
 }
 
+// ---- shape matching of rigid bodies (Sec. 3) -------------------------------
+// Rotation of the polar decomposition of C by the iteration of Mueller et
+// al., "A Robust Method to Extract the Rotational Part of Deformations"
+// (2016): with r_k and c_k the columns of R(q) and C,
+//   omega = sum_k r_k x c_k / (|sum_k r_k . c_k| + eps),  q <- exp(omega) q,
+// started from the body's previous rotation.  q = (x, y, z, w).
+__device__ void quat_to_rows(const float4 q, float R[9])
+{
+    const float x = q.x, y = q.y, z = q.z, w = q.w;
+    R[0] = 1.f - 2.f * (y * y + z * z);
+    R[1] = 2.f * (x * y - z * w);
+    R[2] = 2.f * (x * z + y * w);
+    R[3] = 2.f * (x * y + z * w);
+    R[4] = 1.f - 2.f * (x * x + z * z);
+    R[5] = 2.f * (y * z - x * w);
+    R[6] = 2.f * (x * z - y * w);
+    R[7] = 2.f * (y * z + x * w);
+    R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+__device__ float4 extract_rotation(const float C[9], float4 q)
+{
+    float n2 = 0.f;
+    for (int k = 0; k < 9; ++k) n2 += C[k] * C[k];
+    const float eps = 1e-9f * sqrtf(n2) + 1e-30f;
+    for (int it = 0; it < 24; ++it) {
+        float R[9];
+        quat_to_rows(q, R);
+        float ox = 0.f, oy = 0.f, oz = 0.f, d = 0.f;
+        for (int k = 0; k < 3; ++k) {   // column k of R and of C
+            const float rx = R[k], ry = R[3 + k], rz = R[6 + k];
+            const float cx = C[k], cy = C[3 + k], cz = C[6 + k];
+            ox += ry * cz - rz * cy;
+            oy += rz * cx - rx * cz;
+            oz += rx * cy - ry * cx;
+            d += rx * cx + ry * cy + rz * cz;
+        }
+        const float inv = 1.0f / (fabsf(d) + eps);
+        ox *= inv;
+        oy *= inv;
+        oz *= inv;
+        const float ang = sqrtf(ox * ox + oy * oy + oz * oz);
+        if (!(ang > 1e-7f)) break;
+        const float s = sinf(0.5f * ang) / ang, cw = cosf(0.5f * ang);
+        const float4 e = make_float4(ox * s, oy * s, oz * s, cw);   // exp(omega)
+        float4 nq = make_float4(e.w * q.x + e.x * q.w + e.y * q.z - e.z * q.y,
+                                e.w * q.y - e.x * q.z + e.y * q.w + e.z * q.x,
+                                e.w * q.z + e.x * q.y - e.y * q.x + e.z * q.w,
+                                e.w * q.w - e.x * q.x - e.y * q.y - e.z * q.z);
+        const float nn = rsqrtf(nq.x * nq.x + nq.y * nq.y + nq.z * nq.z + nq.w * nq.w);
+        q = make_float4(nq.x * nn, nq.y * nn, nq.z * nn, nq.w * nn);
+    }
+    return q;
+}
+
+// One block per body.  Sums relative to the body's first particle keep the
+// float32 products small: with p' = x~ - p0, c = p0 + sum m p' / M and
+// C = sum m p' xo^T - (c - p0) (sum m xo)^T.
+__global__ void __launch_bounds__(256) k_body_xform(const uint32_t* __restrict__ start,
+                                                    const uint32_t* __restrict__ members,
+                                                    const uint32_t* __restrict__ slot_of,
+                                                    const float4* __restrict__ xt, const float4* __restrict__ xo,
+                                                    float4* __restrict__ xf)
+{
+    const int b = blockIdx.x;
+    const uint32_t k0 = start[b], k1 = start[b + 1];
+    if (k0 == k1) return;
+    const float4 p0 = xt[slot_of[members[k0]]];
+    float acc[16];   // M, sum m p' (3), sum m xo (3), sum m p' xo^T (9)
+    for (int k = 0; k < 16; ++k) acc[k] = 0.f;
+    for (uint32_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        const uint32_t i = members[k];
+        const float4 x = xt[slot_of[i]], o = xo[i];
+        const float m = o.w, px = x.x - p0.x, py = x.y - p0.y, pz = x.z - p0.z;
+        acc[0] += m;
+        acc[1] += m * px;
+        acc[2] += m * py;
+        acc[3] += m * pz;
+        acc[4] += m * o.x;
+        acc[5] += m * o.y;
+        acc[6] += m * o.z;
+        const float mp[3] = {m * px, m * py, m * pz}, oo[3] = {o.x, o.y, o.z};
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int s = 0; s < 3; ++s) acc[7 + 3 * r + s] += mp[r] * oo[s];
+    }
+    __shared__ float red[8][16];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        float v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int k = 0; k < 16; ++k) {
+        float v = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][k];
+        acc[k] = v;
+    }
+    const float M = acc[0];
+    const float dx = acc[1] / M, dy = acc[2] / M, dz = acc[3] / M;   // c - p0
+    const float d[3] = {dx, dy, dz};
+    float C[9];
+    for (int r = 0; r < 3; ++r)
+        for (int s = 0; s < 3; ++s) C[3 * r + s] = acc[7 + 3 * r + s] - d[r] * acc[4 + s];
+    float4 q = xf[4 * b + 3];
+    if (!(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w > 0.5f)) q = make_float4(0.f, 0.f, 0.f, 1.f);
+    q = extract_rotation(C, q);
+    float R[9];
+    quat_to_rows(q, R);
+    const float c[3] = {p0.x + dx, p0.y + dy, p0.z + dz};
+    for (int r = 0; r < 3; ++r) xf[4 * b + r] = make_float4(R[3 * r], R[3 * r + 1], R[3 * r + 2], c[r]);
+    xf[4 * b + 3] = q;
+}
+
 // ---- CFL-limited LR substeps of a frame (gs_frame_adaptive) ----------------
 __global__ void k_cfl_begin(CflState* st, float t)
 {
@@ -653,10 +788,17 @@ cudaError_t gs_launch_pass(cudaStream_t s, const PbdArgs& a, int stab, const flo
 {
     if (a.n <= 0) return cudaSuccess;
     const FinalOut fin{fin_idx, fin_pos, fin_vel, fin_idx ? fin_rate : nullptr};
-    if (a.mu_cross)
-        k_pass<true><<<gs_blocks(a.n * kLanes, 128), 128, 0, s>>>(a, stab, x_in, xt_in, x_out, xt_out, nbr, cnt, fin);
-    else
-        k_pass<false><<<gs_blocks(a.n * kLanes, 128), 128, 0, s>>>(a, stab, x_in, xt_in, x_out, xt_out, nbr, cnt, fin);
+    const unsigned nb = gs_blocks(a.n * kLanes, 128);
+    if (a.body) {
+        if (a.mu_cross)
+            k_pass<true, true><<<nb, 128, 0, s>>>(a, stab, x_in, xt_in, x_out, xt_out, nbr, cnt, fin);
+        else
+            k_pass<false, true><<<nb, 128, 0, s>>>(a, stab, x_in, xt_in, x_out, xt_out, nbr, cnt, fin);
+    } else if (a.mu_cross) {
+        k_pass<true, false><<<nb, 128, 0, s>>>(a, stab, x_in, xt_in, x_out, xt_out, nbr, cnt, fin);
+    } else {
+        k_pass<false, false><<<nb, 128, 0, s>>>(a, stab, x_in, xt_in, x_out, xt_out, nbr, cnt, fin);
+    }
     *launches += 1;
     return cudaGetLastError();
 }
@@ -730,6 +872,16 @@ cudaError_t gs_launch_cfl_pick(cudaStream_t s, CflState* st, float dt_max, float
                                cudaGraphConditionalHandle h, int in_graph, unsigned body_kernels, int64_t* launches)
 {
     k_cfl_pick<<<1, 1, 0, s>>>(st, dt_max, cfl, max_sub, h, in_graph, body_kernels);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_body_xform(cudaStream_t s, int n_bodies, const uint32_t* start, const uint32_t* members,
+                                 const uint32_t* slot_of, const float4* xt, const float4* xo, float4* xf,
+                                 int64_t* launches)
+{
+    if (n_bodies <= 0) return cudaSuccess;
+    k_body_xform<<<(unsigned)n_bodies, 256, 0, s>>>(start, members, slot_of, xt, xo, xf);
     *launches += 1;
     return cudaGetLastError();
 }

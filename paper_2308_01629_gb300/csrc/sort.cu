@@ -205,13 +205,14 @@ __global__ void k_scene_keys(const float4* __restrict__ pos, int64_t n, const Sc
 
 __global__ void k_cs_keys(const float4* __restrict__ pos, int64_t n, const SceneDev* __restrict__ scenes,
                           const uint32_t* __restrict__ tag, uint32_t* __restrict__ keys, uint32_t* __restrict__ rank,
-                          uint32_t* __restrict__ cnt, unsigned* solid_flag)
+                          uint32_t* __restrict__ cnt, unsigned* solid_flag, const uint32_t* __restrict__ body)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const SceneDev& sc = scenes[tag[i] & ~kPadBit];
     const float4 p = pos[i];
-    if (solid_flag && p.w == 0.0f) atomicOr(solid_flag, 1u);   // a particle of infinite mass
+    // a particle of infinite mass or of a rigid body
+    if (solid_flag && (p.w == 0.0f || (body && body[i] != 0u))) atomicOr(solid_flag, 1u);
     const uint32_t cell = grid_cell_of(sc, p.x, p.y, p.z);
     keys[i] = cell;
     rank[i] = atomicAdd(cnt + cell, 1u);
@@ -346,7 +347,7 @@ __device__ __forceinline__ void order_small(uint32_t* __restrict__ idx, uint32_t
 
 __global__ void k_cs_order(const uint32_t* __restrict__ start, int64_t n_cell, uint32_t* __restrict__ idx,
                            const float4* __restrict__ ga, const float4* __restrict__ gb, float4* __restrict__ ga_out,
-                           float4* __restrict__ gb_out, const uint32_t* __restrict__ gb_w)
+                           float4* __restrict__ gb_out, const CsExtras ex)
 {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_cell) return;
@@ -375,14 +376,18 @@ __global__ void k_cs_order(const uint32_t* __restrict__ start, int64_t n_cell, u
     if (ga) {
         for (uint32_t j = b; j < e; ++j) {
             const uint32_t i = idx[j];
-            ga_out[j] = ga[i];
+            float4 u = ga[i];
+            if (ex.ga_solid && ex.ga_solid[i] != 0u) u.w = 0.0f;
+            ga_out[j] = u;
             if (gb) {
                 float4 v = gb[i];
-                if (gb_w) v.w = __uint_as_float(gb_w[i]);
+                if (ex.gb_w) v.w = __uint_as_float(ex.gb_w[i]);
                 gb_out[j] = v;
             }
         }
     }
+    if (ex.slot_of)
+        for (uint32_t j = b; j < e; ++j) ex.slot_of[idx[j]] = j;
 }
 
 __global__ void k_cell_start(const uint32_t* __restrict__ sk, int64_t n, int64_t n_cell, uint32_t* __restrict__ start)
@@ -488,17 +493,17 @@ cudaError_t gs_cs_clear(cudaStream_t s, uint32_t* cell_start, int64_t n_cell, in
 
 cudaError_t gs_cs_keys(cudaStream_t s, const float4* pos, int64_t n, const SceneDev* scenes, const uint32_t* tag,
                        uint32_t* keys, uint32_t* rank, uint32_t* cell_start, int64_t* launches,
-                       unsigned* solid_flag)
+                       unsigned* solid_flag, const uint32_t* body)
 {
     if (n <= 0) return cudaSuccess;
-    k_cs_keys<<<gs_blocks(n, 256), 256, 0, s>>>(pos, n, scenes, tag, keys, rank, cell_start, solid_flag);
+    k_cs_keys<<<gs_blocks(n, 256), 256, 0, s>>>(pos, n, scenes, tag, keys, rank, cell_start, solid_flag, body);
     *launches += 1;
     return cudaGetLastError();
 }
 
 cudaError_t gs_cs_finish(cudaStream_t s, int64_t n, int64_t n_cell, const uint32_t* keys, const uint32_t* rank,
                          uint32_t* out_keys, uint32_t* out_idx, uint32_t* cell_start, uint32_t* aux, const float4* ga,
-                         const float4* gb, float4* ga_out, float4* gb_out, int64_t* launches, const uint32_t* gb_w)
+                         const float4* gb, float4* ga_out, float4* gb_out, int64_t* launches, const CsExtras& ex)
 {
     const int64_t total = n_cell + 1;
     const int64_t nt = (total + kScanTile - 1) / kScanTile;
@@ -508,7 +513,7 @@ cudaError_t gs_cs_finish(cudaStream_t s, int64_t n, int64_t n_cell, const uint32
     *launches += 3;
     if (n > 0) {
         k_cs_scatter<<<gs_blocks(n, 256), 256, 0, s>>>(keys, rank, n, cell_start, out_keys, out_idx);
-        k_cs_order<<<gs_blocks(n_cell, 256), 256, 0, s>>>(cell_start, n_cell, out_idx, ga, gb, ga_out, gb_out, gb_w);
+        k_cs_order<<<gs_blocks(n_cell, 256), 256, 0, s>>>(cell_start, n_cell, out_idx, ga, gb, ga_out, gb_out, ex);
         *launches += 2;
     }
     return cudaGetLastError();

@@ -421,3 +421,50 @@ def digging_particle_bucket(seed=SEED_BASE + 7, t=0.0, **kw):
     sc["sdfs"] = [sc["sdfs"][0]]
     sc.pop("bucket_index", None)
     return sc
+
+
+# --------------------------------------------------------- rigid bodies ---
+# Sec. 3 / Sec. 5.2: a movable rigid body sampled with LR particles of finite
+# mass that collide like grains and are shape-matched to their rest shape
+# every solver pass.  "lr_body" holds the body of each LR particle (0: a
+# grain).
+def cube_with_block(seed=SEED_BASE + 8, v_scale=0.3):
+    """The stirred cube whose top three layers' central 4 x 4 columns form a
+    rigid block (48 particles)."""
+    sc = stir(cube(), seed=seed, v_scale=v_scale)
+    p = sc["lr_pos"][:, :3]
+    lo, hi = p.min(0), p.max(0)
+    r = sc["r_low"]
+    mid = 0.5 * (lo + hi)
+    sel = (np.abs(p[:, 0] - mid[0]) < 4 * r) & (np.abs(p[:, 1] - mid[1]) < 4 * r) & (p[:, 2] > hi[2] - 5 * r)
+    body = np.zeros(len(p), np.uint32)
+    body[sel] = 1
+    sc = dict(sc)
+    sc["lr_body"] = body
+    return sc
+
+
+def digging_with_boulder(seed=SEED_BASE + 9, radius=0.08, density=5000.0, velocity=(0.0, 0.0, -2.0), **kw):
+    """The digging bed with a boulder hurled into it: a sphere of radius
+    `radius` sampled on a 2 r_LR lattice (density 5000 kg/m^3, the paper's
+    rigid body in the sand-castle scene), its lowest particle 2 r_LR above
+    the bed's highest grain, moving at `velocity`; the HR set is redrawn
+    around the grains."""
+    sc = digging(**kw)
+    r = sc["r_low"]
+    n = int(radius / (2 * r)) + 1
+    g = np.stack(np.meshgrid(*[np.arange(-n, n + 1)] * 3, indexing="ij"), -1).reshape(-1, 3) * 2 * r
+    g = g[np.linalg.norm(g, axis=1) <= radius]
+    top = sc["lr_pos"][:, 2].max()
+    c = np.array([0.5 * sc["box_hi"][0], 0.5 * sc["box_hi"][1], top + 4 * r + radius])
+    xyz = g + c
+    n_g = len(sc["lr_pos"])
+    sc = with_solids(sc, xyz, velocity, seed)
+    m = density * 4.0 / 3.0 * math.pi * r ** 3
+    sc["lr_pos"][n_g:, 3] = np.float32(1.0 / m)
+    body = np.zeros(len(sc["lr_pos"]), np.uint32)
+    body[n_g:] = 1
+    sc["lr_body"] = body
+    sc.pop("n_solid", None)
+    sc["n_body"] = len(xyz)
+    return sc

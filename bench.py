@@ -518,22 +518,32 @@ def run_gpu(args):
     # bucket sampled as LR particles of inverse mass 0 (moving with the
     # bucket's velocity) instead of the bucket SDF, in a second context,
     # timed alike against the SDF bucket's frames
+    # and a rigid body by shape matching (Sec. 3): a boulder of 389 LR
+    # particles (5000 kg/m^3) hurled into the same bed at 2 m/s
     solid = None
     if not args.no_solid and args.workload == "digging":
         ps = scenes.digging_particle_bucket(size=args.bed_size)
-        pctx = gs.Context(ps, stream=stream.cuda_stream)
-        pctx.set_tuning(tune_w, tune_b)
-        pctx.set_graphs(True)
-        tried = {"sdf_bucket": [], "particle_bucket": []}
+        pb = scenes.digging_with_boulder(size=args.bed_size)
+        extra = {}
+        for name, s in (("particle_bucket", ps), ("boulder", pb)):
+            x = gs.Context(s, stream=stream.cuda_stream)
+            x.set_tuning(tune_w, tune_b)
+            x.set_graphs(True)
+            extra[name] = (x, s)
+        tried = {"sdf_bucket": [], "particle_bucket": [], "boulder": []}
         for _ in range(3):
             tried["sdf_bucket"].append(frame_ms(lambda: step(ctx), stream, dev, torch, warm=3, reps=8))
-            tried["particle_bucket"].append(frame_ms(lambda: pctx.frame(DT, N_SUB, ps["iters"]), stream, dev,
-                                                     torch, warm=3, reps=8))
-        pctx.sync()
-        pctx.close()
+            for name, (x, s) in extra.items():
+                tried[name].append(frame_ms(lambda: x.frame(DT, N_SUB, s["iters"]), stream, dev, torch, warm=3,
+                                            reps=8))
+        for x, _ in extra.values():
+            x.sync()
+            x.close()
         solid = {"bucket_particles": int(ps["n_solid"]), "n_low": len(ps["lr_pos"]),
                  "frame_ms_sdf_bucket": float(np.median(tried["sdf_bucket"])),
                  "frame_ms_particle_bucket": float(np.median(tried["particle_bucket"])),
+                 "boulder_particles": int(pb["n_body"]),
+                 "frame_ms_boulder_shape_matched": float(np.median(tried["boulder"])),
                  "timing": "median of 3 alternating runs of 8 graph-replayed frames, L2 not flushed"}
 
     # end to end through the C ABI with host buffers

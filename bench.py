@@ -277,6 +277,8 @@ def run_diff(args, dev, stream, gs, torch):
     with torch.cuda.stream(stream):
         plain = gs.Context(sc, stream=stream.cuda_stream)
         ctx = gs.Context(sc, stream=stream.cuda_stream)
+        plain.set_graphs(True)   # frames, and the functional LR steps, replayed as graphs
+        ctx.set_graphs(True)
         state = [torch.from_numpy(np.ascontiguousarray(sc[n])).to(dev) for n in ("lr_pos", "lr_vel", "hr_pos",
                                                                                   "hr_vel")]
         target = torch.from_numpy(sc["target"]).to(dev)

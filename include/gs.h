@@ -403,8 +403,9 @@ int gs_upsample_backward(gs_ctx* ctx, const float* lr_pos, const float* lr_vel, 
  * friction, SDF contacts with fixed normals), including the dependence of the
  * height-scaled mass ratios on the start-of-step heights.  Outputs are
  * overwritten.  Asynchronous.  Both backward entry points differentiate
- * grains only: they return GS_ERR_STATE (and wait for the stream) when the
- * LR positions hold particles of inverse mass 0. */
+ * grains only: LR positions holding particles of inverse mass 0 make the
+ * next blocking call (gs_sync, gs_read) return GS_ERR_STATE, and the
+ * gradients of that call are invalid. */
 int gs_step_low_forward(gs_ctx* ctx, const float* x_in, const float* v_in, float* x_out, float* v_out, float dt,
                         int iters);
 int gs_step_low_backward(gs_ctx* ctx, const float* x_in, const float* v_in, const float* g_x_out, const float* g_v_out,

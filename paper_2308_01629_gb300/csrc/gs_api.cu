@@ -91,6 +91,9 @@ int report_device_errors(gs_ctx* c)
         if (e & GS_DEVERR_BAD_ID) return fail(c, GS_ERR_STATE, "HR id outside [0, n_high) met while unpermuting");
         if (e & GS_DEVERR_NONFINITE_ASYNC)
             return fail(c, GS_ERR_DOMAIN, "an asynchronously written field held a non-finite value; the state is invalid");
+        if (e & GS_DEVERR_SOLID_REVERSE)
+            return fail(c, GS_ERR_STATE, "a reverse mode was given LR particles of infinite mass; its gradients are "
+                                         "invalid");
         if (e & GS_DEVERR_BARRIER_TIMEOUT)
             return fail(c, GS_ERR_TIMEOUT, "a grid barrier of the persistent LR solver timed out; results are invalid");
     }
@@ -145,12 +148,12 @@ __global__ void k_max_id(const uint32_t* __restrict__ ids, int64_t n, unsigned* 
     if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
 }
 
-// Number of positions with w = 0 (LR particles of infinite mass) into *out.
-__global__ void k_count_solid(const float4* __restrict__ pos, int64_t n, unsigned* out)
+// Sets `bit` in *err when some of the n positions has w = 0 (an LR particle
+// of infinite mass).
+__global__ void k_flag_solid(const float4* __restrict__ pos, int64_t n, int* err, int bit)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const unsigned b = __ballot_sync(0xffffffffu, i < n && pos[i].w == 0.0f);
-    if ((threadIdx.x & 31) == 0 && b) atomicAdd(out, (unsigned)__popc(b));
+    if (i < n && pos[i].w == 0.0f) atomicOr(err, bit);
 }
 
 cudaError_t launch_hr_load(gs_ctx* c, const float4* src, float4* dst, int set_ids)
@@ -596,6 +599,63 @@ void drop_graphs(gs_ctx* c)
         if (g.graph) cudaGraphDestroy(g.graph);
     }
     c->graphs.clear();
+    for (auto& g : c->fgraphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    c->fgraphs.clear();
+}
+
+// The functional LR step entry points copy the caller's buffers in and out
+// around a fixed sequence on the context's own buffers; with graphs enabled
+// (and a stream that can be captured: not the legacy or per-thread default
+// stream) that sequence is captured once per key and replayed.
+bool capturable(const gs_ctx* c)
+{
+    return c->use_graphs && !c->timing && c->stream != nullptr && c->stream != cudaStreamLegacy &&
+           c->stream != cudaStreamPerThread;
+}
+
+template <class F>
+int replay_or_run(gs_ctx* c, uint64_t key, F&& body)
+{
+    if (!capturable(c)) return body();
+    GraphEntry* ge = nullptr;
+    for (auto& g : c->fgraphs)
+        if (g.key == key) ge = &g;
+    if (!ge) {
+        const int64_t l0 = c->launches;
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        const int st = body();
+        const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        if (st != GS_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+        GraphEntry g;
+        g.key = key;
+        g.kernels = c->launches - l0;
+        c->launches = l0;
+        const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) return cuda_fail(c, ei, "instantiate graph");
+        c->fgraphs.push_back(g);
+        ge = &c->fgraphs.back();
+    }
+    CK(cudaGraphLaunch(ge->exec, c->stream), "graph launch");
+    c->launches += ge->kernels;
+    return GS_OK;
+}
+
+uint64_t step_key(const gs_ctx* c, char kind, float dt, int iters)
+{
+    uint32_t db;
+    std::memcpy(&db, &dt, 4);
+    uint64_t k = 0xcbf29ce484222325ull;
+    for (uint64_t v : {(uint64_t)kind, (uint64_t)db, (uint64_t)iters, (uint64_t)c->use_solver,
+                       (uint64_t)c->solver_selftest, (uint64_t)(c->n_materials > 0), (uint64_t)(c->n_bodies > 0)})
+        k = (k ^ v) * 0x100000001b3ull;
+    return k;
 }
 
 // ---- pipelined frames ------------------------------------------------------
@@ -878,7 +938,7 @@ void gs_destroy(gs_ctx* c)
                     c->hr_pos[0],  c->hr_pos[1],  c->hr_vel[0],  c->hr_vel[1],  c->hr_keys[0], c->hr_keys[1],
                     c->hr_vals[0], c->hr_vals[1], c->nbr,        c->nbr_cnt,    c->tmp4,      c->sort_hist,
                     c->d_work,     c->d_err,      c->gXs,        c->gVs,       c->snap,      c->snap_xt,
-                    c->adj_gx,     c->adj_gxt,    c->adj_h,      c->adj_gws,   c->scan_aux,   c->d_bar,
+                    c->adj_io,     c->adj_gx,     c->adj_gxt,    c->adj_h,      c->adj_gws,   c->scan_aux,   c->d_bar,
                     c->step_cell_start, c->d_sdf_pend, c->stage_in, c->lr_mat, c->d_mu, c->d_cfl, c->lr_body, c->lr_xo, c->body_members,
                     c->body_start, c->body_xf, c->lr_slot,
                     c->async_in[0], c->async_in[1], c->async_in[2], c->async_in[3],
@@ -1633,20 +1693,16 @@ int gs_upsample_forward(gs_ctx* c, const float* lr_pos, const float* lr_vel, con
     return GS_OK;
 }
 
-// The reverse modes differentiate grains only: GS_ERR_STATE when the LR
-// positions (device memory, n of them) hold particles of infinite mass.
-static int refuse_solid(gs_ctx* c, const float* pos, int64_t n)
+// The reverse modes differentiate grains only: LR positions (device memory,
+// n of them) holding particles of infinite mass raise a device error bit,
+// reported as GS_ERR_STATE by the next blocking call (no wait here).
+static int flag_solid(gs_ctx* c, const float* pos, int64_t n)
 {
     if (n <= 0) return GS_OK;
-    unsigned* word = (unsigned*)(c->d_err + 1);
-    CK(cudaMemsetAsync(word, 0, sizeof(unsigned), c->stream), "clear word");
-    k_count_solid<<<gs_blocks(n, 256), 256, 0, c->stream>>>((const float4*)pos, n, word);
+    k_flag_solid<<<gs_blocks(n, 256), 256, 0, c->stream>>>((const float4*)pos, n, c->d_err,
+                                                            GS_DEVERR_SOLID_REVERSE);
     c->launches += 1;
-    CK(cudaGetLastError(), "count");
-    CK(cudaMemcpyAsync(c->h_err, word, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream), "read word");
-    CK(cudaStreamSynchronize(c->stream), "synchronize");
-    if (*c->h_err != 0)
-        return fail(c, GS_ERR_STATE, "reverse mode with %u LR particles of infinite mass", (unsigned)*c->h_err);
+    CK(cudaGetLastError(), "flag");
     return GS_OK;
 }
 
@@ -1665,7 +1721,7 @@ int gs_upsample_backward(gs_ctx* c, const float* lr_pos, const float* lr_vel, co
         (M > 0 && (!hr_pos_in || !hr_vel_in || !g_hr_pos_out || !g_hr_vel_out || !g_hr_pos_in || !g_hr_vel_in)))
         return fail(c, GS_ERR_ARG, "null buffer");
     if (c->n_bodies > 0) return fail(c, GS_ERR_STATE, "the reverse modes do not support rigid bodies");
-    st = refuse_solid(c, lr_pos, N);
+    st = flag_solid(c, lr_pos, N);
     if (st) return st;
     if (N) {
         CK(cudaMemcpyAsync(c->lr_pos, lr_pos, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
@@ -1700,12 +1756,17 @@ int gs_step_low_forward(gs_ctx* c, const float* x_in, const float* v_in, float* 
     if (!x_in || !v_in || !x_out || !v_out) return fail(c, GS_ERR_ARG, "null buffer");
     CK(cudaMemcpyAsync(c->lr_pos, x_in, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
     CK(cudaMemcpyAsync(c->lr_vel, v_in, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
-    st = step_low_impl(c, dt, iters);
+    st = replay_or_run(c, step_key(c, 'f', dt, iters), [&] { return step_low_impl(c, dt, iters); });
     if (st) return st;
+    c->lr_sorted_keys = c->lr_keys[1];   // the host state the step leaves, replayed or not
+    c->lr_sorted_idx = c->lr_vals[1];
+    c->lr_binned = false;
     CK(cudaMemcpyAsync(x_out, c->lr_pos, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
     CK(cudaMemcpyAsync(v_out, c->lr_vel, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
     return GS_OK;
 }
+
+static int step_low_reverse(gs_ctx* c, float dt, int iters);
 
 int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const float* g_x_out, const float* g_v_out,
                          float* g_x_in, float* g_v_in, float dt, int iters)
@@ -1722,8 +1783,6 @@ int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const 
     const int64_t N = c->n_low;
     if (N == 0) return GS_OK;
     if (!x_in || !v_in || !g_x_out || !g_v_out || !g_x_in || !g_v_in) return fail(c, GS_ERR_ARG, "null buffer");
-    st = refuse_solid(c, x_in, N);
-    if (st) return st;
     const int total = c->n_stab + iters;
     if (total > c->snap_cap) {
         if (c->snap) cudaFree(c->snap);
@@ -1736,18 +1795,42 @@ int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const 
             return fail(c, GS_ERR_OOM, "no memory for the reverse-mode snapshots");
         }
         c->snap_cap = total;
+        drop_graphs(c);   // captured reverse steps hold the old snapshot buffers
     }
     if (!c->adj_gx) {
         bool ok = dalloc(&c->adj_gx, N) == cudaSuccess && dalloc(&c->adj_gxt, N) == cudaSuccess &&
-                  dalloc(&c->adj_h, N) == cudaSuccess && dalloc(&c->adj_gws, N) == cudaSuccess;
+                  dalloc(&c->adj_h, N) == cudaSuccess && dalloc(&c->adj_gws, N) == cudaSuccess &&
+                  dalloc(&c->adj_io, (size_t)4 * N) == cudaSuccess;
         if (!ok) {
             cudaGetLastError();
             return fail(c, GS_ERR_OOM, "no memory for the reverse-mode buffers");
         }
     }
-    // forward again, keeping what every pass evaluates on
+    // the caller's buffers in; the rest runs on the context's own buffers
+    // (replayed as a graph when graphs are enabled)
     CK(cudaMemcpyAsync(c->lr_pos, x_in, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
     CK(cudaMemcpyAsync(c->lr_vel, v_in, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    CK(cudaMemcpyAsync(c->adj_io, g_x_out, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    CK(cudaMemcpyAsync(c->adj_io + N, g_v_out, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    st = replay_or_run(c, step_key(c, 'b', dt, iters), [&] { return step_low_reverse(c, dt, iters); });
+    if (st) return st;
+    CK(cudaMemcpyAsync(g_x_in, c->adj_io + 2 * N, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    CK(cudaMemcpyAsync(g_v_in, c->adj_io + 3 * N, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    c->lr_sorted_keys = c->lr_keys[1];   // the host state the reverse step leaves
+    c->lr_sorted_idx = c->lr_vals[1];
+    c->lr_binned = false;
+    return GS_OK;
+}
+
+// The reverse LR step on the context's buffers: the step again from
+// (lr_pos, lr_vel) keeping what every pass evaluates on, then the passes in
+// reverse; dL/d outputs from adj_io[0..1], dL/d inputs into adj_io[2..3].
+static int step_low_reverse(gs_ctx* c, float dt, int iters)
+{
+    const int64_t N = c->n_low;
+    const int total = c->n_stab + iters;
+    int st = flag_solid(c, (const float*)c->lr_pos, N);
+    if (st) return st;
     PbdArgs a = pbd_args(c, dt);
     CK(gs_launch_predict(c->stream, a, c->lr_pos, c->lr_vel, c->lr_xt, &c->launches), "predict");
     st = bin_low_at(c, c->lr_xt);
@@ -1775,8 +1858,8 @@ int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const 
     }
     const float4* xfix = c->s_x[bx];          // x after stabilization
     const float4* ws = c->s_xt[0];            // w of xt carries the inverse scaled mass
-    CK(gs_launch_adj_init(c->stream, N, c->lr_sorted_idx, (const float4*)g_x_out, (const float4*)g_v_out, dt,
-                          c->adj_gx, c->adj_gxt, c->adj_gws, &c->launches),
+    CK(gs_launch_adj_init(c->stream, N, c->lr_sorted_idx, c->adj_io, c->adj_io + N, dt, c->adj_gx, c->adj_gxt,
+                          c->adj_gws, &c->launches),
        "reverse init");
     for (int it = total - 1; it >= 0; --it) {
         const int stab = it < c->n_stab;
@@ -1784,8 +1867,8 @@ int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const 
                               c->nbr, c->nbr_cnt, c->adj_h, c->adj_gx, c->adj_gxt, c->adj_gws, &c->launches),
            "reverse pass");
     }
-    CK(gs_launch_adj_final(c->stream, a, c->lr_sorted_idx, ws, c->adj_gx, c->adj_gxt, c->adj_gws, (float4*)g_x_in,
-                           (float4*)g_v_in, &c->launches),
+    CK(gs_launch_adj_final(c->stream, a, c->lr_sorted_idx, ws, c->adj_gx, c->adj_gxt, c->adj_gws, c->adj_io + 2 * N,
+                           c->adj_io + 3 * N, &c->launches),
        "reverse predict");
     c->lr_binned = false;
     return GS_OK;

@@ -49,6 +49,7 @@ enum : int {
     GS_DEVERR_BAD_ID = 2,         // an HR id outside [0, n_high) was met while unpermuting
     GS_DEVERR_BARRIER_TIMEOUT = 4,   // a grid barrier of the persistent LR solver gave up waiting
     GS_DEVERR_NONFINITE_ASYNC = 8,   // an asynchronously written field held a non-finite value
+    GS_DEVERR_SOLID_REVERSE = 16,    // a reverse mode met LR particles of infinite mass
 };
 
 // HR slot tag: scene index, with this bit set on padding slots.
@@ -180,6 +181,8 @@ struct gs_ctx {
     float4* adj_gxt = nullptr;
     float4* adj_h = nullptr;
     float* adj_gws = nullptr;
+    float4* adj_io = nullptr;      // [4][n_low]: dL/dx_out, dL/dv_out in; dL/dx_in, dL/dv_in out (original order)
+    std::vector<GraphEntry> fgraphs;   // graphs of the functional LR step entry points
 
     // radix sort histogram scratch (HR reorder, static-scratch binning)
     uint32_t* sort_hist = nullptr;

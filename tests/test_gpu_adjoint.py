@@ -138,6 +138,41 @@ def test_checkpointed_rollout_equals_plain_rollout():
     g.close()
 
 
+def test_graph_replayed_functional_steps_equal_direct_launches():
+    """With graphs enabled on a stream that can be captured, the functional
+    LR step entry points replay their fixed sequence as a CUDA graph; the
+    forward outputs must be the same bits as direct launches, also on the
+    second and later calls (replays), and the gradients the same up to the
+    order of the reverse kernels' atomic accumulations (which varies from run
+    to run with or without graphs)."""
+    import torch
+
+    import paper_2308_01629_gb300 as gs
+    from paper_2308_01629_gb300.diff import rollout
+    sc = scenes.column(n_low=400, ratio=8)
+    s = torch.cuda.Stream()
+    grads = {}
+    with torch.cuda.stream(s):
+        for graphs in (False, True):
+            g = gs.Context(sc, stream=s.cuda_stream)
+            g.set_graphs(graphs)
+            out = []
+            for rep in range(3):
+                X, V, x, v = (_t(sc[k]) for k in ("lr_pos", "lr_vel", "hr_pos", "hr_vel"))
+                V.requires_grad_(True)
+                res = rollout(g, X, V, x, v, DT, frames=6, n_sub=2, iters=4, checkpoint_every=3)
+                loss = (res[2][:, :3] ** 2).sum()
+                loss.backward()
+                out.append((res[0].detach().cpu().numpy(), V.grad.cpu().numpy()))
+            torch.cuda.synchronize()
+            g.close()
+            grads[graphs] = out
+    for a, b in zip(grads[False], grads[True]):
+        np.testing.assert_array_equal(a[0], b[0])
+        assert _rel(b[1], a[1]) < 1e-5
+    assert np.abs(grads[True][0][1]).max() > 0
+
+
 def _gpu_forward_states(g, sc):
     """The GPU forward of the differentiation workload, step by step, with the
     inputs of every operation kept as float32 tensors."""

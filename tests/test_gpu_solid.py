@@ -161,14 +161,18 @@ def test_reverse_modes_refuse_solid_particles():
     ctx = gs.Context(sc, stream="torch")
     x = torch.tensor(sc["lr_pos"], device="cuda", requires_grad=True)
     v = torch.tensor(sc["lr_vel"], device="cuda", requires_grad=True)
+    # the refusal is a device-side check, reported by the next blocking call
     ox, ov = diff.StepLowFn.apply(ctx, 1.0 / 240.0, 2, x, v)
+    (ox[:, :3].sum() + ov[:, :3].sum()).backward()
     with pytest.raises(gs.GsError) as e:
-        (ox[:, :3].sum() + ov[:, :3].sum()).backward()
+        ctx.sync()
     assert e.value.code == gs.GS_ERR_STATE
     hx = torch.tensor(sc["hr_pos"], device="cuda", requires_grad=True)
     hv = torch.tensor(sc["hr_vel"], device="cuda", requires_grad=True)
     px, pv = diff.UpsampleFn.apply(ctx, DT, x.detach(), v.detach(), hx, hv)
+    (px[:, :3].sum() + pv[:, :3].sum()).backward()
     with pytest.raises(gs.GsError) as e:
-        (px[:, :3].sum() + pv[:, :3].sum()).backward()
+        ctx.sync()
     assert e.value.code == gs.GS_ERR_STATE
+    ctx.sync()   # reported once; the context stays usable
     ctx.close()

@@ -328,7 +328,12 @@ int gs_read_async(gs_ctx* ctx, int field, void* dst, size_t bytes, int dst_is_de
 #define GS_MAX_MATERIALS 16
 int gs_set_materials(gs_ctx* ctx, int n_materials, const float* mu);
 
-/* Enable (1) or disable (0) CUDA-graph replay of gs_frame. */
+/* Enable (1) or disable (0) CUDA-graph replay of gs_frame, and of the fixed
+ * launch sequence inside gs_step_low_forward / gs_step_low_backward (between
+ * the copies of the caller's buffers; not on the legacy or per-thread
+ * default stream, which cannot be captured).  Results are the same bits
+ * (gradients up to the order of atomic accumulations, which varies from run
+ * to run either way). */
 int gs_set_graphs(gs_ctx* ctx, int enable);
 
 /* Pipelined frames (enable = 1): the HR frame of frame f is deferred and

@@ -614,6 +614,32 @@ bool capturable(const gs_ctx* c)
            c->stream != cudaStreamPerThread;
 }
 
+HostAfter host_after(const gs_ctx* c)
+{
+    HostAfter h;
+    h.hr_cur = c->hr_cur;
+    h.hr_identity = c->hr_identity;
+    h.hr_keys_valid = c->hr_keys_valid;
+    h.lr_binned = c->lr_binned;
+    h.hr_sorted_keys = c->hr_sorted_keys;
+    h.lr_sorted_keys = c->lr_sorted_keys;
+    h.lr_sorted_idx = c->lr_sorted_idx;
+    return h;
+}
+
+void apply_after(gs_ctx* c, const HostAfter& h)
+{
+    c->hr_cur = h.hr_cur;
+    c->hr_identity = h.hr_identity;
+    c->hr_keys_valid = h.hr_keys_valid;
+    c->lr_binned = h.lr_binned;
+    c->hr_sorted_keys = h.hr_sorted_keys;
+    c->lr_sorted_keys = h.lr_sorted_keys;
+    c->lr_sorted_idx = h.lr_sorted_idx;
+}
+
+// The key must hold every host-side input the sequence depends on; the
+// host-side state it leaves is recorded at capture and applied on replay.
 template <class F>
 int replay_or_run(gs_ctx* c, uint64_t key, F&& body)
 {
@@ -635,6 +661,7 @@ int replay_or_run(gs_ctx* c, uint64_t key, F&& body)
         GraphEntry g;
         g.key = key;
         g.kernels = c->launches - l0;
+        g.after = host_after(c);
         c->launches = l0;
         const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
         cudaGraphDestroy(graph);
@@ -644,6 +671,7 @@ int replay_or_run(gs_ctx* c, uint64_t key, F&& body)
     }
     CK(cudaGraphLaunch(ge->exec, c->stream), "graph launch");
     c->launches += ge->kernels;
+    apply_after(c, ge->after);
     return GS_OK;
 }
 
@@ -653,7 +681,8 @@ uint64_t step_key(const gs_ctx* c, char kind, float dt, int iters)
     std::memcpy(&db, &dt, 4);
     uint64_t k = 0xcbf29ce484222325ull;
     for (uint64_t v : {(uint64_t)kind, (uint64_t)db, (uint64_t)iters, (uint64_t)c->use_solver,
-                       (uint64_t)c->solver_selftest, (uint64_t)(c->n_materials > 0), (uint64_t)(c->n_bodies > 0)})
+                       (uint64_t)c->solver_selftest, (uint64_t)(c->n_materials > 0), (uint64_t)(c->n_bodies > 0),
+                       (uint64_t)c->hr_cur, (uint64_t)c->tune_warps, (uint64_t)c->tune_blocks_per_sm})
         k = (k ^ v) * 0x100000001b3ull;
     return k;
 }
@@ -938,7 +967,7 @@ void gs_destroy(gs_ctx* c)
                     c->hr_pos[0],  c->hr_pos[1],  c->hr_vel[0],  c->hr_vel[1],  c->hr_keys[0], c->hr_keys[1],
                     c->hr_vals[0], c->hr_vals[1], c->nbr,        c->nbr_cnt,    c->tmp4,      c->sort_hist,
                     c->d_work,     c->d_err,      c->gXs,        c->gVs,       c->snap,      c->snap_xt,
-                    c->adj_io,     c->adj_gx,     c->adj_gxt,    c->adj_h,      c->adj_gws,   c->scan_aux,   c->d_bar,
+                    c->adj_io,     c->fscratch,   c->adj_gx,     c->adj_gxt,    c->adj_h,      c->adj_gws,   c->scan_aux,   c->d_bar,
                     c->step_cell_start, c->d_sdf_pend, c->stage_in, c->lr_mat, c->d_mu, c->d_cfl, c->lr_body, c->lr_xo, c->body_members,
                     c->body_start, c->body_xf, c->lr_slot,
                     c->async_in[0], c->async_in[1], c->async_in[2], c->async_in[3],
@@ -1653,6 +1682,44 @@ int gs_autotune(gs_ctx* c, float dt, int reps, int* warps_per_block, int* blocks
     return GS_OK;
 }
 
+// The functional upsampling entries' copies of the caller's HR buffers
+// (6 x n_high) and LR gradients (2 x n_low), allocated on first use.
+static int ensure_fscratch(gs_ctx* c)
+{
+    if (c->fscratch) return GS_OK;
+    if (dalloc(&c->fscratch, (size_t)(6 * c->n_high + 2 * c->n_low)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, GS_ERR_OOM, "no memory for the functional frame's buffers");
+    }
+    return GS_OK;
+}
+
+// The HR frame on copies: HR state in from fscratch[0..2), out to
+// fscratch[2..4) (original order); the internal order is reset and sorted.
+static int upsample_fwd_seq(gs_ctx* c, float dt)
+{
+    const int64_t M = c->n_high;
+    float4* F = c->fscratch;
+    int cur = c->hr_cur;
+    CK(launch_hr_load(c, F, c->hr_pos[cur], 1), "load");
+    CK(launch_hr_load(c, F + M, c->hr_vel[cur], 0), "load");
+    c->hr_identity = true;
+    int st = resort_high_impl(c);
+    if (st) return st;
+    st = bin_low_impl(c);
+    if (st) return st;
+    cur = c->hr_cur;
+    UpsampleArgs u = upsample_args(c, dt, c->hr_pos[cur], c->hr_vel[cur], c->hr_pos[cur], c->hr_vel[cur]);
+    CK(gs_launch_upsample(c->stream, u, c->tune_warps, c->tune_blocks_per_sm, c->sm_count, &c->launches), "upsample");
+    CK(gs_launch_unpermute(c->stream, c->hr_pos[cur], c->hr_pos[cur], c->hr_scene, F + 2 * M, c->hr_slots, M,
+                           c->d_err, &c->launches),
+       "unpermute");
+    CK(gs_launch_unpermute(c->stream, c->hr_pos[cur], c->hr_vel[cur], c->hr_scene, F + 3 * M, c->hr_slots, M,
+                           c->d_err, &c->launches),
+       "unpermute");
+    return GS_OK;
+}
+
 int gs_upsample_forward(gs_ctx* c, const float* lr_pos, const float* lr_vel, const float* hr_pos_in,
                         const float* hr_vel_in, float* hr_pos_out, float* hr_vel_out, float dt)
 {
@@ -1671,25 +1738,15 @@ int gs_upsample_forward(gs_ctx* c, const float* lr_pos, const float* lr_vel, con
     }
     c->lr_binned = false;
     if (M == 0) return GS_OK;
-    int cur = c->hr_cur;
-    CK(cudaMemcpyAsync(c->tmp4, hr_pos_in, M * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
-    CK(launch_hr_load(c, c->tmp4, c->hr_pos[cur], 1), "load");
-    CK(cudaMemcpyAsync(c->tmp4, hr_vel_in, M * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
-    CK(launch_hr_load(c, c->tmp4, c->hr_vel[cur], 0), "load");
-    c->hr_identity = true;
-    st = resort_high_impl(c);
+    st = ensure_fscratch(c);
     if (st) return st;
-    st = bin_low_impl(c);
+    float4* F = c->fscratch;
+    CK(cudaMemcpyAsync(F, hr_pos_in, M * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    CK(cudaMemcpyAsync(F + M, hr_vel_in, M * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    st = replay_or_run(c, step_key(c, 'u', dt, 0), [&] { return upsample_fwd_seq(c, dt); });
     if (st) return st;
-    cur = c->hr_cur;
-    UpsampleArgs u = upsample_args(c, dt, c->hr_pos[cur], c->hr_vel[cur], c->hr_pos[cur], c->hr_vel[cur]);
-    CK(gs_launch_upsample(c->stream, u, c->tune_warps, c->tune_blocks_per_sm, c->sm_count, &c->launches), "upsample");
-    CK(gs_launch_unpermute(c->stream, c->hr_pos[cur], c->hr_pos[cur], c->hr_scene, (float4*)hr_pos_out, c->hr_slots,
-                           M, c->d_err, &c->launches),
-       "unpermute");
-    CK(gs_launch_unpermute(c->stream, c->hr_pos[cur], c->hr_vel[cur], c->hr_scene, (float4*)hr_vel_out, c->hr_slots,
-                           M, c->d_err, &c->launches),
-       "unpermute");
+    CK(cudaMemcpyAsync(hr_pos_out, F + 2 * M, M * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    CK(cudaMemcpyAsync(hr_vel_out, F + 3 * M, M * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
     return GS_OK;
 }
 
@@ -1703,6 +1760,29 @@ static int flag_solid(gs_ctx* c, const float* pos, int64_t n)
                                                             GS_DEVERR_SOLID_REVERSE);
     c->launches += 1;
     CK(cudaGetLastError(), "flag");
+    return GS_OK;
+}
+
+// The reverse HR frame on copies: HR state and dL/d outputs in from
+// fscratch[0..4), dL/d HR inputs out to fscratch[4..6), dL/d LR inputs out
+// to the two n_low blocks after them (original order).
+static int upsample_bwd_seq(gs_ctx* c, float dt)
+{
+    const int64_t N = c->n_low, M = c->n_high;
+    float4* F = c->fscratch;
+    float4* G = F + 6 * M;
+    int st = flag_solid(c, (const float*)c->lr_pos, N);
+    if (st) return st;
+    if (N) {
+        CK(cudaMemsetAsync(c->gXs, 0, N * sizeof(float4), c->stream), "clear");
+        CK(cudaMemsetAsync(c->gVs, 0, N * sizeof(float4), c->stream), "clear");
+    }
+    st = bin_low_impl(c);
+    if (st) return st;
+    CK(gs_launch_upsample_bwd(c->stream, c->d_scenes, c->d_sdf, c->lr_spos, c->lr_svel, c->lr_cell_start, F, F + M,
+                              F + 2 * M, F + 3 * M, F + 4 * M, F + 5 * M, c->gXs, c->gVs, M, dt, &c->launches),
+       "upsample backward");
+    CK(gs_launch_scatter2(c->stream, c->lr_sorted_idx, c->gXs, c->gVs, G, G + N, N, &c->launches), "scatter");
     return GS_OK;
 }
 
@@ -1721,24 +1801,29 @@ int gs_upsample_backward(gs_ctx* c, const float* lr_pos, const float* lr_vel, co
         (M > 0 && (!hr_pos_in || !hr_vel_in || !g_hr_pos_out || !g_hr_vel_out || !g_hr_pos_in || !g_hr_vel_in)))
         return fail(c, GS_ERR_ARG, "null buffer");
     if (c->n_bodies > 0) return fail(c, GS_ERR_STATE, "the reverse modes do not support rigid bodies");
-    st = flag_solid(c, lr_pos, N);
+    st = ensure_fscratch(c);
     if (st) return st;
+    float4* F = c->fscratch;
+    float4* G = F + 6 * M;
     if (N) {
         CK(cudaMemcpyAsync(c->lr_pos, lr_pos, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
         CK(cudaMemcpyAsync(c->lr_vel, lr_vel, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
-        CK(cudaMemsetAsync(c->gXs, 0, N * sizeof(float4), c->stream), "clear");
-        CK(cudaMemsetAsync(c->gVs, 0, N * sizeof(float4), c->stream), "clear");
     }
-    st = bin_low_impl(c);
+    if (M) {
+        const void* in[4] = {hr_pos_in, hr_vel_in, g_hr_pos_out, g_hr_vel_out};
+        for (int k = 0; k < 4; ++k)
+            CK(cudaMemcpyAsync(F + k * M, in[k], M * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    }
+    st = replay_or_run(c, step_key(c, 'v', dt, 0), [&] { return upsample_bwd_seq(c, dt); });
     if (st) return st;
-    CK(gs_launch_upsample_bwd(c->stream, c->d_scenes, c->d_sdf, c->lr_spos, c->lr_svel, c->lr_cell_start,
-                              (const float4*)hr_pos_in, (const float4*)hr_vel_in, (const float4*)g_hr_pos_out,
-                              (const float4*)g_hr_vel_out, (float4*)g_hr_pos_in, (float4*)g_hr_vel_in, c->gXs, c->gVs,
-                              M, dt, &c->launches),
-       "upsample backward");
-    CK(gs_launch_scatter2(c->stream, c->lr_sorted_idx, c->gXs, c->gVs, (float4*)g_lr_pos, (float4*)g_lr_vel, N,
-                          &c->launches),
-       "scatter");
+    if (M) {
+        CK(cudaMemcpyAsync(g_hr_pos_in, F + 4 * M, M * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+        CK(cudaMemcpyAsync(g_hr_vel_in, F + 5 * M, M * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    }
+    if (N) {
+        CK(cudaMemcpyAsync(g_lr_pos, G, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+        CK(cudaMemcpyAsync(g_lr_vel, G + N, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    }
     return GS_OK;
 }
 

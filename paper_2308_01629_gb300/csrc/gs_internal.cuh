@@ -55,11 +55,22 @@ enum : int {
 // HR slot tag: scene index, with this bit set on padding slots.
 constexpr uint32_t kPadBit = 0x80000000u;
 
+// Host-side bookkeeping a captured sequence leaves behind (applied again on
+// every replay of the functional entry points' graphs).
+struct HostAfter {
+    int hr_cur = 0;
+    bool hr_identity = true, hr_keys_valid = false, lr_binned = false;
+    uint32_t* hr_sorted_keys = nullptr;
+    uint32_t* lr_sorted_keys = nullptr;
+    uint32_t* lr_sorted_idx = nullptr;
+};
+
 struct GraphEntry {
     uint64_t key = 0;
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;    // kernel launches the graph replays
     cudaGraph_t graph = nullptr;   // kept with the exec when it holds a conditional node
+    HostAfter after;        // functional entry points: the state after the sequence
 };
 
 // Device state of an adaptive frame's LR substeps (gs_frame_adaptive).
@@ -182,6 +193,7 @@ struct gs_ctx {
     float4* adj_h = nullptr;
     float* adj_gws = nullptr;
     float4* adj_io = nullptr;      // [4][n_low]: dL/dx_out, dL/dv_out in; dL/dx_in, dL/dv_in out (original order)
+    float4* fscratch = nullptr;    // [6][n_high] + [2][n_low]: the functional upsampling entries' in/out copies
     std::vector<GraphEntry> fgraphs;   // graphs of the functional LR step entry points
 
     // radix sort histogram scratch (HR reorder, static-scratch binning)

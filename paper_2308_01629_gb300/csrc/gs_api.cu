@@ -156,6 +156,45 @@ __global__ void k_flag_solid(const float4* __restrict__ pos, int64_t n, int* err
     if (i < n && pos[i].w == 0.0f) atomicOr(err, bit);
 }
 
+// Asynchronous writes of both fields of a kind, checked on the way: a copy
+// of LR position and velocity, and the load of HR position and velocity into
+// the identity slot order (ids into the w of the position); a non-finite
+// x, y, z sets `bit` in *err.
+__global__ void k_copy2_checked(const float4* __restrict__ a, const float4* __restrict__ b, float4* __restrict__ oa,
+                                float4* __restrict__ ob, int64_t n, int* err, int bit)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 u = a[i], v = b[i];
+    if (!(isfinite(u.x) && isfinite(u.y) && isfinite(u.z) && isfinite(v.x) && isfinite(v.y) && isfinite(v.z)))
+        atomicOr(err, bit);
+    oa[i] = u;
+    ob[i] = v;
+}
+
+__global__ void k_hr_load2_checked(const float4* __restrict__ sp, const float4* __restrict__ sv,
+                                   float4* __restrict__ dp, float4* __restrict__ dv, const uint32_t* __restrict__ tag,
+                                   const SceneDev* __restrict__ scenes, int64_t n_slots, int* err, int bit)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_slots) return;
+    const uint32_t t = tag[p];
+    if (t & kPadBit) {
+        dp[p] = make_float4(0.f, 0.f, 0.f, __uint_as_float(0xffffffffu));
+        dv[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const SceneDev& sc = scenes[t];
+    const int64_t id = sc.hr_real_begin + (p - sc.hr_begin);
+    float4 u = sp[id];
+    const float4 v = sv[id];
+    if (!(isfinite(u.x) && isfinite(u.y) && isfinite(u.z) && isfinite(v.x) && isfinite(v.y) && isfinite(v.z)))
+        atomicOr(err, bit);
+    u.w = __uint_as_float((uint32_t)id);
+    dp[p] = u;
+    dv[p] = v;
+}
+
 cudaError_t launch_hr_load(gs_ctx* c, const float4* src, float4* dst, int set_ids)
 {
     if (c->hr_slots <= 0) return cudaSuccess;
@@ -876,6 +915,32 @@ int apply_field(gs_ctx* c, int field, const float4* dsrc, size_t bytes)
 // reported by the next gs_sync or gs_read) and then applied.
 int commit_async_writes(gs_ctx* c)
 {
+    // both fields of a kind staged (the usual round trip): one checked copy
+    // or load for the pair
+    for (int f = 0; f < 4; f += 2) {
+        if (!(c->in_pending[f] && c->in_pending[f + 1])) continue;
+        c->in_pending[f] = c->in_pending[f + 1] = false;
+        CK(cudaStreamWaitEvent(c->stream, c->ev_in_ready[f], 0), "wait for a staged field");
+        CK(cudaStreamWaitEvent(c->stream, c->ev_in_ready[f + 1], 0), "wait for a staged field");
+        if (f == 0 && c->n_low > 0) {
+            k_copy2_checked<<<gs_blocks(c->n_low, 256), 256, 0, c->stream>>>(
+                c->async_in[0], c->async_in[1], c->lr_pos, c->lr_vel, c->n_low, c->d_err, GS_DEVERR_NONFINITE_ASYNC);
+            c->launches += 1;
+            CK(cudaGetLastError(), "apply");
+            c->lr_binned = false;
+        } else if (f == 2 && c->hr_slots > 0) {
+            const int cur = c->hr_cur;
+            k_hr_load2_checked<<<gs_blocks(c->hr_slots, 256), 256, 0, c->stream>>>(
+                c->async_in[2], c->async_in[3], c->hr_pos[cur], c->hr_vel[cur], c->hr_scene, c->d_scenes, c->hr_slots,
+                c->d_err, GS_DEVERR_NONFINITE_ASYNC);
+            c->launches += 1;
+            CK(cudaGetLastError(), "apply");
+            c->hr_identity = true;
+            c->hr_keys_valid = false;
+        }
+        CK(cudaEventRecord(c->ev_in_free[f], c->stream), "record");
+        CK(cudaEventRecord(c->ev_in_free[f + 1], c->stream), "record");
+    }
     for (int f = 0; f < 4; ++f) {
         if (!c->in_pending[f]) continue;
         c->in_pending[f] = false;

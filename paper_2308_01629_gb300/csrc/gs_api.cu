@@ -432,6 +432,13 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
     A(dalloc(&c->stage_in, std::max(N, MR)));
     c->sort_hist_cap = std::max(gs_sort_hist_words(N), gs_sort_hist_words(MS));
     A(dalloc(&c->sort_hist, c->sort_hist_cap));
+    c->hr_bins = cells * 8;
+    c->hr_counting = MS > 0 && c->hr_bins <= std::max<int64_t>(8 * MS, (int64_t)1 << 20);
+    if (c->hr_counting) {
+        A(dalloc(&c->hr_bin_start, c->hr_bins + 2));
+        A(dalloc(&c->hr_big, MS / 33 + 1));
+        A(dalloc(&c->hr_scan_aux, gs_scan_aux_words(c->hr_bins + 1)));
+    }
     A(dalloc(&c->d_work, 1));
     A(dalloc(&c->d_err, 2));   // [0] device error bits, [1] scratch word of the host checks
     A(dalloc(&c->d_bar, 2));
@@ -477,18 +484,41 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
     return GS_OK;
 }
 
+// The key buffer that holds the sorted HR keys after a reorder.
+uint32_t* hr_sorted_after_resort(const gs_ctx* c)
+{
+    return c->hr_counting ? c->hr_keys[1] : c->hr_keys[((c->hr_key_bits + 7) / 8) & 1];   // where the radix passes end
+}
+
 int resort_high_impl(gs_ctx* c)
 {
     const int64_t MS = c->hr_slots;
     if (MS == 0) return GS_OK;
     Timed t(c, GS_TIMER_RESORT);
     const int cur = c->hr_cur;
-    CK(gs_launch_scene_keys(c->stream, c->hr_pos[cur], MS, c->d_scenes, c->hr_scene, 1, c->hr_keys[0],
-                            c->hr_vals[0], &c->launches),
-       "keys");
     int which = 0;
-    CK(gs_radix_sort(c->stream, c->hr_keys, c->hr_vals, &which, c->sort_hist, MS, c->hr_key_bits, &c->launches),
-       "radix sort");
+    if (c->hr_counting) {
+        CK(gs_cs_clear(c->stream, c->hr_bin_start, c->hr_bins, 1), "clear counts");
+        CK(gs_launch_scene_keys(c->stream, c->hr_pos[cur], MS, c->d_scenes, c->hr_scene, 1, c->hr_keys[0],
+                                c->hr_vals[0], &c->launches, c->hr_bin_start),
+           "keys");
+        CsExtras ex;
+        ex.big_list = c->hr_big;
+        ex.big_count = c->hr_bin_start + c->hr_bins + 1;
+        ex.big_scratch = c->hr_vals[0];   // the ranks are dead once scattered
+        ex.big_bits = gs_key_bits(MS);
+        ex.big_blocks = std::max(c->sm_count, 1);
+        CK(gs_cs_finish(c->stream, MS, c->hr_bins, c->hr_keys[0], c->hr_vals[0], c->hr_keys[1], c->hr_vals[1],
+                        c->hr_bin_start, c->hr_scan_aux, nullptr, nullptr, nullptr, nullptr, &c->launches, ex),
+           "counting sort");
+        which = 1;
+    } else {
+        CK(gs_launch_scene_keys(c->stream, c->hr_pos[cur], MS, c->d_scenes, c->hr_scene, 1, c->hr_keys[0],
+                                c->hr_vals[0], &c->launches),
+           "keys");
+        CK(gs_radix_sort(c->stream, c->hr_keys, c->hr_vals, &which, c->sort_hist, MS, c->hr_key_bits, &c->launches),
+           "radix sort");
+    }
     CK(gs_launch_gather2(c->stream, c->hr_vals[which], c->hr_pos[cur], c->hr_vel[cur], c->hr_pos[cur ^ 1],
                          c->hr_vel[cur ^ 1], MS, &c->launches),
        "permute");
@@ -856,7 +886,7 @@ int frame_pipelined_graph(gs_ctx* c, float dt, int n_sub, int iters)
     c->launches += ge->kernels;
     // host-side state as if the frame had been enqueued directly
     if (had && c->pend_resort) {
-        c->hr_sorted_keys = c->hr_keys[((c->hr_key_bits + 7) / 8) & 1];   // where the radix passes end
+        c->hr_sorted_keys = hr_sorted_after_resort(c);
         c->hr_cur ^= 1;
         c->hr_identity = false;
         c->hr_keys_valid = true;
@@ -1034,7 +1064,7 @@ void gs_destroy(gs_ctx* c)
                     c->d_work,     c->d_err,      c->gXs,        c->gVs,       c->snap,      c->snap_xt,
                     c->adj_io,     c->fscratch,   c->adj_gx,     c->adj_gxt,    c->adj_h,      c->adj_gws,   c->scan_aux,   c->d_bar,
                     c->step_cell_start, c->d_sdf_pend, c->stage_in, c->lr_mat, c->d_mu, c->d_cfl, c->lr_body, c->lr_xo, c->body_members,
-                    c->body_start, c->body_xf, c->lr_slot,
+                    c->body_start, c->body_xf, c->lr_slot, c->hr_bin_start, c->hr_big, c->hr_scan_aux,
                     c->async_in[0], c->async_in[1], c->async_in[2], c->async_in[3],
                     c->async_out[0], c->async_out[1], c->async_out[2], c->async_out[3]};
     for (void* b : bufs)

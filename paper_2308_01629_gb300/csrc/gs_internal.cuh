@@ -168,6 +168,15 @@ struct gs_ctx {
     uint32_t* hr_vals[2] = {nullptr, nullptr};
     uint32_t* hr_sorted_keys = nullptr;
     bool hr_keys_valid = false;
+    // HR reorder by counting sort over the fine cells (hr_bins = 8 x cells
+    // keys), chosen when that key space is not much larger than the HR set;
+    // otherwise the radix sort.  hr_bin_start: counts, then cell starts
+    // (hr_bins + 1 words) and the count of listed big cells; hr_big: the list.
+    bool hr_counting = false;
+    int64_t hr_bins = 0;
+    uint32_t* hr_bin_start = nullptr;
+    uint32_t* hr_big = nullptr;
+    uint32_t* hr_scan_aux = nullptr;
     float4* tmp4 = nullptr;                       // staging for reads / writes
     float4* stage_in = nullptr;                   // host data written in, checked on the device
     // asynchronous field I/O (LR_POS, LR_VEL, HR_POS, HR_VEL): host -> device
@@ -266,6 +275,17 @@ struct CsExtras {
     const uint32_t* gb_w = nullptr;       // the w of gb's copies is gb_w[particle] (as bits)
     const uint32_t* ga_solid = nullptr;   // nonzero: the w of ga's copy is 0
     uint32_t* slot_of = nullptr;          // slot_of[particle] = its slot
+    // Cells of more than 32 entries (big_list not null; only without copies):
+    // listed in big_list (capacity n / 33 + 1, count in *big_count, zero on
+    // entry) and ordered afterwards by big_blocks cooperating blocks, each
+    // cell by LSD passes over its item indices (< 2^big_bits) through
+    // big_scratch (n words; its cells' ranges are overwritten).  Without a
+    // list such cells are ordered by one thread each (insertion sort).
+    uint32_t* big_list = nullptr;
+    uint32_t* big_count = nullptr;
+    uint32_t* big_scratch = nullptr;
+    int big_bits = 32;
+    int big_blocks = 0;
 };
 // ga and gb are copied into cell order: x_out[slot] = x[particle of the
 // slot], with the extras above.
@@ -277,8 +297,11 @@ cudaError_t gs_count_sort_cells(cudaStream_t s, const float4* pos, int64_t n, co
                                 const uint32_t* tag, int64_t n_cell, uint32_t* keys, uint32_t* rank,
                                 uint32_t* out_keys, uint32_t* out_idx, uint32_t* cell_start, uint32_t* aux,
                                 int64_t* launches);
+// vals[i] = i, or with count not null the arrival rank of slot i in its
+// key's counter (count[key] += 1), for a counting sort by key.
 cudaError_t gs_launch_scene_keys(cudaStream_t s, const float4* pos, int64_t n, const SceneDev* scenes,
-                                 const uint32_t* tag, int fine, uint32_t* keys, uint32_t* vals, int64_t* launches);
+                                 const uint32_t* tag, int fine, uint32_t* keys, uint32_t* vals, int64_t* launches,
+                                 uint32_t* count = nullptr);
 cudaError_t gs_launch_cell_start(cudaStream_t s, const uint32_t* sorted_keys, int64_t n, int64_t n_cell,
                                  uint32_t* start, int64_t* launches);
 cudaError_t gs_launch_gather2(cudaStream_t s, const uint32_t* idx, const float4* a, const float4* b, float4* a_out,

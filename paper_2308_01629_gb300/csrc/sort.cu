@@ -1,11 +1,18 @@
-// sort.cu -- uniform-grid binning by stable LSD radix sort on cell keys.
+// sort.cu -- uniform-grid binning: stable sorts of particles by cell key.
 //
 // Neighbour search (the paper uses compact hashing, Sec. 5.1) is replaced by
 // a dense grid whose cell ids follow a fixed float32 quantization contract
 // (gs.h), so that cell ids, counts and the sorted order are bit-exact
-// reproducible.  Sorting is stable by (key, index): each 8-bit pass ranks
-// equal digits in index order within a tile (warp match + per-warp counts),
-// and tiles are laid out in order by an exclusive scan over (digit, tile).
+// reproducible.  Every sort here is stable by (key, index), so the two
+// methods below give the same order:
+//  - counting sort (LR cells; HR fine cells when the key space is not much
+//    larger than the HR set): atomic counts per key, an exclusive scan into
+//    cell starts, a scatter by arrival rank, then each cell's entries put in
+//    index order;
+//  - LSD radix sort (HR fine cells in sparse grids, the static-scratch
+//    binning): each 8-bit pass ranks equal digits in index order within a
+//    tile (warp match + per-warp counts), and tiles are laid out in order by
+//    an exclusive scan over (digit, tile).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -169,31 +176,49 @@ __global__ void k_cell_keys(const float4* __restrict__ pos, int64_t n, GridDev g
     vals[i] = (uint32_t)i;
 }
 
+__device__ __forceinline__ uint32_t scene_key(const float4* __restrict__ pos, int64_t i,
+                                              const SceneDev* __restrict__ scenes, const uint32_t* __restrict__ tag,
+                                              int fine)
+{
+    const uint32_t t = tag[i];
+    const SceneDev& sc = scenes[t & ~kPadBit];
+    if (t & kPadBit) return fine ? (sc.cell_off + sc.n_cell) * 8u : sc.cell_off + sc.n_cell;
+    const GridDev& g = sc.g;
+    float4 p = pos[i];
+    int sx = grid_sub_coord(p.x, g.ox, g.inv_h, g.dx);
+    int sy = grid_sub_coord(p.y, g.oy, g.inv_h, g.dy);
+    int sz = grid_sub_coord(p.z, g.oz, g.inv_h, g.dz);
+    uint32_t cell = sc.cell_off +
+                    ((uint32_t)(sz >> 1) * (uint32_t)g.dy + (uint32_t)(sy >> 1)) * (uint32_t)g.dx + (uint32_t)(sx >> 1);
+    return fine ? cell * 8u + (uint32_t)((sz & 1) * 4 + (sy & 1) * 2 + (sx & 1)) : cell;
+}
+
 // Global key of a slot that belongs to scene tag & ~kPadBit: the scene's
 // cell offset plus its cell id (times 8 plus the octant when fine); padding
 // slots take the scene's padding cell so they sort to the end of its range.
 __global__ void k_scene_keys(const float4* __restrict__ pos, int64_t n, const SceneDev* __restrict__ scenes,
                              const uint32_t* __restrict__ tag, int fine, uint32_t* __restrict__ keys,
-                             uint32_t* __restrict__ vals)
+                             uint32_t* __restrict__ vals, uint32_t* __restrict__ count)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t t = tag[i];
-    const SceneDev& sc = scenes[t & ~kPadBit];
-    uint32_t key;
-    if (t & kPadBit) {
-        key = fine ? (sc.cell_off + sc.n_cell) * 8u : sc.cell_off + sc.n_cell;
-    } else {
-        const GridDev& g = sc.g;
-        float4 p = pos[i];
-        int sx = grid_sub_coord(p.x, g.ox, g.inv_h, g.dx);
-        int sy = grid_sub_coord(p.y, g.oy, g.inv_h, g.dy);
-        int sz = grid_sub_coord(p.z, g.oz, g.inv_h, g.dz);
-        uint32_t cell = sc.cell_off +
-                        ((uint32_t)(sz >> 1) * (uint32_t)g.dy + (uint32_t)(sy >> 1)) * (uint32_t)g.dx + (uint32_t)(sx >> 1);
-        key = fine ? cell * 8u + (uint32_t)((sz & 1) * 4 + (sy & 1) * 2 + (sx & 1)) : cell;
+    if (count) {
+        // counting sort: the lanes of a warp that share a key take
+        // consecutive ranks from one atomic (a reordered set arrives sorted)
+        const bool ok = i < n;
+        const uint32_t key = ok ? scene_key(pos, i, scenes, tag, fine) : 0xffffffffu;   // above every key
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (ok && lane == leader) base = atomicAdd(count + key, (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (ok) {
+            keys[i] = key;
+            vals[i] = base + __popc(peers & ((1u << lane) - 1u));
+        }
+        return;
     }
-    keys[i] = key;
+    if (i >= n) return;
+    keys[i] = scene_key(pos, i, scenes, tag, fine);
     vals[i] = (uint32_t)i;
 }
 
@@ -322,9 +347,10 @@ __global__ void k_cs_scatter(const uint32_t* __restrict__ keys, const uint32_t* 
 }
 
 // every cell's entries in ascending item order.  A cell holds a handful of
-// LR particles: its entries are loaded at once into registers (padded with
-// the largest key) and ordered by a fixed compare-exchange network; larger
-// cells fall back to an insertion sort in place.
+// LR particles (HR fine cells a few dozen): its entries are loaded at once
+// into registers (padded with the largest key) and ordered by a fixed
+// compare-exchange network; larger cells are listed for k_cs_order_big, or
+// without a list fall back to an insertion sort in place.
 template <int K>
 __device__ __forceinline__ void order_small(uint32_t* __restrict__ idx, uint32_t b, uint32_t n)
 {
@@ -338,6 +364,36 @@ __device__ __forceinline__ void order_small(uint32_t* __restrict__ idx, uint32_t
             const uint32_t lo = min(v[j], v[j + 1]), hi = max(v[j], v[j + 1]);
             v[j] = lo;
             v[j + 1] = hi;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        if ((uint32_t)k < n) idx[b + k] = v[k];
+}
+
+// 32 entries: Batcher's odd-even merge sort network (191 compare-exchanges
+// against 496 for the transposition network above).
+__device__ __forceinline__ void order_32(uint32_t* __restrict__ idx, uint32_t b, uint32_t n)
+{
+    constexpr int K = 32;
+    uint32_t v[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = (uint32_t)k < n ? idx[b + k] : 0xffffffffu;
+    // stage (p, k): entry i meets i + k when i lies in the lower half of its
+    // 2k-block counted from k mod p and both lie in the same 2p-block
+#pragma unroll
+    for (int p = 1; p < K; p <<= 1) {
+#pragma unroll
+        for (int k = p; k >= 1; k >>= 1) {
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const int j0 = k % p;
+                if (i >= j0 && ((i - j0) / k) % 2 == 0 && i + k < K && i / (2 * p) == (i + k) / (2 * p)) {
+                    const uint32_t lo = min(v[i], v[i + k]), hi = max(v[i], v[i + k]);
+                    v[i] = lo;
+                    v[i + k] = hi;
+                }
+            }
         }
     }
 #pragma unroll
@@ -361,6 +417,11 @@ __global__ void k_cs_order(const uint32_t* __restrict__ start, int64_t n_cell, u
         order_small<8>(idx, b, n);
     } else if (n <= 16) {
         order_small<16>(idx, b, n);
+    } else if (n <= 32) {
+        order_32(idx, b, n);
+    } else if (ex.big_list) {
+        ex.big_list[atomicAdd(ex.big_count, 1u)] = (uint32_t)c;   // ordered by k_cs_order_big
+        return;
     } else {
         for (uint32_t j = b + 1; j < e; ++j) {
             const uint32_t v = idx[j];
@@ -388,6 +449,122 @@ __global__ void k_cs_order(const uint32_t* __restrict__ start, int64_t n_cell, u
     }
     if (ex.slot_of)
         for (uint32_t j = b; j < e; ++j) ex.slot_of[idx[j]] = j;
+}
+
+// One warp orders a cell of up to 32 R distinct entries: lane l holds
+// entries l, l + 32, ... (coalesced), every entry's place is the number of
+// entries below it, counted against all of them broadcast by shuffles.
+template <int R>
+__device__ __forceinline__ void order_warp(uint32_t* __restrict__ idx, uint32_t b, uint32_t n, int lane)
+{
+    uint32_t v[R], rk[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const uint32_t t = (uint32_t)(r * 32 + lane);
+        v[r] = t < n ? idx[b + t] : 0xffffffffu;   // above every entry: never counted
+        rk[r] = 0;
+    }
+#pragma unroll
+    for (int r2 = 0; r2 < R; ++r2) {
+        if ((uint32_t)(r2 * 32) >= n) break;   // warp-uniform
+#pragma unroll
+        for (int s = 0; s < 32; ++s) {
+            const uint32_t u = __shfl_sync(0xffffffffu, v[r2], s);
+#pragma unroll
+            for (int r = 0; r < R; ++r) rk[r] += u < v[r] ? 1u : 0u;
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if ((uint32_t)(r * 32 + lane) < n) idx[b + rk[r]] = v[r];
+}
+
+// Cells of more than 32 entries, listed by k_cs_order.  Cells of up to 256
+// entries are ordered by one warp each (order_warp).  Larger ones, one block
+// each, by stable 8-bit LSD passes over the cell's item indices (the tile
+// ranking of k_rs_scatter over the cell's range, tiles in order),
+// ping-ponging between idx and scratch over the same range: work linear in
+// the cell's size per pass, so a degenerate cell (every particle at one
+// point) costs a few passes over the set, not a quadratic sort.
+__global__ void __launch_bounds__(kThreads) k_cs_order_big(const uint32_t* __restrict__ start,
+                                                           const uint32_t* __restrict__ list,
+                                                           const uint32_t* __restrict__ count,
+                                                           uint32_t* __restrict__ idx, uint32_t* __restrict__ scratch,
+                                                           int bits)
+{
+    __shared__ uint32_t run[kBins];
+    __shared__ uint32_t wcnt[kWarps][kBins];
+    __shared__ uint32_t wsum[kWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t n_big = *count;
+    const uint32_t n_warps = gridDim.x * kWarps;
+    for (uint32_t q = blockIdx.x * kWarps + warp; q < n_big; q += n_warps) {
+        const uint32_t cell = list[q];
+        const uint32_t b = start[cell], n = start[cell + 1] - b;
+        if (n <= 64) order_warp<2>(idx, b, n, lane);
+        else if (n <= 256) order_warp<8>(idx, b, n, lane);
+    }
+    for (uint32_t q = blockIdx.x; q < n_big; q += gridDim.x) {
+        const uint32_t cell = list[q];
+        const uint32_t b = start[cell], n = start[cell + 1] - b;
+        if (n <= 256) continue;   // the same cell for the whole block: uniform
+        uint32_t* src = idx + b;
+        uint32_t* dst = scratch + b;
+        for (int shift = 0; shift < bits; shift += 8) {
+            run[tid] = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0;
+            __syncthreads();
+            for (uint32_t t = tid; t < n; t += kThreads) atomicAdd(&run[(src[t] >> shift) & (kBins - 1)], 1u);
+            __syncthreads();
+            // exclusive scan of the 256 digit counts, one per thread
+            const uint32_t h = run[tid];
+            uint32_t inc = h;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane == 31) wsum[warp] = inc;
+            __syncthreads();
+            uint32_t before = 0;
+            for (int w = 0; w < warp; ++w) before += wsum[w];
+            run[tid] = before + inc - h;
+            __syncthreads();
+            for (uint32_t base = 0; base < n; base += kThreads) {
+                const uint32_t t = base + tid;
+                const bool valid = t < n;
+                const uint32_t v = valid ? src[t] : 0u;
+                const uint32_t d = valid ? ((v >> shift) & (kBins - 1)) : (uint32_t)kBins;
+                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                const unsigned rank = __popc(peers & lt);
+                if (valid && rank == 0) wcnt[warp][d] = __popc(peers);
+                __syncthreads();
+                if (valid) {
+                    uint32_t pos = run[d] + rank;
+                    for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
+                    dst[pos] = v;
+                }
+                __syncthreads();
+                uint32_t tot = 0;
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w) {
+                    tot += wcnt[w][tid];
+                    wcnt[w][tid] = 0;
+                }
+                run[tid] += tot;
+                __syncthreads();
+            }
+            uint32_t* t = src;
+            src = dst;
+            dst = t;
+        }
+        if (src != idx + b)
+            for (uint32_t t = tid; t < n; t += kThreads) idx[b + t] = src[t];
+        __syncthreads();
+    }
 }
 
 __global__ void k_cell_start(const uint32_t* __restrict__ sk, int64_t n, int64_t n_cell, uint32_t* __restrict__ start)
@@ -512,9 +689,16 @@ cudaError_t gs_cs_finish(cudaStream_t s, int64_t n, int64_t n_cell, const uint32
     k_scan_apply<<<(unsigned)nt, kScanBlock, 0, s>>>(cell_start, total, aux);
     *launches += 3;
     if (n > 0) {
+        if (ex.big_list && (ga || ex.slot_of || ex.big_blocks <= 0 || !ex.big_count || !ex.big_scratch))
+            return cudaErrorInvalidValue;   // listed cells are ordered without copies
         k_cs_scatter<<<gs_blocks(n, 256), 256, 0, s>>>(keys, rank, n, cell_start, out_keys, out_idx);
         k_cs_order<<<gs_blocks(n_cell, 256), 256, 0, s>>>(cell_start, n_cell, out_idx, ga, gb, ga_out, gb_out, ex);
         *launches += 2;
+        if (ex.big_list) {
+            k_cs_order_big<<<(unsigned)ex.big_blocks, kThreads, 0, s>>>(cell_start, ex.big_list, ex.big_count, out_idx,
+                                                                       ex.big_scratch, ex.big_bits);
+            *launches += 1;
+        }
     }
     return cudaGetLastError();
 }
@@ -581,10 +765,11 @@ cudaError_t gs_launch_permute_in(cudaStream_t s, const float4* pos_internal, con
 }
 
 cudaError_t gs_launch_scene_keys(cudaStream_t s, const float4* pos, int64_t n, const SceneDev* scenes,
-                                 const uint32_t* tag, int fine, uint32_t* keys, uint32_t* vals, int64_t* launches)
+                                 const uint32_t* tag, int fine, uint32_t* keys, uint32_t* vals, int64_t* launches,
+                                 uint32_t* count)
 {
     if (n <= 0) return cudaSuccess;
-    k_scene_keys<<<gs_blocks(n, 256), 256, 0, s>>>(pos, n, scenes, tag, fine, keys, vals);
+    k_scene_keys<<<gs_blocks(n, 256), 256, 0, s>>>(pos, n, scenes, tag, fine, keys, vals, count);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -80,6 +80,46 @@ def test_hr_reorder_bit_exact_and_roundtrip(orc, make):
     sc = make()
     if make is scenes.cube:
         sc = scenes.stir(sc, seed=3)
+    _check_hr_reorder(orc, sc)
+
+
+def _wide_box(sc):
+    """The cube in a 5 m box: 8 x cells fine keys far outnumber the HR set,
+    so the reorder takes the radix sort instead of the counting sort."""
+    sc = dict(sc)
+    sc["box_lo"] = [-2.0, -2.0, -2.0]
+    sc["box_hi"] = [3.0, 3.0, 3.0]
+    return sc
+
+
+def _clumped(sc):
+    """HR particles piled on points: one fine cell of more than 3000 entries
+    (a block's LSD passes over many tiles), 40 of 50 or more and 10 of 150
+    or more (one warp each, the two register widths)."""
+    sc = dict(sc)
+    hr = sc["hr_pos"].copy()
+    pts = np.random.default_rng(7).uniform(0.15, 0.35, size=(50, 3)).astype(np.float32)
+    hr[:3000, :3] = np.float32([0.25, 0.25, 0.3])
+    hr[3000:5000, :3] = np.repeat(pts[:40], 50, axis=0)
+    hr[5000:6500, :3] = np.repeat(pts[40:], 150, axis=0)
+    sc["hr_pos"] = hr
+    return sc
+
+
+@pytest.mark.parametrize("case", ["wide_box", "clumped", "clumped_wide_box", "clumped_three_passes"])
+def test_hr_reorder_bit_exact_sort_paths_and_big_cells(orc, case):
+    # 74,088 HR slots need 17 index bits: three 8-bit passes, the last one
+    # ending in the scratch range (copied back); 8,000 slots need two
+    n_side = 21 if case == "clumped_three_passes" else 10
+    sc = scenes.stir(scenes.cube(n_side=n_side), seed=5)
+    if "clumped" in case:
+        sc = _clumped(sc)
+    if "wide" in case:
+        sc = _wide_box(sc)
+    _check_hr_reorder(orc, sc)
+
+
+def _check_hr_reorder(orc, sc):
     gs, ctx = _ctx(sc)
     ctx.resort_high()
     m = len(sc["hr_pos"])

@@ -313,19 +313,30 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_sums(uint32_t* __restrict__
 }
 
 // exclusive scan of every tile plus its tile offset, in place
+// raw_sums: tile_sums holds each tile's own total (k_scan_sums skipped) and
+// every block adds up the totals of the tiles before it (few tiles).
 __global__ void __launch_bounds__(kScanBlock) k_scan_apply(uint32_t* __restrict__ data, int64_t total,
-                                                           const uint32_t* __restrict__ tile_sums)
+                                                           const uint32_t* __restrict__ tile_sums, int raw_sums)
 {
     __shared__ uint32_t ws[32];
+    uint32_t tot;
+    uint32_t base;
+    if (raw_sums) {
+        uint32_t part = 0;
+        for (int64_t t = threadIdx.x; t < (int64_t)blockIdx.x; t += kScanBlock) part += tile_sums[t];
+        block_scan(part, ws, &tot);
+        base = tot;
+    } else {
+        base = tile_sums[blockIdx.x];
+    }
     const int64_t i0 = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
     uint32_t v[kScanPer];
     load_tile(data, total, i0, v);
     uint32_t s = 0;
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) s += v[k];
-    uint32_t tot;
     const uint32_t inc = block_scan(s, ws, &tot);
-    uint32_t run = tile_sums[blockIdx.x] + inc - s;
+    uint32_t run = base + inc - s;
 #pragma unroll
     for (int k = 0; k < kScanPer; ++k) {
         const uint32_t t = v[k];
@@ -684,10 +695,13 @@ cudaError_t gs_cs_finish(cudaStream_t s, int64_t n, int64_t n_cell, const uint32
 {
     const int64_t total = n_cell + 1;
     const int64_t nt = (total + kScanTile - 1) / kScanTile;
+    // up to kScanBlock tiles the apply blocks add up the tile totals before
+    // them themselves (at most one word per thread), saving the tile-sum scan
+    const int raw = nt <= kScanBlock;
     k_scan_tiles<<<(unsigned)nt, kScanBlock, 0, s>>>(cell_start, total, aux);
-    k_scan_sums<<<1, kScanBlock, 0, s>>>(aux, nt);
-    k_scan_apply<<<(unsigned)nt, kScanBlock, 0, s>>>(cell_start, total, aux);
-    *launches += 3;
+    if (!raw) k_scan_sums<<<1, kScanBlock, 0, s>>>(aux, nt);
+    k_scan_apply<<<(unsigned)nt, kScanBlock, 0, s>>>(cell_start, total, aux, raw);
+    *launches += raw ? 2 : 3;
     if (n > 0) {
         if (ex.big_list && (ga || ex.slot_of || ex.big_blocks <= 0 || !ex.big_count || !ex.big_scratch))
             return cudaErrorInvalidValue;   // listed cells are ordered without copies

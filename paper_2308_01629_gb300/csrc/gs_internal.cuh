@@ -280,7 +280,7 @@ struct CsExtras {
     // entry) and ordered afterwards by big_blocks cooperating blocks, each
     // cell by LSD passes over its item indices (< 2^big_bits) through
     // big_scratch (n words; its cells' ranges are overwritten).  Without a
-    // list such cells are ordered by one thread each (insertion sort).
+    // list the warp that meets such a cell orders it (through the ranks).
     uint32_t* big_list = nullptr;
     uint32_t* big_count = nullptr;
     uint32_t* big_scratch = nullptr;
@@ -288,8 +288,9 @@ struct CsExtras {
     int big_blocks = 0;
 };
 // ga and gb are copied into cell order: x_out[slot] = x[particle of the
-// slot], with the extras above.
-cudaError_t gs_cs_finish(cudaStream_t s, int64_t n, int64_t n_cell, const uint32_t* keys, const uint32_t* rank,
+// slot], with the extras above.  rank is overwritten where cells of more
+// than 256 entries are ordered (it is dead once scattered).
+cudaError_t gs_cs_finish(cudaStream_t s, int64_t n, int64_t n_cell, const uint32_t* keys, uint32_t* rank,
                          uint32_t* out_keys, uint32_t* out_idx, uint32_t* cell_start, uint32_t* aux, const float4* ga,
                          const float4* gb, float4* ga_out, float4* gb_out, int64_t* launches,
                          const CsExtras& ex = CsExtras{});

@@ -360,8 +360,8 @@ __global__ void k_cs_scatter(const uint32_t* __restrict__ keys, const uint32_t* 
 // every cell's entries in ascending item order.  A cell holds a handful of
 // LR particles (HR fine cells a few dozen): its entries are loaded at once
 // into registers (padded with the largest key) and ordered by a fixed
-// compare-exchange network; larger cells are listed for k_cs_order_big, or
-// without a list fall back to an insertion sort in place.
+// compare-exchange network; larger cells are ordered cooperatively (see
+// k_cs_order), so no cell costs quadratic work.
 template <int K>
 __device__ __forceinline__ void order_small(uint32_t* __restrict__ idx, uint32_t b, uint32_t n)
 {
@@ -412,56 +412,6 @@ __device__ __forceinline__ void order_32(uint32_t* __restrict__ idx, uint32_t b,
         if ((uint32_t)k < n) idx[b + k] = v[k];
 }
 
-__global__ void k_cs_order(const uint32_t* __restrict__ start, int64_t n_cell, uint32_t* __restrict__ idx,
-                           const float4* __restrict__ ga, const float4* __restrict__ gb, float4* __restrict__ ga_out,
-                           float4* __restrict__ gb_out, const CsExtras ex)
-{
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n_cell) return;
-    const uint32_t b = start[c], e = start[c + 1];
-    const uint32_t n = e - b;
-    if (n == 0) return;
-    if (n == 1) {
-    } else if (n <= 4) {
-        order_small<4>(idx, b, n);
-    } else if (n <= 8) {
-        order_small<8>(idx, b, n);
-    } else if (n <= 16) {
-        order_small<16>(idx, b, n);
-    } else if (n <= 32) {
-        order_32(idx, b, n);
-    } else if (ex.big_list) {
-        ex.big_list[atomicAdd(ex.big_count, 1u)] = (uint32_t)c;   // ordered by k_cs_order_big
-        return;
-    } else {
-        for (uint32_t j = b + 1; j < e; ++j) {
-            const uint32_t v = idx[j];
-            uint32_t k = j;
-            while (k > b && idx[k - 1] > v) {
-                idx[k] = idx[k - 1];
-                --k;
-            }
-            idx[k] = v;
-        }
-    }
-    // the cell's entries of two arrays, copied into cell order
-    if (ga) {
-        for (uint32_t j = b; j < e; ++j) {
-            const uint32_t i = idx[j];
-            float4 u = ga[i];
-            if (ex.ga_solid && ex.ga_solid[i] != 0u) u.w = 0.0f;
-            ga_out[j] = u;
-            if (gb) {
-                float4 v = gb[i];
-                if (ex.gb_w) v.w = __uint_as_float(ex.gb_w[i]);
-                gb_out[j] = v;
-            }
-        }
-    }
-    if (ex.slot_of)
-        for (uint32_t j = b; j < e; ++j) ex.slot_of[idx[j]] = j;
-}
-
 // One warp orders a cell of up to 32 R distinct entries: lane l holds
 // entries l, l + 32, ... (coalesced), every entry's place is the number of
 // entries below it, counted against all of them broadcast by shuffles.
@@ -489,6 +439,135 @@ __device__ __forceinline__ void order_warp(uint32_t* __restrict__ idx, uint32_t 
 #pragma unroll
     for (int r = 0; r < R; ++r)
         if ((uint32_t)(r * 32 + lane) < n) idx[b + rk[r]] = v[r];
+    __syncwarp();
+}
+
+// One warp orders a cell of any size (entries below 2^bits) by stable
+// 4-bit LSD passes, ping-ponging between idx and scratch over the cell's
+// range: per pass a digit histogram (lane d counts digit d), its exclusive
+// scan, then chunks of 32 in order, each entry placed after the earlier
+// lanes of its chunk with the same digit.  Linear work per pass; no shared
+// memory.
+__device__ void warp_lsd(uint32_t* __restrict__ idx, uint32_t* __restrict__ scratch, uint32_t b, uint32_t n,
+                         int bits, int lane)
+{
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t* src = idx + b;
+    uint32_t* dst = scratch + b;
+    for (int shift = 0; shift < bits; shift += 4) {
+        uint32_t cnt = 0;
+        for (uint32_t base = 0; base < n; base += 32) {
+            const uint32_t t = base + (uint32_t)lane;
+            const uint32_t d = t < n ? (src[t] >> shift) & 15u : 16u;
+#pragma unroll
+            for (uint32_t q = 0; q < 16; ++q) {
+                const unsigned m = __ballot_sync(0xffffffffu, d == q);
+                if ((uint32_t)lane == q) cnt += (uint32_t)__popc(m);
+            }
+        }
+        uint32_t inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        uint32_t off = inc - cnt;   // lane d < 16: where digit d starts
+        for (uint32_t base = 0; base < n; base += 32) {
+            const uint32_t t = base + (uint32_t)lane;
+            const bool valid = t < n;
+            const uint32_t v = valid ? src[t] : 0u;
+            const uint32_t d = valid ? (v >> shift) & 15u : 16u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t o = __shfl_sync(0xffffffffu, off, (int)d);
+            if (valid) dst[o + (uint32_t)__popc(peers & lt)] = v;
+#pragma unroll
+            for (uint32_t q = 0; q < 16; ++q) {
+                const unsigned m = __ballot_sync(0xffffffffu, d == q);
+                if ((uint32_t)lane == q) off += (uint32_t)__popc(m);
+            }
+        }
+        __syncwarp();
+        uint32_t* tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    if (src != idx + b)
+        for (uint32_t t = (uint32_t)lane; t < n; t += 32) idx[b + t] = src[t];
+    __syncwarp();
+}
+
+// Entries [b + first, e) step `step` of one ordered cell: two arrays copied
+// into cell order with the extras, and each particle's slot.
+__device__ __forceinline__ void copy_cell(const uint32_t* __restrict__ idx, uint32_t b, uint32_t e, uint32_t first,
+                                          uint32_t step, const float4* __restrict__ ga, const float4* __restrict__ gb,
+                                          float4* __restrict__ ga_out, float4* __restrict__ gb_out,
+                                          const CsExtras& ex)
+{
+    if (ga) {
+        for (uint32_t j = b + first; j < e; j += step) {
+            const uint32_t i = idx[j];
+            float4 u = ga[i];
+            if (ex.ga_solid && ex.ga_solid[i] != 0u) u.w = 0.0f;
+            ga_out[j] = u;
+            if (gb) {
+                float4 v = gb[i];
+                if (ex.gb_w) v.w = __uint_as_float(ex.gb_w[i]);
+                gb_out[j] = v;
+            }
+        }
+    }
+    if (ex.slot_of)
+        for (uint32_t j = b + first; j < e; j += step) ex.slot_of[idx[j]] = j;
+}
+
+// One thread per cell.  Cells of more than 32 entries go to ex.big_list
+// when there is one (ordered by k_cs_order_big, which balances them over
+// the whole grid); otherwise the warp that met them orders them one after
+// another (order_warp up to 256 entries, warp_lsd beyond, scratch: n words
+// of which those cells' ranges are overwritten).
+__global__ void __launch_bounds__(256, 4) k_cs_order(const uint32_t* __restrict__ start, int64_t n_cell,
+                                                     uint32_t* __restrict__ idx, const float4* __restrict__ ga,
+                                                     const float4* __restrict__ gb, float4* __restrict__ ga_out,
+                                                     float4* __restrict__ gb_out, uint32_t* __restrict__ scratch,
+                                                     int bits, const CsExtras ex)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = (int)(threadIdx.x & 31u);
+    uint32_t b = 0, e = 0;
+    bool big = false;   // every lane reaches the ballot below: no early return
+    if (c < n_cell) {
+        b = start[c];
+        e = start[c + 1];
+        const uint32_t n = e - b;
+        if (n > 32) {
+            if (ex.big_list) ex.big_list[atomicAdd(ex.big_count, 1u)] = (uint32_t)c;
+            else big = true;
+        } else if (n > 0) {
+            if (n == 1) {
+            } else if (n <= 4) {
+                order_small<4>(idx, b, n);
+            } else if (n <= 8) {
+                order_small<8>(idx, b, n);
+            } else if (n <= 16) {
+                order_small<16>(idx, b, n);
+            } else {
+                order_32(idx, b, n);
+            }
+            copy_cell(idx, b, e, 0, 1, ga, gb, ga_out, gb_out, ex);
+        }
+    }
+    unsigned pend = __ballot_sync(0xffffffffu, big);
+    while (pend) {   // warp-uniform
+        const int j = __ffs(pend) - 1;
+        pend &= pend - 1u;
+        const uint32_t cb = __shfl_sync(0xffffffffu, b, j), ce = __shfl_sync(0xffffffffu, e, j);
+        const uint32_t n = ce - cb;
+        if (n <= 64) order_warp<2>(idx, cb, n, lane);
+        else if (n <= 256) order_warp<8>(idx, cb, n, lane);
+        else warp_lsd(idx, scratch, cb, n, bits, lane);
+        copy_cell(idx, cb, ce, (uint32_t)lane, 32u, ga, gb, ga_out, gb_out, ex);
+        __syncwarp();
+    }
 }
 
 // Cells of more than 32 entries, listed by k_cs_order.  Cells of up to 256
@@ -689,7 +768,7 @@ cudaError_t gs_cs_keys(cudaStream_t s, const float4* pos, int64_t n, const Scene
     return cudaGetLastError();
 }
 
-cudaError_t gs_cs_finish(cudaStream_t s, int64_t n, int64_t n_cell, const uint32_t* keys, const uint32_t* rank,
+cudaError_t gs_cs_finish(cudaStream_t s, int64_t n, int64_t n_cell, const uint32_t* keys, uint32_t* rank,
                          uint32_t* out_keys, uint32_t* out_idx, uint32_t* cell_start, uint32_t* aux, const float4* ga,
                          const float4* gb, float4* ga_out, float4* gb_out, int64_t* launches, const CsExtras& ex)
 {
@@ -706,7 +785,9 @@ cudaError_t gs_cs_finish(cudaStream_t s, int64_t n, int64_t n_cell, const uint32
         if (ex.big_list && (ga || ex.slot_of || ex.big_blocks <= 0 || !ex.big_count || !ex.big_scratch))
             return cudaErrorInvalidValue;   // listed cells are ordered without copies
         k_cs_scatter<<<gs_blocks(n, 256), 256, 0, s>>>(keys, rank, n, cell_start, out_keys, out_idx);
-        k_cs_order<<<gs_blocks(n_cell, 256), 256, 0, s>>>(cell_start, n_cell, out_idx, ga, gb, ga_out, gb_out, ex);
+        // the ranks are dead once scattered: scratch for large cells
+        k_cs_order<<<gs_blocks(n_cell, 256), 256, 0, s>>>(cell_start, n_cell, out_idx, ga, gb, ga_out, gb_out, rank,
+                                                          gs_key_bits(n), ex);
         *launches += 2;
         if (ex.big_list) {
             k_cs_order_big<<<(unsigned)ex.big_blocks, kThreads, 0, s>>>(cell_start, ex.big_list, ex.big_count, out_idx,

@@ -54,11 +54,17 @@ def test_lr_binning_bit_exact(orc, make):
 def test_lr_binning_outside_box_and_degenerate(orc):
     rng = np.random.default_rng(21)
     base = scenes.cube()
-    for case in ("outside", "one_point", "single", "empty"):
+    for case in ("outside", "one_point", "piles", "single", "empty"):
         sc = dict(base)
         if case == "outside":
             lr = np.zeros((3001, 4), np.float32)
             lr[:, :3] = rng.uniform(-0.2, 0.7, size=(3001, 3))
+        elif case == "piles":   # cells of 40, 100 and 300 among ordinary ones
+            lr = base["lr_pos"].copy()
+            pts = rng.uniform(0.1, 0.4, size=(6, 3)).astype(np.float32)
+            lr[:120, :3] = np.repeat(pts[:3], 40, axis=0)
+            lr[120:320, :3] = np.repeat(pts[3:5], 100, axis=0)
+            lr[320:620, :3] = pts[5]
         elif case == "one_point":
             lr = np.zeros((5000, 4), np.float32)
             lr[:, :3] = 0.25

@@ -51,6 +51,25 @@ def test_full_size_sampled(orc, make, nsub):
     check_hr(sc, DT, x[sub], v[sub], ref)
 
 
+def test_lr_piles_many_particles_per_cell(orc):
+    """LR particles piled on points (cells of 40, 100 and 300, ordered by a
+    warp or the whole block) with distinct velocities: the binning's copies
+    of position and velocity into cell order must be those of the ordered
+    cells."""
+    sc = scenes.stir(scenes.cube(), seed=7)
+    rng = np.random.default_rng(8)
+    lr = sc["lr_pos"].copy()
+    pts = rng.uniform(0.15, 0.35, size=(6, 3)).astype(np.float32)
+    lr[:120, :3] = np.repeat(pts[:3], 40, axis=0)
+    lr[120:320, :3] = np.repeat(pts[3:5], 100, axis=0)
+    lr[320:620, :3] = pts[5]
+    sc["lr_pos"] = lr
+    sc["lr_vel"] = sc["lr_vel"].copy()
+    sc["lr_vel"][:, :3] = rng.normal(scale=0.3, size=(len(lr), 3)).astype(np.float32)
+    x, v = _run(sc)
+    check_hr(sc, DT, x, v, _ref(orc, sc, mode=0))
+
+
 def test_uniform_field_and_isolated_particles(orc):
     sc = scenes.cube()
     u = np.array([0.3, -0.2, 0.1], np.float32)

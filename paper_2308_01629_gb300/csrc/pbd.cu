@@ -221,6 +221,7 @@ __global__ void __launch_bounds__(128) k_neighbors(const PbdArgs a, const float4
 // partial sums are added with shuffles in a fixed order and lane 0 writes
 // the particle.
 constexpr int kLanes = 2;
+constexpr int kContactGroup = 2;   // contact terms whose loads are in flight together
 
 struct PassAcc {
     float Dx, Dy, Dz;
@@ -320,30 +321,64 @@ __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_
     const float wp = xtp.w;                      // inverse height-scaled mass
     const float dpx = xtp.x - xp.x, dpy = xtp.y - xp.y, dpz = xtp.z - xp.z;
     PassAcc acc = {0.f, 0.f, 0.f, 0};
-    // four candidates at a time (k, k + kLanes, ...), their loads in flight
-    // together; the summation order is the candidate order of the lane
-    for (int k = sub; k < nc; k += 4 * kLanes) {
-        uint32_t q[4];
-        bool in[4];
+    // The lane's candidates k = sub, sub + kLanes, ... in windows of 32.
+    // First their distances alone: four at a time, the loads of the
+    // evaluated positions in flight together, a bit per candidate that may
+    // be in contact (a slightly wider test than pair_term's, which decides).
+    // Then the contact terms for the marked candidates only, in candidate
+    // order (the summation order of the lane).  A warp thus runs the contact
+    // code as often as its busiest lane has contacts, not once per candidate
+    // slot that any lane fills.
+    const float4* yq_in = stab ? x_in : xt_in;
+    const float d2_mark = d0 * d0 * 1.0001f;
+    for (int w0 = sub; w0 < nc; w0 += 32 * kLanes) {
+        const int wend = min(nc, w0 + 32 * kLanes);
+        uint32_t marked = 0u;
+        for (int k = w0; k < wend; k += 4 * kLanes) {
+            uint32_t q[4];
+            bool in[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            in[j] = k + j * kLanes < nc;
-            q[j] = in[j] ? __ldg(nbr + (int64_t)(k + j * kLanes) * a.n + p) : (uint32_t)p;
+            for (int j = 0; j < 4; ++j) {
+                in[j] = k + j * kLanes < wend;
+                q[j] = in[j] ? __ldg(nbr + (int64_t)(k + j * kLanes) * a.n + p) : (uint32_t)p;
+            }
+            float4 yq[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) yq[j] = ld_pos<kL2>(yq_in + q[j]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float ex = yq[j].x - yp.x, ey = yq[j].y - yp.y, ez = yq[j].z - yp.z;
+                const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));   // as pair_geo
+                if (in[j] && d2 < d2_mark) marked |= 1u << ((k - w0) / kLanes + j);
+            }
         }
-        float4 xtq[4], xq[4];
+        // the marked candidates kContactGroup at a time, their loads in flight
+        // together, then their terms in candidate order
+        while (marked) {
+            uint32_t q[kContactGroup];
+            bool ok[kContactGroup];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            xtq[j] = ld_pos<kL2>(xt_in + q[j]);
-            xq[j] = ld_pos<kL2>(x_in + q[j]);
-        }
+            for (int j = 0; j < kContactGroup; ++j) {
+                ok[j] = marked != 0u;
+                const int li = ok[j] ? __ffs(marked) - 1 : 0;
+                marked &= marked - 1u;
+                q[j] = ok[j] ? __ldg(nbr + (int64_t)(w0 + li * kLanes) * a.n + p) : (uint32_t)p;
+            }
+            float4 xtq[kContactGroup], xq[kContactGroup];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            if (!in[j]) continue;
-            if constexpr (kMat) {
-                const float2 mu = __ldg(cross_p + __float_as_uint(xq[j].w));
-                pair_term(acc, sc, stab, yp, wp, dpx, dpy, dpz, xtq[j], xq[j], d0, mu.x, mu.y);
-            } else {
-                pair_term(acc, sc, stab, yp, wp, dpx, dpy, dpz, xtq[j], xq[j], d0, sc.mu_s, sc.mu_k);
+            for (int j = 0; j < kContactGroup; ++j) {
+                xtq[j] = ld_pos<kL2>(xt_in + q[j]);
+                xq[j] = ld_pos<kL2>(x_in + q[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < kContactGroup; ++j) {
+                if (!ok[j]) continue;
+                if constexpr (kMat) {
+                    const float2 mu = __ldg(cross_p + __float_as_uint(xq[j].w));
+                    pair_term(acc, sc, stab, yp, wp, dpx, dpy, dpz, xtq[j], xq[j], d0, mu.x, mu.y);
+                } else {
+                    pair_term(acc, sc, stab, yp, wp, dpx, dpy, dpz, xtq[j], xq[j], d0, sc.mu_s, sc.mu_k);
+                }
             }
         }
     }

@@ -221,6 +221,7 @@ __global__ void __launch_bounds__(128) k_neighbors(const PbdArgs a, const float4
 // partial sums are added with shuffles in a fixed order and lane 0 writes
 // the particle.
 constexpr int kLanes = 2;
+constexpr int kDistGroup = 4;      // candidate distances whose loads are in flight together
 constexpr int kContactGroup = 2;   // contact terms whose loads are in flight together
 
 struct PassAcc {
@@ -322,7 +323,7 @@ __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_
     const float dpx = xtp.x - xp.x, dpy = xtp.y - xp.y, dpz = xtp.z - xp.z;
     PassAcc acc = {0.f, 0.f, 0.f, 0};
     // The lane's candidates k = sub, sub + kLanes, ... in windows of 32.
-    // First their distances alone: four at a time, the loads of the
+    // First their distances alone: kDistGroup at a time, the loads of the
     // evaluated positions in flight together, a bit per candidate that may
     // be in contact (a slightly wider test than pair_term's, which decides).
     // Then the contact terms for the marked candidates only, in candidate
@@ -334,19 +335,19 @@ __device__ __forceinline__ void pass_particle(const PbdArgs& a, int stab, int64_
     for (int w0 = sub; w0 < nc; w0 += 32 * kLanes) {
         const int wend = min(nc, w0 + 32 * kLanes);
         uint32_t marked = 0u;
-        for (int k = w0; k < wend; k += 4 * kLanes) {
-            uint32_t q[4];
-            bool in[4];
+        for (int k = w0; k < wend; k += kDistGroup * kLanes) {
+            uint32_t q[kDistGroup];
+            bool in[kDistGroup];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < kDistGroup; ++j) {
                 in[j] = k + j * kLanes < wend;
                 q[j] = in[j] ? __ldg(nbr + (int64_t)(k + j * kLanes) * a.n + p) : (uint32_t)p;
             }
-            float4 yq[4];
+            float4 yq[kDistGroup];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) yq[j] = ld_pos<kL2>(yq_in + q[j]);
+            for (int j = 0; j < kDistGroup; ++j) yq[j] = ld_pos<kL2>(yq_in + q[j]);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < kDistGroup; ++j) {
                 const float ex = yq[j].x - yp.x, ey = yq[j].y - yp.y, ez = yq[j].z - yp.z;
                 const float d2 = fmaf(ez, ez, fmaf(ey, ey, ex * ex));   // as pair_geo
                 if (in[j] && d2 < d2_mark) marked |= 1u << ((k - w0) / kLanes + j);

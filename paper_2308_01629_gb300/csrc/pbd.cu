@@ -216,7 +216,8 @@ __global__ void __launch_bounds__(128) k_neighbors(const PbdArgs a, const float4
 }
 
 // kLanes lanes share one particle: lane `sub` takes candidates sub, sub +
-// kLanes, ... four at a time (so their loads are in flight together)
+// kLanes, ... (their distances kDistGroup at a time, the contact terms of
+// those that may touch kContactGroup at a time, loads in flight together)
 // and the SDF components whose running index is sub modulo kLanes; the
 // partial sums are added with shuffles in a fixed order and lane 0 writes
 // the particle.

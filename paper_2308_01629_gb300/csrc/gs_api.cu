@@ -1806,11 +1806,8 @@ static int upsample_fwd_seq(gs_ctx* c, float dt)
     cur = c->hr_cur;
     UpsampleArgs u = upsample_args(c, dt, c->hr_pos[cur], c->hr_vel[cur], c->hr_pos[cur], c->hr_vel[cur]);
     CK(gs_launch_upsample(c->stream, u, c->tune_warps, c->tune_blocks_per_sm, c->sm_count, &c->launches), "upsample");
-    CK(gs_launch_unpermute(c->stream, c->hr_pos[cur], c->hr_pos[cur], c->hr_scene, F + 2 * M, c->hr_slots, M,
-                           c->d_err, &c->launches),
-       "unpermute");
-    CK(gs_launch_unpermute(c->stream, c->hr_pos[cur], c->hr_vel[cur], c->hr_scene, F + 3 * M, c->hr_slots, M,
-                           c->d_err, &c->launches),
+    CK(gs_launch_unpermute2(c->stream, c->hr_pos[cur], c->hr_vel[cur], c->hr_scene, F + 2 * M, F + 3 * M,
+                            c->hr_slots, M, c->d_err, &c->launches),
        "unpermute");
     return GS_OK;
 }
@@ -2102,21 +2099,40 @@ int gs_read_async(gs_ctx* c, int field, void* dst, size_t bytes, int dst_is_devi
     if (bytes == 0) return GS_OK;
     st = async_buffer(c, &c->async_out[field], field);
     if (st) return st;
-    // snapshot in stream order, then copy it out on its own stream
-    CK(cudaStreamWaitEvent(c->stream, c->ev_out_free[field], 0), "wait for the snapshot buffer");
-    const int cur = c->hr_cur;
     float4* out = c->async_out[field];
-    switch (field) {
-    case GS_FIELD_LR_POS: CK(cudaMemcpyAsync(out, c->lr_pos, bytes, cudaMemcpyDeviceToDevice, c->stream), "snapshot"); break;
-    case GS_FIELD_LR_VEL: CK(cudaMemcpyAsync(out, c->lr_vel, bytes, cudaMemcpyDeviceToDevice, c->stream), "snapshot"); break;
-    default: {
-        const float4* f = field == GS_FIELD_HR_POS ? c->hr_pos[cur] : c->hr_vel[cur];
-        CK(gs_launch_unpermute(c->stream, c->hr_pos[cur], f, c->hr_scene, out, c->hr_slots, c->n_high, c->d_err,
-                               &c->launches),
-           "unpermute");
+    // an HR field whose snapshot the read of the other one took, with no
+    // kernel launched since: only the copy out is left
+    const bool paired = c->hr_pair_field == field && c->hr_pair_launches == c->launches;
+    c->hr_pair_field = -1;
+    if (!paired) {
+        // snapshot in stream order, then copy it out on its own stream
+        CK(cudaStreamWaitEvent(c->stream, c->ev_out_free[field], 0), "wait for the snapshot buffer");
+        const int cur = c->hr_cur;
+        switch (field) {
+        case GS_FIELD_LR_POS:
+            CK(cudaMemcpyAsync(out, c->lr_pos, bytes, cudaMemcpyDeviceToDevice, c->stream), "snapshot");
+            break;
+        case GS_FIELD_LR_VEL:
+            CK(cudaMemcpyAsync(out, c->lr_vel, bytes, cudaMemcpyDeviceToDevice, c->stream), "snapshot");
+            break;
+        default: {
+            // both HR fields in one pass (the ids are read once); the other
+            // snapshot serves the usual next call, the read of that field
+            const int other = field == GS_FIELD_HR_POS ? GS_FIELD_HR_VEL : GS_FIELD_HR_POS;
+            st = async_buffer(c, &c->async_out[other], other);
+            if (st) return st;
+            CK(cudaStreamWaitEvent(c->stream, c->ev_out_free[other], 0), "wait for the snapshot buffer");
+            CK(gs_launch_unpermute2(c->stream, c->hr_pos[cur], c->hr_vel[cur], c->hr_scene,
+                                    c->async_out[GS_FIELD_HR_POS], c->async_out[GS_FIELD_HR_VEL], c->hr_slots,
+                                    c->n_high, c->d_err, &c->launches),
+               "unpermute");
+            CK(cudaEventRecord(c->ev_out_ready[other], c->stream), "record");
+            c->hr_pair_field = other;
+            c->hr_pair_launches = c->launches;
+        }
+        }
+        CK(cudaEventRecord(c->ev_out_ready[field], c->stream), "record");
     }
-    }
-    CK(cudaEventRecord(c->ev_out_ready[field], c->stream), "record");
     CK(cudaStreamWaitEvent(c->stream_d2h, c->ev_out_ready[field], 0), "wait for the snapshot");
     CK(cudaMemcpyAsync(dst, out, bytes, cudaMemcpyDeviceToHost, c->stream_d2h), "copy out");
     CK(cudaEventRecord(c->ev_out_free[field], c->stream_d2h), "record");

@@ -186,6 +186,11 @@ struct gs_ctx {
     cudaStream_t stream_h2d = nullptr, stream_d2h = nullptr;
     float4* async_in[4] = {nullptr, nullptr, nullptr, nullptr};
     float4* async_out[4] = {nullptr, nullptr, nullptr, nullptr};
+    // An asynchronous read of one HR field snapshots both; the other's
+    // snapshot (field hr_pair_field) serves its own read if no kernel was
+    // launched in between (launch count hr_pair_launches).
+    int hr_pair_field = -1;
+    int64_t hr_pair_launches = -1;
     cudaEvent_t ev_in_ready[4] = {}, ev_in_free[4] = {}, ev_out_ready[4] = {}, ev_out_free[4] = {};
     bool in_pending[4] = {false, false, false, false};
     bool in_used[4] = {false, false, false, false}, out_used[4] = {false, false, false, false};
@@ -310,6 +315,11 @@ cudaError_t gs_launch_gather2(cudaStream_t s, const uint32_t* idx, const float4*
 cudaError_t gs_launch_unpermute(cudaStream_t s, const float4* pos_internal, const float4* field_internal,
                                 const uint32_t* hr_tag, float4* out, int64_t n_slots, int64_t n_real, int* err,
                                 int64_t* launches);
+// Both HR fields to original-id order in one pass (out_pos[id] = pos[p],
+// out_vel[id] = vel[p]).
+cudaError_t gs_launch_unpermute2(cudaStream_t s, const float4* pos_internal, const float4* vel_internal,
+                                 const uint32_t* hr_tag, float4* out_pos, float4* out_vel, int64_t n_slots,
+                                 int64_t n_real, int* err, int64_t* launches);
 cudaError_t gs_launch_permute_in(cudaStream_t s, const float4* pos_internal, const float4* field_original,
                                  const uint32_t* hr_tag, float4* out, int64_t n_slots, int64_t n_real, int* err,
                                  int64_t* launches);

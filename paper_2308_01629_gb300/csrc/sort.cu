@@ -696,6 +696,23 @@ __global__ void k_unpermute(const float4* __restrict__ pos, const float4* __rest
     out[id] = f[p];
 }
 
+// Both HR fields at once: position and velocity of slot p to their ids.
+__global__ void k_unpermute2(const float4* __restrict__ pos, const float4* __restrict__ vel,
+                             const uint32_t* __restrict__ tag, float4* __restrict__ out_pos,
+                             float4* __restrict__ out_vel, int64_t n_slots, int64_t n_real, int* err)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_slots || (tag[p] & kPadBit)) return;
+    const float4 x = pos[p];
+    uint32_t id = __float_as_uint(x.w);
+    if ((int64_t)id >= n_real) {
+        atomicOr(err, GS_DEVERR_BAD_ID);
+        return;
+    }
+    out_pos[id] = x;
+    out_vel[id] = vel[p];
+}
+
 __global__ void k_permute_in(const float4* __restrict__ pos, const float4* __restrict__ f,
                              const uint32_t* __restrict__ tag, float4* __restrict__ out, int64_t n_slots,
                              int64_t n_real, int* err)
@@ -844,6 +861,17 @@ cudaError_t gs_launch_unpermute(cudaStream_t s, const float4* pos_internal, cons
     if (n_slots <= 0) return cudaSuccess;
     k_unpermute<<<gs_blocks(n_slots, 256), 256, 0, s>>>(pos_internal, field_internal, hr_tag, out, n_slots, n_real,
                                                         err);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_unpermute2(cudaStream_t s, const float4* pos_internal, const float4* vel_internal,
+                                 const uint32_t* hr_tag, float4* out_pos, float4* out_vel, int64_t n_slots,
+                                 int64_t n_real, int* err, int64_t* launches)
+{
+    if (n_slots <= 0) return cudaSuccess;
+    k_unpermute2<<<gs_blocks(n_slots, 256), 256, 0, s>>>(pos_internal, vel_internal, hr_tag, out_pos, out_vel,
+                                                         n_slots, n_real, err);
     *launches += 1;
     return cudaGetLastError();
 }

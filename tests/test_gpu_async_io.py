@@ -80,6 +80,47 @@ def test_async_read_is_a_snapshot_and_last_write_wins():
     ctx.close()
 
 
+def test_hr_reads_share_one_snapshot_only_while_nothing_ran():
+    """An asynchronous read of one HR field snapshots both; the other's read
+    uses that snapshot only if no kernel ran in between (a frame, a write),
+    in either order, and a field read twice is snapshotted twice."""
+    import paper_2308_01629_gb300 as gs
+    F = _fields(gs)
+    sc = scenes.stir(scenes.cube(n_side=6), seed=5, v_scale=0.3)
+    ctx = gs.Context(sc)
+    ctx.set_graphs(True)
+    ctx.frame(DT, 4, 8)
+    for first, second in (("hr_pos", "hr_vel"), ("hr_vel", "hr_pos")):
+        a = np.zeros_like(sc[first])
+        b = np.zeros_like(sc[second])
+        ctx.read_async(F[first], a)
+        ctx.frame(DT, 4, 8)                  # between the two reads
+        ctx.read_async(F[second], b)
+        ctx.sync()
+        want_b = ctx.read(F[second])         # the state after the frame
+        np.testing.assert_array_equal(b, want_b, err_msg=f"{first} then frame then {second}")
+        # back to back: the pair, then the same field again
+        a2, b2, a3 = np.zeros_like(a), np.zeros_like(b), np.zeros_like(a)
+        ctx.read_async(F[first], a2)
+        ctx.read_async(F[second], b2)
+        ctx.read_async(F[first], a3)
+        ctx.sync()
+        np.testing.assert_array_equal(a2, ctx.read(F[first]))
+        np.testing.assert_array_equal(b2, want_b)
+        np.testing.assert_array_equal(a3, a2)
+    # a write between the two reads is seen by the second one
+    v = np.ascontiguousarray(sc["hr_vel"]).copy()
+    v[:, :3] += 0.25
+    x = np.zeros_like(sc["hr_pos"])
+    got = np.zeros_like(v)
+    ctx.read_async(F["hr_pos"], x)
+    ctx.write_async(F["hr_vel"], v)
+    ctx.read_async(F["hr_vel"], got)
+    ctx.sync()
+    np.testing.assert_array_equal(got, v)
+    ctx.close()
+
+
 def test_non_finite_async_write_is_reported_at_sync():
     import paper_2308_01629_gb300 as gs
     F = _fields(gs)

@@ -57,3 +57,26 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(3.5, 1, None) == 3.5
     assert bench.whole_job_rate(100, 1, 0.5) == 200
+
+
+def test_reference_arm_line_follows_the_contract(monkeypatch):
+    """The reference arm (the FP64 oracle on the host cores, rank 0) prints
+    one JSON line with the contract's keys, the workload's config, a
+    cpu_baseline describing the run and an e2e with no device transfers."""
+    import json
+
+    import bench
+    monkeypatch.delenv("RANK", raising=False)
+    line = bench.run_reference(bench.parse(["--impl", "reference", "--steps", "1", "--warmup", "0"]))
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["steps"] == 1
+    assert line["ms_per_step"] == pytest.approx(1e3 * line["config"]["n_high"] / line["value"])
+    assert line["config"]["workload"].startswith("digging") and line["config"]["n_high"] == 2021080
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    json.loads(json.dumps(line))

@@ -112,6 +112,32 @@ def test_batch_upsample_matches_oracle(orc):
     ctx.close()
 
 
+def test_full_size_batch_in_the_benchmark_configuration_matches_oracle(orc):
+    """The 256-scene batch the benchmark times (about 19M HR particles) in
+    its launch configuration (graph-replayed pipelined frames, persistent
+    gather of 8 warps x 4 blocks per SM): one frame without LR steps, so its
+    HR frame is the upsampling of the initial state, against the oracle on
+    sampled particles of sampled scenes."""
+    import paper_2308_01629_gb300 as gs
+    sl = [scenes.stir(s, seed=70 + k, spread=0.1) for k, s in enumerate(scenes.batch())]
+    ctx = gs.Context(sl)
+    ctx.set_graphs(True)
+    ctx.set_pipeline(True, 8, 4)
+    ctx.frame(DT, 0, 8)
+    hx, hv = ctx.read(gs.GS_FIELD_HR_POS), ctx.read(gs.GS_FIELD_HR_VEL)
+    assert len(hx) == sum(len(s["hr_pos"]) for s in sl) > 15_000_000
+    rng = np.random.default_rng(71)
+    for k in sorted(rng.choice(len(sl), size=8, replace=False)):
+        sc = sl[k]
+        sl_k = ctx.scene_slice(k, gs.GS_FIELD_HR_POS)
+        m = len(sc["hr_pos"])
+        sub = np.sort(rng.choice(m, size=min(m, 2000), replace=False))
+        ref = orc.upsample(sc["lr_pos"][:, :3], sc["lr_vel"][:, :3], sc["hr_pos"][:, :3], sc["hr_vel"][:, :3],
+                           scenes.sdf_table(sc["sdfs"]), up_prm(sc, DT), sub=sub, mode=1)
+        check_hr(sc, DT, hx[sl_k][sub], hv[sl_k][sub], ref)
+    ctx.close()
+
+
 def _empty_like(sc):
     """The same scene with no particles at all (no LR, hence no HR)."""
     e = dict(sc)

@@ -102,6 +102,34 @@ def test_full_step_statistics(orc, case):
         np.testing.assert_allclose(a.std(0), b.std(0), rtol=1e-2, atol=1e-9)
 
 
+@pytest.mark.parametrize("passes", [(0, 1), (1, 0)])
+def test_dense_pack_with_more_candidates_than_one_window(orc, passes):
+    """LR particles packed at spacing r_LR: about 110 candidates within
+    3 r_LR each, so a lane's candidates (every second one) fill more than
+    one 32-candidate window of the pass's distance round; room for 256.
+    One solver pass and one stabilization pass against the oracle."""
+    spatial = pytest.importorskip("scipy.spatial")
+    import paper_2308_01629_gb300 as gs
+    sc = dict(scenes.cube())
+    r = float(sc["r_low"])
+    g = np.stack(np.meshgrid(*[np.arange(10)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    lr = sc["lr_pos"].copy()
+    lr[:, :3] = (0.2 + g * r + np.random.default_rng(5).uniform(-0.1 * r, 0.1 * r, size=g.shape)).astype(np.float32)
+    sc["lr_pos"] = lr
+    counts = np.array([len(c) - 1 for c in spatial.cKDTree(lr[:, :3]).query_ball_point(lr[:, :3], 3 * r)])
+    assert counts.max() > 64 and counts.max() <= 256
+    dt = 1.0 / 240.0
+    ctx = gs.Context(sc, n_stab=passes[0], max_neighbors=256)
+    ctx.step_low(dt, passes[1])
+    x, v = ctx.read(gs.GS_FIELD_LR_POS), ctx.read(gs.GS_FIELD_LR_VEL)
+    ctx.sync()
+    ctx.close()
+    rx, rv, sus, st = orc.pbd_step(sc["lr_pos"][:, :3], sc["lr_vel"][:, :3], sc["lr_pos"][:, 3],
+                                   scenes.sdf_table(sc["sdfs"]), pb_prm(sc, dt, *passes), mode=1)
+    assert st["active"] > 0 and sus.mean() < 0.05, st
+    elementwise(sc, dt, x, v, rx, rv, ~sus)
+
+
 def test_candidate_capacity_overflow_is_reported():
     import paper_2308_01629_gb300 as gs
     sc = scenes.cube()

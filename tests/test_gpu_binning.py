@@ -123,6 +123,11 @@ def test_hr_reorder_bit_exact_sort_paths_and_big_cells(orc, case):
     if "wide" in case:
         sc = _wide_box(sc)
     _check_hr_reorder(orc, sc)
+    if case == "wide_box":   # 4.6M cells: the cell-start scan over more than 1,024 tiles
+        gs, ctx = _ctx(sc)
+        assert ctx.grid.n_cell > 1024 * 4096
+        _check_lr_binning(orc, sc, ctx, gs)
+        ctx.close()
 
 
 def _check_hr_reorder(orc, sc):

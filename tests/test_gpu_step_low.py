@@ -106,7 +106,7 @@ def test_full_step_statistics(orc, case):
 def test_dense_pack_with_more_candidates_than_one_window(orc, passes):
     """LR particles packed at spacing r_LR: about 110 candidates within
     3 r_LR each, so a lane's candidates (every second one) fill more than
-    one 32-candidate window of the pass's distance round; room for 256.
+    one 32-candidate window of the pass's distance phase; room for 256.
     One solver pass and one stabilization pass against the oracle."""
     spatial = pytest.importorskip("scipy.spatial")
     import paper_2308_01629_gb300 as gs

@@ -2012,35 +2012,31 @@ static int step_low_reverse(gs_ctx* c, float dt, int iters)
     CK(gs_launch_predict(c->stream, a, c->lr_pos, c->lr_vel, c->lr_xt, &c->launches), "predict");
     st = bin_low_at(c, c->lr_xt);
     if (st) return st;
-    CK(gs_launch_step_gather(c->stream, N, c->lr_sorted_idx, c->lr_xt, c->lr_pos, c->s_xt[0], c->s_x[0],
-                             &c->launches),
-       "gather");
-    CK(gs_launch_neighbors(c->stream, a, c->s_xt[0], c->lr_sorted_keys, c->lr_cell_start, c->n_cell_total, c->nbr, c->nbr_cnt,
+    // The passes read and write the snapshot buffers themselves: x~ before
+    // pass it is snap_xt[it], x before stabilization pass it is snap[it]
+    // (after the stabilization passes snap[n_stab] throughout).
+    float4* const X = c->snap;
+    float4* const XT = c->snap_xt;
+    CK(gs_launch_step_gather(c->stream, N, c->lr_sorted_idx, c->lr_xt, c->lr_pos, XT, X, &c->launches), "gather");
+    CK(gs_launch_neighbors(c->stream, a, XT, c->lr_sorted_keys, c->lr_cell_start, c->n_cell_total, c->nbr, c->nbr_cnt,
                            c->nbr_cap, c->d_err, &c->launches),
        "neighbours");
-    int bx = 0, bt = 0;
+    auto x_before = [&](int it) { return X + (size_t)std::min(it, c->n_stab) * N; };
     for (int it = 0; it < total; ++it) {
         const int stab = it < c->n_stab;
-        CK(cudaMemcpyAsync(c->snap + (size_t)it * N, stab ? c->s_x[bx] : c->s_xt[bt], N * sizeof(float4),
-                           cudaMemcpyDeviceToDevice, c->stream),
-           "snapshot");
-        CK(cudaMemcpyAsync(c->snap_xt + (size_t)it * N, c->s_xt[bt], N * sizeof(float4), cudaMemcpyDeviceToDevice,
-                           c->stream),
-           "snapshot");
-        CK(gs_launch_pass(c->stream, a, stab, c->s_x[bx], c->s_xt[bt], c->s_x[bx ^ 1], c->s_xt[bt ^ 1], c->nbr,
-                          c->nbr_cnt, &c->launches),
+        CK(gs_launch_pass(c->stream, a, stab, x_before(it), XT + (size_t)it * N, X + (size_t)(it + 1) * N,
+                          XT + (size_t)(it + 1) * N, c->nbr, c->nbr_cnt, &c->launches),
            "pass");
-        bt ^= 1;
-        if (stab) bx ^= 1;
     }
-    const float4* xfix = c->s_x[bx];          // x after stabilization
-    const float4* ws = c->s_xt[0];            // w of xt carries the inverse scaled mass
+    const float4* xfix = x_before(total);     // x after stabilization
+    const float4* ws = XT;                    // w of xt carries the inverse scaled mass (every pass keeps it)
     CK(gs_launch_adj_init(c->stream, N, c->lr_sorted_idx, c->adj_io, c->adj_io + N, dt, c->adj_gx, c->adj_gxt,
                           c->adj_gws, &c->launches),
        "reverse init");
     for (int it = total - 1; it >= 0; --it) {
         const int stab = it < c->n_stab;
-        CK(gs_launch_adj_pass(c->stream, a, stab, c->snap + (size_t)it * N, c->snap_xt + (size_t)it * N, xfix, ws,
+        CK(gs_launch_adj_pass(c->stream, a, stab, stab ? x_before(it) : XT + (size_t)it * N, XT + (size_t)it * N,
+                              xfix, ws,
                               c->nbr, c->nbr_cnt, c->adj_h, c->adj_gx, c->adj_gxt, c->adj_gws, &c->launches),
            "reverse pass");
     }

@@ -80,3 +80,25 @@ def test_reference_arm_line_follows_the_contract(monkeypatch):
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     json.loads(json.dumps(line))
+
+
+def test_profile_commands_use_existing_bench_flags():
+    """Every bench.py flag named in the commands recorded under profiles/
+    exists, so each recorded command still runs."""
+    import pathlib
+    import re
+
+    import bench
+    root = pathlib.Path(bench.__file__).resolve().parent
+    parser_flags = set()
+    src = (root / "bench.py").read_text()
+    parser_flags.update(re.findall(r'add_argument\("(--[a-z0-9-]+)"', src))
+    assert "--gather-shape" in parser_flags and "--no-e2e" in parser_flags
+    files = sorted((root / "profiles").glob("*.md"))
+    assert files
+    for f in files:
+        text = f.read_text()
+        cmd = text[text.index("python bench.py"):]
+        cmd = cmd[:cmd.index("\n\n")]
+        for flag in re.findall(r"(--[a-z0-9-]+)", cmd):
+            assert flag in parser_flags, f"{f.name}: {flag}"

@@ -416,6 +416,29 @@ int gs_step_low_forward(gs_ctx* ctx, const float* x_in, const float* v_in, float
 int gs_step_low_backward(gs_ctx* ctx, const float* x_in, const float* v_in, const float* g_x_out, const float* g_v_out,
                          float* g_x_in, float* g_v_in, float dt, int iters);
 
+/* Pass-by-pass record of one LR step (Algorithm 1, Sec. 3), for checking the
+ * step against a reference one Jacobi pass at a time: each pass is a
+ * function of the state before it, so a pass can be compared on its own
+ * from the record of its input, without the branch decisions of the earlier
+ * passes compounding.  Same step as gs_step_low_forward from (x_in, v_in)
+ * (float4[n_low] device buffers in original order; w of x = inverse mass):
+ * record k = 0 .. n_stab + iters holds, in original particle order, the
+ * positions x (the start-of-step positions as corrected by the
+ * stabilization passes so far) and the predictions x~ (as corrected by all
+ * passes so far) before pass k; record n_stab + iters is the state after
+ * the last pass, from which the step's finalize takes v = (x~ - x) / dt,
+ * x = x~.  The w of an x record is the inverse mass; the w of an x~ record
+ * is the inverse height-scaled mass 1/m* the passes use.
+ *   x_trace, xt_trace  device float4[(n_stab + iters + 1) * n_low], caller-owned
+ *   n_records          must equal n_stab + iters + 1 (GS_ERR_ARG otherwise)
+ * The context is used as workspace; its LR state is overwritten.
+ * GS_ERR_STATE while grain materials or rigid bodies are set; LR positions
+ * with inverse mass 0 make the next blocking call return GS_ERR_STATE (as
+ * for the reverse modes).  GS_ERR_OOM if the per-pass buffers cannot be
+ * allocated (first use).  Asynchronous. */
+int gs_step_low_trace(gs_ctx* ctx, const float* x_in, const float* v_in, float dt, int iters, float* x_trace,
+                      float* xt_trace, int n_records);
+
 /* Block until the context's stream is idle and report device-side errors. */
 int gs_sync(gs_ctx* ctx);
 

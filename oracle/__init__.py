@@ -73,6 +73,9 @@ def _L():
         L.or_upsample_solid.restype = ctypes.c_int
         L.or_pbd_step.argtypes = [P, P, P, ctypes.c_long, P, ctypes.c_int, P, ctypes.c_int, P, P]
         L.or_pbd_step.restype = ctypes.c_int
+        L.or_pbd_pass.argtypes = [P, P, P, P, P, ctypes.c_long, P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
+                                  P, P]
+        L.or_pbd_pass.restype = ctypes.c_int
         L.or_pbd_step_mu.argtypes = [P, P, P, ctypes.c_long, P, ctypes.c_int, P, ctypes.c_int, P, P, P]
         L.or_pbd_step_mu.restype = ctypes.c_int
         L.or_pbd_step_bodies.argtypes = [P, P, P, ctypes.c_long, P, ctypes.c_int, P, ctypes.c_int, P, P, P,
@@ -276,6 +279,28 @@ def pbd_step(x, v, inv_m, sdf, prm, mode=0, mu=None, bodies=None):
     return x, v, sus.astype(bool), dict(pairs=int(stats[0]), significant=int(stats[1]),
                                         max_candidates=int(stats[2]), active=int(stats[3]),
                                         ambiguous=int(stats[4]))
+
+
+def pbd_pass(x, xt, x0, xt0, inv_m, sdf, prm, stab, mode=1):
+    """One Jacobi pass of Algorithm 1 (Sec. 3) from a given state: x (start-
+    of-step positions as stabilized so far) and xt (predictions as corrected
+    so far) are the pass's input; x0 (step start) fixes the height-scaled
+    masses and xt0 (the step's predictions) the candidate pairs; stab selects
+    a stabilization pass (contacts on x, applied to x and xt) or a solver pass
+    (Eqs. 1-4 on xt).  Returns (x, xt, suspect, stats); suspect marks the
+    particles whose result hangs on a decision within this pass's margins."""
+    x, xt = _f64(x, 3).copy(), _f64(xt, 3).copy()
+    x0, xt0 = _f64(x0, 3), _f64(xt0, 3)
+    inv_m = _f64(inv_m)
+    sdf = _f64(sdf, SDF_STRIDE) if sdf is not None and len(sdf) else np.zeros((0, SDF_STRIDE))
+    sus = np.zeros(len(x), np.int32)
+    stats = np.zeros(5, np.int64)
+    rc = _L().or_pbd_pass(_ptr(x), _ptr(xt), _ptr(x0), _ptr(xt0), _ptr(inv_m), len(x), _ptr(sdf), len(sdf),
+                          _ptr(_prm(prm, PB_KEYS)), int(bool(stab)), int(mode), _ptr(sus), _ptr(stats))
+    if rc != 0:
+        raise RuntimeError(f"or_pbd_pass failed ({rc})")
+    return x, xt, sus.astype(bool), dict(pairs=int(stats[0]), significant=int(stats[1]), active=int(stats[3]),
+                                         ambiguous=int(stats[4]))
 
 
 def pbd_step_vjp(x, v, inv_m, sdf, prm, gx, gv):

@@ -870,33 +870,298 @@ typedef struct {
     int n_bodies;
 } or_bodies;
 
-static int pbd_impl(double* x, double* v, const double* inv_m, long N,
-                    const double* sdf, int n_sdf, const double* prm, const double* mu, int mode,
-                    int* suspect, long* stats, int tmode, unsigned char* tape, long tape_cap, long* tape_len,
-                    const or_bodies* bodies)
+/* Everything one Jacobi pass of the LR step reads and writes. */
+typedef struct {
+    long N;
+    double *x, *xt;                /* [N][3]: start-of-step positions (as stabilized so far), predictions */
+    const double* ws;              /* [N] inverse height-scaled masses 1/m* */
+    const double* inv_m;           /* [N] inverse masses (rigid bodies use the unscaled masses) */
+    const double* sdf;
+    int n_sdf, nct;
+    const double* mu;              /* [N][2] per-particle (mu_s, mu_k), or NULL */
+    const or_bodies* bodies;
+    double r, dt, mu_s, mu_k, d0, eps_x, eps_imp;
+    int fmode;
+    const or_pair* P;              /* candidate pairs and their border flags */
+    const unsigned char* border;
+    long np;
+    const or_pair* E;              /* pairs dropped within eps_x of the candidate radius */
+    long n_excl;
+    int tmode;
+    /* scratch and outputs */
+    double* D;                     /* [N][3] summed corrections */
+    long* cnt;                     /* [N] constraint counts n_i */
+    unsigned char* mark;           /* [N] suspect particles */
+    or_alts alts;
+    long n_sig, n_amb, active_last;
+} pbd_work;
+
+/* One Jacobi pass (Algorithm 1; Eqs. 1-2, plus Eqs. 3-4 in a solver pass):
+ * every constraint is evaluated on the pass's input, the corrections are
+ * summed per particle and averaged, delta_i = (1/n_i) sum_k delta_ik, and
+ * applied to xt (and to x in a stabilization pass).  tpair (tape modes): the
+ * pass's decision bytes, one per pair then one per (particle, SDF
+ * component).  Returns 0, or -1 / -4 on allocation / degenerate-body
+ * failures. */
+static int pbd_pass(pbd_work* w, int stab, unsigned char* tpair)
 {
-    double r = prm[PB_R], dt = prm[PB_DT];
-    const double g[3] = {prm[PB_GX], prm[PB_GY], prm[PB_GZ]};
-    double mu_s = prm[PB_MU_S], mu_k = prm[PB_MU_K];
-    int n_stab = (int)prm[PB_N_STAB], iters = (int)prm[PB_ITERS];
-    double mass_k = prm[PB_MASS_K], ground = prm[PB_GROUND_Z], Rc = prm[PB_RC];
-    int fmode = (int)prm[PB_FRIC_MODE];
-    double eps_x = prm[PB_EPS_X], eps_imp = prm[PB_EPS_IMPACT];
-    double d0 = 2.0 * r;
+    const long N = w->N;
+    double *x = w->x, *xt = w->xt, *D = w->D;
+    const double* ws = w->ws;
+    long* cnt = w->cnt;
+    unsigned char* mark = w->mark;
+    const double r = w->r, dt = w->dt, d0 = w->d0, eps_x = w->eps_x;
+    const int tmode = w->tmode;
+    unsigned char* tsdf = tpair ? tpair + w->np : NULL;
+    memset(D, 0, (size_t)N * 3 * sizeof(double));
+    memset(cnt, 0, (size_t)N * sizeof(long));
+    w->alts.n = 0;
+    w->active_last = 0;
+    /* Stabilization repairs invalid positions at the start of the step
+     * (Sec. 3): its contacts are evaluated on x, the solver's on xt. */
+    const double* y = stab ? x : xt;
+    /* a candidate pair decided the other way by a float32 neighbour
+     * search matters only if it comes into contact */
+    for (long p = 0; p < w->n_excl; ++p) {
+        long i = w->E[p].i, j = w->E[p].j;
+        double e[3] = {y[3 * j] - y[3 * i], y[3 * j + 1] - y[3 * i + 1], y[3 * j + 2] - y[3 * i + 2]};
+        if (sqrt(dot3(e, e)) < d0 + eps_x) { mark[i] = mark[j] = 1; ++w->n_sig; }
+    }
+    /* particle-particle contacts: Eqs. 1-2 (+ Eqs. 3-4 when solving) */
+    for (long p = 0; p < w->np; ++p) {
+        long i = w->P[p].i, j = w->P[p].j;
+        double xij[3] = {y[3 * j] - y[3 * i], y[3 * j + 1] - y[3 * i + 1], y[3 * j + 2] - y[3 * i + 2]};
+        double d2 = dot3(xij, xij);
+        double d = sqrt(d2);
+        if (w->border[p] && d < d0 + eps_x) { mark[i] = mark[j] = 1; ++w->n_sig; }
+        int active = d < d0;
+        int amb_act = fabs(d - d0) <= eps_x;
+        if (tmode == TAPE_REPLAY) { active = tpair[p] & 1; amb_act = 0; }
+        else if (tmode == TAPE_RECORD && active) tpair[p] |= 1;
+        if ((!active && !amb_act) || d2 == 0.0) continue;
+        double wsum = ws[i] + ws[j];
+        if (!(wsum > 0)) continue;
+        double mi = ws[i] / wsum, mj = ws[j] / wsum;
+        double pen = d0 - d;
+        double u[3] = {xij[0] / d, xij[1] / d, xij[2] / d};
+        double ci[3], cj[3], ci_alt[3], cj_alt[3];
+        int amb_f = 0;
+        for (int k = 0; k < 3; ++k) {
+            ci[k] = -mi * pen * u[k];
+            cj[k] = mj * pen * u[k];
+        }
+        memcpy(ci_alt, ci, sizeof ci);
+        memcpy(cj_alt, cj, sizeof cj);
+        if (!stab) {
+            double dx[3], perp[3], f[3], fa[3];
+            for (int k = 0; k < 3; ++k)
+                dx[k] = (xt[3 * i + k] - x[3 * i + k]) - (xt[3 * j + k] - x[3 * j + k]);
+            double a = dot3(dx, xij) / d2;
+            for (int k = 0; k < 3; ++k) perp[k] = dx[k] - a * xij[k];
+            double base = (w->fmode == 1) ? pen : d0;
+            double pmu_s = w->mu_s, pmu_k = w->mu_k;
+            if (w->mu) {   /* cross coefficients of the pair (Sec. 3) */
+                pmu_s = sqrt(w->mu[2 * i] * w->mu[2 * j]);
+                pmu_k = sqrt(w->mu[2 * i + 1] * w->mu[2 * j + 1]);
+            }
+            friction_delta(perp, base * pmu_s, base * pmu_k, eps_x, f, fa, &amb_f, tmode, tpair ? tpair + p : NULL);
+            for (int k = 0; k < 3; ++k) {
+                ci_alt[k] = ci[k] - mi * fa[k];
+                cj_alt[k] = cj[k] + mj * fa[k];
+                ci[k] -= mi * f[k];
+                cj[k] += mj * f[k];
+            }
+        }
+        if (active) {
+            for (int k = 0; k < 3; ++k) {
+                D[3 * i + k] += ci[k];
+                D[3 * j + k] += cj[k];
+            }
+            cnt[i]++;
+            cnt[j]++;
+            ++w->active_last;
+        }
+        if (amb_act) {
+            double si = active ? -1.0 : 1.0;
+            double a1[3] = {si * ci[0], si * ci[1], si * ci[2]}, a2[3] = {si * cj[0], si * cj[1], si * cj[2]};
+            alt_push(&w->alts, i, a1, active ? -1 : 1);
+            alt_push(&w->alts, j, a2, active ? -1 : 1);
+        }
+        if (amb_f && active) {
+            double a1[3] = {ci_alt[0] - ci[0], ci_alt[1] - ci[1], ci_alt[2] - ci[2]};
+            double a2[3] = {cj_alt[0] - cj[0], cj_alt[1] - cj[1], cj_alt[2] - cj[2]};
+            alt_push(&w->alts, i, a1, 0);
+            alt_push(&w->alts, j, a2, 0);
+        }
+    }
+    /* SDF contacts */
+    for (long i = 0; i < N; ++i) {
+        if (!(ws[i] > 0)) continue;
+        int comp0 = 0;
+        for (int s = 0; s < w->n_sdf; comp0 += sdf_ncomp(w->sdf + OR_SDF_STRIDE * s), ++s) {
+            const double* rec = w->sdf + OR_SDF_STRIDE * s;
+            double phi[OR_MAX_COMP], nn[3 * OR_MAX_COMP];
+            int tie;
+            int nc = or_sdf_eval(rec, y + 3 * i, phi, nn, &tie, eps_x);
+            const double* ub = rec + 13;
+            double gmu_s = w->mu ? w->mu[2 * i] : w->mu_s, gmu_k = w->mu ? w->mu[2 * i + 1] : w->mu_k;
+            double bmu_s = sqrt(gmu_s * rec[16]), bmu_k = sqrt(gmu_k * rec[17]);
+            for (int c = 0; c < nc; ++c) {
+                int active = phi[c] < r;
+                int amb_act = fabs(phi[c] - r) <= eps_x;
+                unsigned char* tb = tsdf ? tsdf + i * (long)w->nct + comp0 + c : NULL;
+                if (tmode == TAPE_REPLAY) { active = *tb & 1; amb_act = 0; }
+                else if (tmode == TAPE_RECORD && active) *tb |= 1;
+                if (!active && !amb_act) continue;
+                if (tie) { mark[i] = 1; ++w->n_sig; }
+                const double* n = nn + 3 * c;
+                double pen = r - phi[c];
+                double ci[3], ci_alt[3];
+                int amb_f = 0;
+                for (int k = 0; k < 3; ++k) ci[k] = pen * n[k];
+                memcpy(ci_alt, ci, sizeof ci);
+                if (!stab) {
+                    double dx[3], perp[3], f[3], fa[3];
+                    for (int k = 0; k < 3; ++k) dx[k] = (xt[3 * i + k] - x[3 * i + k]) - ub[k] * dt;
+                    double a = dot3(dx, n);
+                    for (int k = 0; k < 3; ++k) perp[k] = dx[k] - a * n[k];
+                    double base = (w->fmode == 1) ? pen : d0;
+                    friction_delta(perp, base * bmu_s, base * bmu_k, eps_x, f, fa, &amb_f, tmode, tb);
+                    for (int k = 0; k < 3; ++k) {
+                        ci_alt[k] = ci[k] - fa[k];
+                        ci[k] -= f[k];
+                    }
+                }
+                if (active) {
+                    for (int k = 0; k < 3; ++k) D[3 * i + k] += ci[k];
+                    cnt[i]++;
+                }
+                if (amb_act) {
+                    double si = active ? -1.0 : 1.0;
+                    double a1[3] = {si * ci[0], si * ci[1], si * ci[2]};
+                    alt_push(&w->alts, i, a1, active ? -1 : 1);
+                }
+                if (amb_f && active) {
+                    double a1[3] = {ci_alt[0] - ci[0], ci_alt[1] - ci[1], ci_alt[2] - ci[2]};
+                    alt_push(&w->alts, i, a1, 0);
+                }
+            }
+        }
+    }
+    /* shape matching of the rigid bodies (solver passes) */
+    if (!stab && w->bodies && w->bodies->n_bodies > 0) {
+        const or_bodies* bd = w->bodies;
+        int nb = bd->n_bodies;
+        double* acc = (double*)calloc((size_t)nb * 13, sizeof(double));   /* M, sum m xt, sum m xt xo^T */
+        double* tf = (double*)malloc((size_t)nb * 12 * sizeof(double));   /* R, c */
+        if (!acc || !tf) return -1;
+        for (long i = 0; i < N; ++i) {
+            int b = bd->body[i];
+            if (b < 1 || b > nb) continue;
+            double m = 1.0 / w->inv_m[i], *a = acc + 13 * (b - 1);
+            a[0] += m;
+            for (int k = 0; k < 3; ++k) a[1 + k] += m * xt[3 * i + k];
+            for (int rr = 0; rr < 3; ++rr)
+                for (int ss = 0; ss < 3; ++ss) a[4 + 3 * rr + ss] += m * xt[3 * i + rr] * bd->xo[3 * i + ss];
+        }
+        for (int b = 0; b < nb; ++b) {
+            double *a = acc + 13 * b, *t = tf + 12 * b, C[9];
+            if (!(a[0] > 0)) continue;
+            for (int k = 0; k < 3; ++k) t[9 + k] = a[1 + k] / a[0];
+            /* C = sum m xt xo^T - c sum m xo^T, and sum m xo = 0 at rest */
+            for (int k = 0; k < 9; ++k) C[k] = a[4 + k];
+            if (polar_rotation(C, t) != 0) { free(acc); free(tf); return -4; }
+        }
+        for (long i = 0; i < N; ++i) {
+            int b = bd->body[i];
+            if (b < 1 || b > nb) continue;
+            const double *t = tf + 12 * (b - 1), *o = bd->xo + 3 * i;
+            for (int rr = 0; rr < 3; ++rr)
+                D[3 * i + rr] += t[3 * rr] * o[0] + t[3 * rr + 1] * o[1] + t[3 * rr + 2] * o[2] + t[9 + rr] - xt[3 * i + rr];
+            cnt[i]++;
+        }
+        free(acc);
+        free(tf);
+    }
+    /* would the other branch of an ambiguous decision move the particle
+     * by more than eps_impact? */
+    for (long q = 0; q < w->alts.n; ++q) {
+        const or_alt* e = &w->alts.a[q];
+        long i = e->i;
+        double u0[3] = {0, 0, 0}, u1[3] = {0, 0, 0};
+        long n0 = cnt[i], n1a = cnt[i] + e->dn;
+        for (int k = 0; k < 3; ++k) {
+            if (n0 > 0) u0[k] = D[3 * i + k] / (double)n0;
+            if (n1a > 0) u1[k] = (D[3 * i + k] + e->dD[k]) / (double)n1a;
+        }
+        double dd[3] = {u1[0] - u0[0], u1[1] - u0[1], u1[2] - u0[2]};
+        ++w->n_amb;
+        if (sqrt(dot3(dd, dd)) > w->eps_imp) { mark[i] = 1; ++w->n_sig; }
+    }
+    /* Jacobi averaging: delta_i = (1/n_i) sum_k delta_ik.  Stabilization
+     * applies it to xt and x, solver iterations to xt only. */
+    for (long i = 0; i < N; ++i) {
+        if (cnt[i] == 0) continue;
+        for (int k = 0; k < 3; ++k) {
+            double dd = D[3 * i + k] / (double)cnt[i];
+            xt[3 * i + k] += dd;
+            if (stab) x[3 * i + k] += dd;
+        }
+    }
+    return 0;
+}
+
+/* The work record of a pass over N particles with its scratch allocated;
+ * pbd_work_free releases the scratch. */
+static int pbd_work_init(pbd_work* w, long N, double* x, double* xt, const double* ws, const double* inv_m,
+                         const double* sdf, int n_sdf, const double* prm, const double* mu, const or_bodies* bodies,
+                         int tmode)
+{
+    memset(w, 0, sizeof *w);
     size_t n1 = (size_t)(N ? N : 1);
+    w->N = N;
+    w->x = x;
+    w->xt = xt;
+    w->ws = ws;
+    w->inv_m = inv_m;
+    w->sdf = sdf;
+    w->n_sdf = n_sdf;
+    w->nct = total_components(sdf, n_sdf);
+    w->mu = mu;
+    w->bodies = bodies;
+    w->r = prm[PB_R];
+    w->dt = prm[PB_DT];
+    w->mu_s = prm[PB_MU_S];
+    w->mu_k = prm[PB_MU_K];
+    w->d0 = 2.0 * w->r;
+    w->eps_x = prm[PB_EPS_X];
+    w->eps_imp = prm[PB_EPS_IMPACT];
+    w->fmode = (int)prm[PB_FRIC_MODE];
+    w->tmode = tmode;
+    w->D = (double*)malloc(n1 * 3 * sizeof(double));
+    w->cnt = (long*)malloc(n1 * sizeof(long));
+    w->mark = (unsigned char*)calloc(n1, 1);
+    return (w->D && w->cnt && w->mark) ? 0 : -1;
+}
 
-    double* xt = (double*)malloc(n1 * 3 * sizeof(double));
-    double* ws = (double*)malloc(n1 * sizeof(double));
-    double* D = (double*)malloc(n1 * 3 * sizeof(double));
-    long* cnt = (long*)malloc(n1 * sizeof(long));
-    unsigned char* mark = (unsigned char*)calloc(n1, 1);
-    unsigned char* mark2 = (unsigned char*)calloc(n1, 1);
-    if (!xt || !ws || !D || !cnt || !mark || !mark2) return -1;
+static void pbd_work_free(pbd_work* w)
+{
+    free(w->D);
+    free(w->cnt);
+    free(w->mark);
+    free(w->alts.a);
+}
 
-    /* Algorithm 1, first loop: v += dt g; xt = x + dt v; m* = m e^{-h(x)}.
-     * Stored as the inverse scaled mass 1/m* = m^-1 e^{h}.  Particles of
-     * infinite mass (m^-1 = 0: sampled boundaries and rigid bodies, Sec. 3)
-     * keep their prescribed velocity: no gravity. */
+/* Algorithm 1, first loop: v += dt g; xt = x + dt v; m* = m e^{-h(x)}
+ * (Sec. 3, height-scaled mass with h = k (z - ground_z)), stored as the
+ * inverse scaled mass 1/m* = m^-1 e^{h}.  Particles of infinite mass
+ * (m^-1 = 0: sampled boundaries and rigid bodies, Sec. 3) keep their
+ * prescribed velocity: no gravity.  v is updated in place. */
+static void pbd_predict(const double* x, double* v, const double* inv_m, long N, const double* prm, double* xt,
+                        double* ws)
+{
+    const double dt = prm[PB_DT], mass_k = prm[PB_MASS_K], ground = prm[PB_GROUND_Z];
+    const double g[3] = {prm[PB_GX], prm[PB_GY], prm[PB_GZ]};
     for (long i = 0; i < N; ++i) {
         for (int k = 0; k < 3; ++k) {
             if (inv_m[i] > 0) v[3 * i + k] += dt * g[k];
@@ -904,6 +1169,22 @@ static int pbd_impl(double* x, double* v, const double* inv_m, long N,
         }
         ws[i] = inv_m[i] * exp(mass_k * (x[3 * i + 2] - ground));
     }
+}
+
+static int pbd_impl(double* x, double* v, const double* inv_m, long N,
+                    const double* sdf, int n_sdf, const double* prm, const double* mu, int mode,
+                    int* suspect, long* stats, int tmode, unsigned char* tape, long tape_cap, long* tape_len,
+                    const or_bodies* bodies)
+{
+    int n_stab = (int)prm[PB_N_STAB], iters = (int)prm[PB_ITERS];
+    double dt = prm[PB_DT], Rc = prm[PB_RC], eps_x = prm[PB_EPS_X];
+    size_t n1 = (size_t)(N ? N : 1);
+
+    double* xt = (double*)malloc(n1 * 3 * sizeof(double));
+    double* ws = (double*)malloc(n1 * sizeof(double));
+    unsigned char* mark2 = (unsigned char*)calloc(n1, 1);
+    if (!xt || !ws || !mark2) return -1;
+    pbd_predict(x, v, inv_m, N, prm, xt, ws);
 
     /* neighbour search and constraint generation */
     or_pair *P = NULL, *E = NULL;
@@ -939,7 +1220,7 @@ static int pbd_impl(double* x, double* v, const double* inv_m, long N,
         }
         tpass = tape + 32 + 16 * np;
     }
-    long n_sig = 0, n_amb = 0, maxc = 0;
+    long maxc = 0;
     if (stats) {
         long* c = (long*)calloc(n1, sizeof(long));
         for (long p = 0; p < np; ++p) { c[P[p].i]++; c[P[p].j]++; }
@@ -947,244 +1228,113 @@ static int pbd_impl(double* x, double* v, const double* inv_m, long N,
             if (c[i] > maxc) maxc = c[i];
         free(c);
     }
-    or_alts alts = {NULL, 0, 0};
 
-    long active_last = 0;
-    for (int it = 0; it < total; ++it) {
-        int stab = it < n_stab;
-        unsigned char* tpair = tpass ? tpass + (long)it * (np + N * (long)nct) : NULL;
-        unsigned char* tsdf = tpair ? tpair + np : NULL;
+    pbd_work w;
+    if (pbd_work_init(&w, N, x, xt, ws, inv_m, sdf, n_sdf, prm, mu, bodies, tmode) != 0) return -1;
+    w.P = P;
+    w.border = border;
+    w.np = np;
+    w.E = E;
+    w.n_excl = n_excl;
+    int rc = 0;
+    for (int it = 0; it < total && rc == 0; ++it) {
         /* a particle that read a suspect candidate partner in an earlier
          * pass is itself suspect from now on */
         if (it > 0) {
-            memcpy(mark2, mark, (size_t)N);
+            memcpy(mark2, w.mark, (size_t)N);
             for (long p = 0; p < np; ++p) {
-                if (mark2[P[p].i]) mark[P[p].j] = 1;
-                if (mark2[P[p].j]) mark[P[p].i] = 1;
+                if (mark2[P[p].i]) w.mark[P[p].j] = 1;
+                if (mark2[P[p].j]) w.mark[P[p].i] = 1;
             }
         }
-        memset(D, 0, (size_t)N * 3 * sizeof(double));
-        memset(cnt, 0, (size_t)N * sizeof(long));
-        alts.n = 0;
-        active_last = 0;
-        /* Stabilization repairs invalid positions at the start of the step
-         * (Sec. 3): its contacts are evaluated on x, the solver's on xt. */
-        const double* y = stab ? x : xt;
-        /* a candidate pair decided the other way by a float32 neighbour
-         * search matters only if it comes into contact */
-        for (long p = 0; p < n_excl; ++p) {
-            long i = E[p].i, j = E[p].j;
-            double e[3] = {y[3 * j] - y[3 * i], y[3 * j + 1] - y[3 * i + 1], y[3 * j + 2] - y[3 * i + 2]};
-            if (sqrt(dot3(e, e)) < d0 + eps_x) { mark[i] = mark[j] = 1; ++n_sig; }
-        }
-        /* particle-particle contacts: Eqs. 1-2 (+ Eqs. 3-4 when solving) */
-        for (long p = 0; p < np; ++p) {
-            long i = P[p].i, j = P[p].j;
-            double xij[3] = {y[3 * j] - y[3 * i], y[3 * j + 1] - y[3 * i + 1], y[3 * j + 2] - y[3 * i + 2]};
-            double d2 = dot3(xij, xij);
-            double d = sqrt(d2);
-            if (border[p] && d < d0 + eps_x) { mark[i] = mark[j] = 1; ++n_sig; }
-            int active = d < d0;
-            int amb_act = fabs(d - d0) <= eps_x;
-            if (tmode == TAPE_REPLAY) { active = tpair[p] & 1; amb_act = 0; }
-            else if (tmode == TAPE_RECORD && active) tpair[p] |= 1;
-            if ((!active && !amb_act) || d2 == 0.0) continue;
-            double wsum = ws[i] + ws[j];
-            if (!(wsum > 0)) continue;
-            double mi = ws[i] / wsum, mj = ws[j] / wsum;
-            double pen = d0 - d;
-            double u[3] = {xij[0] / d, xij[1] / d, xij[2] / d};
-            double ci[3], cj[3], ci_alt[3], cj_alt[3];
-            int amb_f = 0;
+        unsigned char* tpair = tpass ? tpass + (long)it * (np + N * (long)nct) : NULL;
+        rc = pbd_pass(&w, it < n_stab, tpair);
+    }
+    if (rc == 0) {
+        /* last loop of Algorithm 1: v = (xt - x) / dt, x = xt */
+        for (long i = 0; i < N; ++i)
             for (int k = 0; k < 3; ++k) {
-                ci[k] = -mi * pen * u[k];
-                cj[k] = mj * pen * u[k];
+                v[3 * i + k] = (xt[3 * i + k] - x[3 * i + k]) / dt;
+                x[3 * i + k] = xt[3 * i + k];
             }
-            memcpy(ci_alt, ci, sizeof ci);
-            memcpy(cj_alt, cj, sizeof cj);
-            if (!stab) {
-                double dx[3], perp[3], f[3], fa[3];
-                for (int k = 0; k < 3; ++k)
-                    dx[k] = (xt[3 * i + k] - x[3 * i + k]) - (xt[3 * j + k] - x[3 * j + k]);
-                double a = dot3(dx, xij) / d2;
-                for (int k = 0; k < 3; ++k) perp[k] = dx[k] - a * xij[k];
-                double base = (fmode == 1) ? pen : d0;
-                double pmu_s = mu_s, pmu_k = mu_k;
-                if (mu) {   /* cross coefficients of the pair (Sec. 3) */
-                    pmu_s = sqrt(mu[2 * i] * mu[2 * j]);
-                    pmu_k = sqrt(mu[2 * i + 1] * mu[2 * j + 1]);
-                }
-                friction_delta(perp, base * pmu_s, base * pmu_k, eps_x, f, fa, &amb_f, tmode,
-                               tpair ? tpair + p : NULL);
-                for (int k = 0; k < 3; ++k) {
-                    ci_alt[k] = ci[k] - mi * fa[k];
-                    cj_alt[k] = cj[k] + mj * fa[k];
-                    ci[k] -= mi * f[k];
-                    cj[k] += mj * f[k];
-                }
-            }
-            if (active) {
-                for (int k = 0; k < 3; ++k) {
-                    D[3 * i + k] += ci[k];
-                    D[3 * j + k] += cj[k];
-                }
-                cnt[i]++;
-                cnt[j]++;
-                ++active_last;
-            }
-            if (amb_act) {
-                double si = active ? -1.0 : 1.0;
-                double a1[3] = {si * ci[0], si * ci[1], si * ci[2]}, a2[3] = {si * cj[0], si * cj[1], si * cj[2]};
-                alt_push(&alts, i, a1, active ? -1 : 1);
-                alt_push(&alts, j, a2, active ? -1 : 1);
-            }
-            if (amb_f && active) {
-                double a1[3] = {ci_alt[0] - ci[0], ci_alt[1] - ci[1], ci_alt[2] - ci[2]};
-                double a2[3] = {cj_alt[0] - cj[0], cj_alt[1] - cj[1], cj_alt[2] - cj[2]};
-                alt_push(&alts, i, a1, 0);
-                alt_push(&alts, j, a2, 0);
-            }
-        }
-        /* SDF contacts */
-        for (long i = 0; i < N; ++i) {
-            if (!(ws[i] > 0)) continue;
-            int comp0 = 0;
-            for (int s = 0; s < n_sdf; comp0 += sdf_ncomp(sdf + OR_SDF_STRIDE * s), ++s) {
-                const double* rec = sdf + OR_SDF_STRIDE * s;
-                double phi[OR_MAX_COMP], nn[3 * OR_MAX_COMP];
-                int tie;
-                int nc = or_sdf_eval(rec, y + 3 * i, phi, nn, &tie, eps_x);
-                const double* ub = rec + 13;
-                double gmu_s = mu ? mu[2 * i] : mu_s, gmu_k = mu ? mu[2 * i + 1] : mu_k;
-                double bmu_s = sqrt(gmu_s * rec[16]), bmu_k = sqrt(gmu_k * rec[17]);
-                for (int c = 0; c < nc; ++c) {
-                    int active = phi[c] < r;
-                    int amb_act = fabs(phi[c] - r) <= eps_x;
-                    unsigned char* tb = tsdf ? tsdf + i * (long)nct + comp0 + c : NULL;
-                    if (tmode == TAPE_REPLAY) { active = *tb & 1; amb_act = 0; }
-                    else if (tmode == TAPE_RECORD && active) *tb |= 1;
-                    if (!active && !amb_act) continue;
-                    if (tie) { mark[i] = 1; ++n_sig; }
-                    const double* n = nn + 3 * c;
-                    double pen = r - phi[c];
-                    double ci[3], ci_alt[3];
-                    int amb_f = 0;
-                    for (int k = 0; k < 3; ++k) ci[k] = pen * n[k];
-                    memcpy(ci_alt, ci, sizeof ci);
-                    if (!stab) {
-                        double dx[3], perp[3], f[3], fa[3];
-                        for (int k = 0; k < 3; ++k) dx[k] = (xt[3 * i + k] - x[3 * i + k]) - ub[k] * dt;
-                        double a = dot3(dx, n);
-                        for (int k = 0; k < 3; ++k) perp[k] = dx[k] - a * n[k];
-                        double base = (fmode == 1) ? pen : d0;
-                        friction_delta(perp, base * bmu_s, base * bmu_k, eps_x, f, fa, &amb_f, tmode, tb);
-                        for (int k = 0; k < 3; ++k) {
-                            ci_alt[k] = ci[k] - fa[k];
-                            ci[k] -= f[k];
-                        }
-                    }
-                    if (active) {
-                        for (int k = 0; k < 3; ++k) D[3 * i + k] += ci[k];
-                        cnt[i]++;
-                    }
-                    if (amb_act) {
-                        double si = active ? -1.0 : 1.0;
-                        double a1[3] = {si * ci[0], si * ci[1], si * ci[2]};
-                        alt_push(&alts, i, a1, active ? -1 : 1);
-                    }
-                    if (amb_f && active) {
-                        double a1[3] = {ci_alt[0] - ci[0], ci_alt[1] - ci[1], ci_alt[2] - ci[2]};
-                        alt_push(&alts, i, a1, 0);
-                    }
-                }
-            }
-        }
-        /* shape matching of the rigid bodies (solver passes) */
-        if (!stab && bodies && bodies->n_bodies > 0) {
-            int nb = bodies->n_bodies;
-            double* acc = (double*)calloc((size_t)nb * 13, sizeof(double));   /* M, sum m xt, sum m xt xo^T */
-            double* tf = (double*)malloc((size_t)nb * 12 * sizeof(double));   /* R, c */
-            if (!acc || !tf) return -1;
-            for (long i = 0; i < N; ++i) {
-                int b = bodies->body[i];
-                if (b < 1 || b > nb) continue;
-                double m = 1.0 / inv_m[i], *a = acc + 13 * (b - 1);
-                a[0] += m;
-                for (int k = 0; k < 3; ++k) a[1 + k] += m * xt[3 * i + k];
-                for (int r = 0; r < 3; ++r)
-                    for (int s = 0; s < 3; ++s) a[4 + 3 * r + s] += m * xt[3 * i + r] * bodies->xo[3 * i + s];
-            }
-            for (int b = 0; b < nb; ++b) {
-                double *a = acc + 13 * b, *t = tf + 12 * b, C[9];
-                if (!(a[0] > 0)) continue;
-                for (int k = 0; k < 3; ++k) t[9 + k] = a[1 + k] / a[0];
-                /* C = sum m xt xo^T - c sum m xo^T, and sum m xo = 0 at rest */
-                for (int k = 0; k < 9; ++k) C[k] = a[4 + k];
-                if (polar_rotation(C, t) != 0) { free(acc); free(tf); return -4; }
-            }
-            for (long i = 0; i < N; ++i) {
-                int b = bodies->body[i];
-                if (b < 1 || b > nb) continue;
-                const double *t = tf + 12 * (b - 1), *o = bodies->xo + 3 * i;
-                for (int r = 0; r < 3; ++r)
-                    D[3 * i + r] += t[3 * r] * o[0] + t[3 * r + 1] * o[1] + t[3 * r + 2] * o[2] + t[9 + r] - xt[3 * i + r];
-                cnt[i]++;
-            }
-            free(acc);
-            free(tf);
-        }
-        /* would the other branch of an ambiguous decision move the particle
-         * by more than eps_impact? */
-        for (long q = 0; q < alts.n; ++q) {
-            const or_alt* e = &alts.a[q];
-            long i = e->i;
-            double u0[3] = {0, 0, 0}, u1[3] = {0, 0, 0};
-            long n0 = cnt[i], n1a = cnt[i] + e->dn;
-            for (int k = 0; k < 3; ++k) {
-                if (n0 > 0) u0[k] = D[3 * i + k] / (double)n0;
-                if (n1a > 0) u1[k] = (D[3 * i + k] + e->dD[k]) / (double)n1a;
-            }
-            double dd[3] = {u1[0] - u0[0], u1[1] - u0[1], u1[2] - u0[2]};
-            ++n_amb;
-            if (sqrt(dot3(dd, dd)) > eps_imp) { mark[i] = 1; ++n_sig; }
-        }
-        /* Jacobi averaging: delta_i = (1/n_i) sum_k delta_ik.  Stabilization
-         * applies it to xt and x, solver iterations to xt only. */
-        for (long i = 0; i < N; ++i) {
-            if (cnt[i] == 0) continue;
-            for (int k = 0; k < 3; ++k) {
-                double dd = D[3 * i + k] / (double)cnt[i];
-                xt[3 * i + k] += dd;
-                if (stab) x[3 * i + k] += dd;
-            }
+        if (suspect)
+            for (long i = 0; i < N; ++i) suspect[i] = w.mark[i];
+        if (stats) {
+            stats[0] = np;
+            stats[1] = w.n_sig;
+            stats[2] = maxc;
+            stats[3] = w.active_last;
+            stats[4] = w.n_amb;
         }
     }
-    /* last loop of Algorithm 1: v = (xt - x) / dt, x = xt */
-    for (long i = 0; i < N; ++i)
-        for (int k = 0; k < 3; ++k) {
-            v[3 * i + k] = (xt[3 * i + k] - x[3 * i + k]) / dt;
-            x[3 * i + k] = xt[3 * i + k];
-        }
-    if (suspect)
-        for (long i = 0; i < N; ++i) suspect[i] = mark[i];
-    if (stats) {
-        stats[0] = np;
-        stats[1] = n_sig;
-        stats[2] = maxc;
-        stats[3] = active_last;
-        stats[4] = n_amb;
-    }
-    free(alts.a);
+    pbd_work_free(&w);
     free(P);
     free(E);
     free(border);
     free(xt);
     free(ws);
-    free(D);
-    free(cnt);
-    free(mark);
     free(mark2);
-    return 0;
+    return rc;
+}
+
+/* One Jacobi pass of the LR step from a given state, the oracle a pass-by-
+ * pass comparison needs (Algorithm 1, Sec. 3):
+ *   x0        [N][3] positions at the start of the step (they fix the
+ *             height-scaled masses, as in the step's first loop);
+ *   xt0       [N][3] predicted positions (the candidate pairs of the step
+ *             are generated from them, |xt0_i - xt0_j| < Rc);
+ *   x, xt     [N][3] the pass's input, updated in place: x as stabilized so
+ *             far, xt as corrected so far;
+ *   stab      1 for a stabilization pass (contacts only, evaluated on x and
+ *             applied to x and xt), 0 for a solver pass (Eqs. 1-4 on xt).
+ * suspect (optional, N) marks the particles whose result in this pass hangs
+ * on a decision within the margins prm[PB_EPS_X] / prm[PB_EPS_IMPACT]
+ * (candidate membership, contact, static / kinetic friction, SDF contact);
+ * marks are not carried over from earlier passes.  mode as or_pbd_step;
+ * stats as or_pbd_step ([3]: active pair contacts of this pass). */
+int or_pbd_pass(double* x, double* xt, const double* x0, const double* xt0, const double* inv_m, long N,
+                const double* sdf, int n_sdf, const double* prm, int stab, int mode, int* suspect, long* stats)
+{
+    size_t n1 = (size_t)(N ? N : 1);
+    double* ws = (double*)malloc(n1 * sizeof(double));
+    double* vt = (double*)calloc(n1 * 3, sizeof(double));
+    double* xp = (double*)malloc(n1 * 3 * sizeof(double));
+    if (!ws || !vt || !xp) return -1;
+    pbd_predict(x0, vt, inv_m, N, prm, xp, ws);   /* only the masses are used */
+    or_pair *P = NULL, *E = NULL;
+    unsigned char* border = NULL;
+    long n_excl = 0;
+    long np = make_pairs(xt0, N, prm[PB_RC], mode, &P, &border, &E, &n_excl, prm[PB_EPS_X]);
+    if (np < 0) return -1;
+    pbd_work w;
+    int rc = pbd_work_init(&w, N, x, xt, ws, inv_m, sdf, n_sdf, prm, NULL, NULL, TAPE_OFF);
+    if (rc == 0) {
+        w.P = P;
+        w.border = border;
+        w.np = np;
+        w.E = E;
+        w.n_excl = n_excl;
+        rc = pbd_pass(&w, stab, NULL);
+    }
+    if (rc == 0) {
+        if (suspect)
+            for (long i = 0; i < N; ++i) suspect[i] = w.mark[i];
+        if (stats) {
+            stats[0] = np;
+            stats[1] = w.n_sig;
+            stats[2] = 0;
+            stats[3] = w.active_last;
+            stats[4] = w.n_amb;
+        }
+    }
+    pbd_work_free(&w);
+    free(P);
+    free(E);
+    free(border);
+    free(ws);
+    free(vt);
+    free(xp);
+    return rc;
 }
 
 int or_pbd_step(double* x, double* v, const double* inv_m, long N,

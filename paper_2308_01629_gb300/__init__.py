@@ -108,6 +108,7 @@ _SIGS = {
     "gs_upsample_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_float]),
     "gs_step_low_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int]),
     "gs_step_low_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int]),
+    "gs_step_low_trace": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, ctypes.c_int, _P, _P, ctypes.c_int]),
 }
 
 _lib = None
@@ -318,6 +319,10 @@ def gs_step_low_forward(ctx, x_in, v_in, x_out, v_out, dt, iters):
 
 def gs_step_low_backward(ctx, x_in, v_in, g_x_out, g_v_out, g_x_in, g_v_in, dt, iters):
     return lib().gs_step_low_backward(ctx, x_in, v_in, g_x_out, g_v_out, g_x_in, g_v_in, dt, iters)
+
+
+def gs_step_low_trace(ctx, x_in, v_in, dt, iters, x_trace, xt_trace, n_records):
+    return lib().gs_step_low_trace(ctx, x_in, v_in, dt, iters, x_trace, xt_trace, n_records)
 
 
 # ------------------------------------------------------------ marshalling ---

@@ -1943,7 +1943,61 @@ int gs_step_low_forward(gs_ctx* c, const float* x_in, const float* v_in, float* 
     return GS_OK;
 }
 
+// Per-pass snapshot buffers of the LR step ((total + 1) x n_low each),
+// allocated on first use and grown when a step has more passes.
+static int ensure_snapshots(gs_ctx* c, int total)
+{
+    const int64_t N = c->n_low;
+    if (total <= c->snap_cap && c->snap) return GS_OK;
+    if (c->snap) cudaFree(c->snap);
+    if (c->snap_xt) cudaFree(c->snap_xt);
+    c->snap = c->snap_xt = nullptr;
+    c->snap_cap = 0;
+    if (dalloc(&c->snap, (size_t)(total + 1) * N) != cudaSuccess ||
+        dalloc(&c->snap_xt, (size_t)(total + 1) * N) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, GS_ERR_OOM, "no memory for the per-pass snapshots");
+    }
+    c->snap_cap = total;
+    drop_graphs(c);   // captured sequences hold the old snapshot buffers
+    return GS_OK;
+}
+
 static int step_low_reverse(gs_ctx* c, float dt, int iters);
+static int step_low_record(gs_ctx* c, float dt, int iters);
+
+int gs_step_low_trace(gs_ctx* c, const float* x_in, const float* v_in, float dt, int iters, float* x_trace,
+                      float* xt_trace, int n_records)
+{
+    int st = check_state(c);
+    if (st) return st;
+    st = settle(c);
+    if (st) return st;
+    if (!(dt > 0.0f) || !std::isfinite(dt) || iters < 0 || iters > 1000)
+        return fail(c, GS_ERR_ARG, "invalid dt %g or iters %d", (double)dt, iters);
+    if (c->n_materials > 0 || c->n_bodies > 0)
+        return fail(c, GS_ERR_STATE, "the pass record covers grains of the scenes' coefficients only");
+    const int total = c->n_stab + iters;
+    if (n_records != total + 1) return fail(c, GS_ERR_ARG, "n_records must be n_stab + iters + 1 = %d", total + 1);
+    const int64_t N = c->n_low;
+    if (N == 0) return GS_OK;
+    if (!x_in || !v_in || !x_trace || !xt_trace) return fail(c, GS_ERR_ARG, "null buffer");
+    st = ensure_snapshots(c, total);
+    if (st) return st;
+    CK(cudaMemcpyAsync(c->lr_pos, x_in, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    CK(cudaMemcpyAsync(c->lr_vel, v_in, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    st = step_low_record(c, dt, iters);
+    if (st) return st;
+    float4* xo = reinterpret_cast<float4*>(x_trace);
+    float4* xto = reinterpret_cast<float4*>(xt_trace);
+    for (int k = 0; k <= total; ++k)
+        CK(gs_launch_scatter2(c->stream, c->lr_sorted_idx, c->snap + (size_t)std::min(k, c->n_stab) * N,
+                              c->snap_xt + (size_t)k * N, xo + (size_t)k * N, xto + (size_t)k * N, N, &c->launches),
+           "scatter");
+    c->lr_binned = false;
+    return GS_OK;
+}
+
 
 int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const float* g_x_out, const float* g_v_out,
                          float* g_x_in, float* g_v_in, float dt, int iters)
@@ -1960,20 +2014,8 @@ int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const 
     const int64_t N = c->n_low;
     if (N == 0) return GS_OK;
     if (!x_in || !v_in || !g_x_out || !g_v_out || !g_x_in || !g_v_in) return fail(c, GS_ERR_ARG, "null buffer");
-    const int total = c->n_stab + iters;
-    if (total > c->snap_cap) {
-        if (c->snap) cudaFree(c->snap);
-        if (c->snap_xt) cudaFree(c->snap_xt);
-        c->snap = c->snap_xt = nullptr;
-        c->snap_cap = 0;
-        if (dalloc(&c->snap, (size_t)(total + 1) * N) != cudaSuccess ||
-            dalloc(&c->snap_xt, (size_t)(total + 1) * N) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(c, GS_ERR_OOM, "no memory for the reverse-mode snapshots");
-        }
-        c->snap_cap = total;
-        drop_graphs(c);   // captured reverse steps hold the old snapshot buffers
-    }
+    st = ensure_snapshots(c, c->n_stab + iters);
+    if (st) return st;
     if (!c->adj_gx) {
         bool ok = dalloc(&c->adj_gx, N) == cudaSuccess && dalloc(&c->adj_gxt, N) == cudaSuccess &&
                   dalloc(&c->adj_h, N) == cudaSuccess && dalloc(&c->adj_gws, N) == cudaSuccess &&
@@ -1999,10 +2041,13 @@ int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const 
     return GS_OK;
 }
 
-// The reverse LR step on the context's buffers: the step again from
-// (lr_pos, lr_vel) keeping what every pass evaluates on, then the passes in
-// reverse; dL/d outputs from adj_io[0..1], dL/d inputs into adj_io[2..3].
-static int step_low_reverse(gs_ctx* c, float dt, int iters)
+// The LR step on the context's buffers (from lr_pos, lr_vel) keeping what
+// every pass evaluates on, in cell order: x~ before pass it is
+// snap_xt[it], x before stabilization pass it is snap[it] (after the
+// stabilization passes snap[n_stab] throughout); snap_xt[total] holds the
+// step's final x~.  The passes read and write the snapshot buffers
+// themselves.
+static int step_low_record(gs_ctx* c, float dt, int iters)
 {
     const int64_t N = c->n_low;
     const int total = c->n_stab + iters;
@@ -2012,22 +2057,34 @@ static int step_low_reverse(gs_ctx* c, float dt, int iters)
     CK(gs_launch_predict(c->stream, a, c->lr_pos, c->lr_vel, c->lr_xt, &c->launches), "predict");
     st = bin_low_at(c, c->lr_xt);
     if (st) return st;
-    // The passes read and write the snapshot buffers themselves: x~ before
-    // pass it is snap_xt[it], x before stabilization pass it is snap[it]
-    // (after the stabilization passes snap[n_stab] throughout).
     float4* const X = c->snap;
     float4* const XT = c->snap_xt;
     CK(gs_launch_step_gather(c->stream, N, c->lr_sorted_idx, c->lr_xt, c->lr_pos, XT, X, &c->launches), "gather");
     CK(gs_launch_neighbors(c->stream, a, XT, c->lr_sorted_keys, c->lr_cell_start, c->n_cell_total, c->nbr, c->nbr_cnt,
                            c->nbr_cap, c->d_err, &c->launches),
        "neighbours");
-    auto x_before = [&](int it) { return X + (size_t)std::min(it, c->n_stab) * N; };
     for (int it = 0; it < total; ++it) {
         const int stab = it < c->n_stab;
-        CK(gs_launch_pass(c->stream, a, stab, x_before(it), XT + (size_t)it * N, X + (size_t)(it + 1) * N,
-                          XT + (size_t)(it + 1) * N, c->nbr, c->nbr_cnt, &c->launches),
+        CK(gs_launch_pass(c->stream, a, stab, X + (size_t)std::min(it, c->n_stab) * N, XT + (size_t)it * N,
+                          X + (size_t)(it + 1) * N, XT + (size_t)(it + 1) * N, c->nbr, c->nbr_cnt, &c->launches),
            "pass");
     }
+    return GS_OK;
+}
+
+// The reverse LR step on the context's buffers: the step again from
+// (lr_pos, lr_vel) keeping what every pass evaluates on, then the passes in
+// reverse; dL/d outputs from adj_io[0..1], dL/d inputs into adj_io[2..3].
+static int step_low_reverse(gs_ctx* c, float dt, int iters)
+{
+    const int64_t N = c->n_low;
+    const int total = c->n_stab + iters;
+    int st = step_low_record(c, dt, iters);
+    if (st) return st;
+    PbdArgs a = pbd_args(c, dt);
+    float4* const X = c->snap;
+    float4* const XT = c->snap_xt;
+    auto x_before = [&](int it) { return X + (size_t)std::min(it, c->n_stab) * N; };
     const float4* xfix = x_before(total);     // x after stabilization
     const float4* ws = XT;                    // w of xt carries the inverse scaled mass (every pass keeps it)
     CK(gs_launch_adj_init(c->stream, N, c->lr_sorted_idx, c->adj_io, c->adj_io + N, dt, c->adj_gx, c->adj_gxt,

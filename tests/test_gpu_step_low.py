@@ -79,6 +79,9 @@ def test_full_step_small(orc, seed):
     dt = 1.0 / 240.0
     x, v, rx, rv, sus, st = run_both(orc, sc, dt, 2, sc["iters"])
     assert np.all(np.isfinite(x)) and np.all(np.isfinite(v))
+    # marks spread over the passes; these stirred cubes keep 30-73 % of the
+    # particles unmarked (pass-by-pass parity: test_gpu_step_passes.py)
+    assert (~sus).mean() >= 0.25, (~sus).mean()
     elementwise(sc, dt, x, v, rx, rv, ~sus)
     # all particles, including those behind a near-threshold decision
     L = box_size(sc)
@@ -93,6 +96,11 @@ def test_full_step_statistics(orc, case):
     dt = 1.0 / 60.0
     x, v, rx, rv, sus, st = run_both(orc, sc, dt, 2, sc["iters"])
     assert np.all(np.isfinite(x)) and np.all(np.isfinite(v))
+    # in these packed beds the marks of resting contacts spread over the
+    # eight or ten passes to all but 0.1-0.3 % of the particles, so the whole
+    # step is checked by statistics; every single pass is compared particle
+    # by particle in test_gpu_step_passes.py
+    assert (~sus).sum() >= 20, (~sus).sum()
     elementwise(sc, dt, x, v, rx, rv, ~sus)
     r = sc["r_low"]
     dx = np.linalg.norm(x[:, :3] - rx, axis=1)

@@ -416,6 +416,35 @@ int gs_step_low_forward(gs_ctx* ctx, const float* x_in, const float* v_in, float
 int gs_step_low_backward(gs_ctx* ctx, const float* x_in, const float* v_in, const float* g_x_out, const float* g_v_out,
                          float* g_x_in, float* g_v_in, float dt, int iters);
 
+/* Decision record of the reverse modes (not in the paper): where the method
+ * branches (blend case and largest weight, contact activation, static or
+ * kinetic friction, SDF contacts), gs_upsample_backward and
+ * gs_step_low_backward differentiate the branch each decision takes; with a
+ * record set they also write those decisions, so that a reference can be
+ * evaluated on exactly the same smooth piece of the method.  Device
+ * buffers, caller-owned, original particle order; every later backward call
+ * overwrites them.  Single-scene contexts only (GS_ERR_STATE otherwise).
+ *   hr_record      uint32[n_high][4] (NULL: off), per HR particle: the LR
+ *                  particle of largest weight (index, or 0xffffffff), the
+ *                  blend case (1: alpha = 1 - max w, 0: alpha = 0), bit c
+ *                  set when SDF component c is in contact, bit c set when
+ *                  the normal velocity was removed at component c (at most
+ *                  32 components; a box interior counts its six walls).
+ *   lr_candidates  int32[cap][n_low]: the candidate partners of each LR
+ *                  particle (-1 beyond its count); cap = params.max_neighbors
+ *                  (0 there means 64).
+ *   lr_pair_bits   uint8[max_passes][cap][n_low]: per pass (stabilization
+ *                  passes first) and candidate, bit 0 = contact
+ *                  (|x_ij| < 2 r_LR), bit 1 = kinetic friction scale.
+ *   lr_sdf_bits    uint8[max_passes][n_low][n_comp] (n_comp = the SDF
+ *                  components): bit 0 = contact, bit 1 = kinetic friction.
+ *   max_passes     capacity in passes; a backward call with more passes
+ *                  (n_stab + iters) returns GS_ERR_ARG.
+ * The LR pointers are all NULL (off) or all set (lr_sdf_bits may be NULL
+ * without SDFs); GS_ERR_ARG otherwise. */
+int gs_set_decision_record(gs_ctx* ctx, uint32_t* hr_record, int32_t* lr_candidates, uint8_t* lr_pair_bits,
+                           uint8_t* lr_sdf_bits, int max_passes);
+
 /* Pass-by-pass record of one LR step (Algorithm 1, Sec. 3), for checking the
  * step against a reference one Jacobi pass at a time: each pass is a
  * function of the state before it, so a pass can be compared on its own

@@ -88,6 +88,12 @@ def _L():
         L.or_upsample_vjp.argtypes = [P, P, ctypes.c_long, P, P, ctypes.c_long, P, ctypes.c_int, P, P, P,
                                       P, P, P, P]
         L.or_upsample_vjp.restype = ctypes.c_int
+        L.or_upsample_vjp_tape.argtypes = [P, P, ctypes.c_long, P, P, ctypes.c_long, P, ctypes.c_int, P, P, P, P,
+                                           P, P, P, P]
+        L.or_upsample_vjp_tape.restype = ctypes.c_int
+        L.or_pbd_step_vjp_tape.argtypes = [P, P, P, ctypes.c_long, P, ctypes.c_int, P, P, ctypes.c_long, P, P, P,
+                                           P]
+        L.or_pbd_step_vjp_tape.restype = ctypes.c_int
         L.or_pbd_step_vjp.argtypes = [P, P, P, ctypes.c_long, P, ctypes.c_int, P, P, P, P, P]
         L.or_pbd_step_vjp.restype = ctypes.c_int
         L.or_upsample_tape.argtypes = [P, P, ctypes.c_long, P, P, ctypes.c_long, P, ctypes.c_int, P, ctypes.c_int,
@@ -207,17 +213,25 @@ def upsample(lr_x, lr_v, hr_x, hr_v, sdf, prm, sub=None, mode=0, solid=None):
     return out
 
 
-def upsample_vjp(lr_x, lr_v, hr_x, hr_v, sdf, prm, gx, gv):
+def upsample_vjp(lr_x, lr_v, hr_x, hr_v, sdf, prm, gx, gv, tape=None):
     """Reverse mode of ``upsample``: given dL/dx^{t+1}, dL/dv^{t+1} returns
     (dL/dX_LR, dL/dV_LR, dL/dx_HR, dL/dv_HR) for the forward branch
-    decisions (contact normals held fixed)."""
+    decisions (contact normals held fixed), or for the decisions of a tape
+    (``upsample_tape``'s layout) when one is given."""
     lr_x, lr_v = _f64(lr_x, 3), _f64(lr_v, 3)
     hr_x, hr_v = _f64(hr_x, 3), _f64(hr_v, 3)
     sdf = _f64(sdf, SDF_STRIDE) if sdf is not None and len(sdf) else np.zeros((0, SDF_STRIDE))
     gx, gv = _f64(gx, 3), _f64(gv, 3)
     out = [np.zeros_like(lr_x), np.zeros_like(lr_v), np.zeros_like(hr_x), np.zeros_like(hr_v)]
-    rc = _L().or_upsample_vjp(_ptr(lr_x), _ptr(lr_v), len(lr_x), _ptr(hr_x), _ptr(hr_v), len(hr_x), _ptr(sdf),
-                              len(sdf), _ptr(_prm(prm, UP_KEYS)), _ptr(gx), _ptr(gv), *[_ptr(o) for o in out])
+    args = (_ptr(lr_x), _ptr(lr_v), len(lr_x), _ptr(hr_x), _ptr(hr_v), len(hr_x), _ptr(sdf), len(sdf),
+            _ptr(_prm(prm, UP_KEYS)))
+    if tape is None:
+        rc = _L().or_upsample_vjp(*args, _ptr(gx), _ptr(gv), *[_ptr(o) for o in out])
+    else:
+        tape = np.ascontiguousarray(tape, np.uint32)
+        if tape.shape != (len(hr_x), 4):
+            raise ValueError("tape does not match the HR count")
+        rc = _L().or_upsample_vjp_tape(*args, _ptr(tape), _ptr(gx), _ptr(gv), *[_ptr(o) for o in out])
     if rc != 0:
         raise RuntimeError("or_upsample_vjp failed")
     return tuple(out)
@@ -303,15 +317,24 @@ def pbd_pass(x, xt, x0, xt0, inv_m, sdf, prm, stab, mode=1):
                                          ambiguous=int(stats[4]))
 
 
-def pbd_step_vjp(x, v, inv_m, sdf, prm, gx, gv):
+def pbd_step_vjp(x, v, inv_m, sdf, prm, gx, gv, tape=None):
     """Reverse mode of ``pbd_step`` (brute-force pairs): given dL/dx_out,
     dL/dv_out returns (dL/dx, dL/dv) at the start of the step for the
-    forward pass's branch decisions."""
+    forward pass's branch decisions, or, when a tape (``pbd_step_tape``'s
+    layout) is given, for its candidate pairs and decisions."""
     x, v = _f64(x, 3), _f64(v, 3)
     inv_m = _f64(inv_m)
     sdf = _f64(sdf, SDF_STRIDE) if sdf is not None and len(sdf) else np.zeros((0, SDF_STRIDE))
     gx, gv = _f64(gx, 3), _f64(gv, 3)
     ox, ov = np.zeros_like(x), np.zeros_like(v)
+    if tape is not None:
+        tape = np.ascontiguousarray(tape, np.uint8)
+        rc = _L().or_pbd_step_vjp_tape(_ptr(x), _ptr(v), _ptr(inv_m), len(x), _ptr(sdf), len(sdf),
+                                       _ptr(_prm(prm, PB_KEYS)), _ptr(tape), tape.size, _ptr(gx), _ptr(gv), _ptr(ox),
+                                       _ptr(ov))
+        if rc != 0:
+            raise RuntimeError(f"or_pbd_step_vjp_tape failed ({rc})")
+        return ox, ov
     rc = _L().or_pbd_step_vjp(_ptr(x), _ptr(v), _ptr(inv_m), len(x), _ptr(sdf), len(sdf), _ptr(_prm(prm, PB_KEYS)),
                               _ptr(gx), _ptr(gv), _ptr(ox), _ptr(ov))
     if rc != 0:
@@ -450,22 +473,26 @@ def rollout(lr_x, lr_v, inv_m, hr_x, hr_v, sdf, pb, up, frames, n_sub=1, tapes=N
     return dict(lr_x=X, lr_v=V, hr_x=x, hr_v=v, ops=ops, tapes=out_tapes)
 
 
-def rollout_vjp(ro, inv_m, sdf, pb, up, g_hr_x, g_hr_v, g_lr_x=None, g_lr_v=None):
+def rollout_vjp(ro, inv_m, sdf, pb, up, g_hr_x, g_hr_v, g_lr_x=None, g_lr_v=None, replay=False):
     """Reverse mode of ``rollout`` by the chain rule over its operations, last
     first (``pbd_step_vjp`` and ``upsample_vjp`` at the recorded inputs).
-    Returns (dL/dlr_x, dL/dlr_v, dL/dhr_x, dL/dhr_v) at the initial state."""
+    With replay, every operation's reverse mode takes its decisions from the
+    rollout's tapes (ro["tapes"], one per operation in order): the
+    derivative of the replayed rollout.  Returns (dL/dlr_x, dL/dlr_v,
+    dL/dhr_x, dL/dhr_v) at the initial state."""
     a, b = _f64(g_hr_x, 3).copy(), _f64(g_hr_v, 3).copy()
     GX = np.zeros_like(ro["lr_x"]) if g_lr_x is None else _f64(g_lr_x, 3).copy()
     GV = np.zeros_like(ro["lr_v"]) if g_lr_v is None else _f64(g_lr_v, 3).copy()
-    for op in reversed(ro["ops"]):
+    tapes = ro["tapes"] if replay else [None] * len(ro["ops"])
+    for op, tape in zip(reversed(ro["ops"]), reversed(tapes)):
         if op[0] == "hr":
             _, X, V, x, v = op
-            gX, gV, a, b = upsample_vjp(X, V, x, v, sdf, up, a, b)
+            gX, gV, a, b = upsample_vjp(X, V, x, v, sdf, up, a, b, tape=tape)
             GX += gX
             GV += gV
         else:
             _, X, V = op
-            GX, GV = pbd_step_vjp(X, V, inv_m, sdf, pb, GX, GV)
+            GX, GV = pbd_step_vjp(X, V, inv_m, sdf, pb, GX, GV, tape=tape)
     return GX, GV, a, b
 
 

@@ -1432,9 +1432,13 @@ long or_pairs_within_grid(const double* a, long na, const double* b, long nb, do
  * and the removal of an inward normal velocity has Jacobian I - n n^T.
  * gx, gv: dL/dx^{t+1}, dL/dv^{t+1} (HR, n x 3).  Outputs (accumulated, the
  * caller zeroes them): gX, gV (LR, N x 3), ghx, ghv (HR, M x 3). */
-int or_upsample_vjp(const double* lr_x, const double* lr_v, long N, const double* hr_x, const double* hr_v, long M,
-                    const double* sdf, int n_sdf, const double* prm, const double* gx_out, const double* gv_out,
-                    double* gX, double* gV, double* ghx, double* ghv)
+/* tape (optional, uint32[M][4] of or_upsample_tape): the LR particle of
+ * largest weight, the blend case and the SDF decisions of every HR particle
+ * are taken from it, which gives the derivative of the replayed frame. */
+static int upsample_vjp_impl(const double* lr_x, const double* lr_v, long N, const double* hr_x, const double* hr_v,
+                             long M, const double* sdf, int n_sdf, const double* prm, const uint32_t* tape,
+                             const double* gx_out, const double* gv_out, double* gX, double* gV, double* ghx,
+                             double* ghv)
 {
     double r = prm[UP_R_LOW], c1 = prm[UP_C1], c2 = prm[UP_C2], dt = prm[UP_DT], rh = prm[UP_R_HIGH];
     double eps_x = prm[UP_EPS_X];
@@ -1455,10 +1459,21 @@ int or_upsample_vjp(const double* lr_x, const double* lr_v, long N, const double
             for (int m = 0; m < 3; ++m) V[m] += w * lr_v[3 * j + m];
             if (w > wmax) { wmax = w; jstar = j; }
         }
+        const uint32_t* tp = tape ? tape + 4 * i : NULL;
+        if (tp) {
+            jstar = (long)(int32_t)tp[0];
+            wmax = 0.0;
+            if (jstar >= 0 && jstar < N) {
+                double d[3] = {xi[0] - lr_x[3 * jstar], xi[1] - lr_x[3 * jstar + 1], xi[2] - lr_x[3 * jstar + 2]};
+                wmax = or_weight(dot3(d, d), r);
+            } else {
+                jstar = -1;
+            }
+        }
         double vt[3] = {0, 0, 0};
         if (S > 0)
             for (int m = 0; m < 3; ++m) vt[m] = V[m] / S;
-        int branch = (wmax <= c1) || (S > 0 && wmax >= c2 * S);
+        int branch = tp ? (int)tp[1] : (wmax <= c1) || (S > 0 && wmax >= c2 * S);
         double alpha = branch ? 1.0 - wmax : 0.0;
         double vp[3], xp[3];
         for (int m = 0; m < 3; ++m) {
@@ -1467,26 +1482,28 @@ int or_upsample_vjp(const double* lr_x, const double* lr_v, long N, const double
         }
         /* SDF rule forward, recording the normals of the active steps */
         double nrm[64][3];
-        int kind_v[64], n_steps = 0;
+        int kind_v[64], n_steps = 0, dec = 0;
         for (int s = 0; s < n_sdf; ++s) {
             const double* rec = sdf + OR_SDF_STRIDE * s;
             const double* ub = rec + 13;
             int nc = sdf_ncomp(rec);
-            for (int c = 0; c < nc; ++c) {
+            for (int c = 0; c < nc; ++c, ++dec) {
                 double phi[OR_MAX_COMP], nn[3 * OR_MAX_COMP];
                 int tie;
                 or_sdf_eval(rec, xp, phi, nn, &tie, eps_x);
-                if (!(phi[c] < rh)) continue;
+                const int active = tp ? (tp[2] >> dec) & 1u : phi[c] < rh;
+                if (!active) continue;
                 const double* n = nn + 3 * c;
                 double push = rh - phi[c];
                 for (int m = 0; m < 3; ++m) xp[m] += push * n[m];
                 double vr[3] = {vp[0] - ub[0], vp[1] - ub[1], vp[2] - ub[2]};
                 double vn = dot3(vr, n);
-                if (vn < 0)
+                const int rem = tp ? (tp[3] >> dec) & 1u : vn < 0;
+                if (rem)
                     for (int m = 0; m < 3; ++m) vp[m] -= vn * n[m];
                 if (n_steps < 64) {
                     for (int m = 0; m < 3; ++m) nrm[n_steps][m] = n[m];
-                    kind_v[n_steps] = vn < 0;
+                    kind_v[n_steps] = rem;
                     ++n_steps;
                 }
             }
@@ -1537,6 +1554,23 @@ int or_upsample_vjp(const double* lr_x, const double* lr_v, long N, const double
         }
     }
     return 0;
+}
+
+int or_upsample_vjp(const double* lr_x, const double* lr_v, long N, const double* hr_x, const double* hr_v, long M,
+                    const double* sdf, int n_sdf, const double* prm, const double* gx_out, const double* gv_out,
+                    double* gX, double* gV, double* ghx, double* ghv)
+{
+    return upsample_vjp_impl(lr_x, lr_v, N, hr_x, hr_v, M, sdf, n_sdf, prm, NULL, gx_out, gv_out, gX, gV, ghx, ghv);
+}
+
+/* Reverse mode of the HR frame replayed from a tape (uint32[M][4] of
+ * or_upsample_tape's layout). */
+int or_upsample_vjp_tape(const double* lr_x, const double* lr_v, long N, const double* hr_x, const double* hr_v,
+                         long M, const double* sdf, int n_sdf, const double* prm, const uint32_t* tape,
+                         const double* gx_out, const double* gv_out, double* gX, double* gV, double* ghx, double* ghv)
+{
+    if (!tape || total_components(sdf, n_sdf) > 32) return -1;
+    return upsample_vjp_impl(lr_x, lr_v, N, hr_x, hr_v, M, sdf, n_sdf, prm, tape, gx_out, gv_out, gX, gV, ghx, ghv);
 }
 
 /* Reverse mode of one LR step (Algorithm 1) for the branch decisions of the
@@ -1591,7 +1625,7 @@ static void m33_mul(m33* C, const m33* A, const m33* B)
 /* Friction F(rel) with tangent plane normal to e (pair) or n (SDF): value
  * and Jacobians dF/drel and dF/de (zero for SDF, where e_is_normal). */
 static void friction_jac(const double* rel, const double* e, int e_is_normal, double thr_s, double thr_k,
-                         int mode1, double mu_k, const double* u_for_thr, double* F, m33* Frel, m33* Fe)
+                         int mode1, double mu_k, const double* u_for_thr, double* F, m33* Frel, m33* Fe, int force)
 {
     double ee = dot3(e, e);
     double a = dot3(rel, e) / ee;
@@ -1609,6 +1643,7 @@ static void friction_jac(const double* rel, const double* e, int e_is_normal, do
     }
     double Lp = sqrt(dot3(perp, perp));
     int clipped = !(Lp < thr_s) && Lp > 0 && thr_k / Lp < 1.0;
+    if (force >= 0) clipped = force && Lp > 0;   /* a decision replayed from a tape */
     m33 Q;
     if (clipped) {
         double p[3] = {perp[0] / Lp, perp[1] / Lp, perp[2] / Lp};
@@ -1627,8 +1662,13 @@ static void friction_jac(const double* rel, const double* e, int e_is_normal, do
     }
 }
 
-int or_pbd_step_vjp(const double* x0, const double* v0, const double* inv_m, long N, const double* sdf, int n_sdf,
-                    const double* prm, const double* gx_out, const double* gv_out, double* gx0, double* gv0)
+/* tape (optional, the layout of or_pbd_step_tape): the candidate pairs and
+ * every pass's decisions are taken from it instead of from the comparisons,
+ * which gives the derivative of the replayed step (the smooth piece the tape
+ * was recorded on). */
+static int pbd_vjp_impl(const double* x0, const double* v0, const double* inv_m, long N, const double* sdf, int n_sdf,
+                        const double* prm, const unsigned char* tape, long tape_len, const double* gx_out,
+                        const double* gv_out, double* gx0, double* gv0)
 {
     double r = prm[PB_R], dt = prm[PB_DT];
     const double g[3] = {prm[PB_GX], prm[PB_GY], prm[PB_GZ]};
@@ -1659,8 +1699,26 @@ int or_pbd_step_vjp(const double* x0, const double* v0, const double* inv_m, lon
     or_pair *Pp = NULL, *E = NULL;
     unsigned char* border = NULL;
     long n_excl = 0;
-    long np = make_pairs(xt, N, Rc, 0, &Pp, &border, &E, &n_excl, 0.0);
-    if (np < 0) return -1;
+    long np;
+    const int nct = total_components(sdf, n_sdf);
+    if (tape) {
+        const int64_t* th = (const int64_t*)tape;
+        if (tape_len < 32 || th[1] != N || th[2] != nct || th[3] != total) return -3;
+        np = (long)th[0];
+        if (tape_len < pbd_tape_bytes(np, N, nct, total)) return -3;
+        Pp = (or_pair*)malloc((size_t)(np ? np : 1) * sizeof(or_pair));
+        border = (unsigned char*)calloc((size_t)(np ? np : 1), 1);
+        E = (or_pair*)malloc(sizeof(or_pair));
+        if (!Pp || !border || !E) return -1;
+        for (long q = 0; q < np; ++q) { Pp[q].i = (long)th[4 + 2 * q]; Pp[q].j = (long)th[5 + 2 * q]; }
+    } else {
+        np = make_pairs(xt, N, Rc, 0, &Pp, &border, &E, &n_excl, 0.0);
+        if (np < 0) return -1;
+    }
+    /* the decision bytes of pass it: one per pair, then one per (particle,
+     * SDF component); bit 0 = active, bit 1 = kinetic friction scale */
+    const unsigned char* tpass = tape ? tape + 32 + 16 * np : NULL;
+#define PASS_TAPE(it) (tpass ? tpass + (long)(it) * (np + N * (long)nct) : NULL)
     double* Xfix = NULL;
     for (int it = 0; it < total; ++it) {
         int stab = it < n_stab;
@@ -1669,11 +1727,14 @@ int or_pbd_step_vjp(const double* x0, const double* v0, const double* inv_m, lon
         memcpy(XT + (size_t)it * n1 * 3, xt, (size_t)N * 3 * sizeof(double));
         memset(D, 0, (size_t)N * 3 * sizeof(double));
         memset(cnt, 0, (size_t)N * sizeof(long));
+        const unsigned char* tp = PASS_TAPE(it);
         for (long p = 0; p < np; ++p) {
             long i = Pp[p].i, j = Pp[p].j;
             double e[3] = {y[3 * j] - y[3 * i], y[3 * j + 1] - y[3 * i + 1], y[3 * j + 2] - y[3 * i + 2]};
             double L = sqrt(dot3(e, e));
-            if (!(L < d0) || L == 0.0 || !(ws[i] + ws[j] > 0)) continue;
+            const int active = tp ? (tp[p] & 1) : L < d0;
+            const int FORCE_PAIR = tp ? (tp[p] >> 1) & 1 : -1;
+            if (!active || L == 0.0 || !(ws[i] + ws[j] > 0)) continue;
             double W = ws[i] + ws[j], mi = ws[i] / W, mj = ws[j] / W, pen = d0 - L;
             double u[3] = {e[0] / L, e[1] / L, e[2] / L};
             for (int k = 0; k < 3; ++k) {
@@ -1685,7 +1746,7 @@ int or_pbd_step_vjp(const double* x0, const double* v0, const double* inv_m, lon
                 m33 Fr, Fe;
                 for (int k = 0; k < 3; ++k) rel[k] = (xt[3 * i + k] - x[3 * i + k]) - (xt[3 * j + k] - x[3 * j + k]);
                 double base = fmode == 1 ? pen : d0;
-                friction_jac(rel, e, 0, base * mu_s, base * mu_k, fmode == 1, mu_k, u, F, &Fr, &Fe);
+                friction_jac(rel, e, 0, base * mu_s, base * mu_k, fmode == 1, mu_k, u, F, &Fr, &Fe, FORCE_PAIR);
                 for (int k = 0; k < 3; ++k) {
                     D[3 * i + k] -= mi * F[k];
                     D[3 * j + k] += mj * F[k];
@@ -1696,14 +1757,18 @@ int or_pbd_step_vjp(const double* x0, const double* v0, const double* inv_m, lon
         }
         for (long i = 0; i < N; ++i) {
             if (!(ws[i] > 0)) continue;
-            for (int s = 0; s < n_sdf; ++s) {
+            int comp0 = 0;
+            for (int s = 0; s < n_sdf; comp0 += sdf_ncomp(sdf + OR_SDF_STRIDE * s), ++s) {
                 const double* rec = sdf + OR_SDF_STRIDE * s;
                 double phi[OR_MAX_COMP], nn[3 * OR_MAX_COMP];
                 int tie;
                 int nc = or_sdf_eval(rec, y + 3 * i, phi, nn, &tie, 0.0);
                 double bmu_s = sqrt(mu_s * rec[16]), bmu_k = sqrt(mu_k * rec[17]);
                 for (int c = 0; c < nc; ++c) {
-                    if (!(phi[c] < r)) continue;
+                    const unsigned char* tb = tp ? tp + np + i * (long)nct + comp0 + c : NULL;
+                    const int active = tb ? (*tb & 1) : phi[c] < r;
+                    const int FORCE_SDF = tb ? (*tb >> 1) & 1 : -1;
+                    if (!active) continue;
                     const double* n = nn + 3 * c;
                     double pen = r - phi[c];
                     for (int k = 0; k < 3; ++k) D[3 * i + k] += pen * n[k];
@@ -1712,7 +1777,7 @@ int or_pbd_step_vjp(const double* x0, const double* v0, const double* inv_m, lon
                         m33 Fr, Fe;
                         for (int k = 0; k < 3; ++k) d[k] = (xt[3 * i + k] - x[3 * i + k]) - rec[13 + k] * dt;
                         double base = fmode == 1 ? pen : d0;
-                        friction_jac(d, n, 1, base * bmu_s, base * bmu_k, fmode == 1, bmu_k, n, F, &Fr, &Fe);
+                        friction_jac(d, n, 1, base * bmu_s, base * bmu_k, fmode == 1, bmu_k, n, F, &Fr, &Fe, FORCE_SDF);
                         for (int k = 0; k < 3; ++k) D[3 * i + k] -= F[k];
                     }
                     cnt[i]++;
@@ -1761,11 +1826,14 @@ int or_pbd_step_vjp(const double* x0, const double* v0, const double* inv_m, lon
          * the solver, w.r.t. x through the friction */
         memset(acc, 0, (size_t)N * 3 * sizeof(double));
         double* accx = stab ? NULL : (double*)calloc(n1 * 3, sizeof(double));
+        const unsigned char* tp = PASS_TAPE(it);
         for (long p = 0; p < np; ++p) {
             long i = Pp[p].i, j = Pp[p].j;
             double e[3] = {y[3 * j] - y[3 * i], y[3 * j + 1] - y[3 * i + 1], y[3 * j + 2] - y[3 * i + 2]};
             double L = sqrt(dot3(e, e));
-            if (!(L < d0) || L == 0.0 || !(ws[i] + ws[j] > 0)) continue;
+            const int active = tp ? (tp[p] & 1) : L < d0;
+            const int FORCE_PAIR = tp ? (tp[p] >> 1) & 1 : -1;
+            if (!active || L == 0.0 || !(ws[i] + ws[j] > 0)) continue;
             double W = ws[i] + ws[j], mi = ws[i] / W, mj = ws[j] / W, pen = d0 - L;
             double u[3] = {e[0] / L, e[1] / L, e[2] / L};
             const double* hi = H + 3 * i;
@@ -1792,7 +1860,7 @@ int or_pbd_step_vjp(const double* x0, const double* v0, const double* inv_m, lon
                 for (int k = 0; k < 3; ++k)
                     rel[k] = (xtp[3 * i + k] - Xfix[3 * i + k]) - (xtp[3 * j + k] - Xfix[3 * j + k]);
                 double base = fmode == 1 ? pen : d0;
-                friction_jac(rel, e, 0, base * mu_s, base * mu_k, fmode == 1, mu_k, u, F, &Fr, &Fe);
+                friction_jac(rel, e, 0, base * mu_s, base * mu_k, fmode == 1, mu_k, u, F, &Fr, &Fe, FORCE_PAIR);
                 /* c_i -= m_i F, c_j += m_j F; rel = (xt_i - x_i) - (xt_j - x_j) */
                 double hF[3] = {-mi * hi[0] + mj * hj[0], -mi * hi[1] + mj * hj[1], -mi * hi[2] + mj * hj[2]};
                 double grel[3] = {0, 0, 0}, ge[3] = {0, 0, 0};
@@ -1812,14 +1880,18 @@ int or_pbd_step_vjp(const double* x0, const double* v0, const double* inv_m, lon
         for (long i = 0; i < N; ++i) {
             if (!(ws[i] > 0)) continue;
             const double* hi = H + 3 * i;
-            for (int s = 0; s < n_sdf; ++s) {
+            int comp0 = 0;
+            for (int s = 0; s < n_sdf; comp0 += sdf_ncomp(sdf + OR_SDF_STRIDE * s), ++s) {
                 const double* rec = sdf + OR_SDF_STRIDE * s;
                 double phi[OR_MAX_COMP], nn[3 * OR_MAX_COMP];
                 int tie;
                 int nc = or_sdf_eval(rec, y + 3 * i, phi, nn, &tie, 0.0);
                 double bmu_s = sqrt(mu_s * rec[16]), bmu_k = sqrt(mu_k * rec[17]);
                 for (int c = 0; c < nc; ++c) {
-                    if (!(phi[c] < r)) continue;
+                    const unsigned char* tb = tp ? tp + np + i * (long)nct + comp0 + c : NULL;
+                    const int active = tb ? (*tb & 1) : phi[c] < r;
+                    const int FORCE_SDF = tb ? (*tb >> 1) & 1 : -1;
+                    if (!active) continue;
                     const double* n = nn + 3 * c;
                     double a = dot3(n, hi);       /* d((r - phi) n)/dy = -n n^T */
                     for (int k = 0; k < 3; ++k) acc[3 * i + k] -= a * n[k];
@@ -1829,7 +1901,7 @@ int or_pbd_step_vjp(const double* x0, const double* v0, const double* inv_m, lon
                         double pen = r - phi[c];
                         for (int k = 0; k < 3; ++k) d[k] = (xtp[3 * i + k] - Xfix[3 * i + k]) - rec[13 + k] * dt;
                         double base = fmode == 1 ? pen : d0;
-                        friction_jac(d, n, 1, base * bmu_s, base * bmu_k, fmode == 1, bmu_k, n, F, &Fr, &Fe);
+                        friction_jac(d, n, 1, base * bmu_s, base * bmu_k, fmode == 1, bmu_k, n, F, &Fr, &Fe, FORCE_SDF);
                         double gd[3] = {0, 0, 0};
                         m33_tmul_add(gd, -1.0, &Fr, hi);   /* c -= F(d) */
                         for (int k = 0; k < 3; ++k) {
@@ -1846,7 +1918,9 @@ int or_pbd_step_vjp(const double* x0, const double* v0, const double* inv_m, lon
                             double an = dot3(dd, n);
                             for (int k = 0; k < 3; ++k) perp[k] = dd[k] - an * n[k];
                             double Lq = sqrt(dot3(perp, perp));
-                            if (!(Lq < base * bmu_s) && Lq > 0 && base * bmu_k / Lq < 1.0) {
+                            const int clip = FORCE_SDF >= 0 ? FORCE_SDF && Lq > 0
+                                                            : (!(Lq < base * bmu_s) && Lq > 0 && base * bmu_k / Lq < 1.0);
+                            if (clip) {
                                 /* F = pen mu_k perp/|perp|, dpen/dy = -n^T */
                                 double q = dot3(perp, hi) / Lq;
                                 for (int k = 0; k < 3; ++k) acc[3 * i + k] += q * bmu_k * n[k];
@@ -1876,5 +1950,22 @@ int or_pbd_step_vjp(const double* x0, const double* v0, const double* inv_m, lon
     }
     free(x); free(xt); free(ws); free(Y); free(XT); free(D); free(cnt); free(CNT); free(Pp); free(E); free(border);
     free(Xfix); free(gxt); free(gx); free(gws); free(H); free(acc);
+#undef PASS_TAPE
     return 0;
+}
+
+int or_pbd_step_vjp(const double* x0, const double* v0, const double* inv_m, long N, const double* sdf, int n_sdf,
+                    const double* prm, const double* gx_out, const double* gv_out, double* gx0, double* gv0)
+{
+    return pbd_vjp_impl(x0, v0, inv_m, N, sdf, n_sdf, prm, NULL, 0, gx_out, gv_out, gx0, gv0);
+}
+
+/* Reverse mode of the step replayed from a tape of or_pbd_step_tape's
+ * layout (candidate pairs and every pass's decisions from the tape). */
+int or_pbd_step_vjp_tape(const double* x0, const double* v0, const double* inv_m, long N, const double* sdf,
+                         int n_sdf, const double* prm, const unsigned char* tape, long tape_len, const double* gx_out,
+                         const double* gv_out, double* gx0, double* gv0)
+{
+    if (!tape) return -1;
+    return pbd_vjp_impl(x0, v0, inv_m, N, sdf, n_sdf, prm, tape, tape_len, gx_out, gv_out, gx0, gv0);
 }

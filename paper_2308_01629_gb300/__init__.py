@@ -109,6 +109,7 @@ _SIGS = {
     "gs_step_low_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int]),
     "gs_step_low_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int]),
     "gs_step_low_trace": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, ctypes.c_int, _P, _P, ctypes.c_int]),
+    "gs_set_decision_record": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
 }
 
 _lib = None
@@ -319,6 +320,10 @@ def gs_step_low_forward(ctx, x_in, v_in, x_out, v_out, dt, iters):
 
 def gs_step_low_backward(ctx, x_in, v_in, g_x_out, g_v_out, g_x_in, g_v_in, dt, iters):
     return lib().gs_step_low_backward(ctx, x_in, v_in, g_x_out, g_v_out, g_x_in, g_v_in, dt, iters)
+
+
+def gs_set_decision_record(ctx, hr_record, lr_candidates, lr_pair_bits, lr_sdf_bits, max_passes):
+    return lib().gs_set_decision_record(ctx, hr_record, lr_candidates, lr_pair_bits, lr_sdf_bits, max_passes)
 
 
 def gs_step_low_trace(ctx, x_in, v_in, dt, iters, x_trace, xt_trace, n_records):

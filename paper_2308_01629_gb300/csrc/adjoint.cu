@@ -37,12 +37,17 @@ __device__ __forceinline__ int cell_of(float x, float o, float inv_h, int dim)
 
 constexpr int kMaxSteps = 32;
 
+// rec (optional): the decisions this reverse mode differentiates, four words
+// per HR particle: the LR particle of largest weight (original index through
+// lr_idx, or all ones), the blend case (1: alpha = 1 - max w), bit c = SDF
+// component c in contact, bit c = normal velocity removed at component c.
 __global__ void k_upsample_bwd(const SceneDev* __restrict__ scenes, const gs_sdf* __restrict__ sdf,
                                const float4* __restrict__ lr_spos, const float4* __restrict__ lr_svel,
                                const uint32_t* __restrict__ cell_start, const float4* __restrict__ hx,
                                const float4* __restrict__ hv, const float4* __restrict__ gxo,
                                const float4* __restrict__ gvo, float4* __restrict__ ghx, float4* __restrict__ ghv,
-                               float* __restrict__ gXs, float* __restrict__ gVs, int64_t m, float dt)
+                               float* __restrict__ gXs, float* __restrict__ gVs, int64_t m, float dt,
+                               uint32_t* __restrict__ rec, const uint32_t* __restrict__ lr_idx)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
@@ -94,13 +99,15 @@ __global__ void k_upsample_bwd(const SceneDev* __restrict__ scenes, const gs_sdf
     float xpx = p.x + dt * vpx, xpy = p.y + dt * vpy, xpz = p.z + dt * vpz;
     float nx_[kMaxSteps], ny_[kMaxSteps], nz_[kMaxSteps];
     bool vrem[kMaxSteps];
-    int n_steps = 0;
+    int n_steps = 0, dec = 0;
+    uint32_t act_bits = 0u, rem_bits = 0u;
     for (int s = 0; s < sc.n_sdf; ++s) {
         const gs_sdf& bsdf = sdf[sc.sdf_begin + s];
         const int nc = sdf_components(bsdf.kind);
-        for (int c = 0; c < nc; ++c) {
+        for (int c = 0; c < nc; ++c, ++dec) {
             const SdfHit h = sdf_eval(bsdf, c, xpx, xpy, xpz);
             if (!(h.phi < sc.r_high)) continue;
+            if (dec < 32) act_bits |= 1u << dec;
             const float push = sc.r_high - h.phi;
             xpx += push * h.nx;
             xpy += push * h.ny;
@@ -110,6 +117,7 @@ __global__ void k_upsample_bwd(const SceneDev* __restrict__ scenes, const gs_sdf
                 vpx -= vn * h.nx;
                 vpy -= vn * h.ny;
                 vpz -= vn * h.nz;
+                if (dec < 32) rem_bits |= 1u << dec;
             }
             if (n_steps < kMaxSteps) {
                 nx_[n_steps] = h.nx;
@@ -119,6 +127,12 @@ __global__ void k_upsample_bwd(const SceneDev* __restrict__ scenes, const gs_sdf
                 ++n_steps;
             }
         }
+    }
+    if (rec) {
+        rec[4 * i + 0] = jstar != 0xffffffffu ? lr_idx[jstar] : 0xffffffffu;
+        rec[4 * i + 1] = branch ? 1u : 0u;
+        rec[4 * i + 2] = act_bits;
+        rec[4 * i + 3] = rem_bits;
     }
     // reverse
     float4 go = gxo[i], gw = gvo[i];
@@ -234,7 +248,7 @@ __device__ __forceinline__ M3 m3_mul(const M3& A, const M3& B)
 
 // F and its Jacobians with respect to rel and e (e_is_normal: SDF, e = n).
 __device__ void fric_jac(const float* rel, const float* e, float ee, bool e_is_normal, float thr_s, float thr_k,
-                         bool mode1, float mu_k, const float* u, float* F, M3& Fr, M3& Fe)
+                         bool mode1, float mu_k, const float* u, float* F, M3& Fr, M3& Fe, bool* kinetic = nullptr)
 {
     const Tangent tg = tangent_part(rel[0], rel[1], rel[2], e[0], e[1], e[2], ee);
     const float perp[3] = {tg.tx, tg.ty, tg.tz};
@@ -253,6 +267,7 @@ __device__ void fric_jac(const float* rel, const float* e, float ee, bool e_is_n
     }
     const float Lp = tg.L;
     const bool clipped = !(Lp < thr_s) && Lp > 0.0f && thr_k / Lp < 1.0f;
+    if (kinetic) *kinetic = clipped;
     if (clipped) {
         const float pu[3] = {perp[0] / Lp, perp[1] / Lp, perp[2] / Lp};
         M3 Q;
@@ -324,11 +339,17 @@ __global__ void k_adj_h(const PbdArgs a, int stab, const float4* __restrict__ Y,
     H[p] = make_float4(up.x * inv, up.y * inv, up.z * inv, 0.0f);
 }
 
+// rec (optional): the decisions of this pass that the reverse mode
+// differentiates, in original particle order (rec.idx: slot -> particle):
+// for candidate k of particle i, cand[k n + i] = the partner's index and
+// pair[k n + i] = bit 0 contact (|x_ij| < 2 r_LR), bit 1 kinetic friction
+// scale; for SDF component c, sdf[i n_comp + c] = bit 0 contact, bit 1
+// kinetic friction scale.  Entries of absent candidates: index -1, bits 0.
 __global__ void k_adj_pass(const PbdArgs a, int stab, const float4* __restrict__ Y, const float4* __restrict__ XT,
                            const float4* __restrict__ XF, const float4* __restrict__ WS,
                            const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ cnt,
                            const float4* __restrict__ H, float4* __restrict__ gx, float4* __restrict__ gxt,
-                           float* __restrict__ gws)
+                           float* __restrict__ gws, const AdjRecord rec)
 {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.n) return;
@@ -341,10 +362,22 @@ __global__ void k_adj_pass(const PbdArgs a, int stab, const float4* __restrict__
     float acc[3] = {0.f, 0.f, 0.f}, accx[3] = {0.f, 0.f, 0.f}, gw = 0.0f;
     const float4 xtp = XT[p], xfp = XF[p];
     const int nc = (int)cnt[p];
+    const int64_t ri = rec.pair ? (int64_t)rec.idx[p] : 0;
+    if (rec.pair)
+        for (int k = nc; k < rec.cap; ++k) {
+            rec.cand[(int64_t)k * a.n + ri] = -1;
+            rec.pair[(int64_t)k * a.n + ri] = 0;
+        }
     for (int k = 0; k < nc; ++k) {
         const uint32_t q = nbr[(int64_t)k * a.n + p];
         const float4 yq = Y[q];
         const PairGeo g = pair_geo(yp, yq);
+        uint8_t* rb = nullptr;
+        if (rec.pair) {
+            rec.cand[(int64_t)k * a.n + ri] = (int32_t)rec.idx[q];
+            rb = rec.pair + (int64_t)k * a.n + ri;
+            *rb = g.d < d0 ? 1 : 0;
+        }
         if (!(g.d < d0) || g.d2 == 0.0f) continue;
         const float wq = WS[q].w;
         const float W = wp + wq;
@@ -372,8 +405,10 @@ __global__ void k_adj_pass(const PbdArgs a, int stab, const float4* __restrict__
             const float base = sc.friction_mode == 1 ? pen : d0;
             float F[3];
             M3 Fr, Fe;
+            bool kin = false;
             fric_jac(rel, e, g.d2, false, base * sc.mu_s, base * sc.mu_k, sc.friction_mode == 1, sc.mu_k, u, F, Fr,
-                     Fe);
+                     Fe, &kin);
+            if (rb && kin) *rb |= 2;
             const float hF[3] = {-mp * hp[0] + mq * hq[0], -mp * hp[1] + mq * hq[1], -mp * hp[2] + mq * hq[2]};
             float grel[3] = {0.f, 0.f, 0.f}, ge[3] = {0.f, 0.f, 0.f};
             m3_tmul_add(grel, 1.0f, Fr, hF);
@@ -387,14 +422,19 @@ __global__ void k_adj_pass(const PbdArgs a, int stab, const float4* __restrict__
             gw += -(wq / (W * W)) * Fh;
         }
     }
+    if (rec.sdf)
+        for (int c = 0; c < rec.n_comp; ++c) rec.sdf[ri * rec.n_comp + c] = 0;
     if (wp > 0.0f) {
+        int gc = 0;
         for (int s = 0; s < sc.n_sdf; ++s) {
             const gs_sdf& b = a.sdf[sc.sdf_begin + s];
             const int ncomp = sdf_components(b.kind);
             const float bmu_s = sqrtf(sc.mu_s * b.mu_s), bmu_k = sqrtf(sc.mu_k * b.mu_k);
-            for (int c = 0; c < ncomp; ++c) {
+            for (int c = 0; c < ncomp; ++c, ++gc) {
                 const SdfHit h = sdf_eval(b, c, yp.x, yp.y, yp.z);
                 if (!(h.phi < sc.r_low)) continue;
+                uint8_t* sb = (rec.sdf && gc < rec.n_comp) ? rec.sdf + ri * rec.n_comp + gc : nullptr;
+                if (sb) *sb = 1;
                 const float n[3] = {h.nx, h.ny, h.nz};
                 const float an = n[0] * hp[0] + n[1] * hp[1] + n[2] * hp[2];
                 acc[0] -= an * n[0];
@@ -407,7 +447,9 @@ __global__ void k_adj_pass(const PbdArgs a, int stab, const float4* __restrict__
                     const float base = sc.friction_mode == 1 ? pen : d0;
                     float F[3];
                     M3 Fr, Fe;
-                    fric_jac(dv, n, 1.0f, true, base * bmu_s, base * bmu_k, false, bmu_k, n, F, Fr, Fe);
+                    bool kin = false;
+                    fric_jac(dv, n, 1.0f, true, base * bmu_s, base * bmu_k, false, bmu_k, n, F, Fr, Fe, &kin);
+                    if (sb && kin) *sb |= 2;
                     float gd[3] = {0.f, 0.f, 0.f};
                     m3_tmul_add(gd, -1.0f, Fr, hp);
 #pragma unroll
@@ -460,12 +502,13 @@ __global__ void k_adj_final(const PbdArgs a, const uint32_t* __restrict__ idx, c
 cudaError_t gs_launch_upsample_bwd(cudaStream_t s, const SceneDev* scenes, const gs_sdf* sdf, const float4* lr_spos,
                                    const float4* lr_svel, const uint32_t* cell_start, const float4* hx,
                                    const float4* hv, const float4* gxo, const float4* gvo, float4* ghx, float4* ghv,
-                                   float4* gXs, float4* gVs, int64_t m, float dt, int64_t* launches)
+                                   float4* gXs, float4* gVs, int64_t m, float dt, int64_t* launches, uint32_t* rec,
+                                   const uint32_t* lr_idx)
 {
     if (m <= 0) return cudaSuccess;
     k_upsample_bwd<<<gs_blocks(m, 128), 128, 0, s>>>(scenes, sdf, lr_spos, lr_svel, cell_start, hx, hv, gxo, gvo, ghx,
                                                       ghv, reinterpret_cast<float*>(gXs),
-                                                      reinterpret_cast<float*>(gVs), m, dt);
+                                                      reinterpret_cast<float*>(gVs), m, dt, rec, lr_idx);
     *launches += 1;
     return cudaGetLastError();
 }
@@ -490,11 +533,11 @@ cudaError_t gs_launch_adj_init(cudaStream_t s, int64_t n, const uint32_t* idx, c
 
 cudaError_t gs_launch_adj_pass(cudaStream_t s, const PbdArgs& a, int stab, const float4* Y, const float4* XT,
                                const float4* XF, const float4* WS, const uint32_t* nbr, const uint32_t* cnt, float4* H,
-                               float4* gx, float4* gxt, float* gws, int64_t* launches)
+                               float4* gx, float4* gxt, float* gws, int64_t* launches, const AdjRecord& rec)
 {
     if (a.n <= 0) return cudaSuccess;
     k_adj_h<<<gs_blocks(a.n, 128), 128, 0, s>>>(a, stab, Y, WS, nbr, cnt, gx, gxt, H);
-    k_adj_pass<<<gs_blocks(a.n, 128), 128, 0, s>>>(a, stab, Y, XT, XF, WS, nbr, cnt, H, gx, gxt, gws);
+    k_adj_pass<<<gs_blocks(a.n, 128), 128, 0, s>>>(a, stab, Y, XT, XF, WS, nbr, cnt, H, gx, gxt, gws, rec);
     *launches += 2;
     return cudaGetLastError();
 }

@@ -1872,7 +1872,8 @@ static int upsample_bwd_seq(gs_ctx* c, float dt)
     st = bin_low_impl(c);
     if (st) return st;
     CK(gs_launch_upsample_bwd(c->stream, c->d_scenes, c->d_sdf, c->lr_spos, c->lr_svel, c->lr_cell_start, F, F + M,
-                              F + 2 * M, F + 3 * M, F + 4 * M, F + 5 * M, c->gXs, c->gVs, M, dt, &c->launches),
+                              F + 2 * M, F + 3 * M, F + 4 * M, F + 5 * M, c->gXs, c->gVs, M, dt, &c->launches,
+                              c->rec_hr, c->lr_sorted_idx),
        "upsample backward");
     CK(gs_launch_scatter2(c->stream, c->lr_sorted_idx, c->gXs, c->gVs, G, G + N, N, &c->launches), "scatter");
     return GS_OK;
@@ -1940,6 +1941,37 @@ int gs_step_low_forward(gs_ctx* c, const float* x_in, const float* v_in, float* 
     c->lr_binned = false;
     CK(cudaMemcpyAsync(x_out, c->lr_pos, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
     CK(cudaMemcpyAsync(v_out, c->lr_vel, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    return GS_OK;
+}
+
+// SDF components of the context's SDFs (a box interior counts its six walls).
+static int sdf_component_count(const gs_ctx* c)
+{
+    int n = 0;
+    for (const gs_sdf& b : c->sdf_host)
+        n += b.kind == GS_SDF_BOX_INTERIOR ? 6 : ((b.kind == GS_SDF_CONE_SHELL || b.kind == GS_SDF_SOLID_BOX) ? 1 : 0);
+    return n;
+}
+
+int gs_set_decision_record(gs_ctx* c, uint32_t* hr_record, int32_t* lr_candidates, uint8_t* lr_pair_bits,
+                           uint8_t* lr_sdf_bits, int max_passes)
+{
+    int st = check_state(c);
+    if (st) return st;
+    st = settle(c);
+    if (st) return st;
+    if (c->n_scenes != 1) return fail(c, GS_ERR_STATE, "the decision record serves single-scene contexts");
+    const bool lr_any = lr_candidates || lr_pair_bits || lr_sdf_bits;
+    if (lr_any && (!lr_candidates || !lr_pair_bits || max_passes < 1 ||
+                   (sdf_component_count(c) > 0 && !lr_sdf_bits)))
+        return fail(c, GS_ERR_ARG, "the LR record needs candidates, pair bits, SDF bits and max_passes >= 1");
+    if (hr_record && sdf_component_count(c) > 32) return fail(c, GS_ERR_ARG, "more than 32 SDF components");
+    c->rec_hr = hr_record;
+    c->rec_lr_cand = lr_any ? lr_candidates : nullptr;
+    c->rec_lr_pair = lr_any ? lr_pair_bits : nullptr;
+    c->rec_lr_sdf = lr_any ? lr_sdf_bits : nullptr;
+    c->rec_max_passes = lr_any ? max_passes : 0;
+    drop_graphs(c);   // captured reverse sequences hold the previous record pointers
     return GS_OK;
 }
 
@@ -2014,6 +2046,8 @@ int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const 
     const int64_t N = c->n_low;
     if (N == 0) return GS_OK;
     if (!x_in || !v_in || !g_x_out || !g_v_out || !g_x_in || !g_v_in) return fail(c, GS_ERR_ARG, "null buffer");
+    if (c->rec_lr_pair && c->n_stab + iters > c->rec_max_passes)
+        return fail(c, GS_ERR_ARG, "%d passes exceed the decision record's %d", c->n_stab + iters, c->rec_max_passes);
     st = ensure_snapshots(c, c->n_stab + iters);
     if (st) return st;
     if (!c->adj_gx) {
@@ -2092,9 +2126,19 @@ static int step_low_reverse(gs_ctx* c, float dt, int iters)
        "reverse init");
     for (int it = total - 1; it >= 0; --it) {
         const int stab = it < c->n_stab;
+        AdjRecord rec;
+        if (c->rec_lr_pair) {
+            const int n_comp = sdf_component_count(c);
+            rec.idx = c->lr_sorted_idx;
+            rec.cand = c->rec_lr_cand;
+            rec.pair = c->rec_lr_pair + (size_t)it * c->nbr_cap * N;
+            rec.sdf = n_comp > 0 ? c->rec_lr_sdf + (size_t)it * N * n_comp : nullptr;
+            rec.cap = c->nbr_cap;
+            rec.n_comp = n_comp;
+        }
         CK(gs_launch_adj_pass(c->stream, a, stab, stab ? x_before(it) : XT + (size_t)it * N, XT + (size_t)it * N,
                               xfix, ws,
-                              c->nbr, c->nbr_cnt, c->adj_h, c->adj_gx, c->adj_gxt, c->adj_gws, &c->launches),
+                              c->nbr, c->nbr_cnt, c->adj_h, c->adj_gx, c->adj_gxt, c->adj_gws, &c->launches, rec),
            "reverse pass");
     }
     CK(gs_launch_adj_final(c->stream, a, c->lr_sorted_idx, ws, c->adj_gx, c->adj_gxt, c->adj_gws, c->adj_io + 2 * N,

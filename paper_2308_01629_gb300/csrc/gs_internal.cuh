@@ -208,6 +208,12 @@ struct gs_ctx {
     float* adj_gws = nullptr;
     float4* adj_io = nullptr;      // [4][n_low]: dL/dx_out, dL/dv_out in; dL/dx_in, dL/dv_in out (original order)
     float4* fscratch = nullptr;    // [6][n_high] + [2][n_low]: the functional upsampling entries' in/out copies
+    // decision record of the reverse modes (gs_set_decision_record); null: off
+    uint32_t* rec_hr = nullptr;
+    int32_t* rec_lr_cand = nullptr;
+    uint8_t* rec_lr_pair = nullptr;
+    uint8_t* rec_lr_sdf = nullptr;
+    int rec_max_passes = 0;
     std::vector<GraphEntry> fgraphs;   // graphs of the functional LR step entry points
 
     // radix sort histogram scratch (HR reorder, static-scratch binning)
@@ -420,17 +426,32 @@ cudaError_t gs_launch_cfl_pick(cudaStream_t s, CflState* st, float dt_max, float
                                cudaGraphConditionalHandle h, int in_graph, unsigned body_kernels, int64_t* launches);
 
 // adjoint.cu
+// rec (optional): uint32[m][4] decisions of the HR frame's reverse mode in
+// original LR indices (lr_idx: cell-ordered slot -> LR particle).
 cudaError_t gs_launch_upsample_bwd(cudaStream_t s, const SceneDev* scenes, const gs_sdf* sdf, const float4* lr_spos,
                                    const float4* lr_svel, const uint32_t* cell_start, const float4* hx,
                                    const float4* hv, const float4* gxo, const float4* gvo, float4* ghx, float4* ghv,
-                                   float4* gXs, float4* gVs, int64_t m, float dt, int64_t* launches);
+                                   float4* gXs, float4* gVs, int64_t m, float dt, int64_t* launches,
+                                   uint32_t* rec = nullptr, const uint32_t* lr_idx = nullptr);
+// Decisions of one pass of the LR step's reverse mode, in original particle
+// order (idx: slot -> particle): cand / pair [cap][n], sdf [n][n_comp]
+// (gs_set_decision_record).  All null: nothing is recorded.
+struct AdjRecord {
+    const uint32_t* idx = nullptr;
+    int32_t* cand = nullptr;
+    uint8_t* pair = nullptr;
+    uint8_t* sdf = nullptr;
+    int cap = 0;
+    int n_comp = 0;
+};
 cudaError_t gs_launch_scatter2(cudaStream_t s, const uint32_t* idx, const float4* a, const float4* b, float4* ao,
                                float4* bo, int64_t n, int64_t* launches);
 cudaError_t gs_launch_adj_init(cudaStream_t s, int64_t n, const uint32_t* idx, const float4* gxo, const float4* gvo,
                                float dt, float4* gx, float4* gxt, float* gws, int64_t* launches);
 cudaError_t gs_launch_adj_pass(cudaStream_t s, const PbdArgs& a, int stab, const float4* Y, const float4* XT,
                                const float4* XF, const float4* WS, const uint32_t* nbr, const uint32_t* cnt, float4* H,
-                               float4* gx, float4* gxt, float* gws, int64_t* launches);
+                               float4* gx, float4* gxt, float* gws, int64_t* launches,
+                               const AdjRecord& rec = AdjRecord{});
 cudaError_t gs_launch_adj_final(cudaStream_t s, const PbdArgs& a, const uint32_t* idx, const float4* WS,
                                 const float4* gx, const float4* gxt, const float* gws, float4* gx0, float4* gv0,
                                 int64_t* launches);

@@ -194,19 +194,78 @@ def _f64(t):
     return t.cpu().numpy()[:, :3].astype(np.float64)
 
 
+def _lr_tape(cand, pair, sdfb, n):
+    """The oracle's LR-step tape (pbd_step_tape's layout) from the decision
+    record of one GPU reverse step: every candidate pair once (i < j) with
+    its per-pass bits, then the per-pass SDF bits."""
+    k, i = np.nonzero(cand >= 0)
+    j = cand[k, i].astype(np.int64)
+    sel = i < j
+    k, i, j = k[sel], i[sel], j[sel]
+    order = np.lexsort((j, i))
+    k, i, j = k[order], i[order], j[order]
+    passes, ncomp = pair.shape[0], sdfb.shape[2]
+    head = np.array([len(i), n, ncomp, passes], np.int64)
+    parts = [head.view(np.uint8), np.stack([i, j], 1).astype(np.int64).ravel().view(np.uint8)]
+    for q in range(passes):
+        parts.append(np.ascontiguousarray(pair[q][k, i]))
+        parts.append(np.ascontiguousarray(sdfb[q]).ravel())
+    return np.concatenate(parts)
+
+
+def _gpu_decision_tapes(gs, g, sc, ops, iters, n_stab=2):
+    """Oracle tapes of the decisions the GPU's reverse modes take at every
+    operation of its own rollout (gs_set_decision_record)."""
+    import torch
+    n, m = len(sc["lr_pos"]), len(sc["hr_pos"])
+    cap, passes = 64, n_stab + iters
+    ncomp = sum(6 if s["kind"] == scenes.SDF_BOX_INTERIOR else 1 for s in sc["sdfs"])
+    hr = torch.zeros((m, 4), dtype=torch.int32, device="cuda")
+    cand = torch.zeros((cap, n), dtype=torch.int32, device="cuda")
+    pair = torch.zeros((passes, cap, n), dtype=torch.uint8, device="cuda")
+    sdfb = torch.zeros((passes, n, max(ncomp, 1)), dtype=torch.uint8, device="cuda")
+    rc = gs.gs_set_decision_record(g.ctx, hr.data_ptr(), cand.data_ptr(), pair.data_ptr(), sdfb.data_ptr(), passes)
+    assert rc == gs.GS_OK, gs.gs_last_error(g.ctx)
+    zl, zh = torch.zeros((n, 4), device="cuda"), torch.zeros((m, 4), device="cuda")
+    o1, o2 = torch.empty((n, 4), device="cuda"), torch.empty((n, 4), device="cuda")
+    h1, h2 = torch.empty((m, 4), device="cuda"), torch.empty((m, 4), device="cuda")
+    dt = float(np.float32(sc["dt"]))
+    tapes = []
+    for op in ops:
+        if op[0] == "lr":
+            _, X, V = op
+            rc = gs.gs_step_low_backward(g.ctx, X.data_ptr(), V.data_ptr(), zl.data_ptr(), zl.data_ptr(),
+                                         o1.data_ptr(), o2.data_ptr(), dt, iters)
+            assert rc == gs.GS_OK, gs.gs_last_error(g.ctx)
+            g.sync()
+            tapes.append(_lr_tape(cand.cpu().numpy(), pair.cpu().numpy(), sdfb.cpu().numpy()[:, :, :ncomp], n))
+        else:
+            _, X, V, x, v = op
+            rc = gs.gs_upsample_backward(g.ctx, X.data_ptr(), V.data_ptr(), x.data_ptr(), v.data_ptr(), zh.data_ptr(),
+                                         zh.data_ptr(), o1.data_ptr(), o2.data_ptr(), h1.data_ptr(), h2.data_ptr(), dt)
+            assert rc == gs.GS_OK, gs.gs_last_error(g.ctx)
+            g.sync()
+            tapes.append(hr.cpu().numpy().view(np.uint32).copy())
+    assert gs.gs_set_decision_record(g.ctx, None, None, None, None, 0) == gs.GS_OK
+    return tapes
+
+
 def test_rollout_gradient_config4_matches_oracle(orc):
     """Falling column, 4k LR / 64k HR, 30 steps, checkpoints every 5: the GPU
-    gradient of the loss w.r.t. the initial LR velocities against the oracle.
+    gradient of the loss w.r.t. the initial LR velocities against the
+    oracle's analytic gradient on the same smooth piece of the method.
 
-    The oracle's analytic gradient equals central differences (eps 1e-4) of
-    its decision-replayed rollout to 1e-6.  The float32 rollout follows a
-    different smooth piece of the method: resting contacts sit at
-    |x_ij| = 2 r_LR, where the contact test is decided by rounding, and an
-    active contact at zero penetration still contributes the rank-one
-    Jacobian -u u^T and changes n_i.  The end-to-end difference is therefore
-    bounded by what those decisions move (measured: 2.4e-2 on the directional
-    derivative, 8e-2 in L2), not by the kernels, which match the oracle per
-    operation at the same states (test_stepwise_reverse_along_config4_trajectory)."""
+    The method is piecewise smooth: resting contacts sit at |x_ij| = 2 r_LR,
+    where the contact test is decided by rounding, and an active contact at
+    zero penetration still contributes the rank-one Jacobian -u u^T and
+    changes n_i.  The float32 rollout and the FP64 one therefore take some
+    of these decisions differently and differentiate different pieces
+    (measured: 2.4e-2 apart on the directional derivative, 8e-2 in L2).  The
+    GPU's reverse modes record the decisions they differentiate at every
+    operation of the GPU's own rollout; the oracle replays them in its FP64
+    rollout and in its reverse modes, and the GPU gradient must equal that
+    analytic gradient within 1e-3, which central differences (eps 1e-4) of
+    the replayed oracle rollout confirm."""
     import torch
 
     import paper_2308_01629_gb300 as gs
@@ -230,30 +289,53 @@ def test_rollout_gradient_config4_matches_oracle(orc):
     sdf = scenes.sdf_table(sc["sdfs"])
     T = T32.astype(float)
     X0, V0, x0, v0 = (sc[k][:, :3].astype(float) for k in ("lr_pos", "lr_vel", "hr_pos", "hr_vel"))
-    ro = orc.rollout(X0, V0, im, x0, v0, sdf, pb, up, sc["steps"])
-    _, gv_or, _, _ = orc.rollout_vjp(ro, im, sdf, pb, up, 2.0 * (ro["hr_x"] - T), np.zeros_like(T))
     rng = np.random.default_rng(23)
     d = rng.normal(size=V0.shape)
     eps = 1e-4
-    lp = ((orc.rollout(X0, V0 + eps * d, im, x0, v0, sdf, pb, up, sc["steps"], tapes=ro["tapes"])["hr_x"] - T) ** 2)
-    lm = ((orc.rollout(X0, V0 - eps * d, im, x0, v0, sdf, pb, up, sc["steps"], tapes=ro["tapes"])["hr_x"] - T) ** 2)
-    fd = (lp.sum() - lm.sum()) / (2 * eps)
-    # the oracle's own reverse mode along the GPU's float32 trajectory
+
+    def fd_of(tapes):
+        lp = orc.rollout(X0, V0 + eps * d, im, x0, v0, sdf, pb, up, sc["steps"], tapes=tapes)["hr_x"]
+        lm = orc.rollout(X0, V0 - eps * d, im, x0, v0, sdf, pb, up, sc["steps"], tapes=tapes)["hr_x"]
+        return (((lp - T) ** 2).sum() - ((lm - T) ** 2).sum()) / (2 * eps)
+
+    # the oracle's own piece (its FP64 decisions), for the record
+    ro = orc.rollout(X0, V0, im, x0, v0, sdf, pb, up, sc["steps"])
+    _, gv_or, _, _ = orc.rollout_vjp(ro, im, sdf, pb, up, 2.0 * (ro["hr_x"] - T), np.zeros_like(T))
+    fd_own = fd_of(ro["tapes"])
+    # the GPU's piece: its reverse modes' decisions along its own rollout
     ops, Xg, Vg, xg = _gpu_forward_states(g, sc)
-    ops = [(o[0],) + tuple(_f64(t) for t in o[1:]) for o in ops]
-    _, gv_along, _, _ = orc.rollout_vjp(dict(ops=ops, lr_x=_f64(Xg), lr_v=_f64(Vg)), im, sdf, pb, up,
-                                        2.0 * (_f64(xg) - T), np.zeros_like(T))
-    dir_gpu = float((gv_gpu * d).sum())
-    report = dict(fd=fd, dir_gpu=dir_gpu, dir_oracle=float((gv_or * d).sum()),
-                  rel_dir_fd=abs(dir_gpu - fd) / abs(fd), rel_l2_oracle=_rel(gv_gpu, gv_or),
-                  rel_l2_along=_rel(gv_gpu, gv_along), norm=float(np.linalg.norm(gv_or)))
-    report["rel_oracle_fd"] = abs(report["dir_oracle"] - fd) / abs(fd)
+    tapes = _gpu_decision_tapes(gs, g, sc, ops, sc["iters"])
+    rg = orc.rollout(X0, V0, im, x0, v0, sdf, pb, up, sc["steps"], tapes=tapes)
+    _, gv_piece, _, _ = orc.rollout_vjp(rg, im, sdf, pb, up, 2.0 * (rg["hr_x"] - T), np.zeros_like(T), replay=True)
+    fd_piece = fd_of(tapes)
+    dir_gpu, dir_piece = float((gv_gpu * d).sum()), float((gv_piece * d).sum())
+    report = dict(dir_gpu=dir_gpu, dir_piece=dir_piece, fd_piece=fd_piece,
+                  rel_l2_piece=_rel(gv_gpu, gv_piece), rel_dir_piece=abs(dir_gpu - dir_piece) / abs(dir_piece),
+                  rel_piece_fd=abs(dir_piece - fd_piece) / abs(fd_piece),
+                  rel_oracle_fd=abs(float((gv_or * d).sum()) - fd_own) / abs(fd_own),
+                  rel_l2_own_piece=_rel(gv_gpu, gv_or), rel_dir_own_fd=abs(dir_gpu - fd_own) / abs(fd_own),
+                  norm=float(np.linalg.norm(gv_piece)))
+    # the replayed FP64 rollout follows the GPU's float32 one: float32
+    # rounding accumulates to about 1e-3 r_LR over the 30 steps (measured:
+    # 99th percentile 1.1e-5 m, r_LR = 0.01 m), and a rare HR particle moves
+    # further where the upsampling forward and its reverse, which evaluate
+    # the weights in different float32 forms, decide a threshold differently
+    gap = np.linalg.norm(rg["hr_x"] - _f64(xg), axis=1)
+    lgap = np.linalg.norm(rg["lr_x"] - _f64(Xg), axis=1)
+    report.update(hr_gap_q=[float(q) for q in np.quantile(gap, [0.5, 0.99, 0.999, 1.0])],
+                  lr_gap_q=[float(q) for q in np.quantile(lgap, [0.5, 0.99, 0.999, 1.0])],
+                  hr_gap_frac=float((gap > 1e-5).mean()), lr_gap_max=float(lgap.max()))
+    r = sc["r_low"]
     print("config4", report)
     g.close()
+    # the oracle's analytic gradient is the derivative of its replayed rollout
     assert report["rel_oracle_fd"] <= 1e-6, report
-    assert report["rel_dir_fd"] <= 5e-2, report
-    assert report["rel_l2_along"] <= 8e-2, report
-    assert report["rel_l2_oracle"] <= 0.15, report
+    assert report["rel_piece_fd"] <= 1e-6, report
+    assert report["hr_gap_q"][1] <= 5e-3 * r and report["hr_gap_q"][3] <= 5e-2 * r, report
+    assert report["lr_gap_max"] <= 5e-3 * r, report
+    # the GPU gradient on its own smooth piece
+    assert report["rel_l2_piece"] <= 1e-3, report
+    assert report["rel_dir_piece"] <= 1e-3, report
 
 
 def _lr_reverse_case(orc, sc, g, X, V, n_stab, iters, eps_x, rng):

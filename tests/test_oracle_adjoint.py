@@ -170,3 +170,42 @@ def test_rollout_vjp_matches_frozen_central_differences(orc):
         fd = (loss(eps) - loss(-eps)) / (2 * eps)
         an = float((grad * d).sum())
         assert abs(an - fd) <= 1e-3 * abs(fd), (which, an, fd)
+
+
+def test_rollout_vjp_with_foreign_tapes_matches_their_replay(orc):
+    """Reverse modes that take every decision from a tape recorded at another
+    state (the GPU's decisions, in the end-to-end check) are the derivative
+    of the rollout replayed from that tape: pinned against central
+    differences of the replay.  The tapes come from a run whose initial
+    velocities differ by 1e-2 m/s, so many of their decisions differ from
+    the replayed run's own, and the untaped reverse mode gives another
+    gradient."""
+    sc = scenes.diff_column(n_low=400, ratio=8)
+    pb, up = diff_prms(sc)
+    X, V, im, x, v, sdf = _rollout_inputs(sc)
+    T = sc["target"].astype(float)
+    F = 12
+    rng = np.random.default_rng(29)
+    V0 = np.asarray(V, float)
+    Vb = V0 + rng.normal(0.0, 1e-2, V0.shape)
+    ro_a = orc.rollout(X, V0, im, x, v, sdf, pb, up, F)
+    ro_b = orc.rollout(X, Vb, im, x, v, sdf, pb, up, F, tapes=ro_a["tapes"])
+    own_b = orc.rollout(X, Vb, im, x, v, sdf, pb, up, F)
+    differ = sum(int(np.count_nonzero(np.asarray(p) != np.asarray(q))) for p, q in
+                 zip(ro_a["tapes"], own_b["tapes"]) if np.asarray(p).shape == np.asarray(q).shape)
+    assert differ > 0
+    g = 2.0 * (ro_b["hr_x"] - T)
+    _, gV, _, _ = orc.rollout_vjp(ro_b, im, sdf, pb, up, g, np.zeros_like(T), replay=True)
+    _, gV_own, _, _ = orc.rollout_vjp(ro_b, im, sdf, pb, up, g, np.zeros_like(T))
+    assert np.linalg.norm(gV - gV_own) > 1e-6 * np.linalg.norm(gV)
+    for trial in range(2):
+        d = rng.normal(size=V0.shape)
+        eps = 1e-4
+
+        def loss(s):
+            out = orc.rollout(X, Vb + s * d, im, x, v, sdf, pb, up, F, tapes=ro_a["tapes"])
+            return float(((out["hr_x"] - T) ** 2).sum())
+
+        fd = (loss(eps) - loss(-eps)) / (2 * eps)
+        an = float((gV * d).sum())
+        assert abs(an - fd) <= 1e-5 * abs(fd), (trial, an, fd)

@@ -509,12 +509,22 @@ int gs_timing_read(gs_ctx* ctx, int timer, double* total_ms, int64_t* launches);
  * calls whose work overlaps on the GPU race: order them on one stream or
  * synchronize between them.
  * Returns GS_ERR_CAPACITY when n > GS_STATIC_BIN_MAX_POINTS (nothing is
- * enqueued), GS_ERR_ARG for null or misaligned pointers or an inconsistent
- * grid, GS_ERR_CUDA when a CUDA call fails.  Asynchronous on cuda_stream. */
+ * enqueued), GS_ERR_ARG for null or misaligned pointers (pos4 to 16 bytes,
+ * sorted_index and cell_start to 4) or an inconsistent grid (a dimension
+ * below 1 or above 2^20, as gs_create allows), GS_ERR_CUDA when a CUDA call
+ * fails.  Asynchronous on cuda_stream. */
 #define GS_STATIC_BIN_MAX_POINTS 262144
 #define GS_STATIC_BIN_SCRATCH_BYTES 4358144
 int gs_bin_points_static(const float* pos4, int64_t n, const gs_grid_info* grid, uint32_t* sorted_index,
                          uint32_t* cell_start, void* cuda_stream);
+
+/* Failure detection test hook (not in the paper): after `after` more device
+ * allocations by the library, every further one fails as if the device
+ * were out of memory, until the hook is switched off (after < 0).  The
+ * failure is injected on the host, in the library's allocation helper; no
+ * device work is involved.  Calls then return GS_ERR_OOM and release what
+ * they had allocated (gs_create leaves nothing behind).  Process-wide. */
+void gs_set_alloc_failure(long long after);
 
 /* Number of kernels this context has launched since creation. */
 int64_t gs_launch_count(const gs_ctx* ctx);

@@ -110,6 +110,7 @@ _SIGS = {
     "gs_step_low_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int]),
     "gs_step_low_trace": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, ctypes.c_int, _P, _P, ctypes.c_int]),
     "gs_set_decision_record": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
+    "gs_set_alloc_failure": (None, [ctypes.c_longlong]),
 }
 
 _lib = None
@@ -320,6 +321,10 @@ def gs_step_low_forward(ctx, x_in, v_in, x_out, v_out, dt, iters):
 
 def gs_step_low_backward(ctx, x_in, v_in, g_x_out, g_v_out, g_x_in, g_v_in, dt, iters):
     return lib().gs_step_low_backward(ctx, x_in, v_in, g_x_out, g_v_out, g_x_in, g_v_in, dt, iters)
+
+
+def gs_set_alloc_failure(after):
+    lib().gs_set_alloc_failure(int(after))
 
 
 def gs_set_decision_record(ctx, hr_record, lr_candidates, lr_pair_bits, lr_sdf_bits, max_passes):

@@ -4,6 +4,8 @@
 // and the launch-shape autotuner of the upsampling kernel.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -40,11 +42,20 @@ int cuda_fail(gs_ctx* c, cudaError_t e, const char* what)
         if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
     } while (0)
 
+// Host-side allocation failure injection (gs_set_alloc_failure): the
+// countdown of device allocations left before every further one fails;
+// negative: off.  Process-wide, like the allocator it stands in for.
+std::atomic<long long> g_alloc_countdown{-1};
+
 template <class T>
 cudaError_t dalloc(T** p, size_t count)
 {
     *p = nullptr;
     if (count == 0) count = 1;
+    if (g_alloc_countdown.load() >= 0 && g_alloc_countdown.fetch_sub(1) <= 0) {
+        g_alloc_countdown.store(0);
+        return cudaErrorMemoryAllocation;
+    }
     return cudaMalloc((void**)p, count * sizeof(T));
 }
 
@@ -1942,6 +1953,11 @@ int gs_step_low_forward(gs_ctx* c, const float* x_in, const float* v_in, float* 
     CK(cudaMemcpyAsync(x_out, c->lr_pos, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
     CK(cudaMemcpyAsync(v_out, c->lr_vel, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
     return GS_OK;
+}
+
+void gs_set_alloc_failure(long long after)
+{
+    g_alloc_countdown.store(after < 0 ? -1 : after);
 }
 
 // SDF components of the context's SDFs (a box interior counts its six walls).

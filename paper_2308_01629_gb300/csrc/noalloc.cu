@@ -62,8 +62,12 @@ extern "C" int gs_bin_points_static(const float* pos4, int64_t n, const gs_grid_
     if (n > kMaxPoints) return GS_ERR_CAPACITY;
     if (n > 0 && (!pos4 || !sorted_index)) return GS_ERR_ARG;
     if (n > 0 && (reinterpret_cast<uintptr_t>(pos4) & 15u) != 0) return GS_ERR_ARG;   // float4 records
+    // uint32 words: the cell starts are written by a kernel, the sorted
+    // indices by a copy
+    if ((reinterpret_cast<uintptr_t>(cell_start) & 3u) != 0) return GS_ERR_ARG;
+    if (n > 0 && (reinterpret_cast<uintptr_t>(sorted_index) & 3u) != 0) return GS_ERR_ARG;
     for (int k = 0; k < 3; ++k)
-        if (grid->dims[k] < 1) return GS_ERR_ARG;
+        if (grid->dims[k] < 1 || grid->dims[k] > (1 << 20)) return GS_ERR_ARG;   // as gs_create
     const int64_t n_cell = (int64_t)grid->dims[0] * grid->dims[1] * grid->dims[2];
     if (n_cell != grid->n_cell || n_cell >= 0xffffffffLL || !(grid->inv_h > 0.0f)) return GS_ERR_ARG;
     if (gs_sort_hist_words(n) > kHistWords) return GS_ERR_CAPACITY;

@@ -41,3 +41,28 @@ def test_default_params_are_the_papers():
     assert abs(p.c1 - 512.0 / 729.0) < 1e-7 and abs(p.c2 - 0.6) < 1e-7
     assert abs(p.mu_s - 0.35) < 1e-7 and abs(p.mu_k - 0.30) < 1e-7
     assert p.n_stab == 2 and abs(p.gravity[2] + 9.81) < 1e-6
+
+
+def test_static_binning_refuses_bad_arguments_before_any_device_work():
+    """gs_bin_points_static checks its arguments on the host and returns
+    before any CUDA call, so these refusals run without a GPU (the pointers
+    are never dereferenced)."""
+    import paper_2308_01629_gb300 as gs
+    g = gs.gs_grid_info()
+    for k in range(3):
+        g.origin[k] = 0.0
+        g.dims[k] = 8
+    g.h, g.inv_h, g.n_cell = 0.03, 1.0 / 0.03, 512
+    ok_pos, ok_idx, ok_start = 1 << 20, 1 << 21, 1 << 22
+    call = gs.gs_bin_points_static
+    assert call(ok_pos + 8, 10, g, ok_idx, ok_start) == gs.GS_ERR_ARG      # positions not 16-byte aligned
+    assert call(ok_pos, 10, g, ok_idx, ok_start + 2) == gs.GS_ERR_ARG      # cell starts not 4-byte aligned
+    assert call(ok_pos, 10, g, ok_idx + 1, ok_start) == gs.GS_ERR_ARG      # indices not 4-byte aligned
+    assert call(ok_pos, 10, g, ok_idx, None) == gs.GS_ERR_ARG
+    assert call(ok_pos, gs.GS_STATIC_BIN_MAX_POINTS + 1, g, ok_idx, ok_start) == gs.GS_ERR_CAPACITY
+    g.dims[0] = (1 << 20) + 1                                              # wider than gs_create allows
+    g.n_cell = g.dims[0] * 64
+    assert call(ok_pos, 10, g, ok_idx, ok_start) == gs.GS_ERR_ARG
+    g.dims[0] = 8
+    g.n_cell = 511                                                         # inconsistent cell count
+    assert call(ok_pos, 10, g, ok_idx, ok_start) == gs.GS_ERR_ARG

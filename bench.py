@@ -21,7 +21,9 @@ the fused gather / blend / advection / SDF kernel).
 
 --impl reference runs that oracle alone as the reference arm.
 Under torchrun every rank steps its own replica of the scene (weak scaling,
-no collective on the data path); rank 0 prints one JSON line.
+no collective on the data path); rank 0 prints one JSON line.  With
+--partition slab the ranks split one scene's HR set instead (strong scaling,
+an all-gather of the HR slabs before each HR reorder).
 """
 from __future__ import annotations
 
@@ -73,6 +75,10 @@ def parse(argv=None):
     ap.add_argument("--no-solid", action="store_true", help="skip the particle-sampled bucket frame timing")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="do not try pipelined frames (HR frame overlapping the next frame's LR steps)")
+    ap.add_argument("--partition", choices=["replicas", "slab"], default="replicas",
+                    help="under torchrun: every rank steps its own replica of the scene (weak scaling), or the "
+                         "ranks split one scene's HR slots into slabs, each computing the LR state itself, with "
+                         "one all-gather of the slabs before each HR reorder (strong scaling)")
     ap.add_argument("--batch-scenes", type=int, default=256)
     ap.add_argument("--gather-shape", default=None, metavar="WxB",
                     help="fix the gather's launch shape (warps per block x blocks per SM, 0: one item per warp) "
@@ -661,6 +667,91 @@ def run_gpu(args):
     return line
 
 
+def run_slab(args):
+    """One scene's HR set split across the ranks by slabs of its cell-ordered
+    slots, the LR steps run by every rank; before each HR reorder the ranks
+    all-gather their slabs (inside the timed frames).  value = the scene's
+    HR particles per second of the slowest rank (strong scaling)."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_2308_01629_gb300 as gs
+    from paper_2308_01629_gb300 import slabs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    sc = make_scene(args.workload, args.bed_size)
+    M = len(sc["hr_pos"])
+    ctx = gs.Context(sc, stream=stream.cuda_stream)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    if args.gather_shape:
+        ctx.set_tuning(*(int(t) for t in args.gather_shape.split("x")))
+    ctx.set_hr_slab(rank, world)
+    ctx.set_graphs(True)
+    frame = [0]
+    exchanges = [0]
+
+    def step():
+        if world > 1 and frame[0] > 0 and frame[0] % 8 == 0:   # the reorder of this frame needs every slab
+            slabs.assemble(ctx, rank, world)
+            exchanges[0] += 1
+        b = bucket_at(sc, frame[0])
+        if b is not None:
+            ctx.set_sdf(*b)
+        ctx.frame(DT, N_SUB, sc["iters"])
+        frame[0] += 1
+
+    clk = Clocks(local)
+    time.sleep(0.3)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = ctx.launches()
+    ex0 = exchanges[0]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total_ms = 0.0
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        start.record(stream)
+        step()
+        end.record(stream)
+        end.synchronize()   # the exchange synchronizes on the host; time each frame on its own
+        total_ms += start.elapsed_time(end)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    time.sleep(0.15)
+    clocks = clk.stop()
+    launches = ctx.launches() - launches0
+    ctx.sync()
+    b, e = ctx.hr_slab_range(rank, world)
+    total_ms = max_over_ranks(total_ms, world, dev)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    return {"metric": METRIC, "value": M * args.steps / (total_ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded scene generators)",
+            "config": dict(workload_config(sc), partition=f"HR slabs of one scene over {world} rank(s)",
+                           slab_slots_rank0=[b, e], exchanges_timed=exchanges[0] - ex0),
+            "timed_region": "per frame: the slab all-gather when a reorder is due, then one CUDA-graph launch",
+            "gpu_launches": int(launches), "clocks": clocks,
+            "e2e": None, "note": "auxiliary mode: no e2e, roofline or CPU baseline legs"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -687,7 +778,12 @@ def run_reference(args):
 
 def main():
     args = parse()
-    line = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if args.impl == "reference":
+        line = run_reference(args)
+    elif args.partition == "slab":
+        line = run_slab(args)
+    else:
+        line = run_gpu(args)
     if line is not None:
         print(json.dumps(line), flush=True)
 

@@ -286,6 +286,49 @@ int gs_frame(gs_ctx* ctx, float dt, int n_sub, int iters);
 #define GS_MAX_SUBSTEPS 256
 int gs_frame_adaptive(gs_ctx* ctx, float dt, float dt_max, float cfl, int max_sub, int iters);
 
+/* One scene's HR set split across GPUs (Sec. 4: given the LR state, every
+ * HR particle's update depends on the LR particles alone, never on another
+ * HR particle).  Every rank runs the whole LR computation (the same
+ * deterministic kernels on the same input, so the same bits everywhere) and
+ * updates only its slab of the HR slots in internal (cell) order, the
+ * slots of GS_FIELD_HR_POS_INTERNAL; the ranks exchange their slabs (the
+ * caller's all-gather) before each HR reorder and before reading the HR
+ * state in original order.
+ *
+ * gs_hr_slab_range: slab `part` of `n_parts` of n_slots HR slots is
+ * [*begin, *end): whole 32-slot items split as evenly as possible (item
+ * counts differ by one at most; a slab may be empty).  Host arithmetic, no
+ * context, no GPU.  GS_ERR_ARG unless 1 <= n_parts <= 4096,
+ * 0 <= part < n_parts, n_slots >= 0 and a multiple of 32 (the size of
+ * GS_FIELD_HR_POS_INTERNAL in float4 is), begin and end not null. */
+int gs_hr_slab_range(int64_t n_slots, int part, int n_parts, int64_t* begin, int64_t* end);
+
+/* Restricts the HR frames of the context (gs_upsample, gs_frame,
+ * gs_frame_adaptive) to slab `part` of `n_parts` of its HR slots; slots
+ * outside keep their values, and every slot inside gets bitwise the value
+ * the unrestricted context computes (the gather's work items are the same
+ * 32 slots with the same arithmetic).  n_parts = 1 restores the whole set.
+ * After a restricted frame the context's HR state is "partial": until
+ * gs_hr_slab_assemble, a frame on which an HR reorder is due
+ * (params.resort_every), gs_resort_high, reads and writes of GS_FIELD_HR_POS
+ * / GS_FIELD_HR_VEL (synchronous or asynchronous) and another
+ * gs_set_hr_slab return GS_ERR_STATE; the internal fields stay readable.
+ * Not with pipelined frames (GS_ERR_STATE both ways).  Bad part / n_parts:
+ * GS_ERR_ARG. */
+int gs_set_hr_slab(gs_ctx* ctx, int part, int n_parts);
+
+/* The gather-back: writes the whole HR state in internal slot order, pos
+ * and vel each float4[HR slots] (bytes = 16 x HR slots) as read from
+ * GS_FIELD_HR_POS_INTERNAL / GS_FIELD_HR_VEL_INTERNAL, each slab taken from
+ * the context that updated it, and ends the partial state.  The w of every
+ * slot's position (the particle id, padding included) must equal the
+ * context's bit for bit, and every x, y, z must be finite; otherwise
+ * GS_ERR_ARG and nothing changes.  Pending device errors of earlier calls
+ * are reported first.  Host or device sources (src_is_device); blocks until
+ * the state is applied, so the sources may change on return.  A context
+ * without a slab may call it too (a state written back unchanged). */
+int gs_hr_slab_assemble(gs_ctx* ctx, const void* pos, const void* vel, size_t bytes, int src_is_device);
+
 /* The LR steps of the latest adaptive frame: *n_out receives their number
  * and dts[0 .. min(n, cap)) their lengths.  Blocks. */
 int gs_substeps(gs_ctx* ctx, float* dts, int cap, int* n_out);

@@ -111,6 +111,10 @@ _SIGS = {
     "gs_step_low_trace": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, ctypes.c_int, _P, _P, ctypes.c_int]),
     "gs_set_decision_record": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
     "gs_set_alloc_failure": (None, [ctypes.c_longlong]),
+    "gs_hr_slab_range": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_int64)]),
+    "gs_set_hr_slab": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    "gs_hr_slab_assemble": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, ctypes.c_int]),
 }
 
 _lib = None
@@ -327,6 +331,21 @@ def gs_set_alloc_failure(after):
     lib().gs_set_alloc_failure(int(after))
 
 
+def gs_hr_slab_range(n_slots, part, n_parts):
+    """(status, begin, end): slab `part` of `n_parts` of n_slots HR slots."""
+    b, e = ctypes.c_int64(), ctypes.c_int64()
+    rc = lib().gs_hr_slab_range(int(n_slots), int(part), int(n_parts), ctypes.byref(b), ctypes.byref(e))
+    return rc, b.value, e.value
+
+
+def gs_set_hr_slab(ctx, part, n_parts):
+    return lib().gs_set_hr_slab(ctx, int(part), int(n_parts))
+
+
+def gs_hr_slab_assemble(ctx, pos, vel, nbytes, src_is_device):
+    return lib().gs_hr_slab_assemble(ctx, pos, vel, nbytes, int(src_is_device))
+
+
 def gs_set_decision_record(ctx, hr_record, lr_candidates, lr_pair_bits, lr_sdf_bits, max_passes):
     return lib().gs_set_decision_record(ctx, hr_record, lr_candidates, lr_pair_bits, lr_sdf_bits, max_passes)
 
@@ -526,6 +545,26 @@ class Context:
 
     def set_pipeline(self, enable=True, warps_per_block=8, blocks_per_sm=1):
         return _check(self.ctx, gs_set_pipeline(self.ctx, enable, warps_per_block, blocks_per_sm), "gs_set_pipeline")
+
+    def set_hr_slab(self, part, n_parts):
+        """Restrict this context's HR frames to slab `part` of `n_parts` of
+        its cell-ordered HR slots (n_parts = 1: the whole set)."""
+        return _check(self.ctx, gs_set_hr_slab(self.ctx, part, n_parts), "gs_set_hr_slab")
+
+    def hr_slab_range(self, part, n_parts):
+        """[begin, end) of slab `part` of `n_parts` of this context's HR slots."""
+        rc, b, e = gs_hr_slab_range(self.hr_slots, part, n_parts)
+        _check(self.ctx, rc, "gs_hr_slab_range")
+        return b, e
+
+    def hr_slab_assemble(self, pos, vel):
+        """Write the whole HR state in internal slot order (float32 [slots, 4]
+        each, host arrays or device tensors) and end the partial state."""
+        pp, n, dev = _ptr_of(pos)
+        pv, nv, devv = _ptr_of(vel)
+        if nv != n or devv != dev:
+            raise ValueError("pos and vel must have the same size and live on the same side")
+        return _check(self.ctx, gs_hr_slab_assemble(self.ctx, pp, pv, n, dev), "gs_hr_slab_assemble")
 
     def set_tuning(self, warps_per_block, blocks_per_sm):
         return _check(self.ctx, gs_set_tuning(self.ctx, warps_per_block, blocks_per_sm), "gs_set_tuning")

@@ -183,6 +183,20 @@ __global__ void k_copy2_checked(const float4* __restrict__ a, const float4* __re
     ob[i] = v;
 }
 
+// The check of an assembled HR state (gs_hr_slab_assemble): bit 1 of *err
+// when some x, y, z is not finite, bit 2 when the id bits in the w of a
+// slot's position differ from the context's.
+__global__ void k_slab_check(const float4* __restrict__ pos, const float4* __restrict__ vel,
+                             const float4* __restrict__ cur, int64_t n, int* err)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const float4 u = pos[p], v = vel[p];
+    if (!(isfinite(u.x) && isfinite(u.y) && isfinite(u.z) && isfinite(v.x) && isfinite(v.y) && isfinite(v.z)))
+        atomicOr(err, 1);
+    if (__float_as_uint(u.w) != __float_as_uint(cur[p].w)) atomicOr(err, 2);
+}
+
 __global__ void k_hr_load2_checked(const float4* __restrict__ sp, const float4* __restrict__ sv,
                                    float4* __restrict__ dp, float4* __restrict__ dv, const uint32_t* __restrict__ tag,
                                    const SceneDev* __restrict__ scenes, int64_t n_slots, int* err, int bit)
@@ -579,6 +593,7 @@ UpsampleArgs upsample_args(const gs_ctx* c, float dt, const float4* in_pos, cons
     u.sdf = c->d_sdf;
     u.n_scenes = c->n_scenes;
     u.n_warps = c->n_warps;
+    u.item_begin = 0;
     u.work = c->d_work;
     u.solid_flag = c->lr_cell_start + c->n_cell_total + 1;
     u.dt = dt;
@@ -601,6 +616,10 @@ int upsample_impl(gs_ctx* c, float dt)
     if (st) return st;
     const int cur = c->hr_cur;
     UpsampleArgs u = upsample_args(c, dt, c->hr_pos[cur], c->hr_vel[cur], c->hr_pos[cur], c->hr_vel[cur]);
+    if (c->slab_parts > 1) {   // this context's slab of the HR slots only
+        u.item_begin = c->slab_item_begin;
+        u.n_warps = c->slab_item_end - c->slab_item_begin;
+    }
     {
         Timed t(c, GS_TIMER_GATHER);
         CK(gs_launch_upsample(c->stream, u, c->tune_warps, c->tune_blocks_per_sm, c->sm_count, &c->launches),
@@ -669,6 +688,29 @@ int step_low_impl(gs_ctx* c, float dt, int iters, const float* dt_dev = nullptr,
                           &c->launches, rate),
        "finalize");
     c->lr_binned = false;   // the binning above is of the predicted positions
+    return GS_OK;
+}
+
+// HR frames of a context restricted to a slab: a reorder reads the whole
+// HR state, so it must not come while slots outside the slab are stale.
+int slab_frame_begin(gs_ctx* c)
+{
+    if (c->hr_partial && c->n_high > 0 && c->resort_every > 0 && c->frame % c->resort_every == 0)
+        return fail(c, GS_ERR_STATE, "an HR reorder is due and the slots outside this context's slab are stale: "
+                                     "assemble the HR state (gs_hr_slab_assemble) first");
+    return GS_OK;
+}
+
+void slab_frame_end(gs_ctx* c)
+{
+    if (c->slab_parts > 1 && c->n_high > 0) c->hr_partial = true;
+}
+
+int slab_refuse_hr_field(gs_ctx* c, int field)
+{
+    if (c->hr_partial && (field == GS_FIELD_HR_POS || field == GS_FIELD_HR_VEL))
+        return fail(c, GS_ERR_STATE, "field %d needs the whole HR state, and the slots outside this context's slab "
+                                     "are stale (gs_hr_slab_assemble)", field);
     return GS_OK;
 }
 
@@ -1077,7 +1119,7 @@ void gs_destroy(gs_ctx* c)
                     c->step_cell_start, c->d_sdf_pend, c->stage_in, c->lr_mat, c->d_mu, c->d_cfl, c->lr_body, c->lr_xo, c->body_members,
                     c->body_start, c->body_xf, c->lr_slot, c->hr_bin_start, c->hr_big, c->hr_scan_aux,
                     c->async_in[0], c->async_in[1], c->async_in[2], c->async_in[3],
-                    c->async_out[0], c->async_out[1], c->async_out[2], c->async_out[3]};
+                    c->async_out[0], c->async_out[1], c->async_out[2], c->async_out[3], c->slab_stage};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->h_err) cudaFreeHost(c->h_err);
@@ -1294,8 +1336,13 @@ int gs_write(gs_ctx* c, int field, const void* src, size_t bytes, int src_is_dev
     if (field != GS_FIELD_LR_POS && field != GS_FIELD_LR_VEL && field != GS_FIELD_HR_POS && field != GS_FIELD_HR_VEL)
         return fail(c, GS_ERR_ARG, "field %d is not writable", field);
     if (bytes != field_bytes(c, field)) return fail(c, GS_ERR_ARG, "size %zu does not match field %d", bytes, field);
+    st = slab_refuse_hr_field(c, field);
+    if (st) return st;
     if (bytes == 0) return GS_OK;
     if (!src) return fail(c, GS_ERR_ARG, "null source");
+    // errors of earlier work first: the check below reuses the error word
+    st = report_device_errors(c);
+    if (st) return st;
     const int64_t n = (field == GS_FIELD_LR_POS || field == GS_FIELD_LR_VEL) ? c->n_low : c->n_high;
     // host data is staged on the device first; the finiteness check runs
     // there, before anything of the context's state changes
@@ -1326,6 +1373,8 @@ int gs_read(gs_ctx* c, int field, void* dst, size_t bytes, int dst_is_device)
     if (fb == (size_t)-1) return fail(c, GS_ERR_ARG, "unknown field %d", field);
     if (bytes != fb) return fail(c, GS_ERR_ARG, "size %zu does not match field %d", bytes, field);
     if (bytes > 0 && !dst) return fail(c, GS_ERR_ARG, "null destination");
+    st = slab_refuse_hr_field(c, field);
+    if (st) return st;
     const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     const int cur = c->hr_cur;
     const void* srcp = nullptr;
@@ -1391,6 +1440,8 @@ int gs_resort_high(gs_ctx* c)
     if (st) return st;
     st = settle(c);
     if (st) return st;
+    if (c->hr_partial)
+        return fail(c, GS_ERR_STATE, "the slots outside this context's HR slab are stale (gs_hr_slab_assemble)");
     return resort_high_impl(c);
 }
 
@@ -1412,7 +1463,11 @@ int gs_upsample(gs_ctx* c, float dt)
     st = settle(c);
     if (st) return st;
     if (!(dt > 0.0f) || !std::isfinite(dt)) return fail(c, GS_ERR_ARG, "invalid dt %g", (double)dt);
-    return upsample_impl(c, dt);
+    st = slab_frame_begin(c);
+    if (st) return st;
+    st = upsample_impl(c, dt);
+    if (st == GS_OK) slab_frame_end(c);
+    return st;
 }
 
 int gs_set_pipeline(gs_ctx* c, int enable, int warps_per_block, int blocks_per_sm)
@@ -1424,6 +1479,8 @@ int gs_set_pipeline(gs_ctx* c, int enable, int warps_per_block, int blocks_per_s
         return fail(c, GS_ERR_ARG, "unsupported launch shape %d x %d", warps_per_block, blocks_per_sm);
     st = settle(c);
     if (st) return st;
+    if (enable && c->slab_parts > 1)
+        return fail(c, GS_ERR_STATE, "pipelined frames do not combine with an HR slab");
     c->pipeline = enable != 0;
     c->pipe_warps = warps_per_block;
     c->pipe_blocks_per_sm = blocks_per_sm;
@@ -1552,10 +1609,9 @@ static int fold_cfl_launches(gs_ctx* c)
     return GS_OK;
 }
 
-int gs_frame(gs_ctx* c, float dt, int n_sub, int iters)
+static int frame_body(gs_ctx* c, float dt, int n_sub, int iters)
 {
-    int st = check_state(c);
-    if (st) return st;
+    int st;
     if (!(dt > 0.0f) || !std::isfinite(dt) || n_sub < 0 || n_sub > 1000 || iters < 0 || iters > 1000)
         return fail(c, GS_ERR_ARG, "invalid frame arguments");
     if (c->pipeline && !c->timing) {
@@ -1627,10 +1683,9 @@ int gs_frame(gs_ctx* c, float dt, int n_sub, int iters)
     return GS_OK;
 }
 
-int gs_frame_adaptive(gs_ctx* c, float dt, float dt_max, float cfl, int max_sub, int iters)
+static int frame_adaptive_body(gs_ctx* c, float dt, float dt_max, float cfl, int max_sub, int iters)
 {
-    int st = check_state(c);
-    if (st) return st;
+    int st;
     if (!(dt > 0.0f) || !std::isfinite(dt) || !(dt_max > 0.0f) || !std::isfinite(dt_max) || !(cfl > 0.0f) ||
         !std::isfinite(cfl) || max_sub < 1 || max_sub > GS_MAX_SUBSTEPS || iters < 0 || iters > 1000)
         return fail(c, GS_ERR_ARG, "invalid adaptive frame arguments");
@@ -1685,6 +1740,107 @@ int gs_frame_adaptive(gs_ctx* c, float dt, float dt_max, float cfl, int max_sub,
     }
     c->lr_binned = c->n_high > 0;
     c->frame = frame0 + 1;
+    return GS_OK;
+}
+
+int gs_frame(gs_ctx* c, float dt, int n_sub, int iters)
+{
+    int st = check_state(c);
+    if (st) return st;
+    st = slab_frame_begin(c);
+    if (st) return st;
+    st = frame_body(c, dt, n_sub, iters);
+    if (st == GS_OK) slab_frame_end(c);
+    return st;
+}
+
+int gs_frame_adaptive(gs_ctx* c, float dt, float dt_max, float cfl, int max_sub, int iters)
+{
+    int st = check_state(c);
+    if (st) return st;
+    st = slab_frame_begin(c);
+    if (st) return st;
+    st = frame_adaptive_body(c, dt, dt_max, cfl, max_sub, iters);
+    if (st == GS_OK) slab_frame_end(c);
+    return st;
+}
+
+int gs_hr_slab_range(int64_t n_slots, int part, int n_parts, int64_t* begin, int64_t* end)
+{
+    if (!begin || !end || n_parts < 1 || n_parts > 4096 || part < 0 || part >= n_parts || n_slots < 0 ||
+        n_slots % 32 != 0)
+        return GS_ERR_ARG;
+    // whole 32-slot items, as even as possible (item counts differ by one at most)
+    const int64_t items = n_slots / 32;
+    *begin = items * part / n_parts * 32;
+    *end = items * (part + 1) / n_parts * 32;
+    return GS_OK;
+}
+
+int gs_set_hr_slab(gs_ctx* c, int part, int n_parts)
+{
+    int st = check_state(c);
+    if (st) return st;
+    int64_t b = 0, e = 0;
+    if (gs_hr_slab_range(c->hr_slots, part, n_parts, &b, &e) != GS_OK)
+        return fail(c, GS_ERR_ARG, "bad HR slab %d of %d", part, n_parts);
+    st = settle(c);
+    if (st) return st;
+    if (c->pipeline) return fail(c, GS_ERR_STATE, "an HR slab does not combine with pipelined frames");
+    if (c->hr_partial)
+        return fail(c, GS_ERR_STATE, "the slots outside the current HR slab are stale; assemble them first");
+    c->slab_parts = n_parts;
+    c->slab_item_begin = b / 32;
+    c->slab_item_end = e / 32;
+    drop_graphs(c);   // the captured gathers cover the old range
+    return GS_OK;
+}
+
+int gs_hr_slab_assemble(gs_ctx* c, const void* pos, const void* vel, size_t bytes, int src_is_device)
+{
+    int st = check_state(c);
+    if (st) return st;
+    st = settle(c);
+    if (st) return st;
+    if (bytes != (size_t)c->hr_slots * sizeof(float4))
+        return fail(c, GS_ERR_ARG, "size %zu does not match the HR slots (%lld x 16 bytes)", bytes,
+                    (long long)c->hr_slots);
+    if (bytes == 0) {
+        c->hr_partial = false;
+        return GS_OK;
+    }
+    if (!pos || !vel) return fail(c, GS_ERR_ARG, "null source");
+    st = report_device_errors(c);   // the check below reuses the error word
+    if (st) return st;
+    const float4* dp = (const float4*)pos;
+    const float4* dv = (const float4*)vel;
+    if (!src_is_device) {
+        if (!c->slab_stage && dalloc(&c->slab_stage, (size_t)2 * c->hr_slots) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, GS_ERR_OOM, "no memory to stage the assembled HR state");
+        }
+        CK(cudaMemcpyAsync(c->slab_stage, pos, bytes, cudaMemcpyHostToDevice, c->stream), "copy in");
+        CK(cudaMemcpyAsync(c->slab_stage + c->hr_slots, vel, bytes, cudaMemcpyHostToDevice, c->stream), "copy in");
+        dp = c->slab_stage;
+        dv = c->slab_stage + c->hr_slots;
+    }
+    const int cur = c->hr_cur;
+    k_slab_check<<<gs_blocks(c->hr_slots, 256), 256, 0, c->stream>>>(dp, dv, c->hr_pos[cur], c->hr_slots, c->d_err);
+    c->launches += 1;
+    CK(cudaGetLastError(), "check");
+    CK(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read flag");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");   // the sources are consumed from here on
+    const int bad = *c->h_err;
+    if (bad) {
+        CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream), "clear flag");
+        return fail(c, GS_ERR_ARG, (bad & 2) ? "the assembled HR positions' ids differ from this context's slot order"
+                                             : "non-finite value in the assembled HR state");
+    }
+    CK(cudaMemcpyAsync(c->hr_pos[cur], dp, bytes, cudaMemcpyDeviceToDevice, c->stream), "apply");
+    CK(cudaMemcpyAsync(c->hr_vel[cur], dv, bytes, cudaMemcpyDeviceToDevice, c->stream), "apply");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");   // device sources too are consumed on return
+    c->hr_partial = false;
+    c->hr_pair_field = -1;
     return GS_OK;
 }
 
@@ -2184,6 +2340,8 @@ int gs_write_async(gs_ctx* c, int field, const void* src, size_t bytes, int src_
     if (field < GS_FIELD_LR_POS || field > GS_FIELD_HR_VEL)
         return fail(c, GS_ERR_ARG, "field %d is not writable", field);
     if (bytes != field_bytes(c, field)) return fail(c, GS_ERR_ARG, "size %zu does not match field %d", bytes, field);
+    st = slab_refuse_hr_field(c, field);
+    if (st) return st;
     if (bytes == 0) return GS_OK;
     if (!src) return fail(c, GS_ERR_ARG, "null source");
     st = async_buffer(c, &c->async_in[field], field);
@@ -2206,6 +2364,8 @@ int gs_read_async(gs_ctx* c, int field, void* dst, size_t bytes, int dst_is_devi
         return fail(c, GS_ERR_ARG, "field %d has no asynchronous read", field);
     if (bytes != field_bytes(c, field)) return fail(c, GS_ERR_ARG, "size %zu does not match field %d", bytes, field);
     if (bytes > 0 && !dst) return fail(c, GS_ERR_ARG, "null destination");
+    st = slab_refuse_hr_field(c, field);
+    if (st) return st;
     if (dst_is_device) return gs_read(c, field, dst, bytes, 1);   // already asynchronous
     st = settle(c);
     if (st) return st;

@@ -163,6 +163,13 @@ struct gs_ctx {
     float4* hr_pos[2] = {nullptr, nullptr};
     float4* hr_vel[2] = {nullptr, nullptr};
     int hr_cur = 0;
+    // HR slab (gs_set_hr_slab): the HR frames update warp items
+    // [slab_item_begin, slab_item_end) only; hr_partial: the slots outside
+    // were not updated by the latest frames (until gs_hr_slab_assemble)
+    int slab_parts = 1;
+    int64_t slab_item_begin = 0, slab_item_end = 0;
+    bool hr_partial = false;
+    float4* slab_stage = nullptr;       // 2 x hr_slots, for host sources of gs_hr_slab_assemble
     bool hr_identity = true;
     uint32_t* hr_keys[2] = {nullptr, nullptr};
     uint32_t* hr_vals[2] = {nullptr, nullptr};
@@ -346,6 +353,7 @@ struct UpsampleArgs {
     const gs_sdf* sdf;
     int n_scenes;
     int64_t n_warps;           // warp items
+    int64_t item_begin;        // first item: the launch covers items [item_begin, item_begin + n_warps)
     unsigned* work;            // persistent mode: next warp item (zeroed before the launch)
     const unsigned* solid_flag;   // nonzero: some LR particle has w = 0 (set by the LR binning)
     float dt;

@@ -324,6 +324,7 @@ __global__ void __launch_bounds__(WARPS * 32, 24 / WARPS) k_upsample(const Upsam
     // One call site for both launch modes, so both run the same code.  In
     // the persistent mode warps pull items until the counter passes
     // n_warps; every warp leaves after at most n_warps + 1 iterations.
+    // Items are counted from a.item_begin (a slab of the HR slots).
     for (int64_t guard = 0; guard <= a.n_warps; ++guard) {
         int64_t item;
         if (persistent) {
@@ -338,14 +339,15 @@ __global__ void __launch_bounds__(WARPS * 32, 24 / WARPS) k_upsample(const Upsam
             // Pull the HR lines of the item one wave ahead into L2 (one lane
             // per 128-byte line); whichever warp takes that item then finds
             // its first loads there.  ahead < n_warps keeps the address
-            // inside the n_warps * 32 slot arrays.
+            // inside the launch's items, which lie inside the slot arrays.
             const int64_t ahead = item + (int64_t)gridDim.x * WARPS;
             if (ahead < a.n_warps && (lane & 7) == 0) {
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(a.hr_pos + ahead * 32 + lane));
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(a.hr_vel + ahead * 32 + lane));
+                const int64_t line = (a.item_begin + ahead) * 32 + lane;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(a.hr_pos + line));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(a.hr_vel + line));
             }
         }
-        upsample_item<kSolid>(a, item, s_a[warp], s_b[warp], s_sol[kSolid ? warp : 0], lane);
+        upsample_item<kSolid>(a, a.item_begin + item, s_a[warp], s_b[warp], s_sol[kSolid ? warp : 0], lane);
     }
 }
 

@@ -66,3 +66,25 @@ def test_static_binning_refuses_bad_arguments_before_any_device_work():
     g.dims[0] = 8
     g.n_cell = 511                                                         # inconsistent cell count
     assert call(ok_pos, 10, g, ok_idx, ok_start) == gs.GS_ERR_ARG
+
+
+def test_hr_slab_ranges_tile_the_slots_by_whole_items():
+    """gs_hr_slab_range is host arithmetic: the slabs of a partition are
+    contiguous, start at 0, end at n_slots, are made of whole 32-slot items
+    and differ by one item at most; bad arguments give GS_ERR_ARG."""
+    import paper_2308_01629_gb300 as gs
+    for n_slots in (0, 32, 96, 32 * 1000, 32 * 63157):
+        for n_parts in (1, 2, 3, 7, 8, 64, 4096):
+            ranges = []
+            for part in range(n_parts):
+                rc, b, e = gs.gs_hr_slab_range(n_slots, part, n_parts)
+                assert rc == gs.GS_OK
+                ranges.append((b, e))
+            assert ranges[0][0] == 0 and ranges[-1][1] == n_slots
+            for (b0, e0), (b1, e1) in zip(ranges, ranges[1:]):
+                assert e0 == b1
+            sizes = [e - b for b, e in ranges]
+            assert all(s % 32 == 0 and s >= 0 for s in sizes)
+            assert max(sizes) - min(sizes) <= 32
+    for args in ((33, 0, 2), (-32, 0, 1), (64, 2, 2), (64, -1, 2), (64, 0, 0), (64, 0, 4097)):
+        assert gs.gs_hr_slab_range(*args)[0] == gs.GS_ERR_ARG

@@ -1,7 +1,9 @@
-"""Host logic of the multi-rank benchmark on CPU: two gloo ranks, each with
-its own scene replica (weak scaling, no collective on the data path).  The
-timing reduction takes the slowest rank and the whole-job rate counts the
-units of all ranks; the reference arm runs on rank 0 only."""
+"""Host logic of the multi-rank paths on CPU with two gloo ranks: the
+benchmark's replicas (weak scaling, no collective on the data path; the
+timing reduction takes the slowest rank, the whole-job rate counts the units
+of all ranks; the reference arm runs on rank 0 only), and the exchange of one
+scene's HR slabs (every rank updates its slab, one all-gather puts the whole
+state back on every rank)."""
 import os
 import socket
 
@@ -51,6 +53,46 @@ def test_two_gloo_ranks_reduce_to_the_slowest_and_count_all_units():
         assert total_ms == 15.0                       # the maximum over both ranks
         assert rate == pytest.approx(2 * 4000 / 0.015)  # both ranks' units over the slowest time
     assert res[1][3] is None                          # the reference arm does no work off rank 0
+
+
+def _slab_rank_main(rank, world, port, out):
+    """One scene's HR slots split by slabs: each rank's own slab holds the
+    true values, the rest stale values of its own; the gather-back leaves
+    the true values everywhere on every rank."""
+    import torch.distributed as dist
+
+    from paper_2308_01629_gb300 import slabs
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        n = 32 * 37                                    # an odd number of items: unequal slabs
+        true_pos = torch.arange(4 * n, dtype=torch.float32).reshape(n, 4)
+        true_vel = -0.5 * true_pos
+        pos = torch.full((n, 4), 1000.0 + rank)
+        vel = torch.full((n, 4), -1000.0 - rank)
+        b, e = slabs.slab_ranges(n, world)[rank]
+        pos[b:e] = true_pos[b:e]
+        vel[b:e] = true_vel[b:e]
+        slabs.all_gather_slabs(pos, vel, rank, world)
+        out.put((rank, (b, e), bool(torch.equal(pos, true_pos)), bool(torch.equal(vel, true_vel))))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_gather_back_their_hr_slabs():
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_slab_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res[0][1] == (0, 32 * 18) and res[1][1] == (32 * 18, 32 * 37)
+    assert all(r[2] and r[3] for r in res)
 
 
 def test_single_rank_needs_no_process_group():

@@ -8,16 +8,20 @@ upsampling frame of Sec. 4 (LR re-binning, the HR reorder every 8 frames,
 the fused gather / blend / advection / SDF kernel).
 
   value  HR particles per second of whole frames, device-timed with CUDA
-         events on the library's stream, inputs resident, L2 flushed (a
-         512 MiB write) between timed steps; summed over ranks.
+         events on the library's stream, inputs resident, L2 flushed between
+         timed steps (a 512 MiB write, then a 512 MiB read, so no dirty line
+         is written back inside the frame); summed over ranks.  The same
+         frames after the write alone are reported beside it.
   e2e    the same frames through the C ABI with the full state (LR and HR
          position and velocity) copied from pinned host memory before and
          the HR result copied back after every step.
   roofline  the upsampling kernel: algorithmic bytes (64 B per HR particle
          read + written, 32 B per LR particle, 4 B per cell start) over its
          average CUDA-event duration, against the measured HBM copy peak.
-  cpu_baseline  the FP64 oracle on this machine's host cores on a bounded
-         sample (one full LR step + a random HR subset, scaled to the frame).
+  cpu_baseline  the FP64 oracle's plain definitions on this machine's host
+         cores on a bounded sample (the frame's LR steps of the whole LR set
+         + the HR frame of 200,000 random HR particles, scaled to the frame;
+         the LR steps also on one thread).
 
 --impl reference runs that oracle alone as the reference arm.
 Under torchrun every rank steps its own replica of the scene (weak scaling,
@@ -54,6 +58,23 @@ FLUSH_BYTES = 512 << 20
 # (profiles/); reported only while the source is unchanged.
 TRAFFIC_CAPTURE = {"source_sha1": "aba414c880ed8961c3c14dbc91350a0d3a660791", "bytes": 82594560,
                    "dram_throughput_pct": 6.6, "sm_throughput_pct": 66.4, "issue_active_pct": 69.5}
+
+
+class L2Flush:
+    """Evicts L2 (129 MB) between timed steps: a 512 MiB write, then, when
+    clean, a 512 MiB read of a second buffer, which writes the first one's
+    dirty lines back before the timed work instead of inside it.  Runs on
+    torch's current stream (the library's)."""
+
+    def __init__(self, torch, dev):
+        self.w = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        self.r = torch.ones(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        self.sink = None
+
+    def __call__(self, k, clean=True):
+        self.w.fill_(float(k))
+        if clean:
+            self.sink = self.r.sum()
 
 
 def parse(argv=None):
@@ -98,7 +119,7 @@ def workload_config(sc):
             "n_low": len(sc["lr_pos"]), "n_high": len(sc["hr_pos"]), "r_low": sc["r_low"],
             "ratio": sc["ratio"], "dt": DT, "lr_solver_iters": sc["iters"], "n_stab": 2,
             "hr_reorder_every": 8, "lr_steps_per_frame": N_SUB, "dt_low": DT / N_SUB,
-            "l2": "flushed between timed steps (512 MiB write)"}
+            "l2": "flushed between timed steps (512 MiB write, then a 512 MiB read that leaves no dirty line)"}
 
 
 def bucket_at(sc, frame):
@@ -159,14 +180,18 @@ class Clocks:
 
 
 # ------------------------------------------------------- CPU baseline ---
-def oracle_frame_rate(sc, budget_s, sample_hr=1_000_000):
-    """HR particles/s of the FP64 oracle on host cores: one LR step of the
-    whole LR set plus the upsampling of a random HR subset, scaled to the
-    full frame, repeated until the time budget is used."""
+CPU_SAMPLE_HR = 200_000   # HR particles per sample, the same in both arms
+
+
+def oracle_frame_rate(sc, budget_s, sample_hr=CPU_SAMPLE_HR):
+    """HR particles/s of the FP64 oracle's plain definitions on the host
+    cores: the frame's LR steps of the whole LR set plus the HR frame of a
+    random HR subset, scaled to the full frame, repeated until the time
+    budget is used.  The LR steps are timed on one thread and on every core
+    (the value uses every core); the HR sample on every core."""
     import oracle
     oracle.build()
-    cores = os.cpu_count() or 1
-    oracle.set_threads(cores)
+    cores = oracle.max_threads()
     r = sc["r_low"]
     g = sc["gravity"]
     pp = dict(r=r, dt=DT / N_SUB, gx=g[0], gy=g[1], gz=g[2], mu_s=sc["mu_s"], mu_k=sc["mu_k"], n_stab=2,
@@ -180,25 +205,35 @@ def oracle_frame_rate(sc, budget_s, sample_hr=1_000_000):
     sdf = scenes.sdf_table(sc["sdfs"])
     lr_x, lr_v, im = sc["lr_pos"][:, :3], sc["lr_vel"][:, :3], sc["lr_pos"][:, 3]
     hr_x, hr_v = sc["hr_pos"][:, :3], sc["hr_vel"][:, :3]
+
+    def lr_steps(threads):
+        oracle.set_threads(threads)
+        t0 = time.perf_counter()
+        x1, v1 = lr_x, lr_v
+        for _ in range(N_SUB):
+            x1, v1 = oracle.pbd_step_plain(x1, v1, im, sdf, pp)
+        return x1, v1, time.perf_counter() - t0
+
+    _, _, t_lr1 = lr_steps(1)                     # once on one thread
     t_lr = t_up = 0.0
     reps = 0
     t_start = time.perf_counter()
     while reps == 0 or time.perf_counter() - t_start < budget_s:
         sub = np.sort(rng.choice(M, size=ns, replace=False))
+        x1, v1, t = lr_steps(cores)
         t0 = time.perf_counter()
-        x1, v1 = lr_x, lr_v
-        for _ in range(N_SUB):
-            x1, v1, _, _ = oracle.pbd_step(x1, v1, im, sdf, pp, mode=1)
-        t1 = time.perf_counter()
-        oracle.upsample(x1, v1, hr_x, hr_v, sdf, up, sub=sub, mode=1)
-        t2 = time.perf_counter()
-        t_lr += t1 - t0
-        t_up += t2 - t1
+        oracle.upsample_plain(x1, v1, hr_x[sub], hr_v[sub], sdf, up)
+        t_up += time.perf_counter() - t0
+        t_lr += t
         reps += 1
+    oracle.set_threads(1)
     frame_s = (t_lr + t_up * M / ns) / reps
     return {"value": M / frame_s, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{reps} x ({N_SUB} FP64 LR steps of all {len(lr_x)} LR particles on 1 thread + upsampling of "
-                      f"{ns} random HR particles on {cores} threads), scaled to the {M}-particle frame"}
+            "lr_steps_ms_1_thread": 1e3 * t_lr1, f"lr_steps_ms_{cores}_threads": 1e3 * t_lr / reps,
+            "hr_us_per_particle": 1e6 * t_up / reps / ns,
+            "sample": f"{reps} x ({N_SUB} FP64 LR steps of all {len(lr_x)} LR particles + the HR frame of {ns} "
+                      f"random HR particles, on {cores} threads; the oracle's plain definitions), scaled to the "
+                      f"{M}-particle frame; the LR steps also timed once on 1 thread"}
 
 
 # ----------------------------------------------------------- batched ---
@@ -232,10 +267,10 @@ def run_batched(args, dev, stream, gs, torch):
     torch.cuda.synchronize(dev)
     k = max(5, args.steps // 5)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(torch, dev)
     l0 = batch.launches()
     for i in range(k):
-        flush.fill_(float(i))
+        flush(i)
         ev[i][0].record(stream)
         batch.frame(DT, N_SUB, iters)
         ev[i][1].record(stream)
@@ -252,7 +287,7 @@ def run_batched(args, dev, stream, gs, torch):
     k2 = 3
     ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k2)]
     for i in range(k2):
-        flush.fill_(float(i))
+        flush(i)
         ev2[i][0].record(stream)
         for c in ctxs:
             c.frame(DT, N_SUB, iters)
@@ -381,7 +416,7 @@ def run_gpu(args):
     sc = make_scene(args.workload, args.bed_size)
     N, M = len(sc["lr_pos"]), len(sc["hr_pos"])
     ctx = gs.Context(sc, stream=stream.cuda_stream)
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(torch, dev)
     frame = [0]
 
     def step(c, adaptive=False):
@@ -448,21 +483,30 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     wall0 = time.perf_counter()
     for k in range(args.steps):
-        flush.fill_(float(k))
+        flush(k)
         starts[k].record(stream)
         step(ctx)
         ends[k].record(stream)
     torch.cuda.synchronize(dev)
     barrier()
     wall = time.perf_counter() - wall0
-    time.sleep(0.15)
-    clocks = clk.stop()
-    if clocks:
-        clocks["window"] = "warm-up and timed steps"
     launches = ctx.launches() - launches0
     ctx.sync()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = float(sum(step_ms))
+    # the same frames after a write-only flush: its dirty lines are written
+    # back while the frame runs (reported beside the clean-flush number)
+    for k in range(args.steps):
+        flush(k, clean=False)
+        starts[k].record(stream)
+        step(ctx)
+        ends[k].record(stream)
+    torch.cuda.synchronize(dev)
+    dirty_ms = float(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
+    time.sleep(0.15)
+    clocks = clk.stop()
+    if clocks:
+        clocks["window"] = "warm-up and both timed loops"
 
     # The same frames with the library's event timers around each phase
     # (timers bypass the graphs): the breakdown and the gather kernel's
@@ -472,7 +516,7 @@ def run_gpu(args):
         ctx.timing_read(t)
     n_brk = max(4, args.steps // 2)
     for k in range(n_brk):
-        flush.fill_(float(k))
+        flush(k)
         step(ctx)
     torch.cuda.synchronize(dev)
     ctx.sync()
@@ -482,6 +526,7 @@ def run_gpu(args):
     rs_ms, rs_n = ctx.timing_read(gs.GS_TIMER_RESORT)
     ctx.set_timing(False)
     total_ms = max_over_ranks(total_ms, world, dev)
+    dirty_ms = max_over_ranks(dirty_ms, world, dev)
     ms_per_step = total_ms / args.steps
     value = whole_job_rate(M * args.steps, world, total_ms / 1e3)
 
@@ -651,6 +696,10 @@ def run_gpu(args):
         "pipeline": pipe,
         "upsample_kernel_hr_per_s": M / gather_avg_s,
         "wall_s_timed_region": wall,
+        "l2_write_only_flush": {"ms_per_step": dirty_ms / args.steps,
+                                "value": whole_job_rate(M * args.steps, world, dirty_ms / 1e3),
+                                "note": "the same frames after a 512 MiB write alone, whose dirty lines are "
+                                        "written back while the frame runs"},
         "gpu_launches": int(launches),
         "clocks": clocks,
         "e2e": e2e,
@@ -690,7 +739,7 @@ def run_slab(args):
     sc = make_scene(args.workload, args.bed_size)
     M = len(sc["hr_pos"])
     ctx = gs.Context(sc, stream=stream.cuda_stream)
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(torch, dev)
     if args.gather_shape:
         ctx.set_tuning(*(int(t) for t in args.gather_shape.split("x")))
     ctx.set_hr_slab(rank, world)
@@ -721,7 +770,7 @@ def run_slab(args):
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     total_ms = 0.0
     for k in range(args.steps):
-        flush.fill_(float(k))
+        flush(k)
         start.record(stream)
         step()
         end.record(stream)
@@ -759,11 +808,11 @@ def run_reference(args):
     sc = make_scene(args.workload, args.bed_size)
     per = min(8.0, max(1.0, 120.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        oracle_frame_rate(sc, 0.0, sample_hr=50_000)
+        oracle_frame_rate(sc, 0.0, sample_hr=20_000)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(oracle_frame_rate(sc, per, sample_hr=200_000))
+        vals.append(oracle_frame_rate(sc, per))
     wall = time.perf_counter() - t0
     v = float(np.mean([a["value"] for a in vals]))
     M = len(sc["hr_pos"])
@@ -771,8 +820,8 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * M / v, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded scene generators)",
             "config": workload_config(sc), "wall_s": wall,
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
-                             "sample": vals[0]["sample"]},
+            "cpu_baseline": dict({k: a for k, a in vals[0].items() if k not in ("value", "sample")},
+                                 value=v, sample=f"{len(vals)} step(s), each: " + vals[0]["sample"]),
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

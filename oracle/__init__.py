@@ -102,6 +102,10 @@ def _L():
         L.or_pbd_step_tape.argtypes = [P, P, P, ctypes.c_long, P, ctypes.c_int, P, ctypes.c_int, P, ctypes.c_long,
                                        P]
         L.or_pbd_step_tape.restype = ctypes.c_int
+        L.or_upsample_plain.argtypes = [P, P, ctypes.c_long, P, P, ctypes.c_long, P, ctypes.c_int, P, P, P]
+        L.or_upsample_plain.restype = ctypes.c_int
+        L.or_pbd_step_plain.argtypes = [P, P, P, ctypes.c_long, P, ctypes.c_int, P]
+        L.or_pbd_step_plain.restype = ctypes.c_int
         L.or_pairs_within_grid.argtypes = L.or_pairs_within.argtypes
         L.or_pairs_within_grid.restype = ctypes.c_long
         _lib = L
@@ -257,6 +261,35 @@ def body_rest_offsets(x, inv_m, body):
         m = 1.0 / inv_m[sel]
         xo[sel] = x[sel] - (m[:, None] * x[sel]).sum(0) / m.sum()
     return xo
+
+
+def upsample_plain(lr_x, lr_v, hr_x, hr_v, sdf, prm):
+    """One HR frame of Sec. 4 as its plain definition (no decision margins
+    or tapes; parallel over HR particles).  Returns (x, v)."""
+    lr_x, lr_v = _f64(lr_x, 3), _f64(lr_v, 3)
+    hr_x, hr_v = _f64(hr_x, 3), _f64(hr_v, 3)
+    sdf = _f64(sdf, SDF_STRIDE) if sdf is not None and len(sdf) else np.zeros((0, SDF_STRIDE))
+    p = _prm(prm, UP_KEYS)
+    ox, ov = np.zeros_like(hr_x), np.zeros_like(hr_v)
+    rc = _L().or_upsample_plain(_ptr(lr_x), _ptr(lr_v), len(lr_x), _ptr(hr_x), _ptr(hr_v), len(hr_x), _ptr(sdf),
+                                len(sdf), _ptr(p), _ptr(ox), _ptr(ov))
+    if rc != 0:
+        raise RuntimeError(f"or_upsample_plain failed ({rc})")
+    return ox, ov
+
+
+def pbd_step_plain(x, v, inv_m, sdf, prm):
+    """One LR step of Algorithm 1 as its plain definition (no decision
+    margins or tapes; each particle gathers its own corrections, parallel
+    over particles).  Returns (x, v)."""
+    x, v = _f64(x, 3).copy(), _f64(v, 3).copy()
+    inv_m = _f64(inv_m)
+    sdf = _f64(sdf, SDF_STRIDE) if sdf is not None and len(sdf) else np.zeros((0, SDF_STRIDE))
+    p = _prm(prm, PB_KEYS)
+    rc = _L().or_pbd_step_plain(_ptr(x), _ptr(v), _ptr(inv_m), len(x), _ptr(sdf), len(sdf), _ptr(p))
+    if rc != 0:
+        raise RuntimeError(f"or_pbd_step_plain failed ({rc})")
+    return x, v
 
 
 def pbd_step(x, v, inv_m, sdf, prm, mode=0, mu=None, bodies=None):

@@ -1969,3 +1969,244 @@ int or_pbd_step_vjp_tape(const double* x0, const double* v0, const double* inv_m
     if (!tape) return -1;
     return pbd_vjp_impl(x0, v0, inv_m, N, sdf, n_sdf, prm, tape, tape_len, gx_out, gv_out, gx0, gv0);
 }
+
+/* ------------------------------------------------------------------ */
+/* Plain definitions.                                                   */
+/*                                                                      */
+/* The LR step and the HR frame once more, as the paper states them and */
+/* nothing else: no decision margins, tapes or branch bookkeeping, each */
+/* particle's sums gathered by the particle itself (so the loops over   */
+/* particles run in parallel without changing a bit).  They read like   */
+/* Algorithm 1 and Sec. 4 and are checked bit for bit against the       */
+/* instrumented functions above (same partners in the same ascending    */
+/* order, same expressions), which carry the pins.  Scene coefficients */
+/* only (no materials, bodies or solid particles).                      */
+/* ------------------------------------------------------------------ */
+
+/* One HR frame of Sec. 4 for every HR particle:
+ *   w_ij = max(0, 1 - |x_i - x_j|^2 / (3 r_LR)^2)^3 over LR particles j,
+ *   vtilde = sum w v_j / sum w (0 when the sum is 0),
+ *   alpha = 1 - max w if max w <= c1 or max w >= c2 sum w, else 0,
+ *   v = (1 - alpha) vtilde + alpha (v + dt g),  x = x + dt v,
+ * then the SDF rule per component in order (phi < r_HR: move to
+ * phi = r_HR along the normal, remove the normal velocity into the
+ * boundary relative to its velocity).  LR partners in ascending index. */
+int or_upsample_plain(const double* lr_x, const double* lr_v, long N, const double* hr_x, const double* hr_v,
+                      long M, const double* sdf, int n_sdf, const double* prm, double* out_x, double* out_v)
+{
+    const double r = prm[UP_R_LOW], c1 = prm[UP_C1], c2 = prm[UP_C2], dt = prm[UP_DT], rh = prm[UP_R_HIGH];
+    const double eps_x = prm[UP_EPS_X], R2 = 9.0 * r * r;
+    const double g[3] = {prm[UP_GX], prm[UP_GY], prm[UP_GZ]};
+    or_grid_t grid;
+    if (grid_build(&grid, lr_x, N, 3.0 * r) != 0) return -1;
+    int err = 0;
+    const int nth = g_threads;
+#pragma omp parallel num_threads(nth) if (nth > 1)
+    {
+        long* near = (long*)malloc((size_t)(N ? N : 1) * sizeof(long));
+        if (!near) err = -1;
+#pragma omp for schedule(dynamic, 64)
+        for (long i = 0; i < M; ++i) {
+            if (!near) continue;
+            const double *xi = hr_x + 3 * i, *vi = hr_v + 3 * i;
+            double S = 0, V[3] = {0, 0, 0}, wmax = 0;
+            const long nn = grid_query(&grid, xi, near);   /* within 3 r_LR, ascending */
+            for (long q = 0; q < nn; ++q) {
+                const long j = near[q];
+                double d[3] = {xi[0] - lr_x[3 * j], xi[1] - lr_x[3 * j + 1], xi[2] - lr_x[3 * j + 2]};
+                double d2 = dot3(d, d);
+                if (!(d2 < R2)) continue;
+                double w = or_weight(d2, r);
+                S += w;
+                for (int m = 0; m < 3; ++m) V[m] += w * lr_v[3 * j + m];
+                if (w > wmax) wmax = w;
+            }
+            double vt[3] = {0, 0, 0};
+            if (S > 0)
+                for (int m = 0; m < 3; ++m) vt[m] = V[m] / S;
+            const double alpha = (wmax <= c1 || (S > 0 && wmax >= c2 * S)) ? 1.0 - wmax : 0.0;
+            double *xo = out_x + 3 * i, *vo = out_v + 3 * i;
+            for (int m = 0; m < 3; ++m) {
+                vo[m] = (1.0 - alpha) * vt[m] + alpha * (vi[m] + dt * g[m]);
+                xo[m] = xi[m] + dt * vo[m];
+            }
+            for (int s = 0; s < n_sdf; ++s) {
+                const double *rec = sdf + OR_SDF_STRIDE * s, *ub = rec + 13;
+                for (int c = 0; c < sdf_ncomp(rec); ++c) {
+                    double phi[OR_MAX_COMP], nrm[3 * OR_MAX_COMP];
+                    int tie;
+                    or_sdf_eval(rec, xo, phi, nrm, &tie, eps_x);   /* after the previous component moved it */
+                    if (!(phi[c] < rh)) continue;
+                    const double* n = nrm + 3 * c;
+                    const double push = rh - phi[c];
+                    for (int m = 0; m < 3; ++m) xo[m] += push * n[m];
+                    double vr[3] = {vo[0] - ub[0], vo[1] - ub[1], vo[2] - ub[2]};
+                    const double vn = dot3(vr, n);
+                    if (vn < 0)
+                        for (int m = 0; m < 3; ++m) vo[m] -= vn * n[m];
+                }
+            }
+        }
+        free(near);
+    }
+    grid_free(&grid);
+    return err;
+}
+
+/* Friction of Eqs. 3-4 on a tangential displacement perp: all of it below
+ * the static threshold, else the kinetic fraction thr_k / |perp| (capped at
+ * the whole displacement). */
+static void plain_friction(const double* perp, double thr_s, double thr_k, double* f)
+{
+    const double L = sqrt(dot3(perp, perp));
+    const double kin = (L > 0 && thr_k / L < 1.0) ? thr_k / L : 1.0;
+    const double scale = L < thr_s ? 1.0 : kin;
+    for (int k = 0; k < 3; ++k) f[k] = perp[k] * scale;
+}
+
+/* One LR step, Algorithm 1 (Sec. 3), with the readings of the instrumented
+ * or_pbd_step: predict (v += dt g for movable particles, xt = x + dt v,
+ * inverse mass scaled by e^{k (z - ground)}); candidate partners
+ * |xt_i - xt_j| < Rc; n_stab contact-only passes evaluated on x and applied
+ * to x and xt; iters passes of contacts (Eqs. 1-2) and friction (Eqs. 3-4)
+ * on xt, with the relative displacement over the step as the friction
+ * displacement; every analytic SDF component is a partner of infinite mass;
+ * Jacobi averaging x += (1/n_i) sum of the particle's corrections; then
+ * v = (xt - x) / dt, x = xt.  x, v: double[N][3], updated in place. */
+int or_pbd_step_plain(double* x, double* v, const double* inv_m, long N, const double* sdf, int n_sdf,
+                      const double* prm)
+{
+    const int n_stab = (int)prm[PB_N_STAB], iters = (int)prm[PB_ITERS], fmode = (int)prm[PB_FRIC_MODE];
+    const double r = prm[PB_R], dt = prm[PB_DT], Rc = prm[PB_RC], eps_x = prm[PB_EPS_X];
+    const double mu_s = prm[PB_MU_S], mu_k = prm[PB_MU_K], d0 = 2.0 * r;
+    const size_t n1 = (size_t)(N ? N : 1);
+    double* xt = (double*)malloc(n1 * 3 * sizeof(double));
+    double* ws = (double*)malloc(n1 * sizeof(double));
+    double* D = (double*)malloc(n1 * 3 * sizeof(double));
+    long* n_i = (long*)malloc(n1 * sizeof(long));
+    long* first = (long*)calloc(n1 + 1, sizeof(long));   /* partners of i: partner[first[i] .. first[i+1]) */
+    long* partner = NULL;
+    int rc = (xt && ws && D && n_i && first) ? 0 : -1;
+    or_grid_t grid;
+    int have_grid = 0;
+    if (rc == 0) {
+        pbd_predict(x, v, inv_m, N, prm, xt, ws);
+        rc = grid_build(&grid, xt, N, Rc);
+        have_grid = rc == 0;
+    }
+    /* candidate partners from the predicted positions, ascending: counted,
+     * then listed */
+    const int nth = g_threads;
+    for (int round = 0; round < 2 && rc == 0; ++round) {
+#pragma omp parallel num_threads(nth) if (nth > 1)
+        {
+            long* near = (long*)malloc(n1 * sizeof(long));
+            if (!near) rc = -1;
+#pragma omp for schedule(dynamic, 256)
+            for (long i = 0; i < N; ++i) {
+                if (!near) continue;
+                const long nn = grid_query(&grid, xt + 3 * i, near);
+                long c = 0;
+                for (long q = 0; q < nn; ++q) {
+                    if (near[q] == i) continue;
+                    if (round) partner[first[i] + c] = near[q];
+                    ++c;
+                }
+                if (!round) first[i + 1] = c;
+            }
+            free(near);
+        }
+        if (round || rc) continue;
+        for (long i = 0; i < N; ++i) first[i + 1] += first[i];
+        if (!(partner = (long*)malloc((size_t)(first[N] ? first[N] : 1) * sizeof(long)))) rc = -1;
+    }
+    for (int it = 0; it < n_stab + iters && rc == 0; ++it) {
+        const int stab = it < n_stab;
+        const double* y = stab ? x : xt;   /* where the constraints are evaluated */
+#pragma omp parallel for num_threads(nth) if (nth > 1) schedule(dynamic, 256)
+        for (long i = 0; i < N; ++i) {
+            double Di[3] = {0, 0, 0};
+            long cnt = 0;
+            /* Eqs. 1-2 (and 3-4) of each pair, evaluated from its lower index */
+            for (long q = first[i]; q < first[i + 1]; ++q) {
+                const long j = partner[q], a = i < j ? i : j, b = i < j ? j : i;
+                double xab[3] = {y[3 * b] - y[3 * a], y[3 * b + 1] - y[3 * a + 1], y[3 * b + 2] - y[3 * a + 2]};
+                const double d2 = dot3(xab, xab), d = sqrt(d2);
+                if (!(d < d0) || d2 == 0.0) continue;
+                const double wsum = ws[a] + ws[b];
+                if (!(wsum > 0)) continue;
+                const double ma = ws[a] / wsum, mb = ws[b] / wsum, pen = d0 - d;
+                double ca[3], cb[3];
+                for (int k = 0; k < 3; ++k) {
+                    const double u = xab[k] / d;
+                    ca[k] = -ma * pen * u;
+                    cb[k] = mb * pen * u;
+                }
+                if (!stab) {
+                    double dx[3], perp[3], f[3];
+                    for (int k = 0; k < 3; ++k) dx[k] = (xt[3 * a + k] - x[3 * a + k]) - (xt[3 * b + k] - x[3 * b + k]);
+                    const double s = dot3(dx, xab) / d2;
+                    for (int k = 0; k < 3; ++k) perp[k] = dx[k] - s * xab[k];
+                    const double base = fmode == 1 ? pen : d0;
+                    plain_friction(perp, base * mu_s, base * mu_k, f);
+                    for (int k = 0; k < 3; ++k) {
+                        ca[k] -= ma * f[k];
+                        cb[k] += mb * f[k];
+                    }
+                }
+                for (int k = 0; k < 3; ++k) Di[k] += i == a ? ca[k] : cb[k];
+                ++cnt;
+            }
+            /* boundary contacts: partners of infinite mass */
+            for (int s = 0; s < n_sdf && ws[i] > 0; ++s) {
+                const double *rec = sdf + OR_SDF_STRIDE * s, *ub = rec + 13;
+                const double bmu_s = sqrt(mu_s * rec[16]), bmu_k = sqrt(mu_k * rec[17]);
+                double phi[OR_MAX_COMP], nrm[3 * OR_MAX_COMP];
+                int tie;
+                const int nc = or_sdf_eval(rec, y + 3 * i, phi, nrm, &tie, eps_x);
+                for (int c = 0; c < nc; ++c) {
+                    if (!(phi[c] < r)) continue;
+                    const double *n = nrm + 3 * c, pen = r - phi[c];
+                    double ci[3];
+                    for (int k = 0; k < 3; ++k) ci[k] = pen * n[k];
+                    if (!stab) {
+                        double dx[3], perp[3], f[3];
+                        for (int k = 0; k < 3; ++k) dx[k] = (xt[3 * i + k] - x[3 * i + k]) - ub[k] * dt;
+                        const double s2 = dot3(dx, n);
+                        for (int k = 0; k < 3; ++k) perp[k] = dx[k] - s2 * n[k];
+                        const double base = fmode == 1 ? pen : d0;
+                        plain_friction(perp, base * bmu_s, base * bmu_k, f);
+                        for (int k = 0; k < 3; ++k) ci[k] -= f[k];
+                    }
+                    for (int k = 0; k < 3; ++k) Di[k] += ci[k];
+                    ++cnt;
+                }
+            }
+            for (int k = 0; k < 3; ++k) D[3 * i + k] = Di[k];
+            n_i[i] = cnt;
+        }
+        /* Jacobi averaging */
+        for (long i = 0; i < N; ++i) {
+            if (n_i[i] == 0) continue;
+            for (int k = 0; k < 3; ++k) {
+                const double dd = D[3 * i + k] / (double)n_i[i];
+                xt[3 * i + k] += dd;
+                if (stab) x[3 * i + k] += dd;
+            }
+        }
+    }
+    if (rc == 0)
+        for (long i = 0; i < N; ++i)
+            for (int k = 0; k < 3; ++k) {
+                v[3 * i + k] = (xt[3 * i + k] - x[3 * i + k]) / dt;
+                x[3 * i + k] = xt[3 * i + k];
+            }
+    if (have_grid) grid_free(&grid);
+    free(partner);
+    free(first);
+    free(n_i);
+    free(D);
+    free(ws);
+    free(xt);
+    return rc;
+}

@@ -100,6 +100,8 @@ def parse(argv=None):
                     help="under torchrun: every rank steps its own replica of the scene (weak scaling), or the "
                          "ranks split one scene's HR slots into slabs, each computing the LR state itself, with "
                          "one all-gather of the slabs before each HR reorder (strong scaling)")
+    ap.add_argument("--diff-only", action="store_true",
+                    help="time the differentiable rollout alone (--warmup and --steps count rollouts); for profilers")
     ap.add_argument("--batch-scenes", type=int, default=256)
     ap.add_argument("--gather-shape", default=None, metavar="WxB",
                     help="fix the gather's launch shape (warps per block x blocks per SM, 0: one item per warp) "
@@ -306,16 +308,17 @@ def run_batched(args, dev, stream, gs, torch):
                                                                    "upsample_us": tus}}
 
 
-def run_diff(args, dev, stream, gs, torch):
+def run_diff(args, dev, stream, gs, torch, reps=None, warm=2, with_plain=True):
     """The differentiable form on the falling-column workload (4k LR / 64k
     HR, 30 steps of one LR step and one HR frame, recomputation checkpoints
     every 5 steps): forward + loss + backward to the initial LR velocities,
-    against the plain in-place forward of the same rollout."""
+    against the plain in-place forward of the same rollout.  reps timed
+    rollouts of each (default max(3, steps / 10)) after warm untimed ones."""
     from paper_2308_01629_gb300.diff import rollout
     sc = scenes.diff_column()
     dt, F, iters, every = sc["dt"], sc["steps"], sc["iters"], sc["checkpoint_every"]
     M = len(sc["hr_pos"])
-    k = max(3, args.steps // 10)
+    k = max(3, args.steps // 10) if reps is None else reps
     with torch.cuda.stream(stream):
         plain = gs.Context(sc, stream=stream.cuda_stream)
         ctx = gs.Context(sc, stream=stream.cuda_stream)
@@ -338,7 +341,7 @@ def run_diff(args, dev, stream, gs, torch):
             return V.grad
 
         def timed(fn):
-            for _ in range(2):
+            for _ in range(warm):
                 fn()
             torch.cuda.synchronize(dev)
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
@@ -349,17 +352,31 @@ def run_diff(args, dev, stream, gs, torch):
             torch.cuda.synchronize(dev)
             return sum(a.elapsed_time(b) for a, b in ev) / k
 
-        ms_plain = timed(plain_rollout)
+        ms_plain = timed(plain_rollout) if with_plain else None
         l0 = ctx.launches()
         ms_diff = timed(diff_rollout)
-        nl = (ctx.launches() - l0) / (k + 2)
+        nl = (ctx.launches() - l0) / (k + warm)
         plain.close()
         ctx.close()
     return {"workload": f"falling column {len(sc['lr_pos'])} LR / {M} HR, {F} steps of {dt:.6f} s, "
                         f"checkpoint every {every}", "loss": "sum |x_HR - target|^2 after the rollout",
             "plain_forward_ms_per_rollout": ms_plain, "forward_backward_ms_per_rollout": ms_diff,
             "forward_backward_hr_steps_per_s": M * F / (ms_diff / 1e3),
-            "backward_overhead_vs_plain_forward": ms_diff / ms_plain, "library_kernels_per_rollout": nl}
+            "backward_overhead_vs_plain_forward": ms_diff / ms_plain if ms_plain else None,
+            "library_kernels_per_rollout": nl}
+
+
+def run_diff_only(args):
+    """--diff-only: the differentiable rollout alone (--warmup untimed and
+    --steps timed rollouts, no plain forward), for profiler runs."""
+    import torch
+
+    import paper_2308_01629_gb300 as gs
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    return {"differentiable": run_diff(args, dev, stream, gs, torch, reps=max(1, args.steps), warm=args.warmup,
+                                       with_plain=False)}
 
 
 def frame_ms(fn, stream, dev, torch, warm=2, reps=3):
@@ -829,6 +846,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         line = run_reference(args)
+    elif args.diff_only:
+        line = run_diff_only(args)
     elif args.partition == "slab":
         line = run_slab(args)
     else:

@@ -36,6 +36,7 @@ __device__ __forceinline__ int cell_of(float x, float o, float inv_h, int dim)
 }
 
 constexpr int kMaxSteps = 32;
+constexpr int kBwdLanes = 4;
 
 // rec (optional): the decisions this reverse mode differentiates, four words
 // per HR particle: the LR particle of largest weight (original index through
@@ -46,14 +47,21 @@ __global__ void k_upsample_bwd(const SceneDev* __restrict__ scenes, const gs_sdf
                                const uint32_t* __restrict__ cell_start, const float4* __restrict__ hx,
                                const float4* __restrict__ hv, const float4* __restrict__ gxo,
                                const float4* __restrict__ gvo, float4* __restrict__ ghx, float4* __restrict__ ghv,
-                               float* __restrict__ gXs, float* __restrict__ gVs, int64_t m, float dt,
+                               float4* __restrict__ gXs, float4* __restrict__ gVs, int64_t m, float dt,
                                uint32_t* __restrict__ rec, const uint32_t* __restrict__ lr_idx)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
+    // kBwdLanes lanes per HR particle: lane `sub` takes the LR candidates
+    // sub, sub + kBwdLanes, ... of every row of cells; the lanes' partial
+    // sums meet in shuffles, and each lane pushes its own candidates'
+    // gradients.  Every lane stays until the last shuffle.
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = t / kBwdLanes;
+    const int sub = (int)(t % kBwdLanes);
+    const bool live = i < m;
     const SceneDev& sc = scenes[0];
     const GridDev& g = sc.g;
-    const float4 p = hx[i], v = hv[i];
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 p = live ? hx[i] : zero4, v = live ? hv[i] : zero4;
     const float R = 3.0f * sc.r_low;
     const float R2 = R * R;
     const float inv9r2 = 1.0f / R2;
@@ -63,11 +71,11 @@ __global__ void k_upsample_bwd(const SceneDev* __restrict__ scenes, const gs_sdf
     // forward
     float S = 0.f, Vx = 0.f, Vy = 0.f, Vz = 0.f, wmax = 0.f;
     uint32_t jstar = 0xffffffffu;
-    for (int cz = cz0; cz <= cz1; ++cz)
+    for (int cz = cz0; live && cz <= cz1; ++cz)
         for (int cy = cy0; cy <= cy1; ++cy) {
             const int64_t row = (int64_t)sc.cell_off + ((int64_t)cz * g.dy + cy) * g.dx;
             const uint32_t b = cell_start[row + cx0], e = cell_start[row + cx1 + 1];
-            for (uint32_t j = b; j < e; ++j) {
+            for (uint32_t j = b + sub; j < e; j += kBwdLanes) {
                 const float4 q = lr_spos[j];
                 const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
                 const float d2 = dx * dx + dy * dy + dz * dz;
@@ -85,6 +93,21 @@ __global__ void k_upsample_bwd(const SceneDev* __restrict__ scenes, const gs_sdf
                 }
             }
         }
+    // the lanes' sums; the largest weight with the lowest slot among equals
+    // (the first one met in slot order)
+#pragma unroll
+    for (int o = 1; o < kBwdLanes; o <<= 1) {
+        S += __shfl_xor_sync(0xffffffffu, S, o);
+        Vx += __shfl_xor_sync(0xffffffffu, Vx, o);
+        Vy += __shfl_xor_sync(0xffffffffu, Vy, o);
+        Vz += __shfl_xor_sync(0xffffffffu, Vz, o);
+        const float w2 = __shfl_xor_sync(0xffffffffu, wmax, o);
+        const uint32_t j2 = __shfl_xor_sync(0xffffffffu, jstar, o);
+        if (w2 > wmax || (w2 == wmax && j2 < jstar)) {
+            wmax = w2;
+            jstar = j2;
+        }
+    }
     float vtx = 0.f, vty = 0.f, vtz = 0.f;
     if (S > 0.0f) {
         vtx = Vx / S;
@@ -128,14 +151,14 @@ __global__ void k_upsample_bwd(const SceneDev* __restrict__ scenes, const gs_sdf
             }
         }
     }
-    if (rec) {
+    if (rec && live && sub == 0) {
         rec[4 * i + 0] = jstar != 0xffffffffu ? lr_idx[jstar] : 0xffffffffu;
         rec[4 * i + 1] = branch ? 1u : 0u;
         rec[4 * i + 2] = act_bits;
         rec[4 * i + 3] = rem_bits;
     }
     // reverse
-    float4 go = gxo[i], gw = gvo[i];
+    const float4 go = live ? gxo[i] : zero4, gw = live ? gvo[i] : zero4;
     float ax = go.x, ay = go.y, az = go.z, avx = gw.x, avy = gw.y, avz = gw.z;
     for (int k = n_steps - 1; k >= 0; --k) {
         if (vrem[k]) {
@@ -149,20 +172,21 @@ __global__ void k_upsample_bwd(const SceneDev* __restrict__ scenes, const gs_sdf
         ay -= d * ny_[k];
         az -= d * nz_[k];
     }
-    float gpx = ax, gpy = ay, gpz = az;   // dL/dx (HR input)
+    // dL/dx (HR input): the direct term on lane 0, each lane's candidates' terms
+    float gpx = sub == 0 ? ax : 0.f, gpy = sub == 0 ? ay : 0.f, gpz = sub == 0 ? az : 0.f;
     const float gvpx = avx + dt * ax, gvpy = avy + dt * ay, gvpz = avz + dt * az;
     const float gvtx = (1.0f - alpha) * gvpx, gvty = (1.0f - alpha) * gvpy, gvtz = (1.0f - alpha) * gvpz;
     const float galpha = gvpx * (bx - vtx) + gvpy * (by - vty) + gvpz * (bz - vtz);
     const float gwmax = branch ? -galpha : 0.0f;
-    ghv[i] = make_float4(alpha * gvpx, alpha * gvpy, alpha * gvpz, 0.0f);
-    if (S > 0.0f) {
+    if (live && sub == 0) ghv[i] = make_float4(alpha * gvpx, alpha * gvpy, alpha * gvpz, 0.0f);
+    if (live && S > 0.0f) {
         const float gVx = gvtx / S, gVy = gvty / S, gVz = gvtz / S;
         const float gS = -(gvtx * vtx + gvty * vty + gvtz * vtz) / S;
         for (int cz = cz0; cz <= cz1; ++cz)
             for (int cy = cy0; cy <= cy1; ++cy) {
                 const int64_t row = (int64_t)sc.cell_off + ((int64_t)cz * g.dy + cy) * g.dx;
                 const uint32_t b = cell_start[row + cx0], e = cell_start[row + cx1 + 1];
-                for (uint32_t j = b; j < e; ++j) {
+                for (uint32_t j = b + sub; j < e; j += kBwdLanes) {
                     const float4 q = lr_spos[j];
                     const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
                     const float d2 = dx * dx + dy * dy + dz * dz;
@@ -172,19 +196,22 @@ __global__ void k_upsample_bwd(const SceneDev* __restrict__ scenes, const gs_sdf
                     const float4 qv = lr_svel[j];
                     const float gwj = gS + gVx * qv.x + gVy * qv.y + gVz * qv.z + (j == jstar ? gwmax : 0.0f);
                     const float k6 = gwj * 6.0f * t * t * inv9r2;
-                    atomicAdd(gXs + 4 * (int64_t)j + 0, k6 * dx);
-                    atomicAdd(gXs + 4 * (int64_t)j + 1, k6 * dy);
-                    atomicAdd(gXs + 4 * (int64_t)j + 2, k6 * dz);
-                    atomicAdd(gVs + 4 * (int64_t)j + 0, w * gVx);
-                    atomicAdd(gVs + 4 * (int64_t)j + 1, w * gVy);
-                    atomicAdd(gVs + 4 * (int64_t)j + 2, w * gVz);
+                    // one vector reduction per gradient (global float4 atomics, sm_90 and later)
+                    atomicAdd(gXs + j, make_float4(k6 * dx, k6 * dy, k6 * dz, 0.0f));
+                    atomicAdd(gVs + j, make_float4(w * gVx, w * gVy, w * gVz, 0.0f));
                     gpx -= k6 * dx;
                     gpy -= k6 * dy;
                     gpz -= k6 * dz;
                 }
             }
     }
-    ghx[i] = make_float4(gpx, gpy, gpz, 0.0f);
+#pragma unroll
+    for (int o = 1; o < kBwdLanes; o <<= 1) {
+        gpx += __shfl_xor_sync(0xffffffffu, gpx, o);
+        gpy += __shfl_xor_sync(0xffffffffu, gpy, o);
+        gpz += __shfl_xor_sync(0xffffffffu, gpz, o);
+    }
+    if (live && sub == 0) ghx[i] = make_float4(gpx, gpy, gpz, 0.0f);
 }
 
 // out[idx[p]] = in[p] for both arrays
@@ -301,33 +328,61 @@ __global__ void k_adj_init(int64_t n, const uint32_t* __restrict__ idx, const fl
     gws[p] = 0.0f;
 }
 
+// The reverse pass gives each LR particle kAdjLanes lanes of a warp: lane l
+// takes candidates l, l + kAdjLanes, ... and SDF components likewise, and
+// the lanes' sums are added up by shuffles (a small LR set, such as the 4k
+// particles of a differentiable rollout, then still fills the GPU).
+constexpr int kAdjLanes = 8;
+
+__device__ __forceinline__ float lanes_sum(float v)
+{
+#pragma unroll
+    for (int o = kAdjLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int lanes_sum(int v)
+{
+#pragma unroll
+    for (int o = kAdjLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // h_p = upstream_p / n_p for one pass (n_p = active pair and SDF contacts)
 __global__ void k_adj_h(const PbdArgs a, int stab, const float4* __restrict__ Y, const float4* __restrict__ WS,
                         const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ cnt,
                         const float4* __restrict__ gx, const float4* __restrict__ gxt, float4* __restrict__ H)
 {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.n) return;
-    const SceneDev& sc = a.scenes[a.lr_scene[p]];
-    const float d0 = 2.0f * sc.r_low;
-    const float4 yp = Y[p];
-    const float wp = WS[p].w;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t p = t / kAdjLanes;
+    const int lane = (int)(t % kAdjLanes);
+    const bool live = p < a.n;   // every lane stays for the shuffles
     int n_act = 0;
-    const int nc = (int)cnt[p];
-    for (int k = 0; k < nc; ++k) {
-        const uint32_t q = nbr[(int64_t)k * a.n + p];
-        const PairGeo g = pair_geo(yp, Y[q]);
-        if (!(g.d < d0) || g.d2 == 0.0f) continue;
-        if (!(wp + WS[q].w > 0.0f)) continue;
-        ++n_act;
-    }
-    if (wp > 0.0f)
-        for (int s = 0; s < sc.n_sdf; ++s) {
-            const gs_sdf& b = a.sdf[sc.sdf_begin + s];
-            const int ncomp = sdf_components(b.kind);
-            for (int c = 0; c < ncomp; ++c)
-                if (sdf_eval(b, c, yp.x, yp.y, yp.z).phi < sc.r_low) ++n_act;
+    if (live) {
+        const SceneDev& sc = a.scenes[a.lr_scene[p]];
+        const float d0 = 2.0f * sc.r_low;
+        const float4 yp = Y[p];
+        const float wp = WS[p].w;
+        const int nc = (int)cnt[p];
+        for (int k = lane; k < nc; k += kAdjLanes) {
+            const uint32_t q = nbr[(int64_t)k * a.n + p];
+            const PairGeo g = pair_geo(yp, Y[q]);
+            if (!(g.d < d0) || g.d2 == 0.0f) continue;
+            if (!(wp + WS[q].w > 0.0f)) continue;
+            ++n_act;
         }
+        if (wp > 0.0f) {
+            int gc = 0;   // component index over all the scene's SDFs
+            for (int s = 0; s < sc.n_sdf; ++s) {
+                const gs_sdf& b = a.sdf[sc.sdf_begin + s];
+                const int ncomp = sdf_components(b.kind);
+                for (int c = 0; c < ncomp; ++c, ++gc)
+                    if (gc % kAdjLanes == lane && sdf_eval(b, c, yp.x, yp.y, yp.z).phi < sc.r_low) ++n_act;
+            }
+        }
+    }
+    n_act = lanes_sum(n_act);
+    if (!live || lane != 0) return;
     float4 up = gxt[p];
     if (stab) {
         const float4 u2 = gx[p];
@@ -351,126 +406,138 @@ __global__ void k_adj_pass(const PbdArgs a, int stab, const float4* __restrict__
                            const float4* __restrict__ H, float4* __restrict__ gx, float4* __restrict__ gxt,
                            float* __restrict__ gws, const AdjRecord rec)
 {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.n) return;
-    const SceneDev& sc = a.scenes[a.lr_scene[p]];
-    const float d0 = 2.0f * sc.r_low;
-    const float4 yp = Y[p];
-    const float wp = WS[p].w;
-    const float4 hp4 = H[p];
-    const float hp[3] = {hp4.x, hp4.y, hp4.z};
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t p = t / kAdjLanes;
+    const int lane = (int)(t % kAdjLanes);
+    const bool live = p < a.n;   // every lane stays for the shuffles
     float acc[3] = {0.f, 0.f, 0.f}, accx[3] = {0.f, 0.f, 0.f}, gw = 0.0f;
-    const float4 xtp = XT[p], xfp = XF[p];
-    const int nc = (int)cnt[p];
-    const int64_t ri = rec.pair ? (int64_t)rec.idx[p] : 0;
-    if (rec.pair)
-        for (int k = nc; k < rec.cap; ++k) {
-            rec.cand[(int64_t)k * a.n + ri] = -1;
-            rec.pair[(int64_t)k * a.n + ri] = 0;
-        }
-    for (int k = 0; k < nc; ++k) {
-        const uint32_t q = nbr[(int64_t)k * a.n + p];
-        const float4 yq = Y[q];
-        const PairGeo g = pair_geo(yp, yq);
-        uint8_t* rb = nullptr;
-        if (rec.pair) {
-            rec.cand[(int64_t)k * a.n + ri] = (int32_t)rec.idx[q];
-            rb = rec.pair + (int64_t)k * a.n + ri;
-            *rb = g.d < d0 ? 1 : 0;
-        }
-        if (!(g.d < d0) || g.d2 == 0.0f) continue;
-        const float wq = WS[q].w;
-        const float W = wp + wq;
-        if (!(W > 0.0f)) continue;
-        const float mp = wp / W, mq = wq / W, pen = d0 - g.d;
-        const float e[3] = {g.ex, g.ey, g.ez};
-        const float u[3] = {g.ex / g.d, g.ey / g.d, g.ez / g.d};
-        const float4 hq4 = H[q];
-        const float hq[3] = {hq4.x, hq4.y, hq4.z};
-        M3 K;
-        m3_eye(K, d0 / g.d - 1.0f);
-        m3_outer_add(K, -d0 / g.d, u, u);
-        float tv[3] = {0.f, 0.f, 0.f};
-        m3_tmul_add(tv, -mp, K, hp);
-        m3_tmul_add(tv, mq, K, hq);
-        acc[0] -= tv[0];
-        acc[1] -= tv[1];
-        acc[2] -= tv[2];
-        const float uh = u[0] * (hp[0] + hq[0]) + u[1] * (hp[1] + hq[1]) + u[2] * (hp[2] + hq[2]);
-        gw += -pen * (wq / (W * W)) * uh;
-        if (!stab) {
-            const float4 xtq = XT[q], xfq = XF[q];
-            const float rel[3] = {(xtp.x - xfp.x) - (xtq.x - xfq.x), (xtp.y - xfp.y) - (xtq.y - xfq.y),
-                                  (xtp.z - xfp.z) - (xtq.z - xfq.z)};
-            const float base = sc.friction_mode == 1 ? pen : d0;
-            float F[3];
-            M3 Fr, Fe;
-            bool kin = false;
-            fric_jac(rel, e, g.d2, false, base * sc.mu_s, base * sc.mu_k, sc.friction_mode == 1, sc.mu_k, u, F, Fr,
-                     Fe, &kin);
-            if (rb && kin) *rb |= 2;
-            const float hF[3] = {-mp * hp[0] + mq * hq[0], -mp * hp[1] + mq * hq[1], -mp * hp[2] + mq * hq[2]};
-            float grel[3] = {0.f, 0.f, 0.f}, ge[3] = {0.f, 0.f, 0.f};
-            m3_tmul_add(grel, 1.0f, Fr, hF);
-            m3_tmul_add(ge, 1.0f, Fe, hF);
-#pragma unroll
-            for (int k2 = 0; k2 < 3; ++k2) {
-                acc[k2] += grel[k2] - ge[k2];
-                accx[k2] -= grel[k2];
+    if (live) {
+        const SceneDev& sc = a.scenes[a.lr_scene[p]];
+        const float d0 = 2.0f * sc.r_low;
+        const float4 yp = Y[p];
+        const float wp = WS[p].w;
+        const float4 hp4 = H[p];
+        const float hp[3] = {hp4.x, hp4.y, hp4.z};
+        const float4 xtp = XT[p], xfp = XF[p];
+        const int nc = (int)cnt[p];
+        const int64_t ri = rec.pair ? (int64_t)rec.idx[p] : 0;
+        if (rec.pair)
+            for (int k = nc + lane; k < rec.cap; k += kAdjLanes) {
+                rec.cand[(int64_t)k * a.n + ri] = -1;
+                rec.pair[(int64_t)k * a.n + ri] = 0;
             }
-            const float Fh = F[0] * (hp[0] + hq[0]) + F[1] * (hp[1] + hq[1]) + F[2] * (hp[2] + hq[2]);
-            gw += -(wq / (W * W)) * Fh;
+        for (int k = lane; k < nc; k += kAdjLanes) {
+            const uint32_t q = nbr[(int64_t)k * a.n + p];
+            const float4 yq = Y[q];
+            const PairGeo g = pair_geo(yp, yq);
+            uint8_t* rb = nullptr;
+            if (rec.pair) {
+                rec.cand[(int64_t)k * a.n + ri] = (int32_t)rec.idx[q];
+                rb = rec.pair + (int64_t)k * a.n + ri;
+                *rb = g.d < d0 ? 1 : 0;
+            }
+            if (!(g.d < d0) || g.d2 == 0.0f) continue;
+            const float wq = WS[q].w;
+            const float W = wp + wq;
+            if (!(W > 0.0f)) continue;
+            const float mp = wp / W, mq = wq / W, pen = d0 - g.d;
+            const float e[3] = {g.ex, g.ey, g.ez};
+            const float u[3] = {g.ex / g.d, g.ey / g.d, g.ez / g.d};
+            const float4 hq4 = H[q];
+            const float hq[3] = {hq4.x, hq4.y, hq4.z};
+            M3 K;
+            m3_eye(K, d0 / g.d - 1.0f);
+            m3_outer_add(K, -d0 / g.d, u, u);
+            float tv[3] = {0.f, 0.f, 0.f};
+            m3_tmul_add(tv, -mp, K, hp);
+            m3_tmul_add(tv, mq, K, hq);
+            acc[0] -= tv[0];
+            acc[1] -= tv[1];
+            acc[2] -= tv[2];
+            const float uh = u[0] * (hp[0] + hq[0]) + u[1] * (hp[1] + hq[1]) + u[2] * (hp[2] + hq[2]);
+            gw += -pen * (wq / (W * W)) * uh;
+            if (!stab) {
+                const float4 xtq = XT[q], xfq = XF[q];
+                const float rel[3] = {(xtp.x - xfp.x) - (xtq.x - xfq.x), (xtp.y - xfp.y) - (xtq.y - xfq.y),
+                                      (xtp.z - xfp.z) - (xtq.z - xfq.z)};
+                const float base = sc.friction_mode == 1 ? pen : d0;
+                float F[3];
+                M3 Fr, Fe;
+                bool kin = false;
+                fric_jac(rel, e, g.d2, false, base * sc.mu_s, base * sc.mu_k, sc.friction_mode == 1, sc.mu_k, u, F, Fr,
+                         Fe, &kin);
+                if (rb && kin) *rb |= 2;
+                const float hF[3] = {-mp * hp[0] + mq * hq[0], -mp * hp[1] + mq * hq[1], -mp * hp[2] + mq * hq[2]};
+                float grel[3] = {0.f, 0.f, 0.f}, ge[3] = {0.f, 0.f, 0.f};
+                m3_tmul_add(grel, 1.0f, Fr, hF);
+                m3_tmul_add(ge, 1.0f, Fe, hF);
+    #pragma unroll
+                for (int k2 = 0; k2 < 3; ++k2) {
+                    acc[k2] += grel[k2] - ge[k2];
+                    accx[k2] -= grel[k2];
+                }
+                const float Fh = F[0] * (hp[0] + hq[0]) + F[1] * (hp[1] + hq[1]) + F[2] * (hp[2] + hq[2]);
+                gw += -(wq / (W * W)) * Fh;
+            }
         }
-    }
-    if (rec.sdf)
-        for (int c = 0; c < rec.n_comp; ++c) rec.sdf[ri * rec.n_comp + c] = 0;
-    if (wp > 0.0f) {
-        int gc = 0;
-        for (int s = 0; s < sc.n_sdf; ++s) {
-            const gs_sdf& b = a.sdf[sc.sdf_begin + s];
-            const int ncomp = sdf_components(b.kind);
-            const float bmu_s = sqrtf(sc.mu_s * b.mu_s), bmu_k = sqrtf(sc.mu_k * b.mu_k);
-            for (int c = 0; c < ncomp; ++c, ++gc) {
-                const SdfHit h = sdf_eval(b, c, yp.x, yp.y, yp.z);
-                if (!(h.phi < sc.r_low)) continue;
-                uint8_t* sb = (rec.sdf && gc < rec.n_comp) ? rec.sdf + ri * rec.n_comp + gc : nullptr;
-                if (sb) *sb = 1;
-                const float n[3] = {h.nx, h.ny, h.nz};
-                const float an = n[0] * hp[0] + n[1] * hp[1] + n[2] * hp[2];
-                acc[0] -= an * n[0];
-                acc[1] -= an * n[1];
-                acc[2] -= an * n[2];
-                if (!stab) {
-                    const float pen = sc.r_low - h.phi;
-                    const float dv[3] = {(xtp.x - xfp.x) - b.vel[0] * a.dt, (xtp.y - xfp.y) - b.vel[1] * a.dt,
-                                         (xtp.z - xfp.z) - b.vel[2] * a.dt};
-                    const float base = sc.friction_mode == 1 ? pen : d0;
-                    float F[3];
-                    M3 Fr, Fe;
-                    bool kin = false;
-                    fric_jac(dv, n, 1.0f, true, base * bmu_s, base * bmu_k, false, bmu_k, n, F, Fr, Fe, &kin);
-                    if (sb && kin) *sb |= 2;
-                    float gd[3] = {0.f, 0.f, 0.f};
-                    m3_tmul_add(gd, -1.0f, Fr, hp);
-#pragma unroll
-                    for (int k2 = 0; k2 < 3; ++k2) {
-                        acc[k2] += gd[k2];
-                        accx[k2] -= gd[k2];
-                    }
-                    if (sc.friction_mode == 1) {
-                        const Tangent tg = tangent_part(dv[0], dv[1], dv[2], n[0], n[1], n[2], 1.0f);
-                        const float thr_s = base * bmu_s, thr_k = base * bmu_k;
-                        if (!(tg.L < thr_s) && tg.L > 0.0f && thr_k / tg.L < 1.0f) {
-                            const float q = (tg.tx * hp[0] + tg.ty * hp[1] + tg.tz * hp[2]) / tg.L;
-                            acc[0] += q * bmu_k * n[0];
-                            acc[1] += q * bmu_k * n[1];
-                            acc[2] += q * bmu_k * n[2];
+        if (rec.sdf)
+            for (int c = lane; c < rec.n_comp; c += kAdjLanes) rec.sdf[ri * rec.n_comp + c] = 0;
+        if (wp > 0.0f) {
+            int gc = 0;   // component index over all the scene's SDFs; lane gc % kAdjLanes takes it
+            for (int s = 0; s < sc.n_sdf; ++s) {
+                const gs_sdf& b = a.sdf[sc.sdf_begin + s];
+                const int ncomp = sdf_components(b.kind);
+                const float bmu_s = sqrtf(sc.mu_s * b.mu_s), bmu_k = sqrtf(sc.mu_k * b.mu_k);
+                for (int c = 0; c < ncomp; ++c, ++gc) {
+                    if (gc % kAdjLanes != lane) continue;
+                    const SdfHit h = sdf_eval(b, c, yp.x, yp.y, yp.z);
+                    if (!(h.phi < sc.r_low)) continue;
+                    uint8_t* sb = (rec.sdf && gc < rec.n_comp) ? rec.sdf + ri * rec.n_comp + gc : nullptr;
+                    if (sb) *sb = 1;
+                    const float n[3] = {h.nx, h.ny, h.nz};
+                    const float an = n[0] * hp[0] + n[1] * hp[1] + n[2] * hp[2];
+                    acc[0] -= an * n[0];
+                    acc[1] -= an * n[1];
+                    acc[2] -= an * n[2];
+                    if (!stab) {
+                        const float pen = sc.r_low - h.phi;
+                        const float dv[3] = {(xtp.x - xfp.x) - b.vel[0] * a.dt, (xtp.y - xfp.y) - b.vel[1] * a.dt,
+                                             (xtp.z - xfp.z) - b.vel[2] * a.dt};
+                        const float base = sc.friction_mode == 1 ? pen : d0;
+                        float F[3];
+                        M3 Fr, Fe;
+                        bool kin = false;
+                        fric_jac(dv, n, 1.0f, true, base * bmu_s, base * bmu_k, false, bmu_k, n, F, Fr, Fe, &kin);
+                        if (sb && kin) *sb |= 2;
+                        float gd[3] = {0.f, 0.f, 0.f};
+                        m3_tmul_add(gd, -1.0f, Fr, hp);
+    #pragma unroll
+                        for (int k2 = 0; k2 < 3; ++k2) {
+                            acc[k2] += gd[k2];
+                            accx[k2] -= gd[k2];
+                        }
+                        if (sc.friction_mode == 1) {
+                            const Tangent tg = tangent_part(dv[0], dv[1], dv[2], n[0], n[1], n[2], 1.0f);
+                            const float thr_s = base * bmu_s, thr_k = base * bmu_k;
+                            if (!(tg.L < thr_s) && tg.L > 0.0f && thr_k / tg.L < 1.0f) {
+                                const float q = (tg.tx * hp[0] + tg.ty * hp[1] + tg.tz * hp[2]) / tg.L;
+                                acc[0] += q * bmu_k * n[0];
+                                acc[1] += q * bmu_k * n[1];
+                                acc[2] += q * bmu_k * n[2];
+                            }
                         }
                     }
                 }
             }
         }
+    }   // live
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        acc[k] = lanes_sum(acc[k]);
+        accx[k] = lanes_sum(accx[k]);
     }
+    gw = lanes_sum(gw);
+    if (!live || lane != 0) return;
     if (stab) {
         float4 v = gx[p];
         gx[p] = make_float4(v.x + acc[0], v.y + acc[1], v.z + acc[2], 0.0f);
@@ -506,9 +573,8 @@ cudaError_t gs_launch_upsample_bwd(cudaStream_t s, const SceneDev* scenes, const
                                    const uint32_t* lr_idx)
 {
     if (m <= 0) return cudaSuccess;
-    k_upsample_bwd<<<gs_blocks(m, 128), 128, 0, s>>>(scenes, sdf, lr_spos, lr_svel, cell_start, hx, hv, gxo, gvo, ghx,
-                                                      ghv, reinterpret_cast<float*>(gXs),
-                                                      reinterpret_cast<float*>(gVs), m, dt, rec, lr_idx);
+    k_upsample_bwd<<<gs_blocks(m * kBwdLanes, 128), 128, 0, s>>>(scenes, sdf, lr_spos, lr_svel, cell_start, hx, hv, gxo, gvo, ghx,
+                                                      ghv, gXs, gVs, m, dt, rec, lr_idx);
     *launches += 1;
     return cudaGetLastError();
 }
@@ -536,8 +602,9 @@ cudaError_t gs_launch_adj_pass(cudaStream_t s, const PbdArgs& a, int stab, const
                                float4* gx, float4* gxt, float* gws, int64_t* launches, const AdjRecord& rec)
 {
     if (a.n <= 0) return cudaSuccess;
-    k_adj_h<<<gs_blocks(a.n, 128), 128, 0, s>>>(a, stab, Y, WS, nbr, cnt, gx, gxt, H);
-    k_adj_pass<<<gs_blocks(a.n, 128), 128, 0, s>>>(a, stab, Y, XT, XF, WS, nbr, cnt, H, gx, gxt, gws, rec);
+    const int64_t threads = a.n * kAdjLanes;
+    k_adj_h<<<gs_blocks(threads, 128), 128, 0, s>>>(a, stab, Y, WS, nbr, cnt, gx, gxt, H);
+    k_adj_pass<<<gs_blocks(threads, 128), 128, 0, s>>>(a, stab, Y, XT, XF, WS, nbr, cnt, H, gx, gxt, gws, rec);
     *launches += 2;
     return cudaGetLastError();
 }

@@ -106,6 +106,12 @@ def _L():
         L.or_upsample_plain.restype = ctypes.c_int
         L.or_pbd_step_plain.argtypes = [P, P, P, ctypes.c_long, P, ctypes.c_int, P]
         L.or_pbd_step_plain.restype = ctypes.c_int
+        L.or_winding_number.argtypes = [P, P, ctypes.c_long, P]
+        L.or_winding_number.restype = ctypes.c_double
+        L.or_sample_grid.argtypes = [P, ctypes.c_long, ctypes.c_double, P, P, P]
+        L.or_sample_volume.argtypes = [P, ctypes.c_long, P, ctypes.c_long, P, ctypes.c_long, ctypes.c_double, P,
+                                       ctypes.c_long, P]
+        L.or_sample_volume.restype = ctypes.c_long
         L.or_pairs_within_grid.argtypes = L.or_pairs_within.argtypes
         L.or_pairs_within_grid.restype = ctypes.c_long
         _lib = L
@@ -540,3 +546,46 @@ def pairs_within(a, b, R, use_grid=False):
     oj = np.zeros(max(n, 1), np.int64)
     fn(_ptr(a), len(a), _ptr(b), len(b), float(R), _ptr(oi), _ptr(oj), n)
     return oi[:n], oj[:n]
+
+
+# ------------------------------------------------- initial sampling (Sec. 4) ---
+def _mesh(V, T):
+    V = _f64(V, 3)
+    T = np.ascontiguousarray(np.asarray(T, dtype=np.int32).reshape(-1, 3))
+    if len(T) and (T.min() < 0 or T.max() >= len(V)):
+        raise ValueError("triangle index outside the vertex array")
+    return V, T
+
+
+def winding_number(V, T, points):
+    """Generalized winding number of the triangle mesh (V, T) at each point
+    (1 inside a closed counter-clockwise mesh, 0 outside)."""
+    V, T = _mesh(V, T)
+    pts = _f64(points, 3)
+    return np.array([_L().or_winding_number(_ptr(V), _ptr(T), len(T), _ptr(pts[i])) for i in range(len(pts))])
+
+
+def sample_grid(V, r):
+    """(lo, h, dims) of the sampling grid: cells of side 2 r / sqrt(3) over
+    the bounding box of the vertices."""
+    V = _f64(V, 3)
+    lo = np.zeros(3)
+    h = np.zeros(1)
+    dims = np.zeros(3, np.int64)
+    _L().or_sample_grid(_ptr(V), len(V), float(r), _ptr(lo), _ptr(h), _ptr(dims))
+    return lo, float(h[0]), dims
+
+
+def sample_volume(V, T, candidates, r):
+    """The volume sampler of Sec. 4 (see or_sample_volume): indices of the
+    chosen candidates in ascending cell order, and every candidate's inside
+    flag."""
+    V, T = _mesh(V, T)
+    cand = _f64(candidates, 3)
+    sel = np.zeros(max(1, len(cand)), np.int64)
+    inside = np.zeros(max(1, len(cand)), np.uint8)
+    n = _L().or_sample_volume(_ptr(V), len(V), _ptr(T), len(T), _ptr(cand), len(cand), float(r), _ptr(sel), len(sel),
+                              _ptr(inside))
+    if n < 0:
+        raise RuntimeError(f"or_sample_volume failed ({n})")
+    return sel[:n].copy(), inside[:len(cand)].astype(bool)

@@ -2,7 +2,8 @@
  * gs_oracle.c -- plain, slow FP64 CPU oracle for the two-level granular
  * method of "Interactive High-Resolution Simulation of Granular Material"
  * (arXiv 2308.01629): the low-resolution (LR) position-based-dynamics step of
- * Sec. 3 / Algorithm 1 and the high-resolution (HR) upsampling of Sec. 4.
+ * Sec. 3 / Algorithm 1, the high-resolution (HR) upsampling of Sec. 4 and the
+ * initial volume sampling of a closed triangle mesh (Sec. 4).
  *
  * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
  * baseline leg of the benchmark may load this library.  It shares no code,
@@ -2209,4 +2210,161 @@ int or_pbd_step_plain(double* x, double* v, const double* inv_m, long N, const d
     free(ws);
     free(xt);
     return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Initial sampling of a closed triangle mesh's volume (Sec. 4).        */
+/*                                                                      */
+/* The bounding box of the mesh is divided into cells of side           */
+/* 2 r / sqrt(3); candidate positions (uniform random, given as input)  */
+/* that lie inside the mesh are assigned to their cells; then, cell by  */
+/* cell, the first candidate of the cell (in input order) that keeps a  */
+/* distance of at least 2 r from every sample taken so far becomes the  */
+/* cell's sample.  Readings:                                            */
+/*  - inside = generalized winding number > 1/2 (a union of overlapping */
+/*    closed meshes counts where any of them covers the point);        */
+/*  - the cell order, which the paper leaves open: 27 phases            */
+/*    (cx mod 3, cy mod 3, cz mod 3) with the phase index               */
+/*    (cx mod 3) + 3 (cy mod 3) + 9 (cz mod 3) ascending, cells of a    */
+/*    phase by linear index.  Two cells of one phase are at least three */
+/*    cells apart along some axis, more than 2 r, so the cells of a     */
+/*    phase never compete and the result does not depend on their      */
+/*    order (which lets a parallel implementation take a phase at once);*/
+/*  - two points of one cell are closer than 2 r (the cell's diagonal  */
+/*    is 2 r), so a cell holds one sample at most, and a candidate can  */
+/*    only conflict with samples of the 5 x 5 x 5 cells around it.      */
+/* ------------------------------------------------------------------ */
+
+/* Solid angle of triangle (a, b, c) seen from p over 4 pi (Van Oosterom and
+ * Strackee, 1983: tan(Omega / 2) = det[a b c] / (|a||b||c| + (a.b)|c| +
+ * (b.c)|a| + (c.a)|b|) with a, b, c relative to p). */
+static double tri_winding(const double* A, const double* B, const double* C, const double* p)
+{
+    double a[3], b[3], c[3];
+    for (int k = 0; k < 3; ++k) {
+        a[k] = A[k] - p[k];
+        b[k] = B[k] - p[k];
+        c[k] = C[k] - p[k];
+    }
+    const double la = sqrt(dot3(a, a)), lb = sqrt(dot3(b, b)), lc = sqrt(dot3(c, c));
+    const double det = a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) +
+                       a[2] * (b[0] * c[1] - b[1] * c[0]);
+    const double den = la * lb * lc + dot3(a, b) * lc + dot3(b, c) * la + dot3(c, a) * lb;
+    return atan2(det, den) / (2.0 * 3.14159265358979323846);   /* 2 atan2 / (4 pi) */
+}
+
+/* Generalized winding number of the mesh (V: double[nv][3], T: int[nt][3],
+ * counter-clockwise seen from outside) at p: 1 inside a closed mesh, 0
+ * outside. */
+double or_winding_number(const double* V, const int32_t* T, long nt, const double* p)
+{
+    double w = 0.0;
+    for (long t = 0; t < nt; ++t) w += tri_winding(V + 3 * T[3 * t], V + 3 * T[3 * t + 1], V + 3 * T[3 * t + 2], p);
+    return w;
+}
+
+/* The sampling grid over the bounding box of the nv vertices: origin lo[3],
+ * cell side h = 2 r / sqrt(3), dims[3] = floor(extent / h) + 1. */
+void or_sample_grid(const double* V, long nv, double r, double* lo, double* h, long* dims)
+{
+    double hi[3];
+    for (int k = 0; k < 3; ++k) lo[k] = hi[k] = nv ? V[k] : 0.0;
+    for (long i = 0; i < nv; ++i)
+        for (int k = 0; k < 3; ++k) {
+            if (V[3 * i + k] < lo[k]) lo[k] = V[3 * i + k];
+            if (V[3 * i + k] > hi[k]) hi[k] = V[3 * i + k];
+        }
+    *h = 2.0 * r / sqrt(3.0);
+    for (int k = 0; k < 3; ++k) dims[k] = (long)floor((hi[k] - lo[k]) / *h) + 1;
+}
+
+/* The cell of p in the sampling grid (clamped to the grid). */
+static long sample_cell(const double* p, const double* lo, double h, const long* dims, long* c)
+{
+    for (int k = 0; k < 3; ++k) {
+        double f = floor((p[k] - lo[k]) / h);
+        c[k] = f < 0 ? 0 : (f >= (double)(dims[k] - 1) ? dims[k] - 1 : (long)f);
+    }
+    return c[0] + dims[0] * (c[1] + dims[1] * c[2]);
+}
+
+/* The sampler.  cand: double[nc][3] candidate positions (uniform random in
+ * the bounding box, drawn by the caller); r: particle radius.  selected
+ * receives the indices of the chosen candidates in ascending cell order (at
+ * most cap); returns their number, or -1 (allocation), -2 (cap too small),
+ * -3 (grid of more than 2^31 cells).  inside (optional, nc) receives the
+ * inside flag of every candidate. */
+long or_sample_volume(const double* V, long nv, const int32_t* T, long nt, const double* cand, long nc, double r,
+                      long* selected, long cap, unsigned char* inside)
+{
+    double lo[3], h;
+    long dims[3];
+    or_sample_grid(V, nv, r, lo, &h, dims);
+    const double ncell_d = (double)dims[0] * (double)dims[1] * (double)dims[2];
+    if (ncell_d > 2147483647.0) return -3;
+    const long ncell = dims[0] * dims[1] * dims[2];
+    unsigned char* in = (unsigned char*)malloc((size_t)(nc ? nc : 1));
+    long* first = (long*)calloc((size_t)ncell + 1, sizeof(long));   /* inside candidates of cell c: order[first[c] ..) */
+    long* order = (long*)malloc((size_t)(nc ? nc : 1) * sizeof(long));
+    long* pick = (long*)malloc((size_t)ncell * sizeof(long));        /* the cell's sample (candidate index) or -1 */
+    long* cellof = (long*)malloc((size_t)(nc ? nc : 1) * sizeof(long));
+    if (!in || !first || !order || !pick || !cellof) {
+        free(in); free(first); free(order); free(pick); free(cellof);
+        return -1;
+    }
+    const int nth = g_threads;
+#pragma omp parallel for num_threads(nth) if (nth > 1) schedule(dynamic, 64)
+    for (long i = 0; i < nc; ++i) in[i] = or_winding_number(V, T, nt, cand + 3 * i) > 0.5;
+    /* inside candidates by cell, in input order */
+    for (long i = 0; i < nc; ++i) {
+        long c3[3];
+        cellof[i] = sample_cell(cand + 3 * i, lo, h, dims, c3);
+        if (in[i]) first[cellof[i] + 1]++;
+    }
+    for (long c = 0; c < ncell; ++c) first[c + 1] += first[c];
+    {
+        long* fill = (long*)malloc((size_t)ncell * sizeof(long));
+        if (!fill) { free(in); free(first); free(order); free(pick); free(cellof); return -1; }
+        memcpy(fill, first, (size_t)ncell * sizeof(long));
+        for (long i = 0; i < nc; ++i)
+            if (in[i]) order[fill[cellof[i]]++] = i;
+        free(fill);
+    }
+    for (long c = 0; c < ncell; ++c) pick[c] = -1;
+    const double d2min = 4.0 * r * r;
+    for (int phase = 0; phase < 27; ++phase) {
+        const long px = phase % 3, py = (phase / 3) % 3, pz = phase / 9;
+        for (long cz = pz; cz < dims[2]; cz += 3)
+            for (long cy = py; cy < dims[1]; cy += 3)
+                for (long cx = px; cx < dims[0]; cx += 3) {
+                    const long c = cx + dims[0] * (cy + dims[1] * cz);
+                    for (long q = first[c]; q < first[c + 1] && pick[c] < 0; ++q) {
+                        const double* p = cand + 3 * order[q];
+                        int free_ = 1;
+                        for (long z = cz - 2; z <= cz + 2 && free_; ++z)
+                            for (long y = cy - 2; y <= cy + 2 && free_; ++y)
+                                for (long x = cx - 2; x <= cx + 2 && free_; ++x) {
+                                    if (x < 0 || y < 0 || z < 0 || x >= dims[0] || y >= dims[1] || z >= dims[2]) continue;
+                                    const long s = pick[x + dims[0] * (y + dims[1] * z)];
+                                    if (s < 0) continue;
+                                    const double* o = cand + 3 * s;
+                                    double d[3] = {p[0] - o[0], p[1] - o[1], p[2] - o[2]};
+                                    if (dot3(d, d) < d2min) free_ = 0;
+                                }
+                        if (free_) pick[c] = order[q];
+                    }
+                }
+    }
+    long n = 0;
+    int full = 0;
+    for (long c = 0; c < ncell; ++c) {
+        if (pick[c] < 0) continue;
+        if (n < cap) selected[n] = pick[c];
+        else full = 1;
+        ++n;
+    }
+    if (inside)
+        for (long i = 0; i < nc; ++i) inside[i] = in[i];
+    free(in); free(first); free(order); free(pick); free(cellof);
+    return full ? -2 : n;
 }

@@ -468,3 +468,102 @@ def digging_with_boulder(seed=SEED_BASE + 9, radius=0.08, density=5000.0, veloci
     sc.pop("n_solid", None)
     sc["n_body"] = len(xyz)
     return sc
+
+
+# --------------------------------------------------- procedural meshes ---
+# Closed triangle meshes, counter-clockwise seen from outside (outward
+# normals), as vertex array float64 [n][3] and triangle array int32 [m][3].
+# They are input geometry for the volume sampler of Sec. 4 (whose particles
+# the paper seeds from artists' meshes, not available here).
+
+def box_mesh(lo, hi):
+    lo, hi = np.asarray(lo, float), np.asarray(hi, float)
+    V = np.array([[x, y, z] for z in (lo[2], hi[2]) for y in (lo[1], hi[1]) for x in (lo[0], hi[0])])
+    # vertex k = x + 2 y + 4 z (bits); faces as quads (a, b, c, d) counter-clockwise from outside
+    quads = [(0, 2, 3, 1), (4, 5, 7, 6), (0, 1, 5, 4), (2, 6, 7, 3), (0, 4, 6, 2), (1, 3, 7, 5)]
+    T = [(a, b, c) for a, b, c, d in quads] + [(a, c, d) for a, b, c, d in quads]
+    return V, np.array(T, np.int32)
+
+
+def prism_mesh(cx, cy, radius, z0, z1, n=24, apex=None):
+    """A closed n-gon prism (a cylinder's stand-in) from z0 to z1; with apex
+    (a height above z1) a cone on top instead of the flat cap."""
+    ang = 2 * np.pi * np.arange(n) / n
+    ring = np.stack([cx + radius * np.cos(ang), cy + radius * np.sin(ang)], 1)
+    V = [[x, y, z0] for x, y in ring] + [[x, y, z1] for x, y in ring] + [[cx, cy, z0]]
+    bot = 2 * n
+    T = []
+    for k in range(n):
+        k1 = (k + 1) % n
+        T += [(k, k1, n + k1), (k, n + k1, n + k)]     # side
+        T += [(bot, k1, k)]                             # bottom (normal down)
+    if apex is None:
+        V.append([cx, cy, z1])
+        top = 2 * n + 1
+        T += [(top, n + k, n + (k + 1) % n) for k in range(n)]
+    else:
+        V.append([cx, cy, z1 + apex])
+        top = 2 * n + 1
+        T += [(top, n + k, n + (k + 1) % n) for k in range(n)]
+    return np.array(V, float), np.array(T, np.int32)
+
+
+def icosphere(center, radius, subdiv=2):
+    """A subdivided icosahedron with its vertices on the sphere."""
+    t = (1 + 5 ** 0.5) / 2
+    V = [[-1, t, 0], [1, t, 0], [-1, -t, 0], [1, -t, 0], [0, -1, t], [0, 1, t], [0, -1, -t], [0, 1, -t],
+         [t, 0, -1], [t, 0, 1], [-t, 0, -1], [-t, 0, 1]]
+    V = [list(np.array(v) / np.linalg.norm(v)) for v in V]
+    T = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2), (10, 7, 6),
+         (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10),
+         (8, 6, 7), (9, 8, 1)]
+    for _ in range(subdiv):
+        mid = {}
+
+        def m(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in mid:
+                p = np.array(V[a]) + np.array(V[b])
+                V.append(list(p / np.linalg.norm(p)))
+                mid[key] = len(V) - 1
+            return mid[key]
+        T = [t2 for a, b, c in T for t2 in ((a, m(a, b), m(c, a)), (b, m(b, c), m(a, b)), (c, m(c, a), m(b, c)),
+                                             (m(a, b), m(b, c), m(c, a)))]
+    return np.asarray(center, float) + radius * np.array(V), np.array(T, np.int32)
+
+
+def merge_meshes(parts):
+    """Several closed meshes as one triangle soup (overlaps allowed: their
+    union is where the winding number exceeds 1/2)."""
+    Vs, Ts, off = [], [], 0
+    for V, T in parts:
+        Vs.append(V)
+        Ts.append(T + off)
+        off += len(V)
+    return np.concatenate(Vs), np.concatenate(Ts).astype(np.int32)
+
+
+def castle_mesh(base=(0.5, 0.5, 0.0), size=0.6, height=0.2):
+    """A sand castle: a square base, a central keep, four round corner towers
+    with cone roofs (overlapping closed parts)."""
+    cx, cy, z0 = base
+    h2 = size / 2
+    parts = [box_mesh((cx - h2, cy - h2, z0), (cx + h2, cy + h2, z0 + height)),
+             box_mesh((cx - 0.2 * size, cy - 0.2 * size, z0 + 0.5 * height),
+                      (cx + 0.2 * size, cy + 0.2 * size, z0 + 2.0 * height))]
+    for sx in (-1, 1):
+        for sy in (-1, 1):
+            parts.append(prism_mesh(cx + sx * 0.8 * h2, cy + sy * 0.8 * h2, 0.12 * size, z0, z0 + 1.6 * height,
+                                    n=20, apex=0.6 * height))
+    return merge_meshes(parts)
+
+
+def volume_candidates(V, r, per_cell=6.0, seed=SEED_BASE + 10):
+    """Uniform random candidate positions in the bounding box of the mesh
+    vertices for the volume sampler: about per_cell candidates per cell of
+    side 2 r / sqrt(3)."""
+    lo, hi = V.min(0), V.max(0)
+    h = 2 * r / math.sqrt(3)
+    n = int(math.ceil(per_cell * float(np.prod(hi - lo)) / h ** 3))
+    rng = np.random.default_rng(seed)
+    return lo + (hi - lo) * rng.random((n, 3))

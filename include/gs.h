@@ -93,6 +93,8 @@ typedef struct {
     int32_t n_sdf;               /* 0 .. GS_MAX_SDF */
     const gs_sdf* sdf;           /* copied at gs_create */
     gs_params params;
+    int64_t n_high;              /* number of HR particles; 0 selects n_low * ratio (e.g. a volume
+                                    sampling of a mesh gives its own count, Sec. 4) */
 } gs_scene;
 
 /* Readable / writable state.  LR and HR fields hold all scenes of the
@@ -171,7 +173,8 @@ typedef struct {
 void gs_default_params(gs_params* p);
 
 /* Create a context: allocate LR state for scene->n_low particles and HR
- * state for n_low * ratio particles, the neighbour grid over the scene box,
+ * state for scene->n_high particles (n_low * ratio when n_high is 0; total
+ * below 2^31), the neighbour grid over the scene box,
  * and all scratch buffers.  r_low: LR radius (Sec. 3, constant for all LR
  * particles); r_high: HR radius (<= 0 selects r_low * ratio^(-1/3)); ratio:
  * HR per LR (>= 1).  cuda_stream: a cudaStream_t the context enqueues on, or
@@ -328,6 +331,35 @@ int gs_set_hr_slab(gs_ctx* ctx, int part, int n_parts);
  * the state is applied, so the sources may change on return.  A context
  * without a slab may call it too (a state written back unchanged). */
 int gs_hr_slab_assemble(gs_ctx* ctx, const void* pos, const void* vel, size_t bytes, int src_is_device);
+
+/* Initial sampling of a closed triangle mesh's volume (Sec. 4), for seeding
+ * LR and HR particles.  The bounding box of the vertices is divided into
+ * cells of side h = 2 r / sqrt(3) (origin: the box's low corner; dims =
+ * floor(extent / h) + 1 per axis); the candidates (uniform random positions
+ * in the box, drawn by the caller) that lie inside the mesh -- generalized
+ * winding number above 1/2, so overlapping closed parts count as their
+ * union -- are assigned to their cells in input order; then, cell by cell,
+ * the first candidate that is at least 2 r away from every sample taken so
+ * far becomes the cell's sample.  Cells are taken in 27 phases: phase
+ * (cx mod 3) + 3 (cy mod 3) + 9 (cz mod 3) ascending (cells of one phase
+ * never compete, so their order within the phase does not matter).  All
+ * decisions in double precision.
+ *   vertices   double[n_vertices][3];  triangles int32[n_triangles][3],
+ *              counter-clockwise seen from outside, indices < n_vertices;
+ *   candidates double[n_candidates][3], n_candidates < 2^31;
+ *   r          the particle radius (samples are >= 2 r apart);
+ *   selected   receives the indices of the chosen candidates in ascending
+ *              cell order (at most capacity); *n_selected their number;
+ *   inside     (optional) uint8[n_candidates]: 1 for candidates inside.
+ * Host arrays; synchronous; uses the current device with device memory of
+ * its own, freed on return.  GS_ERR_ARG (null pointers, r <= 0, a triangle
+ * index out of range, more than 2^31 - 2 cells), GS_ERR_DOMAIN (a
+ * non-finite coordinate), both before any device work; GS_ERR_CAPACITY when
+ * more than capacity samples were chosen (*n_selected is their number);
+ * GS_ERR_OOM, GS_ERR_CUDA. */
+int gs_sample_volume(const double* vertices, int64_t n_vertices, const int32_t* triangles, int64_t n_triangles,
+                     const double* candidates, int64_t n_candidates, double r, int64_t* selected, int64_t capacity,
+                     int64_t* n_selected, uint8_t* inside);
 
 /* The LR steps of the latest adaptive frame: *n_out receives their number
  * and dts[0 .. min(n, cap)) their lengths.  Blocks. */

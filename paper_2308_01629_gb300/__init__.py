@@ -50,7 +50,8 @@ class gs_params(ctypes.Structure):
 
 class gs_scene(ctypes.Structure):
     _fields_ = [("box_lo", ctypes.c_float * 3), ("box_hi", ctypes.c_float * 3), ("n_low", ctypes.c_int32),
-                ("n_sdf", ctypes.c_int32), ("sdf", ctypes.POINTER(gs_sdf)), ("params", gs_params)]
+                ("n_sdf", ctypes.c_int32), ("sdf", ctypes.POINTER(gs_sdf)), ("params", gs_params),
+                ("n_high", ctypes.c_int64)]
 
 
 class gs_grid_info(ctypes.Structure):
@@ -114,6 +115,8 @@ _SIGS = {
     "gs_hr_slab_range": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_int64)]),
     "gs_set_hr_slab": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    "gs_sample_volume": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_double,
+                                        _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _P]),
     "gs_hr_slab_assemble": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, ctypes.c_int]),
 }
 
@@ -338,6 +341,31 @@ def gs_hr_slab_range(n_slots, part, n_parts):
     return rc, b.value, e.value
 
 
+def gs_sample_volume(vertices, triangles, candidates, r, capacity=None):
+    """(status, selected, inside): the volume sampler of Sec. 4 on a closed
+    triangle mesh (see include/gs.h).  Arrays are marshalled as float64 /
+    int32; selected holds candidate indices in ascending cell order."""
+    V = np.ascontiguousarray(np.asarray(vertices, np.float64).reshape(-1, 3))
+    T = np.ascontiguousarray(np.asarray(triangles, np.int32).reshape(-1, 3))
+    C = np.ascontiguousarray(np.asarray(candidates, np.float64).reshape(-1, 3))
+    cap = len(C) if capacity is None else int(capacity)
+    sel = np.zeros(max(cap, 1), np.int64)
+    inside = np.zeros(max(len(C), 1), np.uint8)
+    n = ctypes.c_int64()
+    rc = lib().gs_sample_volume(V.ctypes.data, len(V), T.ctypes.data, len(T), C.ctypes.data, len(C), float(r),
+                                sel.ctypes.data, cap, ctypes.byref(n), inside.ctypes.data)
+    return rc, sel[:min(n.value, cap)].copy(), inside[:len(C)].astype(bool)
+
+
+def sample_volume(vertices, triangles, candidates, r):
+    """Indices of the chosen candidates (ascending cell order); raises on
+    error."""
+    rc, sel, _ = gs_sample_volume(vertices, triangles, candidates, r)
+    if rc != GS_OK:
+        raise GsError(rc, "gs_sample_volume failed")
+    return sel
+
+
 def gs_set_hr_slab(ctx, part, n_parts):
     return lib().gs_set_hr_slab(ctx, int(part), int(n_parts))
 
@@ -388,6 +416,7 @@ def make_scene(sc, **overrides):
         scene.box_lo[k] = float(sc["box_lo"][k])
         scene.box_hi[k] = float(sc["box_hi"][k])
     scene.n_low = int(len(sc["lr_pos"]))
+    scene.n_high = int(len(sc["hr_pos"])) if "hr_pos" in sc else 0
     scene.n_sdf = len(sc["sdfs"])
     scene.sdf = ctypes.cast(arr, ctypes.POINTER(gs_sdf))
     scene.params = prm

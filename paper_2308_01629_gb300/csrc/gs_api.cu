@@ -59,6 +59,15 @@ cudaError_t dalloc(T** p, size_t count)
     return cudaMalloc((void**)p, count * sizeof(T));
 }
 
+}  // namespace
+
+cudaError_t gs_dalloc_bytes(void** p, size_t bytes)
+{
+    return dalloc((unsigned char**)p, bytes);
+}
+
+namespace {
+
 struct Timed {
     gs_ctx* c;
     int id;
@@ -287,7 +296,8 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
         const float rl = r_low[s];
         const float rh_in = r_high ? r_high[s] : 0.0f;
         const int ra = ratio[s];
-        bool bad = !(rl > 0.0f) || !std::isfinite(rl) || ra < 1 || in.n_low < 0 || in.n_sdf < 0 ||
+        bool bad = !(rl > 0.0f) || !std::isfinite(rl) || ra < 1 || in.n_low < 0 || in.n_high < 0 ||
+                   in.n_high > 0x7fffffffLL || in.n_sdf < 0 ||
                    in.n_sdf > GS_MAX_SDF || (in.n_sdf > 0 && !in.sdf);
         for (int k = 0; k < 3 && !bad; ++k)
             bad = !(in.box_hi[k] > in.box_lo[k]) || !std::isfinite(in.box_lo[k]) || !std::isfinite(in.box_hi[k]);
@@ -336,7 +346,7 @@ int create_impl(int S, const gs_scene* scenes, const float* r_low, const float* 
             delete c;
             return GS_ERR_ARG;
         }
-        const int64_t m = (int64_t)in.n_low * ra;
+        const int64_t m = in.n_high > 0 ? in.n_high : (int64_t)in.n_low * ra;
         d.lr_begin = lr;
         d.lr_end = lr + in.n_low;
         d.hr_begin = hr_slot;

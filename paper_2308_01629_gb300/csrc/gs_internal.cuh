@@ -464,6 +464,10 @@ cudaError_t gs_launch_adj_final(cudaStream_t s, const PbdArgs& a, const uint32_t
                                 const float4* gx, const float4* gxt, const float* gws, float4* gx0, float4* gv0,
                                 int64_t* launches);
 
+// Device allocation through the library's allocation-failure hook
+// (gs_set_alloc_failure), for code outside a context.
+cudaError_t gs_dalloc_bytes(void** p, size_t bytes);
+
 // Grid-stride helper: blocks for n threads of `threads` each, capped.
 inline unsigned gs_blocks(int64_t n, int threads)
 {

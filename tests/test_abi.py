@@ -88,3 +88,23 @@ def test_hr_slab_ranges_tile_the_slots_by_whole_items():
             assert max(sizes) - min(sizes) <= 32
     for args in ((33, 0, 2), (-32, 0, 1), (64, 2, 2), (64, -1, 2), (64, 0, 0), (64, 0, 4097)):
         assert gs.gs_hr_slab_range(*args)[0] == gs.GS_ERR_ARG
+
+
+def test_volume_sampler_refuses_bad_arguments_before_any_device_work():
+    """gs_sample_volume checks its arguments on the host: these calls return
+    before touching a GPU (none is present here)."""
+    import numpy as np
+
+    import paper_2308_01629_gb300 as gs
+    V = np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]])
+    T = np.array([[0, 2, 1], [0, 1, 3], [0, 3, 2], [1, 2, 3]])
+    C = np.array([[0.1, 0.1, 0.1]])
+    assert gs.gs_sample_volume(V, T, C, 0.0)[0] == gs.GS_ERR_ARG              # r <= 0
+    assert gs.gs_sample_volume(V, T, C, float("nan"))[0] == gs.GS_ERR_ARG
+    assert gs.gs_sample_volume(V, T + 1, C, 0.1)[0] == gs.GS_ERR_ARG           # index 4 of 4 vertices
+    assert gs.gs_sample_volume(V, -T, C, 0.1)[0] == gs.GS_ERR_ARG
+    assert gs.gs_sample_volume(V, T, [[0.1, float("inf"), 0]], 0.1)[0] == gs.GS_ERR_DOMAIN
+    V2 = V.copy()
+    V2[1, 0] = float("nan")
+    assert gs.gs_sample_volume(V2, T, C, 0.1)[0] == gs.GS_ERR_DOMAIN
+    assert gs.gs_sample_volume(V * 1e6, T, C, 1e-6)[0] == gs.GS_ERR_ARG       # too many cells

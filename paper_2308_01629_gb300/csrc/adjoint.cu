@@ -332,7 +332,7 @@ __global__ void k_adj_init(int64_t n, const uint32_t* __restrict__ idx, const fl
 // takes candidates l, l + kAdjLanes, ... and SDF components likewise, and
 // the lanes' sums are added up by shuffles (a small LR set, such as the 4k
 // particles of a differentiable rollout, then still fills the GPU).
-constexpr int kAdjLanes = 8;
+constexpr int kAdjLanes = 16;
 
 __device__ __forceinline__ float lanes_sum(float v)
 {

@@ -332,10 +332,10 @@ def run_diff(args, dev, stream, gs, torch, reps=None, warm=2, with_plain=True):
             for _ in range(F):
                 plain.frame(dt, 1, iters)
 
-        def diff_rollout():
+        def diff_rollout(native=True):
             X, V, x, v = state
             V = V.clone().requires_grad_(True)
-            out = rollout(ctx, X, V, x, v, dt, frames=F, n_sub=1, iters=iters, checkpoint_every=every)
+            out = rollout(ctx, X, V, x, v, dt, frames=F, n_sub=1, iters=iters, checkpoint_every=every, native=native)
             loss = ((out[2][:, :3] - target) ** 2).sum()
             loss.backward()
             return V.grad
@@ -356,6 +356,7 @@ def run_diff(args, dev, stream, gs, torch, reps=None, warm=2, with_plain=True):
         l0 = ctx.launches()
         ms_diff = timed(diff_rollout)
         nl = (ctx.launches() - l0) / (k + warm)
+        ms_torch = timed(lambda: diff_rollout(native=False)) if with_plain else None
         plain.close()
         ctx.close()
     return {"workload": f"falling column {len(sc['lr_pos'])} LR / {M} HR, {F} steps of {dt:.6f} s, "
@@ -363,7 +364,9 @@ def run_diff(args, dev, stream, gs, torch, reps=None, warm=2, with_plain=True):
             "plain_forward_ms_per_rollout": ms_plain, "forward_backward_ms_per_rollout": ms_diff,
             "forward_backward_hr_steps_per_s": M * F / (ms_diff / 1e3),
             "backward_overhead_vs_plain_forward": ms_diff / ms_plain if ms_plain else None,
-            "library_kernels_per_rollout": nl}
+            "library_kernels_per_rollout": nl,
+            "rollout": "run by the library (gs_rollout_forward / _backward, one CUDA graph each)",
+            "torch_driven_forward_backward_ms_per_rollout": ms_torch}
 
 
 def run_diff_only(args):

@@ -520,6 +520,51 @@ int gs_step_low_backward(gs_ctx* ctx, const float* x_in, const float* v_in, cons
 int gs_set_decision_record(gs_ctx* ctx, uint32_t* hr_record, int32_t* lr_candidates, uint8_t* lr_pair_bits,
                            uint8_t* lr_sdf_bits, int max_passes);
 
+/* Taped LR steps for checkpointed rollouts.  A differentiable rollout runs
+ * each LR step forward (again, when its segment is recomputed from a
+ * checkpoint) and then backward; gs_step_low_backward records the step once
+ * more to know what every pass evaluated on.  With n_slots > 0,
+ * gs_step_low_forward_taped keeps that record (per-pass snapshots, candidate
+ * lists, cell order) of the latest n_slots steps in slots of the context
+ * (about 2 (n_stab + iters + 1) x 16 + (max_neighbors + 2) x 4 bytes per LR
+ * particle each) under the caller's tag (>= 0; a recomputation of the same
+ * step gives the same tag), and gs_step_low_backward_taped runs only the
+ * reverse passes from the latest kept record with that tag.  Outputs and
+ * gradients equal those of gs_step_low_forward / gs_step_low_backward bit
+ * for bit.  gs_set_step_tapes(ctx, 0) frees the slots (the default); a new
+ * count drops the kept records.  Without slots gs_step_low_forward_taped is
+ * gs_step_low_forward.  gs_step_low_backward_taped returns GS_ERR_STATE when
+ * no kept record has the tag (never taken or overwritten by later steps):
+ * the caller then uses gs_step_low_backward.  Device buffers as for the
+ * functional forms; grains of the scenes' coefficients only (GS_ERR_STATE
+ * with materials or bodies). */
+int gs_set_step_tapes(gs_ctx* ctx, int n_slots);
+int gs_step_low_forward_taped(gs_ctx* ctx, const float* x_in, const float* v_in, float* x_out, float* v_out, float dt,
+                              int iters, int64_t tag);
+int gs_step_low_backward_taped(gs_ctx* ctx, int64_t tag, const float* g_x_out, const float* g_v_out, float* g_x_in,
+                               float* g_v_in);
+
+/* A differentiable rollout run by the library: `frames` frames of n_sub LR
+ * steps of dt / n_sub (Algorithm 1) and one HR frame of dt (Sec. 4) from
+ * the initial state (lr_x0, lr_v0, hr_x0, hr_v0; original order, float4
+ * records as the functional forms) into (lr_x, lr_v, hr_x, hr_v), keeping
+ * the state at every checkpoint_every-th frame inside the context
+ * (2 (n_low + n_high) x 16 bytes each).  gs_rollout_backward then maps the
+ * cotangents of the final state to those of the initial state: each segment
+ * is recomputed from its checkpoint with taped LR steps (gs_set_step_tapes
+ * grows to checkpoint_every x n_sub slots) and reversed frame by frame
+ * (gs_upsample_backward, gs_step_low_backward_taped), the LR cotangent of a
+ * frame's end summing the next step's and the HR frame's.  The same
+ * operations, in the same order, as a checkpointed rollout driven through
+ * the functional entry points.  Single-scene contexts; the context's state
+ * is used as workspace.  Device buffers; the w components carry no
+ * gradient.  GS_ERR_STATE for a backward without a forward. */
+int gs_rollout_forward(gs_ctx* ctx, const float* lr_x0, const float* lr_v0, const float* hr_x0, const float* hr_v0,
+                       float dt, int frames, int n_sub, int iters, int checkpoint_every, float* lr_x, float* lr_v,
+                       float* hr_x, float* hr_v);
+int gs_rollout_backward(gs_ctx* ctx, const float* g_lr_x, const float* g_lr_v, const float* g_hr_x, const float* g_hr_v,
+                        float* g_lr_x0, float* g_lr_v0, float* g_hr_x0, float* g_hr_v0);
+
 /* Pass-by-pass record of one LR step (Algorithm 1, Sec. 3), for checking the
  * step against a reference one Jacobi pass at a time: each pass is a
  * function of the state before it, so a pass can be compared on its own

@@ -115,6 +115,12 @@ _SIGS = {
     "gs_hr_slab_range": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_int64)]),
     "gs_set_hr_slab": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    "gs_set_step_tapes": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gs_step_low_forward_taped": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int, ctypes.c_int64]),
+    "gs_step_low_backward_taped": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, _P]),
+    "gs_rollout_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
+    "gs_rollout_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "gs_sample_volume": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_double,
                                         _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _P]),
     "gs_hr_slab_assemble": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, ctypes.c_int]),
@@ -339,6 +345,28 @@ def gs_hr_slab_range(n_slots, part, n_parts):
     b, e = ctypes.c_int64(), ctypes.c_int64()
     rc = lib().gs_hr_slab_range(int(n_slots), int(part), int(n_parts), ctypes.byref(b), ctypes.byref(e))
     return rc, b.value, e.value
+
+
+def gs_set_step_tapes(ctx, n_slots):
+    return lib().gs_set_step_tapes(ctx, int(n_slots))
+
+
+def gs_step_low_forward_taped(ctx, x_in, v_in, x_out, v_out, dt, iters, tag):
+    return lib().gs_step_low_forward_taped(ctx, x_in, v_in, x_out, v_out, float(dt), int(iters), int(tag))
+
+
+def gs_step_low_backward_taped(ctx, tag, g_x_out, g_v_out, g_x_in, g_v_in):
+    return lib().gs_step_low_backward_taped(ctx, int(tag), g_x_out, g_v_out, g_x_in, g_v_in)
+
+
+def gs_rollout_forward(ctx, lr_x0, lr_v0, hr_x0, hr_v0, dt, frames, n_sub, iters, checkpoint_every, lr_x, lr_v,
+                       hr_x, hr_v):
+    return lib().gs_rollout_forward(ctx, lr_x0, lr_v0, hr_x0, hr_v0, float(dt), int(frames), int(n_sub), int(iters),
+                                    int(checkpoint_every), lr_x, lr_v, hr_x, hr_v)
+
+
+def gs_rollout_backward(ctx, g_lr_x, g_lr_v, g_hr_x, g_hr_v, g_lr_x0, g_lr_v0, g_hr_x0, g_hr_v0):
+    return lib().gs_rollout_backward(ctx, g_lr_x, g_lr_v, g_hr_x, g_hr_v, g_lr_x0, g_lr_v0, g_hr_x0, g_hr_v0)
 
 
 def gs_sample_volume(vertices, triangles, candidates, r, capacity=None):
@@ -574,6 +602,12 @@ class Context:
 
     def set_pipeline(self, enable=True, warps_per_block=8, blocks_per_sm=1):
         return _check(self.ctx, gs_set_pipeline(self.ctx, enable, warps_per_block, blocks_per_sm), "gs_set_pipeline")
+
+    def set_step_tapes(self, n_slots):
+        """Keep the recorded passes of the latest n_slots taped LR steps for
+        their backward (0: none)."""
+        _check(self.ctx, gs_set_step_tapes(self.ctx, n_slots), "gs_set_step_tapes")
+        self.step_tapes = int(n_slots)
 
     def set_hr_slab(self, part, n_parts):
         """Restrict this context's HR frames to slab `part` of `n_parts` of

@@ -61,6 +61,12 @@ cudaError_t dalloc(T** p, size_t count)
 
 }  // namespace
 
+int gs_ctx_fail(gs_ctx* c, int code, const char* msg)
+{
+    return fail(c, code, "%s", msg);
+}
+
+
 cudaError_t gs_dalloc_bytes(void** p, size_t bytes)
 {
     return dalloc((unsigned char**)p, bytes);
@@ -742,7 +748,7 @@ void drop_graphs(gs_ctx* c)
 // stream) that sequence is captured once per key and replayed.
 bool capturable(const gs_ctx* c)
 {
-    return c->use_graphs && !c->timing && c->stream != nullptr && c->stream != cudaStreamLegacy &&
+    return c->use_graphs && !c->timing && !c->capturing && c->stream != nullptr && c->stream != cudaStreamLegacy &&
            c->stream != cudaStreamPerThread;
 }
 
@@ -783,7 +789,9 @@ int replay_or_run(gs_ctx* c, uint64_t key, F&& body)
         const int64_t l0 = c->launches;
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        c->capturing = true;   // sequences called by the body are captured into this graph
         const int st = body();
+        c->capturing = false;
         const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
         if (st != GS_OK) {
             if (graph) cudaGraphDestroy(graph);
@@ -966,6 +974,16 @@ int frame_pipelined_graph(gs_ctx* c, float dt, int n_sub, int iters)
 
 }  // namespace
 
+int gs_replay_or_run(gs_ctx* c, uint64_t key, int (*body)(gs_ctx*, void*), void* arg)
+{
+    return replay_or_run(c, key, [&] { return body(c, arg); });
+}
+
+uint64_t gs_sequence_key(const gs_ctx* c, char kind, float dt, int iters)
+{
+    return step_key(c, kind, dt, iters);
+}
+
 // Writes a checked device copy of a state field (original order) into the
 // context's state, on the main stream.
 int apply_field(gs_ctx* c, int field, const float4* dsrc, size_t bytes)
@@ -1106,6 +1124,8 @@ int gs_batch_create(int n_scenes, const gs_scene* scenes, const float* r_low, co
     return create_impl(n_scenes, scenes, r_low, r_high, ratio, cuda_stream, out);
 }
 
+static void free_tapes(gs_ctx* c);
+
 void gs_destroy(gs_ctx* c)
 {
     if (!c) return;
@@ -1132,6 +1152,10 @@ void gs_destroy(gs_ctx* c)
                     c->async_out[0], c->async_out[1], c->async_out[2], c->async_out[3], c->slab_stage};
     for (void* b : bufs)
         if (b) cudaFree(b);
+    free_tapes(c);
+    if (c->ro_ckpt) cudaFree(c->ro_ckpt);
+    if (c->ro_work) cudaFree(c->ro_work);
+    if (c->ro_io) cudaFree(c->ro_io);
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     if (c->stream_hr) cudaStreamDestroy(c->stream_hr);
@@ -2179,6 +2203,9 @@ static int ensure_snapshots(gs_ctx* c, int total)
 
 static int step_low_reverse(gs_ctx* c, float dt, int iters);
 static int step_low_record(gs_ctx* c, float dt, int iters);
+static int step_low_record_into(gs_ctx* c, float dt, int iters, float4* X, float4* XT, uint32_t* nbr, uint32_t* cnt);
+static int step_low_reverse_from(gs_ctx* c, float dt, int iters, const float4* X, const float4* XT,
+                                 const uint32_t* nbr, const uint32_t* cnt, const uint32_t* idx);
 
 int gs_step_low_trace(gs_ctx* c, const float* x_in, const float* v_in, float dt, int iters, float* x_trace,
                       float* xt_trace, int n_records)
@@ -2213,6 +2240,160 @@ int gs_step_low_trace(gs_ctx* c, const float* x_in, const float* v_in, float dt,
 }
 
 
+static int ensure_adjoint_buffers(gs_ctx* c)
+{
+    const int64_t N = c->n_low;
+    if (c->adj_gx) return GS_OK;
+    bool ok = dalloc(&c->adj_gx, N) == cudaSuccess && dalloc(&c->adj_gxt, N) == cudaSuccess &&
+              dalloc(&c->adj_h, N) == cudaSuccess && dalloc(&c->adj_gws, N) == cudaSuccess &&
+              dalloc(&c->adj_io, (size_t)4 * N) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return fail(c, GS_ERR_OOM, "no memory for the reverse-mode buffers");
+    }
+    return GS_OK;
+}
+
+static void free_tapes(gs_ctx* c)
+{
+    for (auto& t : c->tapes)
+        for (void* b : {(void*)t.X, (void*)t.XT, (void*)t.nbr, (void*)t.cnt, (void*)t.idx})
+            if (b) cudaFree(b);
+    c->tapes.clear();
+    c->tape_passes = 0;
+    c->tape_next = 0;
+}
+
+int gs_set_step_tapes(gs_ctx* c, int n_slots)
+{
+    int st = check_state(c);
+    if (st) return st;
+    if (n_slots < 0 || n_slots > 1024) return fail(c, GS_ERR_ARG, "bad tape count %d", n_slots);
+    st = settle(c);
+    if (st) return st;
+    CK(cudaStreamSynchronize(c->stream), "synchronize");   // no graph still reads the old tapes
+    drop_graphs(c);
+    free_tapes(c);
+    c->tapes.resize((size_t)n_slots);
+    return GS_OK;
+}
+
+// (Re)allocates every tape slot for steps of `total` passes (growing only).
+static int ensure_tapes(gs_ctx* c, int total)
+{
+    if (total <= c->tape_passes && !c->tapes.empty() && c->tapes[0].X) return GS_OK;
+    const size_t n_slots = c->tapes.size();
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    drop_graphs(c);   // captured sequences hold the old tape buffers
+    free_tapes(c);
+    c->tapes.resize(n_slots);
+    const int64_t N = c->n_low;
+    for (auto& t : c->tapes) {
+        bool ok = dalloc(&t.X, (size_t)(total + 1) * N) == cudaSuccess &&
+                  dalloc(&t.XT, (size_t)(total + 1) * N) == cudaSuccess &&
+                  dalloc(&t.nbr, (size_t)c->nbr_cap * N) == cudaSuccess && dalloc(&t.cnt, (size_t)N) == cudaSuccess &&
+                  dalloc(&t.idx, (size_t)N) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            free_tapes(c);
+            c->tapes.resize(n_slots);
+            return fail(c, GS_ERR_OOM, "no memory for the LR step tapes");
+        }
+    }
+    c->tape_passes = total;
+    return GS_OK;
+}
+
+static uint64_t tape_key(const gs_ctx* c, char kind, float dt, int iters, int slot)
+{
+    return (step_key(c, kind, dt, iters) ^ (0x9e3779b97f4a7c15ull * (uint64_t)(slot + 1))) * 0x100000001b3ull;
+}
+
+// The recorded forward into tape slot t, then the step's finalize from the
+// last snapshots (v = (x~ - x) / dt, x = x~, original order).
+static int step_low_tape_forward(gs_ctx* c, gs_ctx::StepTape& t, float dt, int iters)
+{
+    const int64_t N = c->n_low;
+    const int total = c->n_stab + iters;
+    int st = step_low_record_into(c, dt, iters, t.X, t.XT, t.nbr, t.cnt);
+    if (st) return st;
+    CK(cudaMemcpyAsync(t.idx, c->lr_sorted_idx, N * sizeof(uint32_t), cudaMemcpyDeviceToDevice, c->stream),
+       "keep the cell order");
+    const PbdArgs a = pbd_args(c, dt);
+    CK(gs_launch_finalize(c->stream, a, t.idx, t.X + (size_t)std::min(total, c->n_stab) * N, t.XT + (size_t)total * N,
+                          c->lr_pos, c->lr_vel, &c->launches, nullptr),
+       "finalize");
+    c->lr_binned = false;
+    return GS_OK;
+}
+
+int gs_step_low_forward_taped(gs_ctx* c, const float* x_in, const float* v_in, float* x_out, float* v_out, float dt,
+                              int iters, int64_t tag)
+{
+    int st = check_state(c);
+    if (st) return st;
+    if (tag < 0) return fail(c, GS_ERR_ARG, "negative tape tag");
+    if (c->tapes.empty()) return gs_step_low_forward(c, x_in, v_in, x_out, v_out, dt, iters);
+    st = settle(c);
+    if (st) return st;
+    if (!(dt > 0.0f) || !std::isfinite(dt) || iters < 0 || iters > 1000)
+        return fail(c, GS_ERR_ARG, "invalid dt %g or iters %d", (double)dt, iters);
+    if (c->n_materials > 0 || c->n_bodies > 0)
+        return fail(c, GS_ERR_STATE, "taped LR steps cover grains of the scenes' coefficients only");
+    const int64_t N = c->n_low;
+    if (N == 0) return GS_OK;
+    if (!x_in || !v_in || !x_out || !v_out) return fail(c, GS_ERR_ARG, "null buffer");
+    st = ensure_tapes(c, c->n_stab + iters);
+    if (st) return st;
+    const int slot = c->tape_next;
+    gs_ctx::StepTape& t = c->tapes[(size_t)slot];
+    t.tag = -1;   // until the step below is enqueued
+    CK(cudaMemcpyAsync(c->lr_pos, x_in, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    CK(cudaMemcpyAsync(c->lr_vel, v_in, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    st = replay_or_run(c, tape_key(c, 'F', dt, iters, slot), [&] { return step_low_tape_forward(c, t, dt, iters); });
+    if (st) return st;
+    CK(cudaMemcpyAsync(x_out, c->lr_pos, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    CK(cudaMemcpyAsync(v_out, c->lr_vel, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    t.tag = tag;
+    t.serial = c->tape_serial++;
+    t.dt = dt;
+    t.iters = iters;
+    c->tape_next = (slot + 1) % (int)c->tapes.size();
+    return GS_OK;
+}
+
+int gs_step_low_backward_taped(gs_ctx* c, int64_t tag, const float* g_x_out, const float* g_v_out, float* g_x_in,
+                               float* g_v_in)
+{
+    int st = check_state(c);
+    if (st) return st;
+    st = settle(c);
+    if (st) return st;
+    const int64_t N = c->n_low;
+    int slot = -1;
+    for (size_t k = 0; k < c->tapes.size(); ++k)
+        if (tag >= 0 && c->tapes[k].tag == tag && (slot < 0 || c->tapes[k].serial > c->tapes[(size_t)slot].serial))
+            slot = (int)k;
+    if (slot < 0) return fail(c, GS_ERR_STATE, "no kept tape has tag %lld", (long long)tag);
+    if (N == 0) return GS_OK;
+    if (!g_x_out || !g_v_out || !g_x_in || !g_v_in) return fail(c, GS_ERR_ARG, "null buffer");
+    const gs_ctx::StepTape& t = c->tapes[(size_t)slot];
+    if (c->rec_lr_pair && c->n_stab + t.iters > c->rec_max_passes)
+        return fail(c, GS_ERR_ARG, "%d passes exceed the decision record's %d", c->n_stab + t.iters,
+                    c->rec_max_passes);
+    st = ensure_adjoint_buffers(c);
+    if (st) return st;
+    CK(cudaMemcpyAsync(c->adj_io, g_x_out, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    CK(cudaMemcpyAsync(c->adj_io + N, g_v_out, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    st = replay_or_run(c, tape_key(c, 'B', t.dt, t.iters, slot), [&] {
+        return step_low_reverse_from(c, t.dt, t.iters, t.X, t.XT, t.nbr, t.cnt, t.idx);
+    });
+    if (st) return st;
+    CK(cudaMemcpyAsync(g_x_in, c->adj_io + 2 * N, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    CK(cudaMemcpyAsync(g_v_in, c->adj_io + 3 * N, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
+    return GS_OK;
+}
+
 int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const float* g_x_out, const float* g_v_out,
                          float* g_x_in, float* g_v_in, float dt, int iters)
 {
@@ -2232,15 +2413,8 @@ int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const 
         return fail(c, GS_ERR_ARG, "%d passes exceed the decision record's %d", c->n_stab + iters, c->rec_max_passes);
     st = ensure_snapshots(c, c->n_stab + iters);
     if (st) return st;
-    if (!c->adj_gx) {
-        bool ok = dalloc(&c->adj_gx, N) == cudaSuccess && dalloc(&c->adj_gxt, N) == cudaSuccess &&
-                  dalloc(&c->adj_h, N) == cudaSuccess && dalloc(&c->adj_gws, N) == cudaSuccess &&
-                  dalloc(&c->adj_io, (size_t)4 * N) == cudaSuccess;
-        if (!ok) {
-            cudaGetLastError();
-            return fail(c, GS_ERR_OOM, "no memory for the reverse-mode buffers");
-        }
-    }
+    st = ensure_adjoint_buffers(c);
+    if (st) return st;
     // the caller's buffers in; the rest runs on the context's own buffers
     // (replayed as a graph when graphs are enabled)
     CK(cudaMemcpyAsync(c->lr_pos, x_in, N * sizeof(float4), cudaMemcpyDeviceToDevice, c->stream), "copy");
@@ -2263,7 +2437,9 @@ int gs_step_low_backward(gs_ctx* c, const float* x_in, const float* v_in, const 
 // stabilization passes snap[n_stab] throughout); snap_xt[total] holds the
 // step's final x~.  The passes read and write the snapshot buffers
 // themselves.
-static int step_low_record(gs_ctx* c, float dt, int iters)
+// The recording into given buffers (the snapshots X, XT and the candidate
+// lists nbr / cnt; the cell order is left in lr_sorted_idx).
+static int step_low_record_into(gs_ctx* c, float dt, int iters, float4* X, float4* XT, uint32_t* nbr, uint32_t* cnt)
 {
     const int64_t N = c->n_low;
     const int total = c->n_stab + iters;
@@ -2273,45 +2449,58 @@ static int step_low_record(gs_ctx* c, float dt, int iters)
     CK(gs_launch_predict(c->stream, a, c->lr_pos, c->lr_vel, c->lr_xt, &c->launches), "predict");
     st = bin_low_at(c, c->lr_xt);
     if (st) return st;
-    float4* const X = c->snap;
-    float4* const XT = c->snap_xt;
     CK(gs_launch_step_gather(c->stream, N, c->lr_sorted_idx, c->lr_xt, c->lr_pos, XT, X, &c->launches), "gather");
-    CK(gs_launch_neighbors(c->stream, a, XT, c->lr_sorted_keys, c->lr_cell_start, c->n_cell_total, c->nbr, c->nbr_cnt,
+    CK(gs_launch_neighbors(c->stream, a, XT, c->lr_sorted_keys, c->lr_cell_start, c->n_cell_total, nbr, cnt,
                            c->nbr_cap, c->d_err, &c->launches),
        "neighbours");
     for (int it = 0; it < total; ++it) {
         const int stab = it < c->n_stab;
         CK(gs_launch_pass(c->stream, a, stab, X + (size_t)std::min(it, c->n_stab) * N, XT + (size_t)it * N,
-                          X + (size_t)(it + 1) * N, XT + (size_t)(it + 1) * N, c->nbr, c->nbr_cnt, &c->launches),
+                          X + (size_t)(it + 1) * N, XT + (size_t)(it + 1) * N, nbr, cnt, &c->launches),
            "pass");
     }
     return GS_OK;
 }
 
+static int step_low_record(gs_ctx* c, float dt, int iters)
+{
+    return step_low_record_into(c, dt, iters, c->snap, c->snap_xt, c->nbr, c->nbr_cnt);
+}
+
+// The passes of a recorded LR step in reverse: dL/d outputs from
+// adj_io[0..1], dL/d inputs into adj_io[2..3]; X, XT, nbr, cnt as recorded,
+// idx the recording's cell order.
+static int step_low_reverse_from(gs_ctx* c, float dt, int iters, const float4* X, const float4* XT,
+                                 const uint32_t* nbr, const uint32_t* cnt, const uint32_t* idx);
+
 // The reverse LR step on the context's buffers: the step again from
 // (lr_pos, lr_vel) keeping what every pass evaluates on, then the passes in
-// reverse; dL/d outputs from adj_io[0..1], dL/d inputs into adj_io[2..3].
+// reverse.
 static int step_low_reverse(gs_ctx* c, float dt, int iters)
+{
+    int st = step_low_record(c, dt, iters);
+    if (st) return st;
+    return step_low_reverse_from(c, dt, iters, c->snap, c->snap_xt, c->nbr, c->nbr_cnt, c->lr_sorted_idx);
+}
+
+static int step_low_reverse_from(gs_ctx* c, float dt, int iters, const float4* X, const float4* XT,
+                                 const uint32_t* nbr, const uint32_t* cnt, const uint32_t* idx)
 {
     const int64_t N = c->n_low;
     const int total = c->n_stab + iters;
-    int st = step_low_record(c, dt, iters);
-    if (st) return st;
     PbdArgs a = pbd_args(c, dt);
-    float4* const X = c->snap;
-    float4* const XT = c->snap_xt;
     auto x_before = [&](int it) { return X + (size_t)std::min(it, c->n_stab) * N; };
     const float4* xfix = x_before(total);     // x after stabilization
     const float4* ws = XT;                    // w of xt carries the inverse scaled mass (every pass keeps it)
-    CK(gs_launch_adj_init(c->stream, N, c->lr_sorted_idx, c->adj_io, c->adj_io + N, dt, c->adj_gx, c->adj_gxt,
-                          c->adj_gws, &c->launches),
+    CK(gs_launch_adj_init(c->stream, N, idx, c->adj_io, c->adj_io + N, dt, c->adj_gx, c->adj_gxt, c->adj_gws,
+                          &c->launches),
        "reverse init");
     for (int it = total - 1; it >= 0; --it) {
         const int stab = it < c->n_stab;
         AdjRecord rec;
         if (c->rec_lr_pair) {
             const int n_comp = sdf_component_count(c);
-            rec.idx = c->lr_sorted_idx;
+            rec.idx = idx;
             rec.cand = c->rec_lr_cand;
             rec.pair = c->rec_lr_pair + (size_t)it * c->nbr_cap * N;
             rec.sdf = n_comp > 0 ? c->rec_lr_sdf + (size_t)it * N * n_comp : nullptr;
@@ -2319,11 +2508,10 @@ static int step_low_reverse(gs_ctx* c, float dt, int iters)
             rec.n_comp = n_comp;
         }
         CK(gs_launch_adj_pass(c->stream, a, stab, stab ? x_before(it) : XT + (size_t)it * N, XT + (size_t)it * N,
-                              xfix, ws,
-                              c->nbr, c->nbr_cnt, c->adj_h, c->adj_gx, c->adj_gxt, c->adj_gws, &c->launches, rec),
+                              xfix, ws, nbr, cnt, c->adj_h, c->adj_gx, c->adj_gxt, c->adj_gws, &c->launches, rec),
            "reverse pass");
     }
-    CK(gs_launch_adj_final(c->stream, a, c->lr_sorted_idx, ws, c->adj_gx, c->adj_gxt, c->adj_gws, c->adj_io + 2 * N,
+    CK(gs_launch_adj_final(c->stream, a, idx, ws, c->adj_gx, c->adj_gxt, c->adj_gws, c->adj_io + 2 * N,
                            c->adj_io + 3 * N, &c->launches),
        "reverse predict");
     c->lr_binned = false;

@@ -209,6 +209,37 @@ struct gs_ctx {
     float4* snap = nullptr;        // [n_pass_cap][n_low] positions each pass evaluates on
     float4* snap_xt = nullptr;     // [n_pass_cap][n_low] xt at each pass input
     int snap_cap = 0;
+    // taped LR steps (gs_set_step_tapes): each slot keeps what a recorded
+    // forward step evaluated on -- the pass snapshots, the candidate lists
+    // and the cell order -- for the step's backward without recomputation
+    struct StepTape {
+        int64_t tag = -1;          // the caller's tag; -1: empty
+        int64_t serial = -1;       // order of recording (the latest of equal tags wins)
+        float dt = 0.0f;
+        int iters = 0;
+        float4* X = nullptr;       // [tape_passes + 1][n_low], as snap
+        float4* XT = nullptr;      // [tape_passes + 1][n_low], as snap_xt
+        uint32_t* nbr = nullptr;   // [nbr_cap][n_low]
+        uint32_t* cnt = nullptr;   // [n_low]
+        uint32_t* idx = nullptr;   // [n_low] particle of each cell-ordered slot
+    };
+    std::vector<StepTape> tapes;
+    // native differentiable rollout (gs_rollout_forward / _backward): the
+    // checkpoints of the latest forward and the backward's scratch
+    float4* ro_ckpt = nullptr;       // [n_ckpt][2 n_low + 2 n_high]
+    int64_t ro_ckpt_cap = 0;         // float4 records
+    float4* ro_work = nullptr;       // a segment's states and the gradients
+    int64_t ro_work_cap = 0;
+    float4* ro_io = nullptr;         // the rollout's own copies of the caller's buffers (8 fields)
+    bool ro_valid = false;
+    bool capturing = false;          // a sequence is being captured: inner sequences run directly
+    std::vector<uint64_t> ro_seen;   // rollout sequences run once directly (captured on the next call)
+    float ro_dt = 0.0f;
+    int ro_frames = 0, ro_n_sub = 0, ro_iters = 0, ro_every = 0;
+    int64_t ro_serial = 0;
+    int tape_passes = 0;
+    int64_t tape_serial = 0;
+    int tape_next = 0;
     float4* adj_gx = nullptr;
     float4* adj_gxt = nullptr;
     float4* adj_h = nullptr;
@@ -463,6 +494,17 @@ cudaError_t gs_launch_adj_pass(cudaStream_t s, const PbdArgs& a, int stab, const
 cudaError_t gs_launch_adj_final(cudaStream_t s, const PbdArgs& a, const uint32_t* idx, const float4* WS,
                                 const float4* gx, const float4* gxt, const float* gws, float4* gx0, float4* gv0,
                                 int64_t* launches);
+
+// Records an error on the context (gs_last_error) and returns code.
+int gs_ctx_fail(gs_ctx* c, int code, const char* msg);
+// Runs body(c, arg) directly, or (graphs enabled, a capturable stream, not
+// inside another capture) as a CUDA graph captured once per key and
+// replayed; the host-side state the body leaves is recorded at capture and
+// applied on every replay.
+int gs_replay_or_run(gs_ctx* c, uint64_t key, int (*body)(gs_ctx*, void*), void* arg);
+// A key of the functional sequences: kind, step length, passes and the
+// context's launch configuration.
+uint64_t gs_sequence_key(const gs_ctx* c, char kind, float dt, int iters);
 
 // Device allocation through the library's allocation-failure hook
 // (gs_set_alloc_failure), for code outside a context.

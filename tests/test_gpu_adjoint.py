@@ -406,3 +406,99 @@ def test_stepwise_reverse_along_config4_trajectory(orc, step):
             assert val <= 1e-4, (k, res)
     # single passes compare most of the column
     assert res["solve1_suspect_frac"] <= 0.5 and res["stab1_suspect_frac"] <= 0.5, res
+
+
+def test_taped_steps_equal_recording_steps_bitwise():
+    """A taped LR step (the forward keeps its recorded passes under a tag)
+    gives the forward outputs and the gradients of the plain functional
+    forms bit for bit; a record that was overwritten is refused
+    (GS_ERR_STATE), and the checkpointed rollout with tapes gives the
+    gradient of the rollout without them."""
+    torch = pytest.importorskip("torch")
+    import paper_2308_01629_gb300 as gs
+    from paper_2308_01629_gb300.diff import rollout
+    sc = scenes.diff_column()
+    dev = torch.device("cuda")
+    g = gs.Context(sc, stream="torch")
+    g.set_graphs(True)
+    X = torch.from_numpy(sc["lr_pos"]).to(dev)
+    V = torch.from_numpy(sc["lr_vel"]).to(dev)
+    dt, iters = sc["dt"], sc["iters"]
+    ref_x, ref_v = torch.empty_like(X), torch.empty_like(V)
+    assert gs.gs_step_low_forward(g.ctx, X.data_ptr(), V.data_ptr(), ref_x.data_ptr(), ref_v.data_ptr(), dt,
+                                  iters) == 0
+    g.set_step_tapes(2)
+    tapes, outs = [7, 8, 9], []
+    x, v = X, V
+    for k in range(3):   # three taped steps in two slots: the first record is overwritten
+        ox, ov = torch.empty_like(X), torch.empty_like(V)
+        assert gs.gs_step_low_forward_taped(g.ctx, x.data_ptr(), v.data_ptr(), ox.data_ptr(), ov.data_ptr(), dt,
+                                            iters, tapes[k]) == 0
+        outs.append((x, v, ox, ov))
+        x, v = ox, ov
+    torch.cuda.synchronize()
+    assert torch.equal(outs[0][2], ref_x) and torch.equal(outs[0][3], ref_v)
+    gx_o = torch.randn_like(X)
+    gx_o[:, 3] = 0
+    gv_o = torch.randn_like(V)
+    gv_o[:, 3] = 0
+    a = [torch.empty_like(X) for _ in range(4)]
+    assert gs.gs_step_low_backward_taped(g.ctx, tapes[0], gx_o.data_ptr(), gv_o.data_ptr(), a[0].data_ptr(),
+                                         a[1].data_ptr()) == gs.GS_ERR_STATE
+    for k in (2, 1):
+        xi, vi = outs[k][0], outs[k][1]
+        assert gs.gs_step_low_backward_taped(g.ctx, tapes[k], gx_o.data_ptr(), gv_o.data_ptr(), a[0].data_ptr(),
+                                             a[1].data_ptr()) == 0
+        assert gs.gs_step_low_backward(g.ctx, xi.data_ptr(), vi.data_ptr(), gx_o.data_ptr(), gv_o.data_ptr(),
+                                       a[2].data_ptr(), a[3].data_ptr(), dt, iters) == 0
+        torch.cuda.synchronize()
+        assert torch.equal(a[0], a[2]) and torch.equal(a[1], a[3]), k
+    # the rollout: with tapes and without (the HR backward's atomics make the
+    # gradient vary in the last bits from run to run, so compare closely)
+    target = torch.from_numpy(sc["target"]).to(dev)
+    hx, hv = (torch.from_numpy(np.ascontiguousarray(sc[n])).to(dev) for n in ("hr_pos", "hr_vel"))
+
+    def grad(tapes):
+        Vr = V.clone().requires_grad_(True)
+        out = rollout(g, X, Vr, hx, hv, dt, frames=10, n_sub=1, iters=iters, checkpoint_every=5, tapes=tapes)
+        ((out[2][:, :3] - target) ** 2).sum().backward()
+        return Vr.grad
+    g0, g1 = grad(False), grad(True)
+    rel = float((g1 - g0).norm() / g0.norm())
+    assert rel < 1e-5, rel
+    g.close()
+
+
+@pytest.mark.parametrize("frames, every, n_sub", [(7, 3, 2), (6, 6, 1), (5, 1, 1)])
+def test_native_rollout_equals_the_torch_driven_rollout(frames, every, n_sub):
+    """The rollout run by the library (gs_rollout_forward / _backward) gives
+    the final state of the torch-driven checkpointed rollout bit for bit and
+    its gradients with respect to all four initial fields (up to the order
+    of the HR backward's atomic sums); a backward after another rollout's
+    forward is refused."""
+    import torch
+
+    import paper_2308_01629_gb300 as gs
+    from paper_2308_01629_gb300.diff import rollout
+    sc = scenes.column(n_low=400, ratio=8)
+    g = gs.Context(sc, stream="torch")
+    g.set_graphs(True)
+    res = {}
+    for native in (False, True):
+        ins = [_t(sc[k]).requires_grad_(True) for k in ("lr_pos", "lr_vel", "hr_pos", "hr_vel")]
+        out = rollout(g, *ins, DT, frames=frames, n_sub=n_sub, iters=4, checkpoint_every=every, native=native)
+        loss = ((out[2][:, :3] - 0.1) ** 2).sum() + (out[1][:, :3] ** 2).sum() + (out[3][:, :3] ** 2).sum()
+        loss.backward()
+        res[native] = ([o.detach().cpu().numpy() for o in out], [t.grad.cpu().numpy()[:, :3] for t in ins])
+    for a, b in zip(res[False][0], res[True][0]):
+        np.testing.assert_array_equal(a, b)
+    for a, b in zip(res[False][1], res[True][1]):
+        assert np.abs(a).max() > 0
+        assert _rel(b, a) < 1e-5
+    # two forwards, then the first one's backward
+    ins = [_t(sc[k]).requires_grad_(True) for k in ("lr_pos", "lr_vel", "hr_pos", "hr_vel")]
+    o1 = rollout(g, *ins, DT, frames=2, n_sub=1, iters=4, checkpoint_every=1)
+    rollout(g, *[t.detach() for t in ins], DT, frames=2, n_sub=1, iters=4, checkpoint_every=1)
+    with pytest.raises(RuntimeError):
+        o1[2].sum().backward()
+    g.close()

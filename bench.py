@@ -94,6 +94,8 @@ def parse(argv=None):
     ap.add_argument("--no-materials", action="store_true", help="skip the grain-material frame timing")
     ap.add_argument("--no-adaptive", action="store_true", help="skip the CFL-limited substep frame timing")
     ap.add_argument("--no-solid", action="store_true", help="skip the particle-sampled bucket frame timing")
+    ap.add_argument("--no-castle", action="store_true",
+                    help="skip the mesh-sampled sand-castle scene (volume sampler and frame timing)")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="do not try pipelined frames (HR frame overlapping the next frame's LR steps)")
     ap.add_argument("--partition", choices=["replicas", "slab"], default="replicas",
@@ -620,6 +622,34 @@ def run_gpu(args):
                  "frame_ms_boulder_shape_matched": float(np.median(tried["boulder"])),
                  "timing": "median of 3 alternating runs of 8 graph-replayed frames, L2 not flushed"}
 
+    # the sand-castle scene of Sec. 5 seeded by the library's volume sampler
+    # (castle grains and HR particles, an icosphere boulder as one rigid body
+    # flying at it): the sampler's time and the scene's frame time
+    castle = None
+    if not args.no_castle:
+        t_sample = {}
+
+        def timed_sample(V, T, C, r):
+            t0 = time.perf_counter()
+            sel = gs.sample_volume(V, T, C, r)
+            t_sample.setdefault(f"r={r}", []).append((len(C), len(sel), 1e3 * (time.perf_counter() - t0)))
+            return sel
+        cs = scenes.castle_scene(timed_sample)
+        x = gs.Context(cs, stream=stream.cuda_stream)
+        x.set_graphs(True)
+        frames_ms = [frame_ms(lambda: x.frame(DT, N_SUB, cs["iters"]), stream, dev, torch, warm=3, reps=8)
+                     for _ in range(3)]
+        x.sync()
+        x.close()
+        castle = {"n_low_grains": int(len(cs["lr_pos"]) - cs["n_body"]), "boulder_particles": int(cs["n_body"]),
+                  "n_high": len(cs["hr_pos"]), "r_low": cs["r_low"], "r_high": cs["r_high"],
+                  "frame_ms": float(np.median(frames_ms)),
+                  "hr_per_s": len(cs["hr_pos"]) / (float(np.median(frames_ms)) / 1e3),
+                  "sampling": [{"mesh_and_radius": k, "candidates": v[0][0], "samples": v[0][1],
+                                "ms_including_transfers": round(v[0][2], 2)} for k, v in t_sample.items()],
+                  "timing": "median of 3 runs of 8 graph-replayed frames, L2 not flushed; the sampler by host "
+                            "wall clock around gs_sample_volume (host arrays in and out)"}
+
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -728,6 +758,7 @@ def run_gpu(args):
         "materials": materials,
         "adaptive_substeps": adaptive,
         "solid_particles": solid,
+        "castle": castle,
     }
     if not args.no_cpu:
         line["cpu_baseline"] = oracle_frame_rate(sc, args.cpu_seconds)

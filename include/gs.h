@@ -361,6 +361,15 @@ int gs_sample_volume(const double* vertices, int64_t n_vertices, const int32_t* 
                      const double* candidates, int64_t n_candidates, double r, int64_t* selected, int64_t capacity,
                      int64_t* n_selected, uint8_t* inside);
 
+/* Surface sampling for particle-sampled boundaries (Sec. 3: a stationary
+ * body's particles of infinite mass need only cover its surface): the same
+ * grid over the vertices' bounding box and the same cell-by-cell pick as
+ * gs_sample_volume, with every candidate valid; the candidates are points
+ * on the mesh's triangles (uniform by area, drawn by the caller).  Arguments,
+ * outputs and errors as gs_sample_volume. */
+int gs_sample_surface(const double* vertices, int64_t n_vertices, const double* candidates, int64_t n_candidates,
+                      double r, int64_t* selected, int64_t capacity, int64_t* n_selected);
+
 /* The LR steps of the latest adaptive frame: *n_out receives their number
  * and dts[0 .. min(n, cap)) their lengths.  Blocks. */
 int gs_substeps(gs_ctx* ctx, float* dts, int cap, int* n_out);

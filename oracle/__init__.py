@@ -112,6 +112,8 @@ def _L():
         L.or_sample_volume.argtypes = [P, ctypes.c_long, P, ctypes.c_long, P, ctypes.c_long, ctypes.c_double, P,
                                        ctypes.c_long, P]
         L.or_sample_volume.restype = ctypes.c_long
+        L.or_sample_surface.argtypes = [P, ctypes.c_long, P, ctypes.c_long, ctypes.c_double, P, ctypes.c_long]
+        L.or_sample_surface.restype = ctypes.c_long
         L.or_pairs_within_grid.argtypes = L.or_pairs_within.argtypes
         L.or_pairs_within_grid.restype = ctypes.c_long
         _lib = L
@@ -589,3 +591,15 @@ def sample_volume(V, T, candidates, r):
     if n < 0:
         raise RuntimeError(f"or_sample_volume failed ({n})")
     return sel[:n].copy(), inside[:len(cand)].astype(bool)
+
+
+def sample_surface(V, candidates, r):
+    """The surface sampler (see or_sample_surface): indices of the chosen
+    candidates in ascending cell order."""
+    V = _f64(V, 3)
+    cand = _f64(candidates, 3)
+    sel = np.zeros(max(1, len(cand)), np.int64)
+    n = _L().or_sample_surface(_ptr(V), len(V), _ptr(cand), len(cand), float(r), _ptr(sel), len(sel))
+    if n < 0:
+        raise RuntimeError(f"or_sample_surface failed ({n})")
+    return sel[:n].copy()

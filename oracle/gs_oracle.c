@@ -2294,8 +2294,10 @@ static long sample_cell(const double* p, const double* lo, double h, const long*
  * most cap); returns their number, or -1 (allocation), -2 (cap too small),
  * -3 (grid of more than 2^31 cells).  inside (optional, nc) receives the
  * inside flag of every candidate. */
-long or_sample_volume(const double* V, long nv, const int32_t* T, long nt, const double* cand, long nc, double r,
-                      long* selected, long cap, unsigned char* inside)
+/* The cell-by-cell pick among the candidates flagged in in[] (see
+ * or_sample_volume). */
+static long sample_pick(const double* V, long nv, const double* cand, long nc, double r, const unsigned char* in,
+                        long* selected, long cap)
 {
     double lo[3], h;
     long dims[3];
@@ -2303,18 +2305,14 @@ long or_sample_volume(const double* V, long nv, const int32_t* T, long nt, const
     const double ncell_d = (double)dims[0] * (double)dims[1] * (double)dims[2];
     if (ncell_d > 2147483647.0) return -3;
     const long ncell = dims[0] * dims[1] * dims[2];
-    unsigned char* in = (unsigned char*)malloc((size_t)(nc ? nc : 1));
     long* first = (long*)calloc((size_t)ncell + 1, sizeof(long));   /* inside candidates of cell c: order[first[c] ..) */
     long* order = (long*)malloc((size_t)(nc ? nc : 1) * sizeof(long));
     long* pick = (long*)malloc((size_t)ncell * sizeof(long));        /* the cell's sample (candidate index) or -1 */
     long* cellof = (long*)malloc((size_t)(nc ? nc : 1) * sizeof(long));
-    if (!in || !first || !order || !pick || !cellof) {
-        free(in); free(first); free(order); free(pick); free(cellof);
+    if (!first || !order || !pick || !cellof) {
+        free(first); free(order); free(pick); free(cellof);
         return -1;
     }
-    const int nth = g_threads;
-#pragma omp parallel for num_threads(nth) if (nth > 1) schedule(dynamic, 64)
-    for (long i = 0; i < nc; ++i) in[i] = or_winding_number(V, T, nt, cand + 3 * i) > 0.5;
     /* inside candidates by cell, in input order */
     for (long i = 0; i < nc; ++i) {
         long c3[3];
@@ -2324,7 +2322,7 @@ long or_sample_volume(const double* V, long nv, const int32_t* T, long nt, const
     for (long c = 0; c < ncell; ++c) first[c + 1] += first[c];
     {
         long* fill = (long*)malloc((size_t)ncell * sizeof(long));
-        if (!fill) { free(in); free(first); free(order); free(pick); free(cellof); return -1; }
+        if (!fill) { free(first); free(order); free(pick); free(cellof); return -1; }
         memcpy(fill, first, (size_t)ncell * sizeof(long));
         for (long i = 0; i < nc; ++i)
             if (in[i]) order[fill[cellof[i]]++] = i;
@@ -2363,8 +2361,36 @@ long or_sample_volume(const double* V, long nv, const int32_t* T, long nt, const
         else full = 1;
         ++n;
     }
+    free(first); free(order); free(pick); free(cellof);
+    return full ? -2 : n;
+}
+
+long or_sample_volume(const double* V, long nv, const int32_t* T, long nt, const double* cand, long nc, double r,
+                      long* selected, long cap, unsigned char* inside)
+{
+    unsigned char* in = (unsigned char*)malloc((size_t)(nc ? nc : 1));
+    if (!in) return -1;
+    const int nth = g_threads;
+#pragma omp parallel for num_threads(nth) if (nth > 1) schedule(dynamic, 64)
+    for (long i = 0; i < nc; ++i) in[i] = or_winding_number(V, T, nt, cand + 3 * i) > 0.5;
+    const long n = sample_pick(V, nv, cand, nc, r, in, selected, cap);
     if (inside)
         for (long i = 0; i < nc; ++i) inside[i] = in[i];
-    free(in); free(first); free(order); free(pick); free(cellof);
-    return full ? -2 : n;
+    free(in);
+    return n;
+}
+
+/* Surface sampling (Sec. 3: a stationary body needs only its surface
+ * sampled with particles of infinite mass): the same cell-by-cell pick,
+ * every candidate valid.  The candidates are points on the mesh's triangles
+ * (uniform by area, drawn by the caller); the grid is that of the vertices'
+ * bounding box. */
+long or_sample_surface(const double* V, long nv, const double* cand, long nc, double r, long* selected, long cap)
+{
+    unsigned char* in = (unsigned char*)malloc((size_t)(nc ? nc : 1));
+    if (!in) return -1;
+    memset(in, 1, (size_t)(nc ? nc : 1));
+    const long n = sample_pick(V, nv, cand, nc, r, in, selected, cap);
+    free(in);
+    return n;
 }

@@ -121,6 +121,8 @@ _SIGS = {
     "gs_rollout_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_int, _P, _P, _P, _P]),
     "gs_rollout_backward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "gs_sample_surface": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_double, _P,
+                                         ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "gs_sample_volume": (ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_double,
                                         _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _P]),
     "gs_hr_slab_assemble": (ctypes.c_int, [_P, _P, _P, ctypes.c_size_t, ctypes.c_int]),
@@ -383,6 +385,26 @@ def gs_sample_volume(vertices, triangles, candidates, r, capacity=None):
     rc = lib().gs_sample_volume(V.ctypes.data, len(V), T.ctypes.data, len(T), C.ctypes.data, len(C), float(r),
                                 sel.ctypes.data, cap, ctypes.byref(n), inside.ctypes.data)
     return rc, sel[:min(n.value, cap)].copy(), inside[:len(C)].astype(bool)
+
+
+def gs_sample_surface(vertices, candidates, r, capacity=None):
+    """(status, selected): the surface sampler (see include/gs.h)."""
+    V = np.ascontiguousarray(np.asarray(vertices, np.float64).reshape(-1, 3))
+    C = np.ascontiguousarray(np.asarray(candidates, np.float64).reshape(-1, 3))
+    cap = len(C) if capacity is None else int(capacity)
+    sel = np.zeros(max(cap, 1), np.int64)
+    n = ctypes.c_int64()
+    rc = lib().gs_sample_surface(V.ctypes.data, len(V), C.ctypes.data, len(C), float(r), sel.ctypes.data, cap,
+                                 ctypes.byref(n))
+    return rc, sel[:min(n.value, cap)].copy()
+
+
+def sample_surface(vertices, candidates, r):
+    """Indices of the chosen surface candidates; raises on error."""
+    rc, sel = gs_sample_surface(vertices, candidates, r)
+    if rc != GS_OK:
+        raise GsError(rc, "gs_sample_surface failed")
+    return sel
 
 
 def sample_volume(vertices, triangles, candidates, r):

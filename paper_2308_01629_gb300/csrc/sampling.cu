@@ -58,18 +58,23 @@ struct SampleGrid {
 // Inside flag and cell of every candidate; the cell's counter gives the
 // candidate its arrival rank (the counting sort puts each cell in index
 // order afterwards).
+// surface: every candidate counts (points on the surface), no winding number.
 __global__ void k_sample_classify(const double* __restrict__ V, const int32_t* __restrict__ T, int64_t nt,
                                   const double* __restrict__ cand, int64_t nc, const SampleGrid g,
                                   uint8_t* __restrict__ inside, uint32_t* __restrict__ keys,
-                                  uint32_t* __restrict__ rank, uint32_t* __restrict__ cell_count)
+                                  uint32_t* __restrict__ rank, uint32_t* __restrict__ cell_count, int surface)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nc) return;
     const double p[3] = {cand[3 * i], cand[3 * i + 1], cand[3 * i + 2]};
-    double w = 0.0;
-    for (int64_t t = 0; t < nt; ++t)
-        w = __dadd_rn(w, tri_winding(V + 3 * T[3 * t], V + 3 * T[3 * t + 1], V + 3 * T[3 * t + 2], p));
-    inside[i] = w > 0.5 ? 1 : 0;
+    if (surface) {
+        inside[i] = 1;
+    } else {
+        double w = 0.0;
+        for (int64_t t = 0; t < nt; ++t)
+            w = __dadd_rn(w, tri_winding(V + 3 * T[3 * t], V + 3 * T[3 * t + 1], V + 3 * T[3 * t + 2], p));
+        inside[i] = w > 0.5 ? 1 : 0;
+    }
     int64_t c[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -146,9 +151,9 @@ struct StreamGuard {
 
 }  // namespace
 
-extern "C" int gs_sample_volume(const double* vertices, int64_t n_vertices, const int32_t* triangles,
-                                int64_t n_triangles, const double* candidates, int64_t n_candidates, double r,
-                                int64_t* selected, int64_t capacity, int64_t* n_selected, uint8_t* inside)
+static int sample_impl(const double* vertices, int64_t n_vertices, const int32_t* triangles, int64_t n_triangles,
+                       const double* candidates, int64_t n_candidates, double r, int64_t* selected, int64_t capacity,
+                       int64_t* n_selected, uint8_t* inside, int surface)
 {
     if (!n_selected || n_vertices < 0 || n_triangles < 0 || n_candidates < 0 || capacity < 0) return GS_ERR_ARG;
     *n_selected = 0;
@@ -209,7 +214,8 @@ extern "C" int gs_sample_volume(const double* vertices, int64_t n_vertices, cons
     SK(gs_cs_clear(s, start, ncell));
     SK(cudaMemsetAsync(dpick, 0xff, sizeof(int32_t) * (size_t)ncell, s));
     if (nc) {
-        k_sample_classify<<<gs_blocks(nc, 128), 128, 0, s>>>(dV, dT, n_triangles, dC, nc, g, din, keys, rank, start);
+        k_sample_classify<<<gs_blocks(nc, 128), 128, 0, s>>>(dV, dT, n_triangles, dC, nc, g, din, keys, rank, start,
+                                                             surface);
         SK(cudaGetLastError());
         // stable counting sort by cell: each cell's candidates in input order
         SK(gs_cs_finish(s, nc, ncell, keys, rank, okeys, oidx, start, aux, nullptr, nullptr, nullptr, nullptr,
@@ -238,4 +244,20 @@ extern "C" int gs_sample_volume(const double* vertices, int64_t n_vertices, cons
     }
     *n_selected = n;
     return n > capacity ? GS_ERR_CAPACITY : GS_OK;
+}
+
+extern "C" int gs_sample_volume(const double* vertices, int64_t n_vertices, const int32_t* triangles,
+                                int64_t n_triangles, const double* candidates, int64_t n_candidates, double r,
+                                int64_t* selected, int64_t capacity, int64_t* n_selected, uint8_t* inside)
+{
+    return sample_impl(vertices, n_vertices, triangles, n_triangles, candidates, n_candidates, r, selected, capacity,
+                       n_selected, inside, 0);
+}
+
+extern "C" int gs_sample_surface(const double* vertices, int64_t n_vertices, const double* candidates,
+                                 int64_t n_candidates, double r, int64_t* selected, int64_t capacity,
+                                 int64_t* n_selected)
+{
+    return sample_impl(vertices, n_vertices, nullptr, 0, candidates, n_candidates, r, selected, capacity, n_selected,
+                       nullptr, 1);
 }

@@ -603,3 +603,36 @@ def castle_scene(sample, seed=SEED_BASE + 11, size=1.25, height=0.4, r_low=0.02,
                 ratio=ratio, sdfs=[box_interior(lo, hi)], gravity=GRAVITY, mu_s=MU_S, mu_k=MU_K, dt=float(dt),
                 iters=int(iters), lr_pos=lr_pos, lr_vel=lr_vel, hr_pos=hr_pos,
                 hr_vel=np.zeros((len(hr_pos), 4), np.float32), lr_body=body, n_body=len(bd))
+
+
+def surface_candidates(V, T, r, per_cell=6.0, seed=SEED_BASE + 12):
+    """Uniform random candidate positions on the triangles of a mesh (each
+    triangle chosen with probability proportional to its area) for the
+    surface sampler: about per_cell candidates per area h^2 of a cell of
+    side h = 2 r / sqrt(3)."""
+    A, B, C = V[T[:, 0]], V[T[:, 1]], V[T[:, 2]]
+    area = 0.5 * np.linalg.norm(np.cross(B - A, C - A), axis=1)
+    h = 2 * r / math.sqrt(3)
+    n = int(math.ceil(per_cell * float(area.sum()) / h ** 2))
+    rng = np.random.default_rng(seed)
+    tri = rng.choice(len(T), size=n, p=area / area.sum())
+    u, v = rng.random(n), rng.random(n)
+    flip = u + v > 1.0
+    u[flip], v[flip] = 1.0 - u[flip], 1.0 - v[flip]
+    return A[tri] + u[:, None] * (B[tri] - A[tri]) + v[:, None] * (C[tri] - A[tri])
+
+
+def digging_mesh_bucket(sample_surface, seed=SEED_BASE + 13, t=0.0, **kw):
+    """The digging bed with the bucket as particles of inverse mass 0 sampled
+    on the surface of its box mesh by `sample_surface(V, candidates, r)` (the
+    surface sampler, returning the chosen candidates' indices), moving with
+    the bucket's velocity at time t, in place of the bucket SDF."""
+    sc = digging(**kw)
+    c, u = bucket_pose(t)
+    V, T = box_mesh(np.asarray(c) - BUCKET_HALF, np.asarray(c) + BUCKET_HALF)
+    cand = surface_candidates(V, T, sc["r_low"], seed=seed)
+    pts = cand[sample_surface(V, cand, sc["r_low"])]
+    sc = with_solids(sc, pts, u, seed)
+    sc["sdfs"] = [sc["sdfs"][0]]
+    sc.pop("bucket_index", None)
+    return sc

@@ -74,3 +74,25 @@ def test_castle_scene_seeded_by_the_sampler_runs():
     assert np.abs(lr[body, :3] - sc["lr_pos"][body, :3]).max() > 0.05    # the boulder flew
     assert np.abs(x1[:, :3] - x0[:, :3]).max() > 0.0
     ctx.close()
+
+
+def test_surface_samples_equal_the_oracle_and_the_mesh_bucket_runs(orc):
+    import paper_2308_01629_gb300 as gs
+    for V, T, r in [(*scenes.box_mesh((0.1, 0.2, 0.05), (0.35, 0.3, 0.2)), 0.01),
+                    (*scenes.icosphere((0.0, 0.0, 0.0), 0.2, 3), 0.006)]:
+        cand = scenes.surface_candidates(V, T, r, seed=9)
+        rc, sel = gs.gs_sample_surface(V, cand, r)
+        assert rc == gs.GS_OK
+        np.testing.assert_array_equal(sel, orc.sample_surface(V, cand, r))
+    sc = scenes.digging_mesh_bucket(gs.sample_surface, size=0.5)
+    ctx = gs.Context(sc)
+    n_g = len(sc["lr_pos"]) - sc["n_solid"]
+    x0 = ctx.read(gs.GS_FIELD_LR_POS)
+    for _ in range(4):
+        ctx.frame(1.0 / 60.0, 4, sc["iters"])
+    x1 = ctx.read(gs.GS_FIELD_LR_POS)
+    assert np.isfinite(x1).all() and np.isfinite(ctx.read(gs.GS_FIELD_HR_POS)).all()
+    # the boundary particles move with their prescribed velocity
+    u = sc["lr_vel"][n_g:, :3]
+    np.testing.assert_allclose(x1[n_g:, :3] - x0[n_g:, :3], 4 / 60.0 * u, atol=1e-5)
+    ctx.close()

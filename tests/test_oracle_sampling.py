@@ -164,3 +164,36 @@ def test_sampler_edge_cases(orc):
     # two candidates in one cell: the first one wins
     sel, _ = orc.sample_volume(V, T, [[0.05, 0.05, 0.05], [0.0501, 0.05, 0.05]], r)
     np.testing.assert_array_equal(sel, [0])
+
+
+def test_surface_sampler_on_a_box(orc):
+    """Surface sampling (Sec. 3's boundary particles): every sample on a face
+    of the box, pairs at least 2 r apart, one per cell at most, every
+    unchosen candidate blocked by a sample or behind its cell's pick, the
+    brute-force greedy's result, the same samples for the same seed."""
+    lo, hi = np.array([0.1, 0.2, 0.05]), np.array([0.35, 0.3, 0.2])
+    V, T = scenes.box_mesh(lo, hi)
+    r = 0.01
+    cand = scenes.surface_candidates(V, T, r, per_cell=5.0, seed=4)
+    on_face = np.any(np.isclose(cand, lo, atol=1e-12) | np.isclose(cand, hi, atol=1e-12), axis=1)
+    assert on_face.all()   # the candidate generator puts points on the faces
+    sel = orc.sample_surface(V, cand, r)
+    P = cand[sel]
+    assert len(sel) > 100
+    d2 = ((P[:, None, :] - P[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(d2, np.inf)
+    assert d2.min() >= 4 * r * r
+    c, dims, h = _cells(orc, V, r, P)
+    lin = c[:, 0] + dims[0] * (c[:, 1] + dims[1] * c[:, 2])
+    assert len(np.unique(lin)) == len(lin) and np.all(np.diff(lin) > 0)
+    ci, _, _ = _cells(orc, V, r, cand)
+    lin_c = ci[:, 0] + dims[0] * (ci[:, 1] + dims[1] * ci[:, 2])
+    pick_of = dict(zip(lin.tolist(), sel.tolist()))
+    chosen = np.zeros(len(cand), bool)
+    chosen[sel] = True
+    for i in np.flatnonzero(~chosen):
+        assert ((P - cand[i]) ** 2).sum(-1).min() < 4 * r * r or pick_of.get(int(lin_c[i]), 1 << 62) < i, i
+    small = cand[:400]
+    np.testing.assert_array_equal(orc.sample_surface(V, small, r),
+                                  _greedy_brute(orc, V, r, small, np.ones(len(small), bool)))
+    np.testing.assert_array_equal(sel, orc.sample_surface(V, scenes.surface_candidates(V, T, r, 5.0, seed=4), r))

@@ -475,7 +475,7 @@ def run_gpu(args):
         # overlapping the LR steps of frame f + 1, for a few gather shapes):
         # whichever whole frame is faster is timed below
         tried = {}
-        for shape in (None, (8, 1), (4, 2), (4, 0)):
+        for shape in (None, (8, 1), (8, 3), (4, 2), (4, 0)):
             if shape is None:
                 ctx.set_pipeline(False, 8, 1)
             else:

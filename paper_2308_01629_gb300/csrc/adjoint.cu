@@ -348,6 +348,34 @@ __device__ __forceinline__ int lanes_sum(int v)
     return v;
 }
 
+// The active constraints of particle p's pass on y (its pair contacts and
+// SDF contacts), counted by the lanes of p (lane takes candidates lane,
+// lane + kAdjLanes, ...; components likewise); the lanes' partial counts.
+__device__ __forceinline__ int lane_active_count(const PbdArgs& a, const SceneDev& sc, const float4* __restrict__ Y,
+                                                 const float4* __restrict__ WS, const uint32_t* __restrict__ nbr,
+                                                 int64_t p, int nc, float4 yp, float wp, int lane)
+{
+    const float d0 = 2.0f * sc.r_low;
+    int n_act = 0;
+    for (int k = lane; k < nc; k += kAdjLanes) {
+        const uint32_t q = nbr[(int64_t)k * a.n + p];
+        const PairGeo g = pair_geo(yp, Y[q]);
+        if (!(g.d < d0) || g.d2 == 0.0f) continue;
+        if (!(wp + WS[q].w > 0.0f)) continue;
+        ++n_act;
+    }
+    if (wp > 0.0f) {
+        int gc = 0;   // component index over all the scene's SDFs
+        for (int s = 0; s < sc.n_sdf; ++s) {
+            const gs_sdf& b = a.sdf[sc.sdf_begin + s];
+            const int ncomp = sdf_components(b.kind);
+            for (int c = 0; c < ncomp; ++c, ++gc)
+                if (gc % kAdjLanes == lane && sdf_eval(b, c, yp.x, yp.y, yp.z).phi < sc.r_low) ++n_act;
+        }
+    }
+    return n_act;
+}
+
 // h_p = upstream_p / n_p for one pass (n_p = active pair and SDF contacts)
 __global__ void k_adj_h(const PbdArgs a, int stab, const float4* __restrict__ Y, const float4* __restrict__ WS,
                         const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ cnt,
@@ -360,26 +388,7 @@ __global__ void k_adj_h(const PbdArgs a, int stab, const float4* __restrict__ Y,
     int n_act = 0;
     if (live) {
         const SceneDev& sc = a.scenes[a.lr_scene[p]];
-        const float d0 = 2.0f * sc.r_low;
-        const float4 yp = Y[p];
-        const float wp = WS[p].w;
-        const int nc = (int)cnt[p];
-        for (int k = lane; k < nc; k += kAdjLanes) {
-            const uint32_t q = nbr[(int64_t)k * a.n + p];
-            const PairGeo g = pair_geo(yp, Y[q]);
-            if (!(g.d < d0) || g.d2 == 0.0f) continue;
-            if (!(wp + WS[q].w > 0.0f)) continue;
-            ++n_act;
-        }
-        if (wp > 0.0f) {
-            int gc = 0;   // component index over all the scene's SDFs
-            for (int s = 0; s < sc.n_sdf; ++s) {
-                const gs_sdf& b = a.sdf[sc.sdf_begin + s];
-                const int ncomp = sdf_components(b.kind);
-                for (int c = 0; c < ncomp; ++c, ++gc)
-                    if (gc % kAdjLanes == lane && sdf_eval(b, c, yp.x, yp.y, yp.z).phi < sc.r_low) ++n_act;
-            }
-        }
+        n_act = lane_active_count(a, sc, Y, WS, nbr, p, (int)cnt[p], Y[p], WS[p].w, lane);
     }
     n_act = lanes_sum(n_act);
     if (!live || lane != 0) return;
@@ -400,17 +409,27 @@ __global__ void k_adj_h(const PbdArgs a, int stab, const float4* __restrict__ Y,
 // pair[k n + i] = bit 0 contact (|x_ij| < 2 r_LR), bit 1 kinetic friction
 // scale; for SDF component c, sdf[i n_comp + c] = bit 0 contact, bit 1
 // kinetic friction scale.  Entries of absent candidates: index -1, bits 0.
+// Y_next (not null): the evaluation positions of the pass before this one
+// (the next to reverse), whose h = upstream / n_p the particle's lanes
+// compute at the end from its updated gradients (stab_next: that pass is a
+// stabilization pass) into H_next, bitwise as k_adj_h would.
 __global__ void k_adj_pass(const PbdArgs a, int stab, const float4* __restrict__ Y, const float4* __restrict__ XT,
                            const float4* __restrict__ XF, const float4* __restrict__ WS,
                            const uint32_t* __restrict__ nbr, const uint32_t* __restrict__ cnt,
                            const float4* __restrict__ H, float4* __restrict__ gx, float4* __restrict__ gxt,
-                           float* __restrict__ gws, const AdjRecord rec)
+                           float* __restrict__ gws, const AdjRecord rec, const float4* __restrict__ Y_next,
+                           int stab_next, float4* __restrict__ H_next)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t p = t / kAdjLanes;
     const int lane = (int)(t % kAdjLanes);
     const bool live = p < a.n;   // every lane stays for the shuffles
     float acc[3] = {0.f, 0.f, 0.f}, accx[3] = {0.f, 0.f, 0.f}, gw = 0.0f;
+    int n_next = 0;
+    if (live && Y_next) {
+        const SceneDev& sc = a.scenes[a.lr_scene[p]];
+        n_next = lane_active_count(a, sc, Y_next, WS, nbr, p, (int)cnt[p], Y_next[p], WS[p].w, lane);
+    }
     if (live) {
         const SceneDev& sc = a.scenes[a.lr_scene[p]];
         const float d0 = 2.0f * sc.r_low;
@@ -537,17 +556,29 @@ __global__ void k_adj_pass(const PbdArgs a, int stab, const float4* __restrict__
         accx[k] = lanes_sum(accx[k]);
     }
     gw = lanes_sum(gw);
+    if (Y_next) n_next = lanes_sum(n_next);
     if (!live || lane != 0) return;
+    float4 ngx = gx[p], ngxt = gxt[p];
     if (stab) {
-        float4 v = gx[p];
-        gx[p] = make_float4(v.x + acc[0], v.y + acc[1], v.z + acc[2], 0.0f);
+        ngx = make_float4(ngx.x + acc[0], ngx.y + acc[1], ngx.z + acc[2], 0.0f);
+        gx[p] = ngx;
     } else {
-        float4 v = gxt[p];
-        gxt[p] = make_float4(v.x + acc[0], v.y + acc[1], v.z + acc[2], 0.0f);
-        float4 w = gx[p];
-        gx[p] = make_float4(w.x + accx[0], w.y + accx[1], w.z + accx[2], 0.0f);
+        ngxt = make_float4(ngxt.x + acc[0], ngxt.y + acc[1], ngxt.z + acc[2], 0.0f);
+        gxt[p] = ngxt;
+        ngx = make_float4(ngx.x + accx[0], ngx.y + accx[1], ngx.z + accx[2], 0.0f);
+        gx[p] = ngx;
     }
     gws[p] += gw;
+    if (Y_next) {   // h of the next pass to reverse, as k_adj_h
+        float4 up = ngxt;
+        if (stab_next) {
+            up.x += ngx.x;
+            up.y += ngx.y;
+            up.z += ngx.z;
+        }
+        const float inv = n_next > 0 ? 1.0f / (float)n_next : 0.0f;
+        H_next[p] = make_float4(up.x * inv, up.y * inv, up.z * inv, 0.0f);
+    }
 }
 
 // predict: xt = x + dt (v + dt g), w = (1/m) e^{k (z - ground)}
@@ -597,15 +628,25 @@ cudaError_t gs_launch_adj_init(cudaStream_t s, int64_t n, const uint32_t* idx, c
     return cudaGetLastError();
 }
 
-cudaError_t gs_launch_adj_pass(cudaStream_t s, const PbdArgs& a, int stab, const float4* Y, const float4* XT,
-                               const float4* XF, const float4* WS, const uint32_t* nbr, const uint32_t* cnt, float4* H,
-                               float4* gx, float4* gxt, float* gws, int64_t* launches, const AdjRecord& rec)
+cudaError_t gs_launch_adj_h(cudaStream_t s, const PbdArgs& a, int stab, const float4* Y, const float4* WS,
+                            const uint32_t* nbr, const uint32_t* cnt, const float4* gx, const float4* gxt, float4* H,
+                            int64_t* launches)
 {
     if (a.n <= 0) return cudaSuccess;
-    const int64_t threads = a.n * kAdjLanes;
-    k_adj_h<<<gs_blocks(threads, 128), 128, 0, s>>>(a, stab, Y, WS, nbr, cnt, gx, gxt, H);
-    k_adj_pass<<<gs_blocks(threads, 128), 128, 0, s>>>(a, stab, Y, XT, XF, WS, nbr, cnt, H, gx, gxt, gws, rec);
-    *launches += 2;
+    k_adj_h<<<gs_blocks(a.n * kAdjLanes, 128), 128, 0, s>>>(a, stab, Y, WS, nbr, cnt, gx, gxt, H);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_adj_pass(cudaStream_t s, const PbdArgs& a, int stab, const float4* Y, const float4* XT,
+                               const float4* XF, const float4* WS, const uint32_t* nbr, const uint32_t* cnt,
+                               const float4* H, float4* gx, float4* gxt, float* gws, int64_t* launches,
+                               const AdjRecord& rec, const float4* Y_next, int stab_next, float4* H_next)
+{
+    if (a.n <= 0) return cudaSuccess;
+    k_adj_pass<<<gs_blocks(a.n * kAdjLanes, 128), 128, 0, s>>>(a, stab, Y, XT, XF, WS, nbr, cnt, H, gx, gxt, gws, rec,
+                                                                Y_next, stab_next, H_next);
+    *launches += 1;
     return cudaGetLastError();
 }
 

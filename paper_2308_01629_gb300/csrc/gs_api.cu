@@ -1145,7 +1145,7 @@ void gs_destroy(gs_ctx* c)
                     c->hr_pos[0],  c->hr_pos[1],  c->hr_vel[0],  c->hr_vel[1],  c->hr_keys[0], c->hr_keys[1],
                     c->hr_vals[0], c->hr_vals[1], c->nbr,        c->nbr_cnt,    c->tmp4,      c->sort_hist,
                     c->d_work,     c->d_err,      c->gXs,        c->gVs,       c->snap,      c->snap_xt,
-                    c->adj_io,     c->fscratch,   c->adj_gx,     c->adj_gxt,    c->adj_h,      c->adj_gws,   c->scan_aux,   c->d_bar,
+                    c->adj_io,     c->fscratch,   c->adj_gx,     c->adj_gxt,    c->adj_h,      c->adj_h2,     c->adj_gws,   c->scan_aux,   c->d_bar,
                     c->step_cell_start, c->d_sdf_pend, c->stage_in, c->lr_mat, c->d_mu, c->d_cfl, c->lr_body, c->lr_xo, c->body_members,
                     c->body_start, c->body_xf, c->lr_slot, c->hr_bin_start, c->hr_big, c->hr_scan_aux,
                     c->async_in[0], c->async_in[1], c->async_in[2], c->async_in[3],
@@ -2245,7 +2245,8 @@ static int ensure_adjoint_buffers(gs_ctx* c)
     const int64_t N = c->n_low;
     if (c->adj_gx) return GS_OK;
     bool ok = dalloc(&c->adj_gx, N) == cudaSuccess && dalloc(&c->adj_gxt, N) == cudaSuccess &&
-              dalloc(&c->adj_h, N) == cudaSuccess && dalloc(&c->adj_gws, N) == cudaSuccess &&
+              dalloc(&c->adj_h, N) == cudaSuccess && dalloc(&c->adj_h2, N) == cudaSuccess &&
+              dalloc(&c->adj_gws, N) == cudaSuccess &&
               dalloc(&c->adj_io, (size_t)4 * N) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -2495,6 +2496,13 @@ static int step_low_reverse_from(gs_ctx* c, float dt, int iters, const float4* X
     CK(gs_launch_adj_init(c->stream, N, idx, c->adj_io, c->adj_io + N, dt, c->adj_gx, c->adj_gxt, c->adj_gws,
                           &c->launches),
        "reverse init");
+    float4* Hb[2] = {c->adj_h, c->adj_h2};
+    int hc = 0;
+    auto y_of = [&](int it) { return it < c->n_stab ? x_before(it) : XT + (size_t)it * N; };
+    if (total > 0)
+        CK(gs_launch_adj_h(c->stream, a, (total - 1) < c->n_stab, y_of(total - 1), ws, nbr, cnt, c->adj_gx, c->adj_gxt,
+                           Hb[0], &c->launches),
+           "reverse h");
     for (int it = total - 1; it >= 0; --it) {
         const int stab = it < c->n_stab;
         AdjRecord rec;
@@ -2507,9 +2515,11 @@ static int step_low_reverse_from(gs_ctx* c, float dt, int iters, const float4* X
             rec.cap = c->nbr_cap;
             rec.n_comp = n_comp;
         }
-        CK(gs_launch_adj_pass(c->stream, a, stab, stab ? x_before(it) : XT + (size_t)it * N, XT + (size_t)it * N,
-                              xfix, ws, nbr, cnt, c->adj_h, c->adj_gx, c->adj_gxt, c->adj_gws, &c->launches, rec),
+        CK(gs_launch_adj_pass(c->stream, a, stab, y_of(it), XT + (size_t)it * N, xfix, ws, nbr, cnt, Hb[hc],
+                              c->adj_gx, c->adj_gxt, c->adj_gws, &c->launches, rec, it > 0 ? y_of(it - 1) : nullptr,
+                              (it - 1) < c->n_stab, Hb[hc ^ 1]),
            "reverse pass");
+        hc ^= 1;
     }
     CK(gs_launch_adj_final(c->stream, a, idx, ws, c->adj_gx, c->adj_gxt, c->adj_gws, c->adj_io + 2 * N,
                            c->adj_io + 3 * N, &c->launches),

@@ -243,6 +243,7 @@ struct gs_ctx {
     float4* adj_gx = nullptr;
     float4* adj_gxt = nullptr;
     float4* adj_h = nullptr;
+    float4* adj_h2 = nullptr;      // the next pass's h (the reverse passes alternate the two)
     float* adj_gws = nullptr;
     float4* adj_io = nullptr;      // [4][n_low]: dL/dx_out, dL/dv_out in; dL/dx_in, dL/dv_in out (original order)
     float4* fscratch = nullptr;    // [6][n_high] + [2][n_low]: the functional upsampling entries' in/out copies
@@ -487,10 +488,18 @@ cudaError_t gs_launch_scatter2(cudaStream_t s, const uint32_t* idx, const float4
                                float4* bo, int64_t n, int64_t* launches);
 cudaError_t gs_launch_adj_init(cudaStream_t s, int64_t n, const uint32_t* idx, const float4* gxo, const float4* gvo,
                                float dt, float4* gx, float4* gxt, float* gws, int64_t* launches);
+// h = upstream / n per particle for one pass (the first pass to reverse).
+cudaError_t gs_launch_adj_h(cudaStream_t s, const PbdArgs& a, int stab, const float4* Y, const float4* WS,
+                            const uint32_t* nbr, const uint32_t* cnt, const float4* gx, const float4* gxt, float4* H,
+                            int64_t* launches);
+// The reverse of one pass from its h (H); with Y_next the h of the pass
+// before it (evaluated on Y_next, a stabilization pass when stab_next) into
+// H_next, from the gradients this pass leaves.
 cudaError_t gs_launch_adj_pass(cudaStream_t s, const PbdArgs& a, int stab, const float4* Y, const float4* XT,
-                               const float4* XF, const float4* WS, const uint32_t* nbr, const uint32_t* cnt, float4* H,
-                               float4* gx, float4* gxt, float* gws, int64_t* launches,
-                               const AdjRecord& rec = AdjRecord{});
+                               const float4* XF, const float4* WS, const uint32_t* nbr, const uint32_t* cnt,
+                               const float4* H, float4* gx, float4* gxt, float* gws, int64_t* launches,
+                               const AdjRecord& rec = AdjRecord{}, const float4* Y_next = nullptr,
+                               int stab_next = 0, float4* H_next = nullptr);
 cudaError_t gs_launch_adj_final(cudaStream_t s, const PbdArgs& a, const uint32_t* idx, const float4* WS,
                                 const float4* gx, const float4* gxt, const float* gws, float4* gx0, float4* gv0,
                                 int64_t* launches);

@@ -502,3 +502,20 @@ def test_native_rollout_equals_the_torch_driven_rollout(frames, every, n_sub):
     with pytest.raises(RuntimeError):
         o1[2].sum().backward()
     g.close()
+
+
+def test_native_rollout_of_zero_frames_is_the_identity():
+    import torch
+
+    import paper_2308_01629_gb300 as gs
+    from paper_2308_01629_gb300.diff import rollout
+    sc = scenes.column(n_low=400, ratio=8)
+    g = gs.Context(sc, stream="torch")
+    ins = [_t(sc[k]).requires_grad_(True) for k in ("lr_pos", "lr_vel", "hr_pos", "hr_vel")]
+    out = rollout(g, *ins, DT, frames=0, n_sub=1, iters=4, checkpoint_every=3)
+    for a, b in zip(out, ins):
+        assert torch.equal(a, b.detach())
+    sum(o[:, :3].sum() for o in out).backward()
+    for t in ins:
+        assert torch.equal(t.grad[:, :3], torch.ones_like(t.grad[:, :3]))
+    g.close()

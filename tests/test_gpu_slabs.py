@@ -162,3 +162,32 @@ def test_slab_of_the_whole_set_and_empty_slabs():
         np.testing.assert_array_equal(x, y)
     for c in (whole, one, empty):
         c.close()
+
+
+def test_slabs_of_a_batched_context_equal_the_whole_batch():
+    """Slabs are ranges of the warp items of all scenes' HR slots: a batched
+    context split in three equals the whole batch bitwise."""
+    import paper_2308_01629_gb300 as gs
+    sl = scenes.batch(n_scenes=6, lo_count=300, hi_count=1500)
+    whole = gs.Context(sl)
+    parts = [gs.Context(sl) for _ in range(3)]
+    for k, c in enumerate(parts):
+        c.set_hr_slab(k, 3)
+    ranges = [c.hr_slab_range(k, 3) for k, c in enumerate(parts)]
+    for f in range(9):
+        if f == 8:   # the reorder of frame 8 needs every slab
+            pieces = [_internal(gs, c) for c in parts]
+            pos = np.concatenate([pieces[k][0][b:e] for k, (b, e) in enumerate(ranges)])
+            vel = np.concatenate([pieces[k][1][b:e] for k, (b, e) in enumerate(ranges)])
+            for c in parts:
+                c.hr_slab_assemble(pos, vel)
+        for c in [whole] + parts:
+            c.frame(DT, 4, 8)
+    wp, wv = _internal(gs, whole)
+    for k, c in enumerate(parts):
+        b, e = ranges[k]
+        p, v = _internal(gs, c)
+        np.testing.assert_array_equal(p[b:e], wp[b:e])
+        np.testing.assert_array_equal(v[b:e], wv[b:e])
+    for c in [whole] + parts:
+        c.close()

@@ -492,6 +492,12 @@ def run_gpu(args):
                     "note": "each timed frame runs its LR steps on the main stream while the HR frame of the "
                             "previous frame runs on a second stream; K timed frames hold K frames of each"}
         pipe["frame_ms_tried"] = tried
+    # the gather's own time inside the timed frames: events of the library
+    # around its launches, recorded by every replay of the frame graph (not
+    # with pipelined frames, whose gather runs on the library's second stream)
+    gather_live = not pipe["enabled"]
+    if gather_live:
+        ctx.set_gather_timer(True)
     clk = Clocks(local)
     time.sleep(0.3)
     for _ in range(args.warmup):
@@ -500,6 +506,7 @@ def run_gpu(args):
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    gather_ms_live = []
     launches0 = ctx.launches()
     barrier()
     torch.cuda.synchronize(dev)
@@ -509,6 +516,8 @@ def run_gpu(args):
         starts[k].record(stream)
         step(ctx)
         ends[k].record(stream)
+        if gather_live:   # waits for this frame; the next frame's flush and events follow
+            gather_ms_live.append(ctx.gather_timer_ms())
     torch.cuda.synchronize(dev)
     barrier()
     wall = time.perf_counter() - wall0
@@ -715,8 +724,10 @@ def run_gpu(args):
     pk = peaks()
     ncell = int(ctx.grid.n_cell) if hasattr(ctx, "grid") else 0
     alg_bytes = 64 * M + 32 * N + 4 * (ncell + 1)
-    gather_avg_s = gather_ms / max(gather_n, 1) / 1e3
-    achieved = alg_bytes / gather_avg_s / 1e9
+    gather_avg_s = gather_ms / max(gather_n, 1) / 1e3   # breakdown frames, no graphs
+    live_s = float(np.mean(gather_ms_live)) / 1e3 if gather_ms_live else None
+    roof_s = live_s if live_s else gather_avg_s
+    achieved = alg_bytes / roof_s / 1e9
     peak = pk["hbm_gbs"] if pk else 6800.0
     src = open(os.path.join(ROOT, "paper_2308_01629_gb300", "csrc", "upsample.cu"), "rb").read()
     sha = hashlib.sha1(src).hexdigest()
@@ -731,7 +742,11 @@ def run_gpu(args):
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_upsample (fused gather + blend + advection + SDF)",
                      "peak_source": "measured" if pk else "fallback",
-                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": gather_avg_s * 1e6,
+                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_us": roof_s * 1e6,
+                     "duration_source": ("CUDA events of the library around the gather's launches inside each "
+                                         "timed frame (graph event nodes)") if live_s else
+                                        "library event timers in frames after the timed region (no graphs)",
+                     "avg_launch_us_breakdown_frames": gather_avg_s * 1e6,
                      # from the same capture as traffic: the gather is bound by instruction
                      # issue on the CUDA cores, not by DRAM
                      "ncu": ({k: TRAFFIC_CAPTURE[k] for k in ("dram_throughput_pct", "sm_throughput_pct",
@@ -744,7 +759,7 @@ def run_gpu(args):
         "timed_region": "one CUDA-graph launch per frame (bucket pose copied before it)",
         "upsample_tuning": {"warps_per_block": tune_w, "blocks_per_sm": tune_b, "autotune_us": tune_us},
         "pipeline": pipe,
-        "upsample_kernel_hr_per_s": M / gather_avg_s,
+        "upsample_kernel_hr_per_s": M / roof_s,
         "wall_s_timed_region": wall,
         "l2_write_only_flush": {"ms_per_step": dirty_ms / args.steps,
                                 "value": whole_job_rate(M * args.steps, world, dirty_ms / 1e3),

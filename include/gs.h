@@ -449,6 +449,15 @@ int gs_set_pipeline(gs_ctx* ctx, int enable, int warps_per_block, int blocks_per
  * (gs_step_low_forward / _backward), which keep every pass's input. */
 int gs_set_lr_solver(gs_ctx* ctx, int persistent);
 
+/* A timer around the upsampling gather inside whole frames: with it on,
+ * two CUDA events of the context bracket the gather's launches of every HR
+ * frame (in captured frames as event nodes of the graph, so every replay
+ * records them), and gs_gather_timer_ms returns the time between them for
+ * the latest frame (it waits for that frame).  Turning it on or off drops
+ * the captured frames.  GS_ERR_STATE when it is off. */
+int gs_set_gather_timer(gs_ctx* ctx, int enable);
+int gs_gather_timer_ms(gs_ctx* ctx, float* ms);
+
 /* Launch shape of the upsampling kernel: warps per block (4, 8 or 16) and
  * blocks per SM of a persistent grid that pulls 32-particle work items from
  * an atomic counter (0: one warp per item, no persistent loop). */

@@ -116,6 +116,8 @@ _SIGS = {
                                         ctypes.POINTER(ctypes.c_int64)]),
     "gs_set_hr_slab": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "gs_set_step_tapes": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gs_set_gather_timer": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gs_gather_timer_ms": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
     "gs_step_low_forward_taped": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int, ctypes.c_int64]),
     "gs_step_low_backward_taped": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, _P]),
     "gs_rollout_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int, ctypes.c_int,
@@ -347,6 +349,17 @@ def gs_hr_slab_range(n_slots, part, n_parts):
     b, e = ctypes.c_int64(), ctypes.c_int64()
     rc = lib().gs_hr_slab_range(int(n_slots), int(part), int(n_parts), ctypes.byref(b), ctypes.byref(e))
     return rc, b.value, e.value
+
+
+def gs_set_gather_timer(ctx, enable):
+    return lib().gs_set_gather_timer(ctx, int(enable))
+
+
+def gs_gather_timer_ms(ctx):
+    """(status, ms of the latest frame's gather)."""
+    ms = ctypes.c_float()
+    rc = lib().gs_gather_timer_ms(ctx, ctypes.byref(ms))
+    return rc, ms.value
 
 
 def gs_set_step_tapes(ctx, n_slots):
@@ -624,6 +637,16 @@ class Context:
 
     def set_pipeline(self, enable=True, warps_per_block=8, blocks_per_sm=1):
         return _check(self.ctx, gs_set_pipeline(self.ctx, enable, warps_per_block, blocks_per_sm), "gs_set_pipeline")
+
+    def set_gather_timer(self, enable=True):
+        """Events around the gather of every HR frame (graph replays too)."""
+        return _check(self.ctx, gs_set_gather_timer(self.ctx, enable), "gs_set_gather_timer")
+
+    def gather_timer_ms(self):
+        """The latest frame's gather time (waits for that frame)."""
+        rc, ms = gs_gather_timer_ms(self.ctx)
+        _check(self.ctx, rc, "gs_gather_timer_ms")
+        return ms
 
     def set_step_tapes(self, n_slots):
         """Keep the recorded passes of the latest n_slots taped LR steps for

@@ -616,6 +616,18 @@ UpsampleArgs upsample_args(const gs_ctx* c, float dt, const float4* in_pos, cons
     return u;
 }
 
+// Records gather timer event k on the main stream: inside a stream capture
+// as an event record node of the graph, so that every replay records it.
+cudaError_t record_gather_event(gs_ctx* c, int k)
+{
+    if (!c->ev_gather[k]) return cudaSuccess;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(c->stream, &cs);
+    if (e != cudaSuccess) return e;
+    return cudaEventRecordWithFlags(c->ev_gather[k], c->stream,
+                                    cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u);
+}
+
 // The HR frame: reorder when due, bin LR, gather in place.
 int upsample_impl(gs_ctx* c, float dt)
 {
@@ -638,8 +650,10 @@ int upsample_impl(gs_ctx* c, float dt)
     }
     {
         Timed t(c, GS_TIMER_GATHER);
+        CK(record_gather_event(c, 0), "gather timer");
         CK(gs_launch_upsample(c->stream, u, c->tune_warps, c->tune_blocks_per_sm, c->sm_count, &c->launches),
            "upsample");
+        CK(record_gather_event(c, 1), "gather timer");
     }
     c->frame++;
     return GS_OK;
@@ -1160,6 +1174,8 @@ void gs_destroy(gs_ctx* c)
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     if (c->stream_hr) cudaStreamDestroy(c->stream_hr);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    for (cudaEvent_t e : c->ev_gather)
+        if (e) cudaEventDestroy(e);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->stream_h2d) cudaStreamDestroy(c->stream_h2d);
     if (c->stream_d2h) cudaStreamDestroy(c->stream_d2h);
@@ -1915,6 +1931,37 @@ int gs_set_lr_solver(gs_ctx* c, int persistent)
     c->use_solver = persistent != 0;
     c->solver_selftest = persistent == 2;
     drop_graphs(c);
+    return GS_OK;
+}
+
+int gs_set_gather_timer(gs_ctx* c, int enable)
+{
+    int st = check_state(c);
+    if (st) return st;
+    st = settle(c);
+    if (st) return st;
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    drop_graphs(c);   // captured frames hold the event nodes (or lack them)
+    for (auto& e : c->ev_gather)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
+    if (enable)
+        for (auto& e : c->ev_gather) CK(cudaEventCreate(&e), "create timer event");
+    return GS_OK;
+}
+
+int gs_gather_timer_ms(gs_ctx* c, float* ms)
+{
+    int st = check_state(c);
+    if (st) return st;
+    if (!ms) return fail(c, GS_ERR_ARG, "null output");
+    if (!c->ev_gather[0]) return fail(c, GS_ERR_STATE, "the gather timer is off");
+    st = settle(c);
+    if (st) return st;
+    CK(cudaEventSynchronize(c->ev_gather[1]), "synchronize");
+    CK(cudaEventElapsedTime(ms, c->ev_gather[0], c->ev_gather[1]), "elapsed time");
     return GS_OK;
 }
 

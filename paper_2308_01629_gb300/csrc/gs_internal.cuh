@@ -92,6 +92,9 @@ struct gs_ctx {
     // LR steps of frame f + 1 run on stream (fork / join by events)
     cudaStream_t stream_hr = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // gs_set_gather_timer: events around the gather launches, recorded by
+    // direct frames and by every replay of captured frames
+    cudaEvent_t ev_gather[2] = {nullptr, nullptr};
     bool pipeline = false;
     int pipe_warps = 8, pipe_blocks_per_sm = 1;   // gather launch shape while it overlaps the LR steps
     bool pending = false;        // an HR frame is deferred

@@ -123,3 +123,29 @@ def test_several_frames_with_reorders_match_unordered(orc):
     xb, vb = _run(sc, frames=9, resort_every=0)
     np.testing.assert_array_equal(xa[:, 3], xb[:, 3])
     assert np.abs(xa[:, :3] - xb[:, :3]).max() < 1e-5
+
+
+def test_gather_timer_in_graph_replayed_frames():
+    """The gather timer records inside replayed frame graphs: a positive time
+    for every frame, below the whole frame's."""
+    import torch
+
+    import paper_2308_01629_gb300 as gs
+    sc = scenes.cube(n_side=10)
+    s = torch.cuda.Stream()
+    ctx = gs.Context(sc, stream=s.cuda_stream)
+    assert gs.gs_gather_timer_ms(ctx.ctx)[0] == gs.GS_ERR_STATE
+    ctx.set_gather_timer(True)
+    ctx.set_graphs(True)
+    for f in range(4):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        ctx.frame(1 / 60, 4, 4)
+        b.record(s)
+        g = ctx.gather_timer_ms()
+        b.synchronize()
+        assert 0.0 < g < a.elapsed_time(b)
+    ctx.set_gather_timer(False)
+    ctx.frame(1 / 60, 4, 4)
+    ctx.sync()
+    ctx.close()

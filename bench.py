@@ -359,6 +359,9 @@ def run_diff(args, dev, stream, gs, torch, reps=None, warm=2, with_plain=True):
         ms_diff = timed(diff_rollout)
         nl = (ctx.launches() - l0) / (k + warm)
         ms_torch = timed(lambda: diff_rollout(native=False)) if with_plain else None
+        ctx.set_deterministic_backward(True)
+        ms_det = timed(diff_rollout) if with_plain else None
+        ctx.set_deterministic_backward(False)
         plain.close()
         ctx.close()
     return {"workload": f"falling column {len(sc['lr_pos'])} LR / {M} HR, {F} steps of {dt:.6f} s, "
@@ -368,7 +371,8 @@ def run_diff(args, dev, stream, gs, torch, reps=None, warm=2, with_plain=True):
             "backward_overhead_vs_plain_forward": ms_diff / ms_plain if ms_plain else None,
             "library_kernels_per_rollout": nl,
             "rollout": "run by the library (gs_rollout_forward / _backward, one CUDA graph each)",
-            "torch_driven_forward_backward_ms_per_rollout": ms_torch}
+            "torch_driven_forward_backward_ms_per_rollout": ms_torch,
+            "deterministic_backward_ms_per_rollout": ms_det}
 
 
 def run_diff_only(args):

@@ -449,6 +449,16 @@ int gs_set_pipeline(gs_ctx* ctx, int enable, int warps_per_block, int blocks_per
  * (gs_step_low_forward / _backward), which keep every pass's input. */
 int gs_set_lr_solver(gs_ctx* ctx, int persistent);
 
+/* The HR frame's reverse mode (gs_upsample_backward and the rollouts) adds
+ * the LR gradients either by float atomics from every HR particle (the
+ * default; their order, and so the last bits of the sums, vary from run to
+ * run) or (1) deterministically: every HR particle's coefficients first, the
+ * HR particles binned by the LR cells, then one warp per LR particle
+ * gathering the terms of the HR particles in the 27 cells around it in a
+ * fixed order, so gradients are the same bits on every run (about 50 us
+ * more per call for 4k LR / 64k HR). */
+int gs_set_deterministic_backward(gs_ctx* ctx, int enable);
+
 /* A timer around the upsampling gather inside whole frames: with it on,
  * two CUDA events of the context bracket the gather's launches of every HR
  * frame (in captured frames as event nodes of the graph, so every replay

@@ -117,6 +117,7 @@ _SIGS = {
     "gs_set_hr_slab": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "gs_set_step_tapes": (ctypes.c_int, [_P, ctypes.c_int]),
     "gs_set_gather_timer": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gs_set_deterministic_backward": (ctypes.c_int, [_P, ctypes.c_int]),
     "gs_gather_timer_ms": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float)]),
     "gs_step_low_forward_taped": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int, ctypes.c_int64]),
     "gs_step_low_backward_taped": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, _P]),
@@ -349,6 +350,10 @@ def gs_hr_slab_range(n_slots, part, n_parts):
     b, e = ctypes.c_int64(), ctypes.c_int64()
     rc = lib().gs_hr_slab_range(int(n_slots), int(part), int(n_parts), ctypes.byref(b), ctypes.byref(e))
     return rc, b.value, e.value
+
+
+def gs_set_deterministic_backward(ctx, enable):
+    return lib().gs_set_deterministic_backward(ctx, int(enable))
 
 
 def gs_set_gather_timer(ctx, enable):
@@ -637,6 +642,12 @@ class Context:
 
     def set_pipeline(self, enable=True, warps_per_block=8, blocks_per_sm=1):
         return _check(self.ctx, gs_set_pipeline(self.ctx, enable, warps_per_block, blocks_per_sm), "gs_set_pipeline")
+
+    def set_deterministic_backward(self, enable=True):
+        """LR gradients of the HR frame's reverse mode gathered in a fixed
+        order (bitwise reproducible) or added by float atomics (the
+        default)."""
+        return _check(self.ctx, gs_set_deterministic_backward(self.ctx, enable), "gs_set_deterministic_backward")
 
     def set_gather_timer(self, enable=True):
         """Events around the gather of every HR frame (graph replays too)."""

@@ -48,16 +48,22 @@ __global__ void k_upsample_bwd(const SceneDev* __restrict__ scenes, const gs_sdf
                                const float4* __restrict__ hv, const float4* __restrict__ gxo,
                                const float4* __restrict__ gvo, float4* __restrict__ ghx, float4* __restrict__ ghv,
                                float4* __restrict__ gXs, float4* __restrict__ gVs, int64_t m, float dt,
-                               uint32_t* __restrict__ rec, const uint32_t* __restrict__ lr_idx)
+                               uint32_t* __restrict__ rec, const uint32_t* __restrict__ lr_idx,
+                               float4* __restrict__ coef, const uint32_t* __restrict__ order,
+                               float4* __restrict__ pos_sorted)
 {
     // kBwdLanes lanes per HR particle: lane `sub` takes the LR candidates
     // sub, sub + kBwdLanes, ... of every row of cells; the lanes' partial
     // sums meet in shuffles, and each lane pushes its own candidates'
-    // gradients.  Every lane stays until the last shuffle.
+    // gradients.  Every lane stays until the last shuffle.  With coef: the
+    // particles are taken in the order `order` (slot -> particle), and the
+    // coefficients and the position go to the slot (coef[2 slot ..],
+    // pos_sorted[slot]) instead of any atomic.
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t i = t / kBwdLanes;
+    const int64_t slot = t / kBwdLanes;
     const int sub = (int)(t % kBwdLanes);
-    const bool live = i < m;
+    const bool live = slot < m;
+    const int64_t i = (order && live) ? (int64_t)order[slot] : slot;
     const SceneDev& sc = scenes[0];
     const GridDev& g = sc.g;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -196,9 +202,10 @@ __global__ void k_upsample_bwd(const SceneDev* __restrict__ scenes, const gs_sdf
                     const float4 qv = lr_svel[j];
                     const float gwj = gS + gVx * qv.x + gVy * qv.y + gVz * qv.z + (j == jstar ? gwmax : 0.0f);
                     const float k6 = gwj * 6.0f * t * t * inv9r2;
-                    // one vector reduction per gradient (global float4 atomics, sm_90 and later)
-                    atomicAdd(gXs + j, make_float4(k6 * dx, k6 * dy, k6 * dz, 0.0f));
-                    atomicAdd(gVs + j, make_float4(w * gVx, w * gVy, w * gVz, 0.0f));
+                    if (!coef) {   // one vector reduction per gradient (global float4 atomics, sm_90 and later)
+                        atomicAdd(gXs + j, make_float4(k6 * dx, k6 * dy, k6 * dz, 0.0f));
+                        atomicAdd(gVs + j, make_float4(w * gVx, w * gVy, w * gVz, 0.0f));
+                    }
                     gpx -= k6 * dx;
                     gpy -= k6 * dy;
                     gpz -= k6 * dz;
@@ -212,6 +219,109 @@ __global__ void k_upsample_bwd(const SceneDev* __restrict__ scenes, const gs_sdf
         gpz += __shfl_xor_sync(0xffffffffu, gpz, o);
     }
     if (live && sub == 0) ghx[i] = make_float4(gpx, gpy, gpz, 0.0f);
+    if (coef && live && sub == 0) {
+        // the particle's coefficients for the LR side's gather (k_upsample_bwd_lr)
+        float4 c0 = make_float4(0.f, 0.f, 0.f, 0.f), c1 = make_float4(0.f, __uint_as_float(0xffffffffu), 0.f, 0.f);
+        if (S > 0.0f) {
+            c0 = make_float4(-(gvtx * vtx + gvty * vty + gvtz * vtz) / S, gvtx / S, gvty / S, gvtz / S);
+            c1 = make_float4(gwmax, __uint_as_float(jstar), 0.f, 0.f);
+        }
+        coef[2 * slot] = c0;
+        coef[2 * slot + 1] = c1;
+        pos_sorted[slot] = p;
+    }
+}
+
+// The LR side of the HR frame's reverse mode without atomics: one warp per
+// cell-ordered LR slot j gathers over the HR particles of the 27 cells around
+// its own (HR binned by the same cells: hr_cell_start, positions and
+// coefficients in that order: hx_sorted, coef) the terms
+// k_upsample_bwd would add to slot j, from every HR particle's coefficients
+// (gS, gV, max-w gradient, largest-weight slot), lanes over the HR
+// candidates and a fixed shuffle tree for the sums: the same result on every
+// run.
+__global__ void __launch_bounds__(128) k_upsample_bwd_lr(const SceneDev* __restrict__ scenes,
+                                                         const float4* __restrict__ lr_spos,
+                                                         const float4* __restrict__ lr_svel,
+                                                         const uint32_t* __restrict__ lr_skeys,
+                                                         const float4* __restrict__ hx_sorted,
+                                                         const uint32_t* __restrict__ hr_cell_start,
+                                                         const float4* __restrict__ coef, float4* __restrict__ gXs,
+                                                         float4* __restrict__ gVs, int64_t n_low)
+{
+    const int lane = (int)(threadIdx.x & 31u);
+    const int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= n_low) return;   // whole warps
+    const SceneDev& sc = scenes[0];
+    const GridDev& g = sc.g;
+    const uint32_t c = lr_skeys[j] - sc.cell_off;
+    const int cx = (int)(c % (uint32_t)g.dx);
+    const int cy = (int)((c / (uint32_t)g.dx) % (uint32_t)g.dy);
+    const int cz = (int)(c / ((uint32_t)g.dx * (uint32_t)g.dy));
+    const int x0 = cx > 0 ? cx - 1 : 0, x1 = cx + 1 < g.dx ? cx + 1 : g.dx - 1;
+    const float R = 3.0f * sc.r_low;
+    const float R2 = R * R;
+    const float inv9r2 = 1.0f / R2;
+    const float4 q = lr_spos[j], qv = lr_svel[j];
+    // lane r < 9: row r = (z, y) of the 3 x 3 rows around the cell
+    uint32_t rb = 0, len = 0;
+    if (lane < 9) {
+        const int z = cz - 1 + lane / 3, y = cy - 1 + lane % 3;
+        if (z >= 0 && z < g.dz && y >= 0 && y < g.dy) {
+            const int64_t row = (int64_t)sc.cell_off + ((int64_t)z * g.dy + y) * g.dx;
+            rb = hr_cell_start[row + x0];
+            len = hr_cell_start[row + x1 + 1] - rb;
+        }
+    }
+    uint32_t incl = len;
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t excl = incl - len;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 8);
+    float ax = 0.f, ay = 0.f, az = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t f = base + (uint32_t)lane;
+        int r = 0;   // the row of flat index f
+#pragma unroll
+        for (int step = 8; step > 0; step >>= 1) {
+            const uint32_t e = __shfl_sync(0xffffffffu, excl, (r + step) & 31);
+            if (r + step < 9 && e <= f) r += step;
+        }
+        const uint32_t slot = __shfl_sync(0xffffffffu, rb, r) + (f - __shfl_sync(0xffffffffu, excl, r));
+        if (f >= total) continue;
+        const float4 p = hx_sorted[slot];
+        const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+        const float d2 = dx * dx + dy * dy + dz * dz;
+        if (!(d2 < R2)) continue;
+        const float4 c0 = coef[2 * (int64_t)slot], c1 = coef[2 * (int64_t)slot + 1];
+        const float t = 1.0f - d2 * inv9r2;
+        const float w = t * t * t;
+        const float gwj = c0.x + c0.y * qv.x + c0.z * qv.y + c0.w * qv.z +
+                          (__float_as_uint(c1.y) == (uint32_t)j ? c1.x : 0.0f);
+        const float k6 = gwj * 6.0f * t * t * inv9r2;
+        ax += k6 * dx;
+        ay += k6 * dy;
+        az += k6 * dz;
+        bx += w * c0.y;
+        by += w * c0.z;
+        bz += w * c0.w;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        az += __shfl_xor_sync(0xffffffffu, az, o);
+        bx += __shfl_xor_sync(0xffffffffu, bx, o);
+        by += __shfl_xor_sync(0xffffffffu, by, o);
+        bz += __shfl_xor_sync(0xffffffffu, bz, o);
+    }
+    if (lane == 0) {
+        gXs[j] = make_float4(ax, ay, az, 0.0f);
+        gVs[j] = make_float4(bx, by, bz, 0.0f);
+    }
 }
 
 // out[idx[p]] = in[p] for both arrays
@@ -601,11 +711,23 @@ cudaError_t gs_launch_upsample_bwd(cudaStream_t s, const SceneDev* scenes, const
                                    const float4* lr_svel, const uint32_t* cell_start, const float4* hx,
                                    const float4* hv, const float4* gxo, const float4* gvo, float4* ghx, float4* ghv,
                                    float4* gXs, float4* gVs, int64_t m, float dt, int64_t* launches, uint32_t* rec,
-                                   const uint32_t* lr_idx)
+                                   const uint32_t* lr_idx, float4* coef, const uint32_t* order, float4* pos_sorted)
 {
     if (m <= 0) return cudaSuccess;
     k_upsample_bwd<<<gs_blocks(m * kBwdLanes, 128), 128, 0, s>>>(scenes, sdf, lr_spos, lr_svel, cell_start, hx, hv, gxo, gvo, ghx,
-                                                      ghv, gXs, gVs, m, dt, rec, lr_idx);
+                                                      ghv, gXs, gVs, m, dt, rec, lr_idx, coef, order, pos_sorted);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t gs_launch_upsample_bwd_lr(cudaStream_t s, const SceneDev* scenes, const float4* lr_spos,
+                                      const float4* lr_svel, const uint32_t* lr_skeys, const float4* hx_sorted,
+                                      const uint32_t* hr_cell_start, const float4* coef, float4* gXs, float4* gVs,
+                                      int64_t n_low, int64_t* launches)
+{
+    if (n_low <= 0) return cudaSuccess;
+    k_upsample_bwd_lr<<<gs_blocks(n_low * 32, 128), 128, 0, s>>>(scenes, lr_spos, lr_svel, lr_skeys, hx_sorted,
+                                                                  hr_cell_start, coef, gXs, gVs, n_low);
     *launches += 1;
     return cudaGetLastError();
 }

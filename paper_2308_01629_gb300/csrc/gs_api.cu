@@ -1170,6 +1170,8 @@ void gs_destroy(gs_ctx* c)
     if (c->ro_ckpt) cudaFree(c->ro_ckpt);
     if (c->ro_work) cudaFree(c->ro_work);
     if (c->ro_io) cudaFree(c->ro_io);
+    if (c->det_coef) cudaFree(c->det_coef);
+    if (c->det_big) cudaFree(c->det_big);
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     if (c->stream_hr) cudaStreamDestroy(c->stream_hr);
@@ -1934,6 +1936,17 @@ int gs_set_lr_solver(gs_ctx* c, int persistent)
     return GS_OK;
 }
 
+int gs_set_deterministic_backward(gs_ctx* c, int enable)
+{
+    int st = check_state(c);
+    if (st) return st;
+    st = settle(c);
+    if (st) return st;
+    c->det_bwd = enable != 0;
+    drop_graphs(c);
+    return GS_OK;
+}
+
 int gs_set_gather_timer(gs_ctx* c, int enable)
 {
     int st = check_state(c);
@@ -2030,8 +2043,12 @@ int gs_autotune(gs_ctx* c, float dt, int reps, int* warps_per_block, int* blocks
 static int ensure_fscratch(gs_ctx* c)
 {
     if (c->fscratch) return GS_OK;
-    if (dalloc(&c->fscratch, (size_t)(6 * c->n_high + 2 * c->n_low)) != cudaSuccess) {
+    if (dalloc(&c->fscratch, (size_t)(6 * c->n_high + 2 * c->n_low)) != cudaSuccess ||
+        dalloc(&c->det_coef, (size_t)(3 * c->n_high)) != cudaSuccess ||
+        dalloc(&c->det_big, (size_t)(c->n_high / 33 + 2)) != cudaSuccess) {
         cudaGetLastError();
+        if (c->fscratch) cudaFree(c->fscratch);
+        c->fscratch = nullptr;
         return fail(c, GS_ERR_OOM, "no memory for the functional frame's buffers");
     }
     return GS_OK;
@@ -2113,16 +2130,41 @@ static int upsample_bwd_seq(gs_ctx* c, float dt)
     float4* G = F + 6 * M;
     int st = flag_solid(c, (const float*)c->lr_pos, N);
     if (st) return st;
-    if (N) {
+    if (N && !c->det_bwd) {
         CK(cudaMemsetAsync(c->gXs, 0, N * sizeof(float4), c->stream), "clear");
         CK(cudaMemsetAsync(c->gVs, 0, N * sizeof(float4), c->stream), "clear");
     }
     st = bin_low_impl(c);
     if (st) return st;
+    if (c->det_bwd) {   // HR binned by the LR cells, for the LR side's gather
+        // (its cells hold dozens of HR particles: ordered over the whole grid
+        // from a list, as the HR reorder's fine cells of more than 32)
+        uint32_t* big_count = c->det_big + M / 33 + 1;
+        CK(gs_cs_clear(c->stream, c->step_cell_start, c->n_cell_total), "clear counts");
+        CK(cudaMemsetAsync(big_count, 0, sizeof(uint32_t), c->stream), "clear list");
+        CK(gs_cs_keys(c->stream, F, M, c->d_scenes, c->hr_scene, c->hr_keys[0], c->hr_vals[0], c->step_cell_start,
+                      &c->launches),
+           "HR cell keys");
+        CsExtras ex;
+        ex.big_list = c->det_big;
+        ex.big_count = big_count;
+        ex.big_scratch = c->hr_vals[0];   // the ranks are dead once scattered
+        ex.big_bits = gs_key_bits(M);
+        ex.big_blocks = std::max(c->sm_count, 1);
+        CK(gs_cs_finish(c->stream, M, c->n_cell_total, c->hr_keys[0], c->hr_vals[0], c->hr_keys[1], c->hr_vals[1],
+                        c->step_cell_start, c->scan_aux, nullptr, nullptr, nullptr, nullptr, &c->launches, ex),
+           "bin HR by LR cell");
+    }
     CK(gs_launch_upsample_bwd(c->stream, c->d_scenes, c->d_sdf, c->lr_spos, c->lr_svel, c->lr_cell_start, F, F + M,
                               F + 2 * M, F + 3 * M, F + 4 * M, F + 5 * M, c->gXs, c->gVs, M, dt, &c->launches,
-                              c->rec_hr, c->lr_sorted_idx),
+                              c->rec_hr, c->lr_sorted_idx, c->det_bwd ? c->det_coef : nullptr,
+                              c->det_bwd ? c->hr_vals[1] : nullptr, c->det_bwd ? c->det_coef + 2 * M : nullptr),
        "upsample backward");
+    if (c->det_bwd)
+        CK(gs_launch_upsample_bwd_lr(c->stream, c->d_scenes, c->lr_spos, c->lr_svel, c->lr_sorted_keys,
+                                     c->det_coef + 2 * M, c->step_cell_start, c->det_coef, c->gXs, c->gVs, N,
+                                     &c->launches),
+           "upsample backward, LR side");
     CK(gs_launch_scatter2(c->stream, c->lr_sorted_idx, c->gXs, c->gVs, G, G + N, N, &c->launches), "scatter");
     return GS_OK;
 }

@@ -247,6 +247,10 @@ struct gs_ctx {
     float4* adj_gxt = nullptr;
     float4* adj_h = nullptr;
     float4* adj_h2 = nullptr;      // the next pass's h (the reverse passes alternate the two)
+    bool det_bwd = false;          // gs_set_deterministic_backward
+    float4* det_coef = nullptr;    // [3 n_high] the HR particles' coefficients and positions in cell order
+                                   // (deterministic backward)
+    uint32_t* det_big = nullptr;   // its HR binning's list of cells of more than 32, then their count
     float* adj_gws = nullptr;
     float4* adj_io = nullptr;      // [4][n_low]: dL/dx_out, dL/dv_out in; dL/dx_in, dL/dv_in out (original order)
     float4* fscratch = nullptr;    // [6][n_high] + [2][n_low]: the functional upsampling entries' in/out copies
@@ -475,7 +479,19 @@ cudaError_t gs_launch_upsample_bwd(cudaStream_t s, const SceneDev* scenes, const
                                    const float4* lr_svel, const uint32_t* cell_start, const float4* hx,
                                    const float4* hv, const float4* gxo, const float4* gvo, float4* ghx, float4* ghv,
                                    float4* gXs, float4* gVs, int64_t m, float dt, int64_t* launches,
-                                   uint32_t* rec = nullptr, const uint32_t* lr_idx = nullptr);
+                                   uint32_t* rec = nullptr, const uint32_t* lr_idx = nullptr,
+                                   float4* coef = nullptr, const uint32_t* order = nullptr,
+                                   float4* pos_sorted = nullptr);
+// coef (not null): instead of adding into gXs / gVs, the HR particles are
+// taken in the order `order` (slot -> particle: HR binned by the LR cells)
+// and every one's coefficients go to coef[2 slot ..] and its position to
+// pos_sorted[slot]; k_upsample_bwd_lr then gathers them per LR slot
+// (hr_cell_start: the HR binning's cell starts; lr_skeys: the LR slots'
+// cells).
+cudaError_t gs_launch_upsample_bwd_lr(cudaStream_t s, const SceneDev* scenes, const float4* lr_spos,
+                                      const float4* lr_svel, const uint32_t* lr_skeys, const float4* hx_sorted,
+                                      const uint32_t* hr_cell_start, const float4* coef, float4* gXs, float4* gVs,
+                                      int64_t n_low, int64_t* launches);
 // Decisions of one pass of the LR step's reverse mode, in original particle
 // order (idx: slot -> particle): cand / pair [cap][n], sdf [n][n_comp]
 // (gs_set_decision_record).  All null: nothing is recorded.

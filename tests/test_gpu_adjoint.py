@@ -519,3 +519,48 @@ def test_native_rollout_of_zero_frames_is_the_identity():
     for t in ins:
         assert torch.equal(t.grad[:, :3], torch.ones_like(t.grad[:, :3]))
     g.close()
+
+
+def test_deterministic_hr_backward_repeats_bitwise_and_matches_the_atomic_sums():
+    """The HR frame's reverse mode with the LR side gathered per LR particle
+    gives the same bits on every call, also in a rollout; with float atomics
+    (the default) the LR gradients agree within the rounding of a different
+    summation order."""
+    torch = pytest.importorskip("torch")
+    import paper_2308_01629_gb300 as gs
+    sc = scenes.stir(scenes.column(n_low=2000, ratio=16), seed=5)
+    dev = torch.device("cuda")
+    g = gs.Context(sc, stream="torch")
+    g.set_deterministic_backward(True)
+    X, V, x, v = (torch.from_numpy(np.ascontiguousarray(sc[k])).to(dev) for k in ("lr_pos", "lr_vel", "hr_pos",
+                                                                                     "hr_vel"))
+    gen = torch.Generator(device="cpu").manual_seed(3)
+    gxo = torch.randn(x.shape, generator=gen).to(dev)
+    gvo = torch.randn(v.shape, generator=gen).to(dev)
+
+    def backward():
+        out = [torch.empty_like(t) for t in (X, V, x, v)]
+        assert gs.gs_upsample_backward(g.ctx, X.data_ptr(), V.data_ptr(), x.data_ptr(), v.data_ptr(),
+                                       gxo.data_ptr(), gvo.data_ptr(), *[t.data_ptr() for t in out], DT) == 0
+        torch.cuda.synchronize()
+        return [t.cpu().numpy()[:, :3] for t in out]
+    det = [backward() for _ in range(3)]
+    for r in det[1:]:
+        for a, b in zip(det[0], r):
+            np.testing.assert_array_equal(a, b)
+    g.set_deterministic_backward(False)
+    atom = backward()
+    for a, b in zip(det[0], atom):
+        assert np.abs(a).max() > 0
+        assert _rel(b, a) < 1e-5
+    # a whole rollout's gradient repeats bitwise
+    from paper_2308_01629_gb300.diff import rollout
+    g.set_deterministic_backward(True)
+    grads = []
+    for _ in range(2):
+        Vr = V.clone().requires_grad_(True)
+        out = rollout(g, X, Vr, x, v, DT, frames=4, n_sub=1, iters=4, checkpoint_every=2)
+        (out[2][:, :3] ** 2).sum().backward()
+        grads.append(Vr.grad.cpu().numpy())
+    np.testing.assert_array_equal(grads[0], grads[1])
+    g.close()

@@ -570,7 +570,8 @@ def volume_candidates(V, r, per_cell=6.0, seed=SEED_BASE + 10):
 
 
 def castle_scene(sample, seed=SEED_BASE + 11, size=1.25, height=0.4, r_low=0.02, r_high=0.0075,
-                 boulder_radius=0.1, boulder_velocity=(-3.0, 0.0, -1.0), per_cell=4.0, dt=1.0 / 240.0, iters=8):
+                 boulder_radius=0.1, boulder_velocity=(-3.0, 0.0, -1.0), per_cell=4.0, dt=1.0 / 240.0, iters=8,
+                 boulder=True):
     """The sand-castle scene of Sec. 5 (a rigid body hurled into a castle):
     LR grains and HR particles sampled from the castle mesh, a boulder's LR
     particles sampled from an icosphere (density 5000 kg/m^3, one rigid
@@ -586,7 +587,7 @@ def castle_scene(sample, seed=SEED_BASE + 11, size=1.25, height=0.4, r_low=0.02,
     c = np.array([V[:, 0].max() + 0.3, 0.5 * (V[:, 1].min() + V[:, 1].max()), 0.6 * V[:, 2].max()])
     Vb, Tb = icosphere(c, boulder_radius, 2)
     bd = volume_candidates(Vb, r_low, per_cell, seed + 2)
-    bd = bd[sample(Vb, Tb, bd, r_low)]
+    bd = bd[sample(Vb, Tb, bd, r_low)] if boulder else np.zeros((0, 3))
     m_g = RHO * 4.0 / 3.0 * math.pi * r_low ** 3
     m_b = 5000.0 * 4.0 / 3.0 * math.pi * r_low ** 3
     lr_pos = np.concatenate([_pack(lr, np.float32(1.0 / m_g)), _pack(bd, np.float32(1.0 / m_b))])
@@ -599,10 +600,13 @@ def castle_scene(sample, seed=SEED_BASE + 11, size=1.25, height=0.4, r_low=0.02,
     lo = [0.0, 0.0, 0.0]
     hi = [float(V[:, 0].max() + 1.0), float(V[:, 1].max() + 0.3), float(max(V[:, 2].max(), c[2]) + 0.5)]
     ratio = max(1, int(round(len(hr) / max(len(lr), 1))))
-    return dict(name="castle", seed=seed, box_lo=lo, box_hi=hi, r_low=float(r_low), r_high=float(r_high),
-                ratio=ratio, sdfs=[box_interior(lo, hi)], gravity=GRAVITY, mu_s=MU_S, mu_k=MU_K, dt=float(dt),
-                iters=int(iters), lr_pos=lr_pos, lr_vel=lr_vel, hr_pos=hr_pos,
-                hr_vel=np.zeros((len(hr_pos), 4), np.float32), lr_body=body, n_body=len(bd))
+    sc = dict(name="castle", seed=seed, box_lo=lo, box_hi=hi, r_low=float(r_low), r_high=float(r_high),
+              ratio=ratio, sdfs=[box_interior(lo, hi)], gravity=GRAVITY, mu_s=MU_S, mu_k=MU_K, dt=float(dt),
+              iters=int(iters), lr_pos=lr_pos, lr_vel=lr_vel, hr_pos=hr_pos,
+              hr_vel=np.zeros((len(hr_pos), 4), np.float32), n_body=len(bd))
+    if len(bd):
+        sc["lr_body"] = body
+    return sc
 
 
 def surface_candidates(V, T, r, per_cell=6.0, seed=SEED_BASE + 12):

@@ -42,7 +42,13 @@ def test_cube_without_reorder(orc):
     check_hr(sc, DT, x, v, _ref(orc, sc))
 
 
-@pytest.mark.parametrize("make,nsub", [(scenes.funnel, 20000), (scenes.digging, 20000)])
+def _castle():
+    """The grains of the sand castle seeded by the library's volume sampler."""
+    import paper_2308_01629_gb300 as gs
+    return scenes.castle_scene(gs.sample_volume, boulder=False)
+
+
+@pytest.mark.parametrize("make,nsub", [(scenes.funnel, 20000), (scenes.digging, 20000), (_castle, 20000)])
 def test_full_size_sampled(orc, make, nsub):
     sc = scenes.stir(make(), seed=5, spread=0.2)
     x, v = _run(sc)

@@ -56,8 +56,8 @@ FLUSH_BYTES = 512 << 20
 # DRAM bytes of one upsampling launch on this workload, and its DRAM, SM and
 # issue utilisation, from an ncu capture of the kernel source with this hash
 # (profiles/); reported only while the source is unchanged.
-TRAFFIC_CAPTURE = {"source_sha1": "d7f361215ff7ce22597147ef7dcb626086d713bb", "bytes": 82672640,
-                   "dram_throughput_pct": 6.5, "sm_throughput_pct": 66.3, "issue_active_pct": 69.6}
+TRAFFIC_CAPTURE = {"source_sha1": "3f0cf1c3acdedbfa28b5e3725fbcac7f82d4f92a", "bytes": 84401920,
+                   "dram_throughput_pct": 6.7, "sm_throughput_pct": 59.8, "issue_active_pct": 62.8}
 
 
 class L2Flush:

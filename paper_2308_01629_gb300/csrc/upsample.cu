@@ -31,6 +31,13 @@
 namespace {
 
 constexpr int kBuf = 64;   // staged LR per warp; flushed at >= 32
+// The staged LR set of a warp is eight arrays of kBuf floats (structure of
+// arrays): 2 w_x, 2 w_y, 2 w_z, -|w|^2 (w the LR position relative to the
+// group's centre in units of 3 r_LR), v_x, v_y, v_z, and the solid flag, so
+// the evaluation reads four candidates of a component with one 16-byte load
+// and evaluates them in packed pairs (f32x2 arithmetic).
+enum { kAx = 0, kAy = kBuf, kAz = 2 * kBuf, kAw = 3 * kBuf, kVx = 4 * kBuf, kVy = 5 * kBuf, kVz = 6 * kBuf,
+       kFl = 7 * kBuf, kStage = 8 * kBuf };
 
 __device__ __forceinline__ int cell_coord(float x, float o, float inv_h, int dim)
 {
@@ -97,11 +104,11 @@ __device__ __forceinline__ int sub_floor(float x, float o, float inv_h)
 }
 
 // One warp item: the 32 HR slots [32 item, 32 item + 32) of one scene.
-// sol (kSolid): this warp's 5 x 32 sums of solid particles (S, V, max w per
-// lane), zero on entry and on return.
+// st: this warp's staged LR set (kStage floats).  sol (kSolid): this warp's
+// 5 x 32 sums of solid particles (S, V, max w per lane), zero on entry and on
+// return.
 template <bool kSolid>
-__device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t item, float4* ba, float4* bb,
-                                              float* sol, int lane)
+__device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t item, float* st, float* sol, int lane)
 {
     const int64_t first = item * 32;
     const uint32_t tag = __ldg(a.hr_tag + first);          // the first slot of an item is never padding
@@ -123,7 +130,10 @@ __device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t ite
     const float inv3r = 1.0f / (3.0f * sc.r_low);
     const int64_t coff = sc.cell_off;
 
-    float S = 0.f, Vx = 0.f, Vy = 0.f, Vz = 0.f, wmax = 0.f;   // grains
+    // grains: sums over even and odd staged slots (packed pairs), and the
+    // largest clamped t (max w = tmax^3, the cube being monotone)
+    float2 S2 = make_float2(0.f, 0.f), Vx2 = S2, Vy2 = S2, Vz2 = S2;
+    float tmax = 0.f;
     bool any_solid = false;                                    // warp-uniform
     unsigned pending = __ballot_sync(0xffffffffu, valid);
     while (pending) {
@@ -166,10 +176,18 @@ __device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t ite
 
         int cnt = 0;
         bool batch_solid = false;
+        const float2 u2x = make_float2(ux, ux), u2y = make_float2(uy, uy), u2z = make_float2(uz, uz);
+        const float2 ci2 = make_float2(ci, ci);
         auto stage = [&](int slot, float4 c, float4 cv) {
             const float wx = (c.x - c0x) * inv3r, wy = (c.y - c0y) * inv3r, wz = (c.z - c0z) * inv3r;
-            ba[slot] = make_float4(2.0f * wx, 2.0f * wy, 2.0f * wz, -(wx * wx + wy * wy + wz * wz));
-            bb[slot] = make_float4(cv.x, cv.y, cv.z, kSolid && c.w == 0.0f ? 1.0f : 0.0f);
+            st[kAx + slot] = 2.0f * wx;
+            st[kAy + slot] = 2.0f * wy;
+            st[kAz + slot] = 2.0f * wz;
+            st[kAw + slot] = -(wx * wx + wy * wy + wz * wz);
+            st[kVx + slot] = cv.x;
+            st[kVy + slot] = cv.y;
+            st[kVz + slot] = cv.z;
+            if constexpr (kSolid) st[kFl + slot] = c.w == 0.0f ? 1.0f : 0.0f;
         };
         auto flush = [&](int count, bool with_solid) {
             __syncwarp();
@@ -178,23 +196,22 @@ __device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t ite
                 float s = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, sm = 0.f;
 #pragma unroll 1
                 for (int k = 0; k < count; ++k) {
-                    const float4 ra = ba[k];
-                    const float4 rb = bb[k];
-                    float t = fmaf(ra.x, ux, fmaf(ra.y, uy, fmaf(ra.z, uz, ra.w + ci)));
+                    float t = fmaf(st[kAx + k], ux, fmaf(st[kAy + k], uy, fmaf(st[kAz + k], uz, st[kAw + k] + ci)));
                     t = fmaxf(t, 0.0f);
                     const float w = t * t * t;
-                    if (rb.w != 0.0f) {   // the same k on every lane: uniform
+                    const float vx = st[kVx + k], vy = st[kVy + k], vz = st[kVz + k];
+                    if (st[kFl + k] != 0.0f) {   // the same k on every lane: uniform
                         s += w;
-                        sx = fmaf(w, rb.x, sx);
-                        sy = fmaf(w, rb.y, sy);
-                        sz = fmaf(w, rb.z, sz);
+                        sx = fmaf(w, vx, sx);
+                        sy = fmaf(w, vy, sy);
+                        sz = fmaf(w, vz, sz);
                         sm = fmaxf(sm, w);
                     } else {
-                        S += w;
-                        Vx = fmaf(w, rb.x, Vx);
-                        Vy = fmaf(w, rb.y, Vy);
-                        Vz = fmaf(w, rb.z, Vz);
-                        wmax = fmaxf(wmax, w);
+                        S2.x += w;
+                        Vx2.x = fmaf(w, vx, Vx2.x);
+                        Vy2.x = fmaf(w, vy, Vy2.x);
+                        Vz2.x = fmaf(w, vz, Vz2.x);
+                        tmax = fmaxf(tmax, t);
                     }
                 }
                 sol[lane] += s;
@@ -206,18 +223,52 @@ __device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t ite
                 __syncwarp();
                 return;
             }
-#pragma unroll 4
-            for (int k = 0; k < count; ++k) {
-                const float4 ra = ba[k];
-                const float4 rb = bb[k];
-                float t = fmaf(ra.x, ux, fmaf(ra.y, uy, fmaf(ra.z, uz, ra.w + ci)));
-                t = fmaxf(t, 0.0f);
-                const float w = t * t * t;
-                S += w;
-                Vx = fmaf(w, rb.x, Vx);
-                Vy = fmaf(w, rb.y, Vy);
-                Vz = fmaf(w, rb.z, Vz);
-                wmax = fmaxf(wmax, w);
+            // pad to a multiple of 4 with weightless entries (finite values)
+            const int L = (count + 3) & ~3;
+            if (lane < L - count) {
+                const int k = count + lane;
+                st[kAx + k] = 0.0f;
+                st[kAy + k] = 0.0f;
+                st[kAz + k] = 0.0f;
+                st[kAw + k] = -1.0e30f;
+                st[kVx + k] = 0.0f;
+                st[kVy + k] = 0.0f;
+                st[kVz + k] = 0.0f;
+            }
+            __syncwarp();
+#pragma unroll 1
+            for (int k = 0; k < L; k += 4) {
+                const float4 X = *reinterpret_cast<const float4*>(st + kAx + k);
+                const float4 Y = *reinterpret_cast<const float4*>(st + kAy + k);
+                const float4 Z = *reinterpret_cast<const float4*>(st + kAz + k);
+                const float4 B = *reinterpret_cast<const float4*>(st + kAw + k);
+                // t = (1 - |u|^2) + 2 u . w - |w|^2 for candidates (k, k+1) and (k+2, k+3)
+                float2 t0 = __fadd2_rn(make_float2(B.x, B.y), ci2);
+                float2 t1 = __fadd2_rn(make_float2(B.z, B.w), ci2);
+                t0 = __ffma2_rn(make_float2(Z.x, Z.y), u2z, t0);
+                t1 = __ffma2_rn(make_float2(Z.z, Z.w), u2z, t1);
+                t0 = __ffma2_rn(make_float2(Y.x, Y.y), u2y, t0);
+                t1 = __ffma2_rn(make_float2(Y.z, Y.w), u2y, t1);
+                t0 = __ffma2_rn(make_float2(X.x, X.y), u2x, t0);
+                t1 = __ffma2_rn(make_float2(X.z, X.w), u2x, t1);
+                t0.x = fmaxf(t0.x, 0.0f);
+                t0.y = fmaxf(t0.y, 0.0f);
+                t1.x = fmaxf(t1.x, 0.0f);
+                t1.y = fmaxf(t1.y, 0.0f);
+                tmax = fmaxf(fmaxf(tmax, fmaxf(t0.x, t0.y)), fmaxf(t1.x, t1.y));
+                const float2 w0 = __fmul2_rn(__fmul2_rn(t0, t0), t0);
+                const float2 w1 = __fmul2_rn(__fmul2_rn(t1, t1), t1);
+                const float4 VX = *reinterpret_cast<const float4*>(st + kVx + k);
+                const float4 VY = *reinterpret_cast<const float4*>(st + kVy + k);
+                const float4 VZ = *reinterpret_cast<const float4*>(st + kVz + k);
+                S2 = __fadd2_rn(S2, w0);
+                Vx2 = __ffma2_rn(w0, make_float2(VX.x, VX.y), Vx2);
+                Vy2 = __ffma2_rn(w0, make_float2(VY.x, VY.y), Vy2);
+                Vz2 = __ffma2_rn(w0, make_float2(VZ.x, VZ.y), Vz2);
+                S2 = __fadd2_rn(S2, w1);
+                Vx2 = __ffma2_rn(w1, make_float2(VX.z, VX.w), Vx2);
+                Vy2 = __ffma2_rn(w1, make_float2(VY.z, VY.w), Vy2);
+                Vz2 = __ffma2_rn(w1, make_float2(VZ.z, VZ.w), Vz2);
             }
             __syncwarp();
         };
@@ -276,6 +327,8 @@ __device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t ite
         }
         if (cnt > 0) flush(cnt, batch_solid);
     }
+    float S = S2.x + S2.y, Vx = Vx2.x + Vx2.y, Vy = Vy2.x + Vy2.y, Vz = Vz2.x + Vz2.y;
+    float wmax = tmax * tmax * tmax;
     if (kSolid && any_solid) {
         // the solid particles count only where a grain has a positive weight
         if (S > 0.0f) {
@@ -313,8 +366,7 @@ template <int WARPS, bool kSolid>
 __global__ void __launch_bounds__(WARPS * 32, 24 / WARPS) k_upsample(const UpsampleArgs a, int persistent)
 {
     if ((*a.solid_flag != 0u) != kSolid) return;   // the other instantiation does the frame
-    __shared__ float4 s_a[WARPS][kBuf];
-    __shared__ float4 s_b[WARPS][kBuf];
+    __shared__ __align__(16) float s_st[WARPS][kStage];
     __shared__ float s_sol[kSolid ? WARPS : 1][5 * 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if constexpr (kSolid) {
@@ -347,7 +399,7 @@ __global__ void __launch_bounds__(WARPS * 32, 24 / WARPS) k_upsample(const Upsam
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(a.hr_vel + line));
             }
         }
-        upsample_item<kSolid>(a, a.item_begin + item, s_a[warp], s_b[warp], s_sol[kSolid ? warp : 0], lane);
+        upsample_item<kSolid>(a, a.item_begin + item, s_st[warp], s_sol[kSolid ? warp : 0], lane);
     }
 }
 

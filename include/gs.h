@@ -366,7 +366,9 @@ int gs_sample_volume(const double* vertices, int64_t n_vertices, const int32_t* 
  * grid over the vertices' bounding box and the same cell-by-cell pick as
  * gs_sample_volume, with every candidate valid; the candidates are points
  * on the mesh's triangles (uniform by area, drawn by the caller).  Arguments,
- * outputs and errors as gs_sample_volume. */
+ * outputs and errors as gs_sample_volume; in addition GS_ERR_ARG when a
+ * candidate lies more than 0.15 r outside the vertices' bounding box (one
+ * that far out could be picked closer than 2 r to another). */
 int gs_sample_surface(const double* vertices, int64_t n_vertices, const double* candidates, int64_t n_candidates,
                       double r, int64_t* selected, int64_t capacity, int64_t* n_selected);
 

@@ -177,6 +177,16 @@ static int sample_impl(const double* vertices, int64_t n_vertices, const int32_t
             hi[k] = std::fmax(hi[k], vertices[3 * i + k]);
         }
     g.h = 2.0 * r / std::sqrt(3.0);
+    // Surface candidates lie on the triangles, so inside the box up to
+    // rounding.  One farther out would be clamped into an edge cell, and the
+    // phases keep two picks at least 2 r apart only while every candidate is
+    // within (2 h - 2 r) / 2 = 0.154 r of its cell: refuse those beyond 0.15 r.
+    if (surface) {
+        const double m = 0.15 * r;
+        for (int64_t i = 0; i < n_candidates; ++i)
+            for (int k = 0; k < 3; ++k)
+                if (candidates[3 * i + k] < g.lo[k] - m || candidates[3 * i + k] > hi[k] + m) return GS_ERR_ARG;
+    }
     double cells = 1.0;
     for (int k = 0; k < 3; ++k) {
         g.dims[k] = (int64_t)std::floor((hi[k] - g.lo[k]) / g.h) + 1;

@@ -108,3 +108,7 @@ def test_volume_sampler_refuses_bad_arguments_before_any_device_work():
     V2[1, 0] = float("nan")
     assert gs.gs_sample_volume(V2, T, C, 0.1)[0] == gs.GS_ERR_DOMAIN
     assert gs.gs_sample_volume(V * 1e6, T, C, 1e-6)[0] == gs.GS_ERR_ARG       # too many cells
+    # surface candidates must lie on the mesh: within 0.15 r of its bounding box
+    assert gs.gs_sample_surface(V, [[0.5, 0.5, -0.02]], 0.1)[0] == gs.GS_ERR_ARG
+    assert gs.gs_sample_surface(V, [[1.0, 0.5, 0.0], [1.02, 0.0, 0.0]], 0.1)[0] == gs.GS_ERR_ARG
+    assert gs.gs_sample_surface(V, [[0.1, 0.1, 0.0]], 0.0)[0] == gs.GS_ERR_ARG

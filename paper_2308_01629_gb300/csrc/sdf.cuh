@@ -20,6 +20,32 @@ __device__ __forceinline__ int sdf_components(int kind)
     return kind == GS_SDF_BOX_INTERIOR ? 6 : ((kind == GS_SDF_CONE_SHELL || kind == GS_SDF_SOLID_BOX) ? 1 : 0);
 }
 
+// True when the one-component SDF s (cone shell, solid box) is surely at
+// least r away from x, so that its contact test phi < r fails: a lower bound
+// of phi from the bounding rectangle of the cone's profile, or from the box's
+// largest per-axis excess (phi >= max_k (|x_k - c_k| - h_k) when outside),
+// with a margin of 1e-4 r + 1e-6 that covers the rounding of the full
+// evaluation, so skipping the evaluation never changes a decision.  A box
+// interior (six cheap walls) is never skipped.
+__device__ __forceinline__ bool sdf_far(const gs_sdf& s, float x, float y, float z, float r)
+{
+    const float* p = s.p;
+    const float m = r + 1.0e-4f * r + 1.0e-6f;
+    if (s.kind == GS_SDF_SOLID_BOX) {
+        const float q = fmaxf(fmaxf(fabsf(x - p[0]) - p[3], fabsf(y - p[1]) - p[4]), fabsf(z - p[2]) - p[5]);
+        return q > m;
+    }
+    if (s.kind == GS_SDF_CONE_SHELL) {
+        const float dx = x - p[0], dy = y - p[1];
+        const float rho = sqrtf(dx * dx + dy * dy);
+        const float rlo = fminf(p[3], p[5]), rhi = fmaxf(p[3], p[5]);
+        const float zlo = fminf(p[2], p[4]), zhi = fmaxf(p[2], p[4]);
+        const float q = fmaxf(fmaxf(rho - rhi, rlo - rho), fmaxf(z - zhi, zlo - z));
+        return q - p[6] > m;
+    }
+    return false;
+}
+
 // Component c of SDF s at x.
 __device__ __forceinline__ SdfHit sdf_eval(const gs_sdf& s, int c, float x, float y, float z)
 {

@@ -75,6 +75,7 @@ __device__ __forceinline__ void hr_boundary(float& x, float& y, float& z, float&
             wall_project(z, vz, b.p[5], -1.0f, b.vel[2], rh);
             continue;
         }
+        if (sdf_far(b, x, y, z, rh)) continue;
         SdfHit h = sdf_eval(b, 0, x, y, z);
         if (h.phi < rh) {
             float push = rh - h.phi;

@@ -63,6 +63,45 @@ def test_async_transfers_equal_synchronous_ones(graphs):
             np.testing.assert_array_equal(outs[k][n], ref[k][n], err_msg=f"round {k} {n}")
 
 
+def test_async_transfers_at_full_size():
+    """The 2M-particle digging bed, graphs on, as a caller streams it: every
+    round writes all four fields asynchronously, runs frames and reads the HR
+    fields asynchronously, without a sync in between (copies in flight on
+    their own streams while frames run): the results equal the synchronous
+    calls' bit for bit."""
+    import paper_2308_01629_gb300 as gs
+    F = _fields(gs)
+    sc = scenes.stir(scenes.digging(), seed=9, v_scale=0.1)
+    states = [_perturbed(sc, k) for k in range(3)]
+    ref_ctx = gs.Context(sc)
+    ref_ctx.set_graphs(True)
+    ref = []
+    for k, st in enumerate(states):
+        for n in FIELDS:
+            ref_ctx.write(F[n], st[n])
+        for _ in range(2):
+            ref_ctx.frame(DT, 4, 8)
+        ref.append({n: ref_ctx.read(F[n]) for n in ("hr_pos", "hr_vel")})
+    ref_ctx.close()
+    ctx = gs.Context(sc)
+    ctx.set_graphs(True)
+    outs = []
+    for k, st in enumerate(states):
+        for n in FIELDS:
+            ctx.write_async(F[n], st[n])
+        for _ in range(2):
+            ctx.frame(DT, 4, 8)
+        o = {n: np.zeros_like(st[n]) for n in ("hr_pos", "hr_vel")}
+        for n in ("hr_pos", "hr_vel"):
+            ctx.read_async(F[n], o[n])
+        outs.append(o)
+    ctx.sync()
+    ctx.close()
+    for k in range(len(states)):
+        for n in ("hr_pos", "hr_vel"):
+            np.testing.assert_array_equal(outs[k][n], ref[k][n], err_msg=f"round {k} {n}")
+
+
 def test_async_read_is_a_snapshot_and_last_write_wins():
     import paper_2308_01629_gb300 as gs
     F = _fields(gs)

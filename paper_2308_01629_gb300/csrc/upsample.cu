@@ -92,6 +92,19 @@ __device__ __forceinline__ void hr_boundary(float& x, float& y, float& z, float&
     }
 }
 
+// Order-preserving map of non-NaN floats onto unsigned integers (and back),
+// so that a warp's minimum or maximum of a float is one integer reduction.
+__device__ __forceinline__ unsigned f2ord(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    return u ^ ((u & 0x80000000u) ? 0xffffffffu : 0x80000000u);
+}
+
+__device__ __forceinline__ float ord2f(unsigned u)
+{
+    return __uint_as_float(u ^ ((u & 0x80000000u) ? 0x80000000u : 0xffffffffu));
+}
+
 // Lanes whose sub-cells (side h/2) are within one of the group leader's are
 // gathered together; a warp that straddles a jump in the cell order (the end
 // of a row or a slab, or particles that drifted since the last reorder)
@@ -145,17 +158,13 @@ __device__ __forceinline__ void upsample_item(const UpsampleArgs& a, int64_t ite
         const bool member = ((pending >> lane) & 1u) && abs(sx - gx0) <= 1 && abs(sy - gy0) <= 1 && abs(sz - gz0) <= 1;
         pending &= ~__ballot_sync(0xffffffffu, member);
 
-        float lx = member ? p.x : 3.0e38f, ly = member ? p.y : 3.0e38f, lz = member ? p.z : 3.0e38f;
-        float hx = member ? p.x : -3.0e38f, hy = member ? p.y : -3.0e38f, hz = member ? p.z : -3.0e38f;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
-            ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
-            lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
-            hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
-            hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
-            hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
-        }
+        // the group's bounding box (non-members sit at +-3e38)
+        const float lx = ord2f(__reduce_min_sync(0xffffffffu, f2ord(member ? p.x : 3.0e38f)));
+        const float ly = ord2f(__reduce_min_sync(0xffffffffu, f2ord(member ? p.y : 3.0e38f)));
+        const float lz = ord2f(__reduce_min_sync(0xffffffffu, f2ord(member ? p.z : 3.0e38f)));
+        const float hx = ord2f(__reduce_max_sync(0xffffffffu, f2ord(member ? p.x : -3.0e38f)));
+        const float hy = ord2f(__reduce_max_sync(0xffffffffu, f2ord(member ? p.y : -3.0e38f)));
+        const float hz = ord2f(__reduce_max_sync(0xffffffffu, f2ord(member ? p.z : -3.0e38f)));
         const int cx0 = cell_coord(lx - R, g.ox, g.inv_h, g.dx), cx1 = cell_coord(hx + R, g.ox, g.inv_h, g.dx);
         const int cy0 = cell_coord(ly - R, g.oy, g.inv_h, g.dy), cy1 = cell_coord(hy + R, g.oy, g.inv_h, g.dy);
         const int cz0 = cell_coord(lz - R, g.oz, g.inv_h, g.dz), cz1 = cell_coord(hz + R, g.oz, g.inv_h, g.dz);

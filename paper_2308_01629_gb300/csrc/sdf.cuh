@@ -21,11 +21,13 @@ __device__ __forceinline__ int sdf_components(int kind)
 }
 
 // True when the one-component SDF s (cone shell, solid box) is surely at
-// least r away from x, so that its contact test phi < r fails: a lower bound
-// of phi from the bounding rectangle of the cone's profile, or from the box's
-// largest per-axis excess (phi >= max_k (|x_k - c_k| - h_k) when outside),
-// with a margin of 1e-4 r + 1e-6 that covers the rounding of the full
-// evaluation, so skipping the evaluation never changes a decision.  A box
+// least r away from x, so that its contact test phi < r fails.  Solid box:
+// phi >= max_k (|x_k - c_k| - h_k) when outside, with the excesses computed
+// by the same float operations as sdf_eval (and sqrt(a^2 + ...) >= a in
+// float), plus a margin of 1e-4 r + 1e-6.  Cone shell: the distance to the
+// bounding rectangle of its profile, a different rounding path, so the
+// margin also grows with the magnitudes involved (1e-5 of them, far above
+// the evaluation's rounding).  Skipping never changes a decision.  A box
 // interior (six cheap walls) is never skipped.
 __device__ __forceinline__ bool sdf_far(const gs_sdf& s, float x, float y, float z, float r)
 {
@@ -41,7 +43,8 @@ __device__ __forceinline__ bool sdf_far(const gs_sdf& s, float x, float y, float
         const float rlo = fminf(p[3], p[5]), rhi = fmaxf(p[3], p[5]);
         const float zlo = fminf(p[2], p[4]), zhi = fmaxf(p[2], p[4]);
         const float q = fmaxf(fmaxf(rho - rhi, rlo - rho), fmaxf(z - zhi, zlo - z));
-        return q - p[6] > m;
+        const float scale = rho + rhi + fabsf(z) + fmaxf(fabsf(zlo), fabsf(zhi)) + fabsf(p[0]) + fabsf(p[1]);
+        return q - p[6] > m + 1.0e-5f * scale;
     }
     return false;
 }

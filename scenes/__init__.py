@@ -230,6 +230,20 @@ def digging(seed=SEED_BASE + 2, r_low=0.0089, ratio=40, size=1.0, depth=0.3):
                    bucket_index=1)
 
 
+def translated(sc, shift):
+    """A copy of a scene moved by shift (metres, per axis): particles, box and
+    its box-interior boundary; other SDFs are dropped."""
+    sh = np.asarray(shift, np.float32)
+    sc = dict(sc)
+    for k in ("lr_pos", "hr_pos"):
+        sc[k] = sc[k].copy()
+        sc[k][:, :3] += sh
+    sc["box_lo"] = tuple(float(np.float32(b) + s) for b, s in zip(sc["box_lo"], sh))
+    sc["box_hi"] = tuple(float(np.float32(b) + s) for b, s in zip(sc["box_hi"], sh))
+    sc["sdfs"] = [box_interior(sc["box_lo"], sc["box_hi"], mu_s=sc["mu_s"], mu_k=sc["mu_k"])]
+    return sc
+
+
 def column(seed=SEED_BASE + 3, n_low=4000, r_low=0.01, ratio=16, z0=0.1):
     """Falling column (10 x 10 footprint) in a 0.6 m box, lowest layer
     centred z0 above the floor."""

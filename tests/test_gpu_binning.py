@@ -19,7 +19,8 @@ def _oracle_grid(orc, sc):
                     np.float32(sc["box_hi"]).astype(float))
 
 
-@pytest.mark.parametrize("make", [scenes.cube, scenes.funnel, scenes.digging])
+@pytest.mark.parametrize("make", [scenes.cube, scenes.funnel, scenes.digging,
+                                  lambda: scenes.translated(scenes.cube(), (-0.25, -0.25, -0.25))])
 def test_grid_contract_matches_oracle(orc, make):
     sc = make()
     gs, ctx = _ctx(sc)
@@ -43,7 +44,13 @@ def _check_lr_binning(orc, sc, ctx, gs):
     assert np.all(start[nc + 1:] == len(idx))      # the scene's padding cell is empty
 
 
-@pytest.mark.parametrize("make", [scenes.cube, scenes.funnel, scenes.digging])
+def _cube_at_origin():
+    """The cube moved to straddle the origin: a negative grid origin and
+    coordinates of both signs."""
+    return scenes.translated(scenes.cube(), (-0.25, -0.25, -0.25))
+
+
+@pytest.mark.parametrize("make", [scenes.cube, scenes.funnel, scenes.digging, _cube_at_origin])
 def test_lr_binning_bit_exact(orc, make):
     sc = make()
     gs, ctx = _ctx(sc)

@@ -57,6 +57,8 @@ def floor_and_bucket(sc):
 CASES = {
     "cube": lambda: scenes.cube(),
     "cube_stir": lambda: scenes.stir(scenes.cube(), seed=31, v_scale=0.3),
+    # the same cube straddling the origin (negative grid origin, coordinates of both signs)
+    "cube_origin": lambda: scenes.translated(scenes.stir(scenes.cube(), seed=31, v_scale=0.3), (-0.25, -0.25, -0.25)),
     "funnel": lambda: scenes.stir(scenes.funnel(), seed=32, v_scale=0.2),
     "digging_bucket": lambda: floor_and_bucket(scenes.stir(scenes.digging(), seed=33, v_scale=0.1)),
 }

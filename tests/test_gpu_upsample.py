@@ -41,14 +41,7 @@ def test_scene_straddling_the_origin(orc):
     0.25]^3): HR positions of both signs and near zero, a negative grid
     origin; the warp groups' bounding boxes (integer reductions over an
     order-preserving map of the floats) and the grid contract hold there."""
-    sc = dict(scenes.stir(scenes.cube(), seed=13))
-    sh = np.float32(-0.25)
-    for k in ("lr_pos", "hr_pos"):
-        sc[k] = sc[k].copy()
-        sc[k][:, :3] += sh
-    sc["box_lo"] = tuple(float(np.float32(b) + sh) for b in sc["box_lo"])
-    sc["box_hi"] = tuple(float(np.float32(b) + sh) for b in sc["box_hi"])
-    sc["sdfs"] = [scenes.box_interior(sc["box_lo"], sc["box_hi"], mu_s=0.5, mu_k=0.5)]
+    sc = scenes.translated(scenes.stir(scenes.cube(), seed=13), (-0.25, -0.25, -0.25))
     assert (sc["hr_pos"][:, :3] < 0).any() and (sc["hr_pos"][:, :3] > 0).any()
     x, v = _run(sc)
     check_hr(sc, DT, x, v, _ref(orc, sc, mode=0))
